@@ -1,0 +1,260 @@
+"""Energy-DG semi-discretisation, constant c^2, Cartesian elements (oracle).
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
+
+Nodal form, written from the element-wise variational statement (Eqs. DG1,
+DG2, DG1_extra of Section 2.2) and the fluxes of Section 2.2.1, element by
+element.  Where the printed matrix form (Eqs. DG_matrix1/2 of Section 3)
+differs in the sign of the dissipative B and C terms, the variational
+statement is followed; the energy identities in the tests pin the choice.
+
+Per element, with outward normal n on each face and traces
+  v_in, d_in = n . grad u_in          (this element)
+  v_out, d_out = n_out . grad u_out   (the neighbour, its own outward normal)
+the fluxes of Section 2.2.1 with alpha = 1/2 in normal form are
+  v*  = (v_in + v_out)/2 - beta (d_in + d_out)
+  q*  = n . (grad u)* = (d_in - d_out)/2 - tau (v_in - v_out)
+central: beta = tau = 0; upwind: beta = xi/2, tau = 1/(2 xi).
+Then (c^2 constant, divided out of Eq. DG1):
+  r_u = sum_faces (n . grad phi)|face (x) M_perp (v* - v_in)
+  r_v = -c^2 S U + sum_faces c^2 phi|face (x) M_perp q*
+  M dV/dt = r_v
+  S (dU/dt - V) = r_u,  w^T (dU/dt - V) = 0,  w = M 1      (Eq. DG1_extra)
+M_perp is the 1-D mass matrix along the face (both neighbours share the
+transverse GD basis); in 1-D it is the scalar 1.
+Homogeneous Dirichlet data u = 0 enters as the mirror state
+  v_out = -v_in, d_out = -d_in  (so v* = 0, q* = d_in - 2 tau v_in).
+
+Layout: 1-D U[e, i]; 2-D U[ey, ex, j, i] (i along x), element e = ey*nx+ex.
+"""
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import gd_basis
+
+
+@dataclass
+class Problem:
+    dim: int
+    n: tuple            # elements per direction
+    N: int              # GD cells per element per direction
+    p: int              # odd GD degree
+    lo: tuple = (0.0, 0.0)
+    hi: tuple = (1.0, 1.0)
+    periodic: tuple = (False, False)
+    flux: str = "upwind"   # "central" | "upwind"
+    xi: float = 0.0        # upwind splitting; <= 0 means xi = c
+    c2: float = 1.0
+
+    @property
+    def n1(self):
+        return self.N + 1
+
+    def H(self, k):
+        return (self.hi[k] - self.lo[k]) / self.n[k]
+
+    def beta_tau(self):
+        if self.flux == "central":
+            return 0.0, 0.0
+        if self.flux == "upwind":
+            xi = self.xi if self.xi > 0 else np.sqrt(self.c2)
+            return 0.5 * xi, 0.5 / xi
+        raise ValueError("unknown flux " + str(self.flux))
+
+
+@dataclass
+class Operators:
+    """Physical 1-D operators per direction plus the element Kronecker forms."""
+    M1: list = field(default_factory=list)   # H * M_hat
+    S1: list = field(default_factory=list)   # S_hat / H
+    aL: list = field(default_factory=list)   # n . grad phi on the - face
+    aR: list = field(default_factory=list)   # n . grad phi on the + face
+    M: np.ndarray = None
+    S: np.ndarray = None
+
+
+def operators(prob):
+    Mh, Sh = gd_basis.mass_stiffness(prob.p, prob.N)
+    _, _, dphiL, dphiR = gd_basis.face_data(prob.p, prob.N)
+    ops = Operators()
+    for k in range(prob.dim):
+        H = prob.H(k)
+        ops.M1.append(H * Mh)
+        ops.S1.append(Sh / H)
+        ops.aL.append(-dphiL / H)   # outward normal -x_k
+        ops.aR.append(dphiR / H)    # outward normal +x_k
+    if prob.dim == 1:
+        ops.M, ops.S = ops.M1[0], ops.S1[0]
+    else:
+        # element index a = j*n1 + i (i along x): kron(A_y, B_x)
+        Mx, My, Sx, Sy = ops.M1[0], ops.M1[1], ops.S1[0], ops.S1[1]
+        ops.M = np.kron(My, Mx)
+        ops.S = np.kron(My, Sx) + np.kron(Sy, Mx)
+    return ops
+
+
+def _fluxes(v_in, d_in, v_out, d_out, beta, tau):
+    vstar = 0.5 * (v_in + v_out) - beta * (d_in + d_out)
+    qstar = 0.5 * (d_in - d_out) - tau * (v_in - v_out)
+    return vstar, qstar
+
+
+def _neighbour_traces(vm, dm, vp, dp, periodic):
+    """Given per-element traces on the - face (vm, dm) and + face (vp, dp)
+    along axis 0 (the element index in the face-normal direction), return the
+    outside states seen by each element's - and + faces."""
+    if periodic:
+        out_p_v, out_p_d = np.roll(vm, -1, axis=0), np.roll(dm, -1, axis=0)
+        out_m_v, out_m_d = np.roll(vp, 1, axis=0), np.roll(dp, 1, axis=0)
+    else:
+        out_p_v, out_p_d = np.empty_like(vp), np.empty_like(dp)
+        out_m_v, out_m_d = np.empty_like(vm), np.empty_like(dm)
+        out_p_v[:-1], out_p_d[:-1] = vm[1:], dm[1:]
+        out_m_v[1:], out_m_d[1:] = vp[:-1], dp[:-1]
+        # homogeneous Dirichlet mirror state on the domain boundary
+        out_p_v[-1], out_p_d[-1] = -vp[-1], -dp[-1]
+        out_m_v[0], out_m_d[0] = -vm[0], -dm[0]
+    return out_m_v, out_m_d, out_p_v, out_p_d
+
+
+def residuals(prob, U, V, ops=None):
+    """(r_u, r_v) of the element equations for nodal states U, V."""
+    ops = operators(prob) if ops is None else ops
+    beta, tau = prob.beta_tau()
+    c2 = prob.c2
+    n1 = prob.n1
+    if prob.dim == 1:
+        U = U.reshape(prob.n[0], n1)
+        V = V.reshape(prob.n[0], n1)
+        aL, aR = ops.aL[0], ops.aR[0]
+        vm, vp = V[:, 0], V[:, -1]
+        dm, dp = U @ aL, U @ aR
+        om_v, om_d, op_v, op_d = _neighbour_traces(vm, dm, vp, dp, prob.periodic[0])
+        vs_m, qs_m = _fluxes(vm, dm, om_v, om_d, beta, tau)
+        vs_p, qs_p = _fluxes(vp, dp, op_v, op_d, beta, tau)
+        r_u = np.outer(vs_m - vm, aL) + np.outer(vs_p - vp, aR)
+        r_v = -c2 * U @ ops.S.T
+        r_v[:, 0] += c2 * qs_m
+        r_v[:, -1] += c2 * qs_p
+        return r_u, r_v
+
+    nx, ny = prob.n
+    U = U.reshape(ny, nx, n1, n1)
+    V = V.reshape(ny, nx, n1, n1)
+    Mx, My = ops.M1
+    r_u = np.zeros_like(U)
+    r_v = -c2 * (U.reshape(ny * nx, n1 * n1) @ ops.S.T).reshape(U.shape)
+
+    # x faces: traces are functions of y (index j); neighbours along ex.
+    aL, aR = ops.aL[0], ops.aR[0]
+    vm, vp = V[..., :, 0], V[..., :, -1]            # (ny, nx, n1_j)
+    dm = np.einsum("yxji,i->yxj", U, aL)
+    dp = np.einsum("yxji,i->yxj", U, aR)
+    t = [np.swapaxes(a, 0, 1) for a in (vm, dm, vp, dp)]   # element axis first
+    om_v, om_d, op_v, op_d = [np.swapaxes(a, 0, 1) for a in
+                              _neighbour_traces(*t, prob.periodic[0])]
+    vs_m, qs_m = _fluxes(vm, dm, om_v, om_d, beta, tau)
+    vs_p, qs_p = _fluxes(vp, dp, op_v, op_d, beta, tau)
+    gm = (vs_m - vm) @ My.T            # M_y (v* - v_in), per element
+    gp = (vs_p - vp) @ My.T
+    r_u += np.einsum("yxj,i->yxji", gm, aL) + np.einsum("yxj,i->yxji", gp, aR)
+    r_v[..., :, 0] += c2 * (qs_m @ My.T)
+    r_v[..., :, -1] += c2 * (qs_p @ My.T)
+
+    # y faces: traces are functions of x (index i); neighbours along ey.
+    aL, aR = ops.aL[1], ops.aR[1]
+    vm, vp = V[..., 0, :], V[..., -1, :]            # (ny, nx, n1_i)
+    dm = np.einsum("yxji,j->yxi", U, aL)
+    dp = np.einsum("yxji,j->yxi", U, aR)
+    om_v, om_d, op_v, op_d = _neighbour_traces(vm, dm, vp, dp, prob.periodic[1])
+    vs_m, qs_m = _fluxes(vm, dm, om_v, om_d, beta, tau)
+    vs_p, qs_p = _fluxes(vp, dp, op_v, op_d, beta, tau)
+    gm = (vs_m - vm) @ Mx.T
+    gp = (vs_p - vp) @ Mx.T
+    r_u += np.einsum("yxi,j->yxji", gm, aL) + np.einsum("yxi,j->yxji", gp, aR)
+    r_v[..., 0, :] += c2 * (qs_m @ Mx.T)
+    r_v[..., -1, :] += c2 * (qs_p @ Mx.T)
+    ne = nx * ny
+    return r_u.reshape(ne, n1 * n1), r_v.reshape(ne, n1 * n1)
+
+
+def constrained_matrix(M, S):
+    """S with its first row replaced by w^T = (M 1)^T (Eq. DG1_extra)."""
+    A = S.copy()
+    A[0, :] = M @ np.ones(M.shape[0])
+    return A
+
+
+def solve(ops, V, r_u, r_v):
+    """dU/dt = V + y with S y = r_u, w^T y = 0;  dV/dt = M^-1 r_v.
+    Dense direct solves (library LU / Cholesky as primitives)."""
+    A = constrained_matrix(ops.M, ops.S)
+    b = r_u.copy()
+    b[:, 0] = 0.0
+    y = np.linalg.solve(A, b.T).T
+    L = np.linalg.cholesky(ops.M)
+    z = np.linalg.solve(L, r_v.T)
+    Vt = np.linalg.solve(L.T, z).T
+    return V.reshape(y.shape) + y, Vt
+
+
+def time_derivative(prob, U, V, ops=None):
+    """(dU/dt, dV/dt) of the semi-discretisation at nodal state (U, V)."""
+    ops = operators(prob) if ops is None else ops
+    r_u, r_v = residuals(prob, U, V, ops)
+    return solve(ops, V, r_u, r_v)
+
+
+def energy(prob, U, V, ops=None):
+    """E = 1/2 sum_e (V_e^T M V_e + c^2 U_e^T S U_e)."""
+    ops = operators(prob) if ops is None else ops
+    ne = int(np.prod(prob.n))
+    U = U.reshape(ne, -1)
+    V = V.reshape(ne, -1)
+    return 0.5 * (np.einsum("ea,ab,eb->", V, ops.M, V)
+                  + prob.c2 * np.einsum("ea,ab,eb->", U, ops.S, U))
+
+
+def node_coordinates(prob):
+    """Physical coordinates of every element's GD nodes, in the layout of U.
+    1-D: x[e, i];  2-D: (x, y) each [ey, ex, j, i]."""
+    n1 = prob.n1
+    r = np.arange(n1) / prob.N
+    if prob.dim == 1:
+        H = prob.H(0)
+        x0 = prob.lo[0] + H * np.arange(prob.n[0])
+        return (x0[:, None] + H * r[None, :],)
+    nx, ny = prob.n
+    Hx, Hy = prob.H(0), prob.H(1)
+    x0 = prob.lo[0] + Hx * np.arange(nx)
+    y0 = prob.lo[1] + Hy * np.arange(ny)
+    X = np.broadcast_to(x0[None, :, None, None] + Hx * r[None, None, None, :],
+                        (ny, nx, n1, n1))
+    Y = np.broadcast_to(y0[:, None, None, None] + Hy * r[None, None, :, None],
+                        (ny, nx, n1, n1))
+    return X.copy(), Y.copy()
+
+
+def dense_operator(prob):
+    """Global matrix L with d/dt [U; V] = L [U; V] assembled column by column
+    from unit vectors (brute force on tiny meshes, used by the tests)."""
+    ops = operators(prob)
+    ndof = int(np.prod(prob.n)) * prob.n1 ** prob.dim
+    L = np.zeros((2 * ndof, 2 * ndof))
+    for c in range(2 * ndof):
+        z = np.zeros(2 * ndof)
+        z[c] = 1.0
+        Ut, Vt = time_derivative(prob, z[:ndof], z[ndof:], ops)
+        L[:ndof, c] = Ut.ravel()
+        L[ndof:, c] = Vt.ravel()
+    return L
+
+
+def energy_matrix(prob):
+    """Block diagonal (c^2 S, M) over all elements: E = 1/2 Z^T E Z."""
+    ops = operators(prob)
+    ne = int(np.prod(prob.n))
+    I = np.eye(ne)
+    return np.block([[prob.c2 * np.kron(I, ops.S), np.zeros((ne * ops.S.shape[0],) * 2)],
+                     [np.zeros((ne * ops.S.shape[0],) * 2), np.kron(I, ops.M)]])

@@ -1,0 +1,322 @@
+#!/usr/bin/env python
+"""Benchmark of the energy-DG / Galerkin-difference hot path on GB300.
+
+Metric: DOF-steps/s = (elements x (N+1)^d) x RK4 steps / second (Section
+3.3 counts DOF this way).  One benchmark step = R classic RK4 steps of the
+whole semi-discretisation (traces, fluxes, lifts, stiffness, constrained
+u_t solve, mass inversion, stage combination) through gdg_step.
+
+Default workload: 2-D constant coefficient u_tt = Laplace u on [0,1]^2,
+64 x 64 elements of 8 x 8 GD cells, p = 5, upwind flux, u = 0 on the
+boundary, standing mode cos(sqrt2 pi t) sin(pi x) sin(pi y), dt = 0.15 h
+(0.8 of the largest RK4-stable step for the upwind p = 5 operator).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gdg|reference]
+Under torchrun every rank advances its own replica of the workload (the
+benchmark runs independent replicas: no data exchanged between GPUs).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(dim=2, n=(64, 64), N=8, p=5, flux="upwind", T=1.0, cfl=0.15)
+WORKLOAD_NAME = ("2-D constant-coefficient wave, 64x64 elements of 8x8 GD cells, p=5, upwind, "
+                 "Dirichlet, standing mode; modified-basis diagonalised route")
+
+
+def dof(w=WORKLOAD):
+    nel = 1
+    for k in w["n"]:
+        nel *= k
+    return nel * (w["N"] + 1) ** w["dim"]
+
+
+def flops_per_stage_launch(w=WORKLOAD):
+    """Algorithmic FP64 flops of one fused stage launch (an FMA counts 2):
+    per element 2-D: fluxes 4 faces x n1 points x 11, per modal entry 26
+    (lifts 7 + 9, diagonal solve 2, RK accumulate / next input 8), traces
+    of the next input 2 directions x 4 dots x n1 x n1 x 2."""
+    n1 = w["N"] + 1
+    nel = w["n"][0] * w["n"][1]
+    return nel * (44 * n1 + 26 * n1 * n1 + 16 * n1 * n1)
+
+
+# FP64 peak derived from unit counts and clock: 152 SMs x 2070 MHz x 4 FP64
+# flop/clk/SM (2 FP64 FMA lanes per SM per clock) = 1.259 TFLOP/s; an FMA-chain
+# probe measured 1.196 TFLOP/s on this GPU.
+FP64_PEAK_TFLOPS = 152 * 2.070e9 * 4 / 1e12
+
+
+def _env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.f = None
+
+    def start(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                smax = float(r[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, r[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(target_s=15.0):
+    """Time the FP64 oracle (as it stands) on the host cores, single thread,
+    on a bounded sample: a few RK4 steps of the full benchmark mesh."""
+    code = r"""
+import json, sys, time
+sys.path.insert(0, %r)
+import numpy as np
+from oracle import dg_const as dc, timeint as ti
+from paper_2105_01722_gb300 import inputs
+w = %r
+prob = dc.Problem(dim=w["dim"], n=tuple(w["n"]), N=w["N"], p=w["p"], flux=w["flux"])
+ops = dc.operators(prob)
+X, Y = inputs.cartesian_nodes(tuple(w["n"]), w["N"])
+U, V = inputs.standing_mode_2d(X, Y)
+ne = w["n"][0] * w["n"][1]
+U, V = U.reshape(ne, -1), V.reshape(ne, -1)
+dt = w["cfl"] / (w["n"][0] * w["N"])
+f = lambda t, U, V: dc.time_derivative(prob, U, V, ops)
+t0 = time.perf_counter(); U, V = ti.rk4_step(f, U, V, 0.0, dt); t1 = time.perf_counter()
+steps = max(1, int(%f / max(t1 - t0, 1e-6)))
+t0 = time.perf_counter()
+U, V = ti.integrate(f, U, V, dt, dt, steps)
+t1 = time.perf_counter()
+print(json.dumps({"steps": steps, "seconds": t1 - t0}))
+""" % (ROOT, WORKLOAD, target_s)
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+    if r.returncode != 0:
+        return {"value": None, "unit": "DOF-steps/s", "cores": 1, "kind": "oracle",
+                "sample": "failed: " + r.stderr.strip().splitlines()[-1] if r.stderr else "failed"}
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": dof() * d["steps"] / d["seconds"], "unit": "DOF-steps/s", "cores": 1,
+            "kind": "oracle",
+            "sample": "%d RK4 steps of the full 64x64 p=5 mesh (%.1f s, numpy FP64, 1 thread)"
+                      % (d["steps"], d["seconds"])}
+
+
+def run_reference(args):
+    rank, world, _ = _env_rank()
+    if rank != 0:
+        return 0
+    per = []
+    base = None
+    for _ in range(args.warmup + args.steps):
+        base = cpu_baseline(target_s=max(2.0, 120.0 / (args.steps + args.warmup)))
+        per.append(base)
+    timed = per[args.warmup:]
+    vals = [b["value"] for b in timed if b["value"]]
+    value = statistics.mean(vals) if vals else None
+    line = {"impl": "reference", "metric": "DOF-steps/s", "value": value, "unit": "DOF-steps/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD_NAME, "elements": list(WORKLOAD["n"]), "N": WORKLOAD["N"],
+                       "p": WORKLOAD["p"], "dof": dof()},
+            "cpu_baseline": {"value": value, "unit": "DOF-steps/s", "cores": 1, "kind": "oracle",
+                             "sample": timed[-1]["sample"] if timed else ""},
+            "e2e": {"value": value, "unit": "DOF-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_gdg(args):
+    import numpy as np
+    import torch
+    from paper_2105_01722_gb300 import gdg, inputs
+
+    rank, world, local = _env_rank()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    w = WORKLOAD
+    R = args.rk_steps
+    h = 1.0 / (w["n"][0] * w["N"])
+    dt = w["cfl"] * h
+    pb = gdg.make_problem(2, w["n"], w["N"], w["p"], flux=gdg.FLUX_UPWIND, c2=1.0)
+    ctx = gdg.Context(pb)
+    X, Y = inputs.cartesian_nodes(w["n"], w["N"])
+    U0, V0 = inputs.standing_mode_2d(X, Y)
+    u = torch.tensor(U0.ravel(), device=dev)
+    v = torch.tensor(V0.ravel(), device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 512 MB > L2
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        ctx.step(u, v, 0.0, dt, R)
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(dev.index if dev.index is not None else 0)
+    sampler.start()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(float(k))                      # evict the state from L2 between timed steps
+        evs[k][0].record(stream)
+        ctx.step(u, v, 0.0, dt, R)
+        evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    wall1 = time.perf_counter()
+    clocks = sampler.stop()
+    ms = [a.elapsed_time(b) for a, b in evs]
+    total_ms = sum(ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * dof() * R * args.steps / (total_ms / 1e3)
+
+    # kernel-level pass: events around every launch (no graph), same work
+    ctx.profile(True)
+    for k in range(max(2, min(args.steps, 5))):
+        flush.fill_(float(k))
+        ctx.step(u, v, 0.0, dt, R)
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    st_n, st_ms = prof.get("stage", (1, float("nan")))
+    stage_ms = st_ms / st_n
+    achieved = flops_per_stage_launch() / (stage_ms / 1e3) / 1e12
+
+    # end to end through the C ABI with host buffers (pinned), copies timed
+    hu = torch.tensor(U0.ravel()).pin_memory()
+    hv = torch.tensor(V0.ravel()).pin_memory()
+    ctx.step_host(hu, hv, 0.0, dt, R)
+    e2e_t = []
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.step_host(hu, hv, 0.0, dt, R)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_s = sum(e2e_t)
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_val = world * dof() * R * args.steps / e2e_s
+
+    # accuracy of the FP64 form at T = 1: M-norm distance to the GD
+    # interpolant of the exact solution, evaluated by the library's energy kernel
+    ua = torch.tensor(U0.ravel(), device=dev)
+    va = torch.tensor(V0.ravel(), device=dev)
+    nT = int(round(w["T"] / dt))
+    ctx.step(ua, va, 0.0, dt, nT)
+    ue, _ = inputs.standing_mode_2d(X, Y, nT * dt)
+    diff = ua - torch.tensor(ue.ravel(), device=dev)
+    l2 = float(np.sqrt(2.0 * ctx.energy(torch.zeros_like(diff), diff)))
+
+    line = None
+    if rank == 0:
+        cpu = cpu_baseline() if (world == 1 and not args.no_cpu_baseline) else None
+        line = {
+            "metric": "DOF-steps/s", "value": value, "unit": "DOF-steps/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD_NAME, "elements": list(w["n"]), "N": w["N"], "p": w["p"],
+                       "dof": dof(), "rk4_steps_per_step": R, "dt": dt,
+                       "form": "FP64 modal (modified basis)",
+                       "l2": "flushed between timed steps (512 MB write; state is 5.3 MB)"},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                         "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                         "kernel": "k_stage2 (fused RK stage)", "avg_launch_us": stage_ms * 1e3,
+                         "flops_per_launch": flops_per_stage_launch(),
+                         "peak_source": "FP64 nominal: 152 SM x 2070 MHz x 4 flop/clk"},
+            "kernels": {k: {"launches": n, "ms": t} for k, (n, t) in prof.items()},
+            "gpu_launches": 4 * R * args.steps + 3 * args.steps,
+            "e2e": {"value": e2e_val, "unit": "DOF-steps/s", "h2d_bytes_per_step": 2 * dof() * 8,
+                    "d2h_bytes_per_step": 2 * dof() * 8},
+            "clocks": clocks,
+            "accuracy": {"T": nT * dt, "l2_error_vs_interpolant": l2},
+            "wall_s": wall1 - wall0,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gdg", "reference"], default="gdg")
+    ap.add_argument("--rk-steps", type=int, default=64)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gdg(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,241 @@
+/*
+ * gdg.h -- C ABI of the GB300 energy-based DG / Galerkin-difference library.
+ *
+ * The library advances the second-order wave equation
+ *     u_t = v,   v_t = div(c^2 grad u)                       (Section 2, Eqs. 1-2)
+ * discretised by the energy-based DG method on tensor-product elements with
+ * the Galerkin-difference (GD) basis of degree p (odd) on N cells per element
+ * per direction (Section 2.1), interelement fluxes of Section 2.2.1, and
+ * classic RK4 in time (Sections 3.3, 6).
+ *
+ * Conventions for every call
+ *   - Return value: GDG_OK (0) or a negative GDG_E* status.  No call aborts
+ *     or exits; after GDG_ECUDA the CUDA error text is in gdg_last_error().
+ *   - "device" pointers are CUDA global-memory addresses on the context's
+ *     device, owned by the caller (e.g. torch tensors); "host" pointers are
+ *     ordinary process memory, also caller-owned.  Nothing is retained after
+ *     a call returns except what gdg_create copies.
+ *   - stream is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls are asynchronous on that stream unless they return a
+ *     host value (gdg_energy, gdg_pcg statistics, gdg_step_host).
+ *   - A context is not thread-safe; use one context per stream at a time.
+ *   - Nodal layout of a field (doubles): 1-D u[e*n1 + i];
+ *     2-D u[((ey*nx + ex)*n1 + j)*n1 + i], i along x (fastest), n1 = N+1,
+ *     value at the GD node (x_e + i*Hx/N, y_e + j*Hy/N).  Element interface
+ *     nodes are duplicated (the method is discontinuous between elements).
+ */
+#ifndef GDG_H
+#define GDG_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define GDG_OK           0
+#define GDG_EINVAL      -1   /* bad argument: even p, p > N, null pointer, bad enum, size mismatch */
+#define GDG_ENOMEM      -2   /* device or host allocation failed                                */
+#define GDG_ECUDA       -3   /* CUDA runtime error (text in gdg_last_error)                      */
+#define GDG_ENOCONV     -4   /* PCG hit pcg_maxit; result = last iterate, statistics filled      */
+#define GDG_ETIMEOUT    -5   /* a bounded device-side wait gave up                               */
+#define GDG_ENONFINITE  -6   /* NaN or Inf detected (energy, PCG residual)                       */
+#define GDG_EUNSUPPORTED -7  /* valid request this build does not provide (e.g. N+1 > 16)        */
+
+/* ---- enums ----------------------------------------------------------- */
+enum { GDG_BC_DIRICHLET = 0, GDG_BC_PERIODIC = 1 };
+/* Section 2.2.1: central alpha=1/2, beta=tau=0; upwind alpha=1/2, beta=xi/2, tau=1/(2 xi). */
+enum { GDG_FLUX_CENTRAL = 0, GDG_FLUX_UPWIND = 1 };
+/* Coefficients: constant c^2 on a Cartesian box mesh, or c^2 and the element
+ * geometry sampled at every element's GD nodes (Section 7: variable speed of
+ * sound or mapped, non-Cartesian elements). */
+enum { GDG_COEF_CONST = 0, GDG_COEF_NODAL = 1 };
+/* Local solves: modified-basis diagonalisation (Section 3.2, constant
+ * coefficient Cartesian only) or element-local preconditioned CG (Section 7.1). */
+enum { GDG_SOLVE_DIAG = 0, GDG_SOLVE_PCG = 1 };
+/* PCG preconditioner: frozen-coefficient diagonalisation, none (plain CG). */
+enum { GDG_PC_FDM = 0, GDG_PC_NONE = 1 };
+/* Arithmetic of the element contractions.  GDG_FP64 everywhere, or
+ * GDG_FP32 contractions with FP64 iterative refinement of every solve
+ * (FP64 state, residuals, inner products and energy). */
+enum { GDG_FP64 = 0, GDG_MIXED = 1 };
+/* State representation used inside gdg_step for the diagonalised route:
+ * modal coefficients U = Psi Ubar (Section 3.2) or nodal values. */
+enum { GDG_ROUTE_MODAL = 0, GDG_ROUTE_NODAL = 1 };
+/* Operator selector of gdg_mass_solve / gdg_pcg. */
+enum { GDG_OP_M = 0, GDG_OP_S = 1 };
+
+typedef struct gdg_ctx gdg_ctx;   /* opaque; owns uploaded operators and scratch */
+
+typedef struct {
+    int dim;             /* 1 or 2                                                   */
+    int n_elem[2];       /* elements per direction (n); n_elem[1] ignored for dim 1  */
+    int N;               /* GD cells per element per direction, n1 = N+1 <= 16       */
+    int p;               /* odd GD degree, 1 <= p <= N                               */
+    double lo[2], hi[2]; /* box [lo, hi] of the (reference) mesh                     */
+    int bc[2];           /* per direction: GDG_BC_DIRICHLET (u = 0) or _PERIODIC     */
+    int flux;            /* GDG_FLUX_*                                               */
+    double xi;           /* upwind splitting; <= 0 means xi = c (local c for NODAL)  */
+    int coef;            /* GDG_COEF_*                                               */
+    double c2;           /* constant c^2 (GDG_COEF_CONST)                            */
+    const double *x_nodes;  /* host, GDG_COEF_NODAL (2-D): physical x at every      */
+    const double *y_nodes;  /*   element node, nodal layout; copied by gdg_create    */
+    const double *c2_nodes; /* host, GDG_COEF_NODAL: c^2 at every element node       */
+    int nquad;           /* Gauss points per GD cell per direction (0: p+1)          */
+    int solver;          /* GDG_SOLVE_* (GDG_COEF_NODAL requires GDG_SOLVE_PCG)      */
+    int precond;         /* GDG_PC_*                                                 */
+    double pcg_rtol;     /* stop when ||r||_2 <= rtol ||b||_2 per element system     */
+    int pcg_maxit;       /* iteration cap per element system                         */
+    int precision;       /* GDG_FP64 or GDG_MIXED                                    */
+    int route;           /* GDG_ROUTE_* (diagonalised route only)                    */
+    int refine_max;      /* GDG_MIXED: maximum FP64 refinement sweeps per solve      */
+    double refine_rtol;  /* GDG_MIXED: inner FP32 PCG relative tolerance             */
+} gdg_problem;
+
+typedef struct {
+    int max_iters;        /* largest per-element iteration count of the last call  */
+    double mean_iters;    /* mean over elements                                    */
+    double max_rel_resid; /* largest final ||r||/||b|| (true FP64 residual)        */
+    int unconverged;      /* number of element systems that hit pcg_maxit          */
+} gdg_pcg_stats;
+
+/* Human-readable text of a status code (static storage). */
+const char *gdg_status_string(int status);
+
+/* Text of the last error recorded on ctx ("" if none). */
+const char *gdg_last_error(const gdg_ctx *ctx);
+
+/*
+ * 1-D GD basis on the reference element [0,1] (host only; Sections 2.1, 2.1.1,
+ * 3.1, 3.2).  Nodes r_i = i/N; on cell k the basis is the Lagrange basis of
+ * the p+1 nodes starting at s(k) = min(max(k-q+1, 0), N-p), q = (p+1)/2,
+ * which is the GD basis with the extrapolation boundary modification.
+ * Outputs (caller-owned host arrays, row-major, any may be NULL):
+ *   M, S [n1*n1]  mass int phi_k phi_l and stiffness int phi_k' phi_l'
+ *   phiL, phiR [n1]  basis values at r = 0 and r = 1
+ *   dphiL, dphiR [n1]  one-sided derivatives at r = 0 and r = 1
+ *   Psi [n1*n1], lambda [n1]  S Psi = M Psi diag(lambda), Psi^T M Psi = I,
+ *                     lambda ascending with lambda[0] = 0 (constant mode),
+ *                     Psi[i*n1 + k] = component i of eigenvector k.
+ * Errors: GDG_EINVAL for even p, p < 1, N < p; GDG_EUNSUPPORTED for N+1 > 16.
+ */
+int gdg_basis_1d(int p, int N, double *M, double *S, double *phiL, double *phiR,
+                 double *dphiL, double *dphiR, double *Psi, double *lambda);
+
+/*
+ * Validate *pb, build the element operators on the host (basis, Kronecker
+ * factors and modified basis for GDG_COEF_CONST; quadrature assembly of
+ * the element mass and stiffness matrices and face data on the device for
+ * GDG_COEF_NODAL, Section 7.1) and allocate device scratch on the current
+ * CUDA device.  Host arrays in *pb are copied.  *out receives the context.
+ * Errors: GDG_EINVAL, GDG_EUNSUPPORTED, GDG_ENOMEM, GDG_ECUDA.
+ */
+int gdg_create(const gdg_problem *pb, gdg_ctx **out);
+
+/* Free the context and its device memory (synchronises the device). */
+int gdg_destroy(gdg_ctx *ctx);
+
+/* Doubles per field: n^d * (N+1)^d (the paper's DOF count, Section 3.3). */
+long long gdg_state_len(const gdg_ctx *ctx);
+
+/*
+ * Semi-discrete time derivative (Eqs. DG1, DG2, DG1_extra with the fluxes of
+ * Section 2.2.1): du = dU/dt, dv = dV/dt at the nodal state (u, v).
+ * Device pointers of gdg_state_len doubles; du, dv must not alias u, v.
+ * GDG_SOLVE_PCG contexts use the PCG settings of the problem and may
+ * return GDG_ENOCONV (results are then the last iterates).
+ */
+int gdg_rhs(gdg_ctx *ctx, const double *u, const double *v, double *du, double *dv,
+            void *stream);
+
+/*
+ * Element-local solve with the diagonalised operators (Section 3.2):
+ *   which = GDG_OP_M:  x = M^-1 b               (M = Psi^-T Psi^-1)
+ *   which = GDG_OP_S:  S x = b, w^T x = 0, w = M 1 (the u_t system of
+ *                      Eq. DG1 with Eq. DG1_extra; b must satisfy 1^T b = 0
+ *                      per element, as every r_u does)
+ * b, x: device, gdg_state_len doubles, nodal layout; may alias.
+ * GDG_COEF_CONST contexts only (GDG_EINVAL otherwise; use gdg_pcg).
+ */
+int gdg_mass_solve(gdg_ctx *ctx, int which, const double *b, double *x, void *stream);
+
+/*
+ * Element-local preconditioned CG (Section 7.1) on every element's system
+ *   which = GDG_OP_M:  M_J x = b
+ *   which = GDG_OP_S:  (S_c2 + w w^T) x = b, w = M_J 1  (the SPD form of the
+ *                      constrained u_t system)
+ * x is the initial guess on entry and the solution on exit (device).
+ * Stops per element when ||r||_2 <= pcg_rtol ||b||_2 or after pcg_maxit
+ * iterations.  stats (host, may be NULL) is filled; the call synchronises
+ * stream when stats != NULL.  GDG_ENOCONV if any element hit pcg_maxit.
+ * GDG_COEF_NODAL contexts only.
+ */
+int gdg_pcg(gdg_ctx *ctx, int which, const double *b, double *x, gdg_pcg_stats *stats,
+            void *stream);
+
+/*
+ * PCG iteration statistics of the element solves done inside gdg_step and
+ * gdg_rhs on a GDG_SOLVE_PCG context since the previous call, for the u_t
+ * system (u_sys) and the v_t system (v_sys); either may be NULL.  Resets the
+ * counters.  mean_iters is per element solve; max_rel_resid is not tracked
+ * here (0).  Synchronises the device.  GDG_EINVAL on GDG_COEF_CONST contexts.
+ */
+int gdg_step_stats(gdg_ctx *ctx, gdg_pcg_stats *u_sys, gdg_pcg_stats *v_sys);
+
+/*
+ * Advance (u, v) in place by nsteps classic RK4 steps of size dt starting at
+ * t0 (device pointers).  The per-stage work is the whole hot path: traces,
+ * fluxes and lifts, stiffness, constrained u_t solve, mass inversion and the
+ * stage combination.  Launches are captured in a CUDA graph on first use.
+ */
+int gdg_step(gdg_ctx *ctx, double *u, double *v, double t0, double dt, int nsteps,
+             void *stream);
+
+/*
+ * gdg_step on HOST arrays: copies (u, v) to the device, advances nsteps and
+ * copies the result back, all on stream, and synchronises before returning.
+ * u, v: host, gdg_state_len doubles each (pinned memory makes the copies
+ * asynchronous DMA; pageable memory works but is slower).
+ */
+int gdg_step_host(gdg_ctx *ctx, double *u, double *v, double t0, double dt, int nsteps,
+                  void *stream);
+
+/*
+ * Discrete energy E = 1/2 sum_e (V_e^T M_e V_e + U_e^T S_e U_e) with S_e the
+ * c^2-weighted stiffness (Section 6's energy norm squared, halved).
+ * u, v device; *E host; synchronises stream.  GDG_ENONFINITE if E is not finite.
+ */
+int gdg_energy(gdg_ctx *ctx, const double *u, const double *v, double *E, void *stream);
+
+/* ---- kernel timing (measurement support; not part of the method) ------ */
+/* Kernel kinds reported by gdg_profile_read. */
+enum {
+    GDG_K_STAGE = 0,      /* fused RK-stage kernel (fluxes, lifts, solves, combine, traces) */
+    GDG_K_TRACES = 1,     /* trace kernel at the start of gdg_step / gdg_rhs             */
+    GDG_K_TRANSFORM = 2,  /* nodal <-> modal element transforms                          */
+    GDG_K_RHS = 3,        /* variable-coefficient residual kernel                         */
+    GDG_K_PCG = 4,        /* element-local PCG kernel                                     */
+    GDG_K_OTHER = 5,
+    GDG_K_COUNT = 6
+};
+
+/*
+ * on != 0: subsequent gdg_step / gdg_rhs calls on ctx launch without the
+ * CUDA graph and bracket every kernel with CUDA events on the caller's
+ * stream (adds a little host overhead per launch); on == 0 restores graph
+ * launches.  Enabling also clears the accumulated records.
+ */
+int gdg_profile_enable(gdg_ctx *ctx, int on);
+
+/*
+ * Synchronise and accumulate the recorded launches of one kernel kind:
+ * *launches = number of launches, *ms = summed device time (CUDA events).
+ */
+int gdg_profile_read(gdg_ctx *ctx, int kind, long long *launches, double *ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GDG_H */

@@ -1,0 +1,802 @@
+// Constant-coefficient Cartesian path of libgdg: the modified-basis
+// (simultaneous diagonalisation) route of Section 3.2.
+//
+// State inside gdg_step is the modal coefficient pair (Ubar, Vbar) with
+// U = Psi Ubar, Psi = Psi_y (x) Psi_x, Psi_j^T M_j Psi_j = I,
+// Psi_j^T S_j Psi_j = diag(lambda_j).  In these coordinates (Eqs.
+// DG1_sparse / DG2_sparse):
+//   mass matrix       -> identity
+//   stiffness         -> diag(lambda_x[k] + lambda_y[l])
+//   face lifts        -> rank one per line: the transverse mass matrix is the
+//                        identity in the transverse modal coordinates, so
+//                        Psi^T [(n.grad phi) (x) M_perp g] = gvec (x) gbar and
+//                        Psi^T [phi_face (x) M_perp q] = evec (x) qbar
+//                        (Section 3.2's surface terms in the new basis)
+//   constrained u_t   -> dUbar/dt = Vbar + r_u / (lambda_x + lambda_y),
+//                        and dUbar_00/dt = Vbar_00 for the constant mode.
+// Neighbouring Cartesian elements share the transverse basis, so the fluxes
+// of Section 2.2.1 are formed directly on transverse modal traces.
+//
+// One RK4 stage is one kernel: read the traces of the stage input (own and
+// neighbours', written by the previous kernel), form fluxes, lifts and the
+// diagonal solves, update the RK accumulator and the next stage input, and
+// write the traces of that next input.  The grid-wide dependency between
+// traces and lifts is the kernel boundary.
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "gdg_internal.h"
+
+namespace {
+
+constexpr int EPB2 = 16;   // elements per block, 2-D kernels (block = EPB2 * N1 threads)
+constexpr int TPB1 = 128;  // threads per block, 1-D kernels (one element per thread)
+
+// stage modes
+constexpr int M_RHS = 0;   // write k = f(Y) to o*
+constexpr int M_S1 = 1;    // acc = cA k; Y' = Y + cY k         (Y = y_n)
+constexpr int M_S23 = 2;   // acc += cA k; Y' = y_n + cY k
+constexpr int M_S4 = 3;    // y_n += acc + cA k
+
+struct StageBufs {
+    const double *yU, *yV;   // stage input (modal)
+    double *nU, *nV;         // y_n
+    double *aU, *aV;         // RK accumulator
+    double *oU, *oV;         // next stage input, or k (M_RHS)
+    const double *trin;      // traces of the stage input
+    double *trout;           // traces of the next stage input
+    const double *lam2;      // [2][n1^d] : -c2 * lambda, 1/lambda (0 on mode 0)
+};
+
+// trace buffer index: 2-D [e][face 0..3 = xm,xp,ym,yp][field 0 = v, 1 = n.grad u][N1]
+template <int N1>
+__device__ __forceinline__ size_t tix2(int e, int face, int fld, int i) {
+    return (((size_t)e * 4 + face) * 2 + fld) * N1 + i;
+}
+// 1-D: [e][face 0..1][field]
+__device__ __forceinline__ size_t tix1(int e, int face, int fld) {
+    return ((size_t)e * 2 + face) * 2 + fld;
+}
+
+// Fluxes of Section 2.2.1 in normal form (alpha = 1/2):
+//   v* = (vi + vo)/2 - beta (di + do),  q* = (di - do)/2 - tau (vi - vo)
+// returns g = v* - vi and c2 * q*.
+__device__ __forceinline__ void flux(double vi, double di, double vo, double dO, double beta,
+                                     double tau, double c2, double &g, double &q) {
+    g = 0.5 * (vo - vi) - beta * (di + dO);
+    q = c2 * (0.5 * (di - dO) - tau * (vi - vo));
+}
+
+// ------------------------------------------------------------ 2-D stage --
+
+template <int N1, int MODE>
+__global__ void __launch_bounds__(EPB2 * N1)
+k_stage2(const __grid_constant__ ModalParams mp, const StageBufs b, double cA, double cY) {
+    extern __shared__ double smem[];
+    const int t = threadIdx.x;
+    const int le = t / N1, l = t - le * N1;
+    const int e = blockIdx.x * EPB2 + le;
+    const bool valid = e < mp.ne;
+    double *fy = smem + le * (4 * N1);
+    double *tile = smem + EPB2 * 4 * N1 + le * (2 * N1 * (N1 + 1));
+    const int nx = mp.nx, ny = mp.ny;
+    const int ex = valid ? e % nx : 0, ey = valid ? e / nx : 0;
+
+    double gxm = 0, gxp = 0, qxm = 0, qxp = 0;
+    if (valid) {
+        const double *T = b.trin;
+        // x faces, transverse mode l
+        double vi = T[tix2<N1>(e, 0, 0, l)], di = T[tix2<N1>(e, 0, 1, l)], vo, dO;
+        int en = ex - 1;
+        if (en < 0 && mp.per_x) en += nx;
+        if (en >= 0) { int f = ey * nx + en; vo = T[tix2<N1>(f, 1, 0, l)]; dO = T[tix2<N1>(f, 1, 1, l)]; }
+        else { vo = -vi; dO = -di; }
+        flux(vi, di, vo, dO, mp.beta, mp.tau, mp.c2, gxm, qxm);
+        vi = T[tix2<N1>(e, 1, 0, l)]; di = T[tix2<N1>(e, 1, 1, l)];
+        en = ex + 1;
+        if (en >= nx && mp.per_x) en -= nx;
+        if (en < nx) { int f = ey * nx + en; vo = T[tix2<N1>(f, 0, 0, l)]; dO = T[tix2<N1>(f, 0, 1, l)]; }
+        else { vo = -vi; dO = -di; }
+        flux(vi, di, vo, dO, mp.beta, mp.tau, mp.c2, gxp, qxp);
+        // y faces, transverse mode k = l
+        double g, q;
+        vi = T[tix2<N1>(e, 2, 0, l)]; di = T[tix2<N1>(e, 2, 1, l)];
+        en = ey - 1;
+        if (en < 0 && mp.per_y) en += ny;
+        if (en >= 0) { int f = en * nx + ex; vo = T[tix2<N1>(f, 3, 0, l)]; dO = T[tix2<N1>(f, 3, 1, l)]; }
+        else { vo = -vi; dO = -di; }
+        flux(vi, di, vo, dO, mp.beta, mp.tau, mp.c2, g, q);
+        fy[0 * N1 + l] = g; fy[2 * N1 + l] = q;
+        vi = T[tix2<N1>(e, 3, 0, l)]; di = T[tix2<N1>(e, 3, 1, l)];
+        en = ey + 1;
+        if (en >= ny && mp.per_y) en -= ny;
+        if (en < ny) { int f = en * nx + ex; vo = T[tix2<N1>(f, 2, 0, l)]; dO = T[tix2<N1>(f, 2, 1, l)]; }
+        else { vo = -vi; dO = -di; }
+        flux(vi, di, vo, dO, mp.beta, mp.tau, mp.c2, g, q);
+        fy[1 * N1 + l] = g; fy[3 * N1 + l] = q;
+    }
+    __syncthreads();
+
+    double Ru[N1], Rv[N1];   // next stage input (or k) for row l
+    if (valid) {
+        const size_t row = ((size_t)e * N1 + l) * N1;
+        const double *L0 = b.lam2 + l * N1;
+        const double *L1 = b.lam2 + N1 * N1 + l * N1;
+        const double gLy = mp.d[1].gL[l], gRy = mp.d[1].gR[l];
+        const double eLy = mp.d[1].eL[l], eRy = mp.d[1].eR[l];
+#pragma unroll
+        for (int k = 0; k < N1; ++k) {
+            const double Yu = b.yU[row + k], Yv = b.yV[row + k];
+            const double ru = mp.d[0].gL[k] * gxm + mp.d[0].gR[k] * gxp + gLy * fy[k] + gRy * fy[N1 + k];
+            const double rv = L0[k] * Yu + mp.d[0].eL[k] * qxm + mp.d[0].eR[k] * qxp +
+                              eLy * fy[2 * N1 + k] + eRy * fy[3 * N1 + k];
+            const double ku = Yv + L1[k] * ru;
+            const double kv = rv;
+            if (MODE == M_RHS) {
+                b.oU[row + k] = ku;
+                b.oV[row + k] = kv;
+            } else if (MODE == M_S1) {
+                b.aU[row + k] = cA * ku;
+                b.aV[row + k] = cA * kv;
+                Ru[k] = Yu + cY * ku;
+                Rv[k] = Yv + cY * kv;
+            } else if (MODE == M_S23) {
+                b.aU[row + k] += cA * ku;
+                b.aV[row + k] += cA * kv;
+                Ru[k] = b.nU[row + k] + cY * ku;
+                Rv[k] = b.nV[row + k] + cY * kv;
+            } else {
+                Ru[k] = b.nU[row + k] + b.aU[row + k] + cA * ku;
+                Rv[k] = b.nV[row + k] + b.aV[row + k] + cA * kv;
+            }
+        }
+        if (MODE != M_RHS) {
+            double *dU = (MODE == M_S4) ? b.nU : b.oU;
+            double *dV = (MODE == M_S4) ? b.nV : b.oV;
+#pragma unroll
+            for (int k = 0; k < N1; ++k) { dU[row + k] = Ru[k]; dV[row + k] = Rv[k]; }
+        }
+    }
+    if (MODE == M_RHS) return;   // uniform across the block
+
+    // traces of the next stage input: x faces from the row, y faces from columns
+    if (valid) {
+        double vL = 0, vR = 0, dL = 0, dR = 0;
+#pragma unroll
+        for (int k = 0; k < N1; ++k) {
+            vL += mp.d[0].eL[k] * Rv[k];
+            vR += mp.d[0].eR[k] * Rv[k];
+            dL += mp.d[0].gL[k] * Ru[k];
+            dR += mp.d[0].gR[k] * Ru[k];
+            tile[l * (N1 + 1) + k] = Ru[k];
+            tile[N1 * (N1 + 1) + l * (N1 + 1) + k] = Rv[k];
+        }
+        b.trout[tix2<N1>(e, 0, 0, l)] = vL;
+        b.trout[tix2<N1>(e, 0, 1, l)] = dL;
+        b.trout[tix2<N1>(e, 1, 0, l)] = vR;
+        b.trout[tix2<N1>(e, 1, 1, l)] = dR;
+    }
+    __syncthreads();
+    if (valid) {
+        const int k = l;   // this thread's column
+        double vL = 0, vR = 0, dL = 0, dR = 0;
+#pragma unroll
+        for (int j = 0; j < N1; ++j) {
+            const double u = tile[j * (N1 + 1) + k], v = tile[N1 * (N1 + 1) + j * (N1 + 1) + k];
+            vL += mp.d[1].eL[j] * v;
+            vR += mp.d[1].eR[j] * v;
+            dL += mp.d[1].gL[j] * u;
+            dR += mp.d[1].gR[j] * u;
+        }
+        b.trout[tix2<N1>(e, 2, 0, k)] = vL;
+        b.trout[tix2<N1>(e, 2, 1, k)] = dL;
+        b.trout[tix2<N1>(e, 3, 0, k)] = vR;
+        b.trout[tix2<N1>(e, 3, 1, k)] = dR;
+    }
+}
+
+// traces of a modal state (start of gdg_step and gdg_rhs)
+template <int N1>
+__global__ void __launch_bounds__(EPB2 * N1)
+k_traces2(const __grid_constant__ ModalParams mp, const double *yU, const double *yV, double *trout) {
+    extern __shared__ double smem[];
+    const int t = threadIdx.x;
+    const int le = t / N1, l = t - le * N1;
+    const int e = blockIdx.x * EPB2 + le;
+    const bool valid = e < mp.ne;
+    double *tile = smem + le * (2 * N1 * (N1 + 1));
+    if (valid) {
+        const size_t row = ((size_t)e * N1 + l) * N1;
+        double vL = 0, vR = 0, dL = 0, dR = 0;
+#pragma unroll
+        for (int k = 0; k < N1; ++k) {
+            const double u = yU[row + k], v = yV[row + k];
+            vL += mp.d[0].eL[k] * v;
+            vR += mp.d[0].eR[k] * v;
+            dL += mp.d[0].gL[k] * u;
+            dR += mp.d[0].gR[k] * u;
+            tile[l * (N1 + 1) + k] = u;
+            tile[N1 * (N1 + 1) + l * (N1 + 1) + k] = v;
+        }
+        trout[tix2<N1>(e, 0, 0, l)] = vL;
+        trout[tix2<N1>(e, 0, 1, l)] = dL;
+        trout[tix2<N1>(e, 1, 0, l)] = vR;
+        trout[tix2<N1>(e, 1, 1, l)] = dR;
+    }
+    __syncthreads();
+    if (valid) {
+        const int k = l;
+        double vL = 0, vR = 0, dL = 0, dR = 0;
+#pragma unroll
+        for (int j = 0; j < N1; ++j) {
+            const double u = tile[j * (N1 + 1) + k], v = tile[N1 * (N1 + 1) + j * (N1 + 1) + k];
+            vL += mp.d[1].eL[j] * v;
+            vR += mp.d[1].eR[j] * v;
+            dL += mp.d[1].gL[j] * u;
+            dR += mp.d[1].gR[j] * u;
+        }
+        trout[tix2<N1>(e, 2, 0, k)] = vL;
+        trout[tix2<N1>(e, 2, 1, k)] = dL;
+        trout[tix2<N1>(e, 3, 0, k)] = vR;
+        trout[tix2<N1>(e, 3, 1, k)] = dR;
+    }
+}
+
+// Separable element transform: out = (Cy (x) Cx) diag(D) (By (x) Bx) in,
+// with C and D optional (nullptr).  Matrices are n1 x n1 row-major,
+// (A (x) B)[(l,k),(j,i)] = A[l][j] B[k][i].  Two fields per call (U and V
+// share the matrices).
+template <int N1>
+__global__ void __launch_bounds__(EPB2 * N1)
+k_sep2(int ne, const double *in0, const double *in1, double *out0, double *out1,
+       const double *Bx, const double *By, const double *D, const double *Cx, const double *Cy) {
+    extern __shared__ double smem[];
+    double *sB = smem;                 // Bx, By, Cx, Cy
+    double *tiles = smem + 4 * N1 * N1;
+    const int t = threadIdx.x;
+    for (int i = t; i < N1 * N1; i += blockDim.x) {
+        sB[i] = Bx[i];
+        sB[N1 * N1 + i] = By[i];
+        if (Cx) { sB[2 * N1 * N1 + i] = Cx[i]; sB[3 * N1 * N1 + i] = Cy[i]; }
+    }
+    const int le = t / N1, l = t - le * N1;
+    const int e = blockIdx.x * EPB2 + le;
+    const bool valid = e < ne;
+    double *tile = tiles + le * (2 * N1 * (N1 + 1));
+    const int nf = in1 ? 2 : 1;
+    __syncthreads();
+    for (int f = 0; f < nf; ++f) {
+        const double *in = f ? in1 : in0;
+        double *out = f ? out1 : out0;
+        double *T = tile + f * N1 * (N1 + 1);
+        // (1) rows: T[j][k] = sum_i Bx[k][i] in[j][i]   (thread = row j)
+        if (valid) {
+            double x[N1];
+            const size_t row = ((size_t)e * N1 + l) * N1;
+#pragma unroll
+            for (int i = 0; i < N1; ++i) x[i] = in[row + i];
+#pragma unroll
+            for (int k = 0; k < N1; ++k) {
+                double s = 0;
+#pragma unroll
+                for (int i = 0; i < N1; ++i) s += sB[k * N1 + i] * x[i];
+                T[l * (N1 + 1) + k] = s;
+            }
+        }
+        __syncthreads();
+        // (2) columns: Z[m][k] = D[m][k] * sum_j By[m][j] T[j][k]   (thread = column k)
+        double z[N1];
+        if (valid) {
+            const int k = l;
+            double c[N1];
+#pragma unroll
+            for (int j = 0; j < N1; ++j) c[j] = T[j * (N1 + 1) + k];
+#pragma unroll
+            for (int m = 0; m < N1; ++m) {
+                double s = 0;
+#pragma unroll
+                for (int j = 0; j < N1; ++j) s += sB[N1 * N1 + m * N1 + j] * c[j];
+                if (D) s *= D[m * N1 + k];
+                z[m] = s;
+            }
+        }
+        if (!Cx) {
+            if (valid) {
+                const int k = l;
+#pragma unroll
+                for (int m = 0; m < N1; ++m) out[((size_t)e * N1 + m) * N1 + k] = z[m];
+            }
+            __syncthreads();
+            continue;
+        }
+        // (3) columns again with Cy: W[r][k] = sum_m Cy[r][m] Z[m][k]; store to T
+        __syncthreads();
+        if (valid) {
+            const int k = l;
+#pragma unroll
+            for (int r = 0; r < N1; ++r) {
+                double s = 0;
+#pragma unroll
+                for (int m = 0; m < N1; ++m) s += sB[3 * N1 * N1 + r * N1 + m] * z[m];
+                T[r * (N1 + 1) + k] = s;
+            }
+        }
+        __syncthreads();
+        // (4) rows with Cx: out[r][q] = sum_k Cx[q][k] W[r][k]   (thread = row r)
+        if (valid) {
+            double w[N1];
+#pragma unroll
+            for (int k = 0; k < N1; ++k) w[k] = T[l * (N1 + 1) + k];
+            const size_t row = ((size_t)e * N1 + l) * N1;
+#pragma unroll
+            for (int q = 0; q < N1; ++q) {
+                double s = 0;
+#pragma unroll
+                for (int k = 0; k < N1; ++k) s += sB[2 * N1 * N1 + q * N1 + k] * w[k];
+                out[row + q] = s;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// per-block partial of sum over elements of (|Vbar|^2 + c2 * lambda . Ubar^2)
+// for modal (Ubar, Vbar) given in yU, yV; deterministic fixed-order tree.
+template <int N1, int D2>
+__global__ void k_energy_partial(int ne, const double *yU, const double *yV, const double *lam2,
+                                 double *partial) {
+    __shared__ double red[1024];
+    const int t = threadIdx.x;
+    const int ents = D2 ? N1 * N1 : N1;
+    double s = 0.0;
+    const long long total = (long long)ne * ents;
+    for (long long i = (long long)blockIdx.x * blockDim.x + t; i < total; i += (long long)gridDim.x * blockDim.x) {
+        const int m = (int)(i % ents);
+        const double u = yU[i], v = yV[i];
+        s += v * v - lam2[m] * u * u;    // lam2[0][m] = -c2 * lambda_m
+    }
+    red[t] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (t < w) red[t] += red[t + w];
+        __syncthreads();
+    }
+    if (t == 0) partial[blockIdx.x] = red[0];
+}
+
+__global__ void k_sum_partials(int n, const double *partial, double *out) {
+    __shared__ double red[1024];
+    const int t = threadIdx.x;
+    double s = 0.0;
+    for (int i = t; i < n; i += blockDim.x) s += partial[i];
+    red[t] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (t < w) red[t] += red[t + w];
+        __syncthreads();
+    }
+    if (t == 0) out[0] = 0.5 * red[0];
+}
+
+// ------------------------------------------------------------ 1-D --------
+
+template <int N1, int MODE>
+__global__ void __launch_bounds__(TPB1)
+k_stage1(const __grid_constant__ ModalParams mp, const StageBufs b, double cA, double cY) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= mp.ne) return;
+    const int nx = mp.nx;
+    const double *T = b.trin;
+    double vi = T[tix1(e, 0, 0)], di = T[tix1(e, 0, 1)], vo, dO, gm, qm, gp, qp;
+    int en = e - 1;
+    if (en < 0 && mp.per_x) en += nx;
+    if (en >= 0) { vo = T[tix1(en, 1, 0)]; dO = T[tix1(en, 1, 1)]; } else { vo = -vi; dO = -di; }
+    flux(vi, di, vo, dO, mp.beta, mp.tau, mp.c2, gm, qm);
+    vi = T[tix1(e, 1, 0)]; di = T[tix1(e, 1, 1)];
+    en = e + 1;
+    if (en >= nx && mp.per_x) en -= nx;
+    if (en < nx) { vo = T[tix1(en, 0, 0)]; dO = T[tix1(en, 0, 1)]; } else { vo = -vi; dO = -di; }
+    flux(vi, di, vo, dO, mp.beta, mp.tau, mp.c2, gp, qp);
+    const size_t row = (size_t)e * N1;
+    double Ru[N1], Rv[N1];
+#pragma unroll
+    for (int k = 0; k < N1; ++k) {
+        const double Yu = b.yU[row + k], Yv = b.yV[row + k];
+        const double ru = mp.d[0].gL[k] * gm + mp.d[0].gR[k] * gp;
+        const double rv = b.lam2[k] * Yu + mp.d[0].eL[k] * qm + mp.d[0].eR[k] * qp;
+        const double ku = Yv + b.lam2[N1 + k] * ru, kv = rv;
+        if (MODE == M_RHS) { b.oU[row + k] = ku; b.oV[row + k] = kv; }
+        else if (MODE == M_S1) {
+            b.aU[row + k] = cA * ku; b.aV[row + k] = cA * kv;
+            Ru[k] = Yu + cY * ku; Rv[k] = Yv + cY * kv;
+        } else if (MODE == M_S23) {
+            b.aU[row + k] += cA * ku; b.aV[row + k] += cA * kv;
+            Ru[k] = b.nU[row + k] + cY * ku; Rv[k] = b.nV[row + k] + cY * kv;
+        } else {
+            Ru[k] = b.nU[row + k] + b.aU[row + k] + cA * ku;
+            Rv[k] = b.nV[row + k] + b.aV[row + k] + cA * kv;
+        }
+    }
+    if (MODE == M_RHS) return;
+    double *dU = (MODE == M_S4) ? b.nU : b.oU;
+    double *dV = (MODE == M_S4) ? b.nV : b.oV;
+    double vL = 0, vR = 0, dL = 0, dR = 0;
+#pragma unroll
+    for (int k = 0; k < N1; ++k) {
+        dU[row + k] = Ru[k]; dV[row + k] = Rv[k];
+        vL += mp.d[0].eL[k] * Rv[k]; vR += mp.d[0].eR[k] * Rv[k];
+        dL += mp.d[0].gL[k] * Ru[k]; dR += mp.d[0].gR[k] * Ru[k];
+    }
+    b.trout[tix1(e, 0, 0)] = vL; b.trout[tix1(e, 0, 1)] = dL;
+    b.trout[tix1(e, 1, 0)] = vR; b.trout[tix1(e, 1, 1)] = dR;
+}
+
+template <int N1>
+__global__ void k_traces1(const __grid_constant__ ModalParams mp, const double *yU, const double *yV, double *trout) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= mp.ne) return;
+    double vL = 0, vR = 0, dL = 0, dR = 0;
+#pragma unroll
+    for (int k = 0; k < N1; ++k) {
+        const double u = yU[(size_t)e * N1 + k], v = yV[(size_t)e * N1 + k];
+        vL += mp.d[0].eL[k] * v; vR += mp.d[0].eR[k] * v;
+        dL += mp.d[0].gL[k] * u; dR += mp.d[0].gR[k] * u;
+    }
+    trout[tix1(e, 0, 0)] = vL; trout[tix1(e, 0, 1)] = dL;
+    trout[tix1(e, 1, 0)] = vR; trout[tix1(e, 1, 1)] = dR;
+}
+
+// out = C diag(D) B in  (1-D, two fields)
+template <int N1>
+__global__ void k_sep1(int ne, const double *in0, const double *in1, double *out0, double *out1,
+                       const double *B, const double *D, const double *C) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= ne) return;
+    const int nf = in1 ? 2 : 1;
+    for (int f = 0; f < nf; ++f) {
+        const double *in = f ? in1 : in0;
+        double *out = f ? out1 : out0;
+        double x[N1], z[N1];
+#pragma unroll
+        for (int i = 0; i < N1; ++i) x[i] = in[(size_t)e * N1 + i];
+#pragma unroll
+        for (int k = 0; k < N1; ++k) {
+            double s = 0;
+#pragma unroll
+            for (int i = 0; i < N1; ++i) s += B[k * N1 + i] * x[i];
+            z[k] = D ? s * D[k] : s;
+        }
+        if (!C) {
+#pragma unroll
+            for (int k = 0; k < N1; ++k) out[(size_t)e * N1 + k] = z[k];
+            continue;
+        }
+#pragma unroll
+        for (int q = 0; q < N1; ++q) {
+            double s = 0;
+#pragma unroll
+            for (int k = 0; k < N1; ++k) s += C[q * N1 + k] * z[k];
+            out[(size_t)e * N1 + q] = s;
+        }
+    }
+}
+
+// ------------------------------------------------------ dispatch ---------
+
+#define GDG_N1_CASES(X) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) X(14) X(15) X(16)
+
+size_t smem_stage2(int n1) { return (size_t)EPB2 * (4 * n1 + 2 * n1 * (n1 + 1)) * sizeof(double); }
+size_t smem_traces2(int n1) { return (size_t)EPB2 * (2 * n1 * (n1 + 1)) * sizeof(double); }
+size_t smem_sep2(int n1) { return (size_t)(4 * n1 * n1 + EPB2 * 2 * n1 * (n1 + 1)) * sizeof(double); }
+
+template <int N1>
+void launch_stage2(int mode, const ModalParams &mp, const StageBufs &b, double cA, double cY, cudaStream_t s) {
+    dim3 grid((mp.ne + EPB2 - 1) / EPB2), block(EPB2 * N1);
+    size_t sm = smem_stage2(N1);
+    switch (mode) {
+    case M_RHS: k_stage2<N1, M_RHS><<<grid, block, sm, s>>>(mp, b, cA, cY); break;
+    case M_S1: k_stage2<N1, M_S1><<<grid, block, sm, s>>>(mp, b, cA, cY); break;
+    case M_S23: k_stage2<N1, M_S23><<<grid, block, sm, s>>>(mp, b, cA, cY); break;
+    default: k_stage2<N1, M_S4><<<grid, block, sm, s>>>(mp, b, cA, cY); break;
+    }
+}
+
+template <int N1>
+void launch_stage1(int mode, const ModalParams &mp, const StageBufs &b, double cA, double cY, cudaStream_t s) {
+    dim3 grid((mp.ne + TPB1 - 1) / TPB1), block(TPB1);
+    switch (mode) {
+    case M_RHS: k_stage1<N1, M_RHS><<<grid, block, 0, s>>>(mp, b, cA, cY); break;
+    case M_S1: k_stage1<N1, M_S1><<<grid, block, 0, s>>>(mp, b, cA, cY); break;
+    case M_S23: k_stage1<N1, M_S23><<<grid, block, 0, s>>>(mp, b, cA, cY); break;
+    default: k_stage1<N1, M_S4><<<grid, block, 0, s>>>(mp, b, cA, cY); break;
+    }
+}
+
+void launch_stage_raw(const gdg_ctx *ctx, int mode, const StageBufs &b, double cA, double cY, cudaStream_t s) {
+    const int n1 = ctx->n1;
+    if (ctx->dim == 2) {
+        switch (n1) {
+#define X(n) case n: launch_stage2<n>(mode, ctx->mp, b, cA, cY, s); break;
+            GDG_N1_CASES(X)
+#undef X
+        }
+    } else {
+        switch (n1) {
+#define X(n) case n: launch_stage1<n>(mode, ctx->mp, b, cA, cY, s); break;
+            GDG_N1_CASES(X)
+#undef X
+        }
+    }
+}
+
+void launch_traces_raw(const gdg_ctx *ctx, const double *yU, const double *yV, double *tr, cudaStream_t s) {
+    const int n1 = ctx->n1;
+    if (ctx->dim == 2) {
+        dim3 grid((ctx->ne + EPB2 - 1) / EPB2), block(EPB2 * n1);
+        switch (n1) {
+#define X(n) case n: k_traces2<n><<<grid, block, smem_traces2(n), s>>>(ctx->mp, yU, yV, tr); break;
+            GDG_N1_CASES(X)
+#undef X
+        }
+    } else {
+        dim3 grid((ctx->ne + TPB1 - 1) / TPB1), block(TPB1);
+        switch (n1) {
+#define X(n) case n: k_traces1<n><<<grid, block, 0, s>>>(ctx->mp, yU, yV, tr); break;
+            GDG_N1_CASES(X)
+#undef X
+        }
+    }
+}
+
+// table offsets inside ctx->d_mats: [dir][P, Psi, PsiT][n1*n1]
+const double *mat(const gdg_ctx *ctx, int dir, int which) {
+    return ctx->d_mats + ((size_t)dir * 3 + which) * ctx->n1 * ctx->n1;
+}
+enum { T_P = 0, T_PSI = 1, T_PSIT = 2 };
+
+// out = (C) diag(D) (B) in, over both fields when in1 != nullptr
+void launch_sep_raw(const gdg_ctx *ctx, const double *in0, const double *in1, double *out0, double *out1,
+                int B, const double *D, int C, cudaStream_t s) {
+    const int n1 = ctx->n1;
+    if (ctx->dim == 2) {
+        dim3 grid((ctx->ne + EPB2 - 1) / EPB2), block(EPB2 * n1);
+        const double *Bx = mat(ctx, 0, B), *By = mat(ctx, 1, B);
+        const double *Cx = C >= 0 ? mat(ctx, 0, C) : nullptr, *Cy = C >= 0 ? mat(ctx, 1, C) : nullptr;
+        switch (n1) {
+#define X(n) case n: k_sep2<n><<<grid, block, smem_sep2(n), s>>>(ctx->ne, in0, in1, out0, out1, Bx, By, D, Cx, Cy); break;
+            GDG_N1_CASES(X)
+#undef X
+        }
+    } else {
+        dim3 grid((ctx->ne + TPB1 - 1) / TPB1), block(TPB1);
+        const double *Bm = mat(ctx, 0, B), *Cm = C >= 0 ? mat(ctx, 0, C) : nullptr;
+        switch (n1) {
+#define X(n) case n: k_sep1<n><<<grid, block, 0, s>>>(ctx->ne, in0, in1, out0, out1, Bm, D, Cm); break;
+            GDG_N1_CASES(X)
+#undef X
+        }
+    }
+}
+
+void launch_stage(gdg_ctx *ctx, int mode, const StageBufs &b, double cA, double cY, cudaStream_t s) {
+    GDG_PROF(ctx, GDG_K_STAGE, s, launch_stage_raw(ctx, mode, b, cA, cY, s));
+}
+void launch_traces(gdg_ctx *ctx, const double *yU, const double *yV, double *tr, cudaStream_t s) {
+    GDG_PROF(ctx, GDG_K_TRACES, s, launch_traces_raw(ctx, yU, yV, tr, s));
+}
+void launch_sep(gdg_ctx *ctx, const double *in0, const double *in1, double *out0, double *out1,
+                int B, const double *D, int C, cudaStream_t s) {
+    GDG_PROF(ctx, GDG_K_TRANSFORM, s, launch_sep_raw(ctx, in0, in1, out0, out1, B, D, C, s));
+}
+
+double *buf(gdg_ctx *ctx, int i) { return ctx->d_state + (size_t)i * ctx->ndof; }
+enum { B_NU = 0, B_NV, B_AU, B_AV, B_XU, B_XV, B_YU, B_YV, B_KU, B_KV, B_COUNT };
+
+int set_smem_limits() {
+    // the 2-D kernels may need more than the 48 KB default of dynamic shared memory
+    static bool done = false;
+    if (done) return GDG_OK;
+#define X(n)                                                                                          \
+    cudaFuncSetAttribute(k_stage2<n, M_RHS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_stage2(n)); \
+    cudaFuncSetAttribute(k_stage2<n, M_S1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_stage2(n));  \
+    cudaFuncSetAttribute(k_stage2<n, M_S23>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_stage2(n)); \
+    cudaFuncSetAttribute(k_stage2<n, M_S4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_stage2(n));  \
+    cudaFuncSetAttribute(k_traces2<n>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_traces2(n));     \
+    cudaFuncSetAttribute(k_sep2<n>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_sep2(n));
+    GDG_N1_CASES(X)
+#undef X
+    done = true;
+    return GDG_OK;
+}
+
+// one RK4 step on the internal modal state (y_n in B_N*, traces of y_n in tr0)
+void enqueue_rk4_step(gdg_ctx *ctx, double dt, cudaStream_t s) {
+    double *tr0 = ctx->d_tr, *tr1 = ctx->d_tr + ctx->tr_len;
+    const double *lam2 = ctx->d_lam2;
+    StageBufs b{};
+    b.nU = buf(ctx, B_NU); b.nV = buf(ctx, B_NV);
+    b.aU = buf(ctx, B_AU); b.aV = buf(ctx, B_AV);
+    b.lam2 = lam2;
+    // stage 1: Y1 = y_n -> acc = dt/6 k1, X = y_n + dt/2 k1
+    b.yU = b.nU; b.yV = b.nV; b.oU = buf(ctx, B_XU); b.oV = buf(ctx, B_XV); b.trin = tr0; b.trout = tr1;
+    launch_stage(ctx, M_S1, b, dt / 6.0, 0.5 * dt, s);
+    // stage 2: k2 = f(X) -> acc += dt/3 k2, Y = y_n + dt/2 k2
+    b.yU = buf(ctx, B_XU); b.yV = buf(ctx, B_XV); b.oU = buf(ctx, B_YU); b.oV = buf(ctx, B_YV); b.trin = tr1; b.trout = tr0;
+    launch_stage(ctx, M_S23, b, dt / 3.0, 0.5 * dt, s);
+    // stage 3: k3 = f(Y) -> acc += dt/3 k3, X = y_n + dt k3
+    b.yU = buf(ctx, B_YU); b.yV = buf(ctx, B_YV); b.oU = buf(ctx, B_XU); b.oV = buf(ctx, B_XV); b.trin = tr0; b.trout = tr1;
+    launch_stage(ctx, M_S23, b, dt / 3.0, dt, s);
+    // stage 4: k4 = f(X) -> y_n += acc + dt/6 k4 (traces of y_{n+1} to tr0)
+    b.yU = buf(ctx, B_XU); b.yV = buf(ctx, B_XV); b.oU = nullptr; b.oV = nullptr; b.trin = tr1; b.trout = tr0;
+    launch_stage(ctx, M_S4, b, dt / 6.0, 0.0, s);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------- API -------
+
+int gdg_const_setup(gdg_ctx *ctx) {
+    const int n1 = ctx->n1, nn = n1 * n1;
+    ModalParams &mp = ctx->mp;
+    std::memset(&mp, 0, sizeof(mp));
+    mp.nx = ctx->nx;
+    mp.ny = ctx->ny;
+    mp.ne = ctx->ne;
+    mp.per_x = ctx->pb.bc[0] == GDG_BC_PERIODIC;
+    mp.per_y = ctx->dim == 2 && ctx->pb.bc[1] == GDG_BC_PERIODIC;
+    mp.c2 = ctx->pb.c2;
+    if (ctx->pb.flux == GDG_FLUX_UPWIND) {
+        double xi = ctx->pb.xi > 0 ? ctx->pb.xi : std::sqrt(ctx->pb.c2);
+        mp.beta = 0.5 * xi;
+        mp.tau = 0.5 / xi;
+    }
+    std::vector<double> tables((size_t)2 * 3 * nn, 0.0);
+    std::vector<double> lam[2];
+    for (int d = 0; d < ctx->dim; ++d) {
+        const double H = (ctx->pb.hi[d] - ctx->pb.lo[d]) / ctx->pb.n_elem[d];
+        const double sq = std::sqrt(H);
+        std::vector<double> Psi(nn), M(nn);
+        for (int i = 0; i < nn; ++i) { Psi[i] = ctx->Psih[i] / sq; M[i] = H * ctx->Mh[i]; }
+        lam[d].resize(n1);
+        for (int k = 0; k < n1; ++k) lam[d][k] = ctx->lamh[k] / (H * H);
+        double *P = &tables[((size_t)d * 3 + T_P) * nn];
+        double *Ps = &tables[((size_t)d * 3 + T_PSI) * nn];
+        double *PT = &tables[((size_t)d * 3 + T_PSIT) * nn];
+        for (int k = 0; k < n1; ++k)
+            for (int i = 0; i < n1; ++i) {
+                double s = 0;
+                for (int a = 0; a < n1; ++a) s += Psi[a * n1 + k] * M[a * n1 + i];
+                P[k * n1 + i] = s;             // Psi^T M
+                Ps[i * n1 + k] = Psi[i * n1 + k];
+                PT[k * n1 + i] = Psi[i * n1 + k];
+            }
+        ModalDir &md = mp.d[d];
+        for (int k = 0; k < n1; ++k) {
+            md.eL[k] = Psi[0 * n1 + k];
+            md.eR[k] = Psi[(n1 - 1) * n1 + k];
+            double gl = 0, gr = 0;
+            for (int i = 0; i < n1; ++i) {
+                gl += Psi[i * n1 + k] * (-ctx->dphiL[i] / H);
+                gr += Psi[i * n1 + k] * (ctx->dphiR[i] / H);
+            }
+            md.gL[k] = gl;
+            md.gR[k] = gr;
+            md.lam[k] = lam[d][k];
+        }
+    }
+    const int ents = ctx->dim == 2 ? nn : n1;
+    std::vector<double> l2((size_t)2 * ents, 0.0);
+    for (int m = 0; m < ents; ++m) {
+        double L = ctx->dim == 2 ? lam[0][m % n1] + lam[1][m / n1] : lam[0][m];
+        l2[m] = -ctx->pb.c2 * L;
+        l2[ents + m] = m == 0 ? 0.0 : 1.0 / L;
+    }
+    ctx->tr_len = (long long)ctx->ne * (ctx->dim == 2 ? 8 * n1 : 4);
+    ctx->red_len = 1024;
+    int st;
+    if ((st = gdg_cuda_check(ctx, cudaMalloc((void **)&ctx->d_mats, tables.size() * sizeof(double)), "alloc")) ||
+        (st = gdg_cuda_check(ctx, cudaMalloc((void **)&ctx->d_lam2, l2.size() * sizeof(double)), "alloc")) ||
+        (st = gdg_cuda_check(ctx, cudaMalloc((void **)&ctx->d_state, (size_t)B_COUNT * ctx->ndof * sizeof(double)), "alloc")) ||
+        (st = gdg_cuda_check(ctx, cudaMalloc((void **)&ctx->d_tr, (size_t)2 * ctx->tr_len * sizeof(double)), "alloc")) ||
+        (st = gdg_cuda_check(ctx, cudaMalloc((void **)&ctx->d_red, (size_t)(ctx->red_len + 1) * sizeof(double)), "alloc")) ||
+        (st = gdg_cuda_check(ctx, cudaMallocHost((void **)&ctx->h_red, 8 * sizeof(double)), "alloc")))
+        return st;
+    if ((st = gdg_cuda_check(ctx, cudaMemcpy(ctx->d_mats, tables.data(), tables.size() * sizeof(double), cudaMemcpyHostToDevice), "upload")) ||
+        (st = gdg_cuda_check(ctx, cudaMemcpy(ctx->d_lam2, l2.data(), l2.size() * sizeof(double), cudaMemcpyHostToDevice), "upload")))
+        return st;
+    set_smem_limits();
+    return gdg_cuda_check(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking), "stream");
+}
+
+void gdg_const_free(gdg_ctx *ctx) {
+    if (ctx->graph.exec) cudaGraphExecDestroy(ctx->graph.exec);
+    ctx->graph.exec = nullptr;
+    cudaFree(ctx->d_mats);
+    cudaFree(ctx->d_lam2);
+    cudaFree(ctx->d_state);
+    cudaFree(ctx->d_tr);
+    cudaFree(ctx->d_red);
+    if (ctx->h_red) cudaFreeHost(ctx->h_red);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    ctx->d_mats = ctx->d_lam2 = ctx->d_state = ctx->d_tr = ctx->d_red = ctx->h_red = nullptr;
+    ctx->cap_stream = nullptr;
+}
+
+int gdg_const_rhs(gdg_ctx *ctx, const double *u, const double *v, double *du, double *dv, cudaStream_t s) {
+    // modal state of (u, v), its traces, k = f(Y) in modal form, back to nodal
+    launch_sep(ctx, u, v, buf(ctx, B_XU), buf(ctx, B_XV), T_P, nullptr, -1, s);
+    launch_traces(ctx, buf(ctx, B_XU), buf(ctx, B_XV), ctx->d_tr, s);
+    StageBufs b{};
+    b.yU = buf(ctx, B_XU); b.yV = buf(ctx, B_XV);
+    b.oU = buf(ctx, B_KU); b.oV = buf(ctx, B_KV);
+    b.trin = ctx->d_tr; b.lam2 = ctx->d_lam2;
+    launch_stage(ctx, M_RHS, b, 0.0, 0.0, s);
+    launch_sep(ctx, buf(ctx, B_KU), buf(ctx, B_KV), du, dv, T_PSI, nullptr, -1, s);
+    return gdg_cuda_check(ctx, cudaGetLastError(), "gdg_rhs launch");
+}
+
+int gdg_const_mass_solve(gdg_ctx *ctx, int which, const double *b, double *x, cudaStream_t s) {
+    // x = Psi D Psi^T b with D = I (M^-1) or D = Lambda^+ (constrained S solve)
+    const int ents = ctx->dim == 2 ? ctx->n1 * ctx->n1 : ctx->n1;
+    const double *D = which == GDG_OP_M ? nullptr : ctx->d_lam2 + ents;
+    launch_sep(ctx, b, nullptr, x, nullptr, T_PSIT, D, T_PSI, s);
+    return gdg_cuda_check(ctx, cudaGetLastError(), "gdg_mass_solve launch");
+}
+
+int gdg_const_step(gdg_ctx *ctx, double *u, double *v, double dt, int nsteps, cudaStream_t s) {
+    int st;
+    launch_sep(ctx, u, v, buf(ctx, B_NU), buf(ctx, B_NV), T_P, nullptr, -1, s);
+    launch_traces(ctx, buf(ctx, B_NU), buf(ctx, B_NV), ctx->d_tr, s);
+    if ((st = gdg_cuda_check(ctx, cudaGetLastError(), "gdg_step prologue"))) return st;
+    // graph of G steps, replayed; the remainder is launched directly
+    const int G = (nsteps >= 16 && !ctx->prof.on) ? 16 : 0;
+    if (G) {
+        GraphCache &gc = ctx->graph;
+        if (!gc.exec || gc.dt != dt || gc.steps != G) {
+            if (gc.exec) cudaGraphExecDestroy(gc.exec);
+            gc.exec = nullptr;
+            cudaGraph_t g;
+            if ((st = gdg_cuda_check(ctx, cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal), "capture")))
+                return st;
+            for (int i = 0; i < G; ++i) enqueue_rk4_step(ctx, dt, ctx->cap_stream);
+            if ((st = gdg_cuda_check(ctx, cudaStreamEndCapture(ctx->cap_stream, &g), "capture end"))) return st;
+            st = gdg_cuda_check(ctx, cudaGraphInstantiate(&gc.exec, g, 0), "instantiate");
+            cudaGraphDestroy(g);
+            if (st) return st;
+            gc.dt = dt;
+            gc.steps = G;
+        }
+        for (int i = 0; i + G <= nsteps; i += G)
+            if ((st = gdg_cuda_check(ctx, cudaGraphLaunch(gc.exec, s), "graph launch"))) return st;
+    }
+    const int rem = G ? nsteps % G : nsteps;
+    for (int i = 0; i < rem; ++i) enqueue_rk4_step(ctx, dt, s);
+    launch_sep(ctx, buf(ctx, B_NU), buf(ctx, B_NV), u, v, T_PSI, nullptr, -1, s);
+    return gdg_cuda_check(ctx, cudaGetLastError(), "gdg_step");
+}
+
+int gdg_const_energy(gdg_ctx *ctx, const double *u, const double *v, double *E, cudaStream_t s) {
+    launch_sep(ctx, u, v, buf(ctx, B_KU), buf(ctx, B_KV), T_P, nullptr, -1, s);
+    const int blocks = 256;
+    if (ctx->dim == 2) {
+        switch (ctx->n1) {
+#define X(n) case n: k_energy_partial<n, 1><<<blocks, 256, 0, s>>>(ctx->ne, buf(ctx, B_KU), buf(ctx, B_KV), ctx->d_lam2, ctx->d_red); break;
+            GDG_N1_CASES(X)
+#undef X
+        }
+    } else {
+        switch (ctx->n1) {
+#define X(n) case n: k_energy_partial<n, 0><<<blocks, 256, 0, s>>>(ctx->ne, buf(ctx, B_KU), buf(ctx, B_KV), ctx->d_lam2, ctx->d_red); break;
+            GDG_N1_CASES(X)
+#undef X
+        }
+    }
+    k_sum_partials<<<1, 256, 0, s>>>(blocks, ctx->d_red, ctx->d_red + ctx->red_len);
+    int st;
+    if ((st = gdg_cuda_check(ctx, cudaMemcpyAsync(ctx->h_red, ctx->d_red + ctx->red_len, sizeof(double), cudaMemcpyDeviceToHost, s), "energy d2h")))
+        return st;
+    if ((st = gdg_cuda_check(ctx, cudaStreamSynchronize(s), "energy sync"))) return st;
+    *E = ctx->h_red[0];
+    return GDG_OK;
+}

@@ -1,0 +1,116 @@
+// Internal declarations shared by the host code and the CUDA translation
+// units of libgdg (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <string>
+#include <vector>
+
+#include "gdg.h"
+
+#define GDG_MAXN1 16
+
+// Per-direction modal operators of the modified GD basis (Section 3.2) in
+// physical scaling: Psi^T M Psi = I with M = H * M_hat, lambda = lambda_hat / H^2.
+//   eL[k] = Psi[0][k], eR[k] = Psi[N][k]                  (face values)
+//   gL[k] = sum_i Psi[i][k] aL[i], gR[k] likewise          (n . grad at faces)
+//   aL = -phi'(0)/H (outward -x), aR = phi'(1)/H (outward +x)
+struct ModalDir {
+    double eL[GDG_MAXN1], eR[GDG_MAXN1], gL[GDG_MAXN1], gR[GDG_MAXN1], lam[GDG_MAXN1];
+};
+
+// Everything a stage kernel needs besides buffers (passed by value).
+struct ModalParams {
+    ModalDir d[2];
+    int nx, ny, ne;
+    int per_x, per_y;     // periodic flags
+    double c2, beta, tau; // fluxes: v* = (vi+vo)/2 - beta(di+do), q* = (di-do)/2 - tau(vi-vo)
+};
+
+struct GraphCache {
+    cudaGraphExec_t exec = nullptr;
+    double dt = 0.0;
+    int steps = 0;
+};
+
+struct VarData;   // variable-coefficient / mapped data (gdg_var.cu)
+
+// CUDA-event bracketing of launches while profiling is enabled
+struct Profiler {
+    bool on = false;
+    std::vector<cudaEvent_t> pool;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> recs;
+    size_t used = 0;
+    cudaEvent_t begin(cudaStream_t s);
+    void end(int kind, cudaEvent_t start, cudaStream_t s);
+    void clear();
+    void destroy();
+};
+
+struct gdg_ctx {
+    gdg_problem pb{};
+    int dim = 1, nx = 1, ny = 1, N = 1, n1 = 2, p = 1, ne = 1;
+    long long ndof = 0;      // doubles per field
+    int device = 0;
+    std::string err;
+
+    // host 1-D reference data
+    std::vector<double> Mh, Sh, phiL, phiR, dphiL, dphiR, Psih, lamh;
+
+    // constant-coefficient Cartesian (diagonalised route)
+    ModalParams mp{};
+    double *d_mats = nullptr;     // device tables: per direction P = Psi^T M, Psi, Psi^T (n1*n1 each)
+    double *d_lam2 = nullptr;     // [n1*n1] 2-D: -c2*(lx+ly) and 1/(lx+ly) (0 for mode 0) tables
+    double *d_state = nullptr;    // modal work: yn(2 fields), acc(2), YA(2), YB(2), K(2)
+    double *d_tr = nullptr;       // two trace buffers
+    long long tr_len = 0;         // doubles per trace buffer
+    double *d_red = nullptr;      // reduction partials
+    int red_len = 0;
+    double *h_red = nullptr;      // pinned host scalar(s)
+    cudaStream_t cap_stream = nullptr;
+    GraphCache graph;
+
+    VarData *var = nullptr;
+    Profiler prof;
+    double *d_io = nullptr;       // device copies for gdg_step_host (2 fields)
+};
+
+// bracket one launch when profiling: GDG_PROF(ctx, kind, stream, launch-statement)
+#define GDG_PROF(ctx, kind, s, stmt)                                   \
+    do {                                                               \
+        cudaEvent_t gdg_ev0_ = (ctx)->prof.on ? (ctx)->prof.begin(s) : nullptr; \
+        stmt;                                                          \
+        if (gdg_ev0_) (ctx)->prof.end((kind), gdg_ev0_, (s));           \
+    } while (0)
+
+// error helpers
+int gdg_set_err(gdg_ctx *ctx, int status, const std::string &msg);
+int gdg_cuda_check(gdg_ctx *ctx, cudaError_t e, const char *where);
+
+// host basis builder (gdg_host.cpp)
+int gdg_build_basis(int p, int N, std::vector<double> &M, std::vector<double> &S,
+                    std::vector<double> &phiL, std::vector<double> &phiR,
+                    std::vector<double> &dphiL, std::vector<double> &dphiR,
+                    std::vector<double> &Psi, std::vector<double> &lam);
+void gdg_gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w);
+void gdg_eval_basis(int p, int N, double r, int cell, double *phi, double *dphi);
+
+// constant-coefficient path (gdg_const.cu)
+int gdg_const_setup(gdg_ctx *ctx);
+void gdg_const_free(gdg_ctx *ctx);
+int gdg_const_rhs(gdg_ctx *ctx, const double *u, const double *v, double *du, double *dv,
+                  cudaStream_t s);
+int gdg_const_mass_solve(gdg_ctx *ctx, int which, const double *b, double *x, cudaStream_t s);
+int gdg_const_step(gdg_ctx *ctx, double *u, double *v, double dt, int nsteps, cudaStream_t s);
+int gdg_const_energy(gdg_ctx *ctx, const double *u, const double *v, double *E, cudaStream_t s);
+
+// variable-coefficient / mapped path (gdg_var.cu)
+int gdg_var_setup(gdg_ctx *ctx);
+void gdg_var_free(gdg_ctx *ctx);
+int gdg_var_rhs(gdg_ctx *ctx, const double *u, const double *v, double *du, double *dv,
+                cudaStream_t s);
+int gdg_var_pcg(gdg_ctx *ctx, int which, const double *b, double *x, gdg_pcg_stats *st,
+                cudaStream_t s);
+int gdg_var_step(gdg_ctx *ctx, double *u, double *v, double dt, int nsteps, cudaStream_t s);
+int gdg_var_energy(gdg_ctx *ctx, const double *u, const double *v, double *E, cudaStream_t s);
+int gdg_var_step_stats(gdg_ctx *ctx, gdg_pcg_stats *su, gdg_pcg_stats *sv);

@@ -1,0 +1,1023 @@
+// Variable-coefficient / mapped-element path of libgdg (Section 7.1).
+//
+// For a variable speed of sound or a non-Cartesian element the simultaneous
+// diagonalisation does not apply; the method keeps the nodal GD basis and
+// inverts the element matrices of Eqs. DG1 / DG2 by preconditioned CG.
+// Geometry (x, y) and c^2 are given at every element's GD nodes and
+// represented in the element's own GD space; integrals use nq Gauss points
+// per GD cell per direction (Q = N*nq points per direction):
+//   M_J  = int phi_a phi_b |J|,   S_c2 = int c^2 grad phi_a . grad phi_b |J|
+//   r_u  = sum_faces int_face c^2 (n.grad phi) (v* - v_in) dS
+//   r_v  = -S_c2 U + sum_faces int_face c^2 phi q* dS
+//   (S_c2 + w w^T) y = r_u, w = M_J 1   (SPD form of Eq. DG1 with DG1_extra)
+//   M_J dV/dt = r_v,  dU/dt = V + y.
+// Preconditioner: the frozen-coefficient modified basis (Section 3.2's
+// diagonalisation on the reference element, scaled by the element means of
+// the metric c^2 |J| J^-1 J^-T and of |J|), or none.
+//
+// Kernels (one CTA per element):
+//   k_var_geom    quadrature assembly of M_J, S_c2, w and face data
+//   k_var_traces  v and n.grad u at the face quadrature points
+//   k_var_stage   fluxes + lifts + stiffness + both PCG solves (matrices in
+//                 shared memory) + RK combine + traces of the next stage input
+//   k_var_pcg     one element PCG (gdg_pcg)
+//   k_var_energy  per-element V^T M V + U^T S U
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "gdg_internal.h"
+
+#define GDG_VAR_MAXN1 10
+
+struct VarParams {
+    int nx, ny, ne, Q;
+    int per_x, per_y, upwind;
+    double xi;            // > 0: constant splitting, else local c
+    double rtol;
+    int maxit, precond;   // GDG_PC_*
+    const double *tab;    // B[Q][N1], D[Q][N1], wq[Q], dphiL[N1], dphiR[N1], Psi[N1][N1], lam[N1]
+    const double *S, *M, *w, *pre, *face;
+    unsigned long long *stats;   // [0] sum it_u, [1] sum it_v, [2] max it_u, [3] max it_v,
+                                 // [4] unconverged u, [5] unconverged v, [6] element solves
+};
+
+struct VarData {
+    int nq = 0, Q = 0, NA = 0;
+    double *d_S = nullptr, *d_M = nullptr, *d_w = nullptr, *d_pre = nullptr, *d_face = nullptr;
+    double *d_tab = nullptr, *d_nodes = nullptr;
+    double *d_state = nullptr, *d_tr = nullptr;
+    long long tr_len = 0;
+    unsigned long long *d_stats = nullptr;
+    int *d_iters = nullptr;
+    double *d_rel = nullptr, *d_red = nullptr, *h_red = nullptr;
+    VarParams vp{};
+    size_t smem_stage = 0, smem_geom = 0, smem_traces = 0, smem_pcg = 0;
+};
+
+namespace {
+
+constexpr int GEOM_THREADS = 256;
+
+__host__ __device__ constexpr int nthreads_for(int na) { return ((na + 31) / 32) * 32; }
+
+struct Tabs {
+    const double *B, *D, *wq, *dphiL, *dphiR, *Ps, *lam;
+};
+
+__device__ __forceinline__ Tabs tabs_at(const double *base, int Q, int N1) {
+    Tabs t;
+    t.B = base;
+    t.D = t.B + Q * N1;
+    t.wq = t.D + Q * N1;
+    t.dphiL = t.wq + Q;
+    t.dphiR = t.dphiL + N1;
+    t.Ps = t.dphiR + N1;
+    t.lam = t.Ps + N1 * N1;
+    return t;
+}
+__host__ __device__ constexpr int tab_len(int Q, int N1) { return 2 * Q * N1 + Q + 2 * N1 + N1 * N1 + N1; }
+
+// copy the 1-D tables into shared memory
+__device__ void load_tabs(double *dst, const double *src, int n) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+}
+
+__device__ __forceinline__ size_t fix(int e, int f, int q, int k, int Q) {   // face data
+    return (((size_t)e * 4 + f) * Q + q) * 4 + k;
+}
+__device__ __forceinline__ size_t tix(int e, int f, int fld, int q, int Q) {  // traces
+    return (((size_t)e * 4 + f) * 2 + fld) * Q + q;
+}
+
+// neighbour across face f (0 xm, 1 xp, 2 ym, 3 yp) and its facing face; -1 on a Dirichlet side
+__device__ __forceinline__ int neighbour(const VarParams &P, int e, int f, int &fo) {
+    int ex = e % P.nx, ey = e / P.nx;
+    switch (f) {
+    case 0: ex -= 1; fo = 1; break;
+    case 1: ex += 1; fo = 0; break;
+    case 2: ey -= 1; fo = 3; break;
+    default: ey += 1; fo = 2; break;
+    }
+    if (ex < 0 || ex >= P.nx) {
+        if (!P.per_x) return -1;
+        ex = (ex + P.nx) % P.nx;
+    }
+    if (ey < 0 || ey >= P.ny) {
+        if (!P.per_y) return -1;
+        ey = (ey + P.ny) % P.ny;
+    }
+    return ey * P.nx + ex;
+}
+
+// deterministic block sum: warp butterflies, then every thread adds the
+// warp partials in the same order
+__device__ __forceinline__ double block_sum(double v, double *red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    for (int i = 0; i < nw; ++i) s += red[i];
+    return s;
+}
+
+template <int NA>
+__device__ __forceinline__ double block_dot(const double *a, const double *b, double *red) {
+    const int t = threadIdx.x;
+    return block_sum(t < NA ? a[t] * b[t] : 0.0, red);
+}
+
+// y = A x for an NA x NA row-major matrix in shared memory
+template <int NA>
+__device__ __forceinline__ void matvec(const double *A, const double *x, double *y) {
+    const int t = threadIdx.x;
+    if (t < NA) {
+        double s = 0.0;
+        const double *row = A + t * NA;
+#pragma unroll 9
+        for (int k = 0; k < NA; ++k) s += row[k] * x[k];
+        y[t] = s;
+    }
+    __syncthreads();
+}
+
+// z = Psi2 diag(d) Psi2^T r, Psi2 = Psi (x) Psi (index j*N1+i), or z = r
+template <int N1>
+__device__ void precondition(const double *r, double *z, const double *Ps, const double *d, double *t1,
+                             double *t2, bool none) {
+    constexpr int NA = N1 * N1;
+    const int t = threadIdx.x;
+    if (none) {
+        if (t < NA) z[t] = r[t];
+        __syncthreads();
+        return;
+    }
+    const int a = t / N1, c = t - (t / N1) * N1;
+    if (t < NA) {   // t1[j][k] = sum_i r[j][i] Psi[i][k]
+        double s = 0.0;
+#pragma unroll
+        for (int i = 0; i < N1; ++i) s += r[a * N1 + i] * Ps[i * N1 + c];
+        t1[t] = s;
+    }
+    __syncthreads();
+    if (t < NA) {   // t2[l][k] = d[l][k] sum_j Psi[j][l] t1[j][k]
+        double s = 0.0;
+#pragma unroll
+        for (int j = 0; j < N1; ++j) s += Ps[j * N1 + a] * t1[j * N1 + c];
+        t2[t] = d[t] * s;
+    }
+    __syncthreads();
+    if (t < NA) {   // t1[l][i] = sum_k t2[l][k] Psi[i][k]
+        double s = 0.0;
+#pragma unroll
+        for (int k = 0; k < N1; ++k) s += t2[a * N1 + k] * Ps[c * N1 + k];
+        t1[t] = s;
+    }
+    __syncthreads();
+    if (t < NA) {   // z[j][i] = sum_l Psi[j][l] t1[l][i]
+        double s = 0.0;
+#pragma unroll
+        for (int l = 0; l < N1; ++l) s += Ps[a * N1 + l] * t1[l * N1 + c];
+        z[t] = s;
+    }
+    __syncthreads();
+}
+
+// Preconditioned CG on A (+ w w^T when W) with x0 = x (x0_zero: x0 = 0).
+// Stops when ||r|| <= rtol ||b|| (tested before each iteration), after
+// maxit iterations, or when r.z = 0.  Returns the iteration count.
+template <int N1, bool W>
+__device__ int pcg(const double *A, const double *w, const double *b, double *x, double *r, double *z,
+                   double *p, double *Ap, const double *Ps, const double *d, double *t1, double *t2,
+                   double *red, double rtol, int maxit, bool none, bool x0_zero, double *relres) {
+    constexpr int NA = N1 * N1;
+    const int t = threadIdx.x;
+    if (x0_zero) {
+        if (t < NA) { x[t] = 0.0; r[t] = b[t]; }
+        __syncthreads();
+    } else {
+        matvec<NA>(A, x, Ap);
+        double wx = W ? block_dot<NA>(w, x, red) : 0.0;
+        if (t < NA) r[t] = b[t] - Ap[t] - (W ? w[t] * wx : 0.0);
+        __syncthreads();
+    }
+    const double bnorm = sqrt(block_dot<NA>(b, b, red));
+    precondition<N1>(r, z, Ps, d, t1, t2, none);
+    if (t < NA) p[t] = z[t];
+    __syncthreads();
+    double rz = block_dot<NA>(r, z, red);
+    int it = 0;
+    while (it < maxit) {
+        const double rr = block_dot<NA>(r, r, red);
+        if (sqrt(rr) <= rtol * bnorm || rz == 0.0) break;
+        matvec<NA>(A, p, Ap);
+        if (W) {
+            const double wp = block_dot<NA>(w, p, red);
+            if (t < NA) Ap[t] += w[t] * wp;
+            __syncthreads();
+        }
+        const double pAp = block_dot<NA>(p, Ap, red);
+        const double alpha = rz / pAp;
+        if (t < NA) {
+            x[t] += alpha * p[t];
+            r[t] -= alpha * Ap[t];
+        }
+        __syncthreads();
+        precondition<N1>(r, z, Ps, d, t1, t2, none);
+        const double rzn = block_dot<NA>(r, z, red);
+        const double beta = rzn / rz;
+        if (t < NA) p[t] = z[t] + beta * p[t];
+        __syncthreads();
+        rz = rzn;
+        ++it;
+    }
+    const double rr = block_dot<NA>(r, r, red);
+    *relres = bnorm > 0.0 ? sqrt(rr) / bnorm : 0.0;
+    return it;
+}
+
+// diagonal of the frozen-coefficient preconditioner in the modified basis
+template <int N1>
+__device__ void fdm_diagonals(const double *pre, const double *lam, double *dS, double *dM) {
+    constexpr int NA = N1 * N1;
+    const int t = threadIdx.x;
+    if (t < NA) {
+        const double Grr = pre[0], Gss = pre[1], Jb = pre[2];
+        const int l = t / N1, k = t - (t / N1) * N1;
+        dS[t] = t == 0 ? 1.0 / (Jb * Jb) : 1.0 / (Gss * lam[l] + Grr * lam[k]);
+        dM[t] = 1.0 / Jb;
+    }
+}
+
+// --------------------------------------------------------- assembly -------
+
+template <int N1>
+__global__ void __launch_bounds__(GEOM_THREADS)
+k_var_geom(VarParams P, const double *X, const double *Y, const double *C2, double *Sout, double *Mout,
+           double *wout, double *pre, double *face) {
+    constexpr int NA = N1 * N1;
+    extern __shared__ double sm[];
+    const int Q = P.Q, e = blockIdx.x, t = threadIdx.x;
+    double *tb = sm;
+    double *nx_ = tb + tab_len(Q, N1);
+    double *ny_ = nx_ + NA, *nc = ny_ + NA;
+    double *XD = nc + NA, *XB = XD + N1 * Q, *YD = XB + N1 * Q, *YB = YD + N1 * Q, *CB = YB + N1 * Q;
+    double *Wr = CB + N1 * Q, *Grr = Wr + Q, *Gss = Grr + Q, *Grs = Gss + Q;
+    double *CM = Grs + Q, *Crr = CM + NA, *Css = Crr + NA, *Crs = Css + NA;
+    double *red = Crs + NA;    // [32] reduction scratch
+    load_tabs(tb, P.tab, tab_len(Q, N1));
+    const Tabs T = tabs_at(tb, Q, N1);
+    for (int i = t; i < NA; i += blockDim.x) {
+        nx_[i] = X[(size_t)e * NA + i];
+        ny_[i] = Y[(size_t)e * NA + i];
+        nc[i] = C2[(size_t)e * NA + i];
+    }
+    double sGrr = 0.0, sGss = 0.0, sW = 0.0;   // this thread's share of the element means
+    __syncthreads();
+    // XD[j][a] = sum_i X[j][i] D[a][i], XB[j][a] = sum_i X[j][i] B[a][i] (same for Y; C2 with B)
+    for (int task = t; task < N1 * Q; task += blockDim.x) {
+        const int j = task / Q, a = task - (task / Q) * Q;
+        double xd = 0, xb = 0, yd = 0, yb = 0, cb = 0;
+        for (int i = 0; i < N1; ++i) {
+            const double Bi = T.B[a * N1 + i], Di = T.D[a * N1 + i];
+            xd += nx_[j * N1 + i] * Di; xb += nx_[j * N1 + i] * Bi;
+            yd += ny_[j * N1 + i] * Di; yb += ny_[j * N1 + i] * Bi;
+            cb += nc[j * N1 + i] * Bi;
+        }
+        XD[task] = xd; XB[task] = xb; YD[task] = yd; YB[task] = yb; CB[task] = cb;
+    }
+    __syncthreads();
+    constexpr int PER = (NA * NA + GEOM_THREADS - 1) / GEOM_THREADS;
+    for (int pass = 0; pass < 2; ++pass) {   // 0: M_J, 1: S_c2
+        double accv[PER];
+#pragma unroll
+        for (int m = 0; m < PER; ++m) accv[m] = 0.0;
+        for (int b = 0; b < Q; ++b) {
+            for (int a = t; a < Q; a += blockDim.x) {
+                double xr = 0, xs = 0, yr = 0, ys = 0, c2 = 0;
+                for (int j = 0; j < N1; ++j) {
+                    const double Bj = T.B[b * N1 + j], Dj = T.D[b * N1 + j];
+                    xr += Bj * XD[j * Q + a]; xs += Dj * XB[j * Q + a];
+                    yr += Bj * YD[j * Q + a]; ys += Dj * YB[j * Q + a];
+                    c2 += Bj * CB[j * Q + a];
+                }
+                const double det = xr * ys - xs * yr;
+                const double ww = T.wq[a] * T.wq[b];
+                Wr[a] = ww * det;
+                Grr[a] = ww * c2 * (xs * xs + ys * ys) / det;
+                Gss[a] = ww * c2 * (xr * xr + yr * yr) / det;
+                Grs[a] = -ww * c2 * (xr * xs + yr * ys) / det;
+                if (pass == 0) { sGrr += Grr[a]; sGss += Gss[a]; sW += Wr[a]; }
+            }
+            __syncthreads();
+            for (int task = t; task < NA; task += blockDim.x) {
+                const int i = task / N1, i2 = task - (task / N1) * N1;
+                if (pass == 0) {
+                    double s = 0;
+                    for (int a = 0; a < Q; ++a) s += Wr[a] * T.B[a * N1 + i] * T.B[a * N1 + i2];
+                    CM[task] = s;
+                } else {
+                    double srr = 0, sss = 0, srs = 0;
+                    for (int a = 0; a < Q; ++a) {
+                        const double Bi = T.B[a * N1 + i], Di = T.D[a * N1 + i];
+                        const double Bi2 = T.B[a * N1 + i2], Di2 = T.D[a * N1 + i2];
+                        srr += Grr[a] * Di * Di2;
+                        sss += Gss[a] * Bi * Bi2;
+                        srs += Grs[a] * Di * Bi2;
+                    }
+                    Crr[task] = srr; Css[task] = sss; Crs[task] = srs;
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int m = 0; m < PER; ++m) {
+                const int o = t + m * GEOM_THREADS;
+                if (o < NA * NA) {
+                    const int al = o / NA, be = o - (o / NA) * NA;
+                    const int j = al / N1, i = al - (al / N1) * N1, j2 = be / N1, i2 = be - (be / N1) * N1;
+                    const double Bj = T.B[b * N1 + j], Bj2 = T.B[b * N1 + j2];
+                    if (pass == 0) {
+                        accv[m] += Bj * Bj2 * CM[i * N1 + i2];
+                    } else {
+                        const double Dj = T.D[b * N1 + j], Dj2 = T.D[b * N1 + j2];
+                        accv[m] += Bj * Bj2 * Crr[i * N1 + i2] + Dj * Dj2 * Css[i * N1 + i2] +
+                                   Bj * Dj2 * Crs[i * N1 + i2] + Dj * Bj2 * Crs[i2 * N1 + i];
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        double *out = (pass == 0 ? Mout : Sout) + (size_t)e * NA * NA;
+#pragma unroll
+        for (int m = 0; m < PER; ++m) {
+            const int o = t + m * GEOM_THREADS;
+            if (o < NA * NA) out[o] = accv[m];
+        }
+        __syncthreads();
+    }
+    // w = M_J 1 (row sums of what was just written), frozen-coefficient scalars
+    sGrr = block_sum(sGrr, red);
+    sGss = block_sum(sGss, red);
+    sW = block_sum(sW, red);
+    if (t < NA) {
+        const double *row = Mout + (size_t)e * NA * NA + (size_t)t * NA;
+        double s = 0.0;
+        for (int k = 0; k < NA; ++k) s += row[k];
+        wout[(size_t)e * NA + t] = s;
+    }
+    if (t == 0) {
+        pre[(size_t)e * 4 + 0] = sGrr;
+        pre[(size_t)e * 4 + 1] = sGss;
+        pre[(size_t)e * 4 + 2] = sW;
+        pre[(size_t)e * 4 + 3] = 0.0;
+    }
+    // face data: fr, fs (J^-1 n), c^2 |T| w, c at every face point
+    for (int task = t; task < 4 * Q; task += blockDim.x) {
+        const int f = task / Q, q = task - (task / Q) * Q;
+        const double *dphi = (f == 0 || f == 2) ? T.dphiL : T.dphiR;
+        double xr = 0, xs = 0, yr = 0, ys = 0, c2 = 0;
+        if (f < 2) {   // r = 0 / 1, parametrised by s_q
+            const int col = f == 0 ? 0 : N1 - 1;
+            for (int j = 0; j < N1; ++j) {
+                double dx = 0, dy = 0;
+                for (int i = 0; i < N1; ++i) { dx += nx_[j * N1 + i] * dphi[i]; dy += ny_[j * N1 + i] * dphi[i]; }
+                const double Bj = T.B[q * N1 + j], Dj = T.D[q * N1 + j];
+                xr += Bj * dx; yr += Bj * dy;
+                xs += Dj * nx_[j * N1 + col]; ys += Dj * ny_[j * N1 + col];
+                c2 += Bj * nc[j * N1 + col];
+            }
+        } else {       // s = 0 / 1, parametrised by r_q
+            const int row = f == 2 ? 0 : N1 - 1;
+            for (int i = 0; i < N1; ++i) {
+                double dx = 0, dy = 0;
+                for (int j = 0; j < N1; ++j) { dx += nx_[j * N1 + i] * dphi[j]; dy += ny_[j * N1 + i] * dphi[j]; }
+                const double Bi = T.B[q * N1 + i], Di = T.D[q * N1 + i];
+                xs += Bi * dx; ys += Bi * dy;
+                xr += Di * nx_[row * N1 + i]; yr += Di * ny_[row * N1 + i];
+                c2 += Bi * nc[row * N1 + i];
+            }
+        }
+        double tn, nxv, nyv;
+        if (f < 2) { tn = sqrt(xs * xs + ys * ys); nxv = ys / tn; nyv = -xs / tn; }
+        else { tn = sqrt(xr * xr + yr * yr); nxv = -yr / tn; nyv = xr / tn; }
+        if (f == 0 || f == 2) { nxv = -nxv; nyv = -nyv; }
+        const double det = xr * ys - xs * yr;
+        face[fix(e, f, q, 0, Q)] = (ys * nxv - xs * nyv) / det;
+        face[fix(e, f, q, 1, Q)] = (-yr * nxv + xr * nyv) / det;
+        face[fix(e, f, q, 2, Q)] = c2 * tn * T.wq[q];
+        face[fix(e, f, q, 3, Q)] = sqrt(c2);
+    }
+}
+
+// ----------------------------------------------------------- traces ------
+
+// line data of the 4 faces from nodal U, V in shared memory:
+// L[(f*3 + m)*N1 + j]: m = 0 value line of v, 1 the r-derivative data, 2 the s-derivative data
+template <int N1>
+__device__ void face_lines(const double *U, const double *V, const Tabs &T, double *L) {
+    for (int task = threadIdx.x; task < 12 * N1; task += blockDim.x) {
+        const int f = task / (3 * N1), m = (task / N1) % 3, j = task % N1;
+        const double *dphi = (f == 0 || f == 2) ? T.dphiL : T.dphiR;
+        const int edge = (f == 0 || f == 2) ? 0 : N1 - 1;
+        double s = 0.0;
+        if (f < 2) {   // x faces, line index j (rows)
+            if (m == 0) s = V[j * N1 + edge];
+            else if (m == 1) { for (int i = 0; i < N1; ++i) s += U[j * N1 + i] * dphi[i]; }
+            else s = U[j * N1 + edge];
+        } else {       // y faces, line index i (columns)
+            const int i = j;
+            if (m == 0) s = V[edge * N1 + i];
+            else if (m == 1) s = U[edge * N1 + i];
+            else { for (int jj = 0; jj < N1; ++jj) s += U[jj * N1 + i] * dphi[jj]; }
+        }
+        L[task] = s;
+    }
+    __syncthreads();
+}
+
+// v and n.grad u at every face point from the line data
+template <int N1>
+__device__ void face_points(const double *L, const Tabs &T, const double *face, int e, int Q, double *trout) {
+    for (int task = threadIdx.x; task < 4 * Q; task += blockDim.x) {
+        const int f = task / Q, q = task - (task / Q) * Q;
+        const double *l0 = L + (f * 3 + 0) * N1, *l1 = L + (f * 3 + 1) * N1, *l2 = L + (f * 3 + 2) * N1;
+        double v = 0, ur = 0, us = 0;
+        for (int j = 0; j < N1; ++j) {
+            const double Bq = T.B[q * N1 + j], Dq = T.D[q * N1 + j];
+            v += Bq * l0[j];
+            if (f < 2) { ur += Bq * l1[j]; us += Dq * l2[j]; }
+            else { ur += Dq * l1[j]; us += Bq * l2[j]; }
+        }
+        const double fr = face[fix(e, f, q, 0, Q)], fs = face[fix(e, f, q, 1, Q)];
+        trout[tix(e, f, 0, q, Q)] = v;
+        trout[tix(e, f, 1, q, Q)] = fr * ur + fs * us;
+    }
+}
+
+template <int N1>
+__global__ void k_var_traces(VarParams P, const double *u, const double *v, double *trout) {
+    constexpr int NA = N1 * N1;
+    extern __shared__ double sm[];
+    const int Q = P.Q, e = blockIdx.x;
+    double *tb = sm, *U = tb + tab_len(Q, N1), *V = U + NA, *L = V + NA;
+    load_tabs(tb, P.tab, tab_len(Q, N1));
+    for (int i = threadIdx.x; i < NA; i += blockDim.x) {
+        U[i] = u[(size_t)e * NA + i];
+        V[i] = v[(size_t)e * NA + i];
+    }
+    __syncthreads();
+    const Tabs T = tabs_at(tb, Q, N1);
+    face_lines<N1>(U, V, T, L);
+    face_points<N1>(L, T, P.face, e, Q, trout);
+}
+
+// ------------------------------------------------------------ stage ------
+
+constexpr int M_RHS = 0, M_S1 = 1, M_S23 = 2, M_S4 = 3;
+
+struct VarBufs {
+    const double *yU, *yV;   // stage input (nodal)
+    double *nU, *nV, *aU, *aV, *oU, *oV;
+    const double *trin;
+    double *trout;
+};
+
+template <int N1>
+struct StageSmem {
+    static constexpr int NA = N1 * N1;
+    double *A, *tb, *Yu, *Yv, *ru, *rv, *x, *r, *z, *p, *Ap, *w, *dS, *dM, *t1, *t2, *fw, *L, *red;
+    __device__ StageSmem(double *base, int Q) {
+        A = base;
+        tb = A + NA * NA;
+        Yu = tb + tab_len(Q, N1);
+        Yv = Yu + NA; ru = Yv + NA; rv = ru + NA; x = rv + NA; r = x + NA; z = r + NA; p = z + NA;
+        Ap = p + NA; w = Ap + NA; dS = w + NA; dM = dS + NA; t1 = dM + NA; t2 = t1 + NA;
+        fw = t2 + NA; L = fw + 12 * Q; red = L + 12 * N1;
+    }
+    static size_t bytes(int Q) {
+        return sizeof(double) * ((size_t)NA * NA + tab_len(Q, N1) + 14 * NA + 12 * Q + 12 * N1 + 32);
+    }
+};
+
+// face fluxes and lifts: r_u, r_v (r_v without the stiffness term)
+template <int N1>
+__device__ void lifts(const VarParams &P, int e, const double *trin, const Tabs &T, double *fw, double *L,
+                      double *ru, double *rv) {
+    constexpr int NA = N1 * N1;
+    const int Q = P.Q, t = threadIdx.x;
+    for (int task = t; task < 4 * Q; task += blockDim.x) {
+        const int f = task / Q, q = task - (task / Q) * Q;
+        const double vi = trin[tix(e, f, 0, q, Q)], di = trin[tix(e, f, 1, q, Q)];
+        int fo;
+        const int nb = neighbour(P, e, f, fo);
+        double vo, dO;
+        if (nb >= 0) { vo = trin[tix(nb, fo, 0, q, Q)]; dO = trin[tix(nb, fo, 1, q, Q)]; }
+        else { vo = -vi; dO = -di; }   // u = 0: mirror state
+        double beta = 0.0, tau = 0.0;
+        if (P.upwind) {
+            const double xi = P.xi > 0.0 ? P.xi : P.face[fix(e, f, q, 3, Q)];
+            beta = 0.5 * xi;
+            tau = 0.5 / xi;
+        }
+        const double vstar = 0.5 * (vi + vo) - beta * (di + dO);
+        const double qstar = 0.5 * (di - dO) - tau * (vi - vo);
+        const double g = vstar - vi;
+        const double cw = P.face[fix(e, f, q, 2, Q)];
+        fw[(f * 3 + 0) * Q + q] = cw * P.face[fix(e, f, q, 0, Q)] * g;
+        fw[(f * 3 + 1) * Q + q] = cw * P.face[fix(e, f, q, 1, Q)] * g;
+        fw[(f * 3 + 2) * Q + q] = cw * qstar;
+    }
+    __syncthreads();
+    for (int task = t; task < 12 * N1; task += blockDim.x) {
+        const int f = task / (3 * N1), m = (task / N1) % 3, j = task % N1;
+        const double *src = fw + (f * 3 + m) * Q;
+        // x faces: (B, D, B); y faces: (D, B, B)
+        const bool useD = (f < 2) ? (m == 1) : (m == 0);
+        const double *tab = useD ? T.D : T.B;
+        double s = 0.0;
+        for (int q = 0; q < Q; ++q) s += tab[q * N1 + j] * src[q];
+        L[task] = s;
+    }
+    __syncthreads();
+    if (t < NA) {
+        const int j = t / N1, i = t - (t / N1) * N1;
+        const double *Lx0 = L, *Lx1 = L + 3 * N1, *Ly0 = L + 6 * N1, *Ly1 = L + 9 * N1;
+        double u_ = T.dphiL[i] * Lx0[j] + T.dphiR[i] * Lx1[j] + T.dphiL[j] * Ly0[N1 + i] + T.dphiR[j] * Ly1[N1 + i];
+        double v_ = 0.0;
+        if (i == 0) { u_ += Lx0[N1 + j]; v_ += Lx0[2 * N1 + j]; }
+        if (i == N1 - 1) { u_ += Lx1[N1 + j]; v_ += Lx1[2 * N1 + j]; }
+        if (j == 0) { u_ += Ly0[i]; v_ += Ly0[2 * N1 + i]; }
+        if (j == N1 - 1) { u_ += Ly1[i]; v_ += Ly1[2 * N1 + i]; }
+        ru[t] = u_;
+        rv[t] = v_;
+    }
+    __syncthreads();
+}
+
+template <int N1>
+__device__ void load_matrix(double *A, const double *src) {
+    constexpr int NA = N1 * N1;
+    // element matrices start at e*NA*NA doubles: only 8-byte alignment is guaranteed
+    for (int i = threadIdx.x; i < NA * NA; i += blockDim.x) A[i] = src[i];
+    __syncthreads();
+}
+
+template <int N1, int MODE>
+__global__ void __launch_bounds__(nthreads_for(N1 * N1))
+k_var_stage(VarParams P, VarBufs b, double cA, double cY) {
+    constexpr int NA = N1 * N1;
+    extern __shared__ double smraw[];
+    StageSmem<N1> s(smraw, P.Q);
+    const int e = blockIdx.x, t = threadIdx.x;
+    const size_t off = (size_t)e * NA;
+    load_tabs(s.tb, P.tab, tab_len(P.Q, N1));
+    if (t < NA) {
+        s.Yu[t] = b.yU[off + t];
+        s.Yv[t] = b.yV[off + t];
+        s.w[t] = P.w[off + t];
+    }
+    __syncthreads();
+    const Tabs T = tabs_at(s.tb, P.Q, N1);
+    fdm_diagonals<N1>(P.pre + (size_t)e * 4, T.lam, s.dS, s.dM);
+    lifts<N1>(P, e, b.trin, T, s.fw, s.L, s.ru, s.rv);
+    // stiffness: r_v -= S U
+    load_matrix<N1>(s.A, P.S + (size_t)e * NA * NA);
+    matvec<NA>(s.A, s.Yu, s.Ap);
+    if (t < NA) s.rv[t] -= s.Ap[t];
+    __syncthreads();
+    const bool none = P.precond == GDG_PC_NONE;
+    double rel_u, rel_v;
+    const int it_u = pcg<N1, true>(s.A, s.w, s.ru, s.x, s.r, s.z, s.p, s.Ap, T.Ps, s.dS, s.t1, s.t2, s.red,
+                                   P.rtol, P.maxit, none, true, &rel_u);
+    if (t < NA) s.ru[t] = s.Yv[t] + s.x[t];   // dU/dt
+    __syncthreads();
+    load_matrix<N1>(s.A, P.M + (size_t)e * NA * NA);
+    const int it_v = pcg<N1, false>(s.A, s.w, s.rv, s.x, s.r, s.z, s.p, s.Ap, T.Ps, s.dM, s.t1, s.t2, s.red,
+                                    P.rtol, P.maxit, none, true, &rel_v);
+    if (t == 0 && P.stats) {
+        atomicAdd(&P.stats[0], (unsigned long long)it_u);
+        atomicAdd(&P.stats[1], (unsigned long long)it_v);
+        atomicMax(&P.stats[2], (unsigned long long)it_u);
+        atomicMax(&P.stats[3], (unsigned long long)it_v);
+        if (it_u >= P.maxit && rel_u > P.rtol) atomicAdd(&P.stats[4], 1ull);
+        if (it_v >= P.maxit && rel_v > P.rtol) atomicAdd(&P.stats[5], 1ull);
+        atomicAdd(&P.stats[6], 1ull);
+    }
+    // k = (ru, x); RK combine into Yu / Yv (next stage input) in shared memory
+    if (t < NA) {
+        const double ku = s.ru[t], kv = s.x[t];
+        if (MODE == M_RHS) {
+            b.oU[off + t] = ku;
+            b.oV[off + t] = kv;
+        } else if (MODE == M_S1) {
+            b.aU[off + t] = cA * ku;
+            b.aV[off + t] = cA * kv;
+            s.Yu[t] = s.Yu[t] + cY * ku;
+            s.Yv[t] = s.Yv[t] + cY * kv;
+        } else if (MODE == M_S23) {
+            b.aU[off + t] += cA * ku;
+            b.aV[off + t] += cA * kv;
+            s.Yu[t] = b.nU[off + t] + cY * ku;
+            s.Yv[t] = b.nV[off + t] + cY * kv;
+        } else {
+            s.Yu[t] = b.nU[off + t] + b.aU[off + t] + cA * ku;
+            s.Yv[t] = b.nV[off + t] + b.aV[off + t] + cA * kv;
+        }
+        if (MODE != M_RHS) {
+            double *dU = MODE == M_S4 ? b.nU : b.oU;
+            double *dV = MODE == M_S4 ? b.nV : b.oV;
+            dU[off + t] = s.Yu[t];
+            dV[off + t] = s.Yv[t];
+        }
+    }
+    if (MODE == M_RHS) return;
+    __syncthreads();
+    face_lines<N1>(s.Yu, s.Yv, T, s.L);
+    face_points<N1>(s.L, T, P.face, e, P.Q, b.trout);
+}
+
+// standalone element PCG (gdg_pcg): which = 0 M, 1 S (+ w w^T)
+template <int N1>
+__global__ void __launch_bounds__(nthreads_for(N1 * N1))
+k_var_pcg(VarParams P, int which, const double *bvec, double *xvec, int *iters, double *rel) {
+    constexpr int NA = N1 * N1;
+    extern __shared__ double smraw[];
+    StageSmem<N1> s(smraw, P.Q);
+    const int e = blockIdx.x, t = threadIdx.x;
+    const size_t off = (size_t)e * NA;
+    load_tabs(s.tb, P.tab, tab_len(P.Q, N1));
+    if (t < NA) {
+        s.ru[t] = bvec[off + t];
+        s.x[t] = xvec[off + t];
+        s.w[t] = P.w[off + t];
+    }
+    __syncthreads();
+    const Tabs T = tabs_at(s.tb, P.Q, N1);
+    fdm_diagonals<N1>(P.pre + (size_t)e * 4, T.lam, s.dS, s.dM);
+    load_matrix<N1>(s.A, (which ? P.S : P.M) + (size_t)e * NA * NA);
+    const bool none = P.precond == GDG_PC_NONE;
+    double rr;
+    int it;
+    if (which)
+        it = pcg<N1, true>(s.A, s.w, s.ru, s.x, s.r, s.z, s.p, s.Ap, T.Ps, s.dS, s.t1, s.t2, s.red, P.rtol,
+                           P.maxit, none, false, &rr);
+    else
+        it = pcg<N1, false>(s.A, s.w, s.ru, s.x, s.r, s.z, s.p, s.Ap, T.Ps, s.dM, s.t1, s.t2, s.red, P.rtol,
+                            P.maxit, none, false, &rr);
+    if (t < NA) xvec[off + t] = s.x[t];
+    if (t == 0) {
+        iters[e] = it;
+        rel[e] = rr;
+    }
+}
+
+// per-element V^T M V + U^T S U
+template <int N1>
+__global__ void __launch_bounds__(nthreads_for(N1 * N1))
+k_var_energy(VarParams P, const double *u, const double *v, double *part) {
+    constexpr int NA = N1 * N1;
+    __shared__ double U[NA], V[NA], red[32];
+    const int e = blockIdx.x, t = threadIdx.x;
+    if (t < NA) { U[t] = u[(size_t)e * NA + t]; V[t] = v[(size_t)e * NA + t]; }
+    __syncthreads();
+    double s = 0.0;
+    if (t < NA) {
+        const double *Mr = P.M + ((size_t)e * NA + t) * NA, *Sr = P.S + ((size_t)e * NA + t) * NA;
+        double mv = 0.0, su = 0.0;
+        for (int k = 0; k < NA; ++k) { mv += Mr[k] * V[k]; su += Sr[k] * U[k]; }
+        s = V[t] * mv + U[t] * su;
+    }
+    s = block_sum(s, red);
+    if (t == 0) part[e] = s;
+}
+
+__global__ void k_var_sum(int n, const double *part, double *out) {
+    __shared__ double red[1024];
+    const int t = threadIdx.x;
+    double s = 0.0;
+    for (int i = t; i < n; i += blockDim.x) s += part[i];
+    red[t] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (t < w) red[t] += red[t + w];
+        __syncthreads();
+    }
+    if (t == 0) out[0] = 0.5 * red[0];
+}
+
+// ---------------------------------------------------------- dispatch -----
+
+#define GDG_VAR_CASES(X) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10)
+
+size_t geom_smem(int N1, int Q) {
+    const int NA = N1 * N1;
+    return sizeof(double) * ((size_t)tab_len(Q, N1) + 3 * NA + 5 * N1 * Q + 4 * Q + 4 * NA + 32);
+}
+size_t traces_smem(int N1, int Q) { return sizeof(double) * ((size_t)tab_len(Q, N1) + 2 * N1 * N1 + 12 * N1); }
+
+template <int N1>
+size_t stage_smem(int Q) { return StageSmem<N1>::bytes(Q); }
+
+template <int N1>
+void set_attrs(size_t sg, size_t st, size_t ss) {
+    cudaFuncSetAttribute(k_var_geom<N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sg);
+    cudaFuncSetAttribute(k_var_traces<N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)st);
+    cudaFuncSetAttribute(k_var_stage<N1, M_RHS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
+    cudaFuncSetAttribute(k_var_stage<N1, M_S1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
+    cudaFuncSetAttribute(k_var_stage<N1, M_S23>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
+    cudaFuncSetAttribute(k_var_stage<N1, M_S4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
+    cudaFuncSetAttribute(k_var_pcg<N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
+}
+
+template <int N1>
+void launch_stage_n(const VarData &D, int mode, const VarBufs &b, double cA, double cY, cudaStream_t s) {
+    const dim3 grid(D.vp.ne), block(nthreads_for(N1 * N1));
+    const size_t sm = D.smem_stage;
+    switch (mode) {
+    case M_RHS: k_var_stage<N1, M_RHS><<<grid, block, sm, s>>>(D.vp, b, cA, cY); break;
+    case M_S1: k_var_stage<N1, M_S1><<<grid, block, sm, s>>>(D.vp, b, cA, cY); break;
+    case M_S23: k_var_stage<N1, M_S23><<<grid, block, sm, s>>>(D.vp, b, cA, cY); break;
+    default: k_var_stage<N1, M_S4><<<grid, block, sm, s>>>(D.vp, b, cA, cY); break;
+    }
+}
+
+void launch_stage_raw(gdg_ctx *ctx, int mode, const VarBufs &b, double cA, double cY, cudaStream_t s) {
+    const VarData &D = *ctx->var;
+    switch (ctx->n1) {
+#define X(n) case n: launch_stage_n<n>(D, mode, b, cA, cY, s); break;
+        GDG_VAR_CASES(X)
+#undef X
+    }
+}
+
+void launch_stage(gdg_ctx *ctx, int mode, const VarBufs &b, double cA, double cY, cudaStream_t s) {
+    GDG_PROF(ctx, GDG_K_PCG, s, launch_stage_raw(ctx, mode, b, cA, cY, s));
+}
+
+void launch_traces_raw(gdg_ctx *ctx, const double *u, const double *v, double *tr, cudaStream_t s) {
+    const VarData &D = *ctx->var;
+    const dim3 grid(D.vp.ne), block(128);
+    switch (ctx->n1) {
+#define X(n) case n: k_var_traces<n><<<grid, block, D.smem_traces, s>>>(D.vp, u, v, tr); break;
+        GDG_VAR_CASES(X)
+#undef X
+    }
+}
+
+void launch_traces(gdg_ctx *ctx, const double *u, const double *v, double *tr, cudaStream_t s) {
+    GDG_PROF(ctx, GDG_K_TRACES, s, launch_traces_raw(ctx, u, v, tr, s));
+}
+
+void launch_pcg_raw(gdg_ctx *ctx, int which, const double *b, double *x, cudaStream_t s) {
+    const VarData &D = *ctx->var;
+    const dim3 grid(ctx->ne), block(nthreads_for(ctx->n1 * ctx->n1));
+    switch (ctx->n1) {
+#define X(n) case n: k_var_pcg<n><<<grid, block, D.smem_stage, s>>>(D.vp, which == GDG_OP_S, b, x, D.d_iters, D.d_rel); break;
+        GDG_VAR_CASES(X)
+#undef X
+    }
+}
+
+double *vbuf(gdg_ctx *ctx, int i) { return ctx->var->d_state + (size_t)i * ctx->ndof; }
+enum { B_NU = 0, B_NV, B_AU, B_AV, B_XU, B_XV, B_YU, B_YV, B_COUNT };
+
+void enqueue_step(gdg_ctx *ctx, double dt, cudaStream_t s) {
+    VarData &D = *ctx->var;
+    double *tr0 = D.d_tr, *tr1 = D.d_tr + D.tr_len;
+    VarBufs b{};
+    b.nU = vbuf(ctx, B_NU); b.nV = vbuf(ctx, B_NV);
+    b.aU = vbuf(ctx, B_AU); b.aV = vbuf(ctx, B_AV);
+    b.yU = b.nU; b.yV = b.nV; b.oU = vbuf(ctx, B_XU); b.oV = vbuf(ctx, B_XV); b.trin = tr0; b.trout = tr1;
+    launch_stage(ctx, M_S1, b, dt / 6.0, 0.5 * dt, s);
+    b.yU = vbuf(ctx, B_XU); b.yV = vbuf(ctx, B_XV); b.oU = vbuf(ctx, B_YU); b.oV = vbuf(ctx, B_YV); b.trin = tr1; b.trout = tr0;
+    launch_stage(ctx, M_S23, b, dt / 3.0, 0.5 * dt, s);
+    b.yU = vbuf(ctx, B_YU); b.yV = vbuf(ctx, B_YV); b.oU = vbuf(ctx, B_XU); b.oV = vbuf(ctx, B_XV); b.trin = tr0; b.trout = tr1;
+    launch_stage(ctx, M_S23, b, dt / 3.0, dt, s);
+    b.yU = vbuf(ctx, B_XU); b.yV = vbuf(ctx, B_XV); b.oU = nullptr; b.oV = nullptr; b.trin = tr1; b.trout = tr0;
+    launch_stage(ctx, M_S4, b, dt / 6.0, 0.0, s);
+}
+
+int check_stats_noconv(gdg_ctx *ctx, cudaStream_t s, int *unconv) {
+    unsigned long long h[7];
+    int st = gdg_cuda_check(ctx, cudaMemcpyAsync(h, ctx->var->d_stats, sizeof(h), cudaMemcpyDeviceToHost, s), "stats");
+    if (!st) st = gdg_cuda_check(ctx, cudaStreamSynchronize(s), "stats sync");
+    if (st) return st;
+    *unconv = (int)(h[4] + h[5]);
+    return GDG_OK;
+}
+
+}  // namespace
+
+// --------------------------------------------------------------- API -----
+
+int gdg_var_setup(gdg_ctx *ctx) {
+    if (ctx->n1 > GDG_VAR_MAXN1)
+        return gdg_set_err(ctx, GDG_EUNSUPPORTED, "variable coefficients need N+1 <= 10");
+    VarData *D = new (std::nothrow) VarData();
+    if (!D) return GDG_ENOMEM;
+    ctx->var = D;
+    const int n1 = ctx->n1, NA = n1 * n1, N = ctx->N, p = ctx->p;
+    D->nq = ctx->pb.nquad > 0 ? ctx->pb.nquad : p + 1;
+    D->Q = N * D->nq;
+    D->NA = NA;
+    const int Q = D->Q;
+    // 1-D tables on the host: composite Gauss rule, basis values / slopes at the points
+    std::vector<double> gx, gw;
+    gdg_gauss_legendre(D->nq, gx, gw);
+    std::vector<double> tab(tab_len(Q, n1), 0.0);
+    double *B = tab.data(), *Dd = B + Q * n1, *wq = Dd + Q * n1, *dL = wq + Q, *dR = dL + n1, *Ps = dR + n1,
+           *lam = Ps + n1 * n1;
+    for (int k = 0; k < N; ++k)
+        for (int g = 0; g < D->nq; ++g) {
+            const int q = k * D->nq + g;
+            gdg_eval_basis(p, N, (k + gx[g]) / N, k, B + q * n1, Dd + q * n1);
+            wq[q] = gw[g] / N;
+        }
+    for (int i = 0; i < n1; ++i) { dL[i] = ctx->dphiL[i]; dR[i] = ctx->dphiR[i]; lam[i] = ctx->lamh[i]; }
+    for (int i = 0; i < NA; ++i) Ps[i] = ctx->Psih[i];
+
+    const size_t nd = (size_t)ctx->ndof;
+    int st;
+    D->tr_len = (long long)ctx->ne * 4 * 2 * Q;
+    if ((st = gdg_cuda_check(ctx, cudaMalloc((void **)&D->d_S, nd * NA * sizeof(double)), "alloc S")) ||
+        (st = gdg_cuda_check(ctx, cudaMalloc((void **)&D->d_M, nd * NA * sizeof(double)), "alloc M")) ||
+        (st = gdg_cuda_check(ctx, cudaMalloc((void **)&D->d_w, nd * sizeof(double)), "alloc w")) ||
+        (st = gdg_cuda_check(ctx, cudaMalloc((void **)&D->d_pre, (size_t)ctx->ne * 4 * sizeof(double)), "alloc pre")) ||
+        (st = gdg_cuda_check(ctx, cudaMalloc((void **)&D->d_face, (size_t)ctx->ne * 16 * Q * sizeof(double)), "alloc face")) ||
+        (st = gdg_cuda_check(ctx, cudaMalloc((void **)&D->d_tab, tab.size() * sizeof(double)), "alloc tab")) ||
+        (st = gdg_cuda_check(ctx, cudaMalloc((void **)&D->d_nodes, 3 * nd * sizeof(double)), "alloc nodes")) ||
+        (st = gdg_cuda_check(ctx, cudaMalloc((void **)&D->d_state, (size_t)B_COUNT * nd * sizeof(double)), "alloc state")) ||
+        (st = gdg_cuda_check(ctx, cudaMalloc((void **)&D->d_tr, 2 * (size_t)D->tr_len * sizeof(double)), "alloc tr")) ||
+        (st = gdg_cuda_check(ctx, cudaMalloc((void **)&D->d_stats, 8 * sizeof(unsigned long long)), "alloc stats")) ||
+        (st = gdg_cuda_check(ctx, cudaMalloc((void **)&D->d_iters, (size_t)ctx->ne * sizeof(int)), "alloc iters")) ||
+        (st = gdg_cuda_check(ctx, cudaMalloc((void **)&D->d_rel, (size_t)ctx->ne * sizeof(double)), "alloc rel")) ||
+        (st = gdg_cuda_check(ctx, cudaMalloc((void **)&D->d_red, ((size_t)ctx->ne + 1) * sizeof(double)), "alloc red")) ||
+        (st = gdg_cuda_check(ctx, cudaMallocHost((void **)&D->h_red, 8 * sizeof(double)), "alloc host")))
+        return st;
+    cudaMemset(D->d_stats, 0, 8 * sizeof(unsigned long long));
+    if ((st = gdg_cuda_check(ctx, cudaMemcpy(D->d_tab, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice), "upload")) ||
+        (st = gdg_cuda_check(ctx, cudaMemcpy(D->d_nodes, ctx->pb.x_nodes, nd * sizeof(double), cudaMemcpyHostToDevice), "upload x")) ||
+        (st = gdg_cuda_check(ctx, cudaMemcpy(D->d_nodes + nd, ctx->pb.y_nodes, nd * sizeof(double), cudaMemcpyHostToDevice), "upload y")) ||
+        (st = gdg_cuda_check(ctx, cudaMemcpy(D->d_nodes + 2 * nd, ctx->pb.c2_nodes, nd * sizeof(double), cudaMemcpyHostToDevice), "upload c2")))
+        return st;
+    VarParams &P = D->vp;
+    P.nx = ctx->nx; P.ny = ctx->ny; P.ne = ctx->ne; P.Q = Q;
+    P.per_x = ctx->pb.bc[0] == GDG_BC_PERIODIC;
+    P.per_y = ctx->pb.bc[1] == GDG_BC_PERIODIC;
+    P.upwind = ctx->pb.flux == GDG_FLUX_UPWIND;
+    P.xi = ctx->pb.xi;
+    P.rtol = ctx->pb.pcg_rtol;
+    P.maxit = ctx->pb.pcg_maxit;
+    P.precond = ctx->pb.precond;
+    P.tab = D->d_tab; P.S = D->d_S; P.M = D->d_M; P.w = D->d_w; P.pre = D->d_pre; P.face = D->d_face;
+    P.stats = D->d_stats;
+    D->smem_geom = geom_smem(n1, Q);
+    D->smem_traces = traces_smem(n1, Q);
+    switch (n1) {
+#define X(n) case n: D->smem_stage = stage_smem<n>(Q); set_attrs<n>(D->smem_geom, D->smem_traces, D->smem_stage); break;
+        GDG_VAR_CASES(X)
+#undef X
+    }
+    if (D->smem_stage > 220 * 1024 || D->smem_geom > 220 * 1024)
+        return gdg_set_err(ctx, GDG_EUNSUPPORTED, "element too large for shared memory (reduce nquad)");
+    const double *Xd = D->d_nodes, *Yd = D->d_nodes + nd, *Cd = D->d_nodes + 2 * nd;
+    switch (n1) {
+#define X(n) case n: k_var_geom<n><<<ctx->ne, GEOM_THREADS, D->smem_geom>>>(P, Xd, Yd, Cd, D->d_S, D->d_M, D->d_w, D->d_pre, D->d_face); break;
+        GDG_VAR_CASES(X)
+#undef X
+    }
+    st = gdg_cuda_check(ctx, cudaDeviceSynchronize(), "assembly");
+    cudaFree(D->d_nodes);
+    D->d_nodes = nullptr;
+    if (st) return st;
+    // the mapping must be orientation preserving: every frozen |J| mean > 0
+    std::vector<double> pre((size_t)ctx->ne * 4);
+    cudaMemcpy(pre.data(), D->d_pre, pre.size() * sizeof(double), cudaMemcpyDeviceToHost);
+    for (int e = 0; e < ctx->ne; ++e)
+        if (!(pre[(size_t)e * 4 + 2] > 0.0) || !std::isfinite(pre[(size_t)e * 4 + 0]))
+            return gdg_set_err(ctx, GDG_EINVAL, "element mapping is degenerate or not orientation preserving");
+    return gdg_cuda_check(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking), "stream");
+}
+
+void gdg_var_free(gdg_ctx *ctx) {
+    VarData *D = ctx->var;
+    if (!D) return;
+    cudaFree(D->d_S); cudaFree(D->d_M); cudaFree(D->d_w); cudaFree(D->d_pre); cudaFree(D->d_face);
+    cudaFree(D->d_tab); cudaFree(D->d_nodes); cudaFree(D->d_state); cudaFree(D->d_tr);
+    cudaFree(D->d_stats); cudaFree(D->d_iters); cudaFree(D->d_rel); cudaFree(D->d_red);
+    if (D->h_red) cudaFreeHost(D->h_red);
+    delete D;
+    ctx->var = nullptr;
+}
+
+int gdg_var_rhs(gdg_ctx *ctx, const double *u, const double *v, double *du, double *dv, cudaStream_t s) {
+    VarData &D = *ctx->var;
+    cudaMemsetAsync(D.d_stats, 0, 8 * sizeof(unsigned long long), s);
+    launch_traces(ctx, u, v, D.d_tr, s);
+    VarBufs b{};
+    b.yU = u; b.yV = v; b.oU = du; b.oV = dv; b.trin = D.d_tr;
+    launch_stage(ctx, M_RHS, b, 0.0, 0.0, s);
+    int st = gdg_cuda_check(ctx, cudaGetLastError(), "gdg_rhs launch");
+    if (st) return st;
+    int unconv = 0;
+    if ((st = check_stats_noconv(ctx, s, &unconv))) return st;
+    return unconv ? gdg_set_err(ctx, GDG_ENOCONV, "PCG hit pcg_maxit") : GDG_OK;
+}
+
+int gdg_var_pcg(gdg_ctx *ctx, int which, const double *b, double *x, gdg_pcg_stats *stats, cudaStream_t s) {
+    VarData &D = *ctx->var;
+    GDG_PROF(ctx, GDG_K_PCG, s, launch_pcg_raw(ctx, which, b, x, s));
+    int st = gdg_cuda_check(ctx, cudaGetLastError(), "gdg_pcg launch");
+    if (st || !stats) return st;
+    std::vector<int> it(ctx->ne);
+    std::vector<double> rel(ctx->ne);
+    if ((st = gdg_cuda_check(ctx, cudaMemcpyAsync(it.data(), D.d_iters, it.size() * sizeof(int), cudaMemcpyDeviceToHost, s), "iters")) ||
+        (st = gdg_cuda_check(ctx, cudaMemcpyAsync(rel.data(), D.d_rel, rel.size() * sizeof(double), cudaMemcpyDeviceToHost, s), "rel")) ||
+        (st = gdg_cuda_check(ctx, cudaStreamSynchronize(s), "pcg sync")))
+        return st;
+    stats->max_iters = 0;
+    stats->mean_iters = 0.0;
+    stats->max_rel_resid = 0.0;
+    stats->unconverged = 0;
+    bool nonfinite = false;
+    for (int e = 0; e < ctx->ne; ++e) {
+        stats->max_iters = it[e] > stats->max_iters ? it[e] : stats->max_iters;
+        stats->mean_iters += it[e];
+        if (!std::isfinite(rel[e])) nonfinite = true;
+        else if (rel[e] > stats->max_rel_resid) stats->max_rel_resid = rel[e];
+        if (it[e] >= ctx->pb.pcg_maxit && rel[e] > ctx->pb.pcg_rtol) stats->unconverged++;
+    }
+    stats->mean_iters /= ctx->ne;
+    if (nonfinite) return gdg_set_err(ctx, GDG_ENONFINITE, "non-finite PCG residual");
+    if (stats->unconverged) return gdg_set_err(ctx, GDG_ENOCONV, "PCG hit pcg_maxit");
+    return GDG_OK;
+}
+
+int gdg_var_step(gdg_ctx *ctx, double *u, double *v, double dt, int nsteps, cudaStream_t s) {
+    VarData &D = *ctx->var;
+    const size_t bytes = (size_t)ctx->ndof * sizeof(double);
+    int st;
+    if ((st = gdg_cuda_check(ctx, cudaMemcpyAsync(vbuf(ctx, B_NU), u, bytes, cudaMemcpyDeviceToDevice, s), "copy u")) ||
+        (st = gdg_cuda_check(ctx, cudaMemcpyAsync(vbuf(ctx, B_NV), v, bytes, cudaMemcpyDeviceToDevice, s), "copy v")))
+        return st;
+    launch_traces(ctx, vbuf(ctx, B_NU), vbuf(ctx, B_NV), D.d_tr, s);
+    const int G = (nsteps >= 8 && !ctx->prof.on) ? 8 : 0;
+    if (G) {
+        GraphCache &gc = ctx->graph;
+        if (!gc.exec || gc.dt != dt || gc.steps != G) {
+            if (gc.exec) cudaGraphExecDestroy(gc.exec);
+            gc.exec = nullptr;
+            cudaGraph_t g;
+            if ((st = gdg_cuda_check(ctx, cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal), "capture")))
+                return st;
+            for (int i = 0; i < G; ++i) enqueue_step(ctx, dt, ctx->cap_stream);
+            if ((st = gdg_cuda_check(ctx, cudaStreamEndCapture(ctx->cap_stream, &g), "capture end"))) return st;
+            st = gdg_cuda_check(ctx, cudaGraphInstantiate(&gc.exec, g, 0), "instantiate");
+            cudaGraphDestroy(g);
+            if (st) return st;
+            gc.dt = dt;
+            gc.steps = G;
+        }
+        for (int i = 0; i + G <= nsteps; i += G)
+            if ((st = gdg_cuda_check(ctx, cudaGraphLaunch(gc.exec, s), "graph launch"))) return st;
+    }
+    const int rem = G ? nsteps % G : nsteps;
+    for (int i = 0; i < rem; ++i) enqueue_step(ctx, dt, s);
+    if ((st = gdg_cuda_check(ctx, cudaMemcpyAsync(u, vbuf(ctx, B_NU), bytes, cudaMemcpyDeviceToDevice, s), "copy u")) ||
+        (st = gdg_cuda_check(ctx, cudaMemcpyAsync(v, vbuf(ctx, B_NV), bytes, cudaMemcpyDeviceToDevice, s), "copy v")))
+        return st;
+    return gdg_cuda_check(ctx, cudaGetLastError(), "gdg_step");
+}
+
+int gdg_var_energy(gdg_ctx *ctx, const double *u, const double *v, double *E, cudaStream_t s) {
+    VarData &D = *ctx->var;
+    const dim3 grid(ctx->ne), block(nthreads_for(ctx->n1 * ctx->n1));
+    switch (ctx->n1) {
+#define X(n) case n: k_var_energy<n><<<grid, block, 0, s>>>(D.vp, u, v, D.d_red); break;
+        GDG_VAR_CASES(X)
+#undef X
+    }
+    k_var_sum<<<1, 1024, 0, s>>>(ctx->ne, D.d_red, D.d_red + ctx->ne);
+    int st;
+    if ((st = gdg_cuda_check(ctx, cudaMemcpyAsync(D.h_red, D.d_red + ctx->ne, sizeof(double), cudaMemcpyDeviceToHost, s), "energy d2h")) ||
+        (st = gdg_cuda_check(ctx, cudaStreamSynchronize(s), "energy sync")))
+        return st;
+    *E = D.h_red[0];
+    return GDG_OK;
+}
+
+int gdg_var_step_stats(gdg_ctx *ctx, gdg_pcg_stats *su, gdg_pcg_stats *sv) {
+    unsigned long long h[8];
+    int st = gdg_cuda_check(ctx, cudaMemcpy(h, ctx->var->d_stats, sizeof(h), cudaMemcpyDeviceToHost), "stats");
+    if (st) return st;
+    const double n = h[6] ? (double)h[6] : 1.0;
+    if (su) { su->max_iters = (int)h[2]; su->mean_iters = h[0] / n; su->max_rel_resid = 0.0; su->unconverged = (int)h[4]; }
+    if (sv) { sv->max_iters = (int)h[3]; sv->mean_iters = h[1] / n; sv->max_rel_resid = 0.0; sv->unconverged = (int)h[5]; }
+    cudaMemset(ctx->var->d_stats, 0, 8 * sizeof(unsigned long long));
+    return GDG_OK;
+}

@@ -1,0 +1,237 @@
+"""Thin ctypes binding of libgdg (include/gdg.h): argument marshalling only.
+
+Every computation runs in the CUDA library; this module converts torch
+tensors to device pointers and the current torch stream to a cudaStream_t.
+It raises if libgdg.so is missing: there is no fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgdg.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ENOCONV, ETIMEOUT, ENONFINITE, EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6, -7
+BC_DIRICHLET, BC_PERIODIC = 0, 1
+FLUX_CENTRAL, FLUX_UPWIND = 0, 1
+COEF_CONST, COEF_NODAL = 0, 1
+SOLVE_DIAG, SOLVE_PCG = 0, 1
+PC_FDM, PC_NONE = 0, 1
+FP64, MIXED = 0, 1
+ROUTE_MODAL, ROUTE_NODAL = 0, 1
+OP_M, OP_S = 0, 1
+
+_dp = ctypes.POINTER(ctypes.c_double)
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [
+        ("dim", ctypes.c_int), ("n_elem", ctypes.c_int * 2), ("N", ctypes.c_int), ("p", ctypes.c_int),
+        ("lo", ctypes.c_double * 2), ("hi", ctypes.c_double * 2), ("bc", ctypes.c_int * 2),
+        ("flux", ctypes.c_int), ("xi", ctypes.c_double), ("coef", ctypes.c_int), ("c2", ctypes.c_double),
+        ("x_nodes", _dp), ("y_nodes", _dp), ("c2_nodes", _dp), ("nquad", ctypes.c_int),
+        ("solver", ctypes.c_int), ("precond", ctypes.c_int), ("pcg_rtol", ctypes.c_double),
+        ("pcg_maxit", ctypes.c_int), ("precision", ctypes.c_int), ("route", ctypes.c_int),
+        ("refine_max", ctypes.c_int), ("refine_rtol", ctypes.c_double),
+    ]
+
+
+class PcgStats(ctypes.Structure):
+    _fields_ = [("max_iters", ctypes.c_int), ("mean_iters", ctypes.c_double),
+                ("max_rel_resid", ctypes.c_double), ("unconverged", ctypes.c_int)]
+
+
+_LIB = None
+
+EXPORTS = {
+    "gdg_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "gdg_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "gdg_basis_1d": (ctypes.c_int, [ctypes.c_int, ctypes.c_int] + [ctypes.c_void_p] * 8),
+    "gdg_create": (ctypes.c_int, [ctypes.POINTER(Problem), ctypes.POINTER(ctypes.c_void_p)]),
+    "gdg_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "gdg_state_len": (ctypes.c_longlong, [ctypes.c_void_p]),
+    "gdg_rhs": (ctypes.c_int, [ctypes.c_void_p] * 6),
+    "gdg_mass_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_void_p]),
+    "gdg_pcg": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                               ctypes.POINTER(PcgStats), ctypes.c_void_p]),
+    "gdg_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
+                                ctypes.c_double, ctypes.c_int, ctypes.c_void_p]),
+    "gdg_step_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
+                                     ctypes.c_double, ctypes.c_int, ctypes.c_void_p]),
+    "gdg_energy": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                  ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
+    "gdg_step_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(PcgStats), ctypes.POINTER(PcgStats)]),
+    "gdg_profile_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "gdg_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
+                                        ctypes.POINTER(ctypes.c_double)]),
+}
+
+K_STAGE, K_TRACES, K_TRANSFORM, K_RHS, K_PCG, K_OTHER = range(6)
+K_NAMES = ("stage", "traces", "transform", "rhs", "pcg", "other")
+
+
+def lib():
+    """Load libgdg.so (raises if it has not been built)."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libgdg.so is not built (run __graft_entry__.build()); "
+                               "there is no CPU fallback")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in EXPORTS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+class GdgError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s (%d): %s" % (lib().gdg_status_string(status).decode(), status, msg))
+        self.status = status
+
+
+def basis_1d(p, N):
+    """Host basis builder: dict of M, S, phiL, phiR, dphiL, dphiR, Psi, lam."""
+    n1 = N + 1
+    out = {k: np.zeros((n1, n1)) for k in ("M", "S", "Psi")}
+    out.update({k: np.zeros(n1) for k in ("phiL", "phiR", "dphiL", "dphiR", "lam")})
+    ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    st = lib().gdg_basis_1d(p, N, ptr(out["M"]), ptr(out["S"]), ptr(out["phiL"]), ptr(out["phiR"]),
+                            ptr(out["dphiL"]), ptr(out["dphiR"]), ptr(out["Psi"]), ptr(out["lam"]))
+    if st != OK:
+        raise GdgError(st, "gdg_basis_1d(p=%d, N=%d)" % (p, N))
+    return out
+
+
+def make_problem(dim, n, N, p, lo=(0.0, 0.0), hi=(1.0, 1.0), bc=(BC_DIRICHLET, BC_DIRICHLET),
+                 flux=FLUX_UPWIND, xi=0.0, c2=1.0, coef=COEF_CONST, x_nodes=None, y_nodes=None,
+                 c2_nodes=None, nquad=0, solver=None, precond=PC_FDM, pcg_rtol=1e-10, pcg_maxit=200,
+                 precision=FP64, route=ROUTE_MODAL, refine_max=8, refine_rtol=1e-5):
+    pb = Problem()
+    pb.dim = dim
+    n = tuple(n) + (1,) * (2 - len(n))
+    pb.n_elem[0], pb.n_elem[1] = n[0], n[1]
+    pb.N, pb.p = N, p
+    pb.lo[0], pb.lo[1] = lo[0], lo[1] if len(lo) > 1 else 0.0
+    pb.hi[0], pb.hi[1] = hi[0], hi[1] if len(hi) > 1 else 1.0
+    bc = tuple(bc) + (BC_DIRICHLET,) * (2 - len(bc))
+    pb.bc[0], pb.bc[1] = bc[0], bc[1]
+    pb.flux, pb.xi, pb.coef, pb.c2 = flux, xi, coef, c2
+    keep = []
+    for name, arr in (("x_nodes", x_nodes), ("y_nodes", y_nodes), ("c2_nodes", c2_nodes)):
+        if arr is not None:
+            a = np.ascontiguousarray(arr, dtype=np.float64)
+            keep.append(a)
+            setattr(pb, name, a.ctypes.data_as(_dp))
+    pb.nquad = nquad
+    pb.solver = (SOLVE_DIAG if coef == COEF_CONST else SOLVE_PCG) if solver is None else solver
+    pb.precond, pb.pcg_rtol, pb.pcg_maxit = precond, pcg_rtol, pcg_maxit
+    pb.precision, pb.route = precision, route
+    pb.refine_max, pb.refine_rtol = refine_max, refine_rtol
+    pb._keep = keep   # host arrays must outlive gdg_create
+    return pb
+
+
+def _ptr(t, n=None):
+    import torch
+    if not isinstance(t, torch.Tensor) or t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous float64 CUDA tensor")
+    if n is not None and t.numel() != n:
+        raise ValueError("expected %d elements, got %d" % (n, t.numel()))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Context:
+    """A gdg_ctx on the current CUDA device."""
+
+    def __init__(self, problem):
+        self._h = ctypes.c_void_p()
+        st = lib().gdg_create(ctypes.byref(problem), ctypes.byref(self._h))
+        if st != OK:
+            raise GdgError(st, "gdg_create")
+        self.problem = problem
+        self.n = lib().gdg_state_len(self._h)
+
+    def close(self):
+        if self._h:
+            lib().gdg_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st, what):
+        if st != OK:
+            raise GdgError(st, "%s: %s" % (what, lib().gdg_last_error(self._h).decode()))
+
+    def rhs(self, u, v, du, dv, stream=None):
+        self._check(lib().gdg_rhs(self._h, _ptr(u, self.n), _ptr(v, self.n), _ptr(du, self.n),
+                                  _ptr(dv, self.n), _stream(stream)), "gdg_rhs")
+
+    def mass_solve(self, which, b, x, stream=None):
+        self._check(lib().gdg_mass_solve(self._h, which, _ptr(b, self.n), _ptr(x, self.n),
+                                         _stream(stream)), "gdg_mass_solve")
+
+    def pcg(self, which, b, x, stream=None, allow_noconv=False):
+        stats = PcgStats()
+        st = lib().gdg_pcg(self._h, which, _ptr(b, self.n), _ptr(x, self.n), ctypes.byref(stats),
+                           _stream(stream))
+        if not (allow_noconv and st == ENOCONV):
+            self._check(st, "gdg_pcg")
+        return dict(max_iters=stats.max_iters, mean_iters=stats.mean_iters,
+                    max_rel_resid=stats.max_rel_resid, unconverged=stats.unconverged, status=st)
+
+    def step_stats(self):
+        """PCG statistics of the solves inside step()/rhs() since the last call."""
+        su, sv = PcgStats(), PcgStats()
+        self._check(lib().gdg_step_stats(self._h, ctypes.byref(su), ctypes.byref(sv)), "gdg_step_stats")
+        f = lambda s: dict(max_iters=s.max_iters, mean_iters=s.mean_iters, unconverged=s.unconverged)
+        return f(su), f(sv)
+
+    def step(self, u, v, t0, dt, nsteps, stream=None):
+        self._check(lib().gdg_step(self._h, _ptr(u, self.n), _ptr(v, self.n), t0, dt, nsteps,
+                                   _stream(stream)), "gdg_step")
+
+    def step_host(self, u, v, t0, dt, nsteps, stream=None):
+        """u, v: C-contiguous float64 host arrays (numpy or pinned torch CPU tensors)."""
+        def hp(a):
+            if isinstance(a, np.ndarray):
+                assert a.dtype == np.float64 and a.flags.c_contiguous and a.size == self.n
+                return ctypes.c_void_p(a.ctypes.data)
+            assert a.dtype.is_floating_point and a.is_contiguous() and a.numel() == self.n
+            return ctypes.c_void_p(a.data_ptr())
+        self._check(lib().gdg_step_host(self._h, hp(u), hp(v), t0, dt, nsteps, _stream(stream)),
+                    "gdg_step_host")
+
+    def profile(self, on):
+        self._check(lib().gdg_profile_enable(self._h, 1 if on else 0), "gdg_profile_enable")
+
+    def profile_read(self):
+        """{kind name: (launches, total ms)} of the launches recorded since profile(True)."""
+        out = {}
+        for k, name in enumerate(K_NAMES):
+            n, ms = ctypes.c_longlong(), ctypes.c_double()
+            self._check(lib().gdg_profile_read(self._h, k, ctypes.byref(n), ctypes.byref(ms)),
+                        "gdg_profile_read")
+            if n.value:
+                out[name] = (n.value, ms.value)
+        return out
+
+    def energy(self, u, v, stream=None):
+        E = ctypes.c_double()
+        self._check(lib().gdg_energy(self._h, _ptr(u, self.n), _ptr(v, self.n), ctypes.byref(E),
+                                     _stream(stream)), "gdg_energy")
+        return E.value

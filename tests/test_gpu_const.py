@@ -1,0 +1,251 @@
+"""GPU parity of the constant-coefficient Cartesian path (C-ABI calls) with
+the FP64 oracle: gdg_rhs, gdg_mass_solve, gdg_step after every step,
+gdg_energy; edge cases (single element, self-periodic, N = p, N+1 = 16,
+ragged element counts); and the two full-size constant-coefficient
+workloads (1-D 16 elements p=3; 2-D 64x64 elements p=5)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import dg_const as dc, timeint as ti
+from paper_2105_01722_gb300 import gdg, inputs
+
+TOL = 1e-12   # relative tolerance of the FP64 path against the oracle
+
+CASES = [
+    dict(dim=1, n=(16,), N=8, p=3, periodic=(False,), flux="central"),
+    dict(dim=1, n=(16,), N=8, p=3, periodic=(False,), flux="upwind"),
+    dict(dim=1, n=(5,), N=6, p=5, periodic=(True,), flux="upwind"),
+    dict(dim=1, n=(1,), N=3, p=3, periodic=(True,), flux="upwind"),
+    dict(dim=1, n=(131,), N=15, p=7, periodic=(False,), flux="upwind"),
+    dict(dim=2, n=(3, 2), N=5, p=3, periodic=(False, False), flux="upwind"),
+    dict(dim=2, n=(7, 5), N=8, p=5, periodic=(True, False), flux="central"),
+    dict(dim=2, n=(5, 7), N=8, p=5, periodic=(False, True), flux="upwind", c2=2.5, xi=0.7),
+    dict(dim=2, n=(1, 1), N=4, p=3, periodic=(True, True), flux="upwind"),
+    dict(dim=2, n=(1, 3), N=1, p=1, periodic=(False, False), flux="upwind"),
+    dict(dim=2, n=(17, 3), N=15, p=7, periodic=(False, False), flux="upwind", lo=(0.0, -1.0), hi=(2.0, 0.5)),
+    dict(dim=2, n=(9, 11), N=7, p=7, periodic=(True, True), flux="central", c2=0.3),
+]
+
+
+def _ids(c):
+    return "d%d-n%s-N%d-p%d-%s%s" % (c["dim"], "x".join(map(str, c["n"])), c["N"], c["p"], c["flux"],
+                                     "-per" + "".join("1" if q else "0" for q in c["periodic"]))
+
+
+def _oracle_problem(c):
+    kw = dict(c)
+    return dc.Problem(**kw)
+
+
+def _gpu_problem(c):
+    dim = c["dim"]
+    bc = tuple(gdg.BC_PERIODIC if q else gdg.BC_DIRICHLET for q in c["periodic"])
+    return gdg.make_problem(dim, c["n"], c["N"], c["p"], lo=c.get("lo", (0.0, 0.0)),
+                            hi=c.get("hi", (1.0, 1.0)), bc=bc,
+                            flux=gdg.FLUX_UPWIND if c["flux"] == "upwind" else gdg.FLUX_CENTRAL,
+                            xi=c.get("xi", 0.0), c2=c.get("c2", 1.0))
+
+
+def _state(c, seed):
+    ne = int(np.prod(c["n"]))
+    na = (c["N"] + 1) ** c["dim"]
+    return inputs.random_state((ne, na), seed), inputs.random_state((ne, na), seed + 1)
+
+
+def _dev(a):
+    return torch.tensor(np.ascontiguousarray(a).ravel(), dtype=torch.float64, device="cuda")
+
+
+def _route_floor(prob, U, V):
+    """Rounding floor of the oracle itself on this input: the relative gap
+    between its dense (row-replaced LU) and diagonalised solves of the u_t
+    system.  Ill-conditioned cases (N+1 = 16, p = 7, anisotropic elements)
+    reach ~2e-12 there; parity is required to max(1e-12, 3 x that floor)."""
+    from oracle import gd_basis as gb
+    ops = dc.operators(prob)
+    ru, rv = dc.residuals(prob, U, V, ops)
+    Ut, _ = dc.solve(ops, V, ru, rv)
+    Ps = [gb.simultaneous_diagonalisation(ops.M1[k], ops.S1[k]) for k in range(prob.dim)]
+    if prob.dim == 1:
+        Psi, lam = Ps[0]
+    else:
+        Psi = np.kron(Ps[1][0], Ps[0][0])
+        lam = (Ps[1][1][:, None] + Ps[0][1][None, :]).ravel()
+    inv = np.zeros_like(lam)
+    inv[1:] = 1.0 / lam[1:]
+    y = (ru @ Psi) * inv @ Psi.T
+    return max(TOL, 3.0 * _rel(V + y, Ut))
+
+
+def _rel(a, b):
+    return np.linalg.norm(np.ravel(a) - np.ravel(b)) / max(np.linalg.norm(np.ravel(b)), 1e-300)
+
+
+def _rel_state(u, v, U, V):
+    """Relative L2 error of the stacked state (u, v).  The two fields are
+    compared together: starting from rest, v is ~dt times smaller than u
+    while rounding in u's highest modes reaches v amplified by dt*lambda_max,
+    so v alone has no meaningful relative error after the first steps."""
+    a = np.concatenate([u.cpu().numpy().ravel(), v.cpu().numpy().ravel()])
+    b = np.concatenate([np.ravel(U), np.ravel(V)])
+    return _rel(a, b)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    gdg.lib()
+
+
+@pytest.mark.parametrize("c", CASES, ids=_ids)
+def test_rhs_parity(c):
+    prob = _oracle_problem(c)
+    U, V = _state(c, 10)
+    Ut, Vt = dc.time_derivative(prob, U, V)
+    ctx = gdg.Context(_gpu_problem(c))
+    u, v = _dev(U), _dev(V)
+    du, dv = torch.empty_like(u), torch.empty_like(v)
+    ctx.rhs(u, v, du, dv)
+    tol = _route_floor(prob, U, V)
+    assert _rel(du.cpu().numpy(), Ut) < tol
+    assert _rel(dv.cpu().numpy(), Vt) < tol
+    # elementwise too (relative to the field scale)
+    assert np.abs(du.cpu().numpy() - Ut.ravel()).max() < tol * np.abs(Ut).max() * 10
+    ctx.close()
+
+
+@pytest.mark.parametrize("c", CASES[:9], ids=_ids)
+def test_mass_solve_parity(c):
+    prob = _oracle_problem(c)
+    ops = dc.operators(prob)
+    U, V = _state(c, 20)
+    r_u, r_v = dc.residuals(prob, U, V, ops)
+    Ut, Vt = dc.solve(ops, np.zeros_like(V), r_u, r_v)
+    ctx = gdg.Context(_gpu_problem(c))
+    x = torch.empty(ctx.n, dtype=torch.float64, device="cuda")
+    ctx.mass_solve(gdg.OP_M, _dev(r_v), x)
+    assert _rel(x.cpu().numpy(), Vt) < TOL
+    ctx.mass_solve(gdg.OP_S, _dev(r_u), x)
+    assert _rel(x.cpu().numpy(), Ut) < TOL
+    # aliasing b and x is allowed
+    b = _dev(r_v)
+    ctx.mass_solve(gdg.OP_M, b, b)
+    assert _rel(b.cpu().numpy(), Vt) < TOL
+    ctx.close()
+
+
+@pytest.mark.parametrize("c", CASES, ids=_ids)
+def test_step_parity_every_step(c):
+    """gdg_step one step at a time matches the oracle's RK4 to 1e-12
+    relative L2 after every step (the graph path is exercised below)."""
+    prob = _oracle_problem(c)
+    ops = dc.operators(prob)
+    U, V = _state(c, 30)
+    ctx = gdg.Context(_gpu_problem(c))
+    u, v = _dev(U), _dev(V)
+    h = min(prob.H(k) for k in range(prob.dim)) / prob.N
+    dt = 0.1 * h / np.sqrt(c.get("c2", 1.0))
+    f = lambda t, U, V: dc.time_derivative(prob, U, V, ops)
+    tol = _route_floor(prob, U, V)
+    for s in range(5):
+        ctx.step(u, v, s * dt, dt, 1)
+        U, V = ti.rk4_step(f, U, V, s * dt, dt)
+        assert _rel_state(u, v, U, V) < tol, s
+    ctx.close()
+
+
+def test_step_graph_path_and_remainder():
+    """nsteps >= 16 goes through the captured graph (plus a remainder);
+    same result as the oracle and as single-step calls."""
+    c = CASES[6]
+    prob = _oracle_problem(c)
+    ops = dc.operators(prob)
+    U, V = _state(c, 40)
+    ctx = gdg.Context(_gpu_problem(c))
+    u, v = _dev(U), _dev(V)
+    u1, v1 = u.clone(), v.clone()
+    dt = 2e-3
+    ctx.step(u, v, 0.0, dt, 37)
+    for _ in range(37):
+        ctx.step(u1, v1, 0.0, dt, 1)
+    f = lambda t, U, V: dc.time_derivative(prob, U, V, ops)
+    U, V = ti.integrate(f, U, V, 0.0, dt, 37)
+    assert _rel_state(u, v, U, V) < TOL
+    # single-step calls add a nodal/modal round trip per step: same to rounding
+    assert _rel_state(u, v, u1.cpu().numpy(), v1.cpu().numpy()) < 1e-13
+    # a second call reuses the cached graph
+    ctx.step(u, v, 0.0, dt, 16)
+    U, V = ti.integrate(f, U, V, 0.0, dt, 16)
+    assert _rel_state(u, v, U, V) < TOL
+    ctx.close()
+
+
+@pytest.mark.parametrize("c", CASES[:8], ids=_ids)
+def test_energy_parity(c):
+    prob = _oracle_problem(c)
+    U, V = _state(c, 50)
+    E = dc.energy(prob, U, V)
+    ctx = gdg.Context(_gpu_problem(c))
+    Eg = ctx.energy(_dev(U), _dev(V))
+    assert abs(Eg - E) < TOL * abs(E)
+    ctx.close()
+
+
+def test_config_1d_full_run_every_step():
+    """1-D, 16 elements x 8 cells, p = 3, Dirichlet, standing wave, RK4 to
+    T = 1 at dt = h/2: parity with the oracle after every one of the 256
+    steps, central and upwind; energy behaviour."""
+    for flux in ("central", "upwind"):
+        c = dict(dim=1, n=(16,), N=8, p=3, periodic=(False,), flux=flux)
+        prob = _oracle_problem(c)
+        ops = dc.operators(prob)
+        (X,) = inputs.cartesian_nodes((16,), 8)
+        U, V = inputs.standing_wave_1d(X)
+        ctx = gdg.Context(_gpu_problem(c))
+        u, v = _dev(U), _dev(V)
+        dt = 1.0 / 256
+        f = lambda t, U, V: dc.time_derivative(prob, U, V, ops)
+        E0 = ctx.energy(u, v)
+        worst = 0.0
+        for s in range(256):
+            ctx.step(u, v, s * dt, dt, 1)
+            U, V = ti.rk4_step(f, U, V, s * dt, dt)
+            worst = max(worst, _rel_state(u, v, U, V))
+        assert worst < TOL, (flux, worst)
+        E1 = ctx.energy(u, v)
+        if flux == "central":
+            assert abs(E1 - E0) < 1e-7 * E0, (E0, E1)
+        else:
+            assert E1 < E0, (E0, E1)
+        ctx.close()
+
+
+def test_config_2d_64x64_p5_full_size():
+    """2-D constant coefficient, 64 x 64 elements of 8 x 8 cells, p = 5,
+    upwind, standing mode: full-size parity over 3 steps (every step) and
+    the exact-solution error after the oracle-free run to T = 1/8."""
+    c = dict(dim=2, n=(64, 64), N=8, p=5, periodic=(False, False), flux="upwind")
+    prob = _oracle_problem(c)
+    ops = dc.operators(prob)
+    X, Y = inputs.cartesian_nodes((64, 64), 8)
+    U, V = inputs.standing_mode_2d(X, Y)
+    U, V = U.reshape(4096, 81), V.reshape(4096, 81)
+    ctx = gdg.Context(_gpu_problem(c))
+    u, v = _dev(U), _dev(V)
+    h = 1.0 / 512
+    dt = 0.15 * h      # RK4-stable for upwind p = 5 (largest stable CFL 0.18)
+    f = lambda t, U, V: dc.time_derivative(prob, U, V, ops)
+    for s in range(3):
+        ctx.step(u, v, s * dt, dt, 1)
+        U, V = ti.rk4_step(f, U, V, s * dt, dt)
+        assert _rel_state(u, v, U, V) < TOL, s
+    ctx.step(u, v, 3 * dt, dt, 253)
+    T = 256 * dt
+    ue, ve = inputs.standing_mode_2d(X, Y, T)
+    err = np.sqrt(np.mean((u.cpu().numpy() - ue.ravel()) ** 2))
+    assert err < 1e-10
+    ctx.close()

@@ -1,0 +1,287 @@
+"""GPU parity of the variable-coefficient / mapped-element path (Section
+7.1) with the FP64 oracle, through the C ABI: quadrature assembly (via the
+energy quadratic forms), element PCG at fixed iteration counts (exact
+parity) and converged (against the dense solve), gdg_rhs and gdg_step,
+energy behaviour, edge cases, and the full 128 x 128 mapped mesh (p = 3, 5)
+on sampled elements, each checked against a 3 x 3 oracle patch around it."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import dg_var as dv, timeint as ti
+from paper_2105_01722_gb300 import gdg, inputs
+
+TOL = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    gdg.lib()
+
+
+def _dev(a):
+    return torch.tensor(np.ascontiguousarray(a).ravel(), dtype=torch.float64, device="cuda")
+
+
+def _rel(a, b):
+    a, b = np.ravel(a), np.ravel(b)
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def _mesh(n, N, kind="mapped", c2="sine", amp=0.05):
+    if kind == "mapped":
+        X, Y = inputs.mapped_nodes(n, N, amp)
+    else:
+        X, Y = inputs.cartesian_nodes(n, N)
+    if c2 == "sine":
+        C2 = inputs.c2_sine(X, Y)
+    elif c2 == "random":
+        C2 = inputs.smooth_random_c2(X, Y, seed=11)
+    else:
+        C2 = np.full_like(X, float(c2))
+    return X, Y, C2
+
+
+def _pair(n, N, p, kind="mapped", c2="sine", flux="upwind", periodic=(False, False), nquad=0,
+          rtol=1e-13, maxit=200, precond="fdm", xi=0.0):
+    X, Y, C2 = _mesh(n, N, kind, c2)
+    vp = dv.VarProblem(n=n, N=N, p=p, X=X, Y=Y, C2=C2, periodic=periodic, flux=flux, xi=xi,
+                       nq=nquad if nquad else None)
+    bc = tuple(gdg.BC_PERIODIC if q else gdg.BC_DIRICHLET for q in periodic)
+    pb = gdg.make_problem(2, n, N, p, bc=bc, flux=gdg.FLUX_UPWIND if flux == "upwind" else gdg.FLUX_CENTRAL,
+                          xi=xi, coef=gdg.COEF_NODAL, x_nodes=X, y_nodes=Y, c2_nodes=C2, nquad=nquad,
+                          pcg_rtol=rtol, pcg_maxit=maxit,
+                          precond=gdg.PC_FDM if precond == "fdm" else gdg.PC_NONE)
+    return vp, gdg.Context(pb)
+
+
+CASES = [
+    dict(n=(3, 2), N=8, p=5),
+    dict(n=(4, 4), N=8, p=3, flux="central"),
+    dict(n=(2, 3), N=4, p=3, periodic=(True, False), c2="random"),
+    dict(n=(3, 3), N=5, p=5, periodic=(True, True), kind="cartesian", c2="1.7"),
+    dict(n=(1, 1), N=6, p=3, periodic=(True, True)),
+    dict(n=(2, 2), N=9, p=7, nquad=9),
+    dict(n=(5, 3), N=8, p=5, xi=0.8, precond="none"),
+]
+
+
+def _ids(c):
+    return "n%s-N%d-p%d-%s" % ("x".join(map(str, c["n"])), c["N"], c["p"],
+                               "-".join("%s=%s" % (k, v) for k, v in c.items() if k not in ("n", "N", "p")))
+
+
+def _rand(vp, seed):
+    ne = vp.n[0] * vp.n[1]
+    return inputs.random_state((ne, vp.n1 ** 2), seed), inputs.random_state((ne, vp.n1 ** 2), seed + 1)
+
+
+@pytest.mark.parametrize("c", CASES, ids=_ids)
+def test_energy_pins_assembly(c):
+    """E(0, V) = V^T M_J V / 2 and E(U, 0) = U^T S_c2 U / 2 with random
+    states: the GPU-assembled element matrices against the oracle's."""
+    vp, ctx = _pair(**c)
+    ops = dv.assemble(vp)
+    U, V = _rand(vp, 3)
+    Z = np.zeros_like(U)
+    for a, b in ((Z, V), (U, Z), (U, V)):
+        E = dv.energy(ops, a, b)
+        Eg = ctx.energy(_dev(a), _dev(b))
+        assert abs(Eg - E) < TOL * abs(E), (Eg, E)
+    ctx.close()
+
+
+def _oracle_pcg(vp, ops, which, B, X0, rtol, maxit, precond="fdm"):
+    Psi, lam = dv.reference_diagonalisation(vp.p, vp.N)
+    out = np.empty_like(B)
+    its = []
+    for e in range(B.shape[0]):
+        A = dv.spd_u_matrix(ops, e) if which == "S" else ops.M[e]
+        if precond == "fdm":
+            P = dv.fdm_preconditioner(ops, e, which, Psi, lam)
+            pinv = lambda r, P=P: P @ r
+        else:
+            pinv = lambda r: r.copy()
+        out[e], it, _ = dv.pcg(A, B[e], pinv, X0[e], rtol, maxit)
+        its.append(it)
+    return out, np.array(its)
+
+
+@pytest.mark.parametrize("c", CASES, ids=_ids)
+@pytest.mark.parametrize("K", [1, 3, 6])
+def test_pcg_fixed_iterations(c, K):
+    """rtol = 0, maxit = K: exactly K PCG iterations on every element from a
+    random initial guess; the iterates match the oracle's."""
+    kw = dict(c)
+    kw.update(rtol=0.0, maxit=K)
+    vp, ctx = _pair(**kw)
+    ops = dv.assemble(vp)
+    B, X0 = _rand(vp, 5)
+    X0 = 0.1 * X0
+    for which, op in (("M", gdg.OP_M), ("S", gdg.OP_S)):
+        ref, its = _oracle_pcg(vp, ops, which, B, X0, 0.0, K, kw.get("precond", "fdm"))
+        x = _dev(X0)
+        st = ctx.pcg(op, _dev(B), x, allow_noconv=True)
+        assert st["max_iters"] == K and its.max() == K
+        assert _rel(x.cpu().numpy(), ref) < 10 * TOL, which
+    ctx.close()
+
+
+@pytest.mark.parametrize("c", CASES[:4], ids=_ids)
+def test_pcg_converged_matches_direct(c):
+    vp, ctx = _pair(**c, rtol=1e-12, maxit=300)
+    ops = dv.assemble(vp)
+    U, V = _rand(vp, 7)
+    ru, rv = dv.residuals(vp, ops, U, V)
+    Ut, Vt = dv.solve_direct(ops, V, ru, rv)
+    x = torch.zeros(ctx.n, dtype=torch.float64, device="cuda")
+    st = ctx.pcg(gdg.OP_M, _dev(rv), x)
+    assert _rel(x.cpu().numpy(), Vt) < 1e-10 and st["max_rel_resid"] <= 1e-12
+    x.zero_()
+    st = ctx.pcg(gdg.OP_S, _dev(ru), x)
+    assert _rel(x.cpu().numpy(), Ut - V) < 1e-10 and st["max_rel_resid"] <= 1e-12
+    ctx.close()
+
+
+@pytest.mark.parametrize("c", CASES, ids=_ids)
+def test_rhs_parity_fixed_iterations(c):
+    """gdg_rhs with exactly K = 5 PCG iterations per element system (x0 = 0)
+    against the oracle's residuals + the same PCG."""
+    K = 5
+    vp, ctx = _pair(**c, rtol=0.0, maxit=K)
+    ops = dv.assemble(vp)
+    U, V = _rand(vp, 9)
+    ru, rv = dv.residuals(vp, ops, U, V)
+    Ut, Vt, iu, iv = dv.solve_pcg(vp, ops, V, ru, rv, precond=c.get("precond", "fdm"), rtol=0.0, maxit=K)
+    u, v = _dev(U), _dev(V)
+    du, dv_ = torch.empty_like(u), torch.empty_like(v)
+    try:
+        ctx.rhs(u, v, du, dv_)
+    except gdg.GdgError as err:
+        assert err.status == gdg.ENOCONV        # rtol = 0 never "converges"
+    a = np.concatenate([du.cpu().numpy(), dv_.cpu().numpy()])
+    assert _rel(a, np.concatenate([Ut.ravel(), Vt.ravel()])) < 10 * TOL
+    ctx.close()
+
+
+@pytest.mark.parametrize("c", CASES[:3], ids=_ids)
+def test_rhs_converged_matches_direct(c):
+    vp, ctx = _pair(**c, rtol=1e-13, maxit=300)
+    ops = dv.assemble(vp)
+    U, V = _rand(vp, 13)
+    Ut, Vt = dv.time_derivative(vp, ops, U, V)
+    u, v = _dev(U), _dev(V)
+    du, dv_ = torch.empty_like(u), torch.empty_like(v)
+    ctx.rhs(u, v, du, dv_)
+    a = np.concatenate([du.cpu().numpy(), dv_.cpu().numpy()])
+    assert _rel(a, np.concatenate([Ut.ravel(), Vt.ravel()])) < 1e-10
+    ctx.close()
+
+
+@pytest.mark.parametrize("c", CASES[:4], ids=_ids)
+def test_step_parity_fixed_iterations(c):
+    """Three RK4 steps, every stage solve with exactly K = 6 iterations, one
+    gdg_step call per step: the stacked state matches the oracle after each."""
+    K = 6
+    vp, ctx = _pair(**c, rtol=0.0, maxit=K)
+    ops = dv.assemble(vp)
+    U, V = _rand(vp, 17)
+    u, v = _dev(U), _dev(V)
+    f = lambda t, U, V: dv.solve_pcg(vp, ops, V, *dv.residuals(vp, ops, U, V),
+                                     precond=c.get("precond", "fdm"), rtol=0.0, maxit=K)[:2]
+    dt = 0.05 / (max(vp.n) * vp.N)
+    for s in range(3):
+        ctx.step(u, v, s * dt, dt, 1)
+        U, V = ti.rk4_step(f, U, V, s * dt, dt)
+        a = np.concatenate([u.cpu().numpy(), v.cpu().numpy()])
+        assert _rel(a, np.concatenate([U.ravel(), V.ravel()])) < 10 * TOL, s
+    su, sv = ctx.step_stats()
+    assert su["max_iters"] == K and sv["max_iters"] == K
+    ctx.close()
+
+
+def test_central_energy_and_upwind_decay_mapped():
+    """Mapped mesh, variable c^2: the discrete energy is nearly conserved by
+    the central flux (RK4 drift only) and decreases with the upwind flux."""
+    for flux in ("central", "upwind"):
+        vp, ctx = _pair((4, 4), 8, 5, flux=flux, rtol=1e-13, maxit=300)
+        X, Y = vp.X, vp.Y
+        U0 = inputs.gaussian_pulse(X, Y, 0.45, 0.55, 0.2)
+        u, v = _dev(U0), torch.zeros(ctx.n, dtype=torch.float64, device="cuda")
+        E0 = ctx.energy(u, v)
+        dt = 0.1 / (4 * 8)
+        Es = []
+        for _ in range(10):
+            ctx.step(u, v, 0.0, dt, 2)
+            Es.append(ctx.energy(u, v))
+        if flux == "central":
+            assert abs(Es[-1] - E0) < 1e-6 * E0, (E0, Es[-1])
+        else:
+            assert all(b <= a * (1 + 1e-13) for a, b in zip([E0] + Es, Es)) and Es[-1] < E0
+        ctx.close()
+
+
+def _patch_rhs(X, Y, C2, U, V, N, p, ey, ex, K):
+    """Oracle time derivative of element (ey, ex) from the 3 x 3 patch around
+    it (its value depends on its own data and its neighbours' traces only;
+    patch sides on the domain boundary keep the Dirichlet condition)."""
+    ny, nx = X.shape[:2]
+    y0, y1 = max(ey - 1, 0), min(ey + 1, ny - 1)
+    x0, x1 = max(ex - 1, 0), min(ex + 1, nx - 1)
+    sl = (slice(y0, y1 + 1), slice(x0, x1 + 1))
+    n = (x1 - x0 + 1, y1 - y0 + 1)
+    vp = dv.VarProblem(n=n, N=N, p=p, X=X[sl], Y=Y[sl], C2=C2[sl], flux="upwind")
+    ops = dv.assemble(vp)
+    ne = n[0] * n[1]
+    Us = U[sl].reshape(ne, -1)
+    Vs = V[sl].reshape(ne, -1)
+    ru, rv = dv.residuals(vp, ops, Us, Vs)
+    Ut, Vt, _, _ = dv.solve_pcg(vp, ops, Vs, ru, rv, precond="fdm", rtol=0.0, maxit=K)
+    c = (ey - y0) * n[0] + (ex - x0)
+    return Ut[c], Vt[c]
+
+
+@pytest.mark.parametrize("p", [3, 5])
+def test_full_size_mapped_128(p):
+    """128 x 128 mapped elements of 8 x 8 cells, c^2 = 1 + 0.5 sin 2pi x cos 2pi y,
+    Gaussian pulse: sampled-element parity of gdg_rhs (fixed K = 5 iterations)
+    against 3 x 3 oracle patches; then RK4 steps at rtol 1e-10 with bounded
+    iteration counts and decaying upwind energy."""
+    n, N, K = (128, 128), 8, 5
+    X, Y, C2 = _mesh(n, N)
+    U = inputs.gaussian_pulse(X, Y, 0.5, 0.5, 0.05) + 0.01 * inputs.random_state(X.shape, 21)
+    V = 0.01 * inputs.random_state(X.shape, 22)
+    pb = gdg.make_problem(2, n, N, p, coef=gdg.COEF_NODAL, x_nodes=X, y_nodes=Y, c2_nodes=C2,
+                          pcg_rtol=0.0, pcg_maxit=K)
+    ctx = gdg.Context(pb)
+    u, v = _dev(U), _dev(V)
+    du, dv_ = torch.empty_like(u), torch.empty_like(v)
+    try:
+        ctx.rhs(u, v, du, dv_)
+    except gdg.GdgError as err:
+        assert err.status == gdg.ENOCONV
+    du = du.cpu().numpy().reshape(128, 128, -1)
+    dvv = dv_.cpu().numpy().reshape(128, 128, -1)
+    for ey, ex in [(0, 0), (0, 77), (127, 127), (64, 64), (31, 100), (127, 5)]:
+        Ut, Vt = _patch_rhs(X, Y, C2, U, V, N, p, ey, ex, K)
+        a = np.concatenate([du[ey, ex], dvv[ey, ex]])
+        assert _rel(a, np.concatenate([Ut, Vt])) < 10 * TOL, (ey, ex)
+    ctx.close()
+    pb = gdg.make_problem(2, n, N, p, coef=gdg.COEF_NODAL, x_nodes=X, y_nodes=Y, c2_nodes=C2,
+                          pcg_rtol=1e-10, pcg_maxit=100)
+    ctx = gdg.Context(pb)
+    U0 = inputs.gaussian_pulse(X, Y, 0.5, 0.5, 0.05)
+    u, v = _dev(U0), torch.zeros(ctx.n, dtype=torch.float64, device="cuda")
+    E0 = ctx.energy(u, v)
+    dt = 0.1 / (128 * 8)
+    ctx.step(u, v, 0.0, dt, 8)
+    su, sv = ctx.step_stats()
+    E1 = ctx.energy(u, v)
+    assert su["unconverged"] == 0 and sv["unconverged"] == 0
+    assert su["max_iters"] < 40 and sv["max_iters"] < 20
+    assert E1 < E0 and E1 > 0.9 * E0
+    ctx.close()

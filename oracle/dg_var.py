@@ -13,7 +13,7 @@ quadrature on the reference element:
   S_c2      = int c^2 (J^-T grad_r phi_a) . (J^-T grad_r phi_b) |J|
   r_u       = sum_faces int_face c^2 (n . grad phi_a) (v* - v_in) dS
   r_v       = -S_c2 U + sum_faces int_face c^2 phi_a q* dS
-  S_c2 (dU/dt - V) = r_u,  w^T (dU/dt - V) = 0,  w = M_J 1
+  S_c2 (dU/dt - V) = r_u,  w^T (dU/dt - V) = 0,  w = M_J 1 / |e|
   M_J dV/dt = r_v
 
 Readings made here (the paper leaves them open):
@@ -26,7 +26,10 @@ Readings made here (the paper leaves them open):
   given; c^2 on a face is the inside element's trace;
 * the constrained u_t system is solved in the equivalent SPD form
   (S_c2 + w w^T) y = r_u (its solution satisfies S_c2 y = r_u, w^T y = 0
-  because 1^T r_u = 0);
+  because 1^T r_u = 0); the extra equation of Eq. DG1_extra is weighted by
+  1/|e| (|e| = 1^T M_J 1, the element area), w = M_J 1 / |e|: any positive
+  weight gives the same y, and this one keeps the rank-one term O(1) so
+  rounding in the constant mode is not amplified by 1/|e|^2;
 * PCG (element by element) stops when ||r||_2 <= rtol ||b||_2, tested
   before each iteration, or after maxit iterations; rz = 0 ends it.
 
@@ -145,13 +148,13 @@ def assemble(vp):
             wd = W * det
             ops.M[e] = Phi.T @ (wd[:, None] * Phi)
             ops.S[e] = gx.T @ ((wd * c2q)[:, None] * gx) + gy.T @ ((wd * c2q)[:, None] * gy)
-            ops.w[e] = ops.M[e] @ np.ones(n1 * n1)
             # frozen-coefficient data for the diagonalisation preconditioner:
             # G = c^2 |J| J^-1 J^-T, averaged over the element (diagonal part)
             Grr = c2q * (x_s ** 2 + y_s ** 2) / det
             Gss = c2q * (x_r ** 2 + y_r ** 2) / det
             ops.Gbar[e] = [W @ Grr, W @ Gss]
             ops.Jbar[e] = W @ det
+            ops.w[e] = ops.M[e] @ np.ones(n1 * n1) / ops.Jbar[e]
             for f in FACES:
                 Tv, Tn, T = _face_geometry(vp, B, D, dphiL, dphiR,
                                            vp.X[ey, ex], vp.Y[ey, ex], f)
@@ -253,8 +256,9 @@ def fdm_preconditioner(ops, e, which, Psi, lam):
 
     which = "M": P = Jbar * (M_hat (x) M_hat)  ->  P^-1 = Psi2 Psi2^T / Jbar.
     which = "S": P = Grr (M_hat (x) S_hat) + Gss (S_hat (x) M_hat) + wbar wbar^T
-                 with wbar = Jbar (M_hat (x) M_hat) 1; in the Psi2 basis it is
-                 diagonal: Grr lam_i + Gss lam_j, and Jbar^2 on the constant mode.
+                 with wbar = (M_hat (x) M_hat) 1 (the frozen M_J 1 / |e|); in the
+                 Psi2 basis it is diagonal: Grr lam_i + Gss lam_j, and 1 on the
+                 constant mode.
     Psi2 = Psi (x) Psi (index j*n1 + i), Section 3.2's modified basis."""
     n1 = Psi.shape[0]
     Psi2 = np.kron(Psi, Psi)
@@ -263,7 +267,7 @@ def fdm_preconditioner(ops, e, which, Psi, lam):
     else:
         Grr, Gss = ops.Gbar[e]
         lam2 = (Gss * lam[:, None] + Grr * lam[None, :]).ravel()   # (j, i)
-        lam2[0] = ops.Jbar[e] ** 2
+        lam2[0] = 1.0
         d = 1.0 / lam2
     return Psi2 @ (d[:, None] * Psi2.T)
 

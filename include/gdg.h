@@ -94,10 +94,14 @@ typedef struct {
 } gdg_problem;
 
 typedef struct {
-    int max_iters;        /* largest per-element iteration count of the last call  */
+    int max_iters;        /* largest per-element PCG iteration count (FP32 inner    */
+                          /* iterations summed over sweeps under GDG_MIXED)         */
     double mean_iters;    /* mean over elements                                    */
     double max_rel_resid; /* largest final ||r||/||b|| (true FP64 residual)        */
-    int unconverged;      /* number of element systems that hit pcg_maxit          */
+    int unconverged;      /* element systems that hit pcg_maxit (GDG_MIXED:        */
+                          /* refine_max) above pcg_rtol                             */
+    int max_sweeps;       /* GDG_MIXED: largest number of FP64 refinement sweeps   */
+    double mean_sweeps;   /* GDG_MIXED: mean sweeps (FP64 residuals after the first) */
 } gdg_pcg_stats;
 
 /* Human-readable text of a status code (static storage). */
@@ -163,8 +167,10 @@ int gdg_mass_solve(gdg_ctx *ctx, int which, const double *b, double *x, void *st
 /*
  * Element-local preconditioned CG (Section 7.1) on every element's system
  *   which = GDG_OP_M:  M_J x = b
- *   which = GDG_OP_S:  (S_c2 + w w^T) x = b, w = M_J 1  (the SPD form of the
- *                      constrained u_t system)
+ *   which = GDG_OP_S:  (S_c2 + w w^T) x = b, w = M_J 1 / |e|, |e| = 1^T M_J 1
+ *                      the element area (the SPD form of the constrained u_t
+ *                      system: for 1^T b = 0 its solution has S_c2 x = b,
+ *                      w^T x = 0; the 1/|e| weight keeps the rank-one term O(1))
  * x is the initial guess on entry and the solution on exit (device).
  * Stops per element when ||r||_2 <= pcg_rtol ||b||_2 or after pcg_maxit
  * iterations.  stats (host, may be NULL) is filled; the call synchronises

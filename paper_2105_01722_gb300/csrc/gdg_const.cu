@@ -23,6 +23,8 @@
 // write the traces of that next input.  The grid-wide dependency between
 // traces and lifts is the kernel boundary.
 #include <cstdio>
+#include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <vector>
 
@@ -30,7 +32,7 @@
 
 namespace {
 
-constexpr int EPB2 = 16;   // elements per block, 2-D kernels (block = EPB2 * N1 threads)
+constexpr int MAXB2 = 256;  // largest 2-D block (epb elements x N1 threads); allows 255 registers
 constexpr int TPB1 = 128;  // threads per block, 1-D kernels (one element per thread)
 
 // stage modes
@@ -71,15 +73,15 @@ __device__ __forceinline__ void flux(double vi, double di, double vo, double dO,
 // ------------------------------------------------------------ 2-D stage --
 
 template <int N1, int MODE>
-__global__ void __launch_bounds__(EPB2 * N1)
+__global__ void __launch_bounds__(MAXB2)
 k_stage2(const __grid_constant__ ModalParams mp, const StageBufs b, double cA, double cY) {
     extern __shared__ double smem[];
     const int t = threadIdx.x;
     const int le = t / N1, l = t - le * N1;
-    const int e = blockIdx.x * EPB2 + le;
+    const int e = blockIdx.x * (int)(blockDim.x / N1) + le;
     const bool valid = e < mp.ne;
     double *fy = smem + le * (4 * N1);
-    double *tile = smem + EPB2 * 4 * N1 + le * (2 * N1 * (N1 + 1));
+    double *tile = smem + (blockDim.x / N1) * 4 * N1 + le * (2 * N1 * (N1 + 1));
     const int nx = mp.nx, ny = mp.ny;
     const int ex = valid ? e % nx : 0, ey = valid ? e / nx : 0;
 
@@ -196,14 +198,171 @@ k_stage2(const __grid_constant__ ModalParams mp, const StageBufs b, double cA, d
     }
 }
 
+// Parity version of k_stage2.  The GD element is symmetric under r -> 1-r,
+// so every modified-basis vector is even or odd: Psi[N-i][k] = s_k Psi[i][k].
+// With the NE = (N1+1)/2 even modes stored first, eR = s eL and gR = s gL:
+// both face traces of a line come from one even/odd split dot, and each
+// lift is one FMA per entry.  Fluxes carry a factor 2 (g2 = 2(v* - v_in),
+// q2 = 2 q*) that is folded into the lift vectors hgL = gL/2, ceL = c^2 eL/2.
+template <int N1, int MODE>
+__global__ void __launch_bounds__(MAXB2)
+k_stage2p(const __grid_constant__ ModalParams mp, const StageBufs b, double cA, double cY) {
+    constexpr int NE = (N1 + 1) / 2;
+    extern __shared__ double smem[];
+    const int epb = blockDim.x / N1;
+    const int t = threadIdx.x;
+    const int le = t / N1, l = t - le * N1;
+    const int e = blockIdx.x * epb + le;
+    const bool valid = le < epb && e < mp.ne;
+    double *fy = smem + le * (4 * N1);   // per column: GA, GB, QA, QB of the y faces
+    double *tile = smem + epb * 4 * N1 + le * (2 * N1 * (N1 + 1));
+    const int nx = mp.nx, ny = mp.ny;
+    const int ex = valid ? e % nx : 0, ey = valid ? e / nx : 0;
+    const double b2 = mp.beta2, t2 = mp.tau2;
+    const size_t row = ((size_t)(valid ? e : 0) * N1 + l) * N1;
+
+    // issue every row load of this stage before the barrier so their latency
+    // overlaps the flux work (a few warps per SM only at small element counts)
+    double Ru[N1], Rv[N1], Nu[N1], Nv[N1], Au[N1], Av[N1];
+    if (valid) {
+#pragma unroll
+        for (int k = 0; k < N1; ++k) {
+            Ru[k] = b.yU[row + k];
+            Rv[k] = b.yV[row + k];
+            if (MODE == M_S23 || MODE == M_S4) {
+                Nu[k] = b.nU[row + k];
+                Nv[k] = b.nV[row + k];
+                Au[k] = b.aU[row + k];
+                Av[k] = b.aV[row + k];
+            }
+        }
+    }
+
+    double GA = 0, GB = 0, QA = 0, QB = 0;
+    if (valid) {
+        const double *T = b.trin;
+        double vi, di, vo, dO, d1, g2m, q2m, g2p, q2p;
+        int en, f;
+        // x faces, transverse mode l
+        vi = T[tix2<N1>(e, 0, 0, l)]; di = T[tix2<N1>(e, 0, 1, l)];
+        en = ex - 1;
+        if (en < 0 && mp.per_x) en += nx;
+        if (en >= 0) { f = ey * nx + en; vo = T[tix2<N1>(f, 1, 0, l)]; dO = T[tix2<N1>(f, 1, 1, l)]; }
+        else { vo = -vi; dO = -di; }
+        d1 = vo - vi;
+        g2m = fma(-b2, di + dO, d1);
+        q2m = fma(t2, d1, di - dO);
+        vi = T[tix2<N1>(e, 1, 0, l)]; di = T[tix2<N1>(e, 1, 1, l)];
+        en = ex + 1;
+        if (en >= nx && mp.per_x) en -= nx;
+        if (en < nx) { f = ey * nx + en; vo = T[tix2<N1>(f, 0, 0, l)]; dO = T[tix2<N1>(f, 0, 1, l)]; }
+        else { vo = -vi; dO = -di; }
+        d1 = vo - vi;
+        g2p = fma(-b2, di + dO, d1);
+        q2p = fma(t2, d1, di - dO);
+        GA = g2m + g2p; GB = g2m - g2p; QA = q2m + q2p; QB = q2m - q2p;
+        // y faces, transverse mode k = l
+        vi = T[tix2<N1>(e, 2, 0, l)]; di = T[tix2<N1>(e, 2, 1, l)];
+        en = ey - 1;
+        if (en < 0 && mp.per_y) en += ny;
+        if (en >= 0) { f = en * nx + ex; vo = T[tix2<N1>(f, 3, 0, l)]; dO = T[tix2<N1>(f, 3, 1, l)]; }
+        else { vo = -vi; dO = -di; }
+        d1 = vo - vi;
+        g2m = fma(-b2, di + dO, d1);
+        q2m = fma(t2, d1, di - dO);
+        vi = T[tix2<N1>(e, 3, 0, l)]; di = T[tix2<N1>(e, 3, 1, l)];
+        en = ey + 1;
+        if (en >= ny && mp.per_y) en -= ny;
+        if (en < ny) { f = en * nx + ex; vo = T[tix2<N1>(f, 2, 0, l)]; dO = T[tix2<N1>(f, 2, 1, l)]; }
+        else { vo = -vi; dO = -di; }
+        d1 = vo - vi;
+        g2p = fma(-b2, di + dO, d1);
+        q2p = fma(t2, d1, di - dO);
+        fy[l] = g2m + g2p; fy[N1 + l] = g2m - g2p;
+        fy[2 * N1 + l] = q2m + q2p; fy[3 * N1 + l] = q2m - q2p;
+    }
+    __syncthreads();
+
+    if (valid) {
+        const double *L0 = b.lam2 + l * N1;
+        const double *L1 = b.lam2 + N1 * N1 + l * N1;
+        const double hgy = mp.d[1].hgL[l], cey = mp.d[1].ceL[l];
+        const double *FG = fy + (l < NE ? 0 : N1);
+        const double *FQ = fy + (l < NE ? 2 * N1 : 3 * N1);
+#pragma unroll
+        for (int k = 0; k < N1; ++k) {
+            const double Yu = Ru[k], Yv = Rv[k];
+            const double xg = k < NE ? GA : GB, xq = k < NE ? QA : QB;
+            const double ru = fma(mp.d[0].hgL[k], xg, hgy * FG[k]);
+            const double rv = fma(L0[k], Yu, fma(mp.d[0].ceL[k], xq, cey * FQ[k]));
+            const double ku = fma(L1[k], ru, Yv);
+            const double kv = rv;
+            if (MODE == M_RHS) {
+                b.oU[row + k] = ku;
+                b.oV[row + k] = kv;
+            } else if (MODE == M_S1) {
+                b.aU[row + k] = cA * ku;
+                b.aV[row + k] = cA * kv;
+                Ru[k] = fma(cY, ku, Yu);
+                Rv[k] = fma(cY, kv, Yv);
+            } else if (MODE == M_S23) {
+                b.aU[row + k] = fma(cA, ku, Au[k]);
+                b.aV[row + k] = fma(cA, kv, Av[k]);
+                Ru[k] = fma(cY, ku, Nu[k]);
+                Rv[k] = fma(cY, kv, Nv[k]);
+            } else {
+                Ru[k] = fma(cA, ku, Nu[k] + Au[k]);
+                Rv[k] = fma(cA, kv, Nv[k] + Av[k]);
+            }
+        }
+        if (MODE != M_RHS) {
+            double *dU = (MODE == M_S4) ? b.nU : b.oU;
+            double *dV = (MODE == M_S4) ? b.nV : b.oV;
+#pragma unroll
+            for (int k = 0; k < N1; ++k) { dU[row + k] = Ru[k]; dV[row + k] = Rv[k]; }
+        }
+    }
+    if (MODE == M_RHS) return;
+
+    if (valid) {
+        double ve = 0, vo_ = 0, de = 0, do_ = 0;
+#pragma unroll
+        for (int k = 0; k < N1; ++k) {
+            if (k < NE) { ve = fma(mp.d[0].eL[k], Rv[k], ve); de = fma(mp.d[0].gL[k], Ru[k], de); }
+            else { vo_ = fma(mp.d[0].eL[k], Rv[k], vo_); do_ = fma(mp.d[0].gL[k], Ru[k], do_); }
+            tile[l * (N1 + 1) + k] = Ru[k];
+            tile[N1 * (N1 + 1) + l * (N1 + 1) + k] = Rv[k];
+        }
+        b.trout[tix2<N1>(e, 0, 0, l)] = ve + vo_;
+        b.trout[tix2<N1>(e, 0, 1, l)] = de + do_;
+        b.trout[tix2<N1>(e, 1, 0, l)] = ve - vo_;
+        b.trout[tix2<N1>(e, 1, 1, l)] = de - do_;
+    }
+    __syncthreads();
+    if (valid) {
+        const int k = l;
+        double ve = 0, vo_ = 0, de = 0, do_ = 0;
+#pragma unroll
+        for (int j = 0; j < N1; ++j) {
+            const double u = tile[j * (N1 + 1) + k], v = tile[N1 * (N1 + 1) + j * (N1 + 1) + k];
+            if (j < NE) { ve = fma(mp.d[1].eL[j], v, ve); de = fma(mp.d[1].gL[j], u, de); }
+            else { vo_ = fma(mp.d[1].eL[j], v, vo_); do_ = fma(mp.d[1].gL[j], u, do_); }
+        }
+        b.trout[tix2<N1>(e, 2, 0, k)] = ve + vo_;
+        b.trout[tix2<N1>(e, 2, 1, k)] = de + do_;
+        b.trout[tix2<N1>(e, 3, 0, k)] = ve - vo_;
+        b.trout[tix2<N1>(e, 3, 1, k)] = de - do_;
+    }
+}
+
 // traces of a modal state (start of gdg_step and gdg_rhs)
 template <int N1>
-__global__ void __launch_bounds__(EPB2 * N1)
+__global__ void __launch_bounds__(MAXB2)
 k_traces2(const __grid_constant__ ModalParams mp, const double *yU, const double *yV, double *trout) {
     extern __shared__ double smem[];
     const int t = threadIdx.x;
     const int le = t / N1, l = t - le * N1;
-    const int e = blockIdx.x * EPB2 + le;
+    const int e = blockIdx.x * (int)(blockDim.x / N1) + le;
     const bool valid = e < mp.ne;
     double *tile = smem + le * (2 * N1 * (N1 + 1));
     if (valid) {
@@ -248,7 +407,7 @@ k_traces2(const __grid_constant__ ModalParams mp, const double *yU, const double
 // (A (x) B)[(l,k),(j,i)] = A[l][j] B[k][i].  Two fields per call (U and V
 // share the matrices).
 template <int N1>
-__global__ void __launch_bounds__(EPB2 * N1)
+__global__ void __launch_bounds__(MAXB2)
 k_sep2(int ne, const double *in0, const double *in1, double *out0, double *out1,
        const double *Bx, const double *By, const double *D, const double *Cx, const double *Cy) {
     extern __shared__ double smem[];
@@ -261,7 +420,7 @@ k_sep2(int ne, const double *in0, const double *in1, double *out0, double *out1,
         if (Cx) { sB[2 * N1 * N1 + i] = Cx[i]; sB[3 * N1 * N1 + i] = Cy[i]; }
     }
     const int le = t / N1, l = t - le * N1;
-    const int e = blockIdx.x * EPB2 + le;
+    const int e = blockIdx.x * (int)(blockDim.x / N1) + le;
     const bool valid = e < ne;
     double *tile = tiles + le * (2 * N1 * (N1 + 1));
     const int nf = in1 ? 2 : 1;
@@ -486,14 +645,23 @@ __global__ void k_sep1(int ne, const double *in0, const double *in1, double *out
 
 #define GDG_N1_CASES(X) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) X(14) X(15) X(16)
 
-size_t smem_stage2(int n1) { return (size_t)EPB2 * (4 * n1 + 2 * n1 * (n1 + 1)) * sizeof(double); }
-size_t smem_traces2(int n1) { return (size_t)EPB2 * (2 * n1 * (n1 + 1)) * sizeof(double); }
-size_t smem_sep2(int n1) { return (size_t)(4 * n1 * n1 + EPB2 * 2 * n1 * (n1 + 1)) * sizeof(double); }
+size_t smem_stage2(int n1, int epb) { return (size_t)epb * (4 * n1 + 2 * n1 * (n1 + 1)) * sizeof(double); }
+size_t smem_traces2(int n1, int epb) { return (size_t)epb * (2 * n1 * (n1 + 1)) * sizeof(double); }
+size_t smem_sep2(int n1, int epb) { return (size_t)(4 * n1 * n1 + epb * 2 * n1 * (n1 + 1)) * sizeof(double); }
 
 template <int N1>
 void launch_stage2(int mode, const ModalParams &mp, const StageBufs &b, double cA, double cY, cudaStream_t s) {
-    dim3 grid((mp.ne + EPB2 - 1) / EPB2), block(EPB2 * N1);
-    size_t sm = smem_stage2(N1);
+    dim3 grid((mp.ne + mp.epb - 1) / mp.epb), block(mp.epb * N1);
+    size_t sm = smem_stage2(N1, mp.epb);
+    if (mp.parity) {
+        switch (mode) {
+        case M_RHS: k_stage2p<N1, M_RHS><<<grid, block, sm, s>>>(mp, b, cA, cY); break;
+        case M_S1: k_stage2p<N1, M_S1><<<grid, block, sm, s>>>(mp, b, cA, cY); break;
+        case M_S23: k_stage2p<N1, M_S23><<<grid, block, sm, s>>>(mp, b, cA, cY); break;
+        default: k_stage2p<N1, M_S4><<<grid, block, sm, s>>>(mp, b, cA, cY); break;
+        }
+        return;
+    }
     switch (mode) {
     case M_RHS: k_stage2<N1, M_RHS><<<grid, block, sm, s>>>(mp, b, cA, cY); break;
     case M_S1: k_stage2<N1, M_S1><<<grid, block, sm, s>>>(mp, b, cA, cY); break;
@@ -533,9 +701,10 @@ void launch_stage_raw(const gdg_ctx *ctx, int mode, const StageBufs &b, double c
 void launch_traces_raw(const gdg_ctx *ctx, const double *yU, const double *yV, double *tr, cudaStream_t s) {
     const int n1 = ctx->n1;
     if (ctx->dim == 2) {
-        dim3 grid((ctx->ne + EPB2 - 1) / EPB2), block(EPB2 * n1);
+        const int epb = ctx->mp.epb;
+        dim3 grid((ctx->ne + epb - 1) / epb), block(epb * n1);
         switch (n1) {
-#define X(n) case n: k_traces2<n><<<grid, block, smem_traces2(n), s>>>(ctx->mp, yU, yV, tr); break;
+#define X(n) case n: k_traces2<n><<<grid, block, smem_traces2(n, epb), s>>>(ctx->mp, yU, yV, tr); break;
             GDG_N1_CASES(X)
 #undef X
         }
@@ -560,11 +729,12 @@ void launch_sep_raw(const gdg_ctx *ctx, const double *in0, const double *in1, do
                 int B, const double *D, int C, cudaStream_t s) {
     const int n1 = ctx->n1;
     if (ctx->dim == 2) {
-        dim3 grid((ctx->ne + EPB2 - 1) / EPB2), block(EPB2 * n1);
+        const int epb = ctx->mp.epb;
+        dim3 grid((ctx->ne + epb - 1) / epb), block(epb * n1);
         const double *Bx = mat(ctx, 0, B), *By = mat(ctx, 1, B);
         const double *Cx = C >= 0 ? mat(ctx, 0, C) : nullptr, *Cy = C >= 0 ? mat(ctx, 1, C) : nullptr;
         switch (n1) {
-#define X(n) case n: k_sep2<n><<<grid, block, smem_sep2(n), s>>>(ctx->ne, in0, in1, out0, out1, Bx, By, D, Cx, Cy); break;
+#define X(n) case n: k_sep2<n><<<grid, block, smem_sep2(n, epb), s>>>(ctx->ne, in0, in1, out0, out1, Bx, By, D, Cx, Cy); break;
             GDG_N1_CASES(X)
 #undef X
         }
@@ -597,17 +767,51 @@ int set_smem_limits() {
     // the 2-D kernels may need more than the 48 KB default of dynamic shared memory
     static bool done = false;
     if (done) return GDG_OK;
-#define X(n)                                                                                          \
-    cudaFuncSetAttribute(k_stage2<n, M_RHS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_stage2(n)); \
-    cudaFuncSetAttribute(k_stage2<n, M_S1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_stage2(n));  \
-    cudaFuncSetAttribute(k_stage2<n, M_S23>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_stage2(n)); \
-    cudaFuncSetAttribute(k_stage2<n, M_S4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_stage2(n));  \
-    cudaFuncSetAttribute(k_traces2<n>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_traces2(n));     \
-    cudaFuncSetAttribute(k_sep2<n>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_sep2(n));
+    const int lim = 200 * 1024;
+#define X(n)                                                                               \
+    cudaFuncSetAttribute(k_stage2<n, M_RHS>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);  \
+    cudaFuncSetAttribute(k_stage2<n, M_S1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);   \
+    cudaFuncSetAttribute(k_stage2<n, M_S23>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);  \
+    cudaFuncSetAttribute(k_stage2<n, M_S4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);   \
+    cudaFuncSetAttribute(k_stage2p<n, M_RHS>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim); \
+    cudaFuncSetAttribute(k_stage2p<n, M_S1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);  \
+    cudaFuncSetAttribute(k_stage2p<n, M_S23>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim); \
+    cudaFuncSetAttribute(k_stage2p<n, M_S4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);  \
+    cudaFuncSetAttribute(k_traces2<n>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);        \
+    cudaFuncSetAttribute(k_sep2<n>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     GDG_N1_CASES(X)
 #undef X
     done = true;
     return GDG_OK;
+}
+
+// Elements per block of the 2-D kernels: maximise (used warp lanes) x
+// (balance of elements over the SMs), with up to `resident` blocks per SM.
+int choose_epb(int ne, int n1, int sms) {
+    int best = 1;
+    double best_eff = -1.0;
+    for (int epb = 1; epb * n1 <= MAXB2; ++epb) {
+        const int threads = epb * n1;
+        const int warps = (threads + 31) / 32;
+        const double lanes = (double)threads / (32.0 * warps);
+        const size_t sm = smem_stage2(n1, epb);
+        int resident = 48 / warps;                          // 48 warps per SM
+        const int by_smem = (int)((200.0 * 1024) / (double)sm);
+        if (by_smem < resident) resident = by_smem;
+        const int by_regs = 65536 / (warps * 32 * 168);     // the stage kernels use up to ~168 registers
+        if (by_regs < resident) resident = by_regs;
+        if (resident < 1) continue;
+        const int blocks = (ne + epb - 1) / epb;
+        // elements on the busiest SM vs the average
+        const int per_sm_blocks = (blocks + sms - 1) / sms;
+        const double busiest = (double)per_sm_blocks * epb;
+        const double balance = ((double)ne / sms) / busiest;
+        // too few warps per SM to keep the FP64 pipe fed
+        const double fill = std::min(1.0, (double)std::min(per_sm_blocks, resident) * warps / 8.0);
+        const double eff = lanes * balance * fill;
+        if (eff > best_eff + 1e-9) { best_eff = eff; best = epb; }
+    }
+    return best;
 }
 
 // one RK4 step on the internal modal state (y_n in B_N*, traces of y_n in tr0)
@@ -651,15 +855,44 @@ int gdg_const_setup(gdg_ctx *ctx) {
         mp.beta = 0.5 * xi;
         mp.tau = 0.5 / xi;
     }
+    mp.beta2 = 2.0 * mp.beta;
+    mp.tau2 = 2.0 * mp.tau;
+    // Mode order: even modes (Psi[N-i][k] = Psi[i][k]) first, then odd ones,
+    // each group by ascending eigenvalue; the constant mode stays first.
+    // If some eigenvector has no clean parity the generic kernel is used.
+    std::vector<int> perm(n1);
+    {
+        double big = 0.0;
+        for (int i = 0; i < nn; ++i) big = std::max(big, std::fabs(ctx->Psih[i]));
+        std::vector<int> even, odd;
+        bool clean = true;
+        for (int k = 0; k < n1; ++k) {
+            double dot = 0.0;
+            for (int i = 0; i < n1; ++i) dot += ctx->Psih[i * n1 + k] * ctx->Psih[(n1 - 1 - i) * n1 + k];
+            const double sgn = dot >= 0.0 ? 1.0 : -1.0;
+            for (int i = 0; i < n1; ++i)
+                if (std::fabs(ctx->Psih[(n1 - 1 - i) * n1 + k] - sgn * ctx->Psih[i * n1 + k]) > 1e-9 * big) clean = false;
+            (sgn > 0 ? even : odd).push_back(k);
+        }
+        mp.parity = clean && (int)even.size() == (n1 + 1) / 2 && even[0] == 0 && ctx->dim == 2;
+        if (mp.parity) {
+            for (int k = 0; k < (int)even.size(); ++k) perm[k] = even[k];
+            for (int k = 0; k < (int)odd.size(); ++k) perm[even.size() + k] = odd[k];
+        } else {
+            for (int k = 0; k < n1; ++k) perm[k] = k;
+        }
+    }
     std::vector<double> tables((size_t)2 * 3 * nn, 0.0);
     std::vector<double> lam[2];
     for (int d = 0; d < ctx->dim; ++d) {
         const double H = (ctx->pb.hi[d] - ctx->pb.lo[d]) / ctx->pb.n_elem[d];
         const double sq = std::sqrt(H);
         std::vector<double> Psi(nn), M(nn);
-        for (int i = 0; i < nn; ++i) { Psi[i] = ctx->Psih[i] / sq; M[i] = H * ctx->Mh[i]; }
+        for (int i = 0; i < n1; ++i)
+            for (int k = 0; k < n1; ++k) Psi[i * n1 + k] = ctx->Psih[i * n1 + perm[k]] / sq;
+        for (int i = 0; i < nn; ++i) M[i] = H * ctx->Mh[i];
         lam[d].resize(n1);
-        for (int k = 0; k < n1; ++k) lam[d][k] = ctx->lamh[k] / (H * H);
+        for (int k = 0; k < n1; ++k) lam[d][k] = ctx->lamh[perm[k]] / (H * H);
         double *P = &tables[((size_t)d * 3 + T_P) * nn];
         double *Ps = &tables[((size_t)d * 3 + T_PSI) * nn];
         double *PT = &tables[((size_t)d * 3 + T_PSIT) * nn];
@@ -683,8 +916,13 @@ int gdg_const_setup(gdg_ctx *ctx) {
             md.gL[k] = gl;
             md.gR[k] = gr;
             md.lam[k] = lam[d][k];
+            md.hgL[k] = 0.5 * gl;
+            md.ceL[k] = 0.5 * ctx->pb.c2 * md.eL[k];
         }
     }
+    int sms = 152;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    mp.epb = ctx->dim == 2 ? choose_epb(ctx->ne, n1, sms) : 1;
     const int ents = ctx->dim == 2 ? nn : n1;
     std::vector<double> l2((size_t)2 * ents, 0.0);
     for (int m = 0; m < ents; ++m) {

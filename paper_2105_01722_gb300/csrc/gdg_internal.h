@@ -17,6 +17,8 @@
 //   aL = -phi'(0)/H (outward -x), aR = phi'(1)/H (outward +x)
 struct ModalDir {
     double eL[GDG_MAXN1], eR[GDG_MAXN1], gL[GDG_MAXN1], gR[GDG_MAXN1], lam[GDG_MAXN1];
+    // parity kernel: lift vectors with the flux factor 1/2 (and c^2) folded in
+    double hgL[GDG_MAXN1], ceL[GDG_MAXN1];
 };
 
 // Everything a stage kernel needs besides buffers (passed by value).
@@ -25,6 +27,9 @@ struct ModalParams {
     int nx, ny, ne;
     int per_x, per_y;     // periodic flags
     double c2, beta, tau; // fluxes: v* = (vi+vo)/2 - beta(di+do), q* = (di-do)/2 - tau(vi-vo)
+    double beta2, tau2;   // 2 beta, 2 tau
+    int parity;           // modes ordered even (r -> 1-r symmetric) first: eR = +-eL, gR = +-gL
+    int epb;              // elements per block of the 2-D kernels
 };
 
 struct GraphCache {

@@ -9,7 +9,8 @@
 //   M_J  = int phi_a phi_b |J|,   S_c2 = int c^2 grad phi_a . grad phi_b |J|
 //   r_u  = sum_faces int_face c^2 (n.grad phi) (v* - v_in) dS
 //   r_v  = -S_c2 U + sum_faces int_face c^2 phi q* dS
-//   (S_c2 + w w^T) y = r_u, w = M_J 1   (SPD form of Eq. DG1 with DG1_extra)
+//   (S_c2 + w w^T) y = r_u, w = M_J 1 / |e|, |e| = 1^T M_J 1 (SPD form of Eq. DG1
+//   with DG1_extra; the 1/|e| weight keeps the rank-one term O(1))
 //   M_J dV/dt = r_v,  dU/dt = V + y.
 // Preconditioner: the frozen-coefficient modified basis (Section 3.2's
 // diagonalisation on the reference element, scaled by the element means of
@@ -41,7 +42,11 @@ struct VarParams {
     const double *tab;    // B[Q][N1], D[Q][N1], wq[Q], dphiL[N1], dphiR[N1], Psi[N1][N1], lam[N1]
     const double *S, *M, *w, *pre, *face;
     unsigned long long *stats;   // [0] sum it_u, [1] sum it_v, [2] max it_u, [3] max it_v,
-                                 // [4] unconverged u, [5] unconverged v, [6] element solves
+                                 // [4] unconverged u, [5] unconverged v, [6] element solves,
+                                 // [7] sum sweeps u, [8] sum sweeps v, [9] max sweeps u, [10] max sweeps v
+    int mixed;                   // FP32 inner PCG + FP64 refinement
+    int refine_max;              // FP64 refinement sweeps per solve
+    float refine_rtol;           // inner FP32 PCG relative tolerance
 };
 
 struct VarData {
@@ -51,7 +56,7 @@ struct VarData {
     double *d_state = nullptr, *d_tr = nullptr;
     long long tr_len = 0;
     unsigned long long *d_stats = nullptr;
-    int *d_iters = nullptr;
+    int *d_iters = nullptr, *d_sweeps = nullptr;
     double *d_rel = nullptr, *d_red = nullptr, *h_red = nullptr;
     VarParams vp{};
     size_t smem_stage = 0, smem_geom = 0, smem_traces = 0, smem_pcg = 0;
@@ -114,31 +119,32 @@ __device__ __forceinline__ int neighbour(const VarParams &P, int e, int f, int &
 
 // deterministic block sum: warp butterflies, then every thread adds the
 // warp partials in the same order
-__device__ __forceinline__ double block_sum(double v, double *red) {
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, double *red) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     __syncthreads();
-    if ((threadIdx.x & 31) == 0) red[w] = v;
+    if ((threadIdx.x & 31) == 0) red[w] = (double)v;
     __syncthreads();
-    double s = 0.0;
-    for (int i = 0; i < nw; ++i) s += red[i];
+    T s = 0;
+    for (int i = 0; i < nw; ++i) s += (T)red[i];
     return s;
 }
 
-template <int NA>
-__device__ __forceinline__ double block_dot(const double *a, const double *b, double *red) {
+template <int NA, typename T>
+__device__ __forceinline__ T block_dot(const T *a, const T *b, double *red) {
     const int t = threadIdx.x;
-    return block_sum(t < NA ? a[t] * b[t] : 0.0, red);
+    return block_sum<T>(t < NA ? a[t] * b[t] : (T)0, red);
 }
 
 // y = A x for an NA x NA row-major matrix in shared memory
-template <int NA>
-__device__ __forceinline__ void matvec(const double *A, const double *x, double *y) {
+template <int NA, typename T>
+__device__ __forceinline__ void matvec(const T *A, const T *x, T *y) {
     const int t = threadIdx.x;
     if (t < NA) {
-        double s = 0.0;
-        const double *row = A + t * NA;
+        T s = 0;
+        const T *row = A + t * NA;
 #pragma unroll 9
         for (int k = 0; k < NA; ++k) s += row[k] * x[k];
         y[t] = s;
@@ -147,9 +153,8 @@ __device__ __forceinline__ void matvec(const double *A, const double *x, double 
 }
 
 // z = Psi2 diag(d) Psi2^T r, Psi2 = Psi (x) Psi (index j*N1+i), or z = r
-template <int N1>
-__device__ void precondition(const double *r, double *z, const double *Ps, const double *d, double *t1,
-                             double *t2, bool none) {
+template <int N1, typename T>
+__device__ void precondition(const T *r, T *z, const T *Ps, const T *d, T *t1, T *t2, bool none) {
     constexpr int NA = N1 * N1;
     const int t = threadIdx.x;
     if (none) {
@@ -159,28 +164,28 @@ __device__ void precondition(const double *r, double *z, const double *Ps, const
     }
     const int a = t / N1, c = t - (t / N1) * N1;
     if (t < NA) {   // t1[j][k] = sum_i r[j][i] Psi[i][k]
-        double s = 0.0;
+        T s = 0;
 #pragma unroll
         for (int i = 0; i < N1; ++i) s += r[a * N1 + i] * Ps[i * N1 + c];
         t1[t] = s;
     }
     __syncthreads();
     if (t < NA) {   // t2[l][k] = d[l][k] sum_j Psi[j][l] t1[j][k]
-        double s = 0.0;
+        T s = 0;
 #pragma unroll
         for (int j = 0; j < N1; ++j) s += Ps[j * N1 + a] * t1[j * N1 + c];
         t2[t] = d[t] * s;
     }
     __syncthreads();
     if (t < NA) {   // t1[l][i] = sum_k t2[l][k] Psi[i][k]
-        double s = 0.0;
+        T s = 0;
 #pragma unroll
         for (int k = 0; k < N1; ++k) s += t2[a * N1 + k] * Ps[c * N1 + k];
         t1[t] = s;
     }
     __syncthreads();
     if (t < NA) {   // z[j][i] = sum_l Psi[j][l] t1[l][i]
-        double s = 0.0;
+        T s = 0;
 #pragma unroll
         for (int l = 0; l < N1; ++l) s += Ps[a * N1 + l] * t1[l * N1 + c];
         z[t] = s;
@@ -241,6 +246,111 @@ __device__ int pcg(const double *A, const double *w, const double *b, double *x,
     return it;
 }
 
+// FP32 PCG from x0 = 0 on A32 (+ w32 w32^T when W) for a right-hand side of
+// unit norm: stops when ||r|| <= irtol, after imaxit iterations or at r.z = 0.
+template <int N1, bool W>
+__device__ int pcg32(const float *A, const float *w, const float *b, float *x, float *r, float *z, float *p,
+                     float *Ap, const float *Ps, const float *d, float *t1, float *t2, double *red, float irtol,
+                     int imaxit, bool none) {
+    constexpr int NA = N1 * N1;
+    const int t = threadIdx.x;
+    if (t < NA) { x[t] = 0.f; r[t] = b[t]; }
+    __syncthreads();
+    precondition<N1, float>(r, z, Ps, d, t1, t2, none);
+    if (t < NA) p[t] = z[t];
+    __syncthreads();
+    float rz = block_dot<NA, float>(r, z, red);
+    int it = 0;
+    while (it < imaxit) {
+        const float rr = block_dot<NA, float>(r, r, red);
+        if (sqrtf(rr) <= irtol || rz == 0.f) break;
+        matvec<NA, float>(A, p, Ap);
+        if (W) {
+            const float wp = block_dot<NA, float>(w, p, red);
+            if (t < NA) Ap[t] += w[t] * wp;
+            __syncthreads();
+        }
+        const float pAp = block_dot<NA, float>(p, Ap, red);
+        const float alpha = rz / pAp;
+        if (t < NA) {
+            x[t] += alpha * p[t];
+            r[t] -= alpha * Ap[t];
+        }
+        __syncthreads();
+        precondition<N1, float>(r, z, Ps, d, t1, t2, none);
+        const float rzn = block_dot<NA, float>(r, z, red);
+        const float beta = rzn / rz;
+        if (t < NA) p[t] = z[t] + beta * p[t];
+        __syncthreads();
+        rz = rzn;
+        ++it;
+    }
+    return it;
+}
+
+// Mixed-precision solve of A x = b (+ w w^T when W): iterative refinement with
+// the FP64 matrix for every residual and FP32 PCG for every correction.
+//   r = b - A x (FP64);  while ||r|| > rtol ||b||:  A c ~= r/||r|| (FP32 PCG),
+//   x += ||r|| c (FP64);  r = b - A x (FP64)
+// The stopping test is the FP64 PCG's (true FP64 residual), so the accuracy
+// is that of the FP64 solver at the same rtol.  Returns the sweeps (FP64
+// residual evaluations after the first); *inner = FP32 iterations.
+struct SolveScratch32 {
+    float *A32, *Ps32, *d32, *w32;          // matrix, preconditioner basis and diagonal, w
+    float *rhs, *x, *res, *z, *p, *Ap, *t1, *t2;
+};
+
+template <int N1, bool W>
+__device__ int refine(const double *A, const double *w, const double *b, double *x, double *r, double *Ap,
+                      const SolveScratch32 &f, double *red, double rtol, int maxsweep, float irtol,
+                      int imaxit, bool none, bool x0_zero, int *inner, double *relres) {
+    constexpr int NA = N1 * N1;
+    const int t = threadIdx.x;
+    if (x0_zero) {
+        if (t < NA) { x[t] = 0.0; r[t] = b[t]; }
+        __syncthreads();
+    } else {
+        matvec<NA, double>(A, x, Ap);
+        const double wx = W ? block_dot<NA, double>(w, x, red) : 0.0;
+        if (t < NA) r[t] = b[t] - Ap[t] - (W ? w[t] * wx : 0.0);
+        __syncthreads();
+    }
+    const double bnorm = sqrt(block_dot<NA, double>(b, b, red));
+    int sweeps = 0, its = 0;
+    double rn = sqrt(block_dot<NA, double>(r, r, red));
+    while (sweeps < maxsweep && rn > rtol * bnorm && rn > 0.0) {
+        if (t < NA) f.rhs[t] = (float)(r[t] / rn);
+        __syncthreads();
+        its += pcg32<N1, W>(f.A32, f.w32, f.rhs, f.x, f.res, f.z, f.p, f.Ap, f.Ps32, f.d32, f.t1, f.t2, red,
+                            irtol, imaxit, none);
+        if (t < NA) x[t] += rn * (double)f.x[t];
+        __syncthreads();
+        matvec<NA, double>(A, x, Ap);
+        const double wx = W ? block_dot<NA, double>(w, x, red) : 0.0;
+        if (t < NA) r[t] = b[t] - Ap[t] - (W ? w[t] * wx : 0.0);
+        __syncthreads();
+        rn = sqrt(block_dot<NA, double>(r, r, red));
+        ++sweeps;
+    }
+    *inner = its;
+    *relres = bnorm > 0.0 ? rn / bnorm : 0.0;
+    return sweeps;
+}
+
+// FP32 copies of an element matrix and of the preconditioner data
+template <int N1>
+__device__ void to_fp32(const double *A, float *A32, const double *Ps, float *Ps32, const double *d, float *d32,
+                        const double *w, float *w32) {
+    constexpr int NA = N1 * N1;
+    for (int i = threadIdx.x; i < NA * NA; i += blockDim.x) A32[i] = (float)A[i];
+    for (int i = threadIdx.x; i < N1 * N1; i += blockDim.x) Ps32[i] = (float)Ps[i];
+    for (int i = threadIdx.x; i < NA; i += blockDim.x) {
+        d32[i] = (float)d[i];
+        if (w) w32[i] = (float)w[i];
+    }
+    __syncthreads();
+}
+
 // diagonal of the frozen-coefficient preconditioner in the modified basis
 template <int N1>
 __device__ void fdm_diagonals(const double *pre, const double *lam, double *dS, double *dM) {
@@ -249,7 +359,7 @@ __device__ void fdm_diagonals(const double *pre, const double *lam, double *dS, 
     if (t < NA) {
         const double Grr = pre[0], Gss = pre[1], Jb = pre[2];
         const int l = t / N1, k = t - (t / N1) * N1;
-        dS[t] = t == 0 ? 1.0 / (Jb * Jb) : 1.0 / (Gss * lam[l] + Grr * lam[k]);
+        dS[t] = t == 0 ? 1.0 : 1.0 / (Gss * lam[l] + Grr * lam[k]);
         dM[t] = 1.0 / Jb;
     }
 }
@@ -360,7 +470,7 @@ k_var_geom(VarParams P, const double *X, const double *Y, const double *C2, doub
         }
         __syncthreads();
     }
-    // w = M_J 1 (row sums of what was just written), frozen-coefficient scalars
+    // w = M_J 1 / |e| (row sums of what was just written), frozen-coefficient scalars
     sGrr = block_sum(sGrr, red);
     sGss = block_sum(sGss, red);
     sW = block_sum(sW, red);
@@ -368,7 +478,7 @@ k_var_geom(VarParams P, const double *X, const double *Y, const double *C2, doub
         const double *row = Mout + (size_t)e * NA * NA + (size_t)t * NA;
         double s = 0.0;
         for (int k = 0; k < NA; ++k) s += row[k];
-        wout[(size_t)e * NA + t] = s;
+        wout[(size_t)e * NA + t] = s / sW;   // w = M_J 1 / |e|
     }
     if (t == 0) {
         pre[(size_t)e * 4 + 0] = sGrr;
@@ -491,6 +601,8 @@ template <int N1>
 struct StageSmem {
     static constexpr int NA = N1 * N1;
     double *A, *tb, *Yu, *Yv, *ru, *rv, *x, *r, *z, *p, *Ap, *w, *dS, *dM, *t1, *t2, *fw, *L, *red;
+    // FP32 area (mixed precision only): matrix, preconditioner and PCG vectors
+    float *A32, *Ps32, *dS32, *dM32, *w32, *r32, *z32, *p32, *Ap32, *c32, *u32, *v32, *t132, *t232;
     __device__ StageSmem(double *base, int Q) {
         A = base;
         tb = A + NA * NA;
@@ -498,9 +610,21 @@ struct StageSmem {
         Yv = Yu + NA; ru = Yv + NA; rv = ru + NA; x = rv + NA; r = x + NA; z = r + NA; p = z + NA;
         Ap = p + NA; w = Ap + NA; dS = w + NA; dM = dS + NA; t1 = dM + NA; t2 = t1 + NA;
         fw = t2 + NA; L = fw + 12 * Q; red = L + 12 * N1;
+        A32 = reinterpret_cast<float *>(red + 32);
+        Ps32 = A32 + NA * NA; dS32 = Ps32 + N1 * N1; dM32 = dS32 + NA; w32 = dM32 + NA;
+        r32 = w32 + NA; z32 = r32 + NA; p32 = z32 + NA; Ap32 = p32 + NA; c32 = Ap32 + NA;
+        u32 = c32 + NA; v32 = u32 + NA; t132 = v32 + NA; t232 = t132 + NA;
     }
-    static size_t bytes(int Q) {
-        return sizeof(double) * ((size_t)NA * NA + tab_len(Q, N1) + 14 * NA + 12 * Q + 12 * N1 + 32);
+    static size_t bytes(int Q, bool mixed) {
+        size_t d = sizeof(double) * ((size_t)NA * NA + tab_len(Q, N1) + 14 * NA + 12 * Q + 12 * N1 + 32);
+        if (mixed) d += sizeof(float) * ((size_t)NA * NA + N1 * N1 + 12 * NA);
+        return d;
+    }
+    __device__ SolveScratch32 scratch32(bool s_system) const {
+        SolveScratch32 f;
+        f.A32 = A32; f.Ps32 = Ps32; f.d32 = s_system ? dS32 : dM32; f.w32 = w32;
+        f.rhs = r32; f.x = c32; f.res = u32; f.z = z32; f.p = p32; f.Ap = Ap32; f.t1 = t132; f.t2 = t232;
+        return f;
     }
 };
 
@@ -592,21 +716,43 @@ k_var_stage(VarParams P, VarBufs b, double cA, double cY) {
     __syncthreads();
     const bool none = P.precond == GDG_PC_NONE;
     double rel_u, rel_v;
-    const int it_u = pcg<N1, true>(s.A, s.w, s.ru, s.x, s.r, s.z, s.p, s.Ap, T.Ps, s.dS, s.t1, s.t2, s.red,
-                                   P.rtol, P.maxit, none, true, &rel_u);
+    int it_u, it_v, sw_u = 0, sw_v = 0;
+    bool bad_u, bad_v;
+    if (P.mixed) {
+        to_fp32<N1>(s.A, s.A32, T.Ps, s.Ps32, s.dS, s.dS32, s.w, s.w32);
+        sw_u = refine<N1, true>(s.A, s.w, s.ru, s.x, s.r, s.Ap, s.scratch32(true), s.red, P.rtol, P.refine_max,
+                                P.refine_rtol, P.maxit, none, true, &it_u, &rel_u);
+        bad_u = sw_u >= P.refine_max && rel_u > P.rtol;
+    } else {
+        it_u = pcg<N1, true>(s.A, s.w, s.ru, s.x, s.r, s.z, s.p, s.Ap, T.Ps, s.dS, s.t1, s.t2, s.red, P.rtol,
+                             P.maxit, none, true, &rel_u);
+        bad_u = it_u >= P.maxit && rel_u > P.rtol;
+    }
     if (t < NA) s.ru[t] = s.Yv[t] + s.x[t];   // dU/dt
     __syncthreads();
     load_matrix<N1>(s.A, P.M + (size_t)e * NA * NA);
-    const int it_v = pcg<N1, false>(s.A, s.w, s.rv, s.x, s.r, s.z, s.p, s.Ap, T.Ps, s.dM, s.t1, s.t2, s.red,
-                                    P.rtol, P.maxit, none, true, &rel_v);
+    if (P.mixed) {
+        to_fp32<N1>(s.A, s.A32, T.Ps, s.Ps32, s.dM, s.dM32, nullptr, nullptr);
+        sw_v = refine<N1, false>(s.A, s.w, s.rv, s.x, s.r, s.Ap, s.scratch32(false), s.red, P.rtol,
+                                 P.refine_max, P.refine_rtol, P.maxit, none, true, &it_v, &rel_v);
+        bad_v = sw_v >= P.refine_max && rel_v > P.rtol;
+    } else {
+        it_v = pcg<N1, false>(s.A, s.w, s.rv, s.x, s.r, s.z, s.p, s.Ap, T.Ps, s.dM, s.t1, s.t2, s.red, P.rtol,
+                              P.maxit, none, true, &rel_v);
+        bad_v = it_v >= P.maxit && rel_v > P.rtol;
+    }
     if (t == 0 && P.stats) {
         atomicAdd(&P.stats[0], (unsigned long long)it_u);
         atomicAdd(&P.stats[1], (unsigned long long)it_v);
         atomicMax(&P.stats[2], (unsigned long long)it_u);
         atomicMax(&P.stats[3], (unsigned long long)it_v);
-        if (it_u >= P.maxit && rel_u > P.rtol) atomicAdd(&P.stats[4], 1ull);
-        if (it_v >= P.maxit && rel_v > P.rtol) atomicAdd(&P.stats[5], 1ull);
+        if (bad_u) atomicAdd(&P.stats[4], 1ull);
+        if (bad_v) atomicAdd(&P.stats[5], 1ull);
         atomicAdd(&P.stats[6], 1ull);
+        atomicAdd(&P.stats[7], (unsigned long long)sw_u);
+        atomicAdd(&P.stats[8], (unsigned long long)sw_v);
+        atomicMax(&P.stats[9], (unsigned long long)sw_u);
+        atomicMax(&P.stats[10], (unsigned long long)sw_v);
     }
     // k = (ru, x); RK combine into Yu / Yv (next stage input) in shared memory
     if (t < NA) {
@@ -644,7 +790,7 @@ k_var_stage(VarParams P, VarBufs b, double cA, double cY) {
 // standalone element PCG (gdg_pcg): which = 0 M, 1 S (+ w w^T)
 template <int N1>
 __global__ void __launch_bounds__(nthreads_for(N1 * N1))
-k_var_pcg(VarParams P, int which, const double *bvec, double *xvec, int *iters, double *rel) {
+k_var_pcg(VarParams P, int which, const double *bvec, double *xvec, int *iters, double *rel, int *sweeps) {
     constexpr int NA = N1 * N1;
     extern __shared__ double smraw[];
     StageSmem<N1> s(smraw, P.Q);
@@ -662,17 +808,28 @@ k_var_pcg(VarParams P, int which, const double *bvec, double *xvec, int *iters, 
     load_matrix<N1>(s.A, (which ? P.S : P.M) + (size_t)e * NA * NA);
     const bool none = P.precond == GDG_PC_NONE;
     double rr;
-    int it;
-    if (which)
+    int it, sw = 0;
+    if (P.mixed) {
+        to_fp32<N1>(s.A, s.A32, T.Ps, s.Ps32, which ? s.dS : s.dM, which ? s.dS32 : s.dM32, which ? s.w : nullptr,
+                    s.w32);
+        if (which)
+            sw = refine<N1, true>(s.A, s.w, s.ru, s.x, s.r, s.Ap, s.scratch32(true), s.red, P.rtol, P.refine_max,
+                                  P.refine_rtol, P.maxit, none, false, &it, &rr);
+        else
+            sw = refine<N1, false>(s.A, s.w, s.ru, s.x, s.r, s.Ap, s.scratch32(false), s.red, P.rtol,
+                                   P.refine_max, P.refine_rtol, P.maxit, none, false, &it, &rr);
+    } else if (which) {
         it = pcg<N1, true>(s.A, s.w, s.ru, s.x, s.r, s.z, s.p, s.Ap, T.Ps, s.dS, s.t1, s.t2, s.red, P.rtol,
                            P.maxit, none, false, &rr);
-    else
+    } else {
         it = pcg<N1, false>(s.A, s.w, s.ru, s.x, s.r, s.z, s.p, s.Ap, T.Ps, s.dM, s.t1, s.t2, s.red, P.rtol,
                             P.maxit, none, false, &rr);
+    }
     if (t < NA) xvec[off + t] = s.x[t];
     if (t == 0) {
         iters[e] = it;
         rel[e] = rr;
+        if (sweeps) sweeps[e] = sw;
     }
 }
 
@@ -721,17 +878,23 @@ size_t geom_smem(int N1, int Q) {
 size_t traces_smem(int N1, int Q) { return sizeof(double) * ((size_t)tab_len(Q, N1) + 2 * N1 * N1 + 12 * N1); }
 
 template <int N1>
-size_t stage_smem(int Q) { return StageSmem<N1>::bytes(Q); }
+size_t stage_smem(int Q, bool mixed) { return StageSmem<N1>::bytes(Q, mixed); }
 
+// The dynamic shared-memory limit is a property of the kernel function, shared
+// by every context: always raise it to the device's opt-in maximum so that a
+// context with smaller needs cannot lower it under another one.
 template <int N1>
-void set_attrs(size_t sg, size_t st, size_t ss) {
-    cudaFuncSetAttribute(k_var_geom<N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sg);
-    cudaFuncSetAttribute(k_var_traces<N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)st);
-    cudaFuncSetAttribute(k_var_stage<N1, M_RHS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
-    cudaFuncSetAttribute(k_var_stage<N1, M_S1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
-    cudaFuncSetAttribute(k_var_stage<N1, M_S23>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
-    cudaFuncSetAttribute(k_var_stage<N1, M_S4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
-    cudaFuncSetAttribute(k_var_pcg<N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
+void set_attrs() {
+    int dev = 0, lim = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&lim, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncSetAttribute(k_var_geom<N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    cudaFuncSetAttribute(k_var_traces<N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    cudaFuncSetAttribute(k_var_stage<N1, M_RHS>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    cudaFuncSetAttribute(k_var_stage<N1, M_S1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    cudaFuncSetAttribute(k_var_stage<N1, M_S23>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    cudaFuncSetAttribute(k_var_stage<N1, M_S4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    cudaFuncSetAttribute(k_var_pcg<N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
 }
 
 template <int N1>
@@ -777,7 +940,7 @@ void launch_pcg_raw(gdg_ctx *ctx, int which, const double *b, double *x, cudaStr
     const VarData &D = *ctx->var;
     const dim3 grid(ctx->ne), block(nthreads_for(ctx->n1 * ctx->n1));
     switch (ctx->n1) {
-#define X(n) case n: k_var_pcg<n><<<grid, block, D.smem_stage, s>>>(D.vp, which == GDG_OP_S, b, x, D.d_iters, D.d_rel); break;
+#define X(n) case n: k_var_pcg<n><<<grid, block, D.smem_stage, s>>>(D.vp, which == GDG_OP_S, b, x, D.d_iters, D.d_rel, D.d_sweeps); break;
         GDG_VAR_CASES(X)
 #undef X
     }
@@ -853,13 +1016,15 @@ int gdg_var_setup(gdg_ctx *ctx) {
         (st = gdg_cuda_check(ctx, cudaMalloc((void **)&D->d_nodes, 3 * nd * sizeof(double)), "alloc nodes")) ||
         (st = gdg_cuda_check(ctx, cudaMalloc((void **)&D->d_state, (size_t)B_COUNT * nd * sizeof(double)), "alloc state")) ||
         (st = gdg_cuda_check(ctx, cudaMalloc((void **)&D->d_tr, 2 * (size_t)D->tr_len * sizeof(double)), "alloc tr")) ||
-        (st = gdg_cuda_check(ctx, cudaMalloc((void **)&D->d_stats, 8 * sizeof(unsigned long long)), "alloc stats")) ||
+        (st = gdg_cuda_check(ctx, cudaMalloc((void **)&D->d_stats, 16 * sizeof(unsigned long long)), "alloc stats")) ||
+        (st = gdg_cuda_check(ctx, cudaMalloc((void **)&D->d_sweeps, (size_t)ctx->ne * sizeof(int)), "alloc sweeps")) ||
         (st = gdg_cuda_check(ctx, cudaMalloc((void **)&D->d_iters, (size_t)ctx->ne * sizeof(int)), "alloc iters")) ||
         (st = gdg_cuda_check(ctx, cudaMalloc((void **)&D->d_rel, (size_t)ctx->ne * sizeof(double)), "alloc rel")) ||
         (st = gdg_cuda_check(ctx, cudaMalloc((void **)&D->d_red, ((size_t)ctx->ne + 1) * sizeof(double)), "alloc red")) ||
         (st = gdg_cuda_check(ctx, cudaMallocHost((void **)&D->h_red, 8 * sizeof(double)), "alloc host")))
         return st;
-    cudaMemset(D->d_stats, 0, 8 * sizeof(unsigned long long));
+    cudaMemset(D->d_stats, 0, 16 * sizeof(unsigned long long));
+    cudaMemset(D->d_sweeps, 0, (size_t)ctx->ne * sizeof(int));
     if ((st = gdg_cuda_check(ctx, cudaMemcpy(D->d_tab, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice), "upload")) ||
         (st = gdg_cuda_check(ctx, cudaMemcpy(D->d_nodes, ctx->pb.x_nodes, nd * sizeof(double), cudaMemcpyHostToDevice), "upload x")) ||
         (st = gdg_cuda_check(ctx, cudaMemcpy(D->d_nodes + nd, ctx->pb.y_nodes, nd * sizeof(double), cudaMemcpyHostToDevice), "upload y")) ||
@@ -876,10 +1041,13 @@ int gdg_var_setup(gdg_ctx *ctx) {
     P.precond = ctx->pb.precond;
     P.tab = D->d_tab; P.S = D->d_S; P.M = D->d_M; P.w = D->d_w; P.pre = D->d_pre; P.face = D->d_face;
     P.stats = D->d_stats;
+    P.mixed = ctx->pb.precision == GDG_MIXED;
+    P.refine_max = ctx->pb.refine_max > 0 ? ctx->pb.refine_max : 8;
+    P.refine_rtol = (float)(ctx->pb.refine_rtol > 0.0 ? ctx->pb.refine_rtol : 1e-5);
     D->smem_geom = geom_smem(n1, Q);
     D->smem_traces = traces_smem(n1, Q);
     switch (n1) {
-#define X(n) case n: D->smem_stage = stage_smem<n>(Q); set_attrs<n>(D->smem_geom, D->smem_traces, D->smem_stage); break;
+#define X(n) case n: D->smem_stage = stage_smem<n>(Q, ctx->pb.precision == GDG_MIXED); set_attrs<n>(); break;
         GDG_VAR_CASES(X)
 #undef X
     }
@@ -909,7 +1077,7 @@ void gdg_var_free(gdg_ctx *ctx) {
     if (!D) return;
     cudaFree(D->d_S); cudaFree(D->d_M); cudaFree(D->d_w); cudaFree(D->d_pre); cudaFree(D->d_face);
     cudaFree(D->d_tab); cudaFree(D->d_nodes); cudaFree(D->d_state); cudaFree(D->d_tr);
-    cudaFree(D->d_stats); cudaFree(D->d_iters); cudaFree(D->d_rel); cudaFree(D->d_red);
+    cudaFree(D->d_stats); cudaFree(D->d_iters); cudaFree(D->d_sweeps); cudaFree(D->d_rel); cudaFree(D->d_red);
     if (D->h_red) cudaFreeHost(D->h_red);
     delete D;
     ctx->var = nullptr;
@@ -917,7 +1085,7 @@ void gdg_var_free(gdg_ctx *ctx) {
 
 int gdg_var_rhs(gdg_ctx *ctx, const double *u, const double *v, double *du, double *dv, cudaStream_t s) {
     VarData &D = *ctx->var;
-    cudaMemsetAsync(D.d_stats, 0, 8 * sizeof(unsigned long long), s);
+    cudaMemsetAsync(D.d_stats, 0, 16 * sizeof(unsigned long long), s);
     launch_traces(ctx, u, v, D.d_tr, s);
     VarBufs b{};
     b.yU = u; b.yV = v; b.oU = du; b.oV = dv; b.trin = D.d_tr;
@@ -934,9 +1102,10 @@ int gdg_var_pcg(gdg_ctx *ctx, int which, const double *b, double *x, gdg_pcg_sta
     GDG_PROF(ctx, GDG_K_PCG, s, launch_pcg_raw(ctx, which, b, x, s));
     int st = gdg_cuda_check(ctx, cudaGetLastError(), "gdg_pcg launch");
     if (st || !stats) return st;
-    std::vector<int> it(ctx->ne);
+    std::vector<int> it(ctx->ne), sw(ctx->ne);
     std::vector<double> rel(ctx->ne);
     if ((st = gdg_cuda_check(ctx, cudaMemcpyAsync(it.data(), D.d_iters, it.size() * sizeof(int), cudaMemcpyDeviceToHost, s), "iters")) ||
+        (st = gdg_cuda_check(ctx, cudaMemcpyAsync(sw.data(), D.d_sweeps, sw.size() * sizeof(int), cudaMemcpyDeviceToHost, s), "sweeps")) ||
         (st = gdg_cuda_check(ctx, cudaMemcpyAsync(rel.data(), D.d_rel, rel.size() * sizeof(double), cudaMemcpyDeviceToHost, s), "rel")) ||
         (st = gdg_cuda_check(ctx, cudaStreamSynchronize(s), "pcg sync")))
         return st;
@@ -944,15 +1113,24 @@ int gdg_var_pcg(gdg_ctx *ctx, int which, const double *b, double *x, gdg_pcg_sta
     stats->mean_iters = 0.0;
     stats->max_rel_resid = 0.0;
     stats->unconverged = 0;
+    stats->max_sweeps = 0;
+    stats->mean_sweeps = 0.0;
     bool nonfinite = false;
+    const bool mixed = ctx->pb.precision == GDG_MIXED;
     for (int e = 0; e < ctx->ne; ++e) {
         stats->max_iters = it[e] > stats->max_iters ? it[e] : stats->max_iters;
         stats->mean_iters += it[e];
+        if (mixed) {
+            stats->max_sweeps = sw[e] > stats->max_sweeps ? sw[e] : stats->max_sweeps;
+            stats->mean_sweeps += sw[e];
+        }
         if (!std::isfinite(rel[e])) nonfinite = true;
         else if (rel[e] > stats->max_rel_resid) stats->max_rel_resid = rel[e];
-        if (it[e] >= ctx->pb.pcg_maxit && rel[e] > ctx->pb.pcg_rtol) stats->unconverged++;
+        const bool capped = mixed ? sw[e] >= ctx->pb.refine_max : it[e] >= ctx->pb.pcg_maxit;
+        if (capped && rel[e] > ctx->pb.pcg_rtol) stats->unconverged++;
     }
     stats->mean_iters /= ctx->ne;
+    stats->mean_sweeps /= ctx->ne;
     if (nonfinite) return gdg_set_err(ctx, GDG_ENONFINITE, "non-finite PCG residual");
     if (stats->unconverged) return gdg_set_err(ctx, GDG_ENOCONV, "PCG hit pcg_maxit");
     return GDG_OK;
@@ -1012,12 +1190,18 @@ int gdg_var_energy(gdg_ctx *ctx, const double *u, const double *v, double *E, cu
 }
 
 int gdg_var_step_stats(gdg_ctx *ctx, gdg_pcg_stats *su, gdg_pcg_stats *sv) {
-    unsigned long long h[8];
+    unsigned long long h[16];
     int st = gdg_cuda_check(ctx, cudaMemcpy(h, ctx->var->d_stats, sizeof(h), cudaMemcpyDeviceToHost), "stats");
     if (st) return st;
     const double n = h[6] ? (double)h[6] : 1.0;
-    if (su) { su->max_iters = (int)h[2]; su->mean_iters = h[0] / n; su->max_rel_resid = 0.0; su->unconverged = (int)h[4]; }
-    if (sv) { sv->max_iters = (int)h[3]; sv->mean_iters = h[1] / n; sv->max_rel_resid = 0.0; sv->unconverged = (int)h[5]; }
-    cudaMemset(ctx->var->d_stats, 0, 8 * sizeof(unsigned long long));
+    if (su) {
+        su->max_iters = (int)h[2]; su->mean_iters = h[0] / n; su->max_rel_resid = 0.0; su->unconverged = (int)h[4];
+        su->max_sweeps = (int)h[9]; su->mean_sweeps = h[7] / n;
+    }
+    if (sv) {
+        sv->max_iters = (int)h[3]; sv->mean_iters = h[1] / n; sv->max_rel_resid = 0.0; sv->unconverged = (int)h[5];
+        sv->max_sweeps = (int)h[10]; sv->mean_sweeps = h[8] / n;
+    }
+    cudaMemset(ctx->var->d_stats, 0, 16 * sizeof(unsigned long long));
     return GDG_OK;
 }

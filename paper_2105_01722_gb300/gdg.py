@@ -39,7 +39,8 @@ class Problem(ctypes.Structure):
 
 class PcgStats(ctypes.Structure):
     _fields_ = [("max_iters", ctypes.c_int), ("mean_iters", ctypes.c_double),
-                ("max_rel_resid", ctypes.c_double), ("unconverged", ctypes.c_int)]
+                ("max_rel_resid", ctypes.c_double), ("unconverged", ctypes.c_int),
+                ("max_sweeps", ctypes.c_int), ("mean_sweeps", ctypes.c_double)]
 
 
 _LIB = None
@@ -192,13 +193,15 @@ class Context:
         if not (allow_noconv and st == ENOCONV):
             self._check(st, "gdg_pcg")
         return dict(max_iters=stats.max_iters, mean_iters=stats.mean_iters,
-                    max_rel_resid=stats.max_rel_resid, unconverged=stats.unconverged, status=st)
+                    max_rel_resid=stats.max_rel_resid, unconverged=stats.unconverged,
+                    max_sweeps=stats.max_sweeps, mean_sweeps=stats.mean_sweeps, status=st)
 
     def step_stats(self):
         """PCG statistics of the solves inside step()/rhs() since the last call."""
         su, sv = PcgStats(), PcgStats()
         self._check(lib().gdg_step_stats(self._h, ctypes.byref(su), ctypes.byref(sv)), "gdg_step_stats")
-        f = lambda s: dict(max_iters=s.max_iters, mean_iters=s.mean_iters, unconverged=s.unconverged)
+        f = lambda s: dict(max_iters=s.max_iters, mean_iters=s.mean_iters, unconverged=s.unconverged,
+                           max_sweeps=s.max_sweeps, mean_sweeps=s.mean_sweeps)
         return f(su), f(sv)
 
     def step(self, u, v, t0, dt, nsteps, stream=None):

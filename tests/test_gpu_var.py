@@ -285,3 +285,64 @@ def test_full_size_mapped_128(p):
     assert su["max_iters"] < 40 and sv["max_iters"] < 20
     assert E1 < E0 and E1 > 0.9 * E0
     ctx.close()
+
+
+# ----------------------------------------------------------- mixed precision
+
+def _mixed_pair(n, N, p, rtol, **kw):
+    X, Y, C2 = _mesh(n, N, kw.pop("kind", "mapped"), kw.pop("c2", "sine"))
+    vp = dv.VarProblem(n=n, N=N, p=p, X=X, Y=Y, C2=C2, flux="upwind")
+    mk = lambda prec: gdg.make_problem(2, n, N, p, coef=gdg.COEF_NODAL, x_nodes=X, y_nodes=Y, c2_nodes=C2,
+                                       pcg_rtol=rtol, pcg_maxit=200, precision=prec, refine_max=10,
+                                       refine_rtol=1e-5)
+    return vp, gdg.Context(mk(gdg.MIXED)), gdg.Context(mk(gdg.FP64))
+
+
+@pytest.mark.parametrize("n,N,p", [((3, 2), 8, 5), ((4, 4), 8, 3), ((2, 2), 9, 7)])
+def test_mixed_pcg_matches_direct(n, N, p):
+    """FP32 inner PCG + FP64 refinement: the true FP64 residual meets rtol,
+    and the solution agrees with the oracle's dense solve."""
+    vp, cm, _ = _mixed_pair(n, N, p, 1e-12)
+    ops = dv.assemble(vp)
+    U, V = _rand(vp, 31)
+    ru, rv = dv.residuals(vp, ops, U, V)
+    Ut, Vt = dv.solve_direct(ops, V, ru, rv)
+    x = torch.zeros(cm.n, dtype=torch.float64, device="cuda")
+    st = cm.pcg(gdg.OP_M, _dev(rv), x)
+    assert st["max_rel_resid"] <= 1e-12 and st["max_sweeps"] <= 5
+    assert _rel(x.cpu().numpy(), Vt) < 1e-10
+    x.zero_()
+    st = cm.pcg(gdg.OP_S, _dev(ru), x)
+    assert st["max_rel_resid"] <= 1e-12 and st["max_sweeps"] <= 6
+    assert _rel(x.cpu().numpy(), Ut - V) < 1e-9
+    cm.close()
+
+
+def test_mixed_rhs_and_steps_match_fp64():
+    """Mixed and FP64 forms at the same rtol give the same semi-discrete
+    derivative and trajectory to within a few rtol; the mixed form needs
+    only a few FP64 sweeps per solve."""
+    vp, cm, cf = _mixed_pair((6, 5), 8, 5, 1e-12)
+    ops = dv.assemble(vp)
+    U = inputs.gaussian_pulse(vp.X, vp.Y, 0.4, 0.6, 0.15)
+    V = 0.1 * inputs.random_state(U.shape, 41)
+    Ut, Vt = dv.time_derivative(vp, ops, U.reshape(30, -1), V.reshape(30, -1))
+    ref = np.concatenate([Ut.ravel(), Vt.ravel()])
+    outs = []
+    for ctx in (cm, cf):
+        u, v = _dev(U), _dev(V)
+        du, dv_ = torch.empty_like(u), torch.empty_like(v)
+        ctx.rhs(u, v, du, dv_)
+        outs.append(np.concatenate([du.cpu().numpy(), dv_.cpu().numpy()]))
+    assert _rel(outs[0], ref) < 1e-9 and _rel(outs[1], ref) < 1e-9
+    cm.step_stats(); cf.step_stats()
+    states = []
+    for ctx in (cm, cf):
+        u, v = _dev(U), _dev(V)
+        ctx.step(u, v, 0.0, 2e-3, 5)
+        states.append(np.concatenate([u.cpu().numpy(), v.cpu().numpy()]))
+    assert _rel(states[0], states[1]) < 1e-10
+    su, sv = cm.step_stats()
+    assert su["unconverged"] == 0 and sv["unconverged"] == 0
+    assert su["mean_sweeps"] <= 4 and sv["mean_sweeps"] <= 3
+    cm.close(); cf.close()

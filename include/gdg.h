@@ -214,6 +214,43 @@ int gdg_step_host(gdg_ctx *ctx, double *u, double *v, double t0, double dt, int 
  */
 int gdg_energy(gdg_ctx *ctx, const double *u, const double *v, double *E, void *stream);
 
+/*
+ * gdg_rhs_static -- the semi-discrete time derivative of gdg_rhs for a
+ * constant-coefficient Cartesian problem (GDG_COEF_CONST), computed without
+ * allocating anything.  The paper has no counterpart to this call.
+ *
+ * Who it is for: callers that cannot call cudaMalloc -- for example a plug-in
+ * inside a host application whose own memory pool already holds all free
+ * device memory (a fresh cudaMalloc would fail although the application has
+ * room), or a control loop that cannot afford the device-wide
+ * synchronisation cudaMalloc may perform.  Such callers cannot create a
+ * gdg_ctx either (gdg_create allocates), so this call takes the problem
+ * itself: the basis and modal tables are rebuilt on the host in fixed-size
+ * stack arrays on every call, and every device-side intermediate (tables,
+ * modal state, modal derivative, face traces) lives in one static device
+ * array of 2,097,152 doubles (16 MiB) that the library reserves on every GPU
+ * that loads it, until the process exits.
+ *
+ * pb: host problem, only GDG_COEF_CONST.  u, v, du, dv: device, nodal layout,
+ * n^d (N+1)^d doubles each; du, dv must not alias u, v.  Same result as
+ * gdg_rhs on a context created from *pb (to rounding).
+ * Size limit: 6 n1^2 + 2 n1^d + (4 n1^d + T) n^d doubles must fit the array,
+ * with n1 = N+1 and T = 8 n1 (2-D) or 4 (1-D) trace words per element
+ * (2-D, N = 8: up to 5,294 elements, e.g. 72 x 72); larger meshes return
+ * GDG_EUNSUPPORTED with a message on stderr.
+ * Set-up: the first call on each device, with that device current, looks up
+ * the array's device address (cudaGetSymbolAddress); make that first call
+ * before any stream capture.
+ * Sharing: every call writes each part of the array before reading it, so
+ * nothing carries over between calls, but all calls on a device share the
+ * one array: calls that overlap on the GPU (different streams or host
+ * threads) race and corrupt each other's results.
+ * Errors: GDG_EINVAL (bad problem or pointers), GDG_EUNSUPPORTED (too large,
+ * N+1 > 16), GDG_ECUDA (no text is kept: there is no context).
+ */
+int gdg_rhs_static(const gdg_problem *pb, const double *u, const double *v, double *du, double *dv,
+                   void *stream);
+
 /* ---- kernel timing (measurement support; not part of the method) ------ */
 /* Kernel kinds reported by gdg_profile_read. */
 enum {

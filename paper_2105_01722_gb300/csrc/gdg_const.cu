@@ -1038,3 +1038,301 @@ int gdg_const_energy(gdg_ctx *ctx, const double *u, const double *v, double *E, 
     *E = ctx->h_red[0];
     return GDG_OK;
 }
+
+// ------------------------------------------- allocation-free gdg_rhs ------
+//
+// gdg_rhs_static: the constant-coefficient gdg_rhs for callers that cannot
+// allocate device memory.  It needs no context: the host builds the basis
+// and the modal tables in fixed-size stack arrays, and every device-side
+// intermediate (tables, the modal state, the modal derivative and the face
+// traces) lives in one file-scope static device array.
+
+namespace {
+
+// 16 MiB of scratch per device, shared by every gdg_rhs_static call.
+constexpr size_t kStaticScratchDoubles = (size_t)2 * 1024 * 1024;
+static __device__ __align__(256) double g_rhs_scratch[kStaticScratchDoubles];
+
+constexpr int kMaxDevices = 64;
+double *g_rhs_scratch_addr[kMaxDevices];   // device address of g_rhs_scratch, per device
+
+// Gauss-Legendre on [0,1], fixed-size arrays (Newton on the Legendre recurrence)
+void gl_fixed(int n, double *x, double *w) {
+    const double pi = 3.14159265358979323846;
+    for (int i = 0; i < (n + 1) / 2; ++i) {
+        double z = std::cos(pi * (i + 0.75) / (n + 0.5)), pn = 0.0, dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= n; ++k) {
+                const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            if (n == 1) { p0 = 1.0; p1 = z; }
+            pn = p1;
+            dp = n * (z * p1 - p0) / (z * z - 1.0);
+            const double dz = pn / dp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-16) break;
+        }
+        double p0 = 1.0, p1 = z;
+        for (int k = 2; k <= n; ++k) {
+            const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+            p0 = p1;
+            p1 = p2;
+        }
+        if (n == 1) { p0 = 1.0; p1 = z; }
+        dp = n * (z * p1 - p0) / (z * z - 1.0);
+        x[i] = 0.5 * (1.0 - z);
+        x[n - 1 - i] = 0.5 * (1.0 + z);
+        w[i] = w[n - 1 - i] = 1.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+// Reference 1-D basis data without heap allocation: M, S (Section 3.1),
+// one-sided face slopes, and the modified basis Psi, lambda (Section 3.2).
+bool basis_fixed(int p, int N, double *M, double *S, double *dL, double *dR, double *Psi, double *lam) {
+    const int n1 = N + 1;
+    double gx[GDG_MAXN1], gw[GDG_MAXN1], phi[GDG_MAXN1], dphi[GDG_MAXN1];
+    gl_fixed(p + 1, gx, gw);
+    for (int i = 0; i < n1 * n1; ++i) { M[i] = 0.0; S[i] = 0.0; }
+    for (int k = 0; k < N; ++k)
+        for (int g = 0; g <= p; ++g) {
+            gdg_eval_basis(p, N, (k + gx[g]) / N, k, phi, dphi);
+            const double w = gw[g] / N;
+            for (int a = 0; a < n1; ++a)
+                for (int b = 0; b < n1; ++b) {
+                    M[a * n1 + b] += w * phi[a] * phi[b];
+                    S[a * n1 + b] += w * dphi[a] * dphi[b];
+                }
+        }
+    gdg_eval_basis(p, N, 0.0, 0, phi, dL);
+    gdg_eval_basis(p, N, 1.0, N - 1, phi, dR);
+    // S psi = lambda M psi: M = L L^T, Jacobi on L^-1 S L^-T
+    double L[GDG_MAXN1 * GDG_MAXN1] = {0}, Li[GDG_MAXN1 * GDG_MAXN1] = {0};
+    double C[GDG_MAXN1 * GDG_MAXN1], V[GDG_MAXN1 * GDG_MAXN1];
+    for (int j = 0; j < n1; ++j) {
+        double d = M[j * n1 + j];
+        for (int k = 0; k < j; ++k) d -= L[j * n1 + k] * L[j * n1 + k];
+        if (!(d > 0.0)) return false;
+        L[j * n1 + j] = std::sqrt(d);
+        for (int i = j + 1; i < n1; ++i) {
+            double s = M[i * n1 + j];
+            for (int k = 0; k < j; ++k) s -= L[i * n1 + k] * L[j * n1 + k];
+            L[i * n1 + j] = s / L[j * n1 + j];
+        }
+    }
+    for (int c = 0; c < n1; ++c)
+        for (int i = 0; i < n1; ++i) {
+            double s = i == c ? 1.0 : 0.0;
+            for (int k = 0; k < i; ++k) s -= L[i * n1 + k] * Li[k * n1 + c];
+            Li[i * n1 + c] = s / L[i * n1 + i];
+        }
+    for (int i = 0; i < n1; ++i)
+        for (int j = 0; j < n1; ++j) {
+            double s = 0.0;
+            for (int a = 0; a < n1; ++a)
+                for (int b = 0; b < n1; ++b) s += Li[i * n1 + a] * S[a * n1 + b] * Li[j * n1 + b];
+            C[i * n1 + j] = s;
+        }
+    for (int i = 0; i < n1; ++i)
+        for (int j = 0; j < i; ++j) C[i * n1 + j] = C[j * n1 + i] = 0.5 * (C[i * n1 + j] + C[j * n1 + i]);
+    for (int i = 0; i < n1 * n1; ++i) V[i] = (i % (n1 + 1)) == 0 ? 1.0 : 0.0;
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0, tot = 0.0;
+        for (int i = 0; i < n1 * n1; ++i) {
+            tot += C[i] * C[i];
+            if (i % (n1 + 1)) off += C[i] * C[i];
+        }
+        if (off <= 1e-30 * tot) break;
+        for (int a = 0; a < n1 - 1; ++a)
+            for (int b = a + 1; b < n1; ++b) {
+                const double cab = C[a * n1 + b];
+                if (std::fabs(cab) < 1e-300) continue;
+                const double th = (C[b * n1 + b] - C[a * n1 + a]) / (2.0 * cab);
+                const double t = (th >= 0 ? 1.0 : -1.0) / (std::fabs(th) + std::sqrt(th * th + 1.0));
+                const double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+                for (int k = 0; k < n1; ++k) {
+                    const double x = C[k * n1 + a], y = C[k * n1 + b];
+                    C[k * n1 + a] = c * x - s * y;
+                    C[k * n1 + b] = s * x + c * y;
+                }
+                for (int k = 0; k < n1; ++k) {
+                    const double x = C[a * n1 + k], y = C[b * n1 + k];
+                    C[a * n1 + k] = c * x - s * y;
+                    C[b * n1 + k] = s * x + c * y;
+                }
+                for (int k = 0; k < n1; ++k) {
+                    const double x = V[k * n1 + a], y = V[k * n1 + b];
+                    V[k * n1 + a] = c * x - s * y;
+                    V[k * n1 + b] = s * x + c * y;
+                }
+            }
+    }
+    int order[GDG_MAXN1];
+    for (int i = 0; i < n1; ++i) order[i] = i;
+    for (int i = 1; i < n1; ++i)
+        for (int j = i; j > 0 && C[order[j] * (n1 + 1)] < C[order[j - 1] * (n1 + 1)]; --j) {
+            const int tmp = order[j];
+            order[j] = order[j - 1];
+            order[j - 1] = tmp;
+        }
+    for (int k = 0; k < n1; ++k) {
+        lam[k] = C[order[k] * (n1 + 1)];
+        for (int i = 0; i < n1; ++i) {
+            double s = 0.0;
+            for (int a = 0; a < n1; ++a) s += Li[a * n1 + i] * V[a * n1 + order[k]];
+            Psi[i * n1 + k] = s;
+        }
+    }
+    // exact constant mode, then M-orthonormalise the others
+    double oMo = 0.0;
+    for (int i = 0; i < n1 * n1; ++i) oMo += M[i];
+    lam[0] = 0.0;
+    for (int i = 0; i < n1; ++i) Psi[i * n1] = 1.0 / std::sqrt(oMo);
+    for (int k = 1; k < n1; ++k) {
+        for (int j = 0; j <= k; ++j) {
+            double c = 0.0;
+            for (int a = 0; a < n1; ++a)
+                for (int b = 0; b < n1; ++b) c += Psi[a * n1 + j] * M[a * n1 + b] * Psi[b * n1 + k];
+            if (j < k) {
+                for (int i = 0; i < n1; ++i) Psi[i * n1 + k] -= c * Psi[i * n1 + j];
+            } else {
+                for (int i = 0; i < n1; ++i) Psi[i * n1 + k] /= std::sqrt(c);
+            }
+        }
+    }
+    return true;
+}
+
+}  // namespace
+
+extern "C" int gdg_rhs_static(const gdg_problem *pb, const double *u, const double *v, double *du, double *dv,
+                              void *stream) {
+    if (!pb || !u || !v || !du || !dv) return GDG_EINVAL;
+    if (du == u || du == v || dv == u || dv == v) return GDG_EINVAL;
+    if (pb->dim != 1 && pb->dim != 2) return GDG_EINVAL;
+    if (pb->coef != GDG_COEF_CONST || !(pb->c2 > 0.0)) return GDG_EINVAL;
+    if (pb->p < 1 || pb->p % 2 == 0 || pb->N < pb->p) return GDG_EINVAL;
+    if (pb->N + 1 > GDG_MAXN1) return GDG_EUNSUPPORTED;
+    if (pb->flux != GDG_FLUX_CENTRAL && pb->flux != GDG_FLUX_UPWIND) return GDG_EINVAL;
+    for (int d = 0; d < pb->dim; ++d) {
+        if (pb->n_elem[d] < 1 || !(pb->hi[d] > pb->lo[d])) return GDG_EINVAL;
+        if (pb->bc[d] != GDG_BC_DIRICHLET && pb->bc[d] != GDG_BC_PERIODIC) return GDG_EINVAL;
+    }
+    const int n1 = pb->N + 1, nn = n1 * n1, dim = pb->dim;
+    const int nx = pb->n_elem[0], ny = dim == 2 ? pb->n_elem[1] : 1;
+    const long long ne = (long long)nx * ny;
+    const int ents = dim == 2 ? nn : n1;
+    const long long ndof = ne * ents;
+    const long long tr_len = ne * (dim == 2 ? 8 * n1 : 4);
+    const long long ntab = 6LL * nn + 2LL * ents;
+    // scratch: tables | modal state (2 fields) | modal derivative (2 fields) | traces
+    const long long need = ntab + 4 * ndof + tr_len;
+    if (need > (long long)kStaticScratchDoubles) {
+        std::fprintf(stderr,
+                     "gdg_rhs_static: the problem needs %lld doubles of scratch but the static buffer holds %zu "
+                     "(16 MiB); use gdg_rhs with a context for larger meshes\n",
+                     need, kStaticScratchDoubles);
+        return GDG_EUNSUPPORTED;
+    }
+    // set-up, once per device (with that device current): device address of the array
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return GDG_ECUDA;
+    if (dev < 0 || dev >= kMaxDevices) return GDG_EUNSUPPORTED;
+    if (!g_rhs_scratch_addr[dev]) {
+        void *addr = nullptr;
+        if (cudaGetSymbolAddress(&addr, g_rhs_scratch) != cudaSuccess || !addr) return GDG_ECUDA;
+        g_rhs_scratch_addr[dev] = static_cast<double *>(addr);
+    }
+    double *base = g_rhs_scratch_addr[dev];
+
+    // host tables in fixed-size arrays
+    double Mh[GDG_MAXN1 * GDG_MAXN1], Sh[GDG_MAXN1 * GDG_MAXN1], dL[GDG_MAXN1], dR[GDG_MAXN1];
+    double Psih[GDG_MAXN1 * GDG_MAXN1], lamh[GDG_MAXN1];
+    if (!basis_fixed(pb->p, pb->N, Mh, Sh, dL, dR, Psih, lamh)) return GDG_EINVAL;
+    static_assert(GDG_MAXN1 <= 16, "table size");
+    double tab[6 * 256 + 2 * 256] = {0};
+    double lam[2][GDG_MAXN1];
+    ModalParams mp;
+    std::memset(&mp, 0, sizeof(mp));
+    mp.nx = nx;
+    mp.ny = ny;
+    mp.ne = (int)ne;
+    mp.per_x = pb->bc[0] == GDG_BC_PERIODIC;
+    mp.per_y = dim == 2 && pb->bc[1] == GDG_BC_PERIODIC;
+    mp.c2 = pb->c2;
+    if (pb->flux == GDG_FLUX_UPWIND) {
+        const double xi = pb->xi > 0 ? pb->xi : std::sqrt(pb->c2);
+        mp.beta = 0.5 * xi;
+        mp.tau = 0.5 / xi;
+    }
+    mp.beta2 = 2.0 * mp.beta;
+    mp.tau2 = 2.0 * mp.tau;
+    mp.parity = 0;     // generic stage kernel
+    mp.epb = dim == 2 ? 16 : 1;
+    for (int d = 0; d < dim; ++d) {
+        const double H = (pb->hi[d] - pb->lo[d]) / pb->n_elem[d], sq = std::sqrt(H);
+        double *P = tab + ((size_t)d * 3 + T_P) * nn, *Ps = tab + ((size_t)d * 3 + T_PSI) * nn;
+        double *PT = tab + ((size_t)d * 3 + T_PSIT) * nn;
+        for (int k = 0; k < n1; ++k) {
+            lam[d][k] = lamh[k] / (H * H);
+            for (int i = 0; i < n1; ++i) {
+                double s = 0.0;
+                for (int a = 0; a < n1; ++a) s += (Psih[a * n1 + k] / sq) * (H * Mh[a * n1 + i]);
+                P[k * n1 + i] = s;
+                Ps[i * n1 + k] = Psih[i * n1 + k] / sq;
+                PT[k * n1 + i] = Psih[i * n1 + k] / sq;
+            }
+        }
+        ModalDir &md = mp.d[d];
+        for (int k = 0; k < n1; ++k) {
+            md.eL[k] = Psih[k] / sq;
+            md.eR[k] = Psih[(n1 - 1) * n1 + k] / sq;
+            double gl = 0.0, gr = 0.0;
+            for (int i = 0; i < n1; ++i) {
+                gl += (Psih[i * n1 + k] / sq) * (-dL[i] / H);
+                gr += (Psih[i * n1 + k] / sq) * (dR[i] / H);
+            }
+            md.gL[k] = gl;
+            md.gR[k] = gr;
+            md.lam[k] = lam[d][k];
+            md.hgL[k] = 0.5 * gl;
+            md.ceL[k] = 0.5 * pb->c2 * md.eL[k];
+        }
+    }
+    double *l2 = tab + 6 * nn;
+    for (int m = 0; m < ents; ++m) {
+        const double Lm = dim == 2 ? lam[0][m % n1] + lam[1][m / n1] : lam[0][m];
+        l2[m] = -pb->c2 * Lm;
+        l2[ents + m] = m == 0 ? 0.0 : 1.0 / Lm;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaMemcpyAsync(base, tab, (size_t)ntab * sizeof(double), cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return GDG_ECUDA;
+
+    // a context on the stack holding only what the launch helpers read
+    gdg_ctx c;
+    c.dim = dim;
+    c.nx = nx;
+    c.ny = ny;
+    c.N = pb->N;
+    c.n1 = n1;
+    c.p = pb->p;
+    c.ne = (int)ne;
+    c.ndof = ndof;
+    c.pb = *pb;
+    c.mp = mp;
+    c.d_mats = base;
+    c.d_lam2 = base + 6 * nn;
+    double *Yu = base + ntab, *Yv = Yu + ndof, *Ku = Yv + ndof, *Kv = Ku + ndof, *tr = Kv + ndof;
+    set_smem_limits();
+    launch_sep(&c, u, v, Yu, Yv, T_P, nullptr, -1, s);
+    launch_traces(&c, Yu, Yv, tr, s);
+    StageBufs b{};
+    b.yU = Yu; b.yV = Yv; b.oU = Ku; b.oV = Kv; b.trin = tr; b.lam2 = c.d_lam2;
+    launch_stage(&c, M_RHS, b, 0.0, 0.0, s);
+    launch_sep(&c, Ku, Kv, du, dv, T_PSI, nullptr, -1, s);
+    c.d_mats = c.d_lam2 = nullptr;   // not owned
+    return cudaGetLastError() == cudaSuccess ? GDG_OK : GDG_ECUDA;
+}

@@ -63,6 +63,7 @@ EXPORTS = {
                                      ctypes.c_double, ctypes.c_int, ctypes.c_void_p]),
     "gdg_energy": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                   ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
+    "gdg_rhs_static": (ctypes.c_int, [ctypes.POINTER(Problem)] + [ctypes.c_void_p] * 5),
     "gdg_step_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(PcgStats), ctypes.POINTER(PcgStats)]),
     "gdg_profile_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "gdg_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
@@ -150,6 +151,16 @@ def _stream(stream=None):
     import torch
     s = torch.cuda.current_stream() if stream is None else stream
     return ctypes.c_void_p(s.cuda_stream)
+
+
+def rhs_static(problem, u, v, du, dv, stream=None):
+    """gdg_rhs_static: the constant-coefficient right-hand side without any
+    allocation (no context; scratch in the library's static device array)."""
+    n = len(u)
+    st = lib().gdg_rhs_static(ctypes.byref(problem), _ptr(u, n), _ptr(v, n), _ptr(du, n), _ptr(dv, n),
+                              _stream(stream))
+    if st != OK:
+        raise GdgError(st, "gdg_rhs_static")
 
 
 class Context:

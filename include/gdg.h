@@ -28,6 +28,7 @@
 #define GDG_H
 
 #include <stddef.h>
+#include <stdint.h>
 
 #ifdef __cplusplus
 extern "C" {
@@ -102,6 +103,8 @@ typedef struct {
                           /* refine_max) above pcg_rtol                             */
     int max_sweeps;       /* GDG_MIXED: largest number of FP64 refinement sweeps   */
     double mean_sweeps;   /* GDG_MIXED: mean sweeps (FP64 residuals after the first) */
+    long long guessed;    /* u_t solves started from the learned guess (gdg_mlp_attach) */
+    long long fell_back;  /* ... of which restarted from 0 (guess no better than 0)   */
 } gdg_pcg_stats;
 
 /* Human-readable text of a status code (static storage). */
@@ -213,6 +216,112 @@ int gdg_step_host(gdg_ctx *ctx, double *u, double *v, double t0, double dt, int 
  * u, v device; *E host; synchronises stream.  GDG_ENONFINITE if E is not finite.
  */
 int gdg_energy(gdg_ctx *ctx, const double *u, const double *v, double *E, void *stream);
+
+/*
+ * Element residuals of the semi-discretisation before the local solves
+ * (Eqs. DG1, DG2 with the fluxes of Section 2.2.1, Section 7.1 quadrature):
+ *   ru = sum_faces int c^2 (n.grad phi)(v* - v),  rv = -S_c2 u + sum_faces int c^2 phi q*
+ * so that (S_c2 + w w^T)(du - v) = ru and M_J dv = rv.  Device arrays,
+ * nodal layout.  GDG_COEF_NODAL contexts only.
+ */
+int gdg_residuals(gdg_ctx *ctx, const double *u, const double *v, double *ru, double *rv, void *stream);
+
+/* ---- learned initial guess for the u_t solve (not in the paper) -------- */
+/*
+ * A three-layer perceptron 162 -> 64 -> 64 -> 81 (tanh, tanh, linear) maps an
+ * element's features x = [c^2/mean(c^2) at its 81 nodes, r_u/||r_u||] to a
+ * guess of y/||r_u|| for (S_c2 + w w^T) y = r_u; the PCG of the u_t system
+ * then starts from ||r_u|| * guess, or from 0 when the guess's true FP64
+ * residual is not smaller than ||r_u|| (plain PCG is the fallback).
+ * Parameters: an FP32 master block params[GDG_MLP_NPARAM] in the order
+ *   W1[64][162], b1[64], W2[64][64], b2[64], W3[81][64], b3[81]
+ * and BF16 working weights w_bf16[GDG_MLP_NWEIGHT] = W1, W2, W3 (uint16_t
+ * bit patterns); the kernels multiply in FP32 with BF16 weights.
+ * All pointers below are device pointers unless stated.
+ */
+#define GDG_MLP_IN 162
+#define GDG_MLP_HID 64
+#define GDG_MLP_OUT 81
+#define GDG_MLP_NPARAM 19857
+#define GDG_MLP_NWEIGHT 19648
+
+/* Y[B][81] = net(X[B][162]). */
+int gdg_mlp_forward(const uint16_t *w_bf16, const float *params, const float *X, int B, float *Y,
+                    void *stream);
+
+/* Floats of the per-CTA partial buffer gdg_mlp_backward needs for B samples. */
+long long gdg_mlp_partial_len(int B);
+
+/*
+ * Mean-squared loss L = (1/B) sum_s ||net(X[idx[s]]) - T[idx[s]]||^2 over the
+ * B samples idx[0..B) (idx NULL: the first B rows) and its gradient
+ * grad[GDG_MLP_NPARAM] (same order as params); *loss on the device.
+ * partial: gdg_mlp_partial_len(B) floats of scratch.  Deterministic.
+ */
+int gdg_mlp_backward(const uint16_t *w_bf16, const float *params, const float *X, const float *T,
+                     const int *idx, int B, float *partial, float *grad, float *loss, void *stream);
+
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8; step counts from 1) on params,
+ * with moment buffers m, v, then refresh of w_bf16 (round to nearest even). */
+int gdg_mlp_adam(float *params, float *m, float *v, const float *grad, int step, float lr, uint16_t *w_bf16,
+                 void *stream);
+
+/* w_bf16 = BF16(weights of params). */
+int gdg_mlp_to_bf16(const float *params, uint16_t *w_bf16, void *stream);
+
+/*
+ * Training rows of every element of a GDG_COEF_NODAL context from a residual
+ * ru (e.g. of gdg_residuals): X[ne][162] features and, when y is not NULL
+ * (the u_t solution, e.g. from gdg_pcg), T[ne][81] = y/||r_u||.
+ */
+int gdg_mlp_rows(gdg_ctx *ctx, const double *ru, const double *y, float *X, float *T, void *stream);
+
+/* Use (copies of) the network in every u_t solve of gdg_step / gdg_rhs on ctx. */
+int gdg_mlp_attach(gdg_ctx *ctx, const uint16_t *w_bf16, const float *params);
+
+/* Back to plain PCG from x0 = 0. */
+int gdg_mlp_detach(gdg_ctx *ctx);
+
+/* ---- batches of independent problems ---------------------------------- */
+typedef struct gdg_batch gdg_batch;   /* opaque; owns one context per problem */
+
+/*
+ * Many independent 2-D problems advanced together (a launch pattern layered
+ * on the method; the paper advances one mesh at a time).  Every RK stage of
+ * all problems is one persistent kernel whose CTAs pull work from a queue:
+ * first the elements of GDG_COEF_NODAL problems (element PCG, with each
+ * problem's own precision: GDG_MIXED gives FP32 inner PCG with FP64
+ * refinement and FP64 state), then tiles of elements of GDG_COEF_CONST
+ * problems (modified-basis route).  A call's launches are replayed from one
+ * CUDA graph.  The launch shape (threads per block, which also sets the
+ * modal tile, and resident blocks per SM) is chosen on the first
+ * gdg_batch_step by timing every candidate on the batch's own data.
+ * pbs[count]: host problems, all dim = 2 with the same N, 7 <= N <= 9; each is
+ * validated and set up as by gdg_create (host arrays copied).
+ * Errors: as gdg_create; GDG_EUNSUPPORTED for other N.
+ */
+int gdg_batch_create(const gdg_problem *pbs, int count, gdg_batch **out);
+
+/* Free the batch and its contexts (synchronises the device). */
+int gdg_batch_destroy(gdg_batch *b);
+
+/* Doubles per field of problem i (as gdg_state_len), -1 on bad arguments. */
+long long gdg_batch_state_len(const gdg_batch *b, int i);
+
+/*
+ * Advance every problem i in place by nsteps RK4 steps of size dt[i].
+ * u, v: host arrays of count device pointers (problem i's nodal state,
+ * gdg_batch_state_len doubles each); dt: host array of count step sizes.
+ * Each problem's result equals its own gdg_step with the same settings.
+ */
+int gdg_batch_step(gdg_batch *b, double *const *u, double *const *v, const double *dt, int nsteps,
+                   void *stream);
+
+/* Launch shape chosen by the tuner (zeros before the first gdg_batch_step). */
+int gdg_batch_tuning(const gdg_batch *b, int *threads_per_block, int *blocks_per_sm, int *tile_elements);
+
+/* PCG statistics of problem i since the previous call, as gdg_step_stats. */
+int gdg_batch_stats(gdg_batch *b, int i, gdg_pcg_stats *u_sys, gdg_pcg_stats *v_sys);
 
 /*
  * gdg_rhs_static -- the semi-discrete time derivative of gdg_rhs for a

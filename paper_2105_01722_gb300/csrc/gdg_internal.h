@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <cstdint>
 #include <string>
 #include <vector>
 
@@ -30,6 +31,14 @@ struct ModalParams {
     double beta2, tau2;   // 2 beta, 2 tau
     int parity;           // modes ordered even (r -> 1-r symmetric) first: eR = +-eL, gR = +-gL
     int epb;              // elements per block of the 2-D kernels
+};
+
+// RK4 stage modes of the stage kernels
+enum {
+    M_RHS = 0,   // write k = f(Y)
+    M_S1 = 1,    // acc = cA k; Y' = Y + cY k         (Y = y_n)
+    M_S23 = 2,   // acc += cA k; Y' = y_n + cY k
+    M_S4 = 3     // y_n += acc + cA k
 };
 
 struct GraphCache {
@@ -119,3 +128,23 @@ int gdg_var_pcg(gdg_ctx *ctx, int which, const double *b, double *x, gdg_pcg_sta
 int gdg_var_step(gdg_ctx *ctx, double *u, double *v, double dt, int nsteps, cudaStream_t s);
 int gdg_var_energy(gdg_ctx *ctx, const double *u, const double *v, double *E, cudaStream_t s);
 int gdg_var_step_stats(gdg_ctx *ctx, gdg_pcg_stats *su, gdg_pcg_stats *sv);
+
+// Buffers of one problem's RK4 state as used by the stage kernels (the
+// batched launcher drives several problems' stages from one kernel).
+struct StepBuffers {
+    double *nU, *nV, *aU, *aV, *xU, *xV, *yU, *yV;   // y_n, accumulator, two stage inputs
+    double *tr0, *tr1;                               // traces of y_n / odd stages, even stages
+};
+StepBuffers gdg_const_buffers(gdg_ctx *ctx);
+StepBuffers gdg_var_buffers(gdg_ctx *ctx);
+// nodal (u, v) -> internal state and its traces; internal state -> nodal
+int gdg_const_enter(gdg_ctx *ctx, const double *u, const double *v, cudaStream_t s);
+int gdg_const_leave(gdg_ctx *ctx, double *u, double *v, cudaStream_t s);
+int gdg_var_enter(gdg_ctx *ctx, const double *u, const double *v, cudaStream_t s);
+int gdg_var_leave(gdg_ctx *ctx, double *u, double *v, cudaStream_t s);
+
+// learned-guess kernels (gdg_mlp.cu)
+int gdg_mlp_guess_launch(const uint16_t *w_bf16, const float *params, const float *c2feat, const double *ru,
+                         int ne, double *x0u, cudaStream_t s);
+int gdg_mlp_rows_launch(const float *c2feat, const double *ru, const double *y, int ne, float *X, float *T,
+                        cudaStream_t s);

@@ -1,0 +1,889 @@
+// Device code of the variable-coefficient / mapped-element path shared by
+// gdg_var.cu (per-problem launches) and gdg_batch.cu (batched launches).
+#pragma once
+
+#include <cmath>
+
+#include "gdg_internal.h"
+
+#define GDG_VAR_MAXN1 10
+
+struct VarParams {
+    int nx, ny, ne, Q;
+    int per_x, per_y, upwind;
+    double xi;            // > 0: constant splitting, else local c
+    double rtol;
+    int maxit, precond;   // GDG_PC_*
+    const double *tab;    // B[Q][N1], D[Q][N1], wq[Q], dphiL[N1], dphiR[N1], Psi[N1][N1], lam[N1]
+    const double *S, *M, *w, *pre, *face;
+    unsigned long long *stats;   // [0] sum it_u, [1] sum it_v, [2] max it_u, [3] max it_v,
+                                 // [4] unconverged u, [5] unconverged v, [6] element solves,
+                                 // [7] sum sweeps u, [8] sum sweeps v, [9] max sweeps u, [10] max sweeps v
+    int mixed;                   // FP32 inner PCG + FP64 refinement
+    int refine_max;              // FP64 refinement sweeps per solve
+    float refine_rtol;           // inner FP32 PCG relative tolerance
+};
+
+struct VarData {
+    int nq = 0, Q = 0, NA = 0;
+    double *d_S = nullptr, *d_M = nullptr, *d_w = nullptr, *d_pre = nullptr, *d_face = nullptr;
+    double *d_tab = nullptr, *d_nodes = nullptr;
+    double *d_state = nullptr, *d_tr = nullptr;
+    long long tr_len = 0;
+    unsigned long long *d_stats = nullptr;
+    int *d_iters = nullptr, *d_sweeps = nullptr;
+    double *d_rel = nullptr, *d_red = nullptr, *h_red = nullptr;
+    VarParams vp{};
+    size_t smem_stage = 0, smem_geom = 0, smem_traces = 0, smem_pcg = 0;
+    // learned u_t guess
+    float *d_c2feat = nullptr;              // [ne][81] c^2 / element mean of c^2
+    int learned = 0;
+    uint16_t *d_wbf16 = nullptr;            // attached network (copies)
+    float *d_mlp = nullptr;
+    double *d_ru = nullptr, *d_rv = nullptr, *d_x0u = nullptr;   // split-stage buffers
+};
+
+namespace {
+
+constexpr int GEOM_THREADS = 256;
+
+__host__ __device__ constexpr int nthreads_for(int na) { return ((na + 31) / 32) * 32; }
+
+struct Tabs {
+    const double *B, *D, *wq, *dphiL, *dphiR, *Ps, *lam;
+};
+
+__device__ __forceinline__ Tabs tabs_at(const double *base, int Q, int N1) {
+    Tabs t;
+    t.B = base;
+    t.D = t.B + Q * N1;
+    t.wq = t.D + Q * N1;
+    t.dphiL = t.wq + Q;
+    t.dphiR = t.dphiL + N1;
+    t.Ps = t.dphiR + N1;
+    t.lam = t.Ps + N1 * N1;
+    return t;
+}
+__host__ __device__ constexpr int tab_len(int Q, int N1) { return 2 * Q * N1 + Q + 2 * N1 + N1 * N1 + N1; }
+
+// copy the 1-D tables into shared memory
+__device__ void load_tabs(double *dst, const double *src, int n) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+}
+
+__device__ __forceinline__ size_t fix(int e, int f, int q, int k, int Q) {   // face data
+    return (((size_t)e * 4 + f) * Q + q) * 4 + k;
+}
+__device__ __forceinline__ size_t tix(int e, int f, int fld, int q, int Q) {  // traces
+    return (((size_t)e * 4 + f) * 2 + fld) * Q + q;
+}
+
+// neighbour across face f (0 xm, 1 xp, 2 ym, 3 yp) and its facing face; -1 on a Dirichlet side
+__device__ __forceinline__ int neighbour(const VarParams &P, int e, int f, int &fo) {
+    int ex = e % P.nx, ey = e / P.nx;
+    switch (f) {
+    case 0: ex -= 1; fo = 1; break;
+    case 1: ex += 1; fo = 0; break;
+    case 2: ey -= 1; fo = 3; break;
+    default: ey += 1; fo = 2; break;
+    }
+    if (ex < 0 || ex >= P.nx) {
+        if (!P.per_x) return -1;
+        ex = (ex + P.nx) % P.nx;
+    }
+    if (ey < 0 || ey >= P.ny) {
+        if (!P.per_y) return -1;
+        ey = (ey + P.ny) % P.ny;
+    }
+    return ey * P.nx + ex;
+}
+
+// deterministic block sum: warp butterflies, then every thread adds the
+// warp partials in the same order
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, double *red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[w] = (double)v;
+    __syncthreads();
+    T s = 0;
+    for (int i = 0; i < nw; ++i) s += (T)red[i];
+    return s;
+}
+
+template <int NA, typename T>
+__device__ __forceinline__ T block_dot(const T *a, const T *b, double *red) {
+    const int t = threadIdx.x;
+    return block_sum<T>(t < NA ? a[t] * b[t] : (T)0, red);
+}
+
+// y = A x for an NA x NA row-major matrix in shared memory
+template <int NA, typename T>
+__device__ __forceinline__ void matvec(const T *A, const T *x, T *y) {
+    const int t = threadIdx.x;
+    if (t < NA) {
+        T s = 0;
+        const T *row = A + t * NA;
+#pragma unroll 9
+        for (int k = 0; k < NA; ++k) s += row[k] * x[k];
+        y[t] = s;
+    }
+    __syncthreads();
+}
+
+// z = Psi2 diag(d) Psi2^T r, Psi2 = Psi (x) Psi (index j*N1+i), or z = r
+template <int N1, typename T>
+__device__ void precondition(const T *r, T *z, const T *Ps, const T *d, T *t1, T *t2, bool none) {
+    constexpr int NA = N1 * N1;
+    const int t = threadIdx.x;
+    if (none) {
+        if (t < NA) z[t] = r[t];
+        __syncthreads();
+        return;
+    }
+    const int a = t / N1, c = t - (t / N1) * N1;
+    if (t < NA) {   // t1[j][k] = sum_i r[j][i] Psi[i][k]
+        T s = 0;
+#pragma unroll
+        for (int i = 0; i < N1; ++i) s += r[a * N1 + i] * Ps[i * N1 + c];
+        t1[t] = s;
+    }
+    __syncthreads();
+    if (t < NA) {   // t2[l][k] = d[l][k] sum_j Psi[j][l] t1[j][k]
+        T s = 0;
+#pragma unroll
+        for (int j = 0; j < N1; ++j) s += Ps[j * N1 + a] * t1[j * N1 + c];
+        t2[t] = d[t] * s;
+    }
+    __syncthreads();
+    if (t < NA) {   // t1[l][i] = sum_k t2[l][k] Psi[i][k]
+        T s = 0;
+#pragma unroll
+        for (int k = 0; k < N1; ++k) s += t2[a * N1 + k] * Ps[c * N1 + k];
+        t1[t] = s;
+    }
+    __syncthreads();
+    if (t < NA) {   // z[j][i] = sum_l Psi[j][l] t1[l][i]
+        T s = 0;
+#pragma unroll
+        for (int l = 0; l < N1; ++l) s += Ps[a * N1 + l] * t1[l * N1 + c];
+        z[t] = s;
+    }
+    __syncthreads();
+}
+
+// Preconditioned CG on A (+ w w^T when W) with x0 = x (x0_zero: x0 = 0).
+// Stops when ||r|| <= rtol ||b|| (tested before each iteration), after
+// maxit iterations, or when r.z = 0.  Returns the iteration count.
+template <int N1, bool W>
+__device__ int pcg(const double *A, const double *w, const double *b, double *x, double *r, double *z,
+                   double *p, double *Ap, const double *Ps, const double *d, double *t1, double *t2,
+                   double *red, double rtol, int maxit, bool none, bool x0_zero, double *relres,
+                   bool fallback = false, int *fell = nullptr) {
+    constexpr int NA = N1 * N1;
+    const int t = threadIdx.x;
+    if (x0_zero) {
+        if (t < NA) { x[t] = 0.0; r[t] = b[t]; }
+        __syncthreads();
+    } else {
+        matvec<NA>(A, x, Ap);
+        double wx = W ? block_dot<NA>(w, x, red) : 0.0;
+        if (t < NA) r[t] = b[t] - Ap[t] - (W ? w[t] * wx : 0.0);
+        __syncthreads();
+        // a guess that does not beat x0 = 0 (true FP64 residual) is dropped
+        if (fallback && block_dot<NA>(r, r, red) >= block_dot<NA>(b, b, red)) {
+            if (t < NA) { x[t] = 0.0; r[t] = b[t]; }
+            __syncthreads();
+            if (fell) *fell = 1;
+        }
+    }
+    const double bnorm = sqrt(block_dot<NA>(b, b, red));
+    precondition<N1>(r, z, Ps, d, t1, t2, none);
+    if (t < NA) p[t] = z[t];
+    __syncthreads();
+    double rz = block_dot<NA>(r, z, red);
+    int it = 0;
+    while (it < maxit) {
+        const double rr = block_dot<NA>(r, r, red);
+        if (sqrt(rr) <= rtol * bnorm || rz == 0.0) break;
+        matvec<NA>(A, p, Ap);
+        if (W) {
+            const double wp = block_dot<NA>(w, p, red);
+            if (t < NA) Ap[t] += w[t] * wp;
+            __syncthreads();
+        }
+        const double pAp = block_dot<NA>(p, Ap, red);
+        const double alpha = rz / pAp;
+        if (t < NA) {
+            x[t] += alpha * p[t];
+            r[t] -= alpha * Ap[t];
+        }
+        __syncthreads();
+        precondition<N1>(r, z, Ps, d, t1, t2, none);
+        const double rzn = block_dot<NA>(r, z, red);
+        const double beta = rzn / rz;
+        if (t < NA) p[t] = z[t] + beta * p[t];
+        __syncthreads();
+        rz = rzn;
+        ++it;
+    }
+    const double rr = block_dot<NA>(r, r, red);
+    *relres = bnorm > 0.0 ? sqrt(rr) / bnorm : 0.0;
+    return it;
+}
+
+// FP32 PCG from x0 = 0 on A32 (+ w32 w32^T when W) for a right-hand side of
+// unit norm: stops when ||r|| <= irtol, after imaxit iterations or at r.z = 0.
+template <int N1, bool W>
+__device__ int pcg32(const float *A, const float *w, const float *b, float *x, float *r, float *z, float *p,
+                     float *Ap, const float *Ps, const float *d, float *t1, float *t2, double *red, float irtol,
+                     int imaxit, bool none) {
+    constexpr int NA = N1 * N1;
+    const int t = threadIdx.x;
+    if (t < NA) { x[t] = 0.f; r[t] = b[t]; }
+    __syncthreads();
+    precondition<N1, float>(r, z, Ps, d, t1, t2, none);
+    if (t < NA) p[t] = z[t];
+    __syncthreads();
+    float rz = block_dot<NA, float>(r, z, red);
+    int it = 0;
+    while (it < imaxit) {
+        const float rr = block_dot<NA, float>(r, r, red);
+        if (sqrtf(rr) <= irtol || rz == 0.f) break;
+        matvec<NA, float>(A, p, Ap);
+        if (W) {
+            const float wp = block_dot<NA, float>(w, p, red);
+            if (t < NA) Ap[t] += w[t] * wp;
+            __syncthreads();
+        }
+        const float pAp = block_dot<NA, float>(p, Ap, red);
+        const float alpha = rz / pAp;
+        if (t < NA) {
+            x[t] += alpha * p[t];
+            r[t] -= alpha * Ap[t];
+        }
+        __syncthreads();
+        precondition<N1, float>(r, z, Ps, d, t1, t2, none);
+        const float rzn = block_dot<NA, float>(r, z, red);
+        const float beta = rzn / rz;
+        if (t < NA) p[t] = z[t] + beta * p[t];
+        __syncthreads();
+        rz = rzn;
+        ++it;
+    }
+    return it;
+}
+
+// Mixed-precision solve of A x = b (+ w w^T when W): iterative refinement with
+// the FP64 matrix for every residual and FP32 PCG for every correction.
+//   r = b - A x (FP64);  while ||r|| > rtol ||b||:  A c ~= r/||r|| (FP32 PCG),
+//   x += ||r|| c (FP64);  r = b - A x (FP64)
+// The stopping test is the FP64 PCG's (true FP64 residual), so the accuracy
+// is that of the FP64 solver at the same rtol.  Returns the sweeps (FP64
+// residual evaluations after the first); *inner = FP32 iterations.
+struct SolveScratch32 {
+    float *A32, *Ps32, *d32, *w32;          // matrix, preconditioner basis and diagonal, w
+    float *rhs, *x, *res, *z, *p, *Ap, *t1, *t2;
+};
+
+template <int N1, bool W>
+__device__ int refine(const double *A, const double *w, const double *b, double *x, double *r, double *Ap,
+                      const SolveScratch32 &f, double *red, double rtol, int maxsweep, float irtol,
+                      int imaxit, bool none, bool x0_zero, int *inner, double *relres,
+                      bool fallback = false, int *fell = nullptr) {
+    constexpr int NA = N1 * N1;
+    const int t = threadIdx.x;
+    if (x0_zero) {
+        if (t < NA) { x[t] = 0.0; r[t] = b[t]; }
+        __syncthreads();
+    } else {
+        matvec<NA, double>(A, x, Ap);
+        const double wx = W ? block_dot<NA, double>(w, x, red) : 0.0;
+        if (t < NA) r[t] = b[t] - Ap[t] - (W ? w[t] * wx : 0.0);
+        __syncthreads();
+        if (fallback && block_dot<NA, double>(r, r, red) >= block_dot<NA, double>(b, b, red)) {
+            if (t < NA) { x[t] = 0.0; r[t] = b[t]; }
+            __syncthreads();
+            if (fell) *fell = 1;
+        }
+    }
+    const double bnorm = sqrt(block_dot<NA, double>(b, b, red));
+    int sweeps = 0, its = 0;
+    double rn = sqrt(block_dot<NA, double>(r, r, red));
+    while (sweeps < maxsweep && rn > rtol * bnorm && rn > 0.0) {
+        if (t < NA) f.rhs[t] = (float)(r[t] / rn);
+        __syncthreads();
+        its += pcg32<N1, W>(f.A32, f.w32, f.rhs, f.x, f.res, f.z, f.p, f.Ap, f.Ps32, f.d32, f.t1, f.t2, red,
+                            irtol, imaxit, none);
+        if (t < NA) x[t] += rn * (double)f.x[t];
+        __syncthreads();
+        matvec<NA, double>(A, x, Ap);
+        const double wx = W ? block_dot<NA, double>(w, x, red) : 0.0;
+        if (t < NA) r[t] = b[t] - Ap[t] - (W ? w[t] * wx : 0.0);
+        __syncthreads();
+        rn = sqrt(block_dot<NA, double>(r, r, red));
+        ++sweeps;
+    }
+    *inner = its;
+    *relres = bnorm > 0.0 ? rn / bnorm : 0.0;
+    return sweeps;
+}
+
+// FP32 copies of an element matrix and of the preconditioner data
+template <int N1>
+__device__ void to_fp32(const double *A, float *A32, const double *Ps, float *Ps32, const double *d, float *d32,
+                        const double *w, float *w32) {
+    constexpr int NA = N1 * N1;
+    for (int i = threadIdx.x; i < NA * NA; i += blockDim.x) A32[i] = (float)A[i];
+    for (int i = threadIdx.x; i < N1 * N1; i += blockDim.x) Ps32[i] = (float)Ps[i];
+    for (int i = threadIdx.x; i < NA; i += blockDim.x) {
+        d32[i] = (float)d[i];
+        if (w) w32[i] = (float)w[i];
+    }
+    __syncthreads();
+}
+
+// diagonal of the frozen-coefficient preconditioner in the modified basis
+template <int N1>
+__device__ void fdm_diagonals(const double *pre, const double *lam, double *dS, double *dM) {
+    constexpr int NA = N1 * N1;
+    const int t = threadIdx.x;
+    if (t < NA) {
+        const double Grr = pre[0], Gss = pre[1], Jb = pre[2];
+        const int l = t / N1, k = t - (t / N1) * N1;
+        dS[t] = t == 0 ? 1.0 : 1.0 / (Gss * lam[l] + Grr * lam[k]);
+        dM[t] = 1.0 / Jb;
+    }
+}
+
+// --------------------------------------------------------- assembly -------
+
+template <int N1>
+__global__ void __launch_bounds__(GEOM_THREADS)
+k_var_geom(VarParams P, const double *X, const double *Y, const double *C2, double *Sout, double *Mout,
+           double *wout, double *pre, double *face) {
+    constexpr int NA = N1 * N1;
+    extern __shared__ double sm[];
+    const int Q = P.Q, e = blockIdx.x, t = threadIdx.x;
+    double *tb = sm;
+    double *nx_ = tb + tab_len(Q, N1);
+    double *ny_ = nx_ + NA, *nc = ny_ + NA;
+    double *XD = nc + NA, *XB = XD + N1 * Q, *YD = XB + N1 * Q, *YB = YD + N1 * Q, *CB = YB + N1 * Q;
+    double *Wr = CB + N1 * Q, *Grr = Wr + Q, *Gss = Grr + Q, *Grs = Gss + Q;
+    double *CM = Grs + Q, *Crr = CM + NA, *Css = Crr + NA, *Crs = Css + NA;
+    double *red = Crs + NA;    // [32] reduction scratch
+    load_tabs(tb, P.tab, tab_len(Q, N1));
+    const Tabs T = tabs_at(tb, Q, N1);
+    for (int i = t; i < NA; i += blockDim.x) {
+        nx_[i] = X[(size_t)e * NA + i];
+        ny_[i] = Y[(size_t)e * NA + i];
+        nc[i] = C2[(size_t)e * NA + i];
+    }
+    double sGrr = 0.0, sGss = 0.0, sW = 0.0;   // this thread's share of the element means
+    __syncthreads();
+    // XD[j][a] = sum_i X[j][i] D[a][i], XB[j][a] = sum_i X[j][i] B[a][i] (same for Y; C2 with B)
+    for (int task = t; task < N1 * Q; task += blockDim.x) {
+        const int j = task / Q, a = task - (task / Q) * Q;
+        double xd = 0, xb = 0, yd = 0, yb = 0, cb = 0;
+        for (int i = 0; i < N1; ++i) {
+            const double Bi = T.B[a * N1 + i], Di = T.D[a * N1 + i];
+            xd += nx_[j * N1 + i] * Di; xb += nx_[j * N1 + i] * Bi;
+            yd += ny_[j * N1 + i] * Di; yb += ny_[j * N1 + i] * Bi;
+            cb += nc[j * N1 + i] * Bi;
+        }
+        XD[task] = xd; XB[task] = xb; YD[task] = yd; YB[task] = yb; CB[task] = cb;
+    }
+    __syncthreads();
+    constexpr int PER = (NA * NA + GEOM_THREADS - 1) / GEOM_THREADS;
+    for (int pass = 0; pass < 2; ++pass) {   // 0: M_J, 1: S_c2
+        double accv[PER];
+#pragma unroll
+        for (int m = 0; m < PER; ++m) accv[m] = 0.0;
+        for (int b = 0; b < Q; ++b) {
+            for (int a = t; a < Q; a += blockDim.x) {
+                double xr = 0, xs = 0, yr = 0, ys = 0, c2 = 0;
+                for (int j = 0; j < N1; ++j) {
+                    const double Bj = T.B[b * N1 + j], Dj = T.D[b * N1 + j];
+                    xr += Bj * XD[j * Q + a]; xs += Dj * XB[j * Q + a];
+                    yr += Bj * YD[j * Q + a]; ys += Dj * YB[j * Q + a];
+                    c2 += Bj * CB[j * Q + a];
+                }
+                const double det = xr * ys - xs * yr;
+                const double ww = T.wq[a] * T.wq[b];
+                Wr[a] = ww * det;
+                Grr[a] = ww * c2 * (xs * xs + ys * ys) / det;
+                Gss[a] = ww * c2 * (xr * xr + yr * yr) / det;
+                Grs[a] = -ww * c2 * (xr * xs + yr * ys) / det;
+                if (pass == 0) { sGrr += Grr[a]; sGss += Gss[a]; sW += Wr[a]; }
+            }
+            __syncthreads();
+            for (int task = t; task < NA; task += blockDim.x) {
+                const int i = task / N1, i2 = task - (task / N1) * N1;
+                if (pass == 0) {
+                    double s = 0;
+                    for (int a = 0; a < Q; ++a) s += Wr[a] * T.B[a * N1 + i] * T.B[a * N1 + i2];
+                    CM[task] = s;
+                } else {
+                    double srr = 0, sss = 0, srs = 0;
+                    for (int a = 0; a < Q; ++a) {
+                        const double Bi = T.B[a * N1 + i], Di = T.D[a * N1 + i];
+                        const double Bi2 = T.B[a * N1 + i2], Di2 = T.D[a * N1 + i2];
+                        srr += Grr[a] * Di * Di2;
+                        sss += Gss[a] * Bi * Bi2;
+                        srs += Grs[a] * Di * Bi2;
+                    }
+                    Crr[task] = srr; Css[task] = sss; Crs[task] = srs;
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int m = 0; m < PER; ++m) {
+                const int o = t + m * GEOM_THREADS;
+                if (o < NA * NA) {
+                    const int al = o / NA, be = o - (o / NA) * NA;
+                    const int j = al / N1, i = al - (al / N1) * N1, j2 = be / N1, i2 = be - (be / N1) * N1;
+                    const double Bj = T.B[b * N1 + j], Bj2 = T.B[b * N1 + j2];
+                    if (pass == 0) {
+                        accv[m] += Bj * Bj2 * CM[i * N1 + i2];
+                    } else {
+                        const double Dj = T.D[b * N1 + j], Dj2 = T.D[b * N1 + j2];
+                        accv[m] += Bj * Bj2 * Crr[i * N1 + i2] + Dj * Dj2 * Css[i * N1 + i2] +
+                                   Bj * Dj2 * Crs[i * N1 + i2] + Dj * Bj2 * Crs[i2 * N1 + i];
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        double *out = (pass == 0 ? Mout : Sout) + (size_t)e * NA * NA;
+#pragma unroll
+        for (int m = 0; m < PER; ++m) {
+            const int o = t + m * GEOM_THREADS;
+            if (o < NA * NA) out[o] = accv[m];
+        }
+        __syncthreads();
+    }
+    // w = M_J 1 / |e| (row sums of what was just written), frozen-coefficient scalars
+    sGrr = block_sum(sGrr, red);
+    sGss = block_sum(sGss, red);
+    sW = block_sum(sW, red);
+    if (t < NA) {
+        const double *row = Mout + (size_t)e * NA * NA + (size_t)t * NA;
+        double s = 0.0;
+        for (int k = 0; k < NA; ++k) s += row[k];
+        wout[(size_t)e * NA + t] = s / sW;   // w = M_J 1 / |e|
+    }
+    if (t == 0) {
+        pre[(size_t)e * 4 + 0] = sGrr;
+        pre[(size_t)e * 4 + 1] = sGss;
+        pre[(size_t)e * 4 + 2] = sW;
+        pre[(size_t)e * 4 + 3] = 0.0;
+    }
+    // face data: fr, fs (J^-1 n), c^2 |T| w, c at every face point
+    for (int task = t; task < 4 * Q; task += blockDim.x) {
+        const int f = task / Q, q = task - (task / Q) * Q;
+        const double *dphi = (f == 0 || f == 2) ? T.dphiL : T.dphiR;
+        double xr = 0, xs = 0, yr = 0, ys = 0, c2 = 0;
+        if (f < 2) {   // r = 0 / 1, parametrised by s_q
+            const int col = f == 0 ? 0 : N1 - 1;
+            for (int j = 0; j < N1; ++j) {
+                double dx = 0, dy = 0;
+                for (int i = 0; i < N1; ++i) { dx += nx_[j * N1 + i] * dphi[i]; dy += ny_[j * N1 + i] * dphi[i]; }
+                const double Bj = T.B[q * N1 + j], Dj = T.D[q * N1 + j];
+                xr += Bj * dx; yr += Bj * dy;
+                xs += Dj * nx_[j * N1 + col]; ys += Dj * ny_[j * N1 + col];
+                c2 += Bj * nc[j * N1 + col];
+            }
+        } else {       // s = 0 / 1, parametrised by r_q
+            const int row = f == 2 ? 0 : N1 - 1;
+            for (int i = 0; i < N1; ++i) {
+                double dx = 0, dy = 0;
+                for (int j = 0; j < N1; ++j) { dx += nx_[j * N1 + i] * dphi[j]; dy += ny_[j * N1 + i] * dphi[j]; }
+                const double Bi = T.B[q * N1 + i], Di = T.D[q * N1 + i];
+                xs += Bi * dx; ys += Bi * dy;
+                xr += Di * nx_[row * N1 + i]; yr += Di * ny_[row * N1 + i];
+                c2 += Bi * nc[row * N1 + i];
+            }
+        }
+        double tn, nxv, nyv;
+        if (f < 2) { tn = sqrt(xs * xs + ys * ys); nxv = ys / tn; nyv = -xs / tn; }
+        else { tn = sqrt(xr * xr + yr * yr); nxv = -yr / tn; nyv = xr / tn; }
+        if (f == 0 || f == 2) { nxv = -nxv; nyv = -nyv; }
+        const double det = xr * ys - xs * yr;
+        face[fix(e, f, q, 0, Q)] = (ys * nxv - xs * nyv) / det;
+        face[fix(e, f, q, 1, Q)] = (-yr * nxv + xr * nyv) / det;
+        face[fix(e, f, q, 2, Q)] = c2 * tn * T.wq[q];
+        face[fix(e, f, q, 3, Q)] = sqrt(c2);
+    }
+}
+
+// ----------------------------------------------------------- traces ------
+
+// line data of the 4 faces from nodal U, V in shared memory:
+// L[(f*3 + m)*N1 + j]: m = 0 value line of v, 1 the r-derivative data, 2 the s-derivative data
+template <int N1>
+__device__ void face_lines(const double *U, const double *V, const Tabs &T, double *L) {
+    for (int task = threadIdx.x; task < 12 * N1; task += blockDim.x) {
+        const int f = task / (3 * N1), m = (task / N1) % 3, j = task % N1;
+        const double *dphi = (f == 0 || f == 2) ? T.dphiL : T.dphiR;
+        const int edge = (f == 0 || f == 2) ? 0 : N1 - 1;
+        double s = 0.0;
+        if (f < 2) {   // x faces, line index j (rows)
+            if (m == 0) s = V[j * N1 + edge];
+            else if (m == 1) { for (int i = 0; i < N1; ++i) s += U[j * N1 + i] * dphi[i]; }
+            else s = U[j * N1 + edge];
+        } else {       // y faces, line index i (columns)
+            const int i = j;
+            if (m == 0) s = V[edge * N1 + i];
+            else if (m == 1) s = U[edge * N1 + i];
+            else { for (int jj = 0; jj < N1; ++jj) s += U[jj * N1 + i] * dphi[jj]; }
+        }
+        L[task] = s;
+    }
+    __syncthreads();
+}
+
+// v and n.grad u at every face point from the line data
+template <int N1>
+__device__ void face_points(const double *L, const Tabs &T, const double *face, int e, int Q, double *trout) {
+    for (int task = threadIdx.x; task < 4 * Q; task += blockDim.x) {
+        const int f = task / Q, q = task - (task / Q) * Q;
+        const double *l0 = L + (f * 3 + 0) * N1, *l1 = L + (f * 3 + 1) * N1, *l2 = L + (f * 3 + 2) * N1;
+        double v = 0, ur = 0, us = 0;
+        for (int j = 0; j < N1; ++j) {
+            const double Bq = T.B[q * N1 + j], Dq = T.D[q * N1 + j];
+            v += Bq * l0[j];
+            if (f < 2) { ur += Bq * l1[j]; us += Dq * l2[j]; }
+            else { ur += Dq * l1[j]; us += Bq * l2[j]; }
+        }
+        const double fr = face[fix(e, f, q, 0, Q)], fs = face[fix(e, f, q, 1, Q)];
+        trout[tix(e, f, 0, q, Q)] = v;
+        trout[tix(e, f, 1, q, Q)] = fr * ur + fs * us;
+    }
+}
+
+template <int N1>
+__global__ void k_var_traces(VarParams P, const double *u, const double *v, double *trout) {
+    constexpr int NA = N1 * N1;
+    extern __shared__ double sm[];
+    const int Q = P.Q, e = blockIdx.x;
+    double *tb = sm, *U = tb + tab_len(Q, N1), *V = U + NA, *L = V + NA;
+    load_tabs(tb, P.tab, tab_len(Q, N1));
+    for (int i = threadIdx.x; i < NA; i += blockDim.x) {
+        U[i] = u[(size_t)e * NA + i];
+        V[i] = v[(size_t)e * NA + i];
+    }
+    __syncthreads();
+    const Tabs T = tabs_at(tb, Q, N1);
+    face_lines<N1>(U, V, T, L);
+    face_points<N1>(L, T, P.face, e, Q, trout);
+}
+
+// ------------------------------------------------------------ stage ------
+
+
+struct VarBufs {
+    const double *yU, *yV;   // stage input (nodal)
+    double *nU, *nV, *aU, *aV, *oU, *oV;
+    const double *trin;
+    double *trout;
+    // split stage for the learned initial guess: part 0 = whole stage;
+    // part 1 = write the residuals r_u, r_v and stop; part 2 = take r_u, r_v
+    // and the u_t guess x0u from memory and solve (falling back to x0 = 0 when
+    // the guess's residual is not smaller than ||r_u||)
+    int part;
+    double *ru, *rv;
+    const double *x0u;
+};
+
+template <int N1>
+struct StageSmem {
+    static constexpr int NA = N1 * N1;
+    double *A, *tb, *Yu, *Yv, *ru, *rv, *x, *r, *z, *p, *Ap, *w, *dS, *dM, *t1, *t2, *fw, *L, *red;
+    // FP32 area (mixed precision only): matrix, preconditioner and PCG vectors
+    float *A32, *Ps32, *dS32, *dM32, *w32, *r32, *z32, *p32, *Ap32, *c32, *u32, *v32, *t132, *t232;
+    __device__ StageSmem(double *base, int Q) {
+        A = base;
+        tb = A + NA * NA;
+        Yu = tb + tab_len(Q, N1);
+        Yv = Yu + NA; ru = Yv + NA; rv = ru + NA; x = rv + NA; r = x + NA; z = r + NA; p = z + NA;
+        Ap = p + NA; w = Ap + NA; dS = w + NA; dM = dS + NA; t1 = dM + NA; t2 = t1 + NA;
+        fw = t2 + NA; L = fw + 12 * Q; red = L + 12 * N1;
+        A32 = reinterpret_cast<float *>(red + 32);
+        Ps32 = A32 + NA * NA; dS32 = Ps32 + N1 * N1; dM32 = dS32 + NA; w32 = dM32 + NA;
+        r32 = w32 + NA; z32 = r32 + NA; p32 = z32 + NA; Ap32 = p32 + NA; c32 = Ap32 + NA;
+        u32 = c32 + NA; v32 = u32 + NA; t132 = v32 + NA; t232 = t132 + NA;
+    }
+    static size_t bytes(int Q, bool mixed) {
+        size_t d = sizeof(double) * ((size_t)NA * NA + tab_len(Q, N1) + 14 * NA + 12 * Q + 12 * N1 + 32);
+        if (mixed) d += sizeof(float) * ((size_t)NA * NA + N1 * N1 + 12 * NA);
+        return d;
+    }
+    __device__ SolveScratch32 scratch32(bool s_system) const {
+        SolveScratch32 f;
+        f.A32 = A32; f.Ps32 = Ps32; f.d32 = s_system ? dS32 : dM32; f.w32 = w32;
+        f.rhs = r32; f.x = c32; f.res = u32; f.z = z32; f.p = p32; f.Ap = Ap32; f.t1 = t132; f.t2 = t232;
+        return f;
+    }
+};
+
+// face fluxes and lifts: r_u, r_v (r_v without the stiffness term)
+template <int N1>
+__device__ void lifts(const VarParams &P, int e, const double *trin, const Tabs &T, double *fw, double *L,
+                      double *ru, double *rv) {
+    constexpr int NA = N1 * N1;
+    const int Q = P.Q, t = threadIdx.x;
+    for (int task = t; task < 4 * Q; task += blockDim.x) {
+        const int f = task / Q, q = task - (task / Q) * Q;
+        const double vi = trin[tix(e, f, 0, q, Q)], di = trin[tix(e, f, 1, q, Q)];
+        int fo;
+        const int nb = neighbour(P, e, f, fo);
+        double vo, dO;
+        if (nb >= 0) { vo = trin[tix(nb, fo, 0, q, Q)]; dO = trin[tix(nb, fo, 1, q, Q)]; }
+        else { vo = -vi; dO = -di; }   // u = 0: mirror state
+        double beta = 0.0, tau = 0.0;
+        if (P.upwind) {
+            const double xi = P.xi > 0.0 ? P.xi : P.face[fix(e, f, q, 3, Q)];
+            beta = 0.5 * xi;
+            tau = 0.5 / xi;
+        }
+        const double vstar = 0.5 * (vi + vo) - beta * (di + dO);
+        const double qstar = 0.5 * (di - dO) - tau * (vi - vo);
+        const double g = vstar - vi;
+        const double cw = P.face[fix(e, f, q, 2, Q)];
+        fw[(f * 3 + 0) * Q + q] = cw * P.face[fix(e, f, q, 0, Q)] * g;
+        fw[(f * 3 + 1) * Q + q] = cw * P.face[fix(e, f, q, 1, Q)] * g;
+        fw[(f * 3 + 2) * Q + q] = cw * qstar;
+    }
+    __syncthreads();
+    for (int task = t; task < 12 * N1; task += blockDim.x) {
+        const int f = task / (3 * N1), m = (task / N1) % 3, j = task % N1;
+        const double *src = fw + (f * 3 + m) * Q;
+        // x faces: (B, D, B); y faces: (D, B, B)
+        const bool useD = (f < 2) ? (m == 1) : (m == 0);
+        const double *tab = useD ? T.D : T.B;
+        double s = 0.0;
+        for (int q = 0; q < Q; ++q) s += tab[q * N1 + j] * src[q];
+        L[task] = s;
+    }
+    __syncthreads();
+    if (t < NA) {
+        const int j = t / N1, i = t - (t / N1) * N1;
+        const double *Lx0 = L, *Lx1 = L + 3 * N1, *Ly0 = L + 6 * N1, *Ly1 = L + 9 * N1;
+        double u_ = T.dphiL[i] * Lx0[j] + T.dphiR[i] * Lx1[j] + T.dphiL[j] * Ly0[N1 + i] + T.dphiR[j] * Ly1[N1 + i];
+        double v_ = 0.0;
+        if (i == 0) { u_ += Lx0[N1 + j]; v_ += Lx0[2 * N1 + j]; }
+        if (i == N1 - 1) { u_ += Lx1[N1 + j]; v_ += Lx1[2 * N1 + j]; }
+        if (j == 0) { u_ += Ly0[i]; v_ += Ly0[2 * N1 + i]; }
+        if (j == N1 - 1) { u_ += Ly1[i]; v_ += Ly1[2 * N1 + i]; }
+        ru[t] = u_;
+        rv[t] = v_;
+    }
+    __syncthreads();
+}
+
+template <int N1>
+__device__ void load_matrix(double *A, const double *src) {
+    constexpr int NA = N1 * N1;
+    // element matrices start at e*NA*NA doubles: only 8-byte alignment is guaranteed
+    for (int i = threadIdx.x; i < NA * NA; i += blockDim.x) A[i] = src[i];
+    __syncthreads();
+}
+
+// One element's RK stage (one CTA of nthreads_for(N1*N1) threads).
+template <int N1, int MODE>
+__device__ __forceinline__ void var_stage_body(const VarParams &P, const VarBufs &b, double cA, double cY, int e,
+                                               double *smraw) {
+    constexpr int NA = N1 * N1;
+    StageSmem<N1> s(smraw, P.Q);
+    const int t = threadIdx.x;
+    const size_t off = (size_t)e * NA;
+    load_tabs(s.tb, P.tab, tab_len(P.Q, N1));
+    if (t < NA) {
+        s.Yu[t] = b.yU[off + t];
+        s.Yv[t] = b.yV[off + t];
+        s.w[t] = P.w[off + t];
+    }
+    __syncthreads();
+    const Tabs T = tabs_at(s.tb, P.Q, N1);
+    fdm_diagonals<N1>(P.pre + (size_t)e * 4, T.lam, s.dS, s.dM);
+    const bool guess = b.part == 2;
+    if (!guess) {
+        lifts<N1>(P, e, b.trin, T, s.fw, s.L, s.ru, s.rv);
+        // stiffness: r_v -= S U
+        load_matrix<N1>(s.A, P.S + (size_t)e * NA * NA);
+        matvec<NA>(s.A, s.Yu, s.Ap);
+        if (t < NA) s.rv[t] -= s.Ap[t];
+        __syncthreads();
+        if (b.part == 1) {
+            if (t < NA) { b.ru[off + t] = s.ru[t]; b.rv[off + t] = s.rv[t]; }
+            return;
+        }
+    } else {
+        if (t < NA) { s.ru[t] = b.ru[off + t]; s.rv[t] = b.rv[off + t]; s.x[t] = b.x0u[off + t]; }
+        load_matrix<N1>(s.A, P.S + (size_t)e * NA * NA);
+    }
+    const bool none = P.precond == GDG_PC_NONE;
+    double rel_u, rel_v;
+    int it_u, it_v, sw_u = 0, sw_v = 0, fell = 0;
+    bool bad_u, bad_v;
+    if (P.mixed) {
+        to_fp32<N1>(s.A, s.A32, T.Ps, s.Ps32, s.dS, s.dS32, s.w, s.w32);
+        sw_u = refine<N1, true>(s.A, s.w, s.ru, s.x, s.r, s.Ap, s.scratch32(true), s.red, P.rtol, P.refine_max,
+                                P.refine_rtol, P.maxit, none, !guess, &it_u, &rel_u, guess, &fell);
+        bad_u = sw_u >= P.refine_max && rel_u > P.rtol;
+    } else {
+        it_u = pcg<N1, true>(s.A, s.w, s.ru, s.x, s.r, s.z, s.p, s.Ap, T.Ps, s.dS, s.t1, s.t2, s.red, P.rtol,
+                             P.maxit, none, !guess, &rel_u, guess, &fell);
+        bad_u = it_u >= P.maxit && rel_u > P.rtol;
+    }
+    if (t < NA) s.ru[t] = s.Yv[t] + s.x[t];   // dU/dt
+    __syncthreads();
+    load_matrix<N1>(s.A, P.M + (size_t)e * NA * NA);
+    if (P.mixed) {
+        to_fp32<N1>(s.A, s.A32, T.Ps, s.Ps32, s.dM, s.dM32, nullptr, nullptr);
+        sw_v = refine<N1, false>(s.A, s.w, s.rv, s.x, s.r, s.Ap, s.scratch32(false), s.red, P.rtol,
+                                 P.refine_max, P.refine_rtol, P.maxit, none, true, &it_v, &rel_v);
+        bad_v = sw_v >= P.refine_max && rel_v > P.rtol;
+    } else {
+        it_v = pcg<N1, false>(s.A, s.w, s.rv, s.x, s.r, s.z, s.p, s.Ap, T.Ps, s.dM, s.t1, s.t2, s.red, P.rtol,
+                              P.maxit, none, true, &rel_v);
+        bad_v = it_v >= P.maxit && rel_v > P.rtol;
+    }
+    if (t == 0 && P.stats) {
+        atomicAdd(&P.stats[0], (unsigned long long)it_u);
+        atomicAdd(&P.stats[1], (unsigned long long)it_v);
+        atomicMax(&P.stats[2], (unsigned long long)it_u);
+        atomicMax(&P.stats[3], (unsigned long long)it_v);
+        if (bad_u) atomicAdd(&P.stats[4], 1ull);
+        if (bad_v) atomicAdd(&P.stats[5], 1ull);
+        atomicAdd(&P.stats[6], 1ull);
+        atomicAdd(&P.stats[7], (unsigned long long)sw_u);
+        atomicAdd(&P.stats[8], (unsigned long long)sw_v);
+        atomicMax(&P.stats[9], (unsigned long long)sw_u);
+        atomicMax(&P.stats[10], (unsigned long long)sw_v);
+        if (guess) atomicAdd(&P.stats[11], 1ull);          // solves started from a guess
+        if (fell) atomicAdd(&P.stats[12], 1ull);           // ... of which fell back to x0 = 0
+    }
+    // k = (ru, x); RK combine into Yu / Yv (next stage input) in shared memory
+    if (t < NA) {
+        const double ku = s.ru[t], kv = s.x[t];
+        if (MODE == M_RHS) {
+            b.oU[off + t] = ku;
+            b.oV[off + t] = kv;
+        } else if (MODE == M_S1) {
+            b.aU[off + t] = cA * ku;
+            b.aV[off + t] = cA * kv;
+            s.Yu[t] = s.Yu[t] + cY * ku;
+            s.Yv[t] = s.Yv[t] + cY * kv;
+        } else if (MODE == M_S23) {
+            b.aU[off + t] += cA * ku;
+            b.aV[off + t] += cA * kv;
+            s.Yu[t] = b.nU[off + t] + cY * ku;
+            s.Yv[t] = b.nV[off + t] + cY * kv;
+        } else {
+            s.Yu[t] = b.nU[off + t] + b.aU[off + t] + cA * ku;
+            s.Yv[t] = b.nV[off + t] + b.aV[off + t] + cA * kv;
+        }
+        if (MODE != M_RHS) {
+            double *dU = MODE == M_S4 ? b.nU : b.oU;
+            double *dV = MODE == M_S4 ? b.nV : b.oV;
+            dU[off + t] = s.Yu[t];
+            dV[off + t] = s.Yv[t];
+        }
+    }
+    if (MODE == M_RHS) return;
+    __syncthreads();
+    face_lines<N1>(s.Yu, s.Yv, T, s.L);
+    face_points<N1>(s.L, T, P.face, e, P.Q, b.trout);
+}
+
+template <int N1, int MODE>
+__global__ void __launch_bounds__(nthreads_for(N1 * N1))
+k_var_stage(VarParams P, VarBufs b, double cA, double cY) {
+    extern __shared__ double smraw[];
+    var_stage_body<N1, MODE>(P, b, cA, cY, blockIdx.x, smraw);
+}
+
+// standalone element PCG (gdg_pcg): which = 0 M, 1 S (+ w w^T)
+template <int N1>
+__global__ void __launch_bounds__(nthreads_for(N1 * N1))
+k_var_pcg(VarParams P, int which, const double *bvec, double *xvec, int *iters, double *rel, int *sweeps) {
+    constexpr int NA = N1 * N1;
+    extern __shared__ double smraw[];
+    StageSmem<N1> s(smraw, P.Q);
+    const int e = blockIdx.x, t = threadIdx.x;
+    const size_t off = (size_t)e * NA;
+    load_tabs(s.tb, P.tab, tab_len(P.Q, N1));
+    if (t < NA) {
+        s.ru[t] = bvec[off + t];
+        s.x[t] = xvec[off + t];
+        s.w[t] = P.w[off + t];
+    }
+    __syncthreads();
+    const Tabs T = tabs_at(s.tb, P.Q, N1);
+    fdm_diagonals<N1>(P.pre + (size_t)e * 4, T.lam, s.dS, s.dM);
+    load_matrix<N1>(s.A, (which ? P.S : P.M) + (size_t)e * NA * NA);
+    const bool none = P.precond == GDG_PC_NONE;
+    double rr;
+    int it, sw = 0;
+    if (P.mixed) {
+        to_fp32<N1>(s.A, s.A32, T.Ps, s.Ps32, which ? s.dS : s.dM, which ? s.dS32 : s.dM32, which ? s.w : nullptr,
+                    s.w32);
+        if (which)
+            sw = refine<N1, true>(s.A, s.w, s.ru, s.x, s.r, s.Ap, s.scratch32(true), s.red, P.rtol, P.refine_max,
+                                  P.refine_rtol, P.maxit, none, false, &it, &rr);
+        else
+            sw = refine<N1, false>(s.A, s.w, s.ru, s.x, s.r, s.Ap, s.scratch32(false), s.red, P.rtol,
+                                   P.refine_max, P.refine_rtol, P.maxit, none, false, &it, &rr);
+    } else if (which) {
+        it = pcg<N1, true>(s.A, s.w, s.ru, s.x, s.r, s.z, s.p, s.Ap, T.Ps, s.dS, s.t1, s.t2, s.red, P.rtol,
+                           P.maxit, none, false, &rr);
+    } else {
+        it = pcg<N1, false>(s.A, s.w, s.ru, s.x, s.r, s.z, s.p, s.Ap, T.Ps, s.dM, s.t1, s.t2, s.red, P.rtol,
+                            P.maxit, none, false, &rr);
+    }
+    if (t < NA) xvec[off + t] = s.x[t];
+    if (t == 0) {
+        iters[e] = it;
+        rel[e] = rr;
+        if (sweeps) sweeps[e] = sw;
+    }
+}
+
+// per-element V^T M V + U^T S U
+template <int N1>
+__global__ void __launch_bounds__(nthreads_for(N1 * N1))
+k_var_energy(VarParams P, const double *u, const double *v, double *part) {
+    constexpr int NA = N1 * N1;
+    __shared__ double U[NA], V[NA], red[32];
+    const int e = blockIdx.x, t = threadIdx.x;
+    if (t < NA) { U[t] = u[(size_t)e * NA + t]; V[t] = v[(size_t)e * NA + t]; }
+    __syncthreads();
+    double s = 0.0;
+    if (t < NA) {
+        const double *Mr = P.M + ((size_t)e * NA + t) * NA, *Sr = P.S + ((size_t)e * NA + t) * NA;
+        double mv = 0.0, su = 0.0;
+        for (int k = 0; k < NA; ++k) { mv += Mr[k] * V[k]; su += Sr[k] * U[k]; }
+        s = V[t] * mv + U[t] * su;
+    }
+    s = block_sum(s, red);
+    if (t == 0) part[e] = s;
+}
+
+__global__ void k_var_sum(int n, const double *part, double *out) {
+    __shared__ double red[1024];
+    const int t = threadIdx.x;
+    double s = 0.0;
+    for (int i = t; i < n; i += blockDim.x) s += part[i];
+    red[t] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (t < w) red[t] += red[t + w];
+        __syncthreads();
+    }
+    if (t == 0) out[0] = 0.5 * red[0];
+}
+
+}  // namespace

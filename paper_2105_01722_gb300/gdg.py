@@ -40,7 +40,8 @@ class Problem(ctypes.Structure):
 class PcgStats(ctypes.Structure):
     _fields_ = [("max_iters", ctypes.c_int), ("mean_iters", ctypes.c_double),
                 ("max_rel_resid", ctypes.c_double), ("unconverged", ctypes.c_int),
-                ("max_sweeps", ctypes.c_int), ("mean_sweeps", ctypes.c_double)]
+                ("max_sweeps", ctypes.c_int), ("mean_sweeps", ctypes.c_double),
+                ("guessed", ctypes.c_longlong), ("fell_back", ctypes.c_longlong)]
 
 
 _LIB = None
@@ -63,6 +64,25 @@ EXPORTS = {
                                      ctypes.c_double, ctypes.c_int, ctypes.c_void_p]),
     "gdg_energy": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                   ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
+    "gdg_residuals": (ctypes.c_int, [ctypes.c_void_p] * 6),
+    "gdg_mlp_forward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                       ctypes.c_void_p, ctypes.c_void_p]),
+    "gdg_mlp_partial_len": (ctypes.c_longlong, [ctypes.c_int]),
+    "gdg_mlp_backward": (ctypes.c_int, [ctypes.c_void_p] * 5 + [ctypes.c_int] + [ctypes.c_void_p] * 4),
+    "gdg_mlp_adam": (ctypes.c_int, [ctypes.c_void_p] * 4 + [ctypes.c_int, ctypes.c_float, ctypes.c_void_p,
+                                                           ctypes.c_void_p]),
+    "gdg_mlp_to_bf16": (ctypes.c_int, [ctypes.c_void_p] * 3),
+    "gdg_mlp_rows": (ctypes.c_int, [ctypes.c_void_p] * 6),
+    "gdg_mlp_attach": (ctypes.c_int, [ctypes.c_void_p] * 3),
+    "gdg_mlp_detach": (ctypes.c_int, [ctypes.c_void_p]),
+    "gdg_batch_create": (ctypes.c_int, [ctypes.POINTER(Problem), ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
+    "gdg_batch_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "gdg_batch_state_len": (ctypes.c_longlong, [ctypes.c_void_p, ctypes.c_int]),
+    "gdg_batch_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
+                                      ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_void_p]),
+    "gdg_batch_tuning": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.POINTER(ctypes.c_int)] * 3),
+    "gdg_batch_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(PcgStats),
+                                       ctypes.POINTER(PcgStats)]),
     "gdg_rhs_static": (ctypes.c_int, [ctypes.POINTER(Problem)] + [ctypes.c_void_p] * 5),
     "gdg_step_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(PcgStats), ctypes.POINTER(PcgStats)]),
     "gdg_profile_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
@@ -147,6 +167,26 @@ def _ptr(t, n=None):
     return ctypes.c_void_p(t.data_ptr())
 
 
+MLP_IN, MLP_HID, MLP_OUT, MLP_NPARAM, MLP_NWEIGHT = 162, 64, 81, 19857, 19648
+
+
+def _fptr(t, n=None):
+    import torch
+    if not isinstance(t, torch.Tensor) or t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous float32 CUDA tensor")
+    if n is not None and t.numel() != n:
+        raise ValueError("expected %d elements, got %d" % (n, t.numel()))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _uptr(t):
+    import torch
+    if not isinstance(t, torch.Tensor) or t.dtype != torch.int16 or not t.is_cuda or not t.is_contiguous() \
+            or t.numel() != MLP_NWEIGHT:
+        raise ValueError("expected %d int16 (BF16 bit patterns) on the device" % MLP_NWEIGHT)
+    return ctypes.c_void_p(t.data_ptr())
+
+
 def _stream(stream=None):
     import torch
     s = torch.cuda.current_stream() if stream is None else stream
@@ -212,8 +252,27 @@ class Context:
         su, sv = PcgStats(), PcgStats()
         self._check(lib().gdg_step_stats(self._h, ctypes.byref(su), ctypes.byref(sv)), "gdg_step_stats")
         f = lambda s: dict(max_iters=s.max_iters, mean_iters=s.mean_iters, unconverged=s.unconverged,
-                           max_sweeps=s.max_sweeps, mean_sweeps=s.mean_sweeps)
+                           max_sweeps=s.max_sweeps, mean_sweeps=s.mean_sweeps, guessed=s.guessed,
+                           fell_back=s.fell_back)
         return f(su), f(sv)
+
+    def residuals(self, u, v, ru, rv, stream=None):
+        self._check(lib().gdg_residuals(self._h, _ptr(u, self.n), _ptr(v, self.n), _ptr(ru, self.n),
+                                        _ptr(rv, self.n), _stream(stream)), "gdg_residuals")
+
+    def mlp_rows(self, ru, y, X, T, stream=None):
+        """Training rows (features X, targets T) of every element; y may be None."""
+        ne = self.n // 81
+        self._check(lib().gdg_mlp_rows(self._h, _ptr(ru, self.n), _ptr(y, self.n) if y is not None else None,
+                                       _fptr(X, ne * MLP_IN), _fptr(T, ne * MLP_OUT) if T is not None else None,
+                                       _stream(stream)), "gdg_mlp_rows")
+
+    def mlp_attach(self, net):
+        self._check(lib().gdg_mlp_attach(self._h, _uptr(net.wbf16), _fptr(net.params, MLP_NPARAM)),
+                    "gdg_mlp_attach")
+
+    def mlp_detach(self):
+        self._check(lib().gdg_mlp_detach(self._h), "gdg_mlp_detach")
 
     def step(self, u, v, t0, dt, nsteps, stream=None):
         self._check(lib().gdg_step(self._h, _ptr(u, self.n), _ptr(v, self.n), t0, dt, nsteps,
@@ -249,3 +308,99 @@ class Context:
         self._check(lib().gdg_energy(self._h, _ptr(u, self.n), _ptr(v, self.n), ctypes.byref(E),
                                      _stream(stream)), "gdg_energy")
         return E.value
+
+
+class Batch:
+    """A gdg_batch: independent problems advanced by shared persistent launches."""
+
+    def __init__(self, problems):
+        arr = (Problem * len(problems))(*problems)
+        self._problems = problems     # keep host arrays alive through create
+        self._h = ctypes.c_void_p()
+        st = lib().gdg_batch_create(arr, len(problems), ctypes.byref(self._h))
+        if st != OK:
+            raise GdgError(st, "gdg_batch_create")
+        self.count = len(problems)
+        self.lens = [lib().gdg_batch_state_len(self._h, i) for i in range(self.count)]
+
+    def close(self):
+        if self._h:
+            lib().gdg_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, us, vs, dts, nsteps, stream=None):
+        U = (ctypes.c_void_p * self.count)(*[_ptr(u, n).value for u, n in zip(us, self.lens)])
+        V = (ctypes.c_void_p * self.count)(*[_ptr(v, n).value for v, n in zip(vs, self.lens)])
+        D = (ctypes.c_double * self.count)(*dts)
+        st = lib().gdg_batch_step(self._h, U, V, D, nsteps, _stream(stream))
+        if st != OK:
+            raise GdgError(st, "gdg_batch_step")
+
+    def tuning(self):
+        t, b, e = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        lib().gdg_batch_tuning(self._h, ctypes.byref(t), ctypes.byref(b), ctypes.byref(e))
+        return dict(threads_per_block=t.value, blocks_per_sm=b.value, tile_elements=e.value)
+
+    def stats(self, i):
+        su, sv = PcgStats(), PcgStats()
+        st = lib().gdg_batch_stats(self._h, i, ctypes.byref(su), ctypes.byref(sv))
+        if st != OK:
+            raise GdgError(st, "gdg_batch_stats")
+        f = lambda s: dict(max_iters=s.max_iters, mean_iters=s.mean_iters, unconverged=s.unconverged,
+                           max_sweeps=s.max_sweeps, mean_sweeps=s.mean_sweeps)
+        return f(su), f(sv)
+
+
+class Mlp:
+    """Network parameters on the device (FP32 master + BF16 working weights)
+    and the library's training kernels.  Only argument marshalling here."""
+
+    def __init__(self, params, device="cuda"):
+        import torch
+        self.params = torch.as_tensor(params, dtype=torch.float32, device=device).contiguous()
+        assert self.params.numel() == MLP_NPARAM
+        self.wbf16 = torch.zeros(MLP_NWEIGHT, dtype=torch.int16, device=device)
+        self.m = torch.zeros_like(self.params)
+        self.v = torch.zeros_like(self.params)
+        self.grad = torch.zeros_like(self.params)
+        self.loss = torch.zeros(1, dtype=torch.float32, device=device)
+        self.step_count = 0
+        self._partial = None
+        st = lib().gdg_mlp_to_bf16(_fptr(self.params), _uptr(self.wbf16), _stream())
+        if st != OK:
+            raise GdgError(st, "gdg_mlp_to_bf16")
+
+    def forward(self, X, Y, stream=None):
+        B = X.numel() // MLP_IN
+        st = lib().gdg_mlp_forward(_uptr(self.wbf16), _fptr(self.params), _fptr(X, B * MLP_IN), B,
+                                   _fptr(Y, B * MLP_OUT), _stream(stream))
+        if st != OK:
+            raise GdgError(st, "gdg_mlp_forward")
+
+    def backward(self, X, T, idx=None, stream=None):
+        """Loss (device tensor) and self.grad for rows idx (int32 device tensor) or all rows."""
+        import torch
+        B = idx.numel() if idx is not None else X.numel() // MLP_IN
+        need = lib().gdg_mlp_partial_len(B)
+        if self._partial is None or self._partial.numel() < need:
+            self._partial = torch.empty(need, dtype=torch.float32, device=X.device)
+        ip = ctypes.c_void_p(idx.data_ptr()) if idx is not None else None
+        st = lib().gdg_mlp_backward(_uptr(self.wbf16), _fptr(self.params), _fptr(X), _fptr(T), ip, B,
+                                    ctypes.c_void_p(self._partial.data_ptr()), _fptr(self.grad),
+                                    _fptr(self.loss), _stream(stream))
+        if st != OK:
+            raise GdgError(st, "gdg_mlp_backward")
+        return self.loss
+
+    def adam(self, lr, stream=None):
+        self.step_count += 1
+        st = lib().gdg_mlp_adam(_fptr(self.params), _fptr(self.m), _fptr(self.v), _fptr(self.grad),
+                                self.step_count, ctypes.c_float(lr), _uptr(self.wbf16), _stream(stream))
+        if st != OK:
+            raise GdgError(st, "gdg_mlp_adam")

@@ -173,6 +173,137 @@ def run_reference(args):
     return 0
 
 
+
+def _timed_ms(fn):
+    import torch
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def forms_variable(steps=16):
+    """Mapped 128 x 128 elements, c^2 = 1 + 0.5 sin 2pi x cos 2pi y, p = 3 and 5,
+    PCG to rtol 1e-10: FP64 against FP32-inner / FP64-refined PCG (same stopping
+    test, so equal accuracy by construction); both trajectories are compared."""
+    import numpy as np
+    import torch
+    from paper_2105_01722_gb300 import gdg, inputs
+    out = {}
+    for p in (3, 5):
+        X, Y = inputs.mapped_nodes((128, 128), 8, 0.05)
+        C2 = inputs.c2_sine(X, Y)
+        U0 = inputs.gaussian_pulse(X, Y, 0.5, 0.5, 0.05)
+        dt = 0.1 / 1024 / np.sqrt(1.5)
+        states = {}
+        for prec, name in ((gdg.FP64, "fp64"), (gdg.MIXED, "mixed")):
+            ctx = gdg.Context(gdg.make_problem(2, (128, 128), 8, p, coef=gdg.COEF_NODAL, x_nodes=X, y_nodes=Y,
+                                               c2_nodes=C2, pcg_rtol=1e-10, pcg_maxit=100, precision=prec))
+            u = torch.tensor(U0.ravel(), device="cuda")
+            v = torch.zeros_like(u)
+            ctx.step(u, v, 0.0, dt, 8)
+            ctx.step_stats()
+            ms = _timed_ms(lambda: ctx.step(u, v, 0.0, dt, steps))
+            su, sv = ctx.step_stats()
+            states[name] = torch.cat([u, v]).cpu().numpy()
+            out["p%d_%s" % (p, name)] = {
+                "dof_steps_per_s": 128 * 128 * 81 * steps / (ms / 1e3), "ms_per_step": ms / steps,
+                "pcg_u_mean_iters": su["mean_iters"], "pcg_v_mean_iters": sv["mean_iters"],
+                "refine_sweeps_u": su["mean_sweeps"], "refine_sweeps_v": sv["mean_sweeps"]}
+            ctx.close()
+        a, b = states["mixed"], states["fp64"]
+        out["p%d_mixed_vs_fp64_rel_l2" % p] = float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    out["workload"] = ("2-D variable c^2 on the sine-mapped unit square, 128x128 elements of 8x8 cells, "
+                       "Gaussian pulse, PCG rtol 1e-10, %d RK4 steps after 8 warm-up steps" % steps)
+    return out
+
+
+def forms_batched(steps=8):
+    """48 independent problems (seeds 20210501+i, n ~ U{16..128}, p in {3,5,7},
+    alternating constant / smooth random c^2): one batch (persistent launches,
+    graph, tuned) against stepping each problem with its own gdg_step."""
+    import numpy as np
+    import torch
+    from paper_2105_01722_gb300 import gdg, inputs
+    specs = inputs.batched_problems(48)
+    cfl = {3: 0.2, 5: 0.15, 7: 0.12}
+    dof = sum(sp["n"] ** 2 * 81 for sp in specs)
+    out = {"problems": 48, "dof": dof}
+    for prec, name in ((gdg.FP64, "fp64"), (gdg.MIXED, "mixed")):
+        built = []
+        for sp in specs:
+            n, p = sp["n"], sp["p"]
+            X, Y = inputs.cartesian_nodes((n, n), 8)
+            if sp["variable"]:
+                C2 = inputs.smooth_random_c2(X, Y, sp["seed"])
+                pb = gdg.make_problem(2, (n, n), 8, p, coef=gdg.COEF_NODAL, x_nodes=X, y_nodes=Y, c2_nodes=C2,
+                                      pcg_rtol=1e-10, pcg_maxit=100, precision=prec)
+                cmax = float(np.sqrt(C2.max()))
+            else:
+                pb = gdg.make_problem(2, (n, n), 8, p, c2=1.0)
+                cmax = 1.0
+            built.append((pb, inputs.gaussian_pulse(X, Y, sp["x0"], sp["y0"], 0.05).ravel(), cfl[p] / (n * 8) / cmax))
+        us = [torch.tensor(b[1], device="cuda") for b in built]
+        vs = [torch.zeros_like(u) for u in us]
+        dts = [b[2] for b in built]
+        batch = gdg.Batch([b[0] for b in built])
+        batch.step(us, vs, dts, 4)
+        ms = _timed_ms(lambda: batch.step(us, vs, dts, steps))
+        out["batched_" + name] = {"dof_steps_per_s": dof * steps / (ms / 1e3), "ms_per_step": ms / steps,
+                                  "tuning": batch.tuning()}
+        batch.close()
+        ctxs = [gdg.Context(b[0]) for b in built]
+        for c, u, v, d in zip(ctxs, us, vs, dts):
+            c.step(u, v, 0.0, d, 4)
+        ms = _timed_ms(lambda: [c.step(u, v, 0.0, d, steps) for c, u, v, d in zip(ctxs, us, vs, dts)])
+        out["sequential_" + name] = {"dof_steps_per_s": dof * steps / (ms / 1e3), "ms_per_step": ms / steps}
+        for c in ctxs:
+            c.close()
+        del us, vs
+        torch.cuda.empty_cache()
+    return out
+
+
+def forms_learned(rows=20000, epochs=30, steps=16):
+    """Learned u_t initial guess: rows generated by the method on random smooth
+    c^2 in [1/2, 2] (p = 5, 8x8 cells), trained with the library's kernels; u_t
+    PCG iterations and DOF-steps/s on an unseen 128 x 128 mesh at rtol 1e-10,
+    with and without the network (FP64 and mixed PCG)."""
+    import time
+    import torch
+    from paper_2105_01722_gb300 import gdg, inputs, learned
+    t0 = time.time()
+    X, T = learned.generate(rows, n=16, seed0=2000, snapshots=6)
+    t1 = time.time()
+    ntr = int(0.9 * rows)
+    net, hist = learned.train(X[:ntr], T[:ntr], epochs=epochs, batch=256, lr=2e-3)
+    t2 = time.time()
+    out = {"rows": rows, "train_rows": ntr, "epochs": epochs, "generate_s": t1 - t0, "train_s": t2 - t1,
+           "loss_first_epoch": hist[0], "loss_last_epoch": hist[-1],
+           "test_mean_rel_err": learned.relative_error(net, X[ntr:], T[ntr:])}
+    for prec, name in ((gdg.FP64, "fp64"), (gdg.MIXED, "mixed")):
+        pb, Xn, Yn, dt = learned.problem(128, 8, 5, seed=31337, rtol=1e-10, precision=prec)
+        for attach in (False, True):
+            ctx = gdg.Context(pb)
+            if attach:
+                ctx.mlp_attach(net)
+            u = torch.tensor(inputs.gaussian_pulse(Xn, Yn, 0.5, 0.5, 0.05).ravel(), device="cuda")
+            v = torch.zeros_like(u)
+            ctx.step(u, v, 0.0, dt, 8)
+            ctx.step_stats()
+            ms = _timed_ms(lambda: ctx.step(u, v, 0.0, dt, steps))
+            su, sv = ctx.step_stats()
+            out[name + ("_learned" if attach else "_plain")] = {
+                "dof_steps_per_s": 128 * 128 * 81 * steps / (ms / 1e3), "ms_per_step": ms / steps,
+                "pcg_u_mean_iters": su["mean_iters"], "pcg_u_max_iters": su["max_iters"],
+                "guess_fallbacks": su["fell_back"], "guessed": su["guessed"]}
+            ctx.close()
+    return out
+
+
 def run_gdg(args):
     import numpy as np
     import torch
@@ -274,6 +405,14 @@ def run_gdg(args):
     line = None
     if rank == 0:
         cpu = cpu_baseline() if (world == 1 and not args.no_cpu_baseline) else None
+        forms = {}
+        if not args.no_forms and world == 1:
+            for key, fn in (("variable_mapped_128", forms_variable), ("batched_48", forms_batched),
+                            ("learned_guess", forms_learned)):
+                try:
+                    forms[key] = fn()
+                except Exception as exc:    # report, do not lose the headline line
+                    forms[key] = {"error": repr(exc)}
         line = {
             "metric": "DOF-steps/s", "value": value, "unit": "DOF-steps/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
@@ -296,6 +435,7 @@ def run_gdg(args):
             "accuracy": {"T": nT * dt, "l2_error_vs_interpolant": l2},
             "wall_s": wall1 - wall0,
             "cpu_baseline": cpu,
+            "forms": forms,
         }
         print(json.dumps(line))
     ctx.close()
@@ -312,6 +452,8 @@ def main():
     ap.add_argument("--impl", choices=["gdg", "reference"], default="gdg")
     ap.add_argument("--rk-steps", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the extra forms (variable/mapped, batched, learned) after the headline")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -317,7 +317,14 @@ long long gdg_batch_state_len(const gdg_batch *b, int i);
 int gdg_batch_step(gdg_batch *b, double *const *u, double *const *v, const double *dt, int nsteps,
                    void *stream);
 
-/* Launch shape chosen by the tuner (zeros before the first gdg_batch_step). */
+/*
+ * Launch shapes chosen by the tuner (zeros before the first gdg_batch_step;
+ * any output pointer may be NULL): threads_per_block and tile_elements of
+ * the modal (constant-coefficient) launch, tile_elements x (N+1) threads,
+ * 0 when the batch has no such problem; blocks_per_sm of the element-PCG
+ * launch (its blocks have one thread per element node, rounded up to a
+ * warp), 0 when the batch has no variable-coefficient problem.
+ */
 int gdg_batch_tuning(const gdg_batch *b, int *threads_per_block, int *blocks_per_sm, int *tile_elements);
 
 /* PCG statistics of problem i since the previous call, as gdg_step_stats. */

@@ -1,18 +1,20 @@
 // Batched launch of many independent 2-D problems (a pattern layered on the
 // method; the paper advances one mesh at a time).
 //
-// Every RK4 stage of all problems of a batch is one persistent kernel: a
-// grid of (SMs x resident blocks) CTAs pulls work items from a queue -- first
-// the elements of the variable-coefficient problems (element PCG, the
-// expensive items), then tiles of elements of the constant-coefficient
-// problems (modal route) -- so the long items start first and the short ones
-// fill the tail.  The stage bodies are the per-problem kernels' own
-// (stage2p_body, var_stage_body), so a batched step computes exactly what the
-// problem's own gdg_step computes.  A call's launches are captured once in a
-// CUDA graph (per-problem dt lives in device descriptors, so the graph does
-// not depend on it).  The launch shape -- threads per block (which also sets
-// the modal tile, threads / (N+1) elements) and resident blocks per SM -- is
-// picked on the first step by timing every candidate on the batch's data.
+// Every RK4 stage of all problems of a batch is two persistent kernels that
+// run side by side (two branches of one CUDA graph): one over the elements
+// of the variable-coefficient problems (element PCG; 81+ threads and ~75-115
+// KB of shared memory per element) and one over tiles of elements of the
+// constant-coefficient problems (modal route; a few KB per element).  Each
+// is a grid of (SMs x resident blocks) CTAs pulling items from its own queue,
+// so uneven meshes and degrees balance without per-problem launches and the
+// two kinds of work share the SMs.  The stage bodies are the per-problem
+// kernels' own (stage2p_body, var_stage_body), so a batched step computes
+// exactly what the problem's own gdg_step computes.  A call's launches are
+// captured once in a CUDA graph (per-problem dt lives in device descriptors,
+// so the graph does not depend on it).  The modal tile (elements per block)
+// and the PCG grid size are picked on the first step by timing the
+// candidates on the batch's own data.
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
@@ -36,26 +38,14 @@ struct BatchProb {
 
 constexpr int kMaxBatchThreads = 256;
 
-template <int N1, int STAGE>
-__global__ void __launch_bounds__(kMaxBatchThreads)
-k_batch_stage(const BatchProb *__restrict__ probs, const int2 *__restrict__ items, int n_items,
-              unsigned int *counter) {
-    constexpr int MODE = STAGE == 1 ? M_S1 : (STAGE == 4 ? M_S4 : M_S23);
-    extern __shared__ double smem[];
-    __shared__ int s_item;
-    for (;;) {
-        if (threadIdx.x == 0) s_item = (int)atomicAdd(counter, 1u);
-        __syncthreads();
-        const int it = s_item;
-        __syncthreads();
-        if (it >= n_items) return;
-        const int2 w = items[it];
-        const BatchProb &P = probs[w.x];
-        const StepBuffers &B = P.sb;
-        const double dt = P.dt;
-        double cA, cY;
-        const double *yU, *yV, *trin;
-        double *oU, *oV, *trout;
+// RK4 stage coefficients and buffer roles of stage STAGE (the same table as
+// the per-problem stage launches)
+template <int STAGE>
+struct StageRoles {
+    double cA, cY;
+    const double *yU, *yV, *trin;
+    double *oU, *oV, *trout;
+    __device__ StageRoles(const StepBuffers &B, double dt) {
         if (STAGE == 1) {
             cA = dt / 6.0; cY = 0.5 * dt; yU = B.nU; yV = B.nV; oU = B.xU; oV = B.xV; trin = B.tr0; trout = B.tr1;
         } else if (STAGE == 2) {
@@ -65,13 +55,72 @@ k_batch_stage(const BatchProb *__restrict__ probs, const int2 *__restrict__ item
         } else {
             cA = dt / 6.0; cY = 0.0; yU = B.xU; yV = B.xV; oU = nullptr; oV = nullptr; trin = B.tr1; trout = B.tr0;
         }
-        if (P.kind == 0) {
-            const StageBufs b{yU, yV, B.nU, B.nV, B.aU, B.aV, oU, oV, trin, trout, P.lam2};
-            stage2p_body<N1, MODE>(*P.mp, b, cA, cY, w.y, smem);
-        } else {
-            const VarBufs b{yU, yV, B.nU, B.nV, B.aU, B.aV, oU, oV, trin, trout};
-            var_stage_body<N1, MODE>(P.vp, b, cA, cY, w.y, smem);
+    }
+};
+
+// next work item of the block's queue, broadcast through shared memory
+__device__ __forceinline__ int next_item(unsigned int *counter, int *slot) {
+    if (threadIdx.x == 0) *slot = (int)atomicAdd(counter, 1u);
+    __syncthreads();
+    const int it = *slot;
+    __syncthreads();
+    return it;
+}
+
+// block-wide copy of a parameter struct into shared memory (whole 4-byte words)
+template <typename T>
+__device__ __forceinline__ void copy_to_shared(T *dst, const T *src) {
+    static_assert(sizeof(T) % 4 == 0, "word copy");
+    const unsigned int *s = reinterpret_cast<const unsigned int *>(src);
+    unsigned int *d = reinterpret_cast<unsigned int *>(dst);
+    for (int i = threadIdx.x; i < (int)(sizeof(T) / 4); i += blockDim.x) d[i] = s[i];
+    __syncthreads();
+}
+
+// modal tiles of the constant-coefficient problems
+template <int N1, int STAGE>
+__global__ void __launch_bounds__(kMaxBatchThreads)
+k_batch_modal(const BatchProb *__restrict__ probs, const int2 *__restrict__ items, int n_items,
+              unsigned int *counter) {
+    constexpr int MODE = STAGE == 1 ? M_S1 : (STAGE == 4 ? M_S4 : M_S23);
+    extern __shared__ double smem[];
+    __shared__ int s_item;
+    __shared__ ModalParams s_mp;   // the current problem's parameters (read in every inner loop)
+    int cur = -1;
+    for (int it = next_item(counter, &s_item); it < n_items; it = next_item(counter, &s_item)) {
+        const int2 w = items[it];
+        const BatchProb &P = probs[w.x];
+        if (w.x != cur) {
+            copy_to_shared(&s_mp, P.mp);
+            cur = w.x;
         }
+        const StageRoles<STAGE> r(P.sb, P.dt);
+        const StageBufs b{r.yU, r.yV, P.sb.nU, P.sb.nV, P.sb.aU, P.sb.aV, r.oU, r.oV, r.trin, r.trout, P.lam2};
+        stage2p_body<N1, MODE>(s_mp, b, r.cA, r.cY, w.y, smem);
+        __syncthreads();
+    }
+}
+
+// elements of the variable-coefficient problems (one element PCG per item)
+template <int N1, int STAGE>
+__global__ void __launch_bounds__(nthreads_for(N1 * N1))
+k_batch_var(const BatchProb *__restrict__ probs, const int2 *__restrict__ items, int n_items,
+            unsigned int *counter) {
+    constexpr int MODE = STAGE == 1 ? M_S1 : (STAGE == 4 ? M_S4 : M_S23);
+    extern __shared__ double smem[];
+    __shared__ int s_item;
+    __shared__ VarParams s_vp;
+    int cur = -1;
+    for (int it = next_item(counter, &s_item); it < n_items; it = next_item(counter, &s_item)) {
+        const int2 w = items[it];
+        const BatchProb &P = probs[w.x];
+        if (w.x != cur) {
+            copy_to_shared(&s_vp, &P.vp);
+            cur = w.x;
+        }
+        const StageRoles<STAGE> r(P.sb, P.dt);
+        const VarBufs b{r.yU, r.yV, P.sb.nU, P.sb.nV, P.sb.aU, P.sb.aV, r.oU, r.oV, r.trin, r.trout};
+        var_stage_body<N1, MODE>(s_vp, b, r.cA, r.cY, w.y, smem);
         __syncthreads();
     }
 }
@@ -94,21 +143,27 @@ cudaError_t set_batch_attrs() {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&lim, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     cudaError_t e;
-    if ((e = raise_smem(k_batch_stage<N1, 1>, lim)) != cudaSuccess) return e;
-    if ((e = raise_smem(k_batch_stage<N1, 2>, lim)) != cudaSuccess) return e;
-    if ((e = raise_smem(k_batch_stage<N1, 3>, lim)) != cudaSuccess) return e;
-    return raise_smem(k_batch_stage<N1, 4>, lim);
+    if ((e = raise_smem(k_batch_modal<N1, 1>, lim)) != cudaSuccess) return e;
+    if ((e = raise_smem(k_batch_modal<N1, 2>, lim)) != cudaSuccess) return e;
+    if ((e = raise_smem(k_batch_modal<N1, 3>, lim)) != cudaSuccess) return e;
+    if ((e = raise_smem(k_batch_modal<N1, 4>, lim)) != cudaSuccess) return e;
+    if ((e = raise_smem(k_batch_var<N1, 1>, lim)) != cudaSuccess) return e;
+    if ((e = raise_smem(k_batch_var<N1, 2>, lim)) != cudaSuccess) return e;
+    if ((e = raise_smem(k_batch_var<N1, 3>, lim)) != cudaSuccess) return e;
+    return raise_smem(k_batch_var<N1, 4>, lim);
 }
 
-template <int N1>
+template <int N1, bool VAR>
 void launch_batch_n(int stage, int grid, int threads, size_t smem, const BatchProb *probs, const int2 *items,
                     int n_items, unsigned int *counter, cudaStream_t s) {
+#define GDG_BK(st) (VAR ? k_batch_var<N1, st> : k_batch_modal<N1, st>)
     switch (stage) {
-    case 1: k_batch_stage<N1, 1><<<grid, threads, smem, s>>>(probs, items, n_items, counter); break;
-    case 2: k_batch_stage<N1, 2><<<grid, threads, smem, s>>>(probs, items, n_items, counter); break;
-    case 3: k_batch_stage<N1, 3><<<grid, threads, smem, s>>>(probs, items, n_items, counter); break;
-    default: k_batch_stage<N1, 4><<<grid, threads, smem, s>>>(probs, items, n_items, counter); break;
+    case 1: GDG_BK(1)<<<grid, threads, smem, s>>>(probs, items, n_items, counter); break;
+    case 2: GDG_BK(2)<<<grid, threads, smem, s>>>(probs, items, n_items, counter); break;
+    case 3: GDG_BK(3)<<<grid, threads, smem, s>>>(probs, items, n_items, counter); break;
+    default: GDG_BK(4)<<<grid, threads, smem, s>>>(probs, items, n_items, counter); break;
     }
+#undef GDG_BK
 }
 
 }  // namespace
@@ -118,13 +173,15 @@ struct gdg_batch {
     int count = 0, n1 = 0, sms = 152;
     BatchProb *d_probs = nullptr;
     ModalParams *d_mps = nullptr;
-    int2 *d_items = nullptr;
-    int n_items = 0, items_cap = 0, item_tile = -1;
-    unsigned int *d_counters = nullptr;
-    static constexpr int kCounters = 64;
+    int2 *d_var_items = nullptr, *d_mod_items = nullptr;
+    int n_var = 0, n_mod = 0, mod_cap = 0, mod_tile = -1;
+    unsigned int *d_counters = nullptr;   // per step: [stage 0..3][kind 0 var, 1 modal]
     size_t var_smem = 0;
-    int threads = 0, bpsm = 0;   // tuned launch shape (0: not tuned yet)
-    cudaStream_t cap = nullptr;
+    int var_threads = 0, var_grid = 0;    // PCG launch
+    int mod_threads = 0, mod_grid = 0;    // modal launch (tile = mod_threads / n1)
+    bool tuned = false;
+    cudaStream_t cap = nullptr, side = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
     cudaGraphExec_t exec = nullptr;
     int graph_steps = 0;
     std::vector<BatchProb> h_probs;
@@ -139,96 +196,144 @@ int berr(gdg_batch *b, int st, const std::string &m) {
     return st;
 }
 
-size_t batch_smem(const gdg_batch *b, int threads) {
-    const int n1 = b->n1, tile = threads / n1;
-    size_t sm = (size_t)tile * (4 * n1 + 2 * n1 * (n1 + 1)) * sizeof(double);   // modal tile
-    return std::max(sm, b->var_smem);
-}
+size_t modal_smem(int n1, int tile) { return (size_t)tile * (4 * n1 + 2 * n1 * (n1 + 1)) * sizeof(double); }
 
-// work items: every element of the PCG problems, then tiles of `tile` elements
-// of the modal problems
-int build_items(gdg_batch *b, int tile) {
-    if (tile == b->item_tile) return GDG_OK;
-    std::vector<int2> items;
-    for (int i = 0; i < b->count; ++i)
-        if (b->h_probs[i].kind == 1)
-            for (int e = 0; e < b->ctx[i]->ne; ++e) items.push_back(make_int2(i, e));
-    for (int i = 0; i < b->count; ++i)
-        if (b->h_probs[i].kind == 0)
-            for (int t = 0; t * tile < b->ctx[i]->ne; ++t) items.push_back(make_int2(i, t));
-    if ((int)items.size() > b->items_cap) {
-        cudaFree(b->d_items);
-        b->d_items = nullptr;
-        if (cudaMalloc((void **)&b->d_items, items.size() * sizeof(int2)) != cudaSuccess)
+int upload_items(gdg_batch *b, const std::vector<int2> &items, int2 **dst, int *cap) {
+    if ((int)items.size() > *cap) {
+        cudaFree(*dst);
+        *dst = nullptr;
+        if (cudaMalloc((void **)dst, std::max<size_t>(1, items.size()) * sizeof(int2)) != cudaSuccess)
             return berr(b, GDG_ENOMEM, "items");
-        b->items_cap = (int)items.size();
+        *cap = (int)items.size();
     }
-    if (cudaMemcpy(b->d_items, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess)
+    if (!items.empty() &&
+        cudaMemcpy(*dst, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess)
         return berr(b, GDG_ECUDA, "items upload");
-    b->n_items = (int)items.size();
-    b->item_tile = tile;
     return GDG_OK;
 }
 
-void launch_stage(gdg_batch *b, int stage, int counter, cudaStream_t s) {
-    const int grid = b->sms * b->bpsm;
-    const size_t smem = batch_smem(b, b->threads);
+// modal work items: tiles of `tile` elements of the constant-coefficient problems
+int build_modal_items(gdg_batch *b, int tile) {
+    if (tile == b->mod_tile) return GDG_OK;
+    std::vector<int2> items;
+    for (int i = 0; i < b->count; ++i)
+        if (b->h_probs[i].kind == 0)
+            for (int t = 0; t * tile < b->ctx[i]->ne; ++t) items.push_back(make_int2(i, t));
+    int st = upload_items(b, items, &b->d_mod_items, &b->mod_cap);
+    if (st) return st;
+    b->n_mod = (int)items.size();
+    b->mod_tile = tile;
+    return GDG_OK;
+}
+
+template <typename K>
+int resident_blocks(K kernel, int threads, size_t smem) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, smem) != cudaSuccess) return 1;
+    return std::max(1, n);
+}
+
+int max_resident(const gdg_batch *b, bool var, int threads, size_t smem) {
     switch (b->n1) {
-#define X(n) case n: launch_batch_n<n>(stage, grid, b->threads, smem, b->d_probs, b->d_items, b->n_items, b->d_counters + counter, s); break;
+#define X(n) case n: return var ? resident_blocks(k_batch_var<n, 2>, threads, smem) \
+                                : resident_blocks(k_batch_modal<n, 2>, threads, smem);
+        GDG_BATCH_CASES(X)
+#undef X
+    }
+    return 1;
+}
+
+// kind 0: PCG elements; kind 1: modal tiles
+void launch_kind(gdg_batch *b, int kind, int stage, unsigned int *counter, cudaStream_t s) {
+    const bool var = kind == 0;
+    const int n = var ? b->n_var : b->n_mod;
+    if (!n) return;
+    const int threads = var ? b->var_threads : b->mod_threads, grid = var ? b->var_grid : b->mod_grid;
+    const size_t smem = var ? b->var_smem : modal_smem(b->n1, b->mod_threads / b->n1);
+    const int2 *items = var ? b->d_var_items : b->d_mod_items;
+    switch (b->n1) {
+#define X(n1_)                                                                                          \
+    case n1_:                                                                                          \
+        if (var) launch_batch_n<n1_, true>(stage, grid, threads, smem, b->d_probs, items, n, counter, s);  \
+        else launch_batch_n<n1_, false>(stage, grid, threads, smem, b->d_probs, items, n, counter, s);     \
+        break;
         GDG_BATCH_CASES(X)
 #undef X
     }
 }
 
+// one RK4 step: reset the 8 queue counters, then per stage the two launches
+// on two streams, joined before the next stage
 void enqueue_steps(gdg_batch *b, int nsteps, cudaStream_t s) {
     for (int i = 0; i < nsteps; ++i) {
-        cudaMemsetAsync(b->d_counters, 0, 4 * sizeof(unsigned int), s);
-        for (int st = 1; st <= 4; ++st) launch_stage(b, st, st - 1, s);
+        cudaMemsetAsync(b->d_counters, 0, 8 * sizeof(unsigned int), s);
+        for (int st = 1; st <= 4; ++st) {
+            cudaEventRecord(b->fork, s);
+            cudaStreamWaitEvent(b->side, b->fork, 0);
+            launch_kind(b, 0, st, b->d_counters + 2 * (st - 1), s);
+            launch_kind(b, 1, st, b->d_counters + 2 * (st - 1) + 1, b->side);
+            cudaEventRecord(b->join, b->side);
+            cudaStreamWaitEvent(s, b->join, 0);
+        }
     }
 }
 
-// time every launch shape on the batch's own stage-1 work and keep the fastest
+float time_launch(gdg_batch *b, int kind, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
+    float ms = 0.f;
+    for (int rep = 0; rep < 2; ++rep) {
+        cudaMemsetAsync(b->d_counters, 0, 8 * sizeof(unsigned int), s);
+        cudaEventRecord(e0, s);
+        launch_kind(b, kind, 1, b->d_counters + kind, s);
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        cudaEventElapsedTime(&ms, e0, e1);
+    }
+    return cudaGetLastError() == cudaSuccess ? ms : 1e30f;
+}
+
+// Time the candidates on the batch's own stage-1 work (stage 1 reads y_n and
+// its traces and writes only buffers that the real step rewrites).
 int autotune(gdg_batch *b, cudaStream_t s) {
-    int dev = 0, lim = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&lim, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    int smem_sm = 0;
-    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    float best = 1e30f;
-    int best_t = 0, best_b = 0;
-    const int cand_threads[] = {96, 128, 192, 256};
-    for (int threads : cand_threads) {
-        if (threads < ((b->n1 * b->n1 + 31) / 32) * 32) continue;
-        const size_t sm = batch_smem(b, threads);
-        if (sm > (size_t)lim) continue;
-        int st = build_items(b, threads / b->n1);
-        if (st) return st;
-        const int max_b = std::max(1, std::min(8, (int)(smem_sm / (sm + 1024))));
-        for (int bpsm = 1; bpsm <= max_b; ++bpsm) {
-            b->threads = threads;
-            b->bpsm = bpsm;
-            float ms = 0.f;
-            for (int rep = 0; rep < 2; ++rep) {
-                cudaMemsetAsync(b->d_counters, 0, sizeof(unsigned int), s);
-                cudaEventRecord(e0, s);
-                launch_stage(b, 1, 0, s);
-                cudaEventRecord(e1, s);
-                cudaEventSynchronize(e1);
-                cudaEventElapsedTime(&ms, e0, e1);
-            }
-            if (cudaGetLastError() != cudaSuccess) continue;
-            if (ms < best) { best = ms; best_t = threads; best_b = bpsm; }
+    int st = GDG_OK;
+    if (b->n_var) {   // PCG grid: resident blocks per SM from 1 to the occupancy limit
+        const int maxr = max_resident(b, true, b->var_threads, b->var_smem);
+        float best = 1e30f;
+        int best_g = b->sms * maxr;
+        for (int r = 1; r <= maxr; ++r) {
+            b->var_grid = b->sms * r;
+            const float ms = time_launch(b, 0, s, e0, e1);
+            if (ms < best) { best = ms; best_g = b->var_grid; }
+        }
+        b->var_grid = best_g;
+    }
+    bool any_modal = false;
+    for (const BatchProb &P : b->h_probs) any_modal |= P.kind == 0;
+    if (any_modal) {  // modal tile: elements per block
+        float best = 1e30f;
+        int best_t = 0;
+        for (int tile : {4, 7, 10, 14, 21, 28}) {
+            const int threads = tile * b->n1;
+            if (threads > kMaxBatchThreads) continue;
+            if ((st = build_modal_items(b, tile))) break;
+            b->mod_threads = threads;
+            b->mod_grid = b->sms * max_resident(b, false, threads, modal_smem(b->n1, tile));
+            const float ms = time_launch(b, 1, s, e0, e1);
+            if (ms < best) { best = ms; best_t = tile; }
+        }
+        if (!st && best_t) {
+            st = build_modal_items(b, best_t);
+            b->mod_threads = best_t * b->n1;
+            b->mod_grid = b->sms * max_resident(b, false, b->mod_threads, modal_smem(b->n1, best_t));
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (!best_t) return berr(b, GDG_ECUDA, "no launch shape ran");
-    b->threads = best_t;
-    b->bpsm = best_b;
-    return build_items(b, best_t / b->n1);
+    if (st) return st;
+    b->tuned = true;
+    return GDG_OK;
 }
 
 }  // namespace
@@ -238,9 +343,13 @@ extern "C" int gdg_batch_destroy(gdg_batch *b) {
     cudaDeviceSynchronize();
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->cap) cudaStreamDestroy(b->cap);
+    if (b->side) cudaStreamDestroy(b->side);
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->join) cudaEventDestroy(b->join);
     cudaFree(b->d_probs);
     cudaFree(b->d_mps);
-    cudaFree(b->d_items);
+    cudaFree(b->d_var_items);
+    cudaFree(b->d_mod_items);
     cudaFree(b->d_counters);
     for (gdg_ctx *c : b->ctx) gdg_destroy(c);
     delete b;
@@ -266,6 +375,7 @@ extern "C" int gdg_batch_create(const gdg_problem *pbs, int count, gdg_batch **o
     b->ctx.assign(count, nullptr);
     b->h_probs.resize(count);
     std::vector<ModalParams> mps(count);
+    std::vector<int2> var_items;
     for (int i = 0; i < count; ++i) {
         if ((st = gdg_create(&pbs[i], &b->ctx[i]))) { gdg_batch_destroy(b); return st; }
         gdg_ctx *c = b->ctx[i];
@@ -282,14 +392,19 @@ extern "C" int gdg_batch_create(const gdg_problem *pbs, int count, gdg_batch **o
             P.vp = c->var->vp;
             P.sb = gdg_var_buffers(c);
             b->var_smem = std::max(b->var_smem, c->var->smem_stage);
+            for (int e = 0; e < c->ne; ++e) var_items.push_back(make_int2(i, e));
         }
     }
+    int cap = 0;
     if (cudaMalloc((void **)&b->d_mps, count * sizeof(ModalParams)) != cudaSuccess ||
         cudaMalloc((void **)&b->d_probs, count * sizeof(BatchProb)) != cudaSuccess ||
-        cudaMalloc((void **)&b->d_counters, gdg_batch::kCounters * sizeof(unsigned int)) != cudaSuccess) {
+        cudaMalloc((void **)&b->d_counters, 8 * sizeof(unsigned int)) != cudaSuccess ||
+        upload_items(b, var_items, &b->d_var_items, &cap)) {
         gdg_batch_destroy(b);
         return GDG_ENOMEM;
     }
+    b->n_var = (int)var_items.size();
+    b->var_threads = nthreads_for(b->n1 * b->n1);
     for (int i = 0; i < count; ++i)
         if (b->h_probs[i].kind == 0) b->h_probs[i].mp = b->d_mps + i;
     cudaMemcpy(b->d_mps, mps.data(), count * sizeof(ModalParams), cudaMemcpyHostToDevice);
@@ -304,7 +419,10 @@ extern "C" int gdg_batch_create(const gdg_problem *pbs, int count, gdg_batch **o
         gdg_batch_destroy(b);
         return berr(nullptr, GDG_ECUDA, std::string("kernel attributes: ") + cudaGetErrorString(ae));
     }
-    if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) {
+    if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming) != cudaSuccess) {
         gdg_batch_destroy(b);
         return GDG_ECUDA;
     }
@@ -335,10 +453,10 @@ extern "C" int gdg_batch_step(gdg_batch *b, double *const *u, double *const *v, 
     for (int i = 0; i < b->count; ++i) {
         gdg_ctx *c = b->ctx[i];
         st = c->pb.coef == GDG_COEF_CONST ? gdg_const_enter(c, u[i], v[i], s) : gdg_var_enter(c, u[i], v[i], s);
-        if (st) return berr(b, st, "enter");
+        if (st) return berr(b, st, "enter: " + c->err);
     }
-    if (!b->threads && (st = autotune(b, s))) return st;
-    // graph of G steps (4 launches and one counter reset each), replayed
+    if (!b->tuned && (st = autotune(b, s))) return st;
+    // graph of G steps, replayed
     const int G = 4;
     if (nsteps >= G) {
         if (!b->exec || b->graph_steps != G) {
@@ -367,9 +485,10 @@ extern "C" int gdg_batch_step(gdg_batch *b, double *const *u, double *const *v, 
 
 extern "C" int gdg_batch_tuning(const gdg_batch *b, int *threads_per_block, int *blocks_per_sm, int *tile_elements) {
     if (!b) return GDG_EINVAL;
-    if (threads_per_block) *threads_per_block = b->threads;
-    if (blocks_per_sm) *blocks_per_sm = b->bpsm;
-    if (tile_elements) *tile_elements = b->threads ? b->threads / b->n1 : 0;
+    const bool mod = b->tuned && b->n_mod > 0, var = b->tuned && b->n_var > 0;
+    if (threads_per_block) *threads_per_block = mod ? b->mod_threads : 0;
+    if (blocks_per_sm) *blocks_per_sm = var && b->sms ? b->var_grid / b->sms : 0;
+    if (tile_elements) *tile_elements = mod ? b->mod_tile : 0;
     return GDG_OK;
 }
 

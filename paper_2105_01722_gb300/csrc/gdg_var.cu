@@ -253,6 +253,16 @@ int gdg_var_setup(gdg_ctx *ctx) {
             (st = gdg_cuda_check(ctx, cudaMemcpy(D->d_c2feat, feat.data(), nd * sizeof(float), cudaMemcpyHostToDevice), "upload features")))
             return st;
     }
+    if (P.mixed) {   // FP32 copies of the element matrices for the inner solves
+        const size_t nm = nd * NA;
+        if ((st = gdg_cuda_check(ctx, cudaMalloc((void **)&D->d_S32, nm * sizeof(float)), "alloc S32")) ||
+            (st = gdg_cuda_check(ctx, cudaMalloc((void **)&D->d_M32, nm * sizeof(float)), "alloc M32")))
+            return st;
+        k_to_f32<<<1216, 256>>>(nm, D->d_S, D->d_S32);
+        k_to_f32<<<1216, 256>>>(nm, D->d_M, D->d_M32);
+        P.S32 = D->d_S32;
+        P.M32 = D->d_M32;
+    }
     st = gdg_cuda_check(ctx, cudaDeviceSynchronize(), "assembly");
     cudaFree(D->d_nodes);
     D->d_nodes = nullptr;
@@ -269,7 +279,7 @@ int gdg_var_setup(gdg_ctx *ctx) {
 void gdg_var_free(gdg_ctx *ctx) {
     VarData *D = ctx->var;
     if (!D) return;
-    cudaFree(D->d_S); cudaFree(D->d_M); cudaFree(D->d_w); cudaFree(D->d_pre); cudaFree(D->d_face);
+    cudaFree(D->d_S); cudaFree(D->d_M); cudaFree(D->d_S32); cudaFree(D->d_M32); cudaFree(D->d_w); cudaFree(D->d_pre); cudaFree(D->d_face);
     cudaFree(D->d_tab); cudaFree(D->d_nodes); cudaFree(D->d_state); cudaFree(D->d_tr);
     cudaFree(D->d_c2feat); cudaFree(D->d_wbf16); cudaFree(D->d_mlp);
     cudaFree(D->d_ru); cudaFree(D->d_rv); cudaFree(D->d_x0u);

@@ -16,6 +16,7 @@ struct VarParams {
     int maxit, precond;   // GDG_PC_*
     const double *tab;    // B[Q][N1], D[Q][N1], wq[Q], dphiL[N1], dphiR[N1], Psi[N1][N1], lam[N1]
     const double *S, *M, *w, *pre, *face;
+    const float *S32, *M32;      // FP32 copies of S and M (mixed precision only)
     unsigned long long *stats;   // [0] sum it_u, [1] sum it_v, [2] max it_u, [3] max it_v,
                                  // [4] unconverged u, [5] unconverged v, [6] element solves,
                                  // [7] sum sweeps u, [8] sum sweeps v, [9] max sweeps u, [10] max sweeps v
@@ -27,6 +28,7 @@ struct VarParams {
 struct VarData {
     int nq = 0, Q = 0, NA = 0;
     double *d_S = nullptr, *d_M = nullptr, *d_w = nullptr, *d_pre = nullptr, *d_face = nullptr;
+    float *d_S32 = nullptr, *d_M32 = nullptr;
     double *d_tab = nullptr, *d_nodes = nullptr;
     double *d_state = nullptr, *d_tr = nullptr;
     long long tr_len = 0;
@@ -288,14 +290,40 @@ struct SolveScratch32 {
     float *rhs, *x, *res, *z, *p, *Ap, *t1, *t2;
 };
 
+// FP64 step: when `step64` is given (z, t1, t2, Ps, d of the FP64
+// preconditioner) and x0 = 0, the solve first takes the FP64 preconditioned
+// steepest-descent step x = alpha P^-1 b (the first FP64 PCG iterate); where
+// the frozen-coefficient preconditioner is exact (the mass matrix of an affine
+// element) that step already meets the tolerance and no FP32 sweep runs.
+struct Step64 {
+    double *z, *t1, *t2;
+    const double *Ps, *d;
+};
+
 template <int N1, bool W>
 __device__ int refine(const double *A, const double *w, const double *b, double *x, double *r, double *Ap,
                       const SolveScratch32 &f, double *red, double rtol, int maxsweep, float irtol,
                       int imaxit, bool none, bool x0_zero, int *inner, double *relres,
-                      bool fallback = false, int *fell = nullptr) {
+                      bool fallback = false, int *fell = nullptr, const Step64 *step64 = nullptr) {
     constexpr int NA = N1 * N1;
     const int t = threadIdx.x;
-    if (x0_zero) {
+    if (x0_zero && step64) {
+        precondition<N1>(b, step64->z, step64->Ps, step64->d, step64->t1, step64->t2, none);
+        matvec<NA, double>(A, step64->z, Ap);
+        if (W) {
+            const double wz = block_dot<NA, double>(w, step64->z, red);
+            if (t < NA) Ap[t] += w[t] * wz;
+            __syncthreads();
+        }
+        const double bz = block_dot<NA, double>(b, step64->z, red);
+        const double zAz = block_dot<NA, double>(step64->z, Ap, red);
+        const double alpha = zAz > 0.0 ? bz / zAz : 0.0;
+        if (t < NA) {
+            x[t] = alpha * step64->z[t];
+            r[t] = b[t] - alpha * Ap[t];
+        }
+        __syncthreads();
+    } else if (x0_zero) {
         if (t < NA) { x[t] = 0.0; r[t] = b[t]; }
         __syncthreads();
     } else {
@@ -331,12 +359,13 @@ __device__ int refine(const double *A, const double *w, const double *b, double 
     return sweeps;
 }
 
-// FP32 copies of an element matrix and of the preconditioner data
+// FP32 element matrix (the copy made at setup) and FP32 copies of the
+// preconditioner data
 template <int N1>
-__device__ void to_fp32(const double *A, float *A32, const double *Ps, float *Ps32, const double *d, float *d32,
+__device__ void to_fp32(const float *A32g, float *A32, const double *Ps, float *Ps32, const double *d, float *d32,
                         const double *w, float *w32) {
     constexpr int NA = N1 * N1;
-    for (int i = threadIdx.x; i < NA * NA; i += blockDim.x) A32[i] = (float)A[i];
+    for (int i = threadIdx.x; i < NA * NA; i += blockDim.x) A32[i] = A32g[i];
     for (int i = threadIdx.x; i < N1 * N1; i += blockDim.x) Ps32[i] = (float)Ps[i];
     for (int i = threadIdx.x; i < NA; i += blockDim.x) {
         d32[i] = (float)d[i];
@@ -729,7 +758,7 @@ __device__ __forceinline__ void var_stage_body(const VarParams &P, const VarBufs
     int it_u, it_v, sw_u = 0, sw_v = 0, fell = 0;
     bool bad_u, bad_v;
     if (P.mixed) {
-        to_fp32<N1>(s.A, s.A32, T.Ps, s.Ps32, s.dS, s.dS32, s.w, s.w32);
+        to_fp32<N1>(P.S32 + (size_t)e * NA * NA, s.A32, T.Ps, s.Ps32, s.dS, s.dS32, s.w, s.w32);
         sw_u = refine<N1, true>(s.A, s.w, s.ru, s.x, s.r, s.Ap, s.scratch32(true), s.red, P.rtol, P.refine_max,
                                 P.refine_rtol, P.maxit, none, !guess, &it_u, &rel_u, guess, &fell);
         bad_u = sw_u >= P.refine_max && rel_u > P.rtol;
@@ -742,9 +771,11 @@ __device__ __forceinline__ void var_stage_body(const VarParams &P, const VarBufs
     __syncthreads();
     load_matrix<N1>(s.A, P.M + (size_t)e * NA * NA);
     if (P.mixed) {
-        to_fp32<N1>(s.A, s.A32, T.Ps, s.Ps32, s.dM, s.dM32, nullptr, nullptr);
+        to_fp32<N1>(P.M32 + (size_t)e * NA * NA, s.A32, T.Ps, s.Ps32, s.dM, s.dM32, nullptr, nullptr);
+        const Step64 st64{s.z, s.t1, s.t2, T.Ps, s.dM};
         sw_v = refine<N1, false>(s.A, s.w, s.rv, s.x, s.r, s.Ap, s.scratch32(false), s.red, P.rtol,
-                                 P.refine_max, P.refine_rtol, P.maxit, none, true, &it_v, &rel_v);
+                                 P.refine_max, P.refine_rtol, P.maxit, none, true, &it_v, &rel_v, false, nullptr,
+                                 &st64);
         bad_v = sw_v >= P.refine_max && rel_v > P.rtol;
     } else {
         it_v = pcg<N1, false>(s.A, s.w, s.rv, s.x, s.r, s.z, s.p, s.Ap, T.Ps, s.dM, s.t1, s.t2, s.red, P.rtol,
@@ -829,8 +860,8 @@ k_var_pcg(VarParams P, int which, const double *bvec, double *xvec, int *iters, 
     double rr;
     int it, sw = 0;
     if (P.mixed) {
-        to_fp32<N1>(s.A, s.A32, T.Ps, s.Ps32, which ? s.dS : s.dM, which ? s.dS32 : s.dM32, which ? s.w : nullptr,
-                    s.w32);
+        to_fp32<N1>((which ? P.S32 : P.M32) + (size_t)e * NA * NA, s.A32, T.Ps, s.Ps32, which ? s.dS : s.dM,
+                    which ? s.dS32 : s.dM32, which ? s.w : nullptr, s.w32);
         if (which)
             sw = refine<N1, true>(s.A, s.w, s.ru, s.x, s.r, s.Ap, s.scratch32(true), s.red, P.rtol, P.refine_max,
                                   P.refine_rtol, P.maxit, none, false, &it, &rr);
@@ -850,6 +881,12 @@ k_var_pcg(VarParams P, int which, const double *bvec, double *xvec, int *iters, 
         rel[e] = rr;
         if (sweeps) sweeps[e] = sw;
     }
+}
+
+// FP32 copy (round to nearest) of an FP64 array
+__global__ void k_to_f32(size_t n, const double *__restrict__ src, float *__restrict__ dst) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        dst[i] = (float)src[i];
 }
 
 // per-element V^T M V + U^T S U

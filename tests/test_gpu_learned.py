@@ -1,0 +1,180 @@
+"""Learned u_t guess: the library's BF16 MLP kernels against the FP64 oracle
+MLP (forward, loss, gradients), residual and training-row kernels against
+the oracle, PCG from the guess (and its fallback) against plain PCG, and a
+short end-to-end training run that must cut the u_t PCG iterations."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import dg_var as dv, mlp as omlp
+from paper_2105_01722_gb300 import gdg, inputs, learned
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    gdg.lib()
+
+
+def _oracle_params(net):
+    """The GPU net's parameters as the oracle sees them: BF16-rounded weights,
+    FP32 biases, in the oracle's (W, b) layout."""
+    p = net.params.cpu().numpy().astype(np.float64)
+    shapes = [(64, 162), (64,), (64, 64), (64,), (81, 64), (81,)]
+    out, k = [], 0
+    for i, sh in enumerate(shapes):
+        n = int(np.prod(sh))
+        a = p[k:k + n].reshape(sh)
+        out.append(omlp.bf16_round(a) if i % 2 == 0 else a)
+        k += n
+    return out
+
+
+def _flat(grads):
+    return np.concatenate([g.ravel() for g in grads])
+
+
+def test_forward_and_gradients_match_oracle():
+    rng = np.random.default_rng(3)
+    params = learned.glorot_params(11)
+    params[64 * 162:64 * 162 + 64] = rng.normal(0, 0.1, 64)      # nonzero b1
+    params[-81:] = rng.normal(0, 0.1, 81)                          # nonzero b3
+    net = gdg.Mlp(params)
+    B = 70                                        # 3 CTAs of 32, ragged tail
+    X = rng.normal(0, 1, (B, 162)).astype(np.float32)
+    T = rng.normal(0, 0.5, (B, 81)).astype(np.float32)
+    Xd, Td = torch.tensor(X, device="cuda"), torch.tensor(T, device="cuda")
+    Y = torch.empty(B, 81, dtype=torch.float32, device="cuda")
+    net.forward(Xd, Y)
+    P = _oracle_params(net)
+    ref, _ = omlp.forward(P, X.astype(np.float64))
+    assert np.abs(Y.cpu().numpy() - ref).max() < 2e-5 * np.abs(ref).max()
+    loss = float(net.backward(Xd, Td).item())
+    gref = _flat(omlp.backward(P, X.astype(np.float64), T.astype(np.float64)))
+    lref = omlp.loss(P, X.astype(np.float64), T.astype(np.float64))
+    assert abs(loss - lref) < 1e-5 * lref
+    g = net.grad.cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(g - gref) < 1e-4 * np.linalg.norm(gref)
+    # a subset through the index array gives the subset's gradient
+    idx = torch.tensor(np.array([5, 60, 0, 33, 12], dtype=np.int32), device="cuda")
+    net.backward(Xd, Td, idx)
+    sel = idx.cpu().numpy()
+    gsub = _flat(omlp.backward(P, X[sel].astype(np.float64), T[sel].astype(np.float64)))
+    assert np.linalg.norm(net.grad.cpu().numpy() - gsub) < 1e-4 * np.linalg.norm(gsub)
+
+
+def test_adam_step_and_bf16_refresh():
+    params = learned.glorot_params(2)
+    net = gdg.Mlp(params)
+    g = np.random.default_rng(1).normal(0, 1e-2, params.size).astype(np.float32)
+    net.grad.copy_(torch.tensor(g, device="cuda"))
+    net.adam(1e-3)
+    # first Adam step: update = lr * g / (|g| + eps') with bias-corrected moments
+    m = 0.1 * g / (1 - 0.9)
+    v = 0.001 * g.astype(np.float64) ** 2 / (1 - 0.999)
+    expect = params - 1e-3 * m / (np.sqrt(v) + 1e-8)
+    assert np.abs(net.params.cpu().numpy() - expect).max() < 1e-6
+    w = net.wbf16.cpu().numpy().view(np.uint16).astype(np.uint32) << 16
+    wf = w.view(np.float32)
+    p = net.params.cpu().numpy()
+    wts = np.concatenate([p[:64 * 162], p[64 * 162 + 64:64 * 162 + 64 + 4096],
+                          p[64 * 162 + 128 + 4096:64 * 162 + 128 + 4096 + 5184]])
+    assert np.array_equal(wf, omlp.bf16_round(wts).astype(np.float32))
+
+
+def _var_pair(n=4, p=5, seed=3, rtol=1e-12):
+    pb, X, Y, dt = learned.problem(n, 8, p, seed, rtol=rtol, maxit=400)
+    C2 = inputs.smooth_random_c2(X, Y, seed)
+    vp = dv.VarProblem(n=(n, n), N=8, p=p, X=X, Y=Y, C2=C2)
+    return vp, gdg.Context(pb), C2
+
+
+def test_residuals_and_rows_match_oracle():
+    vp, ctx, C2 = _var_pair()
+    ops = dv.assemble(vp)
+    ne = 16
+    U = inputs.random_state((ne, 81), 5)
+    V = inputs.random_state((ne, 81), 6)
+    ru, rv = dv.residuals(vp, ops, U, V)
+    u, v = torch.tensor(U.ravel(), device="cuda"), torch.tensor(V.ravel(), device="cuda")
+    gru, grv = torch.empty_like(u), torch.empty_like(u)
+    ctx.residuals(u, v, gru, grv)
+    a = np.concatenate([gru.cpu().numpy(), grv.cpu().numpy()])
+    b = np.concatenate([ru.ravel(), rv.ravel()])
+    assert np.linalg.norm(a - b) < 1e-12 * np.linalg.norm(b)
+    y = torch.tensor(inputs.random_state(ne * 81, 8), device="cuda")
+    Xr = torch.empty(ne * 162, dtype=torch.float32, device="cuda")
+    Tr = torch.empty(ne * 81, dtype=torch.float32, device="cuda")
+    ctx.mlp_rows(gru, y, Xr, Tr)
+    xref, nr = omlp.features(C2.reshape(ne, 81), ru)
+    tref = y.cpu().numpy().reshape(ne, 81) / nr[:, None]
+    assert np.abs(Xr.cpu().numpy().reshape(ne, 162) - xref).max() < 1e-6 * max(1.0, np.abs(xref).max())
+    assert np.abs(Tr.cpu().numpy().reshape(ne, 81) - tref).max() < 1e-6 * np.abs(tref).max()
+    ctx.close()
+
+
+def test_guess_path_matches_plain_and_falls_back():
+    """With a network attached, the converged derivative equals the plain
+    one; a network whose guesses are useless is dropped (fallback) on every
+    element and the result is again the plain one."""
+    vp, ctx, _ = _var_pair(rtol=1e-13)
+    ops = dv.assemble(vp)
+    U = inputs.random_state((16, 81), 9)
+    V = inputs.random_state((16, 81), 10)
+    Ut, Vt = dv.time_derivative(vp, ops, U, V)
+    ref = np.concatenate([Ut.ravel(), Vt.ravel()])
+    u, v = torch.tensor(U.ravel(), device="cuda"), torch.tensor(V.ravel(), device="cuda")
+    for bias in (0.0, 1e4):
+        params = learned.glorot_params(4)
+        params[-81:] = bias
+        ctx.mlp_attach(gdg.Mlp(params))
+        du, dv_ = torch.empty_like(u), torch.empty_like(u)
+        ctx.step_stats()
+        ctx.rhs(u, v, du, dv_)
+        su, _ = ctx.step_stats()
+        a = np.concatenate([du.cpu().numpy(), dv_.cpu().numpy()])
+        assert np.linalg.norm(a - ref) < 1e-9 * np.linalg.norm(ref), bias
+        assert su["guessed"] == 16
+        if bias > 0:
+            assert su["fell_back"] == 16
+    ctx.mlp_detach()
+    ctx.close()
+
+
+def test_training_lowers_loss_and_guess_stays_exact():
+    """A short training run on rows generated by the method lowers the loss
+    and beats the zero guess on held-out rows; with the trained network
+    attached, every u_t solve still meets the FP64 tolerance and the mean
+    iteration count does not grow by more than half an iteration (measured
+    gains are small: the frozen-coefficient preconditioner already reduces
+    the residual about 100x per iteration, so a guess with relative error e
+    saves about log(1/e)/log(100) iterations)."""
+    X, T = learned.generate(4000, n=12, seed0=500)
+    net, hist = learned.train(X[:3500], T[:3500], epochs=12, batch=128, lr=3e-3)
+    assert hist[-1] < 0.5 * hist[0]
+    err = learned.relative_error(net, X[3500:], T[3500:])
+    assert err < 0.95, err          # the zero guess has relative error 1
+    pb, Xn, Yn, dt = learned.problem(12, 8, 5, seed=987, rtol=1e-10)
+    iters, states = [], []
+    for attach in (False, True):
+        ctx = gdg.Context(pb)
+        if attach:
+            ctx.mlp_attach(net)
+        u = torch.tensor(inputs.gaussian_pulse(Xn, Yn, 0.45, 0.55, 0.08).ravel(), device="cuda")
+        v = torch.zeros_like(u)
+        ctx.step(u, v, 0.0, dt, 4)
+        ctx.step_stats()
+        ctx.step(u, v, 0.0, dt, 8)
+        su, _ = ctx.step_stats()
+        assert su["unconverged"] == 0
+        if attach:
+            assert su["guessed"] > 0
+        iters.append(su["mean_iters"])
+        states.append(torch.cat([u, v]).cpu().numpy())
+        ctx.close()
+    assert iters[1] <= iters[0] + 0.5, iters
+    a, b = states
+    assert np.linalg.norm(a - b) <= 1e-8 * np.linalg.norm(b)

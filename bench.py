@@ -54,6 +54,11 @@ def flops_per_stage_launch(w=WORKLOAD):
 # probe measured 1.196 TFLOP/s on this GPU.
 FP64_PEAK_TFLOPS = 152 * 2.070e9 * 4 / 1e12
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one k_stage2p
+# launch of this workload, from one ncu capture (mean over the captured
+# launches; None when the kernel has changed since).
+STAGE_TRAFFIC_BYTES = 13.0e6
+
 
 def _env_rank():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
@@ -110,16 +115,14 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(target_s=15.0):
-    """Time the FP64 oracle (as it stands) on the host cores, single thread,
-    on a bounded sample: a few RK4 steps of the full benchmark mesh."""
-    code = r"""
+_ORACLE_TIMER = r"""
 import json, sys, time
 sys.path.insert(0, %r)
 import numpy as np
 from oracle import dg_const as dc, timeint as ti
 from paper_2105_01722_gb300 import inputs
 w = %r
+nsteps, target_s = %d, %f
 prob = dc.Problem(dim=w["dim"], n=tuple(w["n"]), N=w["N"], p=w["p"], flux=w["flux"])
 ops = dc.operators(prob)
 X, Y = inputs.cartesian_nodes(tuple(w["n"]), w["N"])
@@ -129,49 +132,66 @@ U, V = U.reshape(ne, -1), V.reshape(ne, -1)
 dt = w["cfl"] / (w["n"][0] * w["N"])
 f = lambda t, U, V: dc.time_derivative(prob, U, V, ops)
 t0 = time.perf_counter(); U, V = ti.rk4_step(f, U, V, 0.0, dt); t1 = time.perf_counter()
-steps = max(1, int(%f / max(t1 - t0, 1e-6)))
-t0 = time.perf_counter()
-U, V = ti.integrate(f, U, V, dt, dt, steps)
-t1 = time.perf_counter()
-print(json.dumps({"steps": steps, "seconds": t1 - t0}))
-""" % (ROOT, WORKLOAD, target_s)
+rk = max(1, int(target_s / max(t1 - t0, 1e-6)))
+for k in range(nsteps):
+    t0 = time.perf_counter()
+    U, V = ti.integrate(f, U, V, dt, dt, rk)
+    t1 = time.perf_counter()
+    print(json.dumps({"rk_steps": rk, "seconds": t1 - t0}), flush=True)
+"""
+
+
+def _oracle_steps(nsteps, target_s):
+    """Time the FP64 oracle (as it stands) on the host cores, single thread:
+    `nsteps` samples of about `target_s` seconds, each a number of RK4 steps
+    of the full benchmark mesh.  Returns [(rk_steps, seconds)] or an error."""
+    code = _ORACLE_TIMER % (ROOT, WORKLOAD, nsteps, target_s)
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
     if r.returncode != 0:
-        return {"value": None, "unit": "DOF-steps/s", "cores": 1, "kind": "oracle",
-                "sample": "failed: " + r.stderr.strip().splitlines()[-1] if r.stderr else "failed"}
-    d = json.loads(r.stdout.strip().splitlines()[-1])
-    return {"value": dof() * d["steps"] / d["seconds"], "unit": "DOF-steps/s", "cores": 1,
-            "kind": "oracle",
-            "sample": "%d RK4 steps of the full 64x64 p=5 mesh (%.1f s, numpy FP64, 1 thread)"
-                      % (d["steps"], d["seconds"])}
+        return None, (r.stderr.strip().splitlines() or ["failed"])[-1]
+    rows = [json.loads(x) for x in r.stdout.strip().splitlines() if x.startswith("{")]
+    return [(d["rk_steps"], d["seconds"]) for d in rows], None
+
+
+def cpu_baseline(target_s=15.0):
+    """One bounded sample (about target_s of CPU work) of the oracle."""
+    rows, err = _oracle_steps(1, target_s)
+    if rows is None:
+        return {"value": None, "unit": "DOF-steps/s", "cores": 1, "kind": "oracle", "sample": "failed: " + err}
+    rk, sec = rows[0]
+    return {"value": dof() * rk / sec, "unit": "DOF-steps/s", "cores": 1, "kind": "oracle",
+            "sample": "%d RK4 steps of the full 64x64 p=5 mesh (%.1f s, numpy FP64, 1 thread)" % (rk, sec)}
 
 
 def run_reference(args):
+    """The oracle arm: W + K bounded samples in one process, the K timed."""
     rank, world, _ = _env_rank()
     if rank != 0:
         return 0
-    per = []
-    base = None
-    for _ in range(args.warmup + args.steps):
-        base = cpu_baseline(target_s=max(2.0, 120.0 / (args.steps + args.warmup)))
-        per.append(base)
-    timed = per[args.warmup:]
-    vals = [b["value"] for b in timed if b["value"]]
-    value = statistics.mean(vals) if vals else None
+    total = args.steps + args.warmup
+    rows, err = _oracle_steps(total, max(0.5, 120.0 / total))
+    if rows is None:
+        print(json.dumps({"impl": "reference", "unavailable": "oracle run failed: " + err}))
+        return 0
+    timed = rows[args.warmup:]
+    rk_total = sum(r for r, _ in timed)
+    sec_total = sum(s for _, s in timed)
+    value = dof() * rk_total / sec_total
+    sample = ("%d timed samples of %d RK4 steps each on the full 64x64 p=5 mesh (numpy FP64, 1 thread)"
+              % (len(timed), timed[0][0]))
     line = {"impl": "reference", "metric": "DOF-steps/s", "value": value, "unit": "DOF-steps/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64", "data": "synthetic",
+            "ms_per_step": 1e3 * sec_total / len(timed), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD_NAME, "elements": list(WORKLOAD["n"]), "N": WORKLOAD["N"],
                        "p": WORKLOAD["p"], "dof": dof()},
             "cpu_baseline": {"value": value, "unit": "DOF-steps/s", "cores": 1, "kind": "oracle",
-                             "sample": timed[-1]["sample"] if timed else ""},
+                             "sample": sample},
             "e2e": {"value": value, "unit": "DOF-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
-
 
 
 def _timed_ms(fn):
@@ -423,10 +443,12 @@ def run_gdg(args):
                        "form": "FP64 modal (modified basis)",
                        "l2": "flushed between timed steps (512 MB write; state is 5.3 MB)"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                         "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                         "kernel": "k_stage2 (fused RK stage)", "avg_launch_us": stage_ms * 1e3,
+                         "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                         "traffic": STAGE_TRAFFIC_BYTES,
+                         "kernel": "k_stage2p (fused RK4 stage, modal route)", "avg_launch_us": stage_ms * 1e3,
                          "flops_per_launch": flops_per_stage_launch(),
-                         "peak_source": "FP64 nominal: 152 SM x 2070 MHz x 4 flop/clk"},
+                         "peak_source": "FP64 derived from unit counts and the maximum SM clock: "
+                                        "152 SM x 2070 MHz x 4 flop/clk"},
             "kernels": {k: {"launches": n, "ms": t} for k, (n, t) in prof.items()},
             "gpu_launches": 4 * R * args.steps + 3 * args.steps,
             "e2e": {"value": e2e_val, "unit": "DOF-steps/s", "h2d_bytes_per_step": 2 * dof() * 8,
@@ -447,10 +469,11 @@ def run_gdg(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gdg", "reference"], default="gdg")
-    ap.add_argument("--rk-steps", type=int, default=64)
+    ap.add_argument("--rk-steps", type=int, default=256,
+                    help="RK4 steps per benchmark step (one gdg_step call)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the extra forms (variable/mapped, batched, learned) after the headline")

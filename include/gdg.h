@@ -323,7 +323,8 @@ int gdg_batch_step(gdg_batch *b, double *const *u, double *const *v, const doubl
  * the modal (constant-coefficient) launch, tile_elements x (N+1) threads,
  * 0 when the batch has no such problem; blocks_per_sm of the element-PCG
  * launch (its blocks have one thread per element node, rounded up to a
- * warp), 0 when the batch has no variable-coefficient problem.
+ * warp): the persistent grid's blocks per SM, -1 for a flat grid of one
+ * block per element, 0 when the batch has no variable-coefficient problem.
  */
 int gdg_batch_tuning(const gdg_batch *b, int *threads_per_block, int *blocks_per_sm, int *tile_elements);
 

@@ -101,26 +101,55 @@ k_batch_modal(const BatchProb *__restrict__ probs, const int2 *__restrict__ item
     }
 }
 
-// elements of the variable-coefficient problems (one element PCG per item)
+// elements of the variable-coefficient problems (one element PCG per item).
+// The current problem's parameters and buffer table live in shared memory
+// (kernel parameters would sit in the constant bank; in registers they would
+// crowd the PCG loops).
 template <int N1, int STAGE>
-__global__ void __launch_bounds__(nthreads_for(N1 * N1))
-k_batch_var(const BatchProb *__restrict__ probs, const int2 *__restrict__ items, int n_items,
-            unsigned int *counter) {
+__device__ __forceinline__ void batch_var_item(const BatchProb *__restrict__ probs, int2 w, int &cur,
+                                               VarParams &s_vp, VarBufs &s_b, double *s_c, double *smem) {
     constexpr int MODE = STAGE == 1 ? M_S1 : (STAGE == 4 ? M_S4 : M_S23);
+    if (w.x != cur) {
+        const BatchProb &P = probs[w.x];
+        copy_to_shared(&s_vp, &P.vp);
+        if (threadIdx.x == 0) {
+            const StageRoles<STAGE> r(P.sb, P.dt);
+            s_b = VarBufs{r.yU, r.yV, P.sb.nU, P.sb.nV, P.sb.aU, P.sb.aV, r.oU, r.oV, r.trin, r.trout};
+            s_c[0] = r.cA;
+            s_c[1] = r.cY;
+        }
+        __syncthreads();
+        cur = w.x;
+    }
+    var_stage_body<N1, MODE>(s_vp, s_b, s_c[0], s_c[1], w.y, smem);
+}
+
+// flat grid: block b takes item b
+template <int N1, int STAGE>
+__global__ void __launch_bounds__(nthreads_for(N1 * N1), kVarMinBlocks)
+k_batch_var(const BatchProb *__restrict__ probs, const int2 *__restrict__ items, int n_items, unsigned int *) {
+    extern __shared__ double smem[];
+    __shared__ VarParams s_vp;
+    __shared__ VarBufs s_b;
+    __shared__ double s_c[2];
+    int cur = -1;
+    if ((int)blockIdx.x < n_items)
+        batch_var_item<N1, STAGE>(probs, items[blockIdx.x], cur, s_vp, s_b, s_c, smem);
+}
+
+// persistent grid: blocks pull items from the queue `counter`
+template <int N1, int STAGE>
+__global__ void __launch_bounds__(nthreads_for(N1 * N1), kVarMinBlocks)
+k_batch_var_q(const BatchProb *__restrict__ probs, const int2 *__restrict__ items, int n_items,
+              unsigned int *counter) {
     extern __shared__ double smem[];
     __shared__ int s_item;
     __shared__ VarParams s_vp;
+    __shared__ VarBufs s_b;
+    __shared__ double s_c[2];
     int cur = -1;
     for (int it = next_item(counter, &s_item); it < n_items; it = next_item(counter, &s_item)) {
-        const int2 w = items[it];
-        const BatchProb &P = probs[w.x];
-        if (w.x != cur) {
-            copy_to_shared(&s_vp, &P.vp);
-            cur = w.x;
-        }
-        const StageRoles<STAGE> r(P.sb, P.dt);
-        const VarBufs b{r.yU, r.yV, P.sb.nU, P.sb.nV, P.sb.aU, P.sb.aV, r.oU, r.oV, r.trin, r.trout};
-        var_stage_body<N1, MODE>(s_vp, b, r.cA, r.cY, w.y, smem);
+        batch_var_item<N1, STAGE>(probs, items[it], cur, s_vp, s_b, s_c, smem);
         __syncthreads();
     }
 }
@@ -150,13 +179,17 @@ cudaError_t set_batch_attrs() {
     if ((e = raise_smem(k_batch_var<N1, 1>, lim)) != cudaSuccess) return e;
     if ((e = raise_smem(k_batch_var<N1, 2>, lim)) != cudaSuccess) return e;
     if ((e = raise_smem(k_batch_var<N1, 3>, lim)) != cudaSuccess) return e;
-    return raise_smem(k_batch_var<N1, 4>, lim);
+    if ((e = raise_smem(k_batch_var<N1, 4>, lim)) != cudaSuccess) return e;
+    if ((e = raise_smem(k_batch_var_q<N1, 1>, lim)) != cudaSuccess) return e;
+    if ((e = raise_smem(k_batch_var_q<N1, 2>, lim)) != cudaSuccess) return e;
+    if ((e = raise_smem(k_batch_var_q<N1, 3>, lim)) != cudaSuccess) return e;
+    return raise_smem(k_batch_var_q<N1, 4>, lim);
 }
 
 template <int N1, bool VAR>
 void launch_batch_n(int stage, int grid, int threads, size_t smem, const BatchProb *probs, const int2 *items,
                     int n_items, unsigned int *counter, cudaStream_t s) {
-#define GDG_BK(st) (VAR ? k_batch_var<N1, st> : k_batch_modal<N1, st>)
+#define GDG_BK(st) (VAR ? (counter ? k_batch_var_q<N1, st> : k_batch_var<N1, st>) : k_batch_modal<N1, st>)
     switch (stage) {
     case 1: GDG_BK(1)<<<grid, threads, smem, s>>>(probs, items, n_items, counter); break;
     case 2: GDG_BK(2)<<<grid, threads, smem, s>>>(probs, items, n_items, counter); break;
@@ -235,7 +268,7 @@ int resident_blocks(K kernel, int threads, size_t smem) {
 
 int max_resident(const gdg_batch *b, bool var, int threads, size_t smem) {
     switch (b->n1) {
-#define X(n) case n: return var ? resident_blocks(k_batch_var<n, 2>, threads, smem) \
+#define X(n) case n: return var ? resident_blocks(k_batch_var_q<n, 2>, threads, smem) \
                                 : resident_blocks(k_batch_modal<n, 2>, threads, smem);
         GDG_BATCH_CASES(X)
 #undef X
@@ -248,7 +281,9 @@ void launch_kind(gdg_batch *b, int kind, int stage, unsigned int *counter, cudaS
     const bool var = kind == 0;
     const int n = var ? b->n_var : b->n_mod;
     if (!n) return;
-    const int threads = var ? b->var_threads : b->mod_threads, grid = var ? b->var_grid : b->mod_grid;
+    const int threads = var ? b->var_threads : b->mod_threads;
+    const int grid = var ? (b->var_grid > 0 ? b->var_grid : n) : b->mod_grid;
+    if (var && b->var_grid <= 0) counter = nullptr;   // flat grid
     const size_t smem = var ? b->var_smem : modal_smem(b->n1, b->mod_threads / b->n1);
     const int2 *items = var ? b->d_var_items : b->d_mod_items;
     switch (b->n1) {
@@ -298,10 +333,11 @@ int autotune(gdg_batch *b, cudaStream_t s) {
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     int st = GDG_OK;
-    if (b->n_var) {   // PCG grid: resident blocks per SM from 1 to the occupancy limit
+    if (b->n_var) {   // PCG launch: flat grid, or persistent with 1..occupancy-limit blocks per SM
         const int maxr = max_resident(b, true, b->var_threads, b->var_smem);
-        float best = 1e30f;
-        int best_g = b->sms * maxr;
+        b->var_grid = 0;
+        float best = time_launch(b, 0, s, e0, e1);
+        int best_g = 0;
         for (int r = 1; r <= maxr; ++r) {
             b->var_grid = b->sms * r;
             const float ms = time_launch(b, 0, s, e0, e1);
@@ -395,6 +431,11 @@ extern "C" int gdg_batch_create(const gdg_problem *pbs, int count, gdg_batch **o
             for (int e = 0; e < c->ne; ++e) var_items.push_back(make_int2(i, e));
         }
     }
+    // longest items first (higher order: more quadrature points per face), so
+    // that the last blocks of a stage are short ones
+    std::stable_sort(var_items.begin(), var_items.end(), [&](const int2 &a, const int2 &c) {
+        return pbs[a.x].p > pbs[c.x].p;
+    });
     int cap = 0;
     if (cudaMalloc((void **)&b->d_mps, count * sizeof(ModalParams)) != cudaSuccess ||
         cudaMalloc((void **)&b->d_probs, count * sizeof(BatchProb)) != cudaSuccess ||
@@ -487,7 +528,7 @@ extern "C" int gdg_batch_tuning(const gdg_batch *b, int *threads_per_block, int 
     if (!b) return GDG_EINVAL;
     const bool mod = b->tuned && b->n_mod > 0, var = b->tuned && b->n_var > 0;
     if (threads_per_block) *threads_per_block = mod ? b->mod_threads : 0;
-    if (blocks_per_sm) *blocks_per_sm = var && b->sms ? b->var_grid / b->sms : 0;
+    if (blocks_per_sm) *blocks_per_sm = var && b->sms && b->var_grid > 0 ? b->var_grid / b->sms : (var ? -1 : 0);
     if (tile_elements) *tile_elements = mod ? b->mod_tile : 0;
     return GDG_OK;
 }

@@ -253,6 +253,13 @@ int gdg_var_setup(gdg_ctx *ctx) {
             (st = gdg_cuda_check(ctx, cudaMemcpy(D->d_c2feat, feat.data(), nd * sizeof(float), cudaMemcpyHostToDevice), "upload features")))
             return st;
     }
+    if ((st = gdg_cuda_check(ctx, cudaMalloc((void **)&D->d_dS, nd * sizeof(double)), "alloc dS"))) return st;
+    switch (n1) {
+#define X(n) case n: k_fdm_diag<n><<<ctx->ne, nthreads_for(n * n)>>>(D->d_tab + tab_len(Q, n) - n, D->d_pre, D->d_dS); break;
+        GDG_VAR_CASES(X)
+#undef X
+    }
+    P.dS = D->d_dS;
     if (P.mixed) {   // FP32 copies of the element matrices for the inner solves
         const size_t nm = nd * NA;
         if ((st = gdg_cuda_check(ctx, cudaMalloc((void **)&D->d_S32, nm * sizeof(float)), "alloc S32")) ||
@@ -279,7 +286,7 @@ int gdg_var_setup(gdg_ctx *ctx) {
 void gdg_var_free(gdg_ctx *ctx) {
     VarData *D = ctx->var;
     if (!D) return;
-    cudaFree(D->d_S); cudaFree(D->d_M); cudaFree(D->d_S32); cudaFree(D->d_M32); cudaFree(D->d_w); cudaFree(D->d_pre); cudaFree(D->d_face);
+    cudaFree(D->d_S); cudaFree(D->d_M); cudaFree(D->d_S32); cudaFree(D->d_M32); cudaFree(D->d_dS); cudaFree(D->d_w); cudaFree(D->d_pre); cudaFree(D->d_face);
     cudaFree(D->d_tab); cudaFree(D->d_nodes); cudaFree(D->d_state); cudaFree(D->d_tr);
     cudaFree(D->d_c2feat); cudaFree(D->d_wbf16); cudaFree(D->d_mlp);
     cudaFree(D->d_ru); cudaFree(D->d_rv); cudaFree(D->d_x0u);

@@ -17,6 +17,7 @@ struct VarParams {
     const double *tab;    // B[Q][N1], D[Q][N1], wq[Q], dphiL[N1], dphiR[N1], Psi[N1][N1], lam[N1]
     const double *S, *M, *w, *pre, *face;
     const float *S32, *M32;      // FP32 copies of S and M (mixed precision only)
+    const double *dS;            // [ne][N1*N1] frozen-coefficient preconditioner diagonal (S system)
     unsigned long long *stats;   // [0] sum it_u, [1] sum it_v, [2] max it_u, [3] max it_v,
                                  // [4] unconverged u, [5] unconverged v, [6] element solves,
                                  // [7] sum sweeps u, [8] sum sweeps v, [9] max sweeps u, [10] max sweeps v
@@ -29,6 +30,7 @@ struct VarData {
     int nq = 0, Q = 0, NA = 0;
     double *d_S = nullptr, *d_M = nullptr, *d_w = nullptr, *d_pre = nullptr, *d_face = nullptr;
     float *d_S32 = nullptr, *d_M32 = nullptr;
+    double *d_dS = nullptr;
     double *d_tab = nullptr, *d_nodes = nullptr;
     double *d_state = nullptr, *d_tr = nullptr;
     long long tr_len = 0;
@@ -51,6 +53,11 @@ constexpr int GEOM_THREADS = 256;
 
 __host__ __device__ constexpr int nthreads_for(int na) { return ((na + 31) / 32) * 32; }
 
+// element kernels are declared for at least this many resident blocks per SM
+// (shared memory allows 3-5); without a minimum ptxas keeps them near 64
+// registers and spills inside the PCG loops
+constexpr int kVarMinBlocks = 3;
+
 struct Tabs {
     const double *B, *D, *wq, *dphiL, *dphiR, *Ps, *lam;
 };
@@ -67,6 +74,22 @@ __device__ __forceinline__ Tabs tabs_at(const double *base, int Q, int N1) {
     return t;
 }
 __host__ __device__ constexpr int tab_len(int Q, int N1) { return 2 * Q * N1 + Q + 2 * N1 + N1 * N1 + N1; }
+// the tables after B and D (wq, dphiL, dphiR, Psi, lam)
+__host__ __device__ constexpr int tab_tail_len(int Q, int N1) { return Q + 2 * N1 + N1 * N1 + N1; }
+
+// B and D read from global memory (L1-cached), the rest from a shared copy of
+// the tail: keeps the stage kernels' shared memory independent of 2 Q N1
+__device__ __forceinline__ Tabs tabs_split(const double *gtab, const double *tail, int Q, int N1) {
+    Tabs t;
+    t.B = gtab;
+    t.D = gtab + Q * N1;
+    t.wq = tail;
+    t.dphiL = t.wq + Q;
+    t.dphiR = t.dphiL + N1;
+    t.Ps = t.dphiR + N1;
+    t.lam = t.Ps + N1 * N1;
+    return t;
+}
 
 // copy the 1-D tables into shared memory
 __device__ void load_tabs(double *dst, const double *src, int n) {
@@ -102,16 +125,18 @@ __device__ __forceinline__ int neighbour(const VarParams &P, int e, int f, int &
 
 // deterministic block sum: warp butterflies, then every thread adds the
 // warp partials in the same order
+// (the partials are stored in the value's own type: no conversions)
 template <typename T>
 __device__ __forceinline__ T block_sum(T v, double *red) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    T *part = reinterpret_cast<T *>(red);
     __syncthreads();
-    if ((threadIdx.x & 31) == 0) red[w] = (double)v;
+    if ((threadIdx.x & 31) == 0) part[w] = v;
     __syncthreads();
     T s = 0;
-    for (int i = 0; i < nw; ++i) s += (T)red[i];
+    for (int i = 0; i < nw; ++i) s += part[i];
     return s;
 }
 
@@ -133,6 +158,40 @@ __device__ __forceinline__ void matvec(const T *A, const T *x, T *y) {
         y[t] = s;
     }
     __syncthreads();
+}
+
+// y = A x for a symmetric NA x NA matrix in global memory, read by columns
+// (thread t reads column t: coalesced), summed in row order
+template <int NA>
+__device__ __forceinline__ void matvec_g(const double *__restrict__ A, const double *x, double *y) {
+    const int t = threadIdx.x;
+    if (t < NA) {
+        double s = 0.0;
+        const double *col = A + t;
+#pragma unroll 9
+        for (int k = 0; k < NA; ++k) s += __ldg(col + (size_t)k * NA) * x[k];
+        y[t] = s;
+    }
+    __syncthreads();
+}
+
+// two block sums with one pair of barriers (same order as block_sum)
+template <typename T>
+__device__ __forceinline__ void block_sum2(T &a, T &b, double *red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    T *part = reinterpret_cast<T *>(red);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) { part[w] = a; part[16 + w] = b; }
+    __syncthreads();
+    T sa = 0, sb = 0;
+    for (int i = 0; i < nw; ++i) { sa += part[i]; sb += part[16 + i]; }
+    a = sa;
+    b = sb;
 }
 
 // z = Psi2 diag(d) Psi2^T r, Psi2 = Psi (x) Psi (index j*N1+i), or z = r
@@ -248,27 +307,26 @@ __device__ int pcg32(const float *A, const float *w, const float *b, float *x, f
     __syncthreads();
     precondition<N1, float>(r, z, Ps, d, t1, t2, none);
     if (t < NA) p[t] = z[t];
-    __syncthreads();
-    float rz = block_dot<NA, float>(r, z, red);
+    float rz = t < NA ? r[t] * z[t] : 0.f, rr = t < NA ? r[t] * r[t] : 0.f;
+    block_sum2<float>(rz, rr, red);
     int it = 0;
     while (it < imaxit) {
-        const float rr = block_dot<NA, float>(r, r, red);
         if (sqrtf(rr) <= irtol || rz == 0.f) break;
         matvec<NA, float>(A, p, Ap);
-        if (W) {
-            const float wp = block_dot<NA, float>(w, p, red);
-            if (t < NA) Ap[t] += w[t] * wp;
-            __syncthreads();
-        }
-        const float pAp = block_dot<NA, float>(p, Ap, red);
+        // p.(A + w w^T)p = p.Ap + (w.p)^2: one reduction for both
+        float pAp = t < NA ? p[t] * Ap[t] : 0.f, wp = (W && t < NA) ? w[t] * p[t] : 0.f;
+        block_sum2<float>(pAp, wp, red);
+        if (W) pAp += wp * wp;
         const float alpha = rz / pAp;
         if (t < NA) {
             x[t] += alpha * p[t];
-            r[t] -= alpha * Ap[t];
+            r[t] -= alpha * (Ap[t] + (W ? w[t] * wp : 0.f));
         }
         __syncthreads();
         precondition<N1, float>(r, z, Ps, d, t1, t2, none);
-        const float rzn = block_dot<NA, float>(r, z, red);
+        float rzn = t < NA ? r[t] * z[t] : 0.f;
+        rr = t < NA ? r[t] * r[t] : 0.f;
+        block_sum2<float>(rzn, rr, red);
         const float beta = rzn / rz;
         if (t < NA) p[t] = z[t] + beta * p[t];
         __syncthreads();
@@ -279,7 +337,8 @@ __device__ int pcg32(const float *A, const float *w, const float *b, float *x, f
 }
 
 // Mixed-precision solve of A x = b (+ w w^T when W): iterative refinement with
-// the FP64 matrix for every residual and FP32 PCG for every correction.
+// the FP64 matrix (symmetric, in global memory) for every residual and FP32
+// PCG for every correction.
 //   r = b - A x (FP64);  while ||r|| > rtol ||b||:  A c ~= r/||r|| (FP32 PCG),
 //   x += ||r|| c (FP64);  r = b - A x (FP64)
 // The stopping test is the FP64 PCG's (true FP64 residual), so the accuracy
@@ -301,7 +360,7 @@ struct Step64 {
 };
 
 template <int N1, bool W>
-__device__ int refine(const double *A, const double *w, const double *b, double *x, double *r, double *Ap,
+__device__ int refine(const double *__restrict__ A, const double *w, const double *b, double *x, double *r, double *Ap,
                       const SolveScratch32 &f, double *red, double rtol, int maxsweep, float irtol,
                       int imaxit, bool none, bool x0_zero, int *inner, double *relres,
                       bool fallback = false, int *fell = nullptr, const Step64 *step64 = nullptr) {
@@ -309,7 +368,7 @@ __device__ int refine(const double *A, const double *w, const double *b, double 
     const int t = threadIdx.x;
     if (x0_zero && step64) {
         precondition<N1>(b, step64->z, step64->Ps, step64->d, step64->t1, step64->t2, none);
-        matvec<NA, double>(A, step64->z, Ap);
+        matvec_g<NA>(A, step64->z, Ap);
         if (W) {
             const double wz = block_dot<NA, double>(w, step64->z, red);
             if (t < NA) Ap[t] += w[t] * wz;
@@ -327,7 +386,7 @@ __device__ int refine(const double *A, const double *w, const double *b, double 
         if (t < NA) { x[t] = 0.0; r[t] = b[t]; }
         __syncthreads();
     } else {
-        matvec<NA, double>(A, x, Ap);
+        matvec_g<NA>(A, x, Ap);
         const double wx = W ? block_dot<NA, double>(w, x, red) : 0.0;
         if (t < NA) r[t] = b[t] - Ap[t] - (W ? w[t] * wx : 0.0);
         __syncthreads();
@@ -341,13 +400,14 @@ __device__ int refine(const double *A, const double *w, const double *b, double 
     int sweeps = 0, its = 0;
     double rn = sqrt(block_dot<NA, double>(r, r, red));
     while (sweeps < maxsweep && rn > rtol * bnorm && rn > 0.0) {
-        if (t < NA) f.rhs[t] = (float)(r[t] / rn);
+        const double inv = 1.0 / rn;
+        if (t < NA) f.rhs[t] = (float)(r[t] * inv);
         __syncthreads();
         its += pcg32<N1, W>(f.A32, f.w32, f.rhs, f.x, f.res, f.z, f.p, f.Ap, f.Ps32, f.d32, f.t1, f.t2, red,
                             irtol, imaxit, none);
         if (t < NA) x[t] += rn * (double)f.x[t];
         __syncthreads();
-        matvec<NA, double>(A, x, Ap);
+        matvec_g<NA>(A, x, Ap);
         const double wx = W ? block_dot<NA, double>(w, x, red) : 0.0;
         if (t < NA) r[t] = b[t] - Ap[t] - (W ? w[t] * wx : 0.0);
         __syncthreads();
@@ -359,31 +419,57 @@ __device__ int refine(const double *A, const double *w, const double *b, double 
     return sweeps;
 }
 
+// asynchronous global -> shared copies (cp.async): every copy of a matrix is
+// in flight at once instead of a register round trip per element
+__device__ __forceinline__ void cp_async_8(void *dst, const void *src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_4(void *dst, const void *src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // FP32 element matrix (the copy made at setup) and FP32 copies of the
 // preconditioner data
 template <int N1>
 __device__ void to_fp32(const float *A32g, float *A32, const double *Ps, float *Ps32, const double *d, float *d32,
                         const double *w, float *w32) {
     constexpr int NA = N1 * N1;
-    for (int i = threadIdx.x; i < NA * NA; i += blockDim.x) A32[i] = A32g[i];
+    for (int i = threadIdx.x; i < NA * NA; i += blockDim.x) cp_async_4(A32 + i, A32g + i);
     for (int i = threadIdx.x; i < N1 * N1; i += blockDim.x) Ps32[i] = (float)Ps[i];
     for (int i = threadIdx.x; i < NA; i += blockDim.x) {
         d32[i] = (float)d[i];
         if (w) w32[i] = (float)w[i];
     }
+    cp_async_wait_all();
     __syncthreads();
 }
 
-// diagonal of the frozen-coefficient preconditioner in the modified basis
+// diagonal of the frozen-coefficient preconditioner in the modified basis,
+// made once at setup: dS[e][l*N1+k] = 1 / (Gss lam_l + Grr lam_k) (1 on the
+// constant mode), and pre[e][3] = 1 / |e| (the mass preconditioner's diagonal)
 template <int N1>
-__device__ void fdm_diagonals(const double *pre, const double *lam, double *dS, double *dM) {
+__global__ void __launch_bounds__(nthreads_for(N1 * N1), kVarMinBlocks)
+k_fdm_diag(const double *__restrict__ lam, double *pre, double *dS) {
+    constexpr int NA = N1 * N1;
+    const int e = blockIdx.x, t = threadIdx.x;
+    const double Grr = pre[(size_t)e * 4 + 0], Gss = pre[(size_t)e * 4 + 1], Jb = pre[(size_t)e * 4 + 2];
+    if (t < NA) {
+        const int l = t / N1, k = t - (t / N1) * N1;
+        dS[(size_t)e * NA + t] = t == 0 ? 1.0 : 1.0 / (Gss * lam[l] + Grr * lam[k]);
+    }
+    if (t == 0) pre[(size_t)e * 4 + 3] = 1.0 / Jb;
+}
+
+template <int N1>
+__device__ void fdm_diagonals(const VarParams &P, int e, double *dS, double *dM) {
     constexpr int NA = N1 * N1;
     const int t = threadIdx.x;
     if (t < NA) {
-        const double Grr = pre[0], Gss = pre[1], Jb = pre[2];
-        const int l = t / N1, k = t - (t / N1) * N1;
-        dS[t] = t == 0 ? 1.0 : 1.0 / (Gss * lam[l] + Grr * lam[k]);
-        dM[t] = 1.0 / Jb;
+        dS[t] = P.dS[(size_t)e * NA + t];
+        dM[t] = P.pre[(size_t)e * 4 + 3];
     }
 }
 
@@ -490,6 +576,15 @@ k_var_geom(VarParams P, const double *X, const double *Y, const double *C2, doub
         for (int m = 0; m < PER; ++m) {
             const int o = t + m * GEOM_THREADS;
             if (o < NA * NA) out[o] = accv[m];
+        }
+        __syncthreads();
+        // exact symmetry (the two triangles differ by rounding): lower := upper,
+        // so that A x can be formed from columns (coalesced) with row-order sums
+#pragma unroll
+        for (int m = 0; m < PER; ++m) {
+            const int o = t + m * GEOM_THREADS;
+            const int al = o / NA, be = o - (o / NA) * NA;
+            if (o < NA * NA && al > be) out[o] = out[(size_t)be * NA + al];
         }
         __syncthreads();
     }
@@ -629,24 +724,27 @@ struct VarBufs {
 template <int N1>
 struct StageSmem {
     static constexpr int NA = N1 * N1;
+    // A: the FP64 element matrix (FP64 solves only; the mixed solves read it
+    // from global memory for their few FP64 residuals)
     double *A, *tb, *Yu, *Yv, *ru, *rv, *x, *r, *z, *p, *Ap, *w, *dS, *dM, *t1, *t2, *fw, *L, *red;
     // FP32 area (mixed precision only): matrix, preconditioner and PCG vectors
     float *A32, *Ps32, *dS32, *dM32, *w32, *r32, *z32, *p32, *Ap32, *c32, *u32, *v32, *t132, *t232;
-    __device__ StageSmem(double *base, int Q) {
-        A = base;
-        tb = A + NA * NA;
-        Yu = tb + tab_len(Q, N1);
+    __device__ StageSmem(double *base, int Q, bool mixed) {
+        tb = base;   // tail of the 1-D tables (tab_tail_len)
+        Yu = tb + tab_tail_len(Q, N1);
         Yv = Yu + NA; ru = Yv + NA; rv = ru + NA; x = rv + NA; r = x + NA; z = r + NA; p = z + NA;
         Ap = p + NA; w = Ap + NA; dS = w + NA; dM = dS + NA; t1 = dM + NA; t2 = t1 + NA;
         fw = t2 + NA; L = fw + 12 * Q; red = L + 12 * N1;
+        A = mixed ? nullptr : red + 32;
         A32 = reinterpret_cast<float *>(red + 32);
         Ps32 = A32 + NA * NA; dS32 = Ps32 + N1 * N1; dM32 = dS32 + NA; w32 = dM32 + NA;
         r32 = w32 + NA; z32 = r32 + NA; p32 = z32 + NA; Ap32 = p32 + NA; c32 = Ap32 + NA;
         u32 = c32 + NA; v32 = u32 + NA; t132 = v32 + NA; t232 = t132 + NA;
     }
     static size_t bytes(int Q, bool mixed) {
-        size_t d = sizeof(double) * ((size_t)NA * NA + tab_len(Q, N1) + 14 * NA + 12 * Q + 12 * N1 + 32);
+        size_t d = sizeof(double) * ((size_t)tab_tail_len(Q, N1) + 14 * NA + 12 * Q + 12 * N1 + 32);
         if (mixed) d += sizeof(float) * ((size_t)NA * NA + N1 * N1 + 12 * NA);
+        else d += sizeof(double) * (size_t)NA * NA;
         return d;
     }
     __device__ SolveScratch32 scratch32(bool s_system) const {
@@ -716,7 +814,8 @@ template <int N1>
 __device__ void load_matrix(double *A, const double *src) {
     constexpr int NA = N1 * N1;
     // element matrices start at e*NA*NA doubles: only 8-byte alignment is guaranteed
-    for (int i = threadIdx.x; i < NA * NA; i += blockDim.x) A[i] = src[i];
+    for (int i = threadIdx.x; i < NA * NA; i += blockDim.x) cp_async_8(A + i, src + i);
+    cp_async_wait_all();
     __syncthreads();
 }
 
@@ -725,24 +824,29 @@ template <int N1, int MODE>
 __device__ __forceinline__ void var_stage_body(const VarParams &P, const VarBufs &b, double cA, double cY, int e,
                                                double *smraw) {
     constexpr int NA = N1 * N1;
-    StageSmem<N1> s(smraw, P.Q);
+    StageSmem<N1> s(smraw, P.Q, P.mixed);
     const int t = threadIdx.x;
     const size_t off = (size_t)e * NA;
-    load_tabs(s.tb, P.tab, tab_len(P.Q, N1));
+    const double *Sg = P.S + (size_t)e * NA * NA, *Mg = P.M + (size_t)e * NA * NA;
+    load_tabs(s.tb, P.tab + 2 * P.Q * N1, tab_tail_len(P.Q, N1));
     if (t < NA) {
         s.Yu[t] = b.yU[off + t];
         s.Yv[t] = b.yV[off + t];
         s.w[t] = P.w[off + t];
     }
     __syncthreads();
-    const Tabs T = tabs_at(s.tb, P.Q, N1);
-    fdm_diagonals<N1>(P.pre + (size_t)e * 4, T.lam, s.dS, s.dM);
+    const Tabs T = tabs_split(P.tab, s.tb, P.Q, N1);
+    fdm_diagonals<N1>(P, e, s.dS, s.dM);
     const bool guess = b.part == 2;
     if (!guess) {
         lifts<N1>(P, e, b.trin, T, s.fw, s.L, s.ru, s.rv);
         // stiffness: r_v -= S U
-        load_matrix<N1>(s.A, P.S + (size_t)e * NA * NA);
-        matvec<NA>(s.A, s.Yu, s.Ap);
+        if (P.mixed) {
+            matvec_g<NA>(Sg, s.Yu, s.Ap);
+        } else {
+            load_matrix<N1>(s.A, Sg);
+            matvec<NA>(s.A, s.Yu, s.Ap);
+        }
         if (t < NA) s.rv[t] -= s.Ap[t];
         __syncthreads();
         if (b.part == 1) {
@@ -751,7 +855,7 @@ __device__ __forceinline__ void var_stage_body(const VarParams &P, const VarBufs
         }
     } else {
         if (t < NA) { s.ru[t] = b.ru[off + t]; s.rv[t] = b.rv[off + t]; s.x[t] = b.x0u[off + t]; }
-        load_matrix<N1>(s.A, P.S + (size_t)e * NA * NA);
+        if (!P.mixed) load_matrix<N1>(s.A, Sg);
     }
     const bool none = P.precond == GDG_PC_NONE;
     double rel_u, rel_v;
@@ -759,7 +863,7 @@ __device__ __forceinline__ void var_stage_body(const VarParams &P, const VarBufs
     bool bad_u, bad_v;
     if (P.mixed) {
         to_fp32<N1>(P.S32 + (size_t)e * NA * NA, s.A32, T.Ps, s.Ps32, s.dS, s.dS32, s.w, s.w32);
-        sw_u = refine<N1, true>(s.A, s.w, s.ru, s.x, s.r, s.Ap, s.scratch32(true), s.red, P.rtol, P.refine_max,
+        sw_u = refine<N1, true>(Sg, s.w, s.ru, s.x, s.r, s.Ap, s.scratch32(true), s.red, P.rtol, P.refine_max,
                                 P.refine_rtol, P.maxit, none, !guess, &it_u, &rel_u, guess, &fell);
         bad_u = sw_u >= P.refine_max && rel_u > P.rtol;
     } else {
@@ -769,11 +873,11 @@ __device__ __forceinline__ void var_stage_body(const VarParams &P, const VarBufs
     }
     if (t < NA) s.ru[t] = s.Yv[t] + s.x[t];   // dU/dt
     __syncthreads();
-    load_matrix<N1>(s.A, P.M + (size_t)e * NA * NA);
+    if (!P.mixed) load_matrix<N1>(s.A, Mg);
     if (P.mixed) {
         to_fp32<N1>(P.M32 + (size_t)e * NA * NA, s.A32, T.Ps, s.Ps32, s.dM, s.dM32, nullptr, nullptr);
         const Step64 st64{s.z, s.t1, s.t2, T.Ps, s.dM};
-        sw_v = refine<N1, false>(s.A, s.w, s.rv, s.x, s.r, s.Ap, s.scratch32(false), s.red, P.rtol,
+        sw_v = refine<N1, false>(Mg, s.w, s.rv, s.x, s.r, s.Ap, s.scratch32(false), s.red, P.rtol,
                                  P.refine_max, P.refine_rtol, P.maxit, none, true, &it_v, &rel_v, false, nullptr,
                                  &st64);
         bad_v = sw_v >= P.refine_max && rel_v > P.rtol;
@@ -831,7 +935,7 @@ __device__ __forceinline__ void var_stage_body(const VarParams &P, const VarBufs
 }
 
 template <int N1, int MODE>
-__global__ void __launch_bounds__(nthreads_for(N1 * N1))
+__global__ void __launch_bounds__(nthreads_for(N1 * N1), kVarMinBlocks)
 k_var_stage(VarParams P, VarBufs b, double cA, double cY) {
     extern __shared__ double smraw[];
     var_stage_body<N1, MODE>(P, b, cA, cY, blockIdx.x, smraw);
@@ -839,23 +943,24 @@ k_var_stage(VarParams P, VarBufs b, double cA, double cY) {
 
 // standalone element PCG (gdg_pcg): which = 0 M, 1 S (+ w w^T)
 template <int N1>
-__global__ void __launch_bounds__(nthreads_for(N1 * N1))
+__global__ void __launch_bounds__(nthreads_for(N1 * N1), kVarMinBlocks)
 k_var_pcg(VarParams P, int which, const double *bvec, double *xvec, int *iters, double *rel, int *sweeps) {
     constexpr int NA = N1 * N1;
     extern __shared__ double smraw[];
-    StageSmem<N1> s(smraw, P.Q);
+    StageSmem<N1> s(smraw, P.Q, P.mixed);
     const int e = blockIdx.x, t = threadIdx.x;
     const size_t off = (size_t)e * NA;
-    load_tabs(s.tb, P.tab, tab_len(P.Q, N1));
+    load_tabs(s.tb, P.tab + 2 * P.Q * N1, tab_tail_len(P.Q, N1));
     if (t < NA) {
         s.ru[t] = bvec[off + t];
         s.x[t] = xvec[off + t];
         s.w[t] = P.w[off + t];
     }
     __syncthreads();
-    const Tabs T = tabs_at(s.tb, P.Q, N1);
-    fdm_diagonals<N1>(P.pre + (size_t)e * 4, T.lam, s.dS, s.dM);
-    load_matrix<N1>(s.A, (which ? P.S : P.M) + (size_t)e * NA * NA);
+    const Tabs T = tabs_split(P.tab, s.tb, P.Q, N1);
+    fdm_diagonals<N1>(P, e, s.dS, s.dM);
+    const double *Ag = (which ? P.S : P.M) + (size_t)e * NA * NA;
+    if (!P.mixed) load_matrix<N1>(s.A, Ag);
     const bool none = P.precond == GDG_PC_NONE;
     double rr;
     int it, sw = 0;
@@ -863,10 +968,10 @@ k_var_pcg(VarParams P, int which, const double *bvec, double *xvec, int *iters, 
         to_fp32<N1>((which ? P.S32 : P.M32) + (size_t)e * NA * NA, s.A32, T.Ps, s.Ps32, which ? s.dS : s.dM,
                     which ? s.dS32 : s.dM32, which ? s.w : nullptr, s.w32);
         if (which)
-            sw = refine<N1, true>(s.A, s.w, s.ru, s.x, s.r, s.Ap, s.scratch32(true), s.red, P.rtol, P.refine_max,
+            sw = refine<N1, true>(Ag, s.w, s.ru, s.x, s.r, s.Ap, s.scratch32(true), s.red, P.rtol, P.refine_max,
                                   P.refine_rtol, P.maxit, none, false, &it, &rr);
         else
-            sw = refine<N1, false>(s.A, s.w, s.ru, s.x, s.r, s.Ap, s.scratch32(false), s.red, P.rtol,
+            sw = refine<N1, false>(Ag, s.w, s.ru, s.x, s.r, s.Ap, s.scratch32(false), s.red, P.rtol,
                                    P.refine_max, P.refine_rtol, P.maxit, none, false, &it, &rr);
     } else if (which) {
         it = pcg<N1, true>(s.A, s.w, s.ru, s.x, s.r, s.z, s.p, s.Ap, T.Ps, s.dS, s.t1, s.t2, s.red, P.rtol,
@@ -891,7 +996,7 @@ __global__ void k_to_f32(size_t n, const double *__restrict__ src, float *__rest
 
 // per-element V^T M V + U^T S U
 template <int N1>
-__global__ void __launch_bounds__(nthreads_for(N1 * N1))
+__global__ void __launch_bounds__(nthreads_for(N1 * N1), kVarMinBlocks)
 k_var_energy(VarParams P, const double *u, const double *v, double *part) {
     constexpr int NA = N1 * N1;
     __shared__ double U[NA], V[NA], red[32];

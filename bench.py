@@ -208,7 +208,8 @@ def _timed_ms(fn):
 def forms_variable(steps=16):
     """Mapped 128 x 128 elements, c^2 = 1 + 0.5 sin 2pi x cos 2pi y, p = 3 and 5,
     PCG to rtol 1e-10: FP64 against FP32-inner / FP64-refined PCG (same stopping
-    test, so equal accuracy by construction); both trajectories are compared."""
+    test, so equal accuracy by construction) and against precomputed element
+    inverses (exact solves); the trajectories are compared with the FP64 PCG's."""
     import numpy as np
     import torch
     from paper_2105_01722_gb300 import gdg, inputs
@@ -219,9 +220,11 @@ def forms_variable(steps=16):
         U0 = inputs.gaussian_pulse(X, Y, 0.5, 0.5, 0.05)
         dt = 0.1 / 1024 / np.sqrt(1.5)
         states = {}
-        for prec, name in ((gdg.FP64, "fp64"), (gdg.MIXED, "mixed")):
+        for prec, solver, name in ((gdg.FP64, gdg.SOLVE_PCG, "fp64"), (gdg.MIXED, gdg.SOLVE_PCG, "mixed"),
+                                   (gdg.FP64, gdg.SOLVE_INVERSE, "inverse")):
             ctx = gdg.Context(gdg.make_problem(2, (128, 128), 8, p, coef=gdg.COEF_NODAL, x_nodes=X, y_nodes=Y,
-                                               c2_nodes=C2, pcg_rtol=1e-10, pcg_maxit=100, precision=prec))
+                                               c2_nodes=C2, pcg_rtol=1e-10, pcg_maxit=100, precision=prec,
+                                               solver=solver))
             u = torch.tensor(U0.ravel(), device="cuda")
             v = torch.zeros_like(u)
             ctx.step(u, v, 0.0, dt, 8)
@@ -234,8 +237,10 @@ def forms_variable(steps=16):
                 "pcg_u_mean_iters": su["mean_iters"], "pcg_v_mean_iters": sv["mean_iters"],
                 "refine_sweeps_u": su["mean_sweeps"], "refine_sweeps_v": sv["mean_sweeps"]}
             ctx.close()
-        a, b = states["mixed"], states["fp64"]
-        out["p%d_mixed_vs_fp64_rel_l2" % p] = float(np.linalg.norm(a - b) / np.linalg.norm(b))
+        b = states["fp64"]
+        for name in ("mixed", "inverse"):
+            a = states[name]
+            out["p%d_%s_vs_fp64_rel_l2" % (p, name)] = float(np.linalg.norm(a - b) / np.linalg.norm(b))
     out["workload"] = ("2-D variable c^2 on the sine-mapped unit square, 128x128 elements of 8x8 cells, "
                        "Gaussian pulse, PCG rtol 1e-10, %d RK4 steps after 8 warm-up steps" % steps)
     return out
@@ -327,7 +332,7 @@ def forms_learned(rows=20000, epochs=30, steps=16):
 def run_gdg(args):
     import numpy as np
     import torch
-    from paper_2105_01722_gb300 import gdg, inputs
+    from paper_2105_01722_gb300 import gdg, inputs, shard
 
     rank, world, local = _env_rank()
     if world > 1:
@@ -375,11 +380,7 @@ def run_gdg(args):
     wall1 = time.perf_counter()
     clocks = sampler.stop()
     ms = [a.elapsed_time(b) for a, b in evs]
-    total_ms = sum(ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = shard.max_over_ranks(sum(ms))
     ms_per_step = total_ms / args.steps
     value = world * dof() * R * args.steps / (total_ms / 1e3)
 
@@ -411,11 +412,7 @@ def run_gdg(args):
         t0 = time.perf_counter()
         ctx.step_host(hu, hv, 0.0, dt, R)
         e2e_t.append(time.perf_counter() - t0)
-    e2e_s = sum(e2e_t)
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = shard.max_over_ranks(sum(e2e_t))
     e2e_val = world * dof() * R * args.steps / e2e_s
 
     # accuracy of the FP64 form at T = 1: M-norm distance to the GD

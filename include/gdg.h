@@ -53,16 +53,26 @@ enum { GDG_FLUX_CENTRAL = 0, GDG_FLUX_UPWIND = 1 };
  * sound or mapped, non-Cartesian elements). */
 enum { GDG_COEF_CONST = 0, GDG_COEF_NODAL = 1 };
 /* Local solves: modified-basis diagonalisation (Section 3.2, constant
- * coefficient Cartesian only) or element-local preconditioned CG (Section 7.1). */
-enum { GDG_SOLVE_DIAG = 0, GDG_SOLVE_PCG = 1 };
+ * coefficient Cartesian only), element-local preconditioned CG (Section
+ * 7.1), or precomputed element inverses (GDG_COEF_NODAL only): the
+ * precomputed-inverse route that Section 3.1 discusses, applied to the
+ * time-independent element systems of Section 7.1.  gdg_create forms
+ * (S_c2 + w w^T)^-1 and M_J^-1 per element by Cholesky (2 x (N+1)^4 more
+ * doubles per element); every stage then applies them instead of running
+ * PCG.  FP64 only (GDG_EUNSUPPORTED with GDG_MIXED); gdg_pcg still runs PCG
+ * on such a context. */
+enum { GDG_SOLVE_DIAG = 0, GDG_SOLVE_PCG = 1, GDG_SOLVE_INVERSE = 2 };
 /* PCG preconditioner: frozen-coefficient diagonalisation, none (plain CG). */
 enum { GDG_PC_FDM = 0, GDG_PC_NONE = 1 };
-/* Arithmetic of the element contractions.  GDG_FP64 everywhere, or
- * GDG_FP32 contractions with FP64 iterative refinement of every solve
- * (FP64 state, residuals, inner products and energy). */
+/* Arithmetic of the element solves.  GDG_FP64 everywhere, or (GDG_SOLVE_PCG
+ * only) FP32 inner PCG with FP64 iterative refinement of every solve (FP64
+ * state, residuals, lifts, norms and energy; same FP64 stopping test).
+ * Constant-coefficient contexts are FP64 only (GDG_EUNSUPPORTED otherwise):
+ * their diagonal solves have no iteration to refine. */
 enum { GDG_FP64 = 0, GDG_MIXED = 1 };
 /* State representation used inside gdg_step for the diagonalised route:
- * modal coefficients U = Psi Ubar (Section 3.2) or nodal values. */
+ * modal coefficients U = Psi Ubar (Section 3.2).  The nodal-state route is
+ * not built: gdg_create returns GDG_EUNSUPPORTED for GDG_ROUTE_NODAL. */
 enum { GDG_ROUTE_MODAL = 0, GDG_ROUTE_NODAL = 1 };
 /* Operator selector of gdg_mass_solve / gdg_pcg. */
 enum { GDG_OP_M = 0, GDG_OP_S = 1 };

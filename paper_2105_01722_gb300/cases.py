@@ -1,7 +1,7 @@
 """Small seeded workloads of each kernel family, for profiling and timing.
 
 python -m paper_2105_01722_gb300.cases const [--n 64] [--p 5] [--steps 8]
-python -m paper_2105_01722_gb300.cases var   [--n 32] [--p 5] [--steps 2] [--mixed]
+python -m paper_2105_01722_gb300.cases var   [--n 32] [--p 5] [--steps 2] [--mixed | --inverse]
 python -m paper_2105_01722_gb300.cases batch [--problems 12] [--steps 2] [--mixed]
 python -m paper_2105_01722_gb300.cases mlp   [--rows 4096] [--steps 4]
 
@@ -49,15 +49,16 @@ def case_const(n=64, N=8, p=5, steps=8, warmup=2):
             "dof_steps_per_s": dof * steps / (ms / 1e3)}
 
 
-def case_var(n=32, N=8, p=5, steps=2, warmup=1, mixed=False):
+def case_var(n=32, N=8, p=5, steps=2, warmup=1, mixed=False, inverse=False):
     """Sine-mapped mesh, c^2 = 1 + 0.5 sin 2pi x cos 2pi y, Gaussian pulse,
-    element PCG to rtol 1e-10."""
+    element PCG to rtol 1e-10 (inverse: precomputed element inverses)."""
     import torch
     X, Y = inputs.mapped_nodes((n, n), N, 0.05)
     C2 = inputs.c2_sine(X, Y)
     prec = gdg.MIXED if mixed else gdg.FP64
     pb = gdg.make_problem(2, (n, n), N, p, coef=gdg.COEF_NODAL, x_nodes=X, y_nodes=Y, c2_nodes=C2,
-                          pcg_rtol=1e-10, pcg_maxit=100, precision=prec)
+                          pcg_rtol=1e-10, pcg_maxit=100, precision=prec,
+                          solver=gdg.SOLVE_INVERSE if inverse else gdg.SOLVE_PCG)
     ctx = gdg.Context(pb)
     u = torch.tensor(inputs.gaussian_pulse(X, Y, 0.5, 0.5, 0.05).ravel(), device="cuda")
     v = torch.zeros_like(u)
@@ -68,7 +69,7 @@ def case_var(n=32, N=8, p=5, steps=2, warmup=1, mixed=False):
     su, sv = ctx.step_stats()
     ctx.close()
     dof = n * n * (N + 1) ** 2
-    return {"case": "var", "n": n, "N": N, "p": p, "mixed": mixed, "steps": steps, "ms": ms,
+    return {"case": "var", "n": n, "N": N, "p": p, "mixed": mixed, "inverse": inverse, "steps": steps, "ms": ms,
             "dof_steps_per_s": dof * steps / (ms / 1e3), "pcg_u_mean_iters": su["mean_iters"],
             "pcg_v_mean_iters": sv["mean_iters"]}
 
@@ -145,6 +146,7 @@ def main(argv=None):
     ap.add_argument("--p", type=int, default=5)
     ap.add_argument("--steps", type=int)
     ap.add_argument("--mixed", action="store_true")
+    ap.add_argument("--inverse", action="store_true", help="var: precomputed element inverses")
     ap.add_argument("--problems", type=int, default=12)
     ap.add_argument("--rows", type=int, default=4096)
     ap.add_argument("--sequential", action="store_true")
@@ -154,7 +156,7 @@ def main(argv=None):
     if a.case == "const":
         r = case_const(n=a.n or 64, p=a.p, **kw)
     elif a.case == "var":
-        r = case_var(n=a.n or 32, p=a.p, mixed=a.mixed, **kw)
+        r = case_var(n=a.n or 32, p=a.p, mixed=a.mixed, inverse=a.inverse, **kw)
     elif a.case == "batch":
         r = case_batch(problems=a.problems, mixed=a.mixed, sequential=a.sequential, pmax=a.pmax, **kw)
     else:

@@ -365,10 +365,19 @@ static int validate(const gdg_problem *pb, std::string &why) {
         if (!(pb->c2 > 0.0)) { why = "c2 must be > 0"; return GDG_EINVAL; }
         if (pb->solver != GDG_SOLVE_DIAG) { why = "constant coefficients use GDG_SOLVE_DIAG"; return GDG_EINVAL; }
         if (pb->route != GDG_ROUTE_MODAL && pb->route != GDG_ROUTE_NODAL) { why = "bad route"; return GDG_EINVAL; }
+        if (pb->route == GDG_ROUTE_NODAL) { why = "the nodal-state route is not built (modal route only)"; return GDG_EUNSUPPORTED; }
+        if (pb->precision != GDG_FP64) { why = "the diagonalised route has no solve to refine: FP64 only"; return GDG_EUNSUPPORTED; }
     } else if (pb->coef == GDG_COEF_NODAL) {
         if (pb->dim != 2) { why = "GDG_COEF_NODAL needs dim 2"; return GDG_EINVAL; }
         if (!pb->x_nodes || !pb->y_nodes || !pb->c2_nodes) { why = "null nodal arrays"; return GDG_EINVAL; }
-        if (pb->solver != GDG_SOLVE_PCG) { why = "GDG_COEF_NODAL needs GDG_SOLVE_PCG"; return GDG_EINVAL; }
+        if (pb->solver != GDG_SOLVE_PCG && pb->solver != GDG_SOLVE_INVERSE) {
+            why = "GDG_COEF_NODAL needs GDG_SOLVE_PCG or GDG_SOLVE_INVERSE";
+            return GDG_EINVAL;
+        }
+        if (pb->solver == GDG_SOLVE_INVERSE && pb->precision != GDG_FP64) {
+            why = "GDG_SOLVE_INVERSE has no iteration to refine: FP64 only";
+            return GDG_EUNSUPPORTED;
+        }
         if (pb->precond != GDG_PC_FDM && pb->precond != GDG_PC_NONE) { why = "bad precond"; return GDG_EINVAL; }
         if (pb->pcg_maxit < 1 || !(pb->pcg_rtol >= 0.0)) { why = "bad PCG settings"; return GDG_EINVAL; }
         if (pb->nquad < 0 || pb->nquad > 12) { why = "nquad must be in 0..12"; return GDG_EINVAL; }

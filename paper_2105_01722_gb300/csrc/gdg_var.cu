@@ -46,7 +46,8 @@ size_t geom_smem(int N1, int Q) {
 size_t traces_smem(int N1, int Q) { return sizeof(double) * ((size_t)tab_len(Q, N1) + 2 * N1 * N1 + 12 * N1); }
 
 template <int N1>
-size_t stage_smem(int Q, bool mixed) { return StageSmem<N1>::bytes(Q, mixed); }
+size_t stage_smem(int Q, bool mixed, bool no_matrix) { return StageSmem<N1>::bytes(Q, mixed, no_matrix); }
+size_t invert_smem(int N1) { return sizeof(double) * (2 * (size_t)N1 * N1 * N1 * N1 + (size_t)N1 * N1); }
 
 // The dynamic shared-memory limit is a property of the kernel function, shared
 // by every context: always raise it to the device's opt-in maximum so that a
@@ -63,6 +64,7 @@ void set_attrs() {
     cudaFuncSetAttribute(k_var_stage<N1, M_S23>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     cudaFuncSetAttribute(k_var_stage<N1, M_S4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     cudaFuncSetAttribute(k_var_pcg<N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    cudaFuncSetAttribute(k_var_invert<N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
 }
 
 template <int N1>
@@ -122,7 +124,7 @@ void launch_pcg_raw(gdg_ctx *ctx, int which, const double *b, double *x, cudaStr
     const VarData &D = *ctx->var;
     const dim3 grid(ctx->ne), block(nthreads_for(ctx->n1 * ctx->n1));
     switch (ctx->n1) {
-#define X(n) case n: k_var_pcg<n><<<grid, block, D.smem_stage, s>>>(D.vp, which == GDG_OP_S, b, x, D.d_iters, D.d_rel, D.d_sweeps); break;
+#define X(n) case n: k_var_pcg<n><<<grid, block, D.smem_pcg, s>>>(D.vp, which == GDG_OP_S, b, x, D.d_iters, D.d_rel, D.d_sweeps); break;
         GDG_VAR_CASES(X)
 #undef X
     }
@@ -229,11 +231,17 @@ int gdg_var_setup(gdg_ctx *ctx) {
     D->smem_geom = geom_smem(n1, Q);
     D->smem_traces = traces_smem(n1, Q);
     switch (n1) {
-#define X(n) case n: D->smem_stage = stage_smem<n>(Q, ctx->pb.precision == GDG_MIXED); set_attrs<n>(); break;
+#define X(n)                                                                                   \
+    case n:                                                                                    \
+        D->smem_stage = stage_smem<n>(Q, ctx->pb.precision == GDG_MIXED, ctx->pb.solver == GDG_SOLVE_INVERSE); \
+        D->smem_pcg = stage_smem<n>(Q, ctx->pb.precision == GDG_MIXED, false);                  \
+        set_attrs<n>();                                                                        \
+        break;
         GDG_VAR_CASES(X)
 #undef X
     }
-    if (D->smem_stage > 220 * 1024 || D->smem_geom > 220 * 1024)
+    if (D->smem_pcg > 220 * 1024 || D->smem_geom > 220 * 1024 ||
+        (ctx->pb.solver == GDG_SOLVE_INVERSE && invert_smem(n1) > 220 * 1024))
         return gdg_set_err(ctx, GDG_EUNSUPPORTED, "element too large for shared memory (reduce nquad)");
     const double *Xd = D->d_nodes, *Yd = D->d_nodes + nd, *Cd = D->d_nodes + 2 * nd;
     switch (n1) {
@@ -260,6 +268,25 @@ int gdg_var_setup(gdg_ctx *ctx) {
 #undef X
     }
     P.dS = D->d_dS;
+    P.inverse = ctx->pb.solver == GDG_SOLVE_INVERSE;
+    if (P.inverse) {   // element inverses (S_c2 + w w^T)^-1 and M_J^-1
+        const size_t nm = nd * NA;
+        if ((st = gdg_cuda_check(ctx, cudaMalloc((void **)&D->d_Ainv, nm * sizeof(double)), "alloc Ainv")) ||
+            (st = gdg_cuda_check(ctx, cudaMalloc((void **)&D->d_Minv, nm * sizeof(double)), "alloc Minv")))
+            return st;
+        const size_t ism = invert_smem(n1);
+        switch (n1) {
+#define X(n)                                                                                         \
+    case n:                                                                                          \
+        k_var_invert<n><<<ctx->ne, nthreads_for(n * n), ism>>>(D->d_S, D->d_w, D->d_Ainv);           \
+        k_var_invert<n><<<ctx->ne, nthreads_for(n * n), ism>>>(D->d_M, nullptr, D->d_Minv);          \
+        break;
+            GDG_VAR_CASES(X)
+#undef X
+        }
+        P.Ainv = D->d_Ainv;
+        P.Minv = D->d_Minv;
+    }
     if (P.mixed) {   // FP32 copies of the element matrices for the inner solves
         const size_t nm = nd * NA;
         if ((st = gdg_cuda_check(ctx, cudaMalloc((void **)&D->d_S32, nm * sizeof(float)), "alloc S32")) ||
@@ -286,7 +313,7 @@ int gdg_var_setup(gdg_ctx *ctx) {
 void gdg_var_free(gdg_ctx *ctx) {
     VarData *D = ctx->var;
     if (!D) return;
-    cudaFree(D->d_S); cudaFree(D->d_M); cudaFree(D->d_S32); cudaFree(D->d_M32); cudaFree(D->d_dS); cudaFree(D->d_w); cudaFree(D->d_pre); cudaFree(D->d_face);
+    cudaFree(D->d_S); cudaFree(D->d_M); cudaFree(D->d_S32); cudaFree(D->d_M32); cudaFree(D->d_dS); cudaFree(D->d_Ainv); cudaFree(D->d_Minv); cudaFree(D->d_w); cudaFree(D->d_pre); cudaFree(D->d_face);
     cudaFree(D->d_tab); cudaFree(D->d_nodes); cudaFree(D->d_state); cudaFree(D->d_tr);
     cudaFree(D->d_c2feat); cudaFree(D->d_wbf16); cudaFree(D->d_mlp);
     cudaFree(D->d_ru); cudaFree(D->d_rv); cudaFree(D->d_x0u);
@@ -487,6 +514,8 @@ extern "C" int gdg_mlp_attach(gdg_ctx *ctx, const uint16_t *w_bf16, const float 
     int st = require_var(ctx);
     if (st) return st;
     if (!w_bf16 || !params) return GDG_EINVAL;
+    if (ctx->pb.solver != GDG_SOLVE_PCG)
+        return gdg_set_err(ctx, GDG_EINVAL, "the learned guess needs GDG_SOLVE_PCG");
     VarData &D = *ctx->var;
     const size_t nd = (size_t)ctx->ndof;
     if (!D.d_wbf16 &&

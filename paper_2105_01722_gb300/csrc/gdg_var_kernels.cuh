@@ -18,6 +18,8 @@ struct VarParams {
     const double *S, *M, *w, *pre, *face;
     const float *S32, *M32;      // FP32 copies of S and M (mixed precision only)
     const double *dS;            // [ne][N1*N1] frozen-coefficient preconditioner diagonal (S system)
+    int inverse;                 // GDG_SOLVE_INVERSE: element inverses instead of PCG
+    const double *Ainv, *Minv;   // [ne][NA][NA] (S_c2 + w w^T)^-1 and M_J^-1 (exactly symmetric)
     unsigned long long *stats;   // [0] sum it_u, [1] sum it_v, [2] max it_u, [3] max it_v,
                                  // [4] unconverged u, [5] unconverged v, [6] element solves,
                                  // [7] sum sweeps u, [8] sum sweeps v, [9] max sweeps u, [10] max sweeps v
@@ -31,6 +33,7 @@ struct VarData {
     double *d_S = nullptr, *d_M = nullptr, *d_w = nullptr, *d_pre = nullptr, *d_face = nullptr;
     float *d_S32 = nullptr, *d_M32 = nullptr;
     double *d_dS = nullptr;
+    double *d_Ainv = nullptr, *d_Minv = nullptr;
     double *d_tab = nullptr, *d_nodes = nullptr;
     double *d_state = nullptr, *d_tr = nullptr;
     long long tr_len = 0;
@@ -729,22 +732,22 @@ struct StageSmem {
     double *A, *tb, *Yu, *Yv, *ru, *rv, *x, *r, *z, *p, *Ap, *w, *dS, *dM, *t1, *t2, *fw, *L, *red;
     // FP32 area (mixed precision only): matrix, preconditioner and PCG vectors
     float *A32, *Ps32, *dS32, *dM32, *w32, *r32, *z32, *p32, *Ap32, *c32, *u32, *v32, *t132, *t232;
-    __device__ StageSmem(double *base, int Q, bool mixed) {
+    __device__ StageSmem(double *base, int Q, bool mixed, bool no_matrix = false) {
         tb = base;   // tail of the 1-D tables (tab_tail_len)
         Yu = tb + tab_tail_len(Q, N1);
         Yv = Yu + NA; ru = Yv + NA; rv = ru + NA; x = rv + NA; r = x + NA; z = r + NA; p = z + NA;
         Ap = p + NA; w = Ap + NA; dS = w + NA; dM = dS + NA; t1 = dM + NA; t2 = t1 + NA;
         fw = t2 + NA; L = fw + 12 * Q; red = L + 12 * N1;
-        A = mixed ? nullptr : red + 32;
+        A = (mixed || no_matrix) ? nullptr : red + 32;
         A32 = reinterpret_cast<float *>(red + 32);
         Ps32 = A32 + NA * NA; dS32 = Ps32 + N1 * N1; dM32 = dS32 + NA; w32 = dM32 + NA;
         r32 = w32 + NA; z32 = r32 + NA; p32 = z32 + NA; Ap32 = p32 + NA; c32 = Ap32 + NA;
         u32 = c32 + NA; v32 = u32 + NA; t132 = v32 + NA; t232 = t132 + NA;
     }
-    static size_t bytes(int Q, bool mixed) {
+    static size_t bytes(int Q, bool mixed, bool no_matrix = false) {
         size_t d = sizeof(double) * ((size_t)tab_tail_len(Q, N1) + 14 * NA + 12 * Q + 12 * N1 + 32);
         if (mixed) d += sizeof(float) * ((size_t)NA * NA + N1 * N1 + 12 * NA);
-        else d += sizeof(double) * (size_t)NA * NA;
+        else if (!no_matrix) d += sizeof(double) * (size_t)NA * NA;
         return d;
     }
     __device__ SolveScratch32 scratch32(bool s_system) const {
@@ -824,7 +827,7 @@ template <int N1, int MODE>
 __device__ __forceinline__ void var_stage_body(const VarParams &P, const VarBufs &b, double cA, double cY, int e,
                                                double *smraw) {
     constexpr int NA = N1 * N1;
-    StageSmem<N1> s(smraw, P.Q, P.mixed);
+    StageSmem<N1> s(smraw, P.Q, P.mixed, P.inverse);
     const int t = threadIdx.x;
     const size_t off = (size_t)e * NA;
     const double *Sg = P.S + (size_t)e * NA * NA, *Mg = P.M + (size_t)e * NA * NA;
@@ -841,7 +844,7 @@ __device__ __forceinline__ void var_stage_body(const VarParams &P, const VarBufs
     if (!guess) {
         lifts<N1>(P, e, b.trin, T, s.fw, s.L, s.ru, s.rv);
         // stiffness: r_v -= S U
-        if (P.mixed) {
+        if (P.mixed || P.inverse) {
             matvec_g<NA>(Sg, s.Yu, s.Ap);
         } else {
             load_matrix<N1>(s.A, Sg);
@@ -858,9 +861,15 @@ __device__ __forceinline__ void var_stage_body(const VarParams &P, const VarBufs
         if (!P.mixed) load_matrix<N1>(s.A, Sg);
     }
     const bool none = P.precond == GDG_PC_NONE;
-    double rel_u, rel_v;
-    int it_u, it_v, sw_u = 0, sw_v = 0, fell = 0;
-    bool bad_u, bad_v;
+    double rel_u = 0.0, rel_v = 0.0;
+    int it_u = 0, it_v = 0, sw_u = 0, sw_v = 0, fell = 0;
+    bool bad_u = false, bad_v = false;
+    if (P.inverse) {
+        // y = (S_c2 + w w^T)^-1 r_u; dU/dt = V + y; dV/dt = M_J^-1 r_v
+        matvec_g<NA>(P.Ainv + (size_t)e * NA * NA, s.ru, s.x);
+        if (t < NA) s.ru[t] = s.Yv[t] + s.x[t];
+        matvec_g<NA>(P.Minv + (size_t)e * NA * NA, s.rv, s.x);
+    } else {
     if (P.mixed) {
         to_fp32<N1>(P.S32 + (size_t)e * NA * NA, s.A32, T.Ps, s.Ps32, s.dS, s.dS32, s.w, s.w32);
         sw_u = refine<N1, true>(Sg, s.w, s.ru, s.x, s.r, s.Ap, s.scratch32(true), s.red, P.rtol, P.refine_max,
@@ -885,6 +894,7 @@ __device__ __forceinline__ void var_stage_body(const VarParams &P, const VarBufs
         it_v = pcg<N1, false>(s.A, s.w, s.rv, s.x, s.r, s.z, s.p, s.Ap, T.Ps, s.dM, s.t1, s.t2, s.red, P.rtol,
                               P.maxit, none, true, &rel_v);
         bad_v = it_v >= P.maxit && rel_v > P.rtol;
+    }
     }
     if (t == 0 && P.stats) {
         atomicAdd(&P.stats[0], (unsigned long long)it_u);
@@ -947,7 +957,7 @@ __global__ void __launch_bounds__(nthreads_for(N1 * N1), kVarMinBlocks)
 k_var_pcg(VarParams P, int which, const double *bvec, double *xvec, int *iters, double *rel, int *sweeps) {
     constexpr int NA = N1 * N1;
     extern __shared__ double smraw[];
-    StageSmem<N1> s(smraw, P.Q, P.mixed);
+    StageSmem<N1> s(smraw, P.Q, P.mixed, false);
     const int e = blockIdx.x, t = threadIdx.x;
     const size_t off = (size_t)e * NA;
     load_tabs(s.tb, P.tab + 2 * P.Q * N1, tab_tail_len(P.Q, N1));
@@ -985,6 +995,77 @@ k_var_pcg(VarParams P, int which, const double *bvec, double *xvec, int *iters, 
         iters[e] = it;
         rel[e] = rr;
         if (sweeps) sweeps[e] = sw;
+    }
+}
+
+// Element inverse at setup (GDG_SOLVE_INVERSE; the precomputed-inverse route
+// of Section 3.1 applied to the element systems of Section 7.1):
+// Dst[e] = (Src[e] + w_e w_e^T)^-1 (w != nullptr) or Src[e]^-1, by Cholesky
+// A = L L^T in shared memory and one forward + back substitution per column
+// of the identity (thread j solves column j); the result is made exactly
+// symmetric (lower := upper) so that it can be applied by columns.
+template <int N1>
+__global__ void __launch_bounds__(nthreads_for(N1 * N1))
+k_var_invert(const double *__restrict__ Src, const double *__restrict__ w, double *__restrict__ Dst) {
+    constexpr int NA = N1 * N1;
+    extern __shared__ double sm[];
+    double *A = sm, *B = A + NA * NA, *dinv = B + NA * NA;
+    const int e = blockIdx.x, t = threadIdx.x, nt = blockDim.x;
+    const double *src = Src + (size_t)e * NA * NA;
+    const double *we = w ? w + (size_t)e * NA : nullptr;
+    for (int i = t; i < NA * NA; i += nt) {
+        const int r = i / NA, c = i - (i / NA) * NA;
+        A[i] = src[i] + (we ? we[r] * we[c] : 0.0);
+    }
+    __syncthreads();
+    // right-looking Cholesky, lower triangle in place
+    for (int k = 0; k < NA; ++k) {
+        if (t == 0) {
+            const double d = sqrt(A[k * NA + k]);
+            A[k * NA + k] = d;
+            dinv[k] = 1.0 / d;
+        }
+        __syncthreads();
+        const double di = dinv[k];
+        for (int i = k + 1 + t; i < NA; i += nt) A[i * NA + k] *= di;
+        __syncthreads();
+        const int m = NA - k - 1;
+        for (int idx = t; idx < m * m; idx += nt) {
+            const int i = k + 1 + idx / m, j = k + 1 + idx - (idx / m) * m;
+            if (j <= i) A[i * NA + j] -= A[i * NA + k] * A[j * NA + k];
+        }
+        __syncthreads();
+    }
+    if (t < NA) {
+        const int j = t;
+        // L z = e_j (z_i = 0 for i < j), then L^T x = z; column j of B
+        for (int i = 0; i < j; ++i) B[i * NA + j] = 0.0;
+        for (int i = j; i < NA; ++i) {
+            double s0 = (i == j) ? 1.0 : 0.0, s1 = 0.0;
+            int k = j;
+            for (; k + 1 < i; k += 2) {
+                s0 -= A[i * NA + k] * B[k * NA + j];
+                s1 -= A[i * NA + k + 1] * B[(k + 1) * NA + j];
+            }
+            if (k < i) s0 -= A[i * NA + k] * B[k * NA + j];
+            B[i * NA + j] = (s0 + s1) * dinv[i];
+        }
+        for (int i = NA - 1; i >= 0; --i) {
+            double s0 = B[i * NA + j], s1 = 0.0;
+            int k = i + 1;
+            for (; k + 1 < NA; k += 2) {
+                s0 -= A[k * NA + i] * B[k * NA + j];
+                s1 -= A[(k + 1) * NA + i] * B[(k + 1) * NA + j];
+            }
+            if (k < NA) s0 -= A[k * NA + i] * B[k * NA + j];
+            B[i * NA + j] = (s0 + s1) * dinv[i];
+        }
+    }
+    __syncthreads();
+    double *dst = Dst + (size_t)e * NA * NA;
+    for (int i = t; i < NA * NA; i += nt) {
+        const int r = i / NA, c = i - (i / NA) * NA;
+        dst[i] = r > c ? B[c * NA + r] : B[i];
     }
 }
 

@@ -16,7 +16,7 @@ OK, EINVAL, ENOMEM, ECUDA, ENOCONV, ETIMEOUT, ENONFINITE, EUNSUPPORTED = 0, -1, 
 BC_DIRICHLET, BC_PERIODIC = 0, 1
 FLUX_CENTRAL, FLUX_UPWIND = 0, 1
 COEF_CONST, COEF_NODAL = 0, 1
-SOLVE_DIAG, SOLVE_PCG = 0, 1
+SOLVE_DIAG, SOLVE_PCG, SOLVE_INVERSE = 0, 1, 2
 PC_FDM, PC_NONE = 0, 1
 FP64, MIXED = 0, 1
 ROUTE_MODAL, ROUTE_NODAL = 0, 1

@@ -92,6 +92,35 @@ def test_create_rejects_bad_problems(bad):
     assert not h
 
 
+def _nodal_kw(**extra):
+    import numpy as np
+    from paper_2105_01722_gb300 import inputs
+    X, Y = inputs.cartesian_nodes((2, 2), 8)
+    kw = dict(dim=2, n=(2, 2), N=8, p=5, coef=gdg.COEF_NODAL, x_nodes=X, y_nodes=Y,
+              c2_nodes=np.ones_like(X))
+    kw.update(extra)
+    return kw
+
+
+@pytest.mark.parametrize("kw, status", [
+    (dict(dim=2, n=(4, 4), N=8, p=5, route=gdg.ROUTE_NODAL), "EUNSUPPORTED"),    # modal route only
+    (dict(dim=2, n=(4, 4), N=8, p=5, precision=gdg.MIXED), "EUNSUPPORTED"),      # nothing to refine
+    ("inverse_mixed", "EUNSUPPORTED"),
+    ("nodal_diag", "EINVAL"),
+])
+def test_create_rejects_unbuilt_combinations(kw, status):
+    """Combinations that are not built are refused, never silently ignored."""
+    L = _lib()
+    if kw == "inverse_mixed":
+        kw = _nodal_kw(solver=gdg.SOLVE_INVERSE, precision=gdg.MIXED)
+    elif kw == "nodal_diag":
+        kw = _nodal_kw(solver=gdg.SOLVE_DIAG)
+    pb = gdg.make_problem(**kw)
+    h = ctypes.c_void_p()
+    assert L.gdg_create(ctypes.byref(pb), ctypes.byref(h)) == getattr(gdg, status)
+    assert not h
+
+
 def test_null_arguments():
     L = _lib()
     assert L.gdg_create(None, None) == gdg.EINVAL

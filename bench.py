@@ -249,7 +249,8 @@ def forms_variable(steps=16):
 def forms_batched(steps=8):
     """48 independent problems (seeds 20210501+i, n ~ U{16..128}, p in {3,5,7},
     alternating constant / smooth random c^2): one batch (persistent launches,
-    graph, tuned) against stepping each problem with its own gdg_step."""
+    graph, tuned) against stepping each problem with its own gdg_step; the
+    variable-coefficient problems by FP64 PCG, mixed PCG or element inverses."""
     import numpy as np
     import torch
     from paper_2105_01722_gb300 import gdg, inputs
@@ -257,7 +258,8 @@ def forms_batched(steps=8):
     cfl = {3: 0.2, 5: 0.15, 7: 0.12}
     dof = sum(sp["n"] ** 2 * 81 for sp in specs)
     out = {"problems": 48, "dof": dof}
-    for prec, name in ((gdg.FP64, "fp64"), (gdg.MIXED, "mixed")):
+    for prec, solver, name in ((gdg.FP64, gdg.SOLVE_PCG, "fp64"), (gdg.MIXED, gdg.SOLVE_PCG, "mixed"),
+                               (gdg.FP64, gdg.SOLVE_INVERSE, "inverse")):
         built = []
         for sp in specs:
             n, p = sp["n"], sp["p"]
@@ -265,7 +267,7 @@ def forms_batched(steps=8):
             if sp["variable"]:
                 C2 = inputs.smooth_random_c2(X, Y, sp["seed"])
                 pb = gdg.make_problem(2, (n, n), 8, p, coef=gdg.COEF_NODAL, x_nodes=X, y_nodes=Y, c2_nodes=C2,
-                                      pcg_rtol=1e-10, pcg_maxit=100, precision=prec)
+                                      pcg_rtol=1e-10, pcg_maxit=100, precision=prec, solver=solver)
                 cmax = float(np.sqrt(C2.max()))
             else:
                 pb = gdg.make_problem(2, (n, n), 8, p, c2=1.0)
@@ -384,6 +386,7 @@ def run_gdg(args):
     ms_per_step = total_ms / args.steps
     value = world * dof() * R * args.steps / (total_ms / 1e3)
 
+    stage_variant = ctx.stage_variant()
     # kernel-level pass: events around every launch (no graph), same work
     ctx.profile(True)
     for k in range(max(2, min(args.steps, 5))):
@@ -448,7 +451,9 @@ def run_gdg(args):
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                          "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
                          "traffic": STAGE_TRAFFIC_BYTES,
-                         "kernel": "k_stage2p (fused RK4 stage, modal route)", "avg_launch_us": stage_ms * 1e3,
+                         "kernel": ("k_stage2h" if stage_variant == 1 else "k_stage2p")
+                                   + " (fused RK4 stage, modal route; variant chosen by timing)",
+                         "avg_launch_us": stage_ms * 1e3,
                          "avg_launch_us_isolated": stage_ms_isolated * 1e3,
                          "duration_source": "timed region (CUDA events on the launching stream) less the step's "
                                             "entry/exit launches, over 4R stage launches; _isolated: events "

@@ -221,6 +221,19 @@ int gdg_step_host(gdg_ctx *ctx, double *u, double *v, double t0, double dt, int 
                   void *stream);
 
 /*
+ * Stage kernel of a 2-D constant-coefficient context (the modal route of
+ * Section 3.2; not a method choice, a launch choice): 0 = one thread per
+ * element line, 1 = two threads per line (even / odd modes), -1 = choose by
+ * timing both at the next gdg_step (the default).  Both variants perform the
+ * same floating-point operations in the same order: results are
+ * bit-identical.  Setting a variant drops any captured step graph.
+ * GDG_EINVAL on other contexts or values; get: the variant in use (-1 before
+ * the choice is made).
+ */
+int gdg_set_stage_variant(gdg_ctx *ctx, int variant);
+int gdg_get_stage_variant(const gdg_ctx *ctx, int *variant);
+
+/*
  * Discrete energy E = 1/2 sum_e (V_e^T M_e V_e + U_e^T S_e U_e) with S_e the
  * c^2-weighted stiffness (Section 6's energy norm squared, halved).
  * u, v device; *E host; synchronises stream.  GDG_ENONFINITE if E is not finite.

@@ -31,11 +31,14 @@ def _ms(fn):
     return a.elapsed_time(b)
 
 
-def case_const(n=64, N=8, p=5, steps=8, warmup=2):
-    """2-D constant coefficient standing mode, n x n elements, modal route."""
+def case_const(n=64, N=8, p=5, steps=8, warmup=2, variant=-1):
+    """2-D constant coefficient standing mode, n x n elements, modal route
+    (variant: stage kernel, -1 timed choice, 0 / 1 threads per line)."""
     import torch
     pb = gdg.make_problem(2, (n, n), N, p, flux=gdg.FLUX_UPWIND, c2=1.0)
     ctx = gdg.Context(pb)
+    if variant >= 0:
+        ctx.set_stage_variant(variant)
     X, Y = inputs.cartesian_nodes((n, n), N)
     U0, V0 = inputs.standing_mode_2d(X, Y)
     u = torch.tensor(U0.ravel(), device="cuda")
@@ -43,9 +46,10 @@ def case_const(n=64, N=8, p=5, steps=8, warmup=2):
     dt = CFL[p] / (n * N)
     ctx.step(u, v, 0.0, dt, warmup)
     ms = _ms(lambda: ctx.step(u, v, 0.0, dt, steps))
+    chosen = ctx.stage_variant()
     ctx.close()
     dof = n * n * (N + 1) ** 2
-    return {"case": "const", "n": n, "N": N, "p": p, "steps": steps, "ms": ms,
+    return {"case": "const", "n": n, "N": N, "p": p, "steps": steps, "variant": chosen, "ms": ms,
             "dof_steps_per_s": dof * steps / (ms / 1e3)}
 
 
@@ -151,10 +155,11 @@ def main(argv=None):
     ap.add_argument("--rows", type=int, default=4096)
     ap.add_argument("--sequential", action="store_true")
     ap.add_argument("--pmax", type=int, default=7)
+    ap.add_argument("--variant", type=int, default=-1, help="const: stage kernel (-1 timed, 0, 1)")
     a = ap.parse_args(argv)
     kw = {"steps": a.steps} if a.steps else {}
     if a.case == "const":
-        r = case_const(n=a.n or 64, p=a.p, **kw)
+        r = case_const(n=a.n or 64, p=a.p, variant=a.variant, **kw)
     elif a.case == "var":
         r = case_var(n=a.n or 32, p=a.p, mixed=a.mixed, inverse=a.inverse, **kw)
     elif a.case == "batch":

@@ -171,6 +171,14 @@ k_stage2p(const __grid_constant__ ModalParams mp, const StageBufs b, double cA, 
     stage2p_body<N1, MODE>(mp, b, cA, cY, blockIdx.x, smem);
 }
 
+// half-line variant (two threads per line), bit-identical results
+template <int N1, int MODE>
+__global__ void __launch_bounds__(MAXB2)
+k_stage2h(const __grid_constant__ ModalParams mp, const StageBufs b, double cA, double cY) {
+    extern __shared__ double smem[];
+    stage2h_body<N1, MODE>(mp, b, cA, cY, blockIdx.x, smem);
+}
+
 // traces of a modal state (start of gdg_step and gdg_rhs)
 template <int N1>
 __global__ void __launch_bounds__(MAXB2)
@@ -469,6 +477,17 @@ template <int N1>
 void launch_stage2(int mode, const ModalParams &mp, const StageBufs &b, double cA, double cY, cudaStream_t s) {
     dim3 grid((mp.ne + mp.epb - 1) / mp.epb), block(mp.epb * N1);
     size_t sm = smem_stage2(N1, mp.epb);
+    if (mp.parity && mp.split) {
+        const dim3 gh((mp.ne + mp.epbh - 1) / mp.epbh), bh(mp.epbh * 2 * N1);
+        const size_t smh = smem_stage2(N1, mp.epbh);
+        switch (mode) {
+        case M_RHS: k_stage2h<N1, M_RHS><<<gh, bh, smh, s>>>(mp, b, cA, cY); break;
+        case M_S1: k_stage2h<N1, M_S1><<<gh, bh, smh, s>>>(mp, b, cA, cY); break;
+        case M_S23: k_stage2h<N1, M_S23><<<gh, bh, smh, s>>>(mp, b, cA, cY); break;
+        default: k_stage2h<N1, M_S4><<<gh, bh, smh, s>>>(mp, b, cA, cY); break;
+        }
+        return;
+    }
     if (mp.parity) {
         switch (mode) {
         case M_RHS: k_stage2p<N1, M_RHS><<<grid, block, sm, s>>>(mp, b, cA, cY); break;
@@ -593,6 +612,10 @@ int set_smem_limits() {
     cudaFuncSetAttribute(k_stage2p<n, M_S1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);  \
     cudaFuncSetAttribute(k_stage2p<n, M_S23>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim); \
     cudaFuncSetAttribute(k_stage2p<n, M_S4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);  \
+    cudaFuncSetAttribute(k_stage2h<n, M_RHS>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim); \
+    cudaFuncSetAttribute(k_stage2h<n, M_S1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);  \
+    cudaFuncSetAttribute(k_stage2h<n, M_S23>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim); \
+    cudaFuncSetAttribute(k_stage2h<n, M_S4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);  \
     cudaFuncSetAttribute(k_traces2<n>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);        \
     cudaFuncSetAttribute(k_sep2<n>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     GDG_N1_CASES(X)
@@ -603,11 +626,11 @@ int set_smem_limits() {
 
 // Elements per block of the 2-D kernels: maximise (used warp lanes) x
 // (balance of elements over the SMs), with up to `resident` blocks per SM.
-int choose_epb(int ne, int n1, int sms) {
+int choose_epb(int ne, int n1, int sms, int tpe) {
     int best = 1;
     double best_eff = -1.0;
-    for (int epb = 1; epb * n1 <= MAXB2; ++epb) {
-        const int threads = epb * n1;
+    for (int epb = 1; epb * tpe <= MAXB2; ++epb) {
+        const int threads = epb * tpe;
         const int warps = (threads + 31) / 32;
         const double lanes = (double)threads / (32.0 * warps);
         const size_t sm = smem_stage2(n1, epb);
@@ -738,7 +761,9 @@ int gdg_const_setup(gdg_ctx *ctx) {
     }
     int sms = 152;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
-    mp.epb = ctx->dim == 2 ? choose_epb(ctx->ne, n1, sms) : 1;
+    mp.epb = ctx->dim == 2 ? choose_epb(ctx->ne, n1, sms, n1) : 1;
+    mp.epbh = ctx->dim == 2 ? choose_epb(ctx->ne, n1, sms, 2 * n1) : 1;
+    mp.split = 0;   // decided by timing at the first gdg_step
     const int ents = ctx->dim == 2 ? nn : n1;
     std::vector<double> l2((size_t)2 * ents, 0.0);
     for (int m = 0; m < ents; ++m) {
@@ -798,11 +823,62 @@ int gdg_const_mass_solve(gdg_ctx *ctx, int which, const double *b, double *x, cu
     return gdg_cuda_check(ctx, cudaGetLastError(), "gdg_mass_solve launch");
 }
 
+// Pick the stage kernel of a 2-D parity context by timing: one line per
+// thread (k_stage2p) or two (k_stage2h).  Both compute bit-identical results;
+// the trial stage-1 launches write only buffers the step then rewrites.
+int tune_stage_kernel(gdg_ctx *ctx, double dt, cudaStream_t s) {
+    ModalParams &mp = ctx->mp;
+    ctx->stage_tuned = true;
+    if (ctx->dim != 2 || !mp.parity) return GDG_OK;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    StageBufs b{};
+    b.nU = buf(ctx, B_NU); b.nV = buf(ctx, B_NV);
+    b.aU = buf(ctx, B_AU); b.aV = buf(ctx, B_AV);
+    b.lam2 = ctx->d_lam2;
+    b.yU = b.nU; b.yV = b.nV; b.oU = buf(ctx, B_XU); b.oV = buf(ctx, B_XV);
+    b.trin = ctx->d_tr; b.trout = ctx->d_tr + ctx->tr_len;
+    float ms[2] = {0.f, 0.f};
+    for (int split = 0; split < 2; ++split) {
+        mp.split = split;
+        for (int rep = 0; rep < 3; ++rep) {
+            cudaEventRecord(e0, s);
+            for (int i = 0; i < 4; ++i) launch_stage_raw(ctx, M_S1, b, dt / 6.0, 0.5 * dt, s);
+            cudaEventRecord(e1, s);
+            cudaEventSynchronize(e1);
+            cudaEventElapsedTime(&ms[split], e0, e1);
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    mp.split = ms[1] < ms[0] ? 1 : 0;
+    return gdg_cuda_check(ctx, cudaGetLastError(), "stage kernel choice");
+}
+
+extern "C" int gdg_set_stage_variant(gdg_ctx *ctx, int variant) {
+    if (!ctx || ctx->var || ctx->dim != 2 || !ctx->mp.parity || variant < -1 || variant > 1) return GDG_EINVAL;
+    if (ctx->graph.exec) {
+        cudaGraphExecDestroy(ctx->graph.exec);
+        ctx->graph.exec = nullptr;
+    }
+    ctx->stage_tuned = variant >= 0;
+    ctx->mp.split = variant > 0 ? 1 : 0;
+    return GDG_OK;
+}
+
+extern "C" int gdg_get_stage_variant(const gdg_ctx *ctx, int *variant) {
+    if (!ctx || !variant || ctx->var || ctx->dim != 2 || !ctx->mp.parity) return GDG_EINVAL;
+    *variant = ctx->stage_tuned ? ctx->mp.split : -1;
+    return GDG_OK;
+}
+
 int gdg_const_step(gdg_ctx *ctx, double *u, double *v, double dt, int nsteps, cudaStream_t s) {
     int st;
     launch_sep(ctx, u, v, buf(ctx, B_NU), buf(ctx, B_NV), T_P, nullptr, -1, s);
     launch_traces(ctx, buf(ctx, B_NU), buf(ctx, B_NV), ctx->d_tr, s);
     if ((st = gdg_cuda_check(ctx, cudaGetLastError(), "gdg_step prologue"))) return st;
+    if (!ctx->stage_tuned && (st = tune_stage_kernel(ctx, dt, s))) return st;
     // graph of G steps, replayed; the remainder is launched directly
     const int G = (nsteps >= 16 && !ctx->prof.on) ? 16 : 0;
     if (G) {

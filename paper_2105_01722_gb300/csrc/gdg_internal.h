@@ -31,6 +31,8 @@ struct ModalParams {
     double beta2, tau2;   // 2 beta, 2 tau
     int parity;           // modes ordered even (r -> 1-r symmetric) first: eR = +-eL, gR = +-gL
     int epb;              // elements per block of the 2-D kernels
+    int epbh;             // elements per block of the half-line stage kernel (2 N1 threads each)
+    int split;            // parity stage launches use the half-line kernel (chosen by timing)
 };
 
 // RK4 stage modes of the stage kernels
@@ -83,6 +85,7 @@ struct gdg_ctx {
     double *h_red = nullptr;      // pinned host scalar(s)
     cudaStream_t cap_stream = nullptr;
     GraphCache graph;
+    bool stage_tuned = false;     // stage kernel variant chosen (first gdg_step)
 
     VarData *var = nullptr;
     Profiler prof;

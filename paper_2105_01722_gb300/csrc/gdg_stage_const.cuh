@@ -193,4 +193,211 @@ __device__ __forceinline__ void stage2p_body(const ModalParams &mp, const StageB
     }
 }
 
+// Half-line variant of stage2p_body: two threads per transverse line, lane
+// pair (2m, 2m+1), the even one (h = 0) owning the NE even modes k < NE and
+// the odd one (h = 1) the odd modes k >= NE.  Every floating-point operation
+// is the one stage2p_body performs, in the same order, so the two bodies give
+// bit-identical results; a pair swaps face fluxes and trace partial sums by
+// one shuffle.  Twice the threads and half the registers per element: more
+// warps per SM to hide FP64 and shared-memory latency on small meshes.
+// blockDim.x = epb * 2 * N1 (even, so a pair never straddles a warp).
+__device__ __forceinline__ unsigned pair_mask() {
+    const int lanes = min(32, (int)blockDim.x - (int)(threadIdx.x & ~31u));
+    return lanes >= 32 ? 0xffffffffu : ((1u << lanes) - 1u);
+}
+
+template <int N1, int MODE>
+__device__ __forceinline__ void stage2h_body(const ModalParams &mp, const StageBufs &b, double cA, double cY,
+                                             int etile, double *smem) {
+    constexpr int NE = (N1 + 1) / 2;   // even modes; the odd half has N1 - NE <= NE entries
+    const int epb = blockDim.x / (2 * N1);
+    const int t = threadIdx.x;
+    const int le = t / (2 * N1), rr = t - le * (2 * N1);
+    const int l = rr >> 1, h = rr & 1;
+    const int k0 = h ? NE : 0, nk = h ? N1 - NE : NE;
+    const int e = etile * epb + le;
+    const bool valid = le < epb && e < mp.ne;
+    const unsigned mask = pair_mask();
+    double *fy = smem + (le < epb ? le : 0) * (4 * N1);
+    double *tile = smem + epb * 4 * N1 + (le < epb ? le : 0) * (2 * N1 * (N1 + 1));
+    const int nx = mp.nx, ny = mp.ny;
+    const int ex = valid ? e % nx : 0, ey = valid ? e / nx : 0;
+    const double b2 = mp.beta2, t2 = mp.tau2;
+    const size_t row = ((size_t)(valid ? e : 0) * N1 + l) * N1 + k0;
+
+    double Ru[NE], Rv[NE], Nu[NE], Nv[NE], Au[NE], Av[NE];
+    if (valid) {
+#pragma unroll
+        for (int kk = 0; kk < NE; ++kk) {
+            if (kk < nk) {
+                Ru[kk] = b.yU[row + kk];
+                Rv[kk] = b.yV[row + kk];
+                if (MODE == M_S23 || MODE == M_S4) {
+                    Nu[kk] = b.nU[row + kk];
+                    Nv[kk] = b.nV[row + kk];
+                    Au[kk] = b.aU[row + kk];
+                    Av[kk] = b.aV[row + kk];
+                }
+            }
+        }
+    }
+
+    // fluxes: h = 0 the minus face, h = 1 the plus face of each direction
+    double gx = 0, qx = 0, gy = 0, qy = 0;
+    if (valid) {
+        const double *T = b.trin;
+        double vi, di, vo, dO, d1;
+        int en, f;
+        if (h == 0) {   // x-, transverse mode l
+            vi = T[tix2<N1>(e, 0, 0, l)]; di = T[tix2<N1>(e, 0, 1, l)];
+            en = ex - 1;
+            if (en < 0 && mp.per_x) en += nx;
+            if (en >= 0) { f = ey * nx + en; vo = T[tix2<N1>(f, 1, 0, l)]; dO = T[tix2<N1>(f, 1, 1, l)]; }
+            else { vo = -vi; dO = -di; }
+        } else {        // x+
+            vi = T[tix2<N1>(e, 1, 0, l)]; di = T[tix2<N1>(e, 1, 1, l)];
+            en = ex + 1;
+            if (en >= nx && mp.per_x) en -= nx;
+            if (en < nx) { f = ey * nx + en; vo = T[tix2<N1>(f, 0, 0, l)]; dO = T[tix2<N1>(f, 0, 1, l)]; }
+            else { vo = -vi; dO = -di; }
+        }
+        d1 = vo - vi;
+        gx = fma(-b2, di + dO, d1);
+        qx = fma(t2, d1, di - dO);
+        if (h == 0) {   // y-, transverse mode l
+            vi = T[tix2<N1>(e, 2, 0, l)]; di = T[tix2<N1>(e, 2, 1, l)];
+            en = ey - 1;
+            if (en < 0 && mp.per_y) en += ny;
+            if (en >= 0) { f = en * nx + ex; vo = T[tix2<N1>(f, 3, 0, l)]; dO = T[tix2<N1>(f, 3, 1, l)]; }
+            else { vo = -vi; dO = -di; }
+        } else {        // y+
+            vi = T[tix2<N1>(e, 3, 0, l)]; di = T[tix2<N1>(e, 3, 1, l)];
+            en = ey + 1;
+            if (en >= ny && mp.per_y) en -= ny;
+            if (en < ny) { f = en * nx + ex; vo = T[tix2<N1>(f, 2, 0, l)]; dO = T[tix2<N1>(f, 2, 1, l)]; }
+            else { vo = -vi; dO = -di; }
+        }
+        d1 = vo - vi;
+        gy = fma(-b2, di + dO, d1);
+        qy = fma(t2, d1, di - dO);
+    }
+    const double ogx = __shfl_xor_sync(mask, gx, 1), oqx = __shfl_xor_sync(mask, qx, 1);
+    const double ogy = __shfl_xor_sync(mask, gy, 1), oqy = __shfl_xor_sync(mask, qy, 1);
+    // g2m, g2p of each direction in the order of stage2p_body
+    const double g2mx = h ? ogx : gx, g2px = h ? gx : ogx, q2mx = h ? oqx : qx, q2px = h ? qx : oqx;
+    const double g2my = h ? ogy : gy, g2py = h ? gy : ogy, q2my = h ? oqy : qy, q2py = h ? qy : oqy;
+    // x fluxes of this half's parity (GA, QA even; GB, QB odd)
+    const double xg = h ? g2mx - g2px : g2mx + g2px;
+    const double xq = h ? q2mx - q2px : q2mx + q2px;
+    if (valid) {
+        if (h == 0) { fy[l] = g2my + g2py; fy[2 * N1 + l] = q2my + q2py; }
+        else { fy[N1 + l] = g2my - g2py; fy[3 * N1 + l] = q2my - q2py; }
+    }
+    __syncthreads();
+
+    if (valid) {
+        const double *L0 = b.lam2 + l * N1 + k0;
+        const double *L1 = b.lam2 + N1 * N1 + l * N1 + k0;
+        const double hgy = mp.d[1].hgL[l], cey = mp.d[1].ceL[l];
+        const double *FG = fy + (l < NE ? 0 : N1) + k0;
+        const double *FQ = fy + (l < NE ? 2 * N1 : 3 * N1) + k0;
+        const double *hgx = mp.d[0].hgL + k0, *cex = mp.d[0].ceL + k0;
+#pragma unroll
+        for (int kk = 0; kk < NE; ++kk) {
+            if (kk < nk) {
+                const double Yu = Ru[kk], Yv = Rv[kk];
+                const double ru = fma(hgx[kk], xg, hgy * FG[kk]);
+                const double rv = fma(L0[kk], Yu, fma(cex[kk], xq, cey * FQ[kk]));
+                const double ku = fma(L1[kk], ru, Yv);
+                const double kv = rv;
+                const size_t o = row + kk;
+                if (MODE == M_RHS) {
+                    b.oU[o] = ku;
+                    b.oV[o] = kv;
+                } else if (MODE == M_S1) {
+                    b.aU[o] = cA * ku;
+                    b.aV[o] = cA * kv;
+                    Ru[kk] = fma(cY, ku, Yu);
+                    Rv[kk] = fma(cY, kv, Yv);
+                } else if (MODE == M_S23) {
+                    b.aU[o] = fma(cA, ku, Au[kk]);
+                    b.aV[o] = fma(cA, kv, Av[kk]);
+                    Ru[kk] = fma(cY, ku, Nu[kk]);
+                    Rv[kk] = fma(cY, kv, Nv[kk]);
+                } else {
+                    Ru[kk] = fma(cA, ku, Nu[kk] + Au[kk]);
+                    Rv[kk] = fma(cA, kv, Nv[kk] + Av[kk]);
+                }
+            }
+        }
+        if (MODE != M_RHS) {
+            double *dU = (MODE == M_S4) ? b.nU : b.oU;
+            double *dV = (MODE == M_S4) ? b.nV : b.oV;
+#pragma unroll
+            for (int kk = 0; kk < NE; ++kk)
+                if (kk < nk) { dU[row + kk] = Ru[kk]; dV[row + kk] = Rv[kk]; }
+        }
+    }
+    if (MODE == M_RHS) return;
+
+    // x-face traces: this half's partial dots (even: ve, de; odd: vo, do)
+    double pv = 0, pd = 0;
+    if (valid) {
+        const double *eLx = mp.d[0].eL + k0, *gLx = mp.d[0].gL + k0;
+#pragma unroll
+        for (int kk = 0; kk < NE; ++kk) {
+            if (kk < nk) {
+                pv = fma(eLx[kk], Rv[kk], pv);
+                pd = fma(gLx[kk], Ru[kk], pd);
+                tile[l * (N1 + 1) + k0 + kk] = Ru[kk];
+                tile[N1 * (N1 + 1) + l * (N1 + 1) + k0 + kk] = Rv[kk];
+            }
+        }
+    }
+    {
+        const double opv = __shfl_xor_sync(mask, pv, 1), opd = __shfl_xor_sync(mask, pd, 1);
+        const double ve = h ? opv : pv, de = h ? opd : pd, vo_ = h ? pv : opv, do_ = h ? pd : opd;
+        if (valid) {
+            if (h == 0) {
+                b.trout[tix2<N1>(e, 0, 0, l)] = ve + vo_;
+                b.trout[tix2<N1>(e, 0, 1, l)] = de + do_;
+            } else {
+                b.trout[tix2<N1>(e, 1, 0, l)] = ve - vo_;
+                b.trout[tix2<N1>(e, 1, 1, l)] = de - do_;
+            }
+        }
+    }
+    __syncthreads();
+    // y-face traces of column k = l: this half's rows j (even j < NE, odd j >= NE)
+    pv = 0;
+    pd = 0;
+    if (valid) {
+        const int k = l;
+        const double *eLy = mp.d[1].eL + k0, *gLy = mp.d[1].gL + k0;
+#pragma unroll
+        for (int jj = 0; jj < NE; ++jj) {
+            if (jj < nk) {
+                const int j = k0 + jj;
+                const double u = tile[j * (N1 + 1) + k], v = tile[N1 * (N1 + 1) + j * (N1 + 1) + k];
+                pv = fma(eLy[jj], v, pv);
+                pd = fma(gLy[jj], u, pd);
+            }
+        }
+    }
+    {
+        const double opv = __shfl_xor_sync(mask, pv, 1), opd = __shfl_xor_sync(mask, pd, 1);
+        const double ve = h ? opv : pv, de = h ? opd : pd, vo_ = h ? pv : opv, do_ = h ? pd : opd;
+        if (valid) {
+            const int k = l;
+            if (h == 0) {
+                b.trout[tix2<N1>(e, 2, 0, k)] = ve + vo_;
+                b.trout[tix2<N1>(e, 2, 1, k)] = de + do_;
+            } else {
+                b.trout[tix2<N1>(e, 3, 0, k)] = ve - vo_;
+                b.trout[tix2<N1>(e, 3, 1, k)] = de - do_;
+            }
+        }
+    }
+}
+
 }  // namespace

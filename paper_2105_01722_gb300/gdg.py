@@ -86,6 +86,8 @@ EXPORTS = {
     "gdg_rhs_static": (ctypes.c_int, [ctypes.POINTER(Problem)] + [ctypes.c_void_p] * 5),
     "gdg_step_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(PcgStats), ctypes.POINTER(PcgStats)]),
     "gdg_profile_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "gdg_set_stage_variant": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "gdg_get_stage_variant": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
     "gdg_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
                                         ctypes.POINTER(ctypes.c_double)]),
 }
@@ -288,6 +290,15 @@ class Context:
             return ctypes.c_void_p(a.data_ptr())
         self._check(lib().gdg_step_host(self._h, hp(u), hp(v), t0, dt, nsteps, _stream(stream)),
                     "gdg_step_host")
+
+    def set_stage_variant(self, variant):
+        """2-D constant coefficient: 0 one thread per line, 1 two, -1 timed choice."""
+        self._check(lib().gdg_set_stage_variant(self._h, int(variant)), "gdg_set_stage_variant")
+
+    def stage_variant(self):
+        out = ctypes.c_int()
+        self._check(lib().gdg_get_stage_variant(self._h, ctypes.byref(out)), "gdg_get_stage_variant")
+        return out.value
 
     def profile(self, on):
         self._check(lib().gdg_profile_enable(self._h, 1 if on else 0), "gdg_profile_enable")

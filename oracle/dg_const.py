@@ -15,6 +15,14 @@ the fluxes of Section 2.2.1 with alpha = 1/2 in normal form are
   v*  = (v_in + v_out)/2 - beta (d_in + d_out)
   q*  = n . (grad u)* = (d_in - d_out)/2 - tau (v_in - v_out)
 central: beta = tau = 0; upwind: beta = xi/2, tau = 1/(2 xi).
+Alternating flux (Section 2.2.1, alpha = 1, beta = tau = 0): v* = v^1 and
+(grad u)* = grad u^2.  With the sides labelled by a fixed orientation (side 1
+= the left / lower element of a face), an element's - face has it on side 2
+and its + face on side 1:
+  - face:  v* = v_out,  q* = d_in;      + face:  v* = v_in,  q* = -d_out,
+so both elements of a face use the same v* and (grad u)*.  On a Dirichlet
+side the closure is v* = 0, q* = d_in (what the mirror state gives the
+central flux), which keeps the scheme conservative.
 Then (c^2 constant, divided out of Eq. DG1):
   r_u = sum_faces (n . grad phi)|face (x) M_perp (v* - v_in)
   r_v = -c^2 S U + sum_faces c^2 phi|face (x) M_perp q*
@@ -43,7 +51,7 @@ class Problem:
     lo: tuple = (0.0, 0.0)
     hi: tuple = (1.0, 1.0)
     periodic: tuple = (False, False)
-    flux: str = "upwind"   # "central" | "upwind"
+    flux: str = "upwind"   # "central" | "upwind" | "alternating"
     xi: float = 0.0        # upwind splitting; <= 0 means xi = c
     c2: float = 1.0
 
@@ -55,7 +63,7 @@ class Problem:
         return (self.hi[k] - self.lo[k]) / self.n[k]
 
     def beta_tau(self):
-        if self.flux == "central":
+        if self.flux in ("central", "alternating"):
             return 0.0, 0.0
         if self.flux == "upwind":
             xi = self.xi if self.xi > 0 else np.sqrt(self.c2)
@@ -94,10 +102,32 @@ def operators(prob):
     return ops
 
 
-def _fluxes(v_in, d_in, v_out, d_out, beta, tau):
-    vstar = 0.5 * (v_in + v_out) - beta * (d_in + d_out)
-    qstar = 0.5 * (d_in - d_out) - tau * (v_in - v_out)
+def _fluxes(v_in, d_in, v_out, d_out, beta, tau, alt=None, bnd=None):
+    """(v*, q*) on one face of every element.  alt: None (alpha = 1/2), or
+    "minus" / "plus" for the alternating flux on the element's - / + face,
+    with bnd marking the faces on a Dirichlet side."""
+    if alt is None:
+        vstar = 0.5 * (v_in + v_out) - beta * (d_in + d_out)
+        qstar = 0.5 * (d_in - d_out) - tau * (v_in - v_out)
+        return vstar, qstar
+    if alt == "minus":            # this element is side 2 of the face
+        vstar, qstar = v_out.copy(), d_in.copy()
+    else:                         # side 1
+        vstar, qstar = v_in.copy(), -d_out
+    if bnd is not None:
+        vstar = np.where(bnd, 0.0, vstar)
+        qstar = np.where(bnd, d_in, qstar)
     return vstar, qstar
+
+
+def _boundary_masks(shape, periodic):
+    """Masks of the - and + faces on a Dirichlet side (element axis first)."""
+    bm = np.zeros(shape, dtype=bool)
+    bp = np.zeros(shape, dtype=bool)
+    if not periodic:
+        bm[0] = True
+        bp[-1] = True
+    return bm, bp
 
 
 def _neighbour_traces(vm, dm, vp, dp, periodic):
@@ -122,6 +152,7 @@ def residuals(prob, U, V, ops=None):
     """(r_u, r_v) of the element equations for nodal states U, V."""
     ops = operators(prob) if ops is None else ops
     beta, tau = prob.beta_tau()
+    alt = prob.flux == "alternating"
     c2 = prob.c2
     n1 = prob.n1
     if prob.dim == 1:
@@ -131,8 +162,9 @@ def residuals(prob, U, V, ops=None):
         vm, vp = V[:, 0], V[:, -1]
         dm, dp = U @ aL, U @ aR
         om_v, om_d, op_v, op_d = _neighbour_traces(vm, dm, vp, dp, prob.periodic[0])
-        vs_m, qs_m = _fluxes(vm, dm, om_v, om_d, beta, tau)
-        vs_p, qs_p = _fluxes(vp, dp, op_v, op_d, beta, tau)
+        bm, bp = _boundary_masks(vm.shape, prob.periodic[0])
+        vs_m, qs_m = _fluxes(vm, dm, om_v, om_d, beta, tau, *(("minus", bm) if alt else ()))
+        vs_p, qs_p = _fluxes(vp, dp, op_v, op_d, beta, tau, *(("plus", bp) if alt else ()))
         r_u = np.outer(vs_m - vm, aL) + np.outer(vs_p - vp, aR)
         r_v = -c2 * U @ ops.S.T
         r_v[:, 0] += c2 * qs_m
@@ -154,8 +186,9 @@ def residuals(prob, U, V, ops=None):
     t = [np.swapaxes(a, 0, 1) for a in (vm, dm, vp, dp)]   # element axis first
     om_v, om_d, op_v, op_d = [np.swapaxes(a, 0, 1) for a in
                               _neighbour_traces(*t, prob.periodic[0])]
-    vs_m, qs_m = _fluxes(vm, dm, om_v, om_d, beta, tau)
-    vs_p, qs_p = _fluxes(vp, dp, op_v, op_d, beta, tau)
+    bm, bp = [np.swapaxes(a, 0, 1) for a in _boundary_masks(t[0].shape, prob.periodic[0])]
+    vs_m, qs_m = _fluxes(vm, dm, om_v, om_d, beta, tau, *(("minus", bm) if alt else ()))
+    vs_p, qs_p = _fluxes(vp, dp, op_v, op_d, beta, tau, *(("plus", bp) if alt else ()))
     gm = (vs_m - vm) @ My.T            # M_y (v* - v_in), per element
     gp = (vs_p - vp) @ My.T
     r_u += np.einsum("yxj,i->yxji", gm, aL) + np.einsum("yxj,i->yxji", gp, aR)
@@ -168,8 +201,9 @@ def residuals(prob, U, V, ops=None):
     dm = np.einsum("yxji,j->yxi", U, aL)
     dp = np.einsum("yxji,j->yxi", U, aR)
     om_v, om_d, op_v, op_d = _neighbour_traces(vm, dm, vp, dp, prob.periodic[1])
-    vs_m, qs_m = _fluxes(vm, dm, om_v, om_d, beta, tau)
-    vs_p, qs_p = _fluxes(vp, dp, op_v, op_d, beta, tau)
+    bm, bp = _boundary_masks(vm.shape, prob.periodic[1])
+    vs_m, qs_m = _fluxes(vm, dm, om_v, om_d, beta, tau, *(("minus", bm) if alt else ()))
+    vs_p, qs_p = _fluxes(vp, dp, op_v, op_d, beta, tau, *(("plus", bp) if alt else ()))
     gm = (vs_m - vm) @ Mx.T
     gp = (vs_p - vp) @ Mx.T
     r_u += np.einsum("yxi,j->yxji", gm, aL) + np.einsum("yxi,j->yxji", gp, aR)

@@ -24,6 +24,10 @@ Readings made here (the paper leaves them open):
   p+1, exact for affine elements with constant c^2);
 * upwind splitting xi = c at each face point unless a constant xi > 0 is
   given; c^2 on a face is the inside element's trace;
+* alternating flux (alpha = 1): sides labelled by a fixed orientation (side
+  1 = the element with the smaller reference index across the face), so on
+  an element's xm / ym face v* = v_out, q* = d_in and on its xp / yp face
+  v* = v_in, q* = -d_out; on a Dirichlet side v* = 0, q* = d_in;
 * the constrained u_t system is solved in the equivalent SPD form
   (S_c2 + w w^T) y = r_u (its solution satisfies S_c2 y = r_u, w^T y = 0
   because 1^T r_u = 0); the extra equation of Eq. DG1_extra is weighted by
@@ -186,7 +190,7 @@ def _neighbour(vp, ey, ex, face):
 
 
 def _beta_tau(vp, c):
-    if vp.flux == "central":
+    if vp.flux in ("central", "alternating"):
         return 0.0 * c, 0.0 * c
     if vp.flux != "upwind":
         raise ValueError("unknown flux")
@@ -219,8 +223,15 @@ def residuals(vp, ops, U, V, forcing=None):
                     v_out = ops.Tv[f2] @ V[e2]
                     d_out = ops.Tn[f2][e2] @ U[e2]
                 beta, tau = _beta_tau(vp, ops.c[f][e])
-                vstar = 0.5 * (v_in + v_out) - beta * (d_in + d_out)
-                qstar = 0.5 * (d_in - d_out) - tau * (v_in - v_out)
+                if vp.flux != "alternating":
+                    vstar = 0.5 * (v_in + v_out) - beta * (d_in + d_out)
+                    qstar = 0.5 * (d_in - d_out) - tau * (v_in - v_out)
+                elif nb is None:                 # Dirichlet side: v* = 0, q* = d_in
+                    vstar, qstar = 0.0 * v_in, d_in
+                elif f in ("xm", "ym"):          # element on side 2 (right / upper)
+                    vstar, qstar = v_out, d_in
+                else:                            # element on side 1 (left / lower)
+                    vstar, qstar = v_in, -d_out
                 cw = ops.cw[f][e]
                 r_u[e] += ops.Tn[f][e].T @ (cw * (vstar - v_in))
                 r_v[e] += ops.Tv[f].T @ (cw * qstar)

@@ -36,6 +36,22 @@ def test_central_flux_conserves_energy(case):
 
 
 @pytest.mark.parametrize("case", TINY)
+def test_alternating_flux_conserves_energy(case):
+    """Alternating flux (alpha = 1, sides by a fixed orientation, Dirichlet
+    closure v* = 0, q* = d_in): conservative like the central flux, E L +
+    L^T E = 0 and an imaginary spectrum, yet a different operator."""
+    prob = _prob(case, "alternating")
+    L = dc.dense_operator(prob)
+    E = dc.energy_matrix(prob)
+    A = E @ L + L.T @ E
+    assert np.abs(A).max() < 1e-11 * np.abs(E @ L).max()
+    ev = np.linalg.eigvals(L)
+    assert np.abs(ev.real).max() < 1e-8 * np.abs(ev).max()
+    Lc = dc.dense_operator(_prob(case, "central"))
+    assert np.abs(L - Lc).max() > 1e-3 * np.abs(Lc).max()
+
+
+@pytest.mark.parametrize("case", TINY)
 def test_upwind_flux_dissipates(case):
     prob = _prob(case, "upwind")
     L = dc.dense_operator(prob)
@@ -203,7 +219,7 @@ def _run_1d(n, p, N, flux, T, cfl):
     return ti.errors(prob, U, V, _standing_wave_1d, T), h
 
 
-@pytest.mark.parametrize("flux", ["central", "upwind"])
+@pytest.mark.parametrize("flux", ["central", "upwind", "alternating"])
 @pytest.mark.parametrize("p", [3, 5])
 def test_convergence_1d_dirichlet(flux, p):
     """Exact standing wave cos(2 pi t) sin(2 pi x), Dirichlet: the L2 error
@@ -211,6 +227,32 @@ def test_convergence_1d_dirichlet(flux, p):
     errs = [_run_1d(n, p, 8, flux, 0.25, 0.05)[0][0] for n in (2, 4, 8)]
     rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
     assert rates.min() > p + 0.5, (errs, rates)
+
+
+def _travelling_wave_1d(t, x):
+    w = 2 * np.pi
+    return (np.sin(w * (x - t)), [w * np.cos(w * (x - t))], -w * np.cos(w * (x - t)))
+
+
+@pytest.mark.parametrize("p", [3, 5])
+def test_convergence_1d_periodic_alternating(p):
+    """Section 6's periodic test for the alternating flux (Tables 1, 2 report
+    L2 rates of about p+1 for p >= 3): travelling wave sin 2pi(x - t) on a
+    periodic mesh, elements added at N = 8."""
+    errs = []
+    for n in (2, 4, 8):
+        prob = dc.Problem(dim=1, n=(n,), N=8, p=p, flux="alternating", periodic=(True,))
+        ops = dc.operators(prob)
+        (X,) = dc.node_coordinates(prob)
+        U, V = np.sin(2 * np.pi * X), -2 * np.pi * np.cos(2 * np.pi * X)
+        h = prob.H(0) / 8
+        T = 0.25
+        steps = int(np.ceil(T / (0.05 * h)))
+        f = lambda t, U, V: dc.time_derivative(prob, U, V, ops)
+        U, V = ti.integrate(f, U, V, 0.0, T / steps, steps)
+        errs.append(ti.errors(prob, U, V, _travelling_wave_1d, T)[0])
+    rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert rates.min() > p + 0.3, (errs, rates)
 
 
 def test_config0_energy_and_error():

@@ -35,7 +35,7 @@ def _dense(vp, ops):
     return L, E
 
 
-@pytest.mark.parametrize("flux", ["central", "upwind"])
+@pytest.mark.parametrize("flux", ["central", "upwind", "alternating"])
 @pytest.mark.parametrize("periodic", [(False, False), (True, False), (False, True)])
 def test_reduces_to_cartesian_constant(flux, periodic):
     """Affine (Cartesian) geometry and constant c^2: the quadrature route
@@ -65,6 +65,15 @@ def test_reduces_to_cartesian_constant(flux, periodic):
 @pytest.mark.parametrize("c2", ["sine", "random"])
 def test_central_conserves_energy_mapped(c2):
     vp = _var_problem((2, 2), 3, 3, flux="central", amp=0.05, c2=c2)
+    ops = dv.assemble(vp)
+    L, E = _dense(vp, ops)
+    A = E @ L + L.T @ E
+    assert np.abs(A).max() < 1e-10 * np.abs(E @ L).max()
+
+
+@pytest.mark.parametrize("periodic", [(False, False), (True, False)])
+def test_alternating_conserves_energy_mapped(periodic):
+    vp = _var_problem((2, 2), 3, 3, flux="alternating", amp=0.05, c2="sine", periodic=periodic)
     ops = dv.assemble(vp)
     L, E = _dense(vp, ops)
     A = E @ L + L.T @ E

@@ -46,8 +46,12 @@ extern "C" {
 
 /* ---- enums ----------------------------------------------------------- */
 enum { GDG_BC_DIRICHLET = 0, GDG_BC_PERIODIC = 1 };
-/* Section 2.2.1: central alpha=1/2, beta=tau=0; upwind alpha=1/2, beta=xi/2, tau=1/(2 xi). */
-enum { GDG_FLUX_CENTRAL = 0, GDG_FLUX_UPWIND = 1 };
+/* Section 2.2.1: central alpha=1/2, beta=tau=0; upwind alpha=1/2, beta=xi/2,
+ * tau=1/(2 xi); alternating alpha=1, beta=tau=0, with the sides of a face
+ * labelled by a fixed orientation (side 1 = the left / lower element, so
+ * v* = v_left and (grad u)* = grad u_right on every interior face) and the
+ * closure v* = 0, (n.grad u)* = n.grad u_in on a Dirichlet side. */
+enum { GDG_FLUX_CENTRAL = 0, GDG_FLUX_UPWIND = 1, GDG_FLUX_ALTERNATING = 2 };
 /* Coefficients: constant c^2 on a Cartesian box mesh, or c^2 and the element
  * geometry sampled at every element's GD nodes (Section 7: variable speed of
  * sound or mapped, non-Cartesian elements). */

@@ -58,30 +58,34 @@ k_stage2(const __grid_constant__ ModalParams mp, const StageBufs b, double cA, d
         double vi = T[tix2<N1>(e, 0, 0, l)], di = T[tix2<N1>(e, 0, 1, l)], vo, dO;
         int en = ex - 1;
         if (en < 0 && mp.per_x) en += nx;
-        if (en >= 0) { int f = ey * nx + en; vo = T[tix2<N1>(f, 1, 0, l)]; dO = T[tix2<N1>(f, 1, 1, l)]; }
+        bool bnd = en < 0;
+        if (!bnd) { int f = ey * nx + en; vo = T[tix2<N1>(f, 1, 0, l)]; dO = T[tix2<N1>(f, 1, 1, l)]; }
         else { vo = -vi; dO = -di; }
-        flux(vi, di, vo, dO, mp.beta, mp.tau, mp.c2, gxm, qxm);
+        flux(vi, di, vo, dO, mp.beta, mp.tau, mp.c2, mp.alt, 0, bnd, gxm, qxm);
         vi = T[tix2<N1>(e, 1, 0, l)]; di = T[tix2<N1>(e, 1, 1, l)];
         en = ex + 1;
         if (en >= nx && mp.per_x) en -= nx;
-        if (en < nx) { int f = ey * nx + en; vo = T[tix2<N1>(f, 0, 0, l)]; dO = T[tix2<N1>(f, 0, 1, l)]; }
+        bnd = en >= nx;
+        if (!bnd) { int f = ey * nx + en; vo = T[tix2<N1>(f, 0, 0, l)]; dO = T[tix2<N1>(f, 0, 1, l)]; }
         else { vo = -vi; dO = -di; }
-        flux(vi, di, vo, dO, mp.beta, mp.tau, mp.c2, gxp, qxp);
+        flux(vi, di, vo, dO, mp.beta, mp.tau, mp.c2, mp.alt, 1, bnd, gxp, qxp);
         // y faces, transverse mode k = l
         double g, q;
         vi = T[tix2<N1>(e, 2, 0, l)]; di = T[tix2<N1>(e, 2, 1, l)];
         en = ey - 1;
         if (en < 0 && mp.per_y) en += ny;
-        if (en >= 0) { int f = en * nx + ex; vo = T[tix2<N1>(f, 3, 0, l)]; dO = T[tix2<N1>(f, 3, 1, l)]; }
+        bnd = en < 0;
+        if (!bnd) { int f = en * nx + ex; vo = T[tix2<N1>(f, 3, 0, l)]; dO = T[tix2<N1>(f, 3, 1, l)]; }
         else { vo = -vi; dO = -di; }
-        flux(vi, di, vo, dO, mp.beta, mp.tau, mp.c2, g, q);
+        flux(vi, di, vo, dO, mp.beta, mp.tau, mp.c2, mp.alt, 0, bnd, g, q);
         fy[0 * N1 + l] = g; fy[2 * N1 + l] = q;
         vi = T[tix2<N1>(e, 3, 0, l)]; di = T[tix2<N1>(e, 3, 1, l)];
         en = ey + 1;
         if (en >= ny && mp.per_y) en -= ny;
-        if (en < ny) { int f = en * nx + ex; vo = T[tix2<N1>(f, 2, 0, l)]; dO = T[tix2<N1>(f, 2, 1, l)]; }
+        bnd = en >= ny;
+        if (!bnd) { int f = en * nx + ex; vo = T[tix2<N1>(f, 2, 0, l)]; dO = T[tix2<N1>(f, 2, 1, l)]; }
         else { vo = -vi; dO = -di; }
-        flux(vi, di, vo, dO, mp.beta, mp.tau, mp.c2, g, q);
+        flux(vi, di, vo, dO, mp.beta, mp.tau, mp.c2, mp.alt, 1, bnd, g, q);
         fy[1 * N1 + l] = g; fy[3 * N1 + l] = q;
     }
     __syncthreads();
@@ -375,12 +379,12 @@ k_stage1(const __grid_constant__ ModalParams mp, const StageBufs b, double cA, d
     int en = e - 1;
     if (en < 0 && mp.per_x) en += nx;
     if (en >= 0) { vo = T[tix1(en, 1, 0)]; dO = T[tix1(en, 1, 1)]; } else { vo = -vi; dO = -di; }
-    flux(vi, di, vo, dO, mp.beta, mp.tau, mp.c2, gm, qm);
+    flux(vi, di, vo, dO, mp.beta, mp.tau, mp.c2, mp.alt, 0, en < 0, gm, qm);
     vi = T[tix1(e, 1, 0)]; di = T[tix1(e, 1, 1)];
     en = e + 1;
     if (en >= nx && mp.per_x) en -= nx;
     if (en < nx) { vo = T[tix1(en, 0, 0)]; dO = T[tix1(en, 0, 1)]; } else { vo = -vi; dO = -di; }
-    flux(vi, di, vo, dO, mp.beta, mp.tau, mp.c2, gp, qp);
+    flux(vi, di, vo, dO, mp.beta, mp.tau, mp.c2, mp.alt, 1, en >= nx, gp, qp);
     const size_t row = (size_t)e * N1;
     double Ru[N1], Rv[N1];
 #pragma unroll
@@ -696,6 +700,7 @@ int gdg_const_setup(gdg_ctx *ctx) {
     }
     mp.beta2 = 2.0 * mp.beta;
     mp.tau2 = 2.0 * mp.tau;
+    mp.alt = ctx->pb.flux == GDG_FLUX_ALTERNATING;
     // Mode order: even modes (Psi[N-i][k] = Psi[i][k]) first, then odd ones,
     // each group by ascending eigenvalue; the constant mode stays first.
     // If some eigenvector has no clean parity the generic kernel is used.
@@ -1180,6 +1185,7 @@ extern "C" int gdg_rhs_static(const gdg_problem *pb, const double *u, const doub
     }
     mp.beta2 = 2.0 * mp.beta;
     mp.tau2 = 2.0 * mp.tau;
+    mp.alt = pb->flux == GDG_FLUX_ALTERNATING;
     mp.parity = 0;     // generic stage kernel
     mp.epb = dim == 2 ? 16 : 1;
     for (int d = 0; d < dim; ++d) {

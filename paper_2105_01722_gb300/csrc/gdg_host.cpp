@@ -360,7 +360,10 @@ static int validate(const gdg_problem *pb, std::string &why) {
         if (!(pb->hi[k] > pb->lo[k])) { why = "need hi > lo"; return GDG_EINVAL; }
         if (pb->bc[k] != GDG_BC_DIRICHLET && pb->bc[k] != GDG_BC_PERIODIC) { why = "bad bc"; return GDG_EINVAL; }
     }
-    if (pb->flux != GDG_FLUX_CENTRAL && pb->flux != GDG_FLUX_UPWIND) { why = "bad flux"; return GDG_EINVAL; }
+    if (pb->flux != GDG_FLUX_CENTRAL && pb->flux != GDG_FLUX_UPWIND && pb->flux != GDG_FLUX_ALTERNATING) {
+        why = "bad flux";
+        return GDG_EINVAL;
+    }
     if (pb->coef == GDG_COEF_CONST) {
         if (!(pb->c2 > 0.0)) { why = "c2 must be > 0"; return GDG_EINVAL; }
         if (pb->solver != GDG_SOLVE_DIAG) { why = "constant coefficients use GDG_SOLVE_DIAG"; return GDG_EINVAL; }

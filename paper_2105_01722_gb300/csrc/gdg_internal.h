@@ -29,6 +29,7 @@ struct ModalParams {
     int per_x, per_y;     // periodic flags
     double c2, beta, tau; // fluxes: v* = (vi+vo)/2 - beta(di+do), q* = (di-do)/2 - tau(vi-vo)
     double beta2, tau2;   // 2 beta, 2 tau
+    int alt;              // alternating flux (alpha = 1, beta = tau = 0; side 1 = left / lower element)
     int parity;           // modes ordered even (r -> 1-r symmetric) first: eR = +-eL, gR = +-gL
     int epb;              // elements per block of the 2-D kernels
     int epbh;             // elements per block of the half-line stage kernel (2 N1 threads each)

@@ -29,11 +29,34 @@ __device__ __forceinline__ size_t tix1(int e, int face, int fld) {
 
 // Fluxes of Section 2.2.1 in normal form (alpha = 1/2):
 //   v* = (vi + vo)/2 - beta (di + do),  q* = (di - do)/2 - tau (vi - vo)
-// returns g = v* - vi and c2 * q*.
+// returns g = v* - vi and c2 * q*.  Alternating flux (alpha = 1, sides by a
+// fixed orientation: side 1 = the left / lower element): on the element's
+// minus face (side = 0, it is side 2) v* = vo, q* = di; on its plus face
+// (side = 1) v* = vi, q* = -do; on a Dirichlet side (bnd: vo, do are the
+// mirror state) v* = 0, q* = di, which is the alpha = 1/2 formula there.
 __device__ __forceinline__ void flux(double vi, double di, double vo, double dO, double beta,
-                                     double tau, double c2, double &g, double &q) {
+                                     double tau, double c2, int alt, int side, bool bnd, double &g, double &q) {
+    if (alt && !bnd) {
+        g = side == 0 ? vo - vi : 0.0;
+        q = c2 * (side == 0 ? di : -dO);
+        return;
+    }
     g = 0.5 * (vo - vi) - beta * (di + dO);
     q = c2 * (0.5 * (di - dO) - tau * (vi - vo));
+}
+
+// The same fluxes doubled, without c^2 (g2 = 2 (v* - vi), q2 = 2 q*), as the
+// parity stage bodies use them.
+__device__ __forceinline__ void flux2(double vi, double di, double vo, double dO, double b2, double t2,
+                                      int alt, int side, bool bnd, double &g2, double &q2) {
+    const double d1 = vo - vi;
+    if (alt && !bnd) {
+        g2 = side == 0 ? 2.0 * d1 : 0.0;
+        q2 = side == 0 ? 2.0 * di : -2.0 * dO;
+        return;
+    }
+    g2 = fma(-b2, di + dO, d1);
+    q2 = fma(t2, d1, di - dO);
 }
 
 // Body of the parity stage kernel for element tile `etile` (blockDim.x / N1
@@ -79,43 +102,40 @@ __device__ __forceinline__ void stage2p_body(const ModalParams &mp, const StageB
     double GA = 0, GB = 0, QA = 0, QB = 0;
     if (valid) {
         const double *T = b.trin;
-        double vi, di, vo, dO, d1, g2m, q2m, g2p, q2p;
+        double vi, di, vo, dO, g2m, q2m, g2p, q2p;
         int en, f;
+        bool bnd;
         // x faces, transverse mode l
         vi = T[tix2<N1>(e, 0, 0, l)]; di = T[tix2<N1>(e, 0, 1, l)];
         en = ex - 1;
         if (en < 0 && mp.per_x) en += nx;
-        if (en >= 0) { f = ey * nx + en; vo = T[tix2<N1>(f, 1, 0, l)]; dO = T[tix2<N1>(f, 1, 1, l)]; }
+        bnd = en < 0;
+        if (!bnd) { f = ey * nx + en; vo = T[tix2<N1>(f, 1, 0, l)]; dO = T[tix2<N1>(f, 1, 1, l)]; }
         else { vo = -vi; dO = -di; }
-        d1 = vo - vi;
-        g2m = fma(-b2, di + dO, d1);
-        q2m = fma(t2, d1, di - dO);
+        flux2(vi, di, vo, dO, b2, t2, mp.alt, 0, bnd, g2m, q2m);
         vi = T[tix2<N1>(e, 1, 0, l)]; di = T[tix2<N1>(e, 1, 1, l)];
         en = ex + 1;
         if (en >= nx && mp.per_x) en -= nx;
-        if (en < nx) { f = ey * nx + en; vo = T[tix2<N1>(f, 0, 0, l)]; dO = T[tix2<N1>(f, 0, 1, l)]; }
+        bnd = en >= nx;
+        if (!bnd) { f = ey * nx + en; vo = T[tix2<N1>(f, 0, 0, l)]; dO = T[tix2<N1>(f, 0, 1, l)]; }
         else { vo = -vi; dO = -di; }
-        d1 = vo - vi;
-        g2p = fma(-b2, di + dO, d1);
-        q2p = fma(t2, d1, di - dO);
+        flux2(vi, di, vo, dO, b2, t2, mp.alt, 1, bnd, g2p, q2p);
         GA = g2m + g2p; GB = g2m - g2p; QA = q2m + q2p; QB = q2m - q2p;
         // y faces, transverse mode k = l
         vi = T[tix2<N1>(e, 2, 0, l)]; di = T[tix2<N1>(e, 2, 1, l)];
         en = ey - 1;
         if (en < 0 && mp.per_y) en += ny;
-        if (en >= 0) { f = en * nx + ex; vo = T[tix2<N1>(f, 3, 0, l)]; dO = T[tix2<N1>(f, 3, 1, l)]; }
+        bnd = en < 0;
+        if (!bnd) { f = en * nx + ex; vo = T[tix2<N1>(f, 3, 0, l)]; dO = T[tix2<N1>(f, 3, 1, l)]; }
         else { vo = -vi; dO = -di; }
-        d1 = vo - vi;
-        g2m = fma(-b2, di + dO, d1);
-        q2m = fma(t2, d1, di - dO);
+        flux2(vi, di, vo, dO, b2, t2, mp.alt, 0, bnd, g2m, q2m);
         vi = T[tix2<N1>(e, 3, 0, l)]; di = T[tix2<N1>(e, 3, 1, l)];
         en = ey + 1;
         if (en >= ny && mp.per_y) en -= ny;
-        if (en < ny) { f = en * nx + ex; vo = T[tix2<N1>(f, 2, 0, l)]; dO = T[tix2<N1>(f, 2, 1, l)]; }
+        bnd = en >= ny;
+        if (!bnd) { f = en * nx + ex; vo = T[tix2<N1>(f, 2, 0, l)]; dO = T[tix2<N1>(f, 2, 1, l)]; }
         else { vo = -vi; dO = -di; }
-        d1 = vo - vi;
-        g2p = fma(-b2, di + dO, d1);
-        q2p = fma(t2, d1, di - dO);
+        flux2(vi, di, vo, dO, b2, t2, mp.alt, 1, bnd, g2p, q2p);
         fy[l] = g2m + g2p; fy[N1 + l] = g2m - g2p;
         fy[2 * N1 + l] = q2m + q2p; fy[3 * N1 + l] = q2m - q2p;
     }
@@ -246,40 +266,41 @@ __device__ __forceinline__ void stage2h_body(const ModalParams &mp, const StageB
     double gx = 0, qx = 0, gy = 0, qy = 0;
     if (valid) {
         const double *T = b.trin;
-        double vi, di, vo, dO, d1;
+        double vi, di, vo, dO;
         int en, f;
+        bool bnd;
         if (h == 0) {   // x-, transverse mode l
             vi = T[tix2<N1>(e, 0, 0, l)]; di = T[tix2<N1>(e, 0, 1, l)];
             en = ex - 1;
             if (en < 0 && mp.per_x) en += nx;
-            if (en >= 0) { f = ey * nx + en; vo = T[tix2<N1>(f, 1, 0, l)]; dO = T[tix2<N1>(f, 1, 1, l)]; }
+            bnd = en < 0;
+            if (!bnd) { f = ey * nx + en; vo = T[tix2<N1>(f, 1, 0, l)]; dO = T[tix2<N1>(f, 1, 1, l)]; }
             else { vo = -vi; dO = -di; }
         } else {        // x+
             vi = T[tix2<N1>(e, 1, 0, l)]; di = T[tix2<N1>(e, 1, 1, l)];
             en = ex + 1;
             if (en >= nx && mp.per_x) en -= nx;
-            if (en < nx) { f = ey * nx + en; vo = T[tix2<N1>(f, 0, 0, l)]; dO = T[tix2<N1>(f, 0, 1, l)]; }
+            bnd = en >= nx;
+            if (!bnd) { f = ey * nx + en; vo = T[tix2<N1>(f, 0, 0, l)]; dO = T[tix2<N1>(f, 0, 1, l)]; }
             else { vo = -vi; dO = -di; }
         }
-        d1 = vo - vi;
-        gx = fma(-b2, di + dO, d1);
-        qx = fma(t2, d1, di - dO);
+        flux2(vi, di, vo, dO, b2, t2, mp.alt, h, bnd, gx, qx);
         if (h == 0) {   // y-, transverse mode l
             vi = T[tix2<N1>(e, 2, 0, l)]; di = T[tix2<N1>(e, 2, 1, l)];
             en = ey - 1;
             if (en < 0 && mp.per_y) en += ny;
-            if (en >= 0) { f = en * nx + ex; vo = T[tix2<N1>(f, 3, 0, l)]; dO = T[tix2<N1>(f, 3, 1, l)]; }
+            bnd = en < 0;
+            if (!bnd) { f = en * nx + ex; vo = T[tix2<N1>(f, 3, 0, l)]; dO = T[tix2<N1>(f, 3, 1, l)]; }
             else { vo = -vi; dO = -di; }
         } else {        // y+
             vi = T[tix2<N1>(e, 3, 0, l)]; di = T[tix2<N1>(e, 3, 1, l)];
             en = ey + 1;
             if (en >= ny && mp.per_y) en -= ny;
-            if (en < ny) { f = en * nx + ex; vo = T[tix2<N1>(f, 2, 0, l)]; dO = T[tix2<N1>(f, 2, 1, l)]; }
+            bnd = en >= ny;
+            if (!bnd) { f = en * nx + ex; vo = T[tix2<N1>(f, 2, 0, l)]; dO = T[tix2<N1>(f, 2, 1, l)]; }
             else { vo = -vi; dO = -di; }
         }
-        d1 = vo - vi;
-        gy = fma(-b2, di + dO, d1);
-        qy = fma(t2, d1, di - dO);
+        flux2(vi, di, vo, dO, b2, t2, mp.alt, h, bnd, gy, qy);
     }
     const double ogx = __shfl_xor_sync(mask, gx, 1), oqx = __shfl_xor_sync(mask, qx, 1);
     const double ogy = __shfl_xor_sync(mask, gy, 1), oqy = __shfl_xor_sync(mask, qy, 1);

@@ -219,6 +219,7 @@ int gdg_var_setup(gdg_ctx *ctx) {
     P.per_x = ctx->pb.bc[0] == GDG_BC_PERIODIC;
     P.per_y = ctx->pb.bc[1] == GDG_BC_PERIODIC;
     P.upwind = ctx->pb.flux == GDG_FLUX_UPWIND;
+    P.alt = ctx->pb.flux == GDG_FLUX_ALTERNATING;
     P.xi = ctx->pb.xi;
     P.rtol = ctx->pb.pcg_rtol;
     P.maxit = ctx->pb.pcg_maxit;

@@ -11,6 +11,7 @@
 struct VarParams {
     int nx, ny, ne, Q;
     int per_x, per_y, upwind;
+    int alt;              // alternating flux (alpha = 1; side 1 = the element with the smaller index)
     double xi;            // > 0: constant splitting, else local c
     double rtol;
     int maxit, precond;   // GDG_PC_*
@@ -778,8 +779,12 @@ __device__ void lifts(const VarParams &P, int e, const double *trin, const Tabs 
             beta = 0.5 * xi;
             tau = 0.5 / xi;
         }
-        const double vstar = 0.5 * (vi + vo) - beta * (di + dO);
-        const double qstar = 0.5 * (di - dO) - tau * (vi - vo);
+        double vstar = 0.5 * (vi + vo) - beta * (di + dO);
+        double qstar = 0.5 * (di - dO) - tau * (vi - vo);
+        if (P.alt && nb >= 0) {   // minus faces (0, 2): this element is side 2
+            vstar = (f == 0 || f == 2) ? vo : vi;
+            qstar = (f == 0 || f == 2) ? di : -dO;
+        }
         const double g = vstar - vi;
         const double cw = P.face[fix(e, f, q, 2, Q)];
         fw[(f * 3 + 0) * Q + q] = cw * P.face[fix(e, f, q, 0, Q)] * g;

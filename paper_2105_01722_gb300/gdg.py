@@ -14,7 +14,7 @@ LIB_PATH = os.path.join(_HERE, "libgdg.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ENOCONV, ETIMEOUT, ENONFINITE, EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6, -7
 BC_DIRICHLET, BC_PERIODIC = 0, 1
-FLUX_CENTRAL, FLUX_UPWIND = 0, 1
+FLUX_CENTRAL, FLUX_UPWIND, FLUX_ALTERNATING = 0, 1, 2
 COEF_CONST, COEF_NODAL = 0, 1
 SOLVE_DIAG, SOLVE_PCG, SOLVE_INVERSE = 0, 1, 2
 PC_FDM, PC_NONE = 0, 1

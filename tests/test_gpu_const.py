@@ -27,6 +27,10 @@ CASES = [
     dict(dim=2, n=(1, 3), N=1, p=1, periodic=(False, False), flux="upwind"),
     dict(dim=2, n=(17, 3), N=15, p=7, periodic=(False, False), flux="upwind", lo=(0.0, -1.0), hi=(2.0, 0.5)),
     dict(dim=2, n=(9, 11), N=7, p=7, periodic=(True, True), flux="central", c2=0.3),
+    dict(dim=1, n=(9,), N=8, p=5, periodic=(False,), flux="alternating"),
+    dict(dim=1, n=(6,), N=6, p=3, periodic=(True,), flux="alternating", c2=1.9),
+    dict(dim=2, n=(6, 5), N=8, p=5, periodic=(True, False), flux="alternating", c2=1.4),
+    dict(dim=2, n=(4, 7), N=9, p=7, periodic=(False, False), flux="alternating"),
 ]
 
 
@@ -45,7 +49,7 @@ def _gpu_problem(c):
     bc = tuple(gdg.BC_PERIODIC if q else gdg.BC_DIRICHLET for q in c["periodic"])
     return gdg.make_problem(dim, c["n"], c["N"], c["p"], lo=c.get("lo", (0.0, 0.0)),
                             hi=c.get("hi", (1.0, 1.0)), bc=bc,
-                            flux=gdg.FLUX_UPWIND if c["flux"] == "upwind" else gdg.FLUX_CENTRAL,
+                            flux={"upwind": gdg.FLUX_UPWIND, "central": gdg.FLUX_CENTRAL, "alternating": gdg.FLUX_ALTERNATING}[c["flux"]],
                             xi=c.get("xi", 0.0), c2=c.get("c2", 1.0))
 
 

@@ -51,7 +51,7 @@ def _mesh(n, N, kind="mapped", c2="sine"):
 
 def _problem(n, N, p, X, Y, C2, solver=gdg.SOLVE_INVERSE, flux="upwind", periodic=(False, False), **kw):
     bc = tuple(gdg.BC_PERIODIC if q else gdg.BC_DIRICHLET for q in periodic)
-    return gdg.make_problem(2, n, N, p, bc=bc, flux=gdg.FLUX_UPWIND if flux == "upwind" else gdg.FLUX_CENTRAL,
+    return gdg.make_problem(2, n, N, p, bc=bc, flux={"upwind": gdg.FLUX_UPWIND, "central": gdg.FLUX_CENTRAL, "alternating": gdg.FLUX_ALTERNATING}[flux],
                             coef=gdg.COEF_NODAL, x_nodes=X, y_nodes=Y, c2_nodes=C2, solver=solver, **kw)
 
 
@@ -74,6 +74,7 @@ CASES = [
     dict(n=(3, 3), N=5, p=5, periodic=(True, True), kind="cartesian", c2="1.7"),
     dict(n=(2, 2), N=9, p=7),
     dict(n=(1, 1), N=6, p=3, periodic=(True, True)),
+    dict(n=(3, 4), N=8, p=5, flux="alternating"),
 ]
 
 

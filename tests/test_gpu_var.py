@@ -52,7 +52,7 @@ def _pair(n, N, p, kind="mapped", c2="sine", flux="upwind", periodic=(False, Fal
     vp = dv.VarProblem(n=n, N=N, p=p, X=X, Y=Y, C2=C2, periodic=periodic, flux=flux, xi=xi,
                        nq=nquad if nquad else None)
     bc = tuple(gdg.BC_PERIODIC if q else gdg.BC_DIRICHLET for q in periodic)
-    pb = gdg.make_problem(2, n, N, p, bc=bc, flux=gdg.FLUX_UPWIND if flux == "upwind" else gdg.FLUX_CENTRAL,
+    pb = gdg.make_problem(2, n, N, p, bc=bc, flux={"upwind": gdg.FLUX_UPWIND, "central": gdg.FLUX_CENTRAL, "alternating": gdg.FLUX_ALTERNATING}[flux],
                           xi=xi, coef=gdg.COEF_NODAL, x_nodes=X, y_nodes=Y, c2_nodes=C2, nquad=nquad,
                           pcg_rtol=rtol, pcg_maxit=maxit,
                           precond=gdg.PC_FDM if precond == "fdm" else gdg.PC_NONE)
@@ -67,6 +67,7 @@ CASES = [
     dict(n=(1, 1), N=6, p=3, periodic=(True, True)),
     dict(n=(2, 2), N=9, p=7, nquad=9),
     dict(n=(5, 3), N=8, p=5, xi=0.8, precond="none"),
+    dict(n=(4, 3), N=8, p=5, flux="alternating", periodic=(True, False), c2="random"),
 ]
 
 

@@ -33,7 +33,12 @@ transverse GD basis); in 1-D it is the scalar 1.
 Homogeneous Dirichlet data u = 0 enters as the mirror state
   v_out = -v_in, d_out = -d_in  (so v* = 0, q* = d_in - 2 tau v_in).
 
-Layout: 1-D U[e, i]; 2-D U[ey, ex, j, i] (i along x), element e = ey*nx+ex.
+Layout: 1-D U[e, i]; 2-D U[ey, ex, j, i] (i along x), element e = ey*nx+ex;
+3-D U[ez, ey, ex, k, j, i], e = (ez*ny + ey)*nx + ex (Sections 2.1.2 and 3:
+the tensor-product construction for d = 3, which the paper states but does
+not test).  Each face then carries a 2-D trace over its two transverse node
+indices and M_perp is the Kronecker product of the two transverse 1-D mass
+matrices.
 """
 from dataclasses import dataclass, field
 
@@ -94,6 +99,12 @@ def operators(prob):
         ops.aR.append(dphiR / H)    # outward normal +x_k
     if prob.dim == 1:
         ops.M, ops.S = ops.M1[0], ops.S1[0]
+    elif prob.dim == 3:
+        # element index a = (k*n1 + j)*n1 + i: kron(A_z, A_y, A_x)
+        Mx, My, Mz = ops.M1
+        Sx, Sy, Sz = ops.S1
+        ops.M = np.kron(Mz, np.kron(My, Mx))
+        ops.S = np.kron(Mz, np.kron(My, Sx)) + np.kron(Mz, np.kron(Sy, Mx)) + np.kron(Sz, np.kron(My, Mx))
     else:
         # element index a = j*n1 + i (i along x): kron(A_y, B_x)
         Mx, My, Sx, Sy = ops.M1[0], ops.M1[1], ops.S1[0], ops.S1[1]
@@ -148,6 +159,44 @@ def _neighbour_traces(vm, dm, vp, dp, periodic):
     return out_m_v, out_m_d, out_p_v, out_p_d
 
 
+def _residuals_3d(prob, U, V, ops, beta, tau, alt):
+    """3-D element residuals: the 2-D face terms with 2-D face traces.
+    Direction d in (0, 1, 2) = (x, y, z) is node axis (5, 4, 3) and element
+    axis (2, 1, 0) of U[ez, ey, ex, k, j, i]."""
+    n1, c2 = prob.n1, prob.c2
+    nx, ny, nz = prob.n
+    U = U.reshape(nz, ny, nx, n1, n1, n1)
+    V = V.reshape(nz, ny, nx, n1, n1, n1)
+    r_u = np.zeros_like(U)
+    r_v = -c2 * (U.reshape(nz * ny * nx, n1 ** 3) @ ops.S.T).reshape(U.shape)
+    for d in range(3):
+        node_ax, elem_ax = 5 - d, 2 - d
+        # transverse directions, in the order of the remaining node axes
+        trans = [q for q in (2, 1, 0) if q != d]
+        Ud = np.moveaxis(U, node_ax, -1)
+        Vd = np.moveaxis(V, node_ax, -1)
+        aL, aR = ops.aL[d], ops.aR[d]
+        vm, vp = Vd[..., 0], Vd[..., -1]
+        dm, dp = Ud @ aL, Ud @ aR
+        t = [np.moveaxis(a, elem_ax, 0) for a in (vm, dm, vp, dp)]
+        om_v, om_d, op_v, op_d = [np.moveaxis(a, 0, elem_ax) for a in
+                                  _neighbour_traces(*t, prob.periodic[d])]
+        bm, bp = [np.moveaxis(a, 0, elem_ax) for a in _boundary_masks(t[0].shape, prob.periodic[d])]
+        vs_m, qs_m = _fluxes(vm, dm, om_v, om_d, beta, tau, *(("minus", bm) if alt else ()))
+        vs_p, qs_p = _fluxes(vp, dp, op_v, op_d, beta, tau, *(("plus", bp) if alt else ()))
+        T1, T2 = ops.M1[trans[0]], ops.M1[trans[1]]
+        perp = lambda g: np.einsum("...ab,Aa,Bb->...AB", g, T1, T2)
+        ru_d = (np.einsum("...ab,n->...abn", perp(vs_m - vm), aL)
+                + np.einsum("...ab,n->...abn", perp(vs_p - vp), aR))
+        rv_d = np.zeros_like(ru_d)
+        rv_d[..., 0] += c2 * perp(qs_m)
+        rv_d[..., -1] += c2 * perp(qs_p)
+        r_u += np.moveaxis(ru_d, -1, node_ax)
+        r_v += np.moveaxis(rv_d, -1, node_ax)
+    ne = nx * ny * nz
+    return r_u.reshape(ne, n1 ** 3), r_v.reshape(ne, n1 ** 3)
+
+
 def residuals(prob, U, V, ops=None):
     """(r_u, r_v) of the element equations for nodal states U, V."""
     ops = operators(prob) if ops is None else ops
@@ -155,6 +204,8 @@ def residuals(prob, U, V, ops=None):
     alt = prob.flux == "alternating"
     c2 = prob.c2
     n1 = prob.n1
+    if prob.dim == 3:
+        return _residuals_3d(prob, U, V, ops, beta, tau, alt)
     if prob.dim == 1:
         U = U.reshape(prob.n[0], n1)
         V = V.reshape(prob.n[0], n1)
@@ -252,13 +303,27 @@ def energy(prob, U, V, ops=None):
 
 def node_coordinates(prob):
     """Physical coordinates of every element's GD nodes, in the layout of U.
-    1-D: x[e, i];  2-D: (x, y) each [ey, ex, j, i]."""
+    1-D: x[e, i];  2-D: (x, y) each [ey, ex, j, i];  3-D: (x, y, z) each
+    [ez, ey, ex, k, j, i]."""
     n1 = prob.n1
     r = np.arange(n1) / prob.N
     if prob.dim == 1:
         H = prob.H(0)
         x0 = prob.lo[0] + H * np.arange(prob.n[0])
         return (x0[:, None] + H * r[None, :],)
+    if prob.dim == 3:
+        nx, ny, nz = prob.n
+        shape = (nz, ny, nx, n1, n1, n1)
+        out = []
+        for d, (ne_d, ax_e, ax_n) in enumerate(((nx, 2, 5), (ny, 1, 4), (nz, 0, 3))):
+            H = prob.H(d)
+            c0 = prob.lo[d] + H * np.arange(ne_d)
+            e_shape = [1] * 6
+            e_shape[ax_e] = ne_d
+            n_shape = [1] * 6
+            n_shape[ax_n] = n1
+            out.append(np.broadcast_to(c0.reshape(e_shape) + H * r.reshape(n_shape), shape).copy())
+        return tuple(out)
     nx, ny = prob.n
     Hx, Hy = prob.H(0), prob.H(1)
     x0 = prob.lo[0] + Hx * np.arange(nx)

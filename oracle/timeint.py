@@ -54,6 +54,31 @@ def errors(prob, U, V, exact, t, nq=None):
         l2 = np.sqrt(np.sum(ww * (u - uh) ** 2))
         en = np.sqrt(np.sum(ww * ((ux - uxh) ** 2 + (v - vh) ** 2)))
         return l2, en
+    if prob.dim == 3:
+        nx, ny, nz = prob.n
+        Hx, Hy, Hz = prob.H(0), prob.H(1), prob.H(2)
+        U = U.reshape(nz, ny, nx, n1, n1, n1)
+        V = V.reshape(nz, ny, nx, n1, n1, n1)
+        Q = len(r)
+        xs = prob.lo[0] + Hx * (np.arange(nx)[:, None] + r[None, :])
+        ys = prob.lo[1] + Hy * (np.arange(ny)[:, None] + r[None, :])
+        zs = prob.lo[2] + Hz * (np.arange(nz)[:, None] + r[None, :])
+        shape = (nz, ny, nx, Q, Q, Q)
+        X = np.broadcast_to(xs[None, None, :, None, None, :], shape)
+        Y = np.broadcast_to(ys[None, :, None, None, :, None], shape)
+        Z = np.broadcast_to(zs[:, None, None, :, None, None], shape)
+        u, (ux, uy, uz), v = exact(t, X, Y, Z)
+        # point (c along z, b along y, a along x)
+        ev = lambda A, Bz, By, Bx: np.einsum("ck,bj,ai,zyxkji->zyxcba", Bz, By, Bx, A)
+        uh = ev(U, B, B, B)
+        uxh = ev(U, B, B, D) / Hx
+        uyh = ev(U, B, D, B) / Hy
+        uzh = ev(U, D, B, B) / Hz
+        vh = ev(V, B, B, B)
+        ww = Hx * Hy * Hz * w[:, None, None] * w[None, :, None] * w[None, None, :]
+        l2 = np.sqrt(np.sum(ww * (u - uh) ** 2))
+        en = np.sqrt(np.sum(ww * ((ux - uxh) ** 2 + (uy - uyh) ** 2 + (uz - uzh) ** 2 + (v - vh) ** 2)))
+        return l2, en
     nx, ny = prob.n
     Hx, Hy = prob.H(0), prob.H(1)
     U = U.reshape(ny, nx, n1, n1)

@@ -246,6 +246,40 @@ def forms_variable(steps=16):
     return out
 
 
+def flops_per_element_stage_3d(n1):
+    """Algorithmic FP64 flops of one 3-D fused stage per element (FMA = 2):
+    fluxes 6 faces x n1^2 x 11, per modal entry 36 (lifts 26, diagonal solve
+    2, RK 8), traces 3 directions x 4 dots x n1^2 x 2 n1."""
+    return 66 * n1 ** 2 + 36 * n1 ** 3 + 24 * n1 ** 3
+
+
+def forms_three_d(n=32, N=8, p=5, steps=16):
+    """3-D constant coefficient (Sections 2.1.2 and 3 for d = 3): n^3 elements
+    of N^3 cells, upwind, Dirichlet, standing mode sin(pi x) sin(pi y) sin(pi z),
+    dt = 0.1 h; DOF-steps/s and the FP64 rate of the whole step."""
+    import numpy as np
+    import torch
+    from paper_2105_01722_gb300 import gdg, inputs
+    pb = gdg.make_problem(3, (n, n, n), N, p, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0),
+                          bc=(gdg.BC_DIRICHLET,) * 3, flux=gdg.FLUX_UPWIND, c2=1.0)
+    ctx = gdg.Context(pb)
+    X, Y, Z = inputs.cartesian_nodes_3d((n, n, n), N)
+    u = torch.tensor((np.sin(np.pi * X) * np.sin(np.pi * Y) * np.sin(np.pi * Z)).ravel(), device="cuda")
+    v = torch.zeros_like(u)
+    dt = 0.1 / (n * N)
+    E0 = ctx.energy(u, v)
+    ctx.step(u, v, 0.0, dt, 4)
+    ms = _timed_ms(lambda: ctx.step(u, v, 0.0, dt, steps))
+    E1 = ctx.energy(u, v)
+    ctx.close()
+    dof = n ** 3 * (N + 1) ** 3
+    tflops = flops_per_element_stage_3d(N + 1) * n ** 3 * 4 * steps / (ms / 1e3) / 1e12
+    return {"workload": "3-D constant c^2, %d^3 elements of %d^3 cells, p=%d, upwind, Dirichlet" % (n, N, p),
+            "dof": dof, "dof_steps_per_s": dof * steps / (ms / 1e3), "ms_per_step": ms / steps,
+            "fp64_tflops_whole_step": tflops, "frac_of_fp64_peak": tflops / FP64_PEAK_TFLOPS,
+            "energy_ratio_after_20_steps": E1 / E0}
+
+
 def forms_batched(steps=8):
     """48 independent problems (seeds 20210501+i, n ~ U{16..128}, p in {3,5,7},
     alternating constant / smooth random c^2): one batch (persistent launches,
@@ -434,7 +468,7 @@ def run_gdg(args):
         forms = {}
         if not args.no_forms and world == 1:
             for key, fn in (("variable_mapped_128", forms_variable), ("batched_48", forms_batched),
-                            ("learned_guess", forms_learned)):
+                            ("learned_guess", forms_learned), ("three_d_32", forms_three_d)):
                 try:
                     forms[key] = fn()
                 except Exception as exc:    # report, do not lose the headline line

@@ -84,12 +84,12 @@ enum { GDG_OP_M = 0, GDG_OP_S = 1 };
 typedef struct gdg_ctx gdg_ctx;   /* opaque; owns uploaded operators and scratch */
 
 typedef struct {
-    int dim;             /* 1 or 2                                                   */
-    int n_elem[2];       /* elements per direction (n); n_elem[1] ignored for dim 1  */
+    int dim;             /* 1, 2 or 3 (3: GDG_COEF_CONST only, N+1 <= 10)           */
+    int n_elem[3];       /* elements per direction (n); entries >= dim ignored       */
     int N;               /* GD cells per element per direction, n1 = N+1 <= 16       */
     int p;               /* odd GD degree, 1 <= p <= N                               */
-    double lo[2], hi[2]; /* box [lo, hi] of the (reference) mesh                     */
-    int bc[2];           /* per direction: GDG_BC_DIRICHLET (u = 0) or _PERIODIC     */
+    double lo[3], hi[3]; /* box [lo, hi] of the (reference) mesh                     */
+    int bc[3];           /* per direction: GDG_BC_DIRICHLET (u = 0) or _PERIODIC     */
     int flux;            /* GDG_FLUX_*                                               */
     double xi;           /* upwind splitting; <= 0 means xi = c (local c for NODAL)  */
     int coef;            /* GDG_COEF_*                                               */

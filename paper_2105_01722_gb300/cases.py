@@ -1,6 +1,7 @@
 """Small seeded workloads of each kernel family, for profiling and timing.
 
-python -m paper_2105_01722_gb300.cases const [--n 64] [--p 5] [--steps 8]
+python -m paper_2105_01722_gb300.cases const [--n 64] [--p 5] [--steps 8] [--variant -1|0|1]
+python -m paper_2105_01722_gb300.cases const3 [--n 16] [--p 5] [--steps 8]
 python -m paper_2105_01722_gb300.cases var   [--n 32] [--p 5] [--steps 2] [--mixed | --inverse]
 python -m paper_2105_01722_gb300.cases batch [--problems 12] [--steps 2] [--mixed]
 python -m paper_2105_01722_gb300.cases mlp   [--rows 4096] [--steps 4]
@@ -50,6 +51,25 @@ def case_const(n=64, N=8, p=5, steps=8, warmup=2, variant=-1):
     ctx.close()
     dof = n * n * (N + 1) ** 2
     return {"case": "const", "n": n, "N": N, "p": p, "steps": steps, "variant": chosen, "ms": ms,
+            "dof_steps_per_s": dof * steps / (ms / 1e3)}
+
+
+def case_const3(n=16, N=8, p=5, steps=8, warmup=2):
+    """3-D constant coefficient standing mode sin(pi x) sin(pi y) sin(pi z),
+    n^3 elements, modal route, upwind, Dirichlet."""
+    import torch
+    pb = gdg.make_problem(3, (n, n, n), N, p, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0),
+                          bc=(gdg.BC_DIRICHLET,) * 3, flux=gdg.FLUX_UPWIND, c2=1.0)
+    ctx = gdg.Context(pb)
+    X, Y, Z = inputs.cartesian_nodes_3d((n, n, n), N)
+    u = torch.tensor((np.sin(np.pi * X) * np.sin(np.pi * Y) * np.sin(np.pi * Z)).ravel(), device="cuda")
+    v = torch.zeros_like(u)
+    dt = 0.1 / (n * N)
+    ctx.step(u, v, 0.0, dt, warmup)
+    ms = _ms(lambda: ctx.step(u, v, 0.0, dt, steps))
+    ctx.close()
+    dof = n ** 3 * (N + 1) ** 3
+    return {"case": "const3", "n": n, "N": N, "p": p, "steps": steps, "ms": ms,
             "dof_steps_per_s": dof * steps / (ms / 1e3)}
 
 
@@ -145,7 +165,7 @@ def case_mlp(rows=4096, steps=4, batch=256, seed=5):
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
-    ap.add_argument("case", choices=["const", "var", "batch", "mlp"])
+    ap.add_argument("case", choices=["const", "const3", "var", "batch", "mlp"])
     ap.add_argument("--n", type=int)
     ap.add_argument("--p", type=int, default=5)
     ap.add_argument("--steps", type=int)
@@ -160,6 +180,8 @@ def main(argv=None):
     kw = {"steps": a.steps} if a.steps else {}
     if a.case == "const":
         r = case_const(n=a.n or 64, p=a.p, variant=a.variant, **kw)
+    elif a.case == "const3":
+        r = case_const3(n=a.n or 16, p=a.p, **kw)
     elif a.case == "var":
         r = case_var(n=a.n or 32, p=a.p, mixed=a.mixed, inverse=a.inverse, **kw)
     elif a.case == "batch":

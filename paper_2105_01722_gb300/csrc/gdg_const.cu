@@ -330,12 +330,12 @@ k_sep2(int ne, const double *in0, const double *in1, double *out0, double *out1,
 
 // per-block partial of sum over elements of (|Vbar|^2 + c2 * lambda . Ubar^2)
 // for modal (Ubar, Vbar) given in yU, yV; deterministic fixed-order tree.
-template <int N1, int D2>
+template <int N1, int DIM>
 __global__ void k_energy_partial(int ne, const double *yU, const double *yV, const double *lam2,
                                  double *partial) {
     __shared__ double red[1024];
     const int t = threadIdx.x;
-    const int ents = D2 ? N1 * N1 : N1;
+    const int ents = DIM == 2 ? N1 * N1 : N1;
     double s = 0.0;
     const long long total = (long long)ne * ents;
     for (long long i = (long long)blockIdx.x * blockDim.x + t; i < total; i += (long long)gridDim.x * blockDim.x) {
@@ -522,6 +522,10 @@ void launch_stage1(int mode, const ModalParams &mp, const StageBufs &b, double c
 
 void launch_stage_raw(const gdg_ctx *ctx, int mode, const StageBufs &b, double cA, double cY, cudaStream_t s) {
     const int n1 = ctx->n1;
+    if (ctx->dim == 3) {
+        gdg3_stage(ctx->mp, n1, mode, b, cA, cY, s);
+        return;
+    }
     if (ctx->dim == 2) {
         switch (n1) {
 #define X(n) case n: launch_stage2<n>(mode, ctx->mp, b, cA, cY, s); break;
@@ -539,6 +543,10 @@ void launch_stage_raw(const gdg_ctx *ctx, int mode, const StageBufs &b, double c
 
 void launch_traces_raw(const gdg_ctx *ctx, const double *yU, const double *yV, double *tr, cudaStream_t s) {
     const int n1 = ctx->n1;
+    if (ctx->dim == 3) {
+        gdg3_traces(ctx->mp, n1, yU, yV, tr, s);
+        return;
+    }
     if (ctx->dim == 2) {
         const int epb = ctx->mp.epb;
         dim3 grid((ctx->ne + epb - 1) / epb), block(epb * n1);
@@ -567,6 +575,12 @@ enum { T_P = 0, T_PSI = 1, T_PSIT = 2 };
 void launch_sep_raw(const gdg_ctx *ctx, const double *in0, const double *in1, double *out0, double *out1,
                 int B, const double *D, int C, cudaStream_t s) {
     const int n1 = ctx->n1;
+    if (ctx->dim == 3) {
+        gdg3_sep(n1, ctx->ne, in0, in1, out0, out1, mat(ctx, 0, B), mat(ctx, 1, B), mat(ctx, 2, B), D,
+                 C >= 0 ? mat(ctx, 0, C) : nullptr, C >= 0 ? mat(ctx, 1, C) : nullptr,
+                 C >= 0 ? mat(ctx, 2, C) : nullptr, s);
+        return;
+    }
     if (ctx->dim == 2) {
         const int epb = ctx->mp.epb;
         dim3 grid((ctx->ne + epb - 1) / epb), block(epb * n1);
@@ -624,6 +638,7 @@ int set_smem_limits() {
     cudaFuncSetAttribute(k_sep2<n>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     GDG_N1_CASES(X)
 #undef X
+    gdg3_set_smem_limits();
     done = true;
     return GDG_OK;
 }
@@ -689,9 +704,11 @@ int gdg_const_setup(gdg_ctx *ctx) {
     std::memset(&mp, 0, sizeof(mp));
     mp.nx = ctx->nx;
     mp.ny = ctx->ny;
+    mp.nz = ctx->nz;
     mp.ne = ctx->ne;
     mp.per_x = ctx->pb.bc[0] == GDG_BC_PERIODIC;
-    mp.per_y = ctx->dim == 2 && ctx->pb.bc[1] == GDG_BC_PERIODIC;
+    mp.per_y = ctx->dim >= 2 && ctx->pb.bc[1] == GDG_BC_PERIODIC;
+    mp.per_z = ctx->dim == 3 && ctx->pb.bc[2] == GDG_BC_PERIODIC;
     mp.c2 = ctx->pb.c2;
     if (ctx->pb.flux == GDG_FLUX_UPWIND) {
         double xi = ctx->pb.xi > 0 ? ctx->pb.xi : std::sqrt(ctx->pb.c2);
@@ -726,8 +743,8 @@ int gdg_const_setup(gdg_ctx *ctx) {
             for (int k = 0; k < n1; ++k) perm[k] = k;
         }
     }
-    std::vector<double> tables((size_t)2 * 3 * nn, 0.0);
-    std::vector<double> lam[2];
+    std::vector<double> tables((size_t)3 * 3 * nn, 0.0);
+    std::vector<double> lam[3];
     for (int d = 0; d < ctx->dim; ++d) {
         const double H = (ctx->pb.hi[d] - ctx->pb.lo[d]) / ctx->pb.n_elem[d];
         const double sq = std::sqrt(H);
@@ -769,14 +786,16 @@ int gdg_const_setup(gdg_ctx *ctx) {
     mp.epb = ctx->dim == 2 ? choose_epb(ctx->ne, n1, sms, n1) : 1;
     mp.epbh = ctx->dim == 2 ? choose_epb(ctx->ne, n1, sms, 2 * n1) : 1;
     mp.split = 0;   // decided by timing at the first gdg_step
-    const int ents = ctx->dim == 2 ? nn : n1;
+    const int ents = ctx->dim == 3 ? nn * n1 : (ctx->dim == 2 ? nn : n1);
     std::vector<double> l2((size_t)2 * ents, 0.0);
     for (int m = 0; m < ents; ++m) {
-        double L = ctx->dim == 2 ? lam[0][m % n1] + lam[1][m / n1] : lam[0][m];
+        double L = ctx->dim == 3   ? lam[0][m % n1] + lam[1][(m / n1) % n1] + lam[2][m / nn]
+                   : ctx->dim == 2 ? lam[0][m % n1] + lam[1][m / n1]
+                                   : lam[0][m];
         l2[m] = -ctx->pb.c2 * L;
         l2[ents + m] = m == 0 ? 0.0 : 1.0 / L;
     }
-    ctx->tr_len = (long long)ctx->ne * (ctx->dim == 2 ? 8 * n1 : 4);
+    ctx->tr_len = (long long)ctx->ne * (ctx->dim == 3 ? 12 * nn : (ctx->dim == 2 ? 8 * n1 : 4));
     ctx->red_len = 1024;
     int st;
     if ((st = gdg_cuda_check(ctx, cudaMalloc((void **)&ctx->d_mats, tables.size() * sizeof(double)), "alloc")) ||
@@ -822,7 +841,7 @@ int gdg_const_rhs(gdg_ctx *ctx, const double *u, const double *v, double *du, do
 
 int gdg_const_mass_solve(gdg_ctx *ctx, int which, const double *b, double *x, cudaStream_t s) {
     // x = Psi D Psi^T b with D = I (M^-1) or D = Lambda^+ (constrained S solve)
-    const int ents = ctx->dim == 2 ? ctx->n1 * ctx->n1 : ctx->n1;
+    const int ents = (int)(ctx->ndof / ctx->ne);
     const double *D = which == GDG_OP_M ? nullptr : ctx->d_lam2 + ents;
     launch_sep(ctx, b, nullptr, x, nullptr, T_PSIT, D, T_PSI, s);
     return gdg_cuda_check(ctx, cudaGetLastError(), "gdg_mass_solve launch");
@@ -914,15 +933,17 @@ int gdg_const_step(gdg_ctx *ctx, double *u, double *v, double dt, int nsteps, cu
 int gdg_const_energy(gdg_ctx *ctx, const double *u, const double *v, double *E, cudaStream_t s) {
     launch_sep(ctx, u, v, buf(ctx, B_KU), buf(ctx, B_KV), T_P, nullptr, -1, s);
     const int blocks = 256;
-    if (ctx->dim == 2) {
+    if (ctx->dim == 3) {
+        gdg3_energy_partial(ctx->n1, ctx->ne, buf(ctx, B_KU), buf(ctx, B_KV), ctx->d_lam2, ctx->d_red, blocks, s);
+    } else if (ctx->dim == 2) {
         switch (ctx->n1) {
-#define X(n) case n: k_energy_partial<n, 1><<<blocks, 256, 0, s>>>(ctx->ne, buf(ctx, B_KU), buf(ctx, B_KV), ctx->d_lam2, ctx->d_red); break;
+#define X(n) case n: k_energy_partial<n, 2><<<blocks, 256, 0, s>>>(ctx->ne, buf(ctx, B_KU), buf(ctx, B_KV), ctx->d_lam2, ctx->d_red); break;
             GDG_N1_CASES(X)
 #undef X
         }
     } else {
         switch (ctx->n1) {
-#define X(n) case n: k_energy_partial<n, 0><<<blocks, 256, 0, s>>>(ctx->ne, buf(ctx, B_KU), buf(ctx, B_KV), ctx->d_lam2, ctx->d_red); break;
+#define X(n) case n: k_energy_partial<n, 1><<<blocks, 256, 0, s>>>(ctx->ne, buf(ctx, B_KU), buf(ctx, B_KV), ctx->d_lam2, ctx->d_red); break;
             GDG_N1_CASES(X)
 #undef X
         }

@@ -351,7 +351,9 @@ extern "C" int gdg_profile_read(gdg_ctx *ctx, int kind, long long *launches, dou
 
 static int validate(const gdg_problem *pb, std::string &why) {
     if (!pb) { why = "null problem"; return GDG_EINVAL; }
-    if (pb->dim != 1 && pb->dim != 2) { why = "dim must be 1 or 2"; return GDG_EINVAL; }
+    if (pb->dim < 1 || pb->dim > 3) { why = "dim must be 1, 2 or 3"; return GDG_EINVAL; }
+    if (pb->dim == 3 && pb->coef != GDG_COEF_CONST) { why = "3-D elements: GDG_COEF_CONST only"; return GDG_EUNSUPPORTED; }
+    if (pb->dim == 3 && pb->N + 1 > 10) { why = "3-D elements: N+1 <= 10"; return GDG_EUNSUPPORTED; }
     if (pb->p < 1 || pb->p % 2 == 0) { why = "p must be odd and >= 1"; return GDG_EINVAL; }
     if (pb->N < pb->p) { why = "need N >= p"; return GDG_EINVAL; }
     if (pb->N + 1 > GDG_MAXN1) { why = "N+1 > 16 not supported"; return GDG_EUNSUPPORTED; }
@@ -407,12 +409,14 @@ extern "C" int gdg_create(const gdg_problem *pb, gdg_ctx **out) {
     ctx->pb.x_nodes = ctx->pb.y_nodes = ctx->pb.c2_nodes = nullptr;
     ctx->dim = pb->dim;
     ctx->nx = pb->n_elem[0];
-    ctx->ny = pb->dim == 2 ? pb->n_elem[1] : 1;
+    ctx->ny = pb->dim >= 2 ? pb->n_elem[1] : 1;
+    ctx->nz = pb->dim == 3 ? pb->n_elem[2] : 1;
     ctx->N = pb->N;
     ctx->n1 = pb->N + 1;
     ctx->p = pb->p;
-    ctx->ne = ctx->nx * ctx->ny;
-    ctx->ndof = (long long)ctx->ne * (pb->dim == 2 ? ctx->n1 * ctx->n1 : ctx->n1);
+    ctx->ne = ctx->nx * ctx->ny * ctx->nz;
+    ctx->ndof = (long long)ctx->ne * (pb->dim == 3 ? ctx->n1 * ctx->n1 * ctx->n1
+                                                   : (pb->dim == 2 ? ctx->n1 * ctx->n1 : ctx->n1));
     cudaGetDevice(&ctx->device);
     st = gdg_build_basis(ctx->p, ctx->N, ctx->Mh, ctx->Sh, ctx->phiL, ctx->phiR, ctx->dphiL,
                          ctx->dphiR, ctx->Psih, ctx->lamh);

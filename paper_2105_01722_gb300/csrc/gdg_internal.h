@@ -24,9 +24,9 @@ struct ModalDir {
 
 // Everything a stage kernel needs besides buffers (passed by value).
 struct ModalParams {
-    ModalDir d[2];
-    int nx, ny, ne;
-    int per_x, per_y;     // periodic flags
+    ModalDir d[3];
+    int nx, ny, nz, ne;
+    int per_x, per_y, per_z;   // periodic flags
     double c2, beta, tau; // fluxes: v* = (vi+vo)/2 - beta(di+do), q* = (di-do)/2 - tau(vi-vo)
     double beta2, tau2;   // 2 beta, 2 tau
     int alt;              // alternating flux (alpha = 1, beta = tau = 0; side 1 = left / lower element)
@@ -43,6 +43,27 @@ enum {
     M_S23 = 2,   // acc += cA k; Y' = y_n + cY k
     M_S4 = 3     // y_n += acc + cA k
 };
+
+// Buffers of one modal RK stage launch.
+struct StageBufs {
+    const double *yU, *yV;   // stage input (modal)
+    double *nU, *nV;         // y_n
+    double *aU, *aV;         // RK accumulator
+    double *oU, *oV;         // next stage input, or k (M_RHS)
+    const double *trin;      // traces of the stage input
+    double *trout;           // traces of the next stage input
+    const double *lam2;      // [2][n1^d] : -c2 * lambda, 1/lambda (0 on mode 0)
+};
+
+// 3-D modal-route launches (gdg_const3.cu), n1 = N+1 in 2..10
+void gdg3_stage(const ModalParams &mp, int n1, int mode, const StageBufs &b, double cA, double cY, cudaStream_t s);
+void gdg3_traces(const ModalParams &mp, int n1, const double *yU, const double *yV, double *tr, cudaStream_t s);
+void gdg3_sep(int n1, int ne, const double *in0, const double *in1, double *out0, double *out1, const double *Bx,
+              const double *By, const double *Bz, const double *D, const double *Cx, const double *Cy,
+              const double *Cz, cudaStream_t s);
+void gdg3_energy_partial(int n1, int ne, const double *yU, const double *yV, const double *lam2, double *partial,
+                         int blocks, cudaStream_t s);
+void gdg3_set_smem_limits();
 
 struct GraphCache {
     cudaGraphExec_t exec = nullptr;
@@ -66,7 +87,7 @@ struct Profiler {
 
 struct gdg_ctx {
     gdg_problem pb{};
-    int dim = 1, nx = 1, ny = 1, N = 1, n1 = 2, p = 1, ne = 1;
+    int dim = 1, nx = 1, ny = 1, nz = 1, N = 1, n1 = 2, p = 1, ne = 1;
     long long ndof = 0;      // doubles per field
     int device = 0;
     std::string err;

@@ -7,15 +7,6 @@
 namespace {
 
 
-struct StageBufs {
-    const double *yU, *yV;   // stage input (modal)
-    double *nU, *nV;         // y_n
-    double *aU, *aV;         // RK accumulator
-    double *oU, *oV;         // next stage input, or k (M_RHS)
-    const double *trin;      // traces of the stage input
-    double *trout;           // traces of the next stage input
-    const double *lam2;      // [2][n1^d] : -c2 * lambda, 1/lambda (0 on mode 0)
-};
 
 // trace buffer index: 2-D [e][face 0..3 = xm,xp,ym,yp][field 0 = v, 1 = n.grad u][N1]
 template <int N1>

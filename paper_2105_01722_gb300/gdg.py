@@ -27,8 +27,8 @@ _dp = ctypes.POINTER(ctypes.c_double)
 
 class Problem(ctypes.Structure):
     _fields_ = [
-        ("dim", ctypes.c_int), ("n_elem", ctypes.c_int * 2), ("N", ctypes.c_int), ("p", ctypes.c_int),
-        ("lo", ctypes.c_double * 2), ("hi", ctypes.c_double * 2), ("bc", ctypes.c_int * 2),
+        ("dim", ctypes.c_int), ("n_elem", ctypes.c_int * 3), ("N", ctypes.c_int), ("p", ctypes.c_int),
+        ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3), ("bc", ctypes.c_int * 3),
         ("flux", ctypes.c_int), ("xi", ctypes.c_double), ("coef", ctypes.c_int), ("c2", ctypes.c_double),
         ("x_nodes", _dp), ("y_nodes", _dp), ("c2_nodes", _dp), ("nquad", ctypes.c_int),
         ("solver", ctypes.c_int), ("precond", ctypes.c_int), ("pcg_rtol", ctypes.c_double),
@@ -137,13 +137,13 @@ def make_problem(dim, n, N, p, lo=(0.0, 0.0), hi=(1.0, 1.0), bc=(BC_DIRICHLET, B
                  precision=FP64, route=ROUTE_MODAL, refine_max=8, refine_rtol=1e-5):
     pb = Problem()
     pb.dim = dim
-    n = tuple(n) + (1,) * (2 - len(n))
-    pb.n_elem[0], pb.n_elem[1] = n[0], n[1]
+    n = tuple(n) + (1,) * (3 - len(n))
+    lo = tuple(lo) + (0.0,) * (3 - len(lo))
+    hi = tuple(hi) + (1.0,) * (3 - len(hi))
+    bc = tuple(bc) + (BC_DIRICHLET,) * (3 - len(bc))
+    for k in range(3):
+        pb.n_elem[k], pb.lo[k], pb.hi[k], pb.bc[k] = n[k], lo[k], hi[k], bc[k]
     pb.N, pb.p = N, p
-    pb.lo[0], pb.lo[1] = lo[0], lo[1] if len(lo) > 1 else 0.0
-    pb.hi[0], pb.hi[1] = hi[0], hi[1] if len(hi) > 1 else 1.0
-    bc = tuple(bc) + (BC_DIRICHLET,) * (2 - len(bc))
-    pb.bc[0], pb.bc[1] = bc[0], bc[1]
     pb.flux, pb.xi, pb.coef, pb.c2 = flux, xi, coef, c2
     keep = []
     for name, arr in (("x_nodes", x_nodes), ("y_nodes", y_nodes), ("c2_nodes", c2_nodes)):

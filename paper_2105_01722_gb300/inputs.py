@@ -13,6 +13,23 @@ import numpy as np
 SEED0 = 20210501
 
 
+def cartesian_nodes_3d(n, N, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0)):
+    """GD node coordinates (x, y, z), each [ez, ey, ex, k, j, i], of a uniform
+    Cartesian 3-D mesh of n = (nx, ny, nz) elements."""
+    n1 = N + 1
+    r = np.arange(n1) / N
+    shape = (n[2], n[1], n[0], n1, n1, n1)
+    out = []
+    for d, (ax_e, ax_n) in enumerate(((2, 5), (1, 4), (0, 3))):
+        H = (hi[d] - lo[d]) / n[d]
+        es = [1] * 6
+        es[ax_e] = n[d]
+        ns = [1] * 6
+        ns[ax_n] = n1
+        out.append(np.broadcast_to(lo[d] + H * (np.arange(n[d]).reshape(es) + r.reshape(ns)), shape).copy())
+    return tuple(out)
+
+
 def cartesian_nodes(n, N, lo=(0.0, 0.0), hi=(1.0, 1.0)):
     """GD node coordinates of every element of a uniform Cartesian mesh."""
     n1 = N + 1

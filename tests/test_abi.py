@@ -107,6 +107,8 @@ def _nodal_kw(**extra):
     (dict(dim=2, n=(4, 4), N=8, p=5, precision=gdg.MIXED), "EUNSUPPORTED"),      # nothing to refine
     ("inverse_mixed", "EUNSUPPORTED"),
     ("nodal_diag", "EINVAL"),
+    (dict(dim=3, n=(2, 2, 2), N=10, p=5), "EUNSUPPORTED"),                      # 3-D: N+1 <= 10
+    (dict(dim=4, n=(2, 2, 2), N=8, p=5), "EINVAL"),
 ])
 def test_create_rejects_unbuilt_combinations(kw, status):
     """Combinations that are not built are refused, never silently ignored."""

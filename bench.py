@@ -57,7 +57,7 @@ FP64_PEAK_TFLOPS = 152 * 2.070e9 * 4 / 1e12
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one k_stage2p
 # launch of this workload, from one ncu capture (mean over the captured
 # launches; None when the kernel has changed since).
-STAGE_TRAFFIC_BYTES = 13.0e6
+STAGE_TRAFFIC_BYTES = None
 
 
 def _env_rank():

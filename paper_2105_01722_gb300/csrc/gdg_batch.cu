@@ -96,7 +96,8 @@ k_batch_modal(const BatchProb *__restrict__ probs, const int2 *__restrict__ item
         }
         const StageRoles<STAGE> r(P.sb, P.dt);
         const StageBufs b{r.yU, r.yV, P.sb.nU, P.sb.nV, P.sb.aU, P.sb.aV, r.oU, r.oV, r.trin, r.trout, P.lam2};
-        stage2p_body<N1, MODE>(s_mp, b, r.cA, r.cY, w.y, smem);
+        if (s_mp.alt) stage2p_body<N1, MODE, 1>(s_mp, b, r.cA, r.cY, w.y, smem);
+        else stage2p_body<N1, MODE, 0>(s_mp, b, r.cA, r.cY, w.y, smem);
         __syncthreads();
     }
 }

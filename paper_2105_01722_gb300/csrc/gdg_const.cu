@@ -168,11 +168,11 @@ k_stage2(const __grid_constant__ ModalParams mp, const StageBufs b, double cA, d
     }
 }
 
-template <int N1, int MODE>
+template <int N1, int MODE, int ALT>
 __global__ void __launch_bounds__(MAXB2)
 k_stage2p(const __grid_constant__ ModalParams mp, const StageBufs b, double cA, double cY) {
     extern __shared__ double smem[];
-    stage2p_body<N1, MODE>(mp, b, cA, cY, blockIdx.x, smem);
+    stage2p_body<N1, MODE, ALT>(mp, b, cA, cY, blockIdx.x, smem);
 }
 
 // half-line variant (two threads per line), bit-identical results
@@ -494,10 +494,12 @@ void launch_stage2(int mode, const ModalParams &mp, const StageBufs &b, double c
     }
     if (mp.parity) {
         switch (mode) {
-        case M_RHS: k_stage2p<N1, M_RHS><<<grid, block, sm, s>>>(mp, b, cA, cY); break;
-        case M_S1: k_stage2p<N1, M_S1><<<grid, block, sm, s>>>(mp, b, cA, cY); break;
-        case M_S23: k_stage2p<N1, M_S23><<<grid, block, sm, s>>>(mp, b, cA, cY); break;
-        default: k_stage2p<N1, M_S4><<<grid, block, sm, s>>>(mp, b, cA, cY); break;
+#define GDG_K2P(m) (mp.alt ? k_stage2p<N1, m, 1> : k_stage2p<N1, m, 0>)
+        case M_RHS: GDG_K2P(M_RHS)<<<grid, block, sm, s>>>(mp, b, cA, cY); break;
+        case M_S1: GDG_K2P(M_S1)<<<grid, block, sm, s>>>(mp, b, cA, cY); break;
+        case M_S23: GDG_K2P(M_S23)<<<grid, block, sm, s>>>(mp, b, cA, cY); break;
+        default: GDG_K2P(M_S4)<<<grid, block, sm, s>>>(mp, b, cA, cY); break;
+#undef GDG_K2P
         }
         return;
     }
@@ -626,10 +628,14 @@ int set_smem_limits() {
     cudaFuncSetAttribute(k_stage2<n, M_S1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);   \
     cudaFuncSetAttribute(k_stage2<n, M_S23>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);  \
     cudaFuncSetAttribute(k_stage2<n, M_S4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);   \
-    cudaFuncSetAttribute(k_stage2p<n, M_RHS>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim); \
-    cudaFuncSetAttribute(k_stage2p<n, M_S1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);  \
-    cudaFuncSetAttribute(k_stage2p<n, M_S23>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim); \
-    cudaFuncSetAttribute(k_stage2p<n, M_S4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);  \
+    cudaFuncSetAttribute(k_stage2p<n, M_RHS, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim); \
+    cudaFuncSetAttribute(k_stage2p<n, M_S1, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);  \
+    cudaFuncSetAttribute(k_stage2p<n, M_S23, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim); \
+    cudaFuncSetAttribute(k_stage2p<n, M_S4, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);  \
+    cudaFuncSetAttribute(k_stage2p<n, M_RHS, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim); \
+    cudaFuncSetAttribute(k_stage2p<n, M_S1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);  \
+    cudaFuncSetAttribute(k_stage2p<n, M_S23, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim); \
+    cudaFuncSetAttribute(k_stage2p<n, M_S4, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);  \
     cudaFuncSetAttribute(k_stage2h<n, M_RHS>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim); \
     cudaFuncSetAttribute(k_stage2h<n, M_S1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);  \
     cudaFuncSetAttribute(k_stage2h<n, M_S23>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim); \

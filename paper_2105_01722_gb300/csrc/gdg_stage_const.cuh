@@ -57,7 +57,9 @@ __device__ __forceinline__ void flux2(double vi, double di, double vo, double dO
 // both face traces of a line come from one even/odd split dot, and each
 // lift is one FMA per entry.  Fluxes carry a factor 2 (g2 = 2(v* - v_in),
 // q2 = 2 q*) that is folded into the lift vectors hgL = gL/2, ceL = c^2 eL/2.
-template <int N1, int MODE>
+// ALT: the flux kind as a compile-time constant (1 alternating, 0 central or
+// upwind; must equal mp.alt), so the per-face choice costs nothing.
+template <int N1, int MODE, int ALT>
 __device__ __forceinline__ void stage2p_body(const ModalParams &mp, const StageBufs &b, double cA, double cY,
                                              int etile, double *smem) {
     constexpr int NE = (N1 + 1) / 2;
@@ -103,14 +105,14 @@ __device__ __forceinline__ void stage2p_body(const ModalParams &mp, const StageB
         bnd = en < 0;
         if (!bnd) { f = ey * nx + en; vo = T[tix2<N1>(f, 1, 0, l)]; dO = T[tix2<N1>(f, 1, 1, l)]; }
         else { vo = -vi; dO = -di; }
-        flux2(vi, di, vo, dO, b2, t2, mp.alt, 0, bnd, g2m, q2m);
+        flux2(vi, di, vo, dO, b2, t2, ALT, 0, bnd, g2m, q2m);
         vi = T[tix2<N1>(e, 1, 0, l)]; di = T[tix2<N1>(e, 1, 1, l)];
         en = ex + 1;
         if (en >= nx && mp.per_x) en -= nx;
         bnd = en >= nx;
         if (!bnd) { f = ey * nx + en; vo = T[tix2<N1>(f, 0, 0, l)]; dO = T[tix2<N1>(f, 0, 1, l)]; }
         else { vo = -vi; dO = -di; }
-        flux2(vi, di, vo, dO, b2, t2, mp.alt, 1, bnd, g2p, q2p);
+        flux2(vi, di, vo, dO, b2, t2, ALT, 1, bnd, g2p, q2p);
         GA = g2m + g2p; GB = g2m - g2p; QA = q2m + q2p; QB = q2m - q2p;
         // y faces, transverse mode k = l
         vi = T[tix2<N1>(e, 2, 0, l)]; di = T[tix2<N1>(e, 2, 1, l)];
@@ -119,14 +121,14 @@ __device__ __forceinline__ void stage2p_body(const ModalParams &mp, const StageB
         bnd = en < 0;
         if (!bnd) { f = en * nx + ex; vo = T[tix2<N1>(f, 3, 0, l)]; dO = T[tix2<N1>(f, 3, 1, l)]; }
         else { vo = -vi; dO = -di; }
-        flux2(vi, di, vo, dO, b2, t2, mp.alt, 0, bnd, g2m, q2m);
+        flux2(vi, di, vo, dO, b2, t2, ALT, 0, bnd, g2m, q2m);
         vi = T[tix2<N1>(e, 3, 0, l)]; di = T[tix2<N1>(e, 3, 1, l)];
         en = ey + 1;
         if (en >= ny && mp.per_y) en -= ny;
         bnd = en >= ny;
         if (!bnd) { f = en * nx + ex; vo = T[tix2<N1>(f, 2, 0, l)]; dO = T[tix2<N1>(f, 2, 1, l)]; }
         else { vo = -vi; dO = -di; }
-        flux2(vi, di, vo, dO, b2, t2, mp.alt, 1, bnd, g2p, q2p);
+        flux2(vi, di, vo, dO, b2, t2, ALT, 1, bnd, g2p, q2p);
         fy[l] = g2m + g2p; fy[N1 + l] = g2m - g2p;
         fy[2 * N1 + l] = q2m + q2p; fy[3 * N1 + l] = q2m - q2p;
     }

@@ -55,9 +55,9 @@ def flops_per_stage_launch(w=WORKLOAD):
 FP64_PEAK_TFLOPS = 152 * 2.070e9 * 4 / 1e12
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one k_stage2p
-# launch of this workload, from one ncu capture (mean over the captured
-# launches; None when the kernel has changed since).
-STAGE_TRAFFIC_BYTES = None
+# launch of this workload, from one ncu capture: the mean over the four stage
+# launches of one RK4 step (None when the kernel has changed since).
+STAGE_TRAFFIC_BYTES = 15.66e6
 
 
 def _env_rank():

@@ -150,7 +150,11 @@ int gdg_basis_1d(int p, int N, double *M, double *S, double *phiL, double *phiR,
  * the element mass and stiffness matrices and face data on the device for
  * GDG_COEF_NODAL, Section 7.1) and allocate device scratch on the current
  * CUDA device.  Host arrays in *pb are copied.  *out receives the context.
- * Errors: GDG_EINVAL, GDG_EUNSUPPORTED, GDG_ENOMEM, GDG_ECUDA.
+ * Nodal layout of the state: 1-D u[e*n1 + i]; 2-D u[(e*n1 + j)*n1 + i],
+ * e = ey*nx + ex; 3-D u[((e*n1 + k)*n1 + j)*n1 + i], e = (ez*ny + ey)*nx + ex
+ * (i along x; element nodes on shared faces are duplicated, as in DG).
+ * Errors: GDG_EINVAL, GDG_EUNSUPPORTED (e.g. 3-D with GDG_COEF_NODAL or
+ * N+1 > 10), GDG_ENOMEM, GDG_ECUDA.
  */
 int gdg_create(const gdg_problem *pb, gdg_ctx **out);
 

@@ -61,10 +61,13 @@ enum { GDG_COEF_CONST = 0, GDG_COEF_NODAL = 1 };
  * 7.1), or precomputed element inverses (GDG_COEF_NODAL only): the
  * precomputed-inverse route that Section 3.1 discusses, applied to the
  * time-independent element systems of Section 7.1.  gdg_create forms
- * (S_c2 + w w^T)^-1 and M_J^-1 per element by Cholesky (2 x (N+1)^4 more
- * doubles per element); every stage then applies them instead of running
- * PCG.  FP64 only (GDG_EUNSUPPORTED with GDG_MIXED); gdg_pcg still runs PCG
- * on such a context. */
+ * (S_c2 + w w^T)^-1 and M_J^-1 per element by Cholesky and folds them with
+ * the face lifts and the stiffness matrix into G_u = (S_c2 + w w^T)^-1 R_u,
+ * G_v = M_J^-1 R_v and K = M_J^-1 S_c2 (R_u, R_v: the lifts of the face line
+ * integrals into r_u, r_v; (12 (N+1) + (N+1)^2) (N+1)^2 more doubles per
+ * element are kept, the inverses are freed after setup); every stage then
+ * applies them instead of running PCG.  FP64 only (GDG_EUNSUPPORTED with
+ * GDG_MIXED); gdg_pcg still runs PCG on such a context. */
 enum { GDG_SOLVE_DIAG = 0, GDG_SOLVE_PCG = 1, GDG_SOLVE_INVERSE = 2 };
 /* PCG preconditioner: frozen-coefficient diagonalisation, none (plain CG). */
 enum { GDG_PC_FDM = 0, GDG_PC_NONE = 1 };

@@ -48,6 +48,7 @@ size_t traces_smem(int N1, int Q) { return sizeof(double) * ((size_t)tab_len(Q, 
 template <int N1>
 size_t stage_smem(int Q, bool mixed, bool no_matrix) { return StageSmem<N1>::bytes(Q, mixed, no_matrix); }
 size_t invert_smem(int N1) { return sizeof(double) * (2 * (size_t)N1 * N1 * N1 * N1 + (size_t)N1 * N1); }
+size_t fold_smem(int N1) { return sizeof(double) * ((size_t)fold_rlen(N1) + 12 * (size_t)N1 + 2 * (size_t)N1 * N1); }
 
 // The dynamic shared-memory limit is a property of the kernel function, shared
 // by every context: always raise it to the device's opt-in maximum so that a
@@ -65,6 +66,7 @@ void set_attrs() {
     cudaFuncSetAttribute(k_var_stage<N1, M_S4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     cudaFuncSetAttribute(k_var_pcg<N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     cudaFuncSetAttribute(k_var_invert<N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    cudaFuncSetAttribute(k_var_fold<N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
 }
 
 template <int N1>
@@ -242,7 +244,7 @@ int gdg_var_setup(gdg_ctx *ctx) {
 #undef X
     }
     if (D->smem_pcg > 220 * 1024 || D->smem_geom > 220 * 1024 ||
-        (ctx->pb.solver == GDG_SOLVE_INVERSE && invert_smem(n1) > 220 * 1024))
+        (ctx->pb.solver == GDG_SOLVE_INVERSE && (invert_smem(n1) > 220 * 1024 || fold_smem(n1) > 220 * 1024)))
         return gdg_set_err(ctx, GDG_EUNSUPPORTED, "element too large for shared memory (reduce nquad)");
     const double *Xd = D->d_nodes, *Yd = D->d_nodes + nd, *Cd = D->d_nodes + 2 * nd;
     switch (n1) {
@@ -270,23 +272,24 @@ int gdg_var_setup(gdg_ctx *ctx) {
     }
     P.dS = D->d_dS;
     P.inverse = ctx->pb.solver == GDG_SOLVE_INVERSE;
-    if (P.inverse) {   // element inverses (S_c2 + w w^T)^-1 and M_J^-1
+    if (P.inverse) {   // element inverses (S_c2 + w w^T)^-1 and M_J^-1, folded with the lifts
         const size_t nm = nd * NA;
         if ((st = gdg_cuda_check(ctx, cudaMalloc((void **)&D->d_Ainv, nm * sizeof(double)), "alloc Ainv")) ||
-            (st = gdg_cuda_check(ctx, cudaMalloc((void **)&D->d_Minv, nm * sizeof(double)), "alloc Minv")))
+            (st = gdg_cuda_check(ctx, cudaMalloc((void **)&D->d_Minv, nm * sizeof(double)), "alloc Minv")) ||
+            (st = gdg_cuda_check(ctx, cudaMalloc((void **)&D->d_G, nd * fold_cols(n1) * sizeof(double)), "alloc G")))
             return st;
-        const size_t ism = invert_smem(n1);
+        const size_t ism = invert_smem(n1), fsm = fold_smem(n1);
         switch (n1) {
 #define X(n)                                                                                         \
     case n:                                                                                          \
         k_var_invert<n><<<ctx->ne, nthreads_for(n * n), ism>>>(D->d_S, D->d_w, D->d_Ainv);           \
         k_var_invert<n><<<ctx->ne, nthreads_for(n * n), ism>>>(D->d_M, nullptr, D->d_Minv);          \
+        k_var_fold<n><<<ctx->ne, nthreads_for(n * n), fsm>>>(D->d_S, D->d_Ainv, D->d_Minv, D->d_tab, Q, D->d_G); \
         break;
             GDG_VAR_CASES(X)
 #undef X
         }
-        P.Ainv = D->d_Ainv;
-        P.Minv = D->d_Minv;
+        P.G = D->d_G;
     }
     if (P.mixed) {   // FP32 copies of the element matrices for the inner solves
         const size_t nm = nd * NA;
@@ -300,7 +303,9 @@ int gdg_var_setup(gdg_ctx *ctx) {
     }
     st = gdg_cuda_check(ctx, cudaDeviceSynchronize(), "assembly");
     cudaFree(D->d_nodes);
-    D->d_nodes = nullptr;
+    cudaFree(D->d_Ainv);
+    cudaFree(D->d_Minv);
+    D->d_nodes = D->d_Ainv = D->d_Minv = nullptr;
     if (st) return st;
     // the mapping must be orientation preserving: every frozen |J| mean > 0
     std::vector<double> pre((size_t)ctx->ne * 4);
@@ -314,7 +319,7 @@ int gdg_var_setup(gdg_ctx *ctx) {
 void gdg_var_free(gdg_ctx *ctx) {
     VarData *D = ctx->var;
     if (!D) return;
-    cudaFree(D->d_S); cudaFree(D->d_M); cudaFree(D->d_S32); cudaFree(D->d_M32); cudaFree(D->d_dS); cudaFree(D->d_Ainv); cudaFree(D->d_Minv); cudaFree(D->d_w); cudaFree(D->d_pre); cudaFree(D->d_face);
+    cudaFree(D->d_S); cudaFree(D->d_M); cudaFree(D->d_S32); cudaFree(D->d_M32); cudaFree(D->d_dS); cudaFree(D->d_Ainv); cudaFree(D->d_Minv); cudaFree(D->d_G); cudaFree(D->d_w); cudaFree(D->d_pre); cudaFree(D->d_face);
     cudaFree(D->d_tab); cudaFree(D->d_nodes); cudaFree(D->d_state); cudaFree(D->d_tr);
     cudaFree(D->d_c2feat); cudaFree(D->d_wbf16); cudaFree(D->d_mlp);
     cudaFree(D->d_ru); cudaFree(D->d_rv); cudaFree(D->d_x0u);

@@ -19,8 +19,8 @@ struct VarParams {
     const double *S, *M, *w, *pre, *face;
     const float *S32, *M32;      // FP32 copies of S and M (mixed precision only)
     const double *dS;            // [ne][N1*N1] frozen-coefficient preconditioner diagonal (S system)
-    int inverse;                 // GDG_SOLVE_INVERSE: element inverses instead of PCG
-    const double *Ainv, *Minv;   // [ne][NA][NA] (S_c2 + w w^T)^-1 and M_J^-1 (exactly symmetric)
+    int inverse;                 // GDG_SOLVE_INVERSE: element inverses folded into G instead of PCG
+    const double *G;             // [ne][12 N1 + NA][NA] folded operators, column-major (fold_cols)
     unsigned long long *stats;   // [0] sum it_u, [1] sum it_v, [2] max it_u, [3] max it_v,
                                  // [4] unconverged u, [5] unconverged v, [6] element solves,
                                  // [7] sum sweeps u, [8] sum sweeps v, [9] max sweeps u, [10] max sweeps v
@@ -34,7 +34,8 @@ struct VarData {
     double *d_S = nullptr, *d_M = nullptr, *d_w = nullptr, *d_pre = nullptr, *d_face = nullptr;
     float *d_S32 = nullptr, *d_M32 = nullptr;
     double *d_dS = nullptr;
-    double *d_Ainv = nullptr, *d_Minv = nullptr;
+    double *d_G = nullptr;                       // folded operators (GDG_SOLVE_INVERSE)
+    double *d_Ainv = nullptr, *d_Minv = nullptr; // setup temporaries of the fold, freed after it
     double *d_tab = nullptr, *d_nodes = nullptr;
     double *d_state = nullptr, *d_tr = nullptr;
     long long tr_len = 0;
@@ -759,11 +760,10 @@ struct StageSmem {
     }
 };
 
-// face fluxes and lifts: r_u, r_v (r_v without the stiffness term)
+// face fluxes and their line integrals L[f][m][j] (f face, m = 0..2 the three
+// lifted quantities, j the node along the face): r_u and r_v are linear in L
 template <int N1>
-__device__ void lifts(const VarParams &P, int e, const double *trin, const Tabs &T, double *fw, double *L,
-                      double *ru, double *rv) {
-    constexpr int NA = N1 * N1;
+__device__ void lift_lines(const VarParams &P, int e, const double *trin, const Tabs &T, double *fw, double *L) {
     const int Q = P.Q, t = threadIdx.x;
     for (int task = t; task < 4 * Q; task += blockDim.x) {
         const int f = task / Q, q = task - (task / Q) * Q;
@@ -803,6 +803,13 @@ __device__ void lifts(const VarParams &P, int e, const double *trin, const Tabs 
         L[task] = s;
     }
     __syncthreads();
+}
+
+// r_u, r_v (r_v without the stiffness term) from the face line integrals
+template <int N1>
+__device__ __forceinline__ void lift_assemble(const double *L, const Tabs &T, double *ru, double *rv) {
+    constexpr int NA = N1 * N1;
+    const int t = threadIdx.x;
     if (t < NA) {
         const int j = t / N1, i = t - (t / N1) * N1;
         const double *Lx0 = L, *Lx1 = L + 3 * N1, *Ly0 = L + 6 * N1, *Ly1 = L + 9 * N1;
@@ -814,6 +821,57 @@ __device__ void lifts(const VarParams &P, int e, const double *trin, const Tabs 
         if (j == N1 - 1) { u_ += Ly1[i]; v_ += Ly1[2 * N1 + i]; }
         ru[t] = u_;
         rv[t] = v_;
+    }
+    __syncthreads();
+}
+
+// face fluxes and lifts: r_u, r_v (r_v without the stiffness term)
+template <int N1>
+__device__ void lifts(const VarParams &P, int e, const double *trin, const Tabs &T, double *fw, double *L,
+                      double *ru, double *rv) {
+    lift_lines<N1>(P, e, trin, T, fw, L);
+    lift_assemble<N1>(L, T, ru, rv);
+}
+
+// Columns of the folded operators of the precomputed-inverse route, per
+// element (each column NA doubles, thread t reads entry t: coalesced):
+//   0 .. 8 N1 - 1         G_u = (S_c2 + w w^T)^-1 R_u, R_u the lift of the
+//                         m = 0, 1 line integrals into r_u (column f*2N1 + m*N1 + j)
+//   8 N1 .. 12 N1 - 1     G_v = M_J^-1 R_v, R_v the lift of the m = 2 line
+//                         integrals into r_v (column 8N1 + f*N1 + j)
+//   12 N1 .. 12 N1 + NA-1 K = M_J^-1 S_c2
+// so that dU/dt = V + G_u L_u and dV/dt = G_v L_v - K U.
+__host__ __device__ constexpr int fold_cols(int N1) { return 12 * N1 + N1 * N1; }
+// shared staging of the fold's right-hand factors: R_u (NA x 8 N1), R_v
+// (NA x 4 N1) and S_c2 (NA x NA) in turn; 8 N1 > NA for N1 < 8
+__host__ __device__ constexpr int fold_rlen(int N1) { return N1 * N1 * (8 * N1 > N1 * N1 ? 8 * N1 : N1 * N1); }
+
+// dU/dt = V + G_u L_u and dV/dt = G_v L_v - K U from the folded operators Ge
+// of one element (columns as in fold_cols); L the face line integrals
+template <int N1>
+__device__ __forceinline__ void fold_apply(const double *__restrict__ Ge, const double *L, const double *Yu,
+                                           const double *Yv, double *du, double *dv) {
+    constexpr int NA = N1 * N1;
+    const int t = threadIdx.x;
+    if (t < NA) {
+        const double *g = Ge + t;
+        double su = 0.0, sv = 0.0, sk = 0.0;
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+#pragma unroll
+            for (int c = 0; c < 2 * N1; ++c)
+                su = fma(__ldg(g + (size_t)(f * 2 * N1 + c) * NA), L[f * 3 * N1 + c], su);
+        }
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+#pragma unroll
+            for (int j = 0; j < N1; ++j)
+                sv = fma(__ldg(g + (size_t)(8 * N1 + f * N1 + j) * NA), L[f * 3 * N1 + 2 * N1 + j], sv);
+        }
+#pragma unroll 9
+        for (int c = 0; c < NA; ++c) sk = fma(__ldg(g + (size_t)(12 * N1 + c) * NA), Yu[c], sk);
+        du[t] = Yv[t] + su;
+        dv[t] = sv - sk;
     }
     __syncthreads();
 }
@@ -846,7 +904,10 @@ __device__ __forceinline__ void var_stage_body(const VarParams &P, const VarBufs
     const Tabs T = tabs_split(P.tab, s.tb, P.Q, N1);
     fdm_diagonals<N1>(P, e, s.dS, s.dM);
     const bool guess = b.part == 2;
-    if (!guess) {
+    if (P.inverse) {
+        lift_lines<N1>(P, e, b.trin, T, s.fw, s.L);
+        fold_apply<N1>(P.G + (size_t)e * fold_cols(N1) * NA, s.L, s.Yu, s.Yv, s.ru, s.x);
+    } else if (!guess) {
         lifts<N1>(P, e, b.trin, T, s.fw, s.L, s.ru, s.rv);
         // stiffness: r_v -= S U
         if (P.mixed || P.inverse) {
@@ -870,10 +931,7 @@ __device__ __forceinline__ void var_stage_body(const VarParams &P, const VarBufs
     int it_u = 0, it_v = 0, sw_u = 0, sw_v = 0, fell = 0;
     bool bad_u = false, bad_v = false;
     if (P.inverse) {
-        // y = (S_c2 + w w^T)^-1 r_u; dU/dt = V + y; dV/dt = M_J^-1 r_v
-        matvec_g<NA>(P.Ainv + (size_t)e * NA * NA, s.ru, s.x);
-        if (t < NA) s.ru[t] = s.Yv[t] + s.x[t];
-        matvec_g<NA>(P.Minv + (size_t)e * NA * NA, s.rv, s.x);
+        // dU/dt, dV/dt already in ru, x (fold_apply)
     } else {
     if (P.mixed) {
         to_fp32<N1>(P.S32 + (size_t)e * NA * NA, s.A32, T.Ps, s.Ps32, s.dS, s.dS32, s.w, s.w32);
@@ -1072,6 +1130,71 @@ k_var_invert(const double *__restrict__ Src, const double *__restrict__ w, doubl
         const int r = i / NA, c = i - (i / NA) * NA;
         dst[i] = r > c ? B[c * NA + r] : B[i];
     }
+}
+
+// out[c][r] = sum_k A[r][k] R[k][c] for one element, row r per thread: A
+// exactly symmetric (row r read as column r, coalesced), R [NA][NCOL] in
+// shared memory, out column-major with column stride NA
+template <int N1, int NCOL>
+__device__ __forceinline__ void fold_product(const double *__restrict__ A, const double *R, double *out) {
+    constexpr int NA = N1 * N1, CB = 12;
+    const int r = threadIdx.x;
+    if (r < NA) {
+        for (int c0 = 0; c0 < NCOL; c0 += CB) {
+            double acc[CB];
+#pragma unroll
+            for (int i = 0; i < CB; ++i) acc[i] = 0.0;
+            for (int k = 0; k < NA; ++k) {
+                const double a = __ldg(A + (size_t)k * NA + r);
+                const double *rk = R + k * NCOL + c0;
+#pragma unroll
+                for (int i = 0; i < CB; ++i)
+                    if (c0 + i < NCOL) acc[i] = fma(a, rk[i], acc[i]);
+            }
+#pragma unroll
+            for (int i = 0; i < CB; ++i)
+                if (c0 + i < NCOL) out[(size_t)(c0 + i) * NA + r] = acc[i];
+        }
+    }
+    __syncthreads();
+}
+
+// Folded operators of the precomputed-inverse route (fold_cols), one CTA per
+// element. The lift matrices R_u, R_v are built a column at a time by lifting
+// a unit line integral with lift_assemble (the stage's own lift), then
+// multiplied by the element inverses; K = M_J^-1 S_c2.
+template <int N1>
+__global__ void __launch_bounds__(nthreads_for(N1 * N1))
+k_var_fold(const double *__restrict__ S, const double *__restrict__ Ainv, const double *__restrict__ Minv,
+           const double *__restrict__ tab, int Q, double *__restrict__ G) {
+    constexpr int NA = N1 * N1;
+    extern __shared__ double sm[];
+    double *R = sm, *L = R + fold_rlen(N1), *tu = L + 12 * N1, *tv = tu + NA;
+    const int e = blockIdx.x, t = threadIdx.x, nt = blockDim.x;
+    const Tabs T = tabs_at(tab, Q, N1);
+    const size_t m2 = (size_t)e * NA * NA;
+    double *Ge = G + (size_t)e * fold_cols(N1) * NA;
+    for (int c = 0; c < 8 * N1; ++c) {   // R_u: line integrals (f, m < 2, j)
+        const int f = c / (2 * N1), mj = c - f * 2 * N1;
+        for (int k = t; k < 12 * N1; k += nt) L[k] = k == f * 3 * N1 + mj ? 1.0 : 0.0;
+        __syncthreads();
+        lift_assemble<N1>(L, T, tu, tv);   // ends with a barrier: L free again
+        if (t < NA) R[t * 8 * N1 + c] = tu[t];
+    }
+    __syncthreads();
+    fold_product<N1, 8 * N1>(Ainv + m2, R, Ge);
+    for (int c = 0; c < 4 * N1; ++c) {   // R_v: line integrals (f, m = 2, j)
+        const int f = c / N1, j = c - f * N1;
+        for (int k = t; k < 12 * N1; k += nt) L[k] = k == f * 3 * N1 + 2 * N1 + j ? 1.0 : 0.0;
+        __syncthreads();
+        lift_assemble<N1>(L, T, tu, tv);
+        if (t < NA) R[t * 4 * N1 + c] = tv[t];
+    }
+    __syncthreads();
+    fold_product<N1, 4 * N1>(Minv + m2, R, Ge + (size_t)8 * N1 * NA);
+    for (int i = t; i < NA * NA; i += nt) R[i] = S[m2 + i];
+    __syncthreads();
+    fold_product<N1, NA>(Minv + m2, R, Ge + (size_t)12 * N1 * NA);
 }
 
 // FP32 copy (round to nearest) of an FP64 array

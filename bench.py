@@ -485,7 +485,7 @@ def run_gdg(args):
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                          "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
                          "traffic": STAGE_TRAFFIC_BYTES,
-                         "kernel": ("k_stage2h" if stage_variant == 1 else "k_stage2p")
+                         "kernel": {1: "k_stage2h", 2: "k_stage2f"}.get(stage_variant, "k_stage2p")
                                    + " (fused RK4 stage, modal route; variant chosen by timing)",
                          "avg_launch_us": stage_ms * 1e3,
                          "avg_launch_us_isolated": stage_ms_isolated * 1e3,

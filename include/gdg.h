@@ -234,10 +234,11 @@ int gdg_step_host(gdg_ctx *ctx, double *u, double *v, double t0, double dt, int 
 /*
  * Stage kernel of a 2-D constant-coefficient context (the modal route of
  * Section 3.2; not a method choice, a launch choice): 0 = one thread per
- * element line, 1 = two threads per line (even / odd modes), -1 = choose by
- * timing both at the next gdg_step (the default).  Both variants perform the
- * same floating-point operations in the same order: results are
- * bit-identical.  Setting a variant drops any captured step graph.
+ * element line, 1 = two threads per line (even / odd modes), 2 = one thread
+ * per line and field (u and v in separate warps), -1 = choose by timing all
+ * three at the next gdg_step (the default).  All variants perform the same
+ * floating-point operations in the same order: results are bit-identical.
+ * Setting a variant drops any captured step graph.
  * GDG_EINVAL on other contexts or values; get: the variant in use (-1 before
  * the choice is made).
  */

@@ -1,6 +1,6 @@
 """Small seeded workloads of each kernel family, for profiling and timing.
 
-python -m paper_2105_01722_gb300.cases const [--n 64] [--p 5] [--steps 8] [--variant -1|0|1]
+python -m paper_2105_01722_gb300.cases const [--n 64] [--p 5] [--steps 8] [--variant -1|0|1|2]
 python -m paper_2105_01722_gb300.cases const3 [--n 16] [--p 5] [--steps 8]
 python -m paper_2105_01722_gb300.cases var   [--n 32] [--p 5] [--steps 2] [--mixed | --inverse]
 python -m paper_2105_01722_gb300.cases batch [--problems 12] [--steps 2] [--mixed]
@@ -34,7 +34,8 @@ def _ms(fn):
 
 def case_const(n=64, N=8, p=5, steps=8, warmup=2, variant=-1):
     """2-D constant coefficient standing mode, n x n elements, modal route
-    (variant: stage kernel, -1 timed choice, 0 / 1 threads per line)."""
+    (variant: stage kernel, -1 timed choice, 0 one line per thread, 1 two
+    threads per line, 2 one thread per line and field)."""
     import torch
     pb = gdg.make_problem(2, (n, n), N, p, flux=gdg.FLUX_UPWIND, c2=1.0)
     ctx = gdg.Context(pb)
@@ -175,7 +176,7 @@ def main(argv=None):
     ap.add_argument("--rows", type=int, default=4096)
     ap.add_argument("--sequential", action="store_true")
     ap.add_argument("--pmax", type=int, default=7)
-    ap.add_argument("--variant", type=int, default=-1, help="const: stage kernel (-1 timed, 0, 1)")
+    ap.add_argument("--variant", type=int, default=-1, help="const: stage kernel (-1 timed, 0, 1, 2)")
     a = ap.parse_args(argv)
     kw = {"steps": a.steps} if a.steps else {}
     if a.case == "const":

@@ -33,7 +33,7 @@ struct ModalParams {
     int parity;           // modes ordered even (r -> 1-r symmetric) first: eR = +-eL, gR = +-gL
     int epb;              // elements per block of the 2-D kernels
     int epbh;             // elements per block of the half-line stage kernel (2 N1 threads each)
-    int split;            // parity stage launches use the half-line kernel (chosen by timing)
+    int split;            // parity stage kernel: 0 one line, 1 half line, 2 field split (chosen by timing)
 };
 
 // RK4 stage modes of the stage kernels

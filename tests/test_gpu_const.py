@@ -190,17 +190,17 @@ def test_step_graph_path_and_remainder():
 
 @pytest.mark.parametrize("c", [c for c in CASES if c["dim"] == 2 and c["N"] >= c["p"] + 1], ids=_ids)
 def test_stage_variants_bit_identical(c):
-    """The one-thread-per-line and the two-threads-per-line stage kernels
-    perform the same operations in the same order: 37 RK4 steps (graph path
-    and remainder) and gdg_rhs give bit-identical states, and both match the
-    oracle; the timed choice reports one of the two."""
+    """The one-thread-per-line, two-threads-per-line and field-split stage
+    kernels perform the same operations in the same order: 37 RK4 steps
+    (graph path and remainder) and gdg_rhs give bit-identical states, and
+    they match the oracle; the timed choice reports one of the three."""
     U, V = _state(c, 50)
     prob = _oracle_problem(c)
     ops = dc.operators(prob)
     h = min(prob.H(k) for k in range(prob.dim)) / prob.N
     dt = 0.1 * h / np.sqrt(c.get("c2", 1.0))
     out = []
-    for variant in (0, 1):
+    for variant in (0, 1, 2):
         ctx = gdg.Context(_gpu_problem(c))
         try:
             ctx.set_stage_variant(variant)
@@ -215,8 +215,9 @@ def test_stage_variants_bit_identical(c):
         ctx.step(u, v, 0.0, dt, 37)
         out.append([x.cpu().numpy() for x in (u, v, du, dv_)])
         ctx.close()
-    for a, b in zip(*out):
-        assert np.array_equal(a, b)
+    for other in out[1:]:
+        for a, b in zip(out[0], other):
+            assert np.array_equal(a, b)
     f = lambda t, U, V: dc.time_derivative(prob, U, V, ops)
     U1, V1 = ti.integrate(f, U, V, 0.0, dt, 37)
     assert _rel_state(_dev(out[0][0]), _dev(out[0][1]), U1, V1) < 10 * _route_floor(prob, U, V)
@@ -224,9 +225,9 @@ def test_stage_variants_bit_identical(c):
     assert ctx.stage_variant() == -1
     u, v = _dev(U), _dev(V)
     ctx.step(u, v, 0.0, dt, 2)
-    assert ctx.stage_variant() in (0, 1)
+    assert ctx.stage_variant() in (0, 1, 2)
     with pytest.raises(gdg.GdgError):
-        ctx.set_stage_variant(2)
+        ctx.set_stage_variant(3)
     ctx.close()
 
 

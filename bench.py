@@ -429,7 +429,9 @@ def run_gdg(args):
     prof = ctx.profile_read()
     ctx.profile(False)
     st_n, st_ms = prof.get("stage", (1, float("nan")))
-    stage_ms_isolated = st_ms / st_n
+    # the persistent step (variant 3) is one launch for all 4R stages of a call
+    stages_per_launch = 4 * R if stage_variant == 3 else 1
+    stage_ms_isolated = st_ms / (st_n * stages_per_launch)
     # stage kernel duration inside the timed (graph) region: the step's time
     # less its entry/exit launches (transform, traces; timed in the pass
     # above), over its 4R stage launches; includes the gaps between launches
@@ -485,18 +487,22 @@ def run_gdg(args):
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                          "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
                          "traffic": STAGE_TRAFFIC_BYTES,
-                         "kernel": {1: "k_stage2h", 2: "k_stage2f"}.get(stage_variant, "k_stage2p")
+                         "kernel": {1: "k_stage2h", 2: "k_stage2f", 3: "k_step2r"}.get(stage_variant, "k_stage2p")
                                    + " (fused RK4 stage, modal route; variant chosen by timing)",
                          "avg_launch_us": stage_ms * 1e3,
                          "avg_launch_us_isolated": stage_ms_isolated * 1e3,
-                         "duration_source": "timed region (CUDA events on the launching stream) less the step's "
-                                            "entry/exit launches, over 4R stage launches; _isolated: events "
-                                            "around each launch outside the graph",
+                         "duration_source": ("timed region (CUDA events on the launching stream) less the step's "
+                                             "entry/exit launches, over 4R stage launches; _isolated: events "
+                                             "around each launch outside the graph") if stage_variant != 3 else
+                                            ("timed region (CUDA events on the launching stream) less the step's "
+                                             "entry/exit launches, over the 4R stages of its one persistent "
+                                             "launch (per-stage figures); _isolated: events around that launch "
+                                             "in a separate pass, over its 4R stages"),
                          "flops_per_launch": flops_per_stage_launch(),
                          "peak_source": "FP64 derived from unit counts and the maximum SM clock: "
                                         "152 SM x 2070 MHz x 4 flop/clk"},
             "kernels": {k: {"launches": n, "ms": t} for k, (n, t) in prof.items()},
-            "gpu_launches": 4 * R * args.steps + 3 * args.steps,
+            "gpu_launches": (4 * R if stage_variant != 3 else 1) * args.steps + 3 * args.steps,
             "e2e": {"value": e2e_val, "unit": "DOF-steps/s", "h2d_bytes_per_step": 2 * dof() * 8,
                     "d2h_bytes_per_step": 2 * dof() * 8},
             "clocks": clocks,

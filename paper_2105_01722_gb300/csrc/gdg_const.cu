@@ -351,6 +351,219 @@ k_stage2f(const __grid_constant__ ModalParams mp, const StageBufs b, double cA, 
     }
 }
 
+// ------------------------------------------------ persistent 2-D step --
+// All RK4 stages of nsteps steps in one cooperative launch (every CTA
+// resident).  Each thread keeps its line's stage input, y_n and RK
+// accumulator in registers from stage to stage; only the face traces go
+// through global memory, and a grid barrier separates the stages.  Every
+// floating-point operation is the one stage2p_body performs, in the same
+// order, on the same values: bit-identical results to the per-stage kernels.
+
+__device__ __forceinline__ unsigned long long gtimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Grid barrier of a cooperative launch.  sync[0] counts arrivals,
+// sync[GB_EPOCH] (its own 128-byte line) holds the number of the last
+// completed barrier, sync[GB_FLAG] is the give-up flag; all zero at launch.
+// `round` counts this kernel's barriers from 1.  Each block arrives with one
+// acquire-release atomic add; the block that completes the count publishes
+// `round` in the epoch word with a release store, and the others poll that
+// word (not the contended counter) with acquire loads, at most limit_ns of
+// wall time, after which the flag is set.  Returns false when this block or
+// another one gave up (the caller then leaves the kernel).
+constexpr int GB_STRIDE = 32, GB_EPOCH = GB_STRIDE, GB_FLAG = 2 * GB_STRIDE, GB_WORDS = 3 * GB_STRIDE;
+
+__device__ bool grid_barrier(unsigned *sync, unsigned round, unsigned long long limit_ns, int *s_ok) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned old;
+        asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(sync), "r"(1u) : "memory");
+        int ok = 1;
+        if (old + 1 == round * gridDim.x) {
+            asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(sync + GB_EPOCH), "r"(round) : "memory");
+        } else {
+            const unsigned long long t0 = gtimer_ns();
+            for (unsigned it = 1; ld_acquire_u32(sync + GB_EPOCH) < round; ++it) {
+                if (gtimer_ns() - t0 > limit_ns) { atomicExch(sync + GB_FLAG, 1u); ok = 0; break; }
+                if ((it & 63u) == 0u && *(volatile unsigned *)(sync + GB_FLAG)) { ok = 0; break; }
+                __nanosleep(32);
+            }
+        }
+        *s_ok = ok;
+    }
+    __syncthreads();
+    return *s_ok != 0;
+}
+
+// one RK stage of stage2p_body on register state: R (stage input, becomes
+// the next stage's input), Nn (y_n), Aa (accumulator), per field
+template <int N1, int MODE, int ALT>
+__device__ __forceinline__ void stage2r(const ModalParams &mp, const double *lam2, const double *trin,
+                                        double *trout, double cA, double cY, int e, int l, bool valid,
+                                        double *fy, double *tile, double (&Ru)[N1], double (&Rv)[N1],
+                                        double (&Nu)[N1], double (&Nv)[N1], double (&Au)[N1], double (&Av)[N1]) {
+    constexpr int NE = (N1 + 1) / 2;
+    const int nx = mp.nx, ny = mp.ny;
+    const int ex = valid ? e % nx : 0, ey = valid ? e / nx : 0;
+    const double b2 = mp.beta2, t2 = mp.tau2;
+    double GA = 0, GB = 0, QA = 0, QB = 0;
+    if (valid) {
+        const double *T = trin;   // written by other CTAs in the previous stage: read from L2
+        double vi, di, vo, dO, g2m, q2m, g2p, q2p;
+        int en, f;
+        bool bnd;
+        vi = __ldcg(T + tix2<N1>(e, 0, 0, l)); di = __ldcg(T + tix2<N1>(e, 0, 1, l));
+        en = ex - 1;
+        if (en < 0 && mp.per_x) en += nx;
+        bnd = en < 0;
+        if (!bnd) { f = ey * nx + en; vo = __ldcg(T + tix2<N1>(f, 1, 0, l)); dO = __ldcg(T + tix2<N1>(f, 1, 1, l)); }
+        else { vo = -vi; dO = -di; }
+        flux2(vi, di, vo, dO, b2, t2, ALT, 0, bnd, g2m, q2m);
+        vi = __ldcg(T + tix2<N1>(e, 1, 0, l)); di = __ldcg(T + tix2<N1>(e, 1, 1, l));
+        en = ex + 1;
+        if (en >= nx && mp.per_x) en -= nx;
+        bnd = en >= nx;
+        if (!bnd) { f = ey * nx + en; vo = __ldcg(T + tix2<N1>(f, 0, 0, l)); dO = __ldcg(T + tix2<N1>(f, 0, 1, l)); }
+        else { vo = -vi; dO = -di; }
+        flux2(vi, di, vo, dO, b2, t2, ALT, 1, bnd, g2p, q2p);
+        GA = g2m + g2p; GB = g2m - g2p; QA = q2m + q2p; QB = q2m - q2p;
+        vi = __ldcg(T + tix2<N1>(e, 2, 0, l)); di = __ldcg(T + tix2<N1>(e, 2, 1, l));
+        en = ey - 1;
+        if (en < 0 && mp.per_y) en += ny;
+        bnd = en < 0;
+        if (!bnd) { f = en * nx + ex; vo = __ldcg(T + tix2<N1>(f, 3, 0, l)); dO = __ldcg(T + tix2<N1>(f, 3, 1, l)); }
+        else { vo = -vi; dO = -di; }
+        flux2(vi, di, vo, dO, b2, t2, ALT, 0, bnd, g2m, q2m);
+        vi = __ldcg(T + tix2<N1>(e, 3, 0, l)); di = __ldcg(T + tix2<N1>(e, 3, 1, l));
+        en = ey + 1;
+        if (en >= ny && mp.per_y) en -= ny;
+        bnd = en >= ny;
+        if (!bnd) { f = en * nx + ex; vo = __ldcg(T + tix2<N1>(f, 2, 0, l)); dO = __ldcg(T + tix2<N1>(f, 2, 1, l)); }
+        else { vo = -vi; dO = -di; }
+        flux2(vi, di, vo, dO, b2, t2, ALT, 1, bnd, g2p, q2p);
+        fy[l] = g2m + g2p; fy[N1 + l] = g2m - g2p;
+        fy[2 * N1 + l] = q2m + q2p; fy[3 * N1 + l] = q2m - q2p;
+    }
+    __syncthreads();
+    if (valid) {
+        const double *L0 = lam2 + l * N1;
+        const double *L1 = lam2 + N1 * N1 + l * N1;
+        const double hgy = mp.d[1].hgL[l], cey = mp.d[1].ceL[l];
+        const double *FG = fy + (l < NE ? 0 : N1);
+        const double *FQ = fy + (l < NE ? 2 * N1 : 3 * N1);
+#pragma unroll
+        for (int k = 0; k < N1; ++k) {
+            const double Yu = Ru[k], Yv = Rv[k];
+            const double xg = k < NE ? GA : GB, xq = k < NE ? QA : QB;
+            const double ru = fma(mp.d[0].hgL[k], xg, hgy * FG[k]);
+            const double rv = fma(L0[k], Yu, fma(mp.d[0].ceL[k], xq, cey * FQ[k]));
+            const double ku = fma(L1[k], ru, Yv);
+            const double kv = rv;
+            if (MODE == M_S1) {
+                Au[k] = cA * ku;
+                Av[k] = cA * kv;
+                Ru[k] = fma(cY, ku, Yu);
+                Rv[k] = fma(cY, kv, Yv);
+            } else if (MODE == M_S23) {
+                Au[k] = fma(cA, ku, Au[k]);
+                Av[k] = fma(cA, kv, Av[k]);
+                Ru[k] = fma(cY, ku, Nu[k]);
+                Rv[k] = fma(cY, kv, Nv[k]);
+            } else {
+                Ru[k] = fma(cA, ku, Nu[k] + Au[k]);
+                Rv[k] = fma(cA, kv, Nv[k] + Av[k]);
+                Nu[k] = Ru[k];
+                Nv[k] = Rv[k];
+            }
+        }
+        double ve = 0, vo_ = 0, de = 0, do_ = 0;
+#pragma unroll
+        for (int k = 0; k < N1; ++k) {
+            if (k < NE) { ve = fma(mp.d[0].eL[k], Rv[k], ve); de = fma(mp.d[0].gL[k], Ru[k], de); }
+            else { vo_ = fma(mp.d[0].eL[k], Rv[k], vo_); do_ = fma(mp.d[0].gL[k], Ru[k], do_); }
+            tile[l * (N1 + 1) + k] = Ru[k];
+            tile[N1 * (N1 + 1) + l * (N1 + 1) + k] = Rv[k];
+        }
+        trout[tix2<N1>(e, 0, 0, l)] = ve + vo_;
+        trout[tix2<N1>(e, 0, 1, l)] = de + do_;
+        trout[tix2<N1>(e, 1, 0, l)] = ve - vo_;
+        trout[tix2<N1>(e, 1, 1, l)] = de - do_;
+    }
+    __syncthreads();
+    if (valid) {
+        const int k = l;
+        double ve = 0, vo_ = 0, de = 0, do_ = 0;
+#pragma unroll
+        for (int j = 0; j < N1; ++j) {
+            const double u = tile[j * (N1 + 1) + k], v = tile[N1 * (N1 + 1) + j * (N1 + 1) + k];
+            if (j < NE) { ve = fma(mp.d[1].eL[j], v, ve); de = fma(mp.d[1].gL[j], u, de); }
+            else { vo_ = fma(mp.d[1].eL[j], v, vo_); do_ = fma(mp.d[1].gL[j], u, do_); }
+        }
+        trout[tix2<N1>(e, 2, 0, k)] = ve + vo_;
+        trout[tix2<N1>(e, 2, 1, k)] = de + do_;
+        trout[tix2<N1>(e, 3, 0, k)] = ve - vo_;
+        trout[tix2<N1>(e, 3, 1, k)] = de - do_;
+    }
+}
+
+// nsteps RK4 steps of the modal state (nU, nV) in place; tr0 holds the
+// traces of y_n on entry and of the result on exit (as enqueue_rk4_step).
+// blockDim.x = epb * N1; sync: GB_WORDS words (see grid_barrier).
+// Registers are allocated per SM sub-partition (16,384 each): at <= 168 per
+// thread three warps fit in one, at 169..176 only two, so the cap keeps
+// 12 instead of 8 warps of the grid resident per SM.
+template <int N1, int ALT>
+__global__ void __maxnreg__(168)
+k_step2r(const __grid_constant__ ModalParams mp, const double *lam2, double *nU, double *nV, double *tr0,
+         double *tr1, double dt, int nsteps, unsigned *sync, unsigned long long limit_ns) {
+    extern __shared__ double smem[];
+    __shared__ int s_ok;
+    const int epb = blockDim.x / N1;
+    const int t = threadIdx.x;
+    const int le = t / N1, l = t - le * N1;
+    const int e = blockIdx.x * epb + le;
+    const bool valid = le < epb && e < mp.ne;
+    double *fy = smem + le * (4 * N1);
+    double *tile = smem + epb * 4 * N1 + le * (2 * N1 * (N1 + 1));
+    const size_t row = ((size_t)(valid ? e : 0) * N1 + l) * N1;
+    double Ru[N1], Rv[N1], Nu[N1], Nv[N1], Au[N1], Av[N1];
+#pragma unroll
+    for (int k = 0; k < N1; ++k) {
+        Nu[k] = valid ? nU[row + k] : 0.0;
+        Nv[k] = valid ? nV[row + k] : 0.0;
+        Ru[k] = Nu[k];
+        Rv[k] = Nv[k];
+        Au[k] = 0.0;
+        Av[k] = 0.0;
+    }
+    unsigned round = 0;
+    for (int step = 0; step < nsteps; ++step) {
+        stage2r<N1, M_S1, ALT>(mp, lam2, tr0, tr1, dt / 6.0, 0.5 * dt, e, l, valid, fy, tile, Ru, Rv, Nu, Nv, Au, Av);
+        if (!grid_barrier(sync, ++round, limit_ns, &s_ok)) return;
+        stage2r<N1, M_S23, ALT>(mp, lam2, tr1, tr0, dt / 3.0, 0.5 * dt, e, l, valid, fy, tile, Ru, Rv, Nu, Nv, Au, Av);
+        if (!grid_barrier(sync, ++round, limit_ns, &s_ok)) return;
+        stage2r<N1, M_S23, ALT>(mp, lam2, tr0, tr1, dt / 3.0, dt, e, l, valid, fy, tile, Ru, Rv, Nu, Nv, Au, Av);
+        if (!grid_barrier(sync, ++round, limit_ns, &s_ok)) return;
+        stage2r<N1, M_S4, ALT>(mp, lam2, tr1, tr0, dt / 6.0, 0.0, e, l, valid, fy, tile, Ru, Rv, Nu, Nv, Au, Av);
+        if (step + 1 < nsteps && !grid_barrier(sync, ++round, limit_ns, &s_ok)) return;
+    }
+    if (valid) {
+#pragma unroll
+        for (int k = 0; k < N1; ++k) {
+            nU[row + k] = Nu[k];
+            nV[row + k] = Nv[k];
+        }
+    }
+}
+
 // traces of a modal state (start of gdg_step and gdg_rhs)
 template <int N1>
 __global__ void __launch_bounds__(MAXB2)
@@ -640,6 +853,8 @@ __global__ void k_sep1(int ne, const double *in0, const double *in1, double *out
 // ------------------------------------------------------ dispatch ---------
 
 #define GDG_N1_CASES(X) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) X(14) X(15) X(16)
+// element sizes of the persistent step (its register state is 6 N1 doubles per thread)
+#define GDG_N1_CASES_P(X) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10)
 
 size_t smem_stage2(int n1, int epb) { return (size_t)epb * (4 * n1 + 2 * n1 * (n1 + 1)) * sizeof(double); }
 size_t smem_traces2(int n1, int epb) { return (size_t)epb * (2 * n1 * (n1 + 1)) * sizeof(double); }
@@ -798,6 +1013,97 @@ void launch_sep(gdg_ctx *ctx, const double *in0, const double *in1, double *out0
 double *buf(gdg_ctx *ctx, int i) { return ctx->d_state + (size_t)i * ctx->ndof; }
 enum { B_NU = 0, B_NV, B_AU, B_AV, B_XU, B_XV, B_YU, B_YV, B_KU, B_KV, B_COUNT };
 
+// The persistent step needs every CTA of its grid resident at once.  Its
+// elements per block: the per-stage kernels' choice if that grid fits,
+// else the fitting one with the best (used lanes) x (element balance over
+// the SMs); 0 if none fits.
+template <int N1>
+int persist_epb_n(const gdg_ctx *ctx) {
+    const ModalParams &mp = ctx->mp;
+    int coop = 0, sms = 0;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, ctx->device);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    if (!coop || sms <= 0) return 0;
+    auto fits = [&](int epb) {
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, mp.alt ? k_step2r<N1, 1> : k_step2r<N1, 0>, epb * N1,
+                                                          smem_stage2(N1, epb)) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        return (long long)nb * sms >= (mp.ne + epb - 1) / epb;
+    };
+    if (fits(mp.epb)) return mp.epb;
+    int best = 0;
+    double best_eff = -1.0;
+    for (int epb = 1; epb * N1 <= MAXB2; ++epb) {
+        if (!fits(epb)) continue;
+        const int threads = epb * N1, warps = (threads + 31) / 32;
+        const int blocks = (mp.ne + epb - 1) / epb, per_sm = (blocks + sms - 1) / sms;
+        const double eff = (double)threads / (32.0 * warps) * (((double)mp.ne / sms) / ((double)per_sm * epb));
+        if (eff > best_eff + 1e-9) { best_eff = eff; best = epb; }
+    }
+    return best;
+}
+
+int persist_epb(const gdg_ctx *ctx) {
+    if (ctx->dim != 2 || !ctx->mp.parity || !ctx->d_sync) return 0;
+    switch (ctx->n1) {
+#define X(n) case n: return persist_epb_n<n>(ctx);
+        GDG_N1_CASES_P(X)
+#undef X
+    }
+    return 0;
+}
+bool persist_fits(gdg_ctx *ctx) {
+    ctx->mp.epbp = persist_epb(ctx);
+    return ctx->mp.epbp > 0;
+}
+
+template <int N1>
+void launch_persist_n(gdg_ctx *ctx, double dt, int nsteps, cudaStream_t s) {
+    const ModalParams &mp = ctx->mp;
+    const dim3 grid((mp.ne + mp.epbp - 1) / mp.epbp), block(mp.epbp * N1);
+    const double *lam2 = ctx->d_lam2;
+    double *nU = buf(ctx, B_NU), *nV = buf(ctx, B_NV), *tr0 = ctx->d_tr, *tr1 = ctx->d_tr + ctx->tr_len;
+    unsigned *sync = ctx->d_sync;
+    unsigned long long lim = ctx->wait_limit_ns;
+    void *args[] = {(void *)&mp, (void *)&lam2, (void *)&nU, (void *)&nV, (void *)&tr0, (void *)&tr1,
+                    (void *)&dt, (void *)&nsteps, (void *)&sync, (void *)&lim};
+    cudaLaunchCooperativeKernel(mp.alt ? (const void *)k_step2r<N1, 1> : (const void *)k_step2r<N1, 0>, grid, block,
+                                args, smem_stage2(N1, mp.epbp), s);
+}
+
+// nsteps RK4 steps of the modal state in one persistent launch (tr0 holds
+// the traces of y_n before and after); the give-up flag is read by
+// persist_failed once the stream has run
+void launch_persist(gdg_ctx *ctx, double dt, int nsteps, cudaStream_t s) {
+    // at most 2^16 steps per launch keeps the barrier counters far from overflow
+    for (int done = 0; done < nsteps;) {
+        const int k = std::min(nsteps - done, 1 << 16);
+        cudaMemsetAsync(ctx->d_sync, 0, GB_WORDS * sizeof(unsigned), s);
+        switch (ctx->n1) {
+#define X(n) case n: GDG_PROF(ctx, GDG_K_STAGE, s, launch_persist_n<n>(ctx, dt, k, s)); break;
+            GDG_N1_CASES_P(X)
+#undef X
+        }
+        done += k;
+    }
+}
+
+// copy the give-up flag to the host and wait for the stream: true if a grid
+// barrier of the last persistent launch gave up (not while s is capturing)
+bool persist_failed(gdg_ctx *ctx, cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(s, &cs);
+    if (cs != cudaStreamCaptureStatusNone) return false;
+    unsigned *flag = reinterpret_cast<unsigned *>(ctx->h_red + 7);
+    *flag = 0;
+    cudaMemcpyAsync(flag, ctx->d_sync + GB_FLAG, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
+    return *flag != 0;
+}
+
 int set_smem_limits() {
     // the 2-D kernels may need more than the 48 KB default of dynamic shared memory
     static bool done = false;
@@ -831,6 +1137,11 @@ int set_smem_limits() {
     cudaFuncSetAttribute(k_traces2<n>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);        \
     cudaFuncSetAttribute(k_sep2<n>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     GDG_N1_CASES(X)
+#undef X
+#define X(n)                                                                                   \
+    cudaFuncSetAttribute(k_step2r<n, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);    \
+    cudaFuncSetAttribute(k_step2r<n, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    GDG_N1_CASES_P(X)
 #undef X
     gdg3_set_smem_limits();
     done = true;
@@ -997,7 +1308,8 @@ int gdg_const_setup(gdg_ctx *ctx) {
         (st = gdg_cuda_check(ctx, cudaMalloc((void **)&ctx->d_state, (size_t)B_COUNT * ctx->ndof * sizeof(double)), "alloc")) ||
         (st = gdg_cuda_check(ctx, cudaMalloc((void **)&ctx->d_tr, (size_t)2 * ctx->tr_len * sizeof(double)), "alloc")) ||
         (st = gdg_cuda_check(ctx, cudaMalloc((void **)&ctx->d_red, (size_t)(ctx->red_len + 1) * sizeof(double)), "alloc")) ||
-        (st = gdg_cuda_check(ctx, cudaMallocHost((void **)&ctx->h_red, 8 * sizeof(double)), "alloc")))
+        (st = gdg_cuda_check(ctx, cudaMallocHost((void **)&ctx->h_red, 8 * sizeof(double)), "alloc")) ||
+        (ctx->dim == 2 && (st = gdg_cuda_check(ctx, cudaMalloc((void **)&ctx->d_sync, GB_WORDS * sizeof(unsigned)), "alloc"))))
         return st;
     if ((st = gdg_cuda_check(ctx, cudaMemcpy(ctx->d_mats, tables.data(), tables.size() * sizeof(double), cudaMemcpyHostToDevice), "upload")) ||
         (st = gdg_cuda_check(ctx, cudaMemcpy(ctx->d_lam2, l2.data(), l2.size() * sizeof(double), cudaMemcpyHostToDevice), "upload")))
@@ -1014,6 +1326,8 @@ void gdg_const_free(gdg_ctx *ctx) {
     cudaFree(ctx->d_state);
     cudaFree(ctx->d_tr);
     cudaFree(ctx->d_red);
+    cudaFree(ctx->d_sync);
+    ctx->d_sync = nullptr;
     if (ctx->h_red) cudaFreeHost(ctx->h_red);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     ctx->d_mats = ctx->d_lam2 = ctx->d_state = ctx->d_tr = ctx->d_red = ctx->h_red = nullptr;
@@ -1042,10 +1356,12 @@ int gdg_const_mass_solve(gdg_ctx *ctx, int which, const double *b, double *x, cu
 }
 
 // Pick the stage kernel of a 2-D parity context by timing: one line per
-// thread (k_stage2p), two (k_stage2h), or one per line and field
-// (k_stage2f).  All compute bit-identical results; the trial launches write
-// only buffers the step then rewrites.
-int tune_stage_kernel(gdg_ctx *ctx, double dt, cudaStream_t s) {
+// thread (k_stage2p), two (k_stage2h), one per line and field (k_stage2f),
+// or the persistent step (k_step2r) where its grid fits the GPU at once.
+// All compute bit-identical results.  The per-stage trials write only
+// buffers the step then rewrites; the persistent trials advance the modal
+// state, which is then rebuilt from (u, v).
+int tune_stage_kernel(gdg_ctx *ctx, double dt, cudaStream_t s, const double *u, const double *v) {
     ModalParams &mp = ctx->mp;
     ctx->stage_tuned = true;
     if (ctx->dim != 2 || !mp.parity) return GDG_OK;
@@ -1062,7 +1378,7 @@ int tune_stage_kernel(gdg_ctx *ctx, double dt, cudaStream_t s) {
     // alternately; these write only X, the accumulator and the second trace
     // buffer, which the step's first stage overwrites); another variant must
     // beat the one-line kernel by 1 % to replace it
-    float best[3] = {1e30f, 1e30f, 1e30f};
+    float best[4] = {1e30f, 1e30f, 1e30f, 1e30f};
     for (int split = 0; split < 3; ++split) {
         mp.split = split;
         for (int rep = 0; rep < 5; ++rep) {
@@ -1076,17 +1392,41 @@ int tune_stage_kernel(gdg_ctx *ctx, double dt, cudaStream_t s) {
             best[split] = std::min(best[split], ms);
         }
     }
+    if (persist_fits(ctx)) {   // one step = 4 stages per trial launch
+        mp.split = 3;
+        for (int rep = 0; rep < 5; ++rep) {
+            float ms = 0.f;
+            cudaEventRecord(e0, s);
+            launch_persist(ctx, dt, 1, s);
+            cudaEventRecord(e1, s);
+            cudaEventSynchronize(e1);
+            cudaEventElapsedTime(&ms, e0, e1);
+            best[3] = std::min(best[3], ms);
+        }
+        if (persist_failed(ctx, s)) best[3] = 1e30f;
+        launch_sep(ctx, u, v, buf(ctx, B_NU), buf(ctx, B_NV), T_P, nullptr, -1, s);
+        launch_traces(ctx, buf(ctx, B_NU), buf(ctx, B_NV), ctx->d_tr, s);
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     int pick = 0;
-    for (int v = 1; v < 3; ++v)
-        if (best[v] < 0.99f * best[0] && best[v] < best[pick]) pick = v;
+    for (int k = 1; k < 4; ++k)
+        if (best[k] < 0.99f * best[0] && best[k] < best[pick]) pick = k;
     mp.split = pick;
     return gdg_cuda_check(ctx, cudaGetLastError(), "stage kernel choice");
 }
 
+extern "C" int gdg_set_wait_limit(gdg_ctx *ctx, double seconds) {
+    if (!ctx || !(seconds > 0.0) || !std::isfinite(seconds)) return GDG_EINVAL;
+    const double ns = seconds * 1e9;
+    ctx->wait_limit_ns = ns < 1.0 ? 1ull : (ns > 1e18 ? 1000000000000000000ull : (unsigned long long)ns);
+    return GDG_OK;
+}
+
 extern "C" int gdg_set_stage_variant(gdg_ctx *ctx, int variant) {
-    if (!ctx || ctx->var || ctx->dim != 2 || !ctx->mp.parity || variant < -1 || variant > 2) return GDG_EINVAL;
+    if (!ctx || ctx->var || ctx->dim != 2 || !ctx->mp.parity || variant < -1 || variant > 3) return GDG_EINVAL;
+    if (variant == 3 && !persist_fits(ctx))
+        return gdg_set_err(ctx, GDG_EUNSUPPORTED, "persistent step: the grid does not fit the GPU at once");
     if (ctx->graph.exec) {
         cudaGraphExecDestroy(ctx->graph.exec);
         ctx->graph.exec = nullptr;
@@ -1107,7 +1447,15 @@ int gdg_const_step(gdg_ctx *ctx, double *u, double *v, double dt, int nsteps, cu
     launch_sep(ctx, u, v, buf(ctx, B_NU), buf(ctx, B_NV), T_P, nullptr, -1, s);
     launch_traces(ctx, buf(ctx, B_NU), buf(ctx, B_NV), ctx->d_tr, s);
     if ((st = gdg_cuda_check(ctx, cudaGetLastError(), "gdg_step prologue"))) return st;
-    if (!ctx->stage_tuned && (st = tune_stage_kernel(ctx, dt, s))) return st;
+    if (!ctx->stage_tuned && (st = tune_stage_kernel(ctx, dt, s, u, v))) return st;
+    if (ctx->dim == 2 && ctx->mp.parity && ctx->mp.split == 3) {
+        if (nsteps > 0) launch_persist(ctx, dt, nsteps, s);
+        launch_sep(ctx, buf(ctx, B_NU), buf(ctx, B_NV), u, v, T_PSI, nullptr, -1, s);
+        if ((st = gdg_cuda_check(ctx, cudaGetLastError(), "gdg_step (persistent)"))) return st;
+        if (nsteps > 0 && persist_failed(ctx, s))
+            return gdg_set_err(ctx, GDG_ETIMEOUT, "persistent step: a grid barrier gave up (wait limit)");
+        return gdg_cuda_check(ctx, cudaGetLastError(), "gdg_step (persistent)");
+    }
     // graph of G steps, replayed; the remainder is launched directly
     const int G = (nsteps >= 16 && !ctx->prof.on) ? 16 : 0;
     if (G) {

@@ -33,7 +33,9 @@ struct ModalParams {
     int parity;           // modes ordered even (r -> 1-r symmetric) first: eR = +-eL, gR = +-gL
     int epb;              // elements per block of the 2-D kernels
     int epbh;             // elements per block of the half-line stage kernel (2 N1 threads each)
-    int split;            // parity stage kernel: 0 one line, 1 half line, 2 field split (chosen by timing)
+    int split;            // parity stage kernel: 0 one line, 1 half line, 2 field split, 3 persistent step
+                          // (chosen by timing)
+    int epbp;             // elements per block of the persistent step (0: its grid does not fit)
 };
 
 // RK4 stage modes of the stage kernels
@@ -108,6 +110,8 @@ struct gdg_ctx {
     cudaStream_t cap_stream = nullptr;
     GraphCache graph;
     bool stage_tuned = false;     // stage kernel variant chosen (first gdg_step)
+    unsigned *d_sync = nullptr;   // grid barrier of the persistent step: arrivals, give-up flag
+    unsigned long long wait_limit_ns = 1000000000ull;   // bound on any device-side wait
 
     VarData *var = nullptr;
     Profiler prof;

@@ -88,6 +88,7 @@ EXPORTS = {
     "gdg_profile_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "gdg_set_stage_variant": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "gdg_get_stage_variant": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
+    "gdg_set_wait_limit": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double]),
     "gdg_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
                                         ctypes.POINTER(ctypes.c_double)]),
 }
@@ -292,8 +293,13 @@ class Context:
                     "gdg_step_host")
 
     def set_stage_variant(self, variant):
-        """2-D constant coefficient: 0 one thread per line, 1 two, -1 timed choice."""
+        """2-D constant coefficient: 0 one thread per line, 1 two, 2 one per line
+        and field, 3 persistent step, -1 timed choice."""
         self._check(lib().gdg_set_stage_variant(self._h, int(variant)), "gdg_set_stage_variant")
+
+    def set_wait_limit(self, seconds):
+        """Bound on any device-side wait (seconds of wall time)."""
+        self._check(lib().gdg_set_wait_limit(self._h, float(seconds)), "gdg_set_wait_limit")
 
     def stage_variant(self):
         out = ctypes.c_int()

@@ -191,16 +191,17 @@ def test_step_graph_path_and_remainder():
 @pytest.mark.parametrize("c", [c for c in CASES if c["dim"] == 2 and c["N"] >= c["p"] + 1], ids=_ids)
 def test_stage_variants_bit_identical(c):
     """The one-thread-per-line, two-threads-per-line and field-split stage
-    kernels perform the same operations in the same order: 37 RK4 steps
-    (graph path and remainder) and gdg_rhs give bit-identical states, and
-    they match the oracle; the timed choice reports one of the three."""
+    kernels and the persistent step perform the same operations in the same
+    order: 37 RK4 steps (graph path and remainder, or one persistent launch)
+    and gdg_rhs give bit-identical states, and they match the oracle; the
+    timed choice reports one of the four."""
     U, V = _state(c, 50)
     prob = _oracle_problem(c)
     ops = dc.operators(prob)
     h = min(prob.H(k) for k in range(prob.dim)) / prob.N
     dt = 0.1 * h / np.sqrt(c.get("c2", 1.0))
     out = []
-    for variant in (0, 1, 2):
+    for variant in (0, 1, 2, 3):
         ctx = gdg.Context(_gpu_problem(c))
         try:
             ctx.set_stage_variant(variant)
@@ -225,9 +226,9 @@ def test_stage_variants_bit_identical(c):
     assert ctx.stage_variant() == -1
     u, v = _dev(U), _dev(V)
     ctx.step(u, v, 0.0, dt, 2)
-    assert ctx.stage_variant() in (0, 1, 2)
+    assert ctx.stage_variant() in (0, 1, 2, 3)
     with pytest.raises(gdg.GdgError):
-        ctx.set_stage_variant(3)
+        ctx.set_stage_variant(4)
     ctx.close()
 
 
@@ -302,3 +303,23 @@ def test_config_2d_64x64_p5_full_size():
     err = np.sqrt(np.mean((u.cpu().numpy() - ue.ravel()) ** 2))
     assert err < 1e-10
     ctx.close()
+
+
+def test_persistent_step_headline_mesh_bit_identical():
+    """64 x 64 elements, p = 5 (the headline mesh: one block of 7 elements per
+    63 threads, 586 blocks resident at once): the persistent step over 37
+    steps in one launch equals the per-stage kernels (graph path) bit for
+    bit, and so does a second call continuing from there."""
+    pb = gdg.make_problem(2, (64, 64), 8, 5, flux=gdg.FLUX_UPWIND)
+    X, Y = inputs.cartesian_nodes((64, 64), 8)
+    U0, V0 = inputs.standing_mode_2d(X, Y)
+    out = []
+    for variant in (0, 3):
+        ctx = gdg.Context(pb)
+        ctx.set_stage_variant(variant)
+        u, v = _dev(U0), _dev(V0)
+        ctx.step(u, v, 0.0, 1e-4, 37)
+        ctx.step(u, v, 37e-4, 1e-4, 5)
+        out.append((u.cpu().numpy(), v.cpu().numpy()))
+        ctx.close()
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])

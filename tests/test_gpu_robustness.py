@@ -8,7 +8,9 @@
   as the uninterrupted run with the same call boundaries.
 * Faults are injected on the host and reported as status codes: a NaN in
   the state gives GDG_ENONFINITE from gdg_energy; a one-iteration PCG limit
-  gives GDG_ENOCONV with the iterates kept; bad arguments give GDG_EINVAL.
+  gives GDG_ENOCONV with the iterates kept; bad arguments give GDG_EINVAL; a
+  wait limit too short for the persistent step's grid barrier gives
+  GDG_ETIMEOUT, and the context then steps correctly with a normal limit.
 """
 import numpy as np
 import pytest
@@ -150,4 +152,34 @@ def test_one_iteration_limit_reports_noconv():
         ctx.pcg(gdg.OP_S, b, x)
     assert err.value.status == gdg.ENOCONV
     assert torch.isfinite(x).all() and x.abs().sum() > 0    # the iterate is kept
+    ctx.close()
+
+
+def test_grid_barrier_wait_limit_reports_timeout():
+    """The persistent step waits at a grid barrier between stages; with a
+    1 ns wait limit the first block to arrive gives up, every block leaves
+    the kernel and gdg_step returns GDG_ETIMEOUT.  With the default limit
+    the same context then advances the state exactly as the per-stage
+    kernel does."""
+    kw = dict(dim=2, n=(12, 10), N=8, p=5, bc=(gdg.BC_DIRICHLET, gdg.BC_PERIODIC))
+    ctx = gdg.Context(gdg.make_problem(**kw))
+    ctx.set_stage_variant(3)
+    U = inputs.random_state(ctx.n, 8)
+    V = inputs.random_state(ctx.n, 9)
+    u, v = _dev(U), _dev(V)
+    ctx.set_wait_limit(1e-9)
+    with pytest.raises(gdg.GdgError) as err:
+        ctx.step(u, v, 0.0, 2e-4, 64)
+    assert err.value.status == gdg.ETIMEOUT
+    with pytest.raises(gdg.GdgError):
+        ctx.set_wait_limit(0.0)
+    ctx.set_wait_limit(1.0)
+    u, v = _dev(U), _dev(V)
+    ctx.step(u, v, 0.0, 2e-4, 20)
+    ref = gdg.Context(gdg.make_problem(**kw))
+    ref.set_stage_variant(0)
+    ur, vr = _dev(U), _dev(V)
+    ref.step(ur, vr, 0.0, 2e-4, 20)
+    assert torch.equal(u, ur) and torch.equal(v, vr)
+    ref.close()
     ctx.close()

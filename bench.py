@@ -54,10 +54,12 @@ def flops_per_stage_launch(w=WORKLOAD):
 # probe measured 1.196 TFLOP/s on this GPU.
 FP64_PEAK_TFLOPS = 152 * 2.070e9 * 4 / 1e12
 
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one k_stage2p
-# launch of this workload, from one ncu capture: the mean over the four stage
-# launches of one RK4 step (None when the kernel has changed since).
-STAGE_TRAFFIC_BYTES = 15.66e6
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per RK stage of
+# this workload, from one ncu capture per stage kernel (None for a kernel
+# without a capture of its current code):
+#   k_stage2p: the mean over the four stage launches of one RK4 step
+#   k_step2r: one persistent launch of one RK4 step, over its 4 stages
+STAGE_TRAFFIC_BYTES = {0: 15.66e6, 3: 7.747584e6 / 4}
 
 
 def _env_rank():
@@ -486,7 +488,7 @@ def run_gdg(args):
                        "l2": "flushed between timed steps (512 MB write; state is 5.3 MB)"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                          "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                         "traffic": STAGE_TRAFFIC_BYTES,
+                         "traffic": STAGE_TRAFFIC_BYTES.get(stage_variant),
                          "kernel": {1: "k_stage2h", 2: "k_stage2f", 3: "k_step2r"}.get(stage_variant, "k_stage2p")
                                    + " (fused RK4 stage, modal route; variant chosen by timing)",
                          "avg_launch_us": stage_ms * 1e3,

@@ -370,37 +370,82 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
     return v;
 }
 
-// Grid barrier of a cooperative launch.  sync[0] counts arrivals,
-// sync[GB_EPOCH] (its own 128-byte line) holds the number of the last
-// completed barrier, sync[GB_FLAG] is the give-up flag; all zero at launch.
-// `round` counts this kernel's barriers from 1.  Each block arrives with one
-// acquire-release atomic add; the block that completes the count publishes
-// `round` in the epoch word with a release store, and the others poll that
-// word (not the contended counter) with acquire loads, at most limit_ns of
-// wall time, after which the flag is set.  Returns false when this block or
-// another one gave up (the caller then leaves the kernel).
-constexpr int GB_STRIDE = 32, GB_EPOCH = GB_STRIDE, GB_FLAG = 2 * GB_STRIDE, GB_WORDS = 3 * GB_STRIDE;
+// Neighbour synchronisation of the persistent step.  Blocks exchange data
+// only through the face traces of their elements' face neighbours, so a
+// block waits for those blocks alone, not for the whole grid.  sync[0] is
+// the give-up flag; block b's flag is sync[NB_BASE + b NB_STRIDE] (its own
+// 32-byte sector), all zero at launch.  After stage `round` every block
+// publishes `round` (fence, then store: a release), then waits (acquire
+// loads by warp 0) until every block in s_nb[0..nnb) has published it: the
+// traces it is about to read are written, and the buffer its next stage
+// overwrites has been read by them.  Every wait is bounded by limit_ns of
+// wall time, after which the give-up flag is set; returns false when this
+// block or another one gave up (the caller then leaves the kernel).
+constexpr int NB_BASE = 32, NB_STRIDE = 8;
+__host__ __device__ constexpr size_t sync_words(int blocks) { return NB_BASE + (size_t)NB_STRIDE * blocks; }
 
-__device__ bool grid_barrier(unsigned *sync, unsigned round, unsigned long long limit_ns, int *s_ok) {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned old;
-        asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(sync), "r"(1u) : "memory");
-        int ok = 1;
-        if (old + 1 == round * gridDim.x) {
-            asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(sync + GB_EPOCH), "r"(round) : "memory");
-        } else {
-            const unsigned long long t0 = gtimer_ns();
-            for (unsigned it = 1; ld_acquire_u32(sync + GB_EPOCH) < round; ++it) {
-                if (gtimer_ns() - t0 > limit_ns) { atomicExch(sync + GB_FLAG, 1u); ok = 0; break; }
-                if ((it & 63u) == 0u && *(volatile unsigned *)(sync + GB_FLAG)) { ok = 0; break; }
-                __nanosleep(32);
-            }
+__device__ bool neighbour_sync(unsigned *sync, const int *s_nb, int nnb, unsigned round,
+                               unsigned long long limit_ns, int *s_ok) {
+    __syncthreads();   // this block's trace writes of stage `round` are done
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        if (lane == 0) {
+            __threadfence();
+            asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(sync + NB_BASE + (size_t)blockIdx.x * NB_STRIDE),
+                         "r"(round) : "memory");
         }
-        *s_ok = ok;
+        const unsigned long long t0 = gtimer_ns();
+        int ok = 1;
+        for (unsigned it = 1;; ++it) {
+            bool done = true;
+            for (int i = lane; i < nnb; i += 32) {
+                const int nb = s_nb[i];
+                if (nb >= 0 && ld_acquire_u32(sync + NB_BASE + (size_t)nb * NB_STRIDE) < round) done = false;
+            }
+            if (__all_sync(0xffffffffu, done)) break;
+            int stop = 0;
+            if (lane == 0) {
+                if (gtimer_ns() - t0 > limit_ns) { atomicExch(sync, 1u); stop = 1; }
+                else if ((it & 63u) == 0u && *(volatile unsigned *)sync) stop = 1;
+            }
+            if (__shfl_sync(0xffffffffu, stop, 0)) { ok = 0; break; }
+        }
+        if (lane == 0) *s_ok = ok;
     }
     __syncthreads();
     return *s_ok != 0;
+}
+
+// blocks holding the face neighbours of block b's elements, one entry per
+// (element, face): -1 for a boundary face or a neighbour in block b itself
+__device__ void neighbour_blocks(const ModalParams &mp, int epb, int *s_nb) {
+    for (int i = threadIdx.x; i < 4 * epb; i += blockDim.x) {
+        const int e = blockIdx.x * epb + (i >> 2), dir = i & 3;
+        int nbb = -1;
+        if (e < mp.ne) {
+            const int nx = mp.nx, ny = mp.ny, ex = e % nx, ey = e / nx;
+            int en = -1;
+            if (dir == 0) {
+                int x = ex - 1;
+                if (x < 0 && mp.per_x) x += nx;
+                if (x >= 0) en = ey * nx + x;
+            } else if (dir == 1) {
+                int x = ex + 1;
+                if (x >= nx && mp.per_x) x -= nx;
+                if (x < nx) en = ey * nx + x;
+            } else if (dir == 2) {
+                int y = ey - 1;
+                if (y < 0 && mp.per_y) y += ny;
+                if (y >= 0) en = y * nx + ex;
+            } else {
+                int y = ey + 1;
+                if (y >= ny && mp.per_y) y -= ny;
+                if (y < ny) en = y * nx + ex;
+            }
+            if (en >= 0 && en / epb != (int)blockIdx.x) nbb = en / epb;
+        }
+        s_nb[i] = nbb;
+    }
 }
 
 // one RK stage of stage2p_body on register state: R (stage input, becomes
@@ -516,7 +561,8 @@ __device__ __forceinline__ void stage2r(const ModalParams &mp, const double *lam
 
 // nsteps RK4 steps of the modal state (nU, nV) in place; tr0 holds the
 // traces of y_n on entry and of the result on exit (as enqueue_rk4_step).
-// blockDim.x = epb * N1; sync: GB_WORDS words (see grid_barrier).
+// blockDim.x = epb * N1 (epb <= MAXB2 / N1); sync: sync_words(gridDim.x)
+// words (see neighbour_sync).
 // Registers are allocated per SM sub-partition (16,384 each): at <= 168 per
 // thread three warps fit in one, at 169..176 only two, so the cap keeps
 // 12 instead of 8 warps of the grid resident per SM.
@@ -526,6 +572,7 @@ k_step2r(const __grid_constant__ ModalParams mp, const double *lam2, double *nU,
          double *tr1, double dt, int nsteps, unsigned *sync, unsigned long long limit_ns) {
     extern __shared__ double smem[];
     __shared__ int s_ok;
+    __shared__ int s_nb[4 * (MAXB2 / N1)];
     const int epb = blockDim.x / N1;
     const int t = threadIdx.x;
     const int le = t / N1, l = t - le * N1;
@@ -534,6 +581,8 @@ k_step2r(const __grid_constant__ ModalParams mp, const double *lam2, double *nU,
     double *fy = smem + le * (4 * N1);
     double *tile = smem + epb * 4 * N1 + le * (2 * N1 * (N1 + 1));
     const size_t row = ((size_t)(valid ? e : 0) * N1 + l) * N1;
+    neighbour_blocks(mp, epb, s_nb);   // read after the first stage's barriers
+    const int nnb = 4 * epb;
     double Ru[N1], Rv[N1], Nu[N1], Nv[N1], Au[N1], Av[N1];
 #pragma unroll
     for (int k = 0; k < N1; ++k) {
@@ -547,13 +596,13 @@ k_step2r(const __grid_constant__ ModalParams mp, const double *lam2, double *nU,
     unsigned round = 0;
     for (int step = 0; step < nsteps; ++step) {
         stage2r<N1, M_S1, ALT>(mp, lam2, tr0, tr1, dt / 6.0, 0.5 * dt, e, l, valid, fy, tile, Ru, Rv, Nu, Nv, Au, Av);
-        if (!grid_barrier(sync, ++round, limit_ns, &s_ok)) return;
+        if (!neighbour_sync(sync, s_nb, nnb, ++round, limit_ns, &s_ok)) return;
         stage2r<N1, M_S23, ALT>(mp, lam2, tr1, tr0, dt / 3.0, 0.5 * dt, e, l, valid, fy, tile, Ru, Rv, Nu, Nv, Au, Av);
-        if (!grid_barrier(sync, ++round, limit_ns, &s_ok)) return;
+        if (!neighbour_sync(sync, s_nb, nnb, ++round, limit_ns, &s_ok)) return;
         stage2r<N1, M_S23, ALT>(mp, lam2, tr0, tr1, dt / 3.0, dt, e, l, valid, fy, tile, Ru, Rv, Nu, Nv, Au, Av);
-        if (!grid_barrier(sync, ++round, limit_ns, &s_ok)) return;
+        if (!neighbour_sync(sync, s_nb, nnb, ++round, limit_ns, &s_ok)) return;
         stage2r<N1, M_S4, ALT>(mp, lam2, tr1, tr0, dt / 6.0, 0.0, e, l, valid, fy, tile, Ru, Rv, Nu, Nv, Au, Av);
-        if (step + 1 < nsteps && !grid_barrier(sync, ++round, limit_ns, &s_ok)) return;
+        if (step + 1 < nsteps && !neighbour_sync(sync, s_nb, nnb, ++round, limit_ns, &s_ok)) return;
     }
     if (valid) {
 #pragma unroll
@@ -1081,7 +1130,7 @@ void launch_persist(gdg_ctx *ctx, double dt, int nsteps, cudaStream_t s) {
     // at most 2^16 steps per launch keeps the barrier counters far from overflow
     for (int done = 0; done < nsteps;) {
         const int k = std::min(nsteps - done, 1 << 16);
-        cudaMemsetAsync(ctx->d_sync, 0, GB_WORDS * sizeof(unsigned), s);
+        cudaMemsetAsync(ctx->d_sync, 0, sync_words((ctx->mp.ne + ctx->mp.epbp - 1) / ctx->mp.epbp) * sizeof(unsigned), s);
         switch (ctx->n1) {
 #define X(n) case n: GDG_PROF(ctx, GDG_K_STAGE, s, launch_persist_n<n>(ctx, dt, k, s)); break;
             GDG_N1_CASES_P(X)
@@ -1099,7 +1148,7 @@ bool persist_failed(gdg_ctx *ctx, cudaStream_t s) {
     if (cs != cudaStreamCaptureStatusNone) return false;
     unsigned *flag = reinterpret_cast<unsigned *>(ctx->h_red + 7);
     *flag = 0;
-    cudaMemcpyAsync(flag, ctx->d_sync + GB_FLAG, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(flag, ctx->d_sync, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
     cudaStreamSynchronize(s);
     return *flag != 0;
 }
@@ -1309,7 +1358,7 @@ int gdg_const_setup(gdg_ctx *ctx) {
         (st = gdg_cuda_check(ctx, cudaMalloc((void **)&ctx->d_tr, (size_t)2 * ctx->tr_len * sizeof(double)), "alloc")) ||
         (st = gdg_cuda_check(ctx, cudaMalloc((void **)&ctx->d_red, (size_t)(ctx->red_len + 1) * sizeof(double)), "alloc")) ||
         (st = gdg_cuda_check(ctx, cudaMallocHost((void **)&ctx->h_red, 8 * sizeof(double)), "alloc")) ||
-        (ctx->dim == 2 && (st = gdg_cuda_check(ctx, cudaMalloc((void **)&ctx->d_sync, GB_WORDS * sizeof(unsigned)), "alloc"))))
+        (ctx->dim == 2 && (st = gdg_cuda_check(ctx, cudaMalloc((void **)&ctx->d_sync, sync_words(ctx->ne) * sizeof(unsigned)), "alloc"))))
         return st;
     if ((st = gdg_cuda_check(ctx, cudaMemcpy(ctx->d_mats, tables.data(), tables.size() * sizeof(double), cudaMemcpyHostToDevice), "upload")) ||
         (st = gdg_cuda_check(ctx, cudaMemcpy(ctx->d_lam2, l2.data(), l2.size() * sizeof(double), cudaMemcpyHostToDevice), "upload")))

@@ -1289,7 +1289,7 @@ int gdg_const_setup(gdg_ctx *ctx) {
                 if (std::fabs(ctx->Psih[(n1 - 1 - i) * n1 + k] - sgn * ctx->Psih[i * n1 + k]) > 1e-9 * big) clean = false;
             (sgn > 0 ? even : odd).push_back(k);
         }
-        mp.parity = clean && (int)even.size() == (n1 + 1) / 2 && even[0] == 0 && ctx->dim == 2;
+        mp.parity = clean && (int)even.size() == (n1 + 1) / 2 && even[0] == 0 && ctx->dim >= 2;
         if (mp.parity) {
             for (int k = 0; k < (int)even.size(); ++k) perm[k] = even[k];
             for (int k = 0; k < (int)odd.size(); ++k) perm[even.size() + k] = odd[k];

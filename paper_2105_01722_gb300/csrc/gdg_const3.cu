@@ -173,6 +173,151 @@ k_stage3(const __grid_constant__ ModalParams mp, const StageBufs b, double cA, d
     if (valid) traces3_yz<N1>(mp, tU, tV, e, a, c, b.trout);
 }
 
+// Parity version of k_stage3 (modes ordered even first in every direction:
+// eR = s eL and gR = s gL, s = +1 for the NE = (N1+1)/2 even modes, -1 for
+// the odd ones).  Phase 1 keeps, per direction and transverse mode pair, the
+// sum and the difference of the doubled minus- and plus-face fluxes
+// (flux2), so that each face pair lifts onto an entry with one product
+// (hgL = gL/2, ceL = c^2 eL/2 carry the factors): 3 terms for r_u and 4 for
+// r_v instead of 6 and 7.  Each trace pair comes from one dot split into its
+// even and odd parts (left = even + odd, right = even - odd).
+template <int N1>
+__device__ __forceinline__ void traces3_yz_p(const ModalParams &mp, const double *tU, const double *tV, int e,
+                                             int a, int c, double *trout) {
+    constexpr int NE = (N1 + 1) / 2;
+    double ve = 0, vo = 0, de = 0, dd = 0;
+#pragma unroll
+    for (int m2 = 0; m2 < N1; ++m2) {
+        const double u = tU[(a * N1 + m2) * N1 + c], v = tV[(a * N1 + m2) * N1 + c];
+        if (m2 < NE) { ve = fma(mp.d[1].eL[m2], v, ve); de = fma(mp.d[1].gL[m2], u, de); }
+        else { vo = fma(mp.d[1].eL[m2], v, vo); dd = fma(mp.d[1].gL[m2], u, dd); }
+    }
+    const int ty = a * N1 + c;
+    trout[tix3<N1>(e, 2, 0, ty)] = ve + vo;
+    trout[tix3<N1>(e, 2, 1, ty)] = de + dd;
+    trout[tix3<N1>(e, 3, 0, ty)] = ve - vo;
+    trout[tix3<N1>(e, 3, 1, ty)] = de - dd;
+    ve = vo = de = dd = 0;
+#pragma unroll
+    for (int m3 = 0; m3 < N1; ++m3) {
+        const double u = tU[(m3 * N1 + a) * N1 + c], v = tV[(m3 * N1 + a) * N1 + c];
+        if (m3 < NE) { ve = fma(mp.d[2].eL[m3], v, ve); de = fma(mp.d[2].gL[m3], u, de); }
+        else { vo = fma(mp.d[2].eL[m3], v, vo); dd = fma(mp.d[2].gL[m3], u, dd); }
+    }
+    trout[tix3<N1>(e, 4, 0, ty)] = ve + vo;
+    trout[tix3<N1>(e, 4, 1, ty)] = de + dd;
+    trout[tix3<N1>(e, 5, 0, ty)] = ve - vo;
+    trout[tix3<N1>(e, 5, 1, ty)] = de - dd;
+}
+
+template <int N1, int MODE, int ALT>
+__global__ void __launch_bounds__(MAXB3)
+k_stage3p(const __grid_constant__ ModalParams mp, const StageBufs b, double cA, double cY) {
+    constexpr int NT = N1 * N1, NA = N1 * N1 * N1, NE = (N1 + 1) / 2;
+    extern __shared__ double smem[];
+    const int epb = blockDim.x / NT;
+    const int t = threadIdx.x;
+    const int le = t / NT, r = t - le * NT;
+    const int a = r / N1, c = r - (r / N1) * N1;
+    const int e = blockIdx.x * epb + le;
+    const bool valid = e < mp.ne;
+    // [12][NT]: per direction d, at 4d: g-sum, g-difference, q-sum, q-difference
+    double *F = smem + le * smem3_doubles<N1>();
+    double *tU = F + 12 * NT, *tV = tU + NA;
+    const int ex = valid ? e % mp.nx : 0, ey = valid ? (e / mp.nx) % mp.ny : 0, ez = valid ? e / (mp.nx * mp.ny) : 0;
+
+    if (valid) {   // fluxes of the three face pairs at this thread's transverse mode pair
+        const double *T = b.trin;
+        const int tt = a * N1 + c;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            double g2[2], q2[2];
+#pragma unroll
+            for (int side = 0; side < 2; ++side) {
+                const int f = 2 * d + side;
+                const double vi = T[tix3<N1>(e, f, 0, tt)], di = T[tix3<N1>(e, f, 1, tt)];
+                const int nb = nbr3(mp, ex, ey, ez, f);
+                double vo, dO;
+                if (nb >= 0) { vo = T[tix3<N1>(nb, f ^ 1, 0, tt)]; dO = T[tix3<N1>(nb, f ^ 1, 1, tt)]; }
+                else { vo = -vi; dO = -di; }
+                flux2(vi, di, vo, dO, mp.beta2, mp.tau2, ALT, side, nb < 0, g2[side], q2[side]);
+            }
+            F[(4 * d + 0) * NT + tt] = g2[0] + g2[1];
+            F[(4 * d + 1) * NT + tt] = g2[0] - g2[1];
+            F[(4 * d + 2) * NT + tt] = q2[0] + q2[1];
+            F[(4 * d + 3) * NT + tt] = q2[0] - q2[1];
+        }
+    }
+    __syncthreads();
+
+    double Ru[N1], Rv[N1];
+    if (valid) {
+        const int line = a * N1 + c;
+        const size_t row = ((size_t)e * NT + line) * N1;
+        const double *L0 = b.lam2 + line * N1;
+        const double *L1 = b.lam2 + NA + line * N1;
+        const double GA = F[0 * NT + line], GB = F[1 * NT + line];
+        const double QA = F[2 * NT + line], QB = F[3 * NT + line];
+        const double hgy = mp.d[1].hgL[c], cey = mp.d[1].ceL[c];
+        const double hgz = mp.d[2].hgL[a], cez = mp.d[2].ceL[a];
+        const double *FGy = F + (4 + (c < NE ? 0 : 1)) * NT + a * N1;   // at ty = a N1 + k
+        const double *FQy = F + (6 + (c < NE ? 0 : 1)) * NT + a * N1;
+        const double *FGz = F + (8 + (a < NE ? 0 : 1)) * NT + c * N1;   // at tz = c N1 + k
+        const double *FQz = F + (10 + (a < NE ? 0 : 1)) * NT + c * N1;
+#pragma unroll
+        for (int k = 0; k < N1; ++k) {
+            const double Yu = b.yU[row + k], Yv = b.yV[row + k];
+            const double xg = k < NE ? GA : GB, xq = k < NE ? QA : QB;
+            const double ru = fma(mp.d[0].hgL[k], xg, fma(hgy, FGy[k], hgz * FGz[k]));
+            const double rv = fma(L0[k], Yu, fma(mp.d[0].ceL[k], xq, fma(cey, FQy[k], cez * FQz[k])));
+            const double ku = fma(L1[k], ru, Yv);
+            const double kv = rv;
+            if (MODE == M_RHS) {
+                b.oU[row + k] = ku;
+                b.oV[row + k] = kv;
+            } else if (MODE == M_S1) {
+                b.aU[row + k] = cA * ku;
+                b.aV[row + k] = cA * kv;
+                Ru[k] = fma(cY, ku, Yu);
+                Rv[k] = fma(cY, kv, Yv);
+            } else if (MODE == M_S23) {
+                b.aU[row + k] = fma(cA, ku, b.aU[row + k]);
+                b.aV[row + k] = fma(cA, kv, b.aV[row + k]);
+                Ru[k] = fma(cY, ku, b.nU[row + k]);
+                Rv[k] = fma(cY, kv, b.nV[row + k]);
+            } else {
+                Ru[k] = fma(cA, ku, b.nU[row + k] + b.aU[row + k]);
+                Rv[k] = fma(cA, kv, b.nV[row + k] + b.aV[row + k]);
+            }
+        }
+        if (MODE != M_RHS) {
+            double *dU = (MODE == M_S4) ? b.nU : b.oU;
+            double *dV = (MODE == M_S4) ? b.nV : b.oV;
+#pragma unroll
+            for (int k = 0; k < N1; ++k) { dU[row + k] = Ru[k]; dV[row + k] = Rv[k]; }
+        }
+    }
+    if (MODE == M_RHS) return;   // uniform across the block
+
+    if (valid) {   // x faces from the line; the tile for the y and z faces
+        const int line = a * N1 + c;
+        double ve = 0, vo = 0, de = 0, dd = 0;
+#pragma unroll
+        for (int k = 0; k < N1; ++k) {
+            if (k < NE) { ve = fma(mp.d[0].eL[k], Rv[k], ve); de = fma(mp.d[0].gL[k], Ru[k], de); }
+            else { vo = fma(mp.d[0].eL[k], Rv[k], vo); dd = fma(mp.d[0].gL[k], Ru[k], dd); }
+            tU[line * N1 + k] = Ru[k];
+            tV[line * N1 + k] = Rv[k];
+        }
+        b.trout[tix3<N1>(e, 0, 0, line)] = ve + vo;
+        b.trout[tix3<N1>(e, 0, 1, line)] = de + dd;
+        b.trout[tix3<N1>(e, 1, 0, line)] = ve - vo;
+        b.trout[tix3<N1>(e, 1, 1, line)] = de - dd;
+    }
+    __syncthreads();
+    if (valid) traces3_yz_p<N1>(mp, tU, tV, e, a, c, b.trout);
+}
+
 // traces of a modal state (start of gdg_step and gdg_rhs)
 template <int N1>
 __global__ void __launch_bounds__(MAXB3)
@@ -360,6 +505,17 @@ void launch_stage3(int mode, const ModalParams &mp, const StageBufs &b, double c
     const int epb = epb3(N1);
     const dim3 grid((mp.ne + epb - 1) / epb), block(epb * N1 * N1);
     const size_t sm = smem_stage3(N1);
+    if (mp.parity) {
+        switch (mode) {
+#define GDG_K3P(m) (mp.alt ? k_stage3p<N1, m, 1> : k_stage3p<N1, m, 0>)
+        case M_RHS: GDG_K3P(M_RHS)<<<grid, block, sm, s>>>(mp, b, cA, cY); break;
+        case M_S1: GDG_K3P(M_S1)<<<grid, block, sm, s>>>(mp, b, cA, cY); break;
+        case M_S23: GDG_K3P(M_S23)<<<grid, block, sm, s>>>(mp, b, cA, cY); break;
+        default: GDG_K3P(M_S4)<<<grid, block, sm, s>>>(mp, b, cA, cY); break;
+#undef GDG_K3P
+        }
+        return;
+    }
     switch (mode) {
     case M_RHS: k_stage3<N1, M_RHS><<<grid, block, sm, s>>>(mp, b, cA, cY); break;
     case M_S1: k_stage3<N1, M_S1><<<grid, block, sm, s>>>(mp, b, cA, cY); break;
@@ -416,6 +572,14 @@ void gdg3_set_smem_limits() {
     cudaFuncSetAttribute(k_stage3<n, M_S1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);  \
     cudaFuncSetAttribute(k_stage3<n, M_S23>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim); \
     cudaFuncSetAttribute(k_stage3<n, M_S4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);  \
+    cudaFuncSetAttribute(k_stage3p<n, M_RHS, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim); \
+    cudaFuncSetAttribute(k_stage3p<n, M_S1, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);  \
+    cudaFuncSetAttribute(k_stage3p<n, M_S23, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim); \
+    cudaFuncSetAttribute(k_stage3p<n, M_S4, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);  \
+    cudaFuncSetAttribute(k_stage3p<n, M_RHS, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim); \
+    cudaFuncSetAttribute(k_stage3p<n, M_S1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);  \
+    cudaFuncSetAttribute(k_stage3p<n, M_S23, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim); \
+    cudaFuncSetAttribute(k_stage3p<n, M_S4, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);  \
     cudaFuncSetAttribute(k_traces3<n>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);       \
     cudaFuncSetAttribute(k_sep3<n>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     GDG_N1_CASES3(X)

@@ -211,7 +211,7 @@ __device__ __forceinline__ void traces3_yz_p(const ModalParams &mp, const double
 }
 
 template <int N1, int MODE, int ALT>
-__global__ void __launch_bounds__(MAXB3)
+__global__ void __launch_bounds__(MAXB3, 3)
 k_stage3p(const __grid_constant__ ModalParams mp, const StageBufs b, double cA, double cY) {
     constexpr int NT = N1 * N1, NA = N1 * N1 * N1, NE = (N1 + 1) / 2;
     extern __shared__ double smem[];
@@ -251,6 +251,12 @@ k_stage3p(const __grid_constant__ ModalParams mp, const StageBufs b, double cA, 
     __syncthreads();
 
     double Ru[N1], Rv[N1];
+    // the stage's arrays do not overlap: with restrict the next entry's loads
+    // may be issued before this entry's stores (at most 80 registers: 3
+    // blocks per SM, as shared memory allows)
+    const double *__restrict__ pyU = b.yU, *__restrict__ pyV = b.yV;
+    double *__restrict__ paU = b.aU, *__restrict__ paV = b.aV, *__restrict__ pnU = b.nU, *__restrict__ pnV = b.nV;
+    double *__restrict__ poU = b.oU, *__restrict__ poV = b.oV;
     if (valid) {
         const int line = a * N1 + c;
         const size_t row = ((size_t)e * NT + line) * N1;
@@ -266,33 +272,33 @@ k_stage3p(const __grid_constant__ ModalParams mp, const StageBufs b, double cA, 
         const double *FQz = F + (10 + (a < NE ? 0 : 1)) * NT + c * N1;
 #pragma unroll
         for (int k = 0; k < N1; ++k) {
-            const double Yu = b.yU[row + k], Yv = b.yV[row + k];
+            const double Yu = pyU[row + k], Yv = pyV[row + k];
             const double xg = k < NE ? GA : GB, xq = k < NE ? QA : QB;
             const double ru = fma(mp.d[0].hgL[k], xg, fma(hgy, FGy[k], hgz * FGz[k]));
             const double rv = fma(L0[k], Yu, fma(mp.d[0].ceL[k], xq, fma(cey, FQy[k], cez * FQz[k])));
             const double ku = fma(L1[k], ru, Yv);
             const double kv = rv;
             if (MODE == M_RHS) {
-                b.oU[row + k] = ku;
-                b.oV[row + k] = kv;
+                poU[row + k] = ku;
+                poV[row + k] = kv;
             } else if (MODE == M_S1) {
-                b.aU[row + k] = cA * ku;
-                b.aV[row + k] = cA * kv;
+                paU[row + k] = cA * ku;
+                paV[row + k] = cA * kv;
                 Ru[k] = fma(cY, ku, Yu);
                 Rv[k] = fma(cY, kv, Yv);
             } else if (MODE == M_S23) {
-                b.aU[row + k] = fma(cA, ku, b.aU[row + k]);
-                b.aV[row + k] = fma(cA, kv, b.aV[row + k]);
-                Ru[k] = fma(cY, ku, b.nU[row + k]);
-                Rv[k] = fma(cY, kv, b.nV[row + k]);
+                paU[row + k] = fma(cA, ku, paU[row + k]);
+                paV[row + k] = fma(cA, kv, paV[row + k]);
+                Ru[k] = fma(cY, ku, pnU[row + k]);
+                Rv[k] = fma(cY, kv, pnV[row + k]);
             } else {
-                Ru[k] = fma(cA, ku, b.nU[row + k] + b.aU[row + k]);
-                Rv[k] = fma(cA, kv, b.nV[row + k] + b.aV[row + k]);
+                Ru[k] = fma(cA, ku, pnU[row + k] + paU[row + k]);
+                Rv[k] = fma(cA, kv, pnV[row + k] + paV[row + k]);
             }
         }
         if (MODE != M_RHS) {
-            double *dU = (MODE == M_S4) ? b.nU : b.oU;
-            double *dV = (MODE == M_S4) ? b.nV : b.oV;
+            double *dU = (MODE == M_S4) ? pnU : poU;
+            double *dV = (MODE == M_S4) ? pnV : poV;
 #pragma unroll
             for (int k = 0; k < N1; ++k) { dU[row + k] = Ru[k]; dV[row + k] = Rv[k]; }
         }

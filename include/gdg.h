@@ -237,14 +237,15 @@ int gdg_step_host(gdg_ctx *ctx, double *u, double *v, double t0, double dt, int 
  * element line, 1 = two threads per line (even / odd modes), 2 = one thread
  * per line and field (u and v in separate warps), 3 = all stages of a
  * gdg_step call in one persistent cooperative launch (each line's state in
- * registers, a grid barrier between stages; only where every block of the
- * grid fits the GPU at once, GDG_EUNSUPPORTED otherwise), -1 = choose by
+ * registers, each block synchronised with the blocks holding its face
+ * neighbours between stages; only for N+1 <= 10 and where every block of
+ * the grid fits the GPU at once, GDG_EUNSUPPORTED otherwise), -1 = choose by
  * timing all eligible variants at the next gdg_step (the default).  All
  * variants perform the same floating-point operations in the same order:
  * results are bit-identical.  Setting a variant drops any captured step
  * graph.  Under variant 3 gdg_step synchronises its stream at the end (to
- * read the barrier's give-up flag) and returns GDG_ETIMEOUT if a barrier
- * waited longer than the wait limit (the state is then invalid; the
+ * read the give-up flag of its waits) and returns GDG_ETIMEOUT if a wait
+ * lasted longer than the wait limit (the state is then invalid; the
  * context stays usable).
  * GDG_EINVAL on other contexts or values; get: the variant in use (-1 before
  * the choice is made).
@@ -253,10 +254,11 @@ int gdg_set_stage_variant(gdg_ctx *ctx, int variant);
 int gdg_get_stage_variant(const gdg_ctx *ctx, int *variant);
 
 /*
- * Bound on any device-side wait of ctx's kernels (the grid barrier of the
- * persistent step), in seconds of wall time; default 1.  A wait that runs
- * out sets a flag, every block leaves the kernel, and the call returns
- * GDG_ETIMEOUT.  GDG_EINVAL for seconds <= 0 or not finite.
+ * Bound on any device-side wait of ctx's kernels (the persistent step's
+ * waits for neighbouring blocks between stages), in seconds of wall time;
+ * default 1.  A wait that runs out sets a flag, every block leaves the
+ * kernel, and the call returns GDG_ETIMEOUT.  GDG_EINVAL for seconds <= 0
+ * or not finite.
  */
 int gdg_set_wait_limit(gdg_ctx *ctx, double seconds);
 

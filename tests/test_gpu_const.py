@@ -205,8 +205,10 @@ def test_stage_variants_bit_identical(c):
         ctx = gdg.Context(_gpu_problem(c))
         try:
             ctx.set_stage_variant(variant)
-        except gdg.GdgError:
+        except gdg.GdgError as err:
             ctx.close()
+            if variant == 3 and err.status == gdg.EUNSUPPORTED and c["N"] + 1 > 10:
+                continue   # the persistent step is built for N + 1 <= 10
             assert (c["N"], c["p"]) != (8, 5), "the benchmark element must use the parity kernels"
             pytest.skip("element without an even/odd mode ordering: generic stage kernel only")
         assert ctx.stage_variant() == variant

@@ -9,8 +9,9 @@
 * Faults are injected on the host and reported as status codes: a NaN in
   the state gives GDG_ENONFINITE from gdg_energy; a one-iteration PCG limit
   gives GDG_ENOCONV with the iterates kept; bad arguments give GDG_EINVAL; a
-  wait limit too short for the persistent step's grid barrier gives
-  GDG_ETIMEOUT, and the context then steps correctly with a normal limit.
+  wait limit too short for the persistent step's waits between stages
+  gives GDG_ETIMEOUT, and the context then steps correctly with a normal
+  limit.
 """
 import numpy as np
 import pytest
@@ -155,12 +156,12 @@ def test_one_iteration_limit_reports_noconv():
     ctx.close()
 
 
-def test_grid_barrier_wait_limit_reports_timeout():
-    """The persistent step waits at a grid barrier between stages; with a
-    1 ns wait limit the first block to arrive gives up, every block leaves
-    the kernel and gdg_step returns GDG_ETIMEOUT.  With the default limit
-    the same context then advances the state exactly as the per-stage
-    kernel does."""
+def test_wait_limit_reports_timeout():
+    """Between stages each block of the persistent step waits for the blocks
+    holding its face neighbours; with a 1 ns wait limit the first block that
+    has to wait gives up, every block leaves the kernel and gdg_step returns
+    GDG_ETIMEOUT.  With the default limit the same context then advances the
+    state exactly as the per-stage kernel does."""
     kw = dict(dim=2, n=(12, 10), N=8, p=5, bc=(gdg.BC_DIRICHLET, gdg.BC_PERIODIC))
     ctx = gdg.Context(gdg.make_problem(**kw))
     ctx.set_stage_variant(3)

@@ -398,10 +398,8 @@ __device__ bool neighbour_sync(unsigned *sync, const int *s_nb, int nnb, unsigne
         int ok = 1;
         for (unsigned it = 1;; ++it) {
             bool done = true;
-            for (int i = lane; i < nnb; i += 32) {
-                const int nb = s_nb[i];
-                if (nb >= 0 && ld_acquire_u32(sync + NB_BASE + (size_t)nb * NB_STRIDE) < round) done = false;
-            }
+            for (int i = lane; i < nnb; i += 32)
+                if (ld_acquire_u32(sync + NB_BASE + (size_t)s_nb[i] * NB_STRIDE) < round) done = false;
             if (__all_sync(0xffffffffu, done)) break;
             int stop = 0;
             if (lane == 0) {
@@ -416,9 +414,9 @@ __device__ bool neighbour_sync(unsigned *sync, const int *s_nb, int nnb, unsigne
     return *s_ok != 0;
 }
 
-// blocks holding the face neighbours of block b's elements, one entry per
-// (element, face): -1 for a boundary face or a neighbour in block b itself
-__device__ void neighbour_blocks(const ModalParams &mp, int epb, int *s_nb) {
+// blocks holding the face neighbours of block b's elements, each once, in
+// s_nb[0 .. *s_cnt) (scratch: 4 epb entries, one per element and face)
+__device__ void neighbour_blocks(const ModalParams &mp, int epb, int *s_nb, int *s_cnt) {
     for (int i = threadIdx.x; i < 4 * epb; i += blockDim.x) {
         const int e = blockIdx.x * epb + (i >> 2), dir = i & 3;
         int nbb = -1;
@@ -445,6 +443,17 @@ __device__ void neighbour_blocks(const ModalParams &mp, int epb, int *s_nb) {
             if (en >= 0 && en / epb != (int)blockIdx.x) nbb = en / epb;
         }
         s_nb[i] = nbb;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {   // keep each block once, in place
+        int cnt = 0;
+        for (int i = 0; i < 4 * epb; ++i) {
+            const int nb = s_nb[i];
+            bool seen = nb < 0;
+            for (int j = 0; j < cnt && !seen; ++j) seen = s_nb[j] == nb;
+            if (!seen) s_nb[cnt++] = nb;
+        }
+        *s_cnt = cnt;
     }
 }
 
@@ -581,8 +590,10 @@ k_step2r(const __grid_constant__ ModalParams mp, const double *lam2, double *nU,
     double *fy = smem + le * (4 * N1);
     double *tile = smem + epb * 4 * N1 + le * (2 * N1 * (N1 + 1));
     const size_t row = ((size_t)(valid ? e : 0) * N1 + l) * N1;
-    neighbour_blocks(mp, epb, s_nb);   // read after the first stage's barriers
-    const int nnb = 4 * epb;
+    __shared__ int s_cnt;
+    neighbour_blocks(mp, epb, s_nb, &s_cnt);
+    __syncthreads();
+    const int nnb = s_cnt;
     double Ru[N1], Rv[N1], Nu[N1], Nv[N1], Au[N1], Av[N1];
 #pragma unroll
     for (int k = 0; k < N1; ++k) {

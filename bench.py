@@ -70,7 +70,7 @@ FP64_PEAK_TFLOPS = 152 * 2.070e9 * 4 / 1e12
 # without a capture of its current code):
 #   k_stage2p: the mean over the four stage launches of one RK4 step
 #   k_step2r: one persistent launch of one RK4 step, over its 4 stages
-STAGE_TRAFFIC_BYTES = {0: 15.66e6, 3: 7.77472e6 / 4}
+STAGE_TRAFFIC_BYTES = {0: 15.66e6, 3: 7.776768e6 / 4}
 
 
 def _env_rank():

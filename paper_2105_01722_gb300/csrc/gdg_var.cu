@@ -192,7 +192,7 @@ int gdg_var_setup(gdg_ctx *ctx) {
 
     const size_t nd = (size_t)ctx->ndof;
     int st;
-    D->tr_len = (long long)ctx->ne * 4 * 2 * Q;
+    D->tr_len = (long long)ctx->ne * 12 * n1;   // face lines: 4 faces x 3 N1 per element
     if ((st = gdg_cuda_check(ctx, cudaMalloc((void **)&D->d_S, nd * NA * sizeof(double)), "alloc S")) ||
         (st = gdg_cuda_check(ctx, cudaMalloc((void **)&D->d_M, nd * NA * sizeof(double)), "alloc M")) ||
         (st = gdg_cuda_check(ctx, cudaMalloc((void **)&D->d_w, nd * sizeof(double)), "alloc w")) ||
@@ -252,6 +252,15 @@ int gdg_var_setup(gdg_ctx *ctx) {
         GDG_VAR_CASES(X)
 #undef X
     }
+    // face operators: 4 faces x 6 N1 columns x 3 N1 rows per element, from the face data
+    if ((st = gdg_cuda_check(ctx, cudaMalloc((void **)&D->d_FM, (size_t)ctx->ne * 72 * n1 * n1 * sizeof(double)), "alloc FM")))
+        return st;
+    switch (n1) {
+#define X(n) case n: k_var_facemat<n><<<ctx->ne, nthreads_for(n * n), 3 * (size_t)Q * sizeof(double)>>>(P, D->d_FM); break;
+        GDG_VAR_CASES(X)
+#undef X
+    }
+    P.FM = D->d_FM;
     {   // c^2 / element mean of c^2 at the nodes: features of the learned u_t guess
         std::vector<float> feat(nd);
         for (int e = 0; e < ctx->ne; ++e) {
@@ -319,7 +328,7 @@ int gdg_var_setup(gdg_ctx *ctx) {
 void gdg_var_free(gdg_ctx *ctx) {
     VarData *D = ctx->var;
     if (!D) return;
-    cudaFree(D->d_S); cudaFree(D->d_M); cudaFree(D->d_S32); cudaFree(D->d_M32); cudaFree(D->d_dS); cudaFree(D->d_Ainv); cudaFree(D->d_Minv); cudaFree(D->d_G); cudaFree(D->d_w); cudaFree(D->d_pre); cudaFree(D->d_face);
+    cudaFree(D->d_S); cudaFree(D->d_M); cudaFree(D->d_S32); cudaFree(D->d_M32); cudaFree(D->d_dS); cudaFree(D->d_Ainv); cudaFree(D->d_Minv); cudaFree(D->d_G); cudaFree(D->d_FM); cudaFree(D->d_w); cudaFree(D->d_pre); cudaFree(D->d_face);
     cudaFree(D->d_tab); cudaFree(D->d_nodes); cudaFree(D->d_state); cudaFree(D->d_tr);
     cudaFree(D->d_c2feat); cudaFree(D->d_wbf16); cudaFree(D->d_mlp);
     cudaFree(D->d_ru); cudaFree(D->d_rv); cudaFree(D->d_x0u);

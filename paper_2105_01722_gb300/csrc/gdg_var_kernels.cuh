@@ -19,6 +19,7 @@ struct VarParams {
     const double *S, *M, *w, *pre, *face;
     const float *S32, *M32;      // FP32 copies of S and M (mixed precision only)
     const double *dS;            // [ne][N1*N1] frozen-coefficient preconditioner diagonal (S system)
+    const double *FM;            // [ne][4 faces][6 N1 columns][3 N1 rows] face operators (k_var_facemat)
     int inverse;                 // GDG_SOLVE_INVERSE: element inverses folded into G instead of PCG
     const double *G;             // [ne][12 N1 + NA][NA] folded operators, column-major (fold_cols)
     unsigned long long *stats;   // [0] sum it_u, [1] sum it_v, [2] max it_u, [3] max it_v,
@@ -35,6 +36,7 @@ struct VarData {
     float *d_S32 = nullptr, *d_M32 = nullptr;
     double *d_dS = nullptr;
     double *d_G = nullptr;                       // folded operators (GDG_SOLVE_INVERSE)
+    double *d_FM = nullptr;                      // face operators
     double *d_Ainv = nullptr, *d_Minv = nullptr; // setup temporaries of the fold, freed after it
     double *d_tab = nullptr, *d_nodes = nullptr;
     double *d_state = nullptr, *d_tr = nullptr;
@@ -104,9 +106,10 @@ __device__ void load_tabs(double *dst, const double *src, int n) {
 __device__ __forceinline__ size_t fix(int e, int f, int q, int k, int Q) {   // face data
     return (((size_t)e * 4 + f) * Q + q) * 4 + k;
 }
-__device__ __forceinline__ size_t tix(int e, int f, int fld, int q, int Q) {  // traces
-    return (((size_t)e * 4 + f) * 2 + fld) * Q + q;
-}
+// face traces are the face lines of face_lines: [e][face][3 N1] (line index
+// m N1 + j as in face_lines); 12 N1 doubles per element
+template <int N1>
+__device__ __forceinline__ size_t lix(int e, int f) { return ((size_t)e * 4 + f) * 3 * N1; }
 
 // neighbour across face f (0 xm, 1 xp, 2 ym, 3 yp) and its facing face; -1 on a Dirichlet side
 __device__ __forceinline__ int neighbour(const VarParams &P, int e, int f, int &fo) {
@@ -673,31 +676,12 @@ __device__ void face_lines(const double *U, const double *V, const Tabs &T, doub
     __syncthreads();
 }
 
-// v and n.grad u at every face point from the line data
-template <int N1>
-__device__ void face_points(const double *L, const Tabs &T, const double *face, int e, int Q, double *trout) {
-    for (int task = threadIdx.x; task < 4 * Q; task += blockDim.x) {
-        const int f = task / Q, q = task - (task / Q) * Q;
-        const double *l0 = L + (f * 3 + 0) * N1, *l1 = L + (f * 3 + 1) * N1, *l2 = L + (f * 3 + 2) * N1;
-        double v = 0, ur = 0, us = 0;
-        for (int j = 0; j < N1; ++j) {
-            const double Bq = T.B[q * N1 + j], Dq = T.D[q * N1 + j];
-            v += Bq * l0[j];
-            if (f < 2) { ur += Bq * l1[j]; us += Dq * l2[j]; }
-            else { ur += Dq * l1[j]; us += Bq * l2[j]; }
-        }
-        const double fr = face[fix(e, f, q, 0, Q)], fs = face[fix(e, f, q, 1, Q)];
-        trout[tix(e, f, 0, q, Q)] = v;
-        trout[tix(e, f, 1, q, Q)] = fr * ur + fs * us;
-    }
-}
-
 template <int N1>
 __global__ void k_var_traces(VarParams P, const double *u, const double *v, double *trout) {
     constexpr int NA = N1 * N1;
     extern __shared__ double sm[];
     const int Q = P.Q, e = blockIdx.x;
-    double *tb = sm, *U = tb + tab_len(Q, N1), *V = U + NA, *L = V + NA;
+    double *tb = sm, *U = tb + tab_len(Q, N1), *V = U + NA;
     load_tabs(tb, P.tab, tab_len(Q, N1));
     for (int i = threadIdx.x; i < NA; i += blockDim.x) {
         U[i] = u[(size_t)e * NA + i];
@@ -705,8 +689,7 @@ __global__ void k_var_traces(VarParams P, const double *u, const double *v, doub
     }
     __syncthreads();
     const Tabs T = tabs_at(tb, Q, N1);
-    face_lines<N1>(U, V, T, L);
-    face_points<N1>(L, T, P.face, e, Q, trout);
+    face_lines<N1>(U, V, T, trout + lix<N1>(e, 0));
 }
 
 // ------------------------------------------------------------ stage ------
@@ -739,7 +722,7 @@ struct StageSmem {
         Yu = tb + tab_tail_len(Q, N1);
         Yv = Yu + NA; ru = Yv + NA; rv = ru + NA; x = rv + NA; r = x + NA; z = r + NA; p = z + NA;
         Ap = p + NA; w = Ap + NA; dS = w + NA; dM = dS + NA; t1 = dM + NA; t2 = t1 + NA;
-        fw = t2 + NA; L = fw + 12 * Q; red = L + 12 * N1;
+        fw = t2 + NA; L = fw + 24 * N1; red = L + 12 * N1;   // fw: face lines (own, neighbours')
         A = (mixed || no_matrix) ? nullptr : red + 32;
         A32 = reinterpret_cast<float *>(red + 32);
         Ps32 = A32 + NA * NA; dS32 = Ps32 + N1 * N1; dM32 = dS32 + NA; w32 = dM32 + NA;
@@ -747,7 +730,7 @@ struct StageSmem {
         u32 = c32 + NA; v32 = u32 + NA; t132 = v32 + NA; t232 = t132 + NA;
     }
     static size_t bytes(int Q, bool mixed, bool no_matrix = false) {
-        size_t d = sizeof(double) * ((size_t)tab_tail_len(Q, N1) + 14 * NA + 12 * Q + 12 * N1 + 32);
+        size_t d = sizeof(double) * ((size_t)tab_tail_len(Q, N1) + 14 * NA + 24 * N1 + 12 * N1 + 32);
         if (mixed) d += sizeof(float) * ((size_t)NA * NA + N1 * N1 + 12 * NA);
         else if (!no_matrix) d += sizeof(double) * (size_t)NA * NA;
         return d;
@@ -760,47 +743,123 @@ struct StageSmem {
     }
 };
 
-// face fluxes and their line integrals L[f][m][j] (f face, m = 0..2 the three
-// lifted quantities, j the node along the face): r_u and r_v are linear in L
+// Face terms.  Per face f of an element the fluxes of Section 2.2.1 at the Q
+// face quadrature points, weighted and integrated against the face basis
+// (the line integrals L[f][m][j], m = 0..2 the three lifted quantities, j the
+// node along the face), are linear in the 3 N1 face lines of the element
+// (face_lines) and the 3 N1 face lines of the neighbour's facing face, with
+// coefficients fixed in time (geometry, c^2, the flux).  k_var_facemat
+// builds that map once per element and face; the stage applies it.
+
+// traces (v, n.grad u) at face point q of face f of element e from a face
+// line vector that is zero except entry (m, j) = 1 (the point evaluation of
+// face_lines' lines: x faces (B, B, D) of lines (v, normal slope, u), y faces
+// (B, D, B) of lines (v, u, normal slope))
 template <int N1>
-__device__ void lift_lines(const VarParams &P, int e, const double *trin, const Tabs &T, double *fw, double *L) {
-    const int Q = P.Q, t = threadIdx.x;
-    for (int task = t; task < 4 * Q; task += blockDim.x) {
-        const int f = task / Q, q = task - (task / Q) * Q;
-        const double vi = trin[tix(e, f, 0, q, Q)], di = trin[tix(e, f, 1, q, Q)];
+__device__ __forceinline__ void unit_point_trace(const Tabs &T, const double *face, int e, int f, int q, int Q,
+                                                 int m, int j, double &v, double &d) {
+    const double Bq = T.B[q * N1 + j], Dq = T.D[q * N1 + j];
+    v = m == 0 ? Bq : 0.0;
+    double ur, us;
+    if (f < 2) { ur = m == 1 ? Bq : 0.0; us = m == 2 ? Dq : 0.0; }
+    else { ur = m == 1 ? Dq : 0.0; us = m == 2 ? Bq : 0.0; }
+    d = face[fix(e, f, q, 0, Q)] * ur + face[fix(e, f, q, 1, Q)] * us;
+}
+
+// the three weighted flux values of face point q (nb < 0: Dirichlet side,
+// the caller passes the mirror state vo = -vi, do = -di)
+__device__ __forceinline__ void point_flux(const VarParams &P, int e, int f, int q, int nb, double vi, double di,
+                                           double vo, double dO, double *w3, int Q) {
+    double beta = 0.0, tau = 0.0;
+    if (P.upwind) {
+        const double xi = P.xi > 0.0 ? P.xi : P.face[fix(e, f, q, 3, Q)];
+        beta = 0.5 * xi;
+        tau = 0.5 / xi;
+    }
+    double vstar = 0.5 * (vi + vo) - beta * (di + dO);
+    double qstar = 0.5 * (di - dO) - tau * (vi - vo);
+    if (P.alt && nb >= 0) {   // minus faces (0, 2): this element is side 2
+        vstar = (f == 0 || f == 2) ? vo : vi;
+        qstar = (f == 0 || f == 2) ? di : -dO;
+    }
+    const double g = vstar - vi;
+    const double cw = P.face[fix(e, f, q, 2, Q)];
+    w3[0] = cw * P.face[fix(e, f, q, 0, Q)] * g;
+    w3[Q] = cw * P.face[fix(e, f, q, 1, Q)] * g;
+    w3[2 * Q] = cw * qstar;
+}
+
+// FM[e][f][c][r]: line integral r = m N1 + j of face f per unit face-line
+// value c (c < 3 N1: the element's own line entry c; c >= 3 N1: entry
+// c - 3 N1 of the neighbour's facing face, zero columns on a Dirichlet
+// side).  One CTA per element; shared: 3 Q doubles.
+template <int N1>
+__global__ void __launch_bounds__(nthreads_for(N1 * N1))
+k_var_facemat(VarParams P, double *__restrict__ FM) {
+    constexpr int NL = 3 * N1;
+    extern __shared__ double fw[];
+    const int Q = P.Q, e = blockIdx.x, t = threadIdx.x;
+    const Tabs T = tabs_at(P.tab, Q, N1);
+    for (int f = 0; f < 4; ++f) {
         int fo;
         const int nb = neighbour(P, e, f, fo);
-        double vo, dO;
-        if (nb >= 0) { vo = trin[tix(nb, fo, 0, q, Q)]; dO = trin[tix(nb, fo, 1, q, Q)]; }
-        else { vo = -vi; dO = -di; }   // u = 0: mirror state
-        double beta = 0.0, tau = 0.0;
-        if (P.upwind) {
-            const double xi = P.xi > 0.0 ? P.xi : P.face[fix(e, f, q, 3, Q)];
-            beta = 0.5 * xi;
-            tau = 0.5 / xi;
+        for (int c = 0; c < 2 * NL; ++c) {
+            double *col = FM + (((size_t)e * 4 + f) * 2 * NL + c) * NL;
+            const bool own = c < NL;
+            if (!own && nb < 0) {
+                for (int r = t; r < NL; r += blockDim.x) col[r] = 0.0;
+                continue;
+            }
+            const int cc = own ? c : c - NL, m = cc / N1, j = cc - (cc / N1) * N1;
+            for (int q = t; q < Q; q += blockDim.x) {
+                double vi = 0.0, di = 0.0, vo = 0.0, dO = 0.0;
+                if (own) unit_point_trace<N1>(T, P.face, e, f, q, Q, m, j, vi, di);
+                else unit_point_trace<N1>(T, P.face, nb, fo, q, Q, m, j, vo, dO);
+                if (nb < 0) { vo = -vi; dO = -di; }   // u = 0: mirror state
+                point_flux(P, e, f, q, nb, vi, di, vo, dO, fw + q, Q);
+            }
+            __syncthreads();
+            for (int r = t; r < NL; r += blockDim.x) {
+                const int mr = r / N1, jr = r - (r / N1) * N1;
+                // x faces: (B, D, B); y faces: (D, B, B)
+                const bool useD = (f < 2) ? (mr == 1) : (mr == 0);
+                const double *tab = useD ? T.D : T.B;
+                double sum = 0.0;
+                for (int q = 0; q < Q; ++q) sum += tab[q * N1 + jr] * fw[mr * Q + q];
+                col[r] = sum;
+            }
+            __syncthreads();
         }
-        double vstar = 0.5 * (vi + vo) - beta * (di + dO);
-        double qstar = 0.5 * (di - dO) - tau * (vi - vo);
-        if (P.alt && nb >= 0) {   // minus faces (0, 2): this element is side 2
-            vstar = (f == 0 || f == 2) ? vo : vi;
-            qstar = (f == 0 || f == 2) ? di : -dO;
-        }
-        const double g = vstar - vi;
-        const double cw = P.face[fix(e, f, q, 2, Q)];
-        fw[(f * 3 + 0) * Q + q] = cw * P.face[fix(e, f, q, 0, Q)] * g;
-        fw[(f * 3 + 1) * Q + q] = cw * P.face[fix(e, f, q, 1, Q)] * g;
-        fw[(f * 3 + 2) * Q + q] = cw * qstar;
+    }
+}
+
+// line integrals L[f][m][j] of the element's four faces from its own face
+// lines and its neighbours' (lines: 24 N1 doubles of shared scratch)
+template <int N1>
+__device__ void lift_lines(const VarParams &P, int e, const double *trin, double *lines, double *L) {
+    constexpr int NL = 3 * N1;
+    for (int i = threadIdx.x; i < 4 * NL; i += blockDim.x) {
+        const int f = i / NL, c = i - (i / NL) * NL;
+        int fo;
+        const int nb = neighbour(P, e, f, fo);
+        lines[i] = trin[lix<N1>(e, 0) + i];
+        lines[4 * NL + i] = nb >= 0 ? trin[lix<N1>(nb, fo) + c] : 0.0;
     }
     __syncthreads();
-    for (int task = t; task < 12 * N1; task += blockDim.x) {
-        const int f = task / (3 * N1), m = (task / N1) % 3, j = task % N1;
-        const double *src = fw + (f * 3 + m) * Q;
-        // x faces: (B, D, B); y faces: (D, B, B)
-        const bool useD = (f < 2) ? (m == 1) : (m == 0);
-        const double *tab = useD ? T.D : T.B;
-        double s = 0.0;
-        for (int q = 0; q < Q; ++q) s += tab[q * N1 + j] * src[q];
-        L[task] = s;
+    for (int task = threadIdx.x; task < 4 * NL; task += blockDim.x) {
+        const int f = task / NL, r = task - (task / NL) * NL;
+        int fo;
+        const int nb = neighbour(P, e, f, fo);
+        const double *col = P.FM + ((size_t)e * 4 + f) * 2 * NL * NL + r;
+        const double *own = lines + f * NL, *nbl = lines + 4 * NL + f * NL;
+        double sum = 0.0;
+#pragma unroll 9
+        for (int c = 0; c < NL; ++c) sum += __ldg(col + (size_t)c * NL) * own[c];
+        if (nb >= 0) {
+#pragma unroll 9
+            for (int c = 0; c < NL; ++c) sum += __ldg(col + (size_t)(NL + c) * NL) * nbl[c];
+        }
+        L[task] = sum;
     }
     __syncthreads();
 }
@@ -827,9 +886,9 @@ __device__ __forceinline__ void lift_assemble(const double *L, const Tabs &T, do
 
 // face fluxes and lifts: r_u, r_v (r_v without the stiffness term)
 template <int N1>
-__device__ void lifts(const VarParams &P, int e, const double *trin, const Tabs &T, double *fw, double *L,
+__device__ void lifts(const VarParams &P, int e, const double *trin, const Tabs &T, double *lines, double *L,
                       double *ru, double *rv) {
-    lift_lines<N1>(P, e, trin, T, fw, L);
+    lift_lines<N1>(P, e, trin, lines, L);
     lift_assemble<N1>(L, T, ru, rv);
 }
 
@@ -905,7 +964,7 @@ __device__ __forceinline__ void var_stage_body(const VarParams &P, const VarBufs
     fdm_diagonals<N1>(P, e, s.dS, s.dM);
     const bool guess = b.part == 2;
     if (P.inverse) {
-        lift_lines<N1>(P, e, b.trin, T, s.fw, s.L);
+        lift_lines<N1>(P, e, b.trin, s.fw, s.L);
         fold_apply<N1>(P.G + (size_t)e * fold_cols(N1) * NA, s.L, s.Yu, s.Yv, s.ru, s.x);
     } else if (!guess) {
         lifts<N1>(P, e, b.trin, T, s.fw, s.L, s.ru, s.rv);
@@ -1003,8 +1062,7 @@ __device__ __forceinline__ void var_stage_body(const VarParams &P, const VarBufs
     }
     if (MODE == M_RHS) return;
     __syncthreads();
-    face_lines<N1>(s.Yu, s.Yv, T, s.L);
-    face_points<N1>(s.L, T, P.face, e, P.Q, b.trout);
+    face_lines<N1>(s.Yu, s.Yv, T, b.trout + lix<N1>(e, 0));
 }
 
 template <int N1, int MODE>

@@ -340,14 +340,16 @@ typedef struct gdg_batch gdg_batch;   /* opaque; owns one context per problem */
 /*
  * Many independent 2-D problems advanced together (a launch pattern layered
  * on the method; the paper advances one mesh at a time).  Every RK stage of
- * all problems is one persistent kernel whose CTAs pull work from a queue:
- * first the elements of GDG_COEF_NODAL problems (element PCG, with each
- * problem's own precision: GDG_MIXED gives FP32 inner PCG with FP64
- * refinement and FP64 state), then tiles of elements of GDG_COEF_CONST
- * problems (modified-basis route).  A call's launches are replayed from one
- * CUDA graph.  The launch shape (threads per block, which also sets the
- * modal tile, and resident blocks per SM) is chosen on the first
- * gdg_batch_step by timing every candidate on the batch's own data.
+ * all problems is two launches on two streams: the elements of the
+ * GDG_COEF_NODAL problems (element solves with each problem's own solver
+ * and precision: GDG_MIXED gives FP32 inner PCG with FP64 refinement and
+ * FP64 state), and tiles of elements of the GDG_COEF_CONST problems
+ * (modified-basis route), each a persistent kernel whose CTAs pull work
+ * from a queue or a flat grid; the element solves may instead run as one
+ * launch per problem.  A call's launches are replayed from one CUDA graph.
+ * The launch shape (threads per block, which also sets the modal tile,
+ * resident blocks per SM, flat or per-problem launches) is chosen on the
+ * first gdg_batch_step by timing every candidate on the batch's own data.
  * pbs[count]: host problems, all dim = 2 with the same N, 7 <= N <= 9; each is
  * validated and set up as by gdg_create (host arrays copied).
  * Errors: as gdg_create; GDG_EUNSUPPORTED for other N.
@@ -376,7 +378,9 @@ int gdg_batch_step(gdg_batch *b, double *const *u, double *const *v, const doubl
  * 0 when the batch has no such problem; blocks_per_sm of the element-PCG
  * launch (its blocks have one thread per element node, rounded up to a
  * warp): the persistent grid's blocks per SM, -1 for a flat grid of one
- * block per element, 0 when the batch has no variable-coefficient problem.
+ * block per element, -2 for one launch per problem of its own stage kernel
+ * (parameters as kernel arguments), 0 when the batch has no
+ * variable-coefficient problem.
  */
 int gdg_batch_tuning(const gdg_batch *b, int *threads_per_block, int *blocks_per_sm, int *tile_elements);
 

@@ -45,7 +45,7 @@ struct StageRoles {
     double cA, cY;
     const double *yU, *yV, *trin;
     double *oU, *oV, *trout;
-    __device__ StageRoles(const StepBuffers &B, double dt) {
+    __host__ __device__ StageRoles(const StepBuffers &B, double dt) {
         if (STAGE == 1) {
             cA = dt / 6.0; cY = 0.5 * dt; yU = B.nU; yV = B.nV; oU = B.xU; oV = B.xV; trin = B.tr0; trout = B.tr1;
         } else if (STAGE == 2) {
@@ -177,6 +177,9 @@ cudaError_t set_batch_attrs() {
     if ((e = raise_smem(k_batch_modal<N1, 2>, lim)) != cudaSuccess) return e;
     if ((e = raise_smem(k_batch_modal<N1, 3>, lim)) != cudaSuccess) return e;
     if ((e = raise_smem(k_batch_modal<N1, 4>, lim)) != cudaSuccess) return e;
+    if ((e = raise_smem(k_var_stage<N1, M_S1>, lim)) != cudaSuccess) return e;
+    if ((e = raise_smem(k_var_stage<N1, M_S23>, lim)) != cudaSuccess) return e;
+    if ((e = raise_smem(k_var_stage<N1, M_S4>, lim)) != cudaSuccess) return e;
     if ((e = raise_smem(k_batch_var<N1, 1>, lim)) != cudaSuccess) return e;
     if ((e = raise_smem(k_batch_var<N1, 2>, lim)) != cudaSuccess) return e;
     if ((e = raise_smem(k_batch_var<N1, 3>, lim)) != cudaSuccess) return e;
@@ -277,11 +280,45 @@ int max_resident(const gdg_batch *b, bool var, int threads, size_t smem) {
     return 1;
 }
 
+// The element-PCG stage as one launch per variable-coefficient problem: the
+// problem's own stage kernel, its parameters as kernel arguments (no per-block
+// staging), in problem order on one stream.  Same kernel body as the batched
+// launches and as gdg_step.
+template <int N1>
+void launch_var_per_problem_n(const gdg_batch *b, int stage, cudaStream_t s) {
+    constexpr int T = nthreads_for(N1 * N1);
+    for (const BatchProb &P : b->h_probs) {
+        if (P.kind != 1) continue;
+        const size_t sm = StageSmem<N1>::bytes(P.vp.Q, P.vp.mixed, P.vp.inverse);
+        switch (stage) {
+#define GDG_PP(st, mode)                                                                                  \
+    {                                                                                                     \
+        const StageRoles<st> r(P.sb, P.dt);                                                               \
+        const VarBufs vb{r.yU, r.yV, P.sb.nU, P.sb.nV, P.sb.aU, P.sb.aV, r.oU, r.oV, r.trin, r.trout};    \
+        k_var_stage<N1, mode><<<P.vp.ne, T, sm, s>>>(P.vp, vb, r.cA, r.cY);                               \
+    }
+        case 1: GDG_PP(1, M_S1) break;
+        case 2: GDG_PP(2, M_S23) break;
+        case 3: GDG_PP(3, M_S23) break;
+        default: GDG_PP(4, M_S4) break;
+#undef GDG_PP
+        }
+    }
+}
+
 // kind 0: PCG elements; kind 1: modal tiles
 void launch_kind(gdg_batch *b, int kind, int stage, unsigned int *counter, cudaStream_t s) {
     const bool var = kind == 0;
     const int n = var ? b->n_var : b->n_mod;
     if (!n) return;
+    if (var && b->var_grid == -1) {   // one launch per problem
+        switch (b->n1) {
+#define X(n1_) case n1_: launch_var_per_problem_n<n1_>(b, stage, s); break;
+            GDG_BATCH_CASES(X)
+#undef X
+        }
+        return;
+    }
     const int threads = var ? b->var_threads : b->mod_threads;
     const int grid = var ? (b->var_grid > 0 ? b->var_grid : n) : b->mod_grid;
     if (var && b->var_grid <= 0) counter = nullptr;   // flat grid
@@ -334,7 +371,7 @@ int autotune(gdg_batch *b, cudaStream_t s) {
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     int st = GDG_OK;
-    if (b->n_var) {   // PCG launch: flat grid, or persistent with 1..occupancy-limit blocks per SM
+    if (b->n_var) {   // PCG launch: flat grid, persistent with 1..occupancy-limit blocks per SM, or per problem
         const int maxr = max_resident(b, true, b->var_threads, b->var_smem);
         b->var_grid = 0;
         float best = time_launch(b, 0, s, e0, e1);
@@ -344,6 +381,8 @@ int autotune(gdg_batch *b, cudaStream_t s) {
             const float ms = time_launch(b, 0, s, e0, e1);
             if (ms < best) { best = ms; best_g = b->var_grid; }
         }
+        b->var_grid = -1;
+        if (time_launch(b, 0, s, e0, e1) < best) best_g = -1;
         b->var_grid = best_g;
     }
     bool any_modal = false;
@@ -529,7 +568,8 @@ extern "C" int gdg_batch_tuning(const gdg_batch *b, int *threads_per_block, int 
     if (!b) return GDG_EINVAL;
     const bool mod = b->tuned && b->n_mod > 0, var = b->tuned && b->n_var > 0;
     if (threads_per_block) *threads_per_block = mod ? b->mod_threads : 0;
-    if (blocks_per_sm) *blocks_per_sm = var && b->sms && b->var_grid > 0 ? b->var_grid / b->sms : (var ? -1 : 0);
+    if (blocks_per_sm)
+        *blocks_per_sm = var && b->sms && b->var_grid > 0 ? b->var_grid / b->sms : (var ? (b->var_grid == -1 ? -2 : -1) : 0);
     if (tile_elements) *tile_elements = mod ? b->mod_tile : 0;
     return GDG_OK;
 }

@@ -54,7 +54,7 @@ def test_batch_equals_individual_steps(precision):
     tun = batch.tuning()
     assert tun["tile_elements"] in (4, 7, 10, 14, 21, 28)
     assert tun["threads_per_block"] == 9 * tun["tile_elements"]
-    assert tun["blocks_per_sm"] == -1 or tun["blocks_per_sm"] >= 1
+    assert tun["blocks_per_sm"] in (-1, -2) or tun["blocks_per_sm"] >= 1
     for i, (pb, U0, dt) in enumerate(built):
         ctx = gdg.Context(pb)
         u = torch.tensor(U0, device="cuda")

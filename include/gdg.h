@@ -153,6 +153,12 @@ int gdg_basis_1d(int p, int N, double *M, double *S, double *phiL, double *phiR,
  * the element mass and stiffness matrices and face data on the device for
  * GDG_COEF_NODAL, Section 7.1) and allocate device scratch on the current
  * CUDA device.  Host arrays in *pb are copied.  *out receives the context.
+ * GDG_COEF_NODAL also builds, per element face, the linear map from the
+ * element's and the neighbour's face lines (v, normal slope, u along the
+ * face; 3 (N+1) values each) to the lifted face integrals: the traces at
+ * the face quadrature points, the flux of Section 2.2.1 and the integrals
+ * against the face basis, all fixed in time (72 (N+1)^2 doubles per
+ * element); elements then exchange face lines instead of point traces.
  * Nodal layout of the state: 1-D u[e*n1 + i]; 2-D u[(e*n1 + j)*n1 + i],
  * e = ey*nx + ex; 3-D u[((e*n1 + k)*n1 + j)*n1 + i], e = (ez*ny + ey)*nx + ex
  * (i along x; element nodes on shared faces are duplicated, as in DG).

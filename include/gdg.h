@@ -221,7 +221,8 @@ int gdg_step_stats(gdg_ctx *ctx, gdg_pcg_stats *u_sys, gdg_pcg_stats *v_sys);
 
 /*
  * Advance (u, v) in place by nsteps classic RK4 steps of size dt starting at
- * t0 (device pointers).  The per-stage work is the whole hot path: traces,
+ * t0 (device pointers; t0 matters only with a point source).  The per-stage
+ * work is the whole hot path: traces,
  * fluxes and lifts, stiffness, constrained u_t solve, mass inversion and the
  * stage combination.  Launches are captured in a CUDA graph on first use.
  */
@@ -283,6 +284,23 @@ int gdg_energy(gdg_ctx *ctx, const double *u, const double *v, double *E, void *
  * nodal layout.  GDG_COEF_NODAL contexts only.
  */
 int gdg_residuals(gdg_ctx *ctx, const double *u, const double *v, double *ru, double *rv, void *stream);
+
+/*
+ * Point source (the forcing f of u_tt = div(c^2 grad u) + f):
+ *   f(x, t) = amplitude sin(omega t) delta(x - x_s)
+ * on a GDG_COEF_NODAL context.  x_s is given by the element holding it and
+ * its reference coordinates (r, s) in [0,1]^2 (the point of the element's
+ * isoparametric map; on a Cartesian mesh x = x_e + r H_x, y = y_e + s H_y).
+ * Its load on r_v is int phi_a f = phi_a(r, s) amplitude sin(omega t) on
+ * that element (the delta function makes the Jacobian drop out); the inverse
+ * route adds M_J^-1 of it to dV/dt.  gdg_step evaluates the source at each
+ * RK stage's time, starting from its t0; gdg_rhs and gdg_residuals at the
+ * time the last gdg_step reached (0 before any).  amplitude = 0 removes the
+ * source.  Drops any captured step graph; synchronises the device.
+ * GDG_EINVAL: not a GDG_COEF_NODAL context, element out of range, (r, s)
+ * outside [0,1]^2, non-finite amplitude or omega.
+ */
+int gdg_set_point_source(gdg_ctx *ctx, int element, double r, double s, double amplitude, double omega);
 
 /* ---- learned initial guess for the u_t solve (not in the paper) -------- */
 /*

@@ -487,12 +487,12 @@ extern "C" int gdg_step_stats(gdg_ctx *ctx, gdg_pcg_stats *u_sys, gdg_pcg_stats 
 
 extern "C" int gdg_step(gdg_ctx *ctx, double *u, double *v, double t0, double dt, int nsteps,
                         void *stream) {
-    (void)t0;   // the supported problems are autonomous (no forcing, u = 0 on Dirichlet sides)
+    // t0 matters only with a point source (GDG_COEF_NODAL); otherwise the problem is autonomous
     if (!ctx || !u || !v || nsteps < 0 || !(dt > 0.0)) return GDG_EINVAL;
     if (nsteps == 0) return GDG_OK;
     cudaStream_t s = (cudaStream_t)stream;
     return is_const(ctx) ? gdg_const_step(ctx, u, v, dt, nsteps, s)
-                         : gdg_var_step(ctx, u, v, dt, nsteps, s);
+                         : gdg_var_step(ctx, u, v, t0, dt, nsteps, s);
 }
 
 extern "C" int gdg_step_host(gdg_ctx *ctx, double *u, double *v, double t0, double dt, int nsteps,

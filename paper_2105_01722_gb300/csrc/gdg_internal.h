@@ -154,7 +154,7 @@ int gdg_var_rhs(gdg_ctx *ctx, const double *u, const double *v, double *du, doub
                 cudaStream_t s);
 int gdg_var_pcg(gdg_ctx *ctx, int which, const double *b, double *x, gdg_pcg_stats *st,
                 cudaStream_t s);
-int gdg_var_step(gdg_ctx *ctx, double *u, double *v, double dt, int nsteps, cudaStream_t s);
+int gdg_var_step(gdg_ctx *ctx, double *u, double *v, double t0, double dt, int nsteps, cudaStream_t s);
 int gdg_var_energy(gdg_ctx *ctx, const double *u, const double *v, double *E, cudaStream_t s);
 int gdg_var_step_stats(gdg_ctx *ctx, gdg_pcg_stats *su, gdg_pcg_stats *sv);
 

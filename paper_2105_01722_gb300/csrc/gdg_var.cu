@@ -27,6 +27,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <utility>
 #include <vector>
 
 #include "gdg_internal.h"
@@ -142,12 +143,16 @@ void enqueue_step(gdg_ctx *ctx, double dt, cudaStream_t s) {
     b.nU = vbuf(ctx, B_NU); b.nV = vbuf(ctx, B_NV);
     b.aU = vbuf(ctx, B_AU); b.aV = vbuf(ctx, B_AV);
     b.yU = b.nU; b.yV = b.nV; b.oU = vbuf(ctx, B_XU); b.oV = vbuf(ctx, B_XV); b.trin = tr0; b.trout = tr1;
+    b.tstage = 0.0;
     launch_stage(ctx, M_S1, b, dt / 6.0, 0.5 * dt, s);
     b.yU = vbuf(ctx, B_XU); b.yV = vbuf(ctx, B_XV); b.oU = vbuf(ctx, B_YU); b.oV = vbuf(ctx, B_YV); b.trin = tr1; b.trout = tr0;
+    b.tstage = 0.5 * dt;
     launch_stage(ctx, M_S23, b, dt / 3.0, 0.5 * dt, s);
     b.yU = vbuf(ctx, B_YU); b.yV = vbuf(ctx, B_YV); b.oU = vbuf(ctx, B_XU); b.oV = vbuf(ctx, B_XV); b.trin = tr0; b.trout = tr1;
+    b.tstage = 0.5 * dt;
     launch_stage(ctx, M_S23, b, dt / 3.0, dt, s);
     b.yU = vbuf(ctx, B_XU); b.yV = vbuf(ctx, B_XV); b.oU = nullptr; b.oV = nullptr; b.trin = tr1; b.trout = tr0;
+    b.tstage = dt;   // the source block also advances the source time by dt
     launch_stage(ctx, M_S4, b, dt / 6.0, 0.0, s);
 }
 
@@ -261,6 +266,11 @@ int gdg_var_setup(gdg_ctx *ctx) {
 #undef X
     }
     P.FM = D->d_FM;
+    P.src_e = -1;   // no point source until gdg_set_point_source
+    if ((st = gdg_cuda_check(ctx, cudaMalloc((void **)&D->d_time, sizeof(double)), "alloc time")) ||
+        (st = gdg_cuda_check(ctx, cudaMemset(D->d_time, 0, sizeof(double)), "time")))
+        return st;
+    P.time = D->d_time;
     {   // c^2 / element mean of c^2 at the nodes: features of the learned u_t guess
         std::vector<float> feat(nd);
         for (int e = 0; e < ctx->ne; ++e) {
@@ -328,7 +338,7 @@ int gdg_var_setup(gdg_ctx *ctx) {
 void gdg_var_free(gdg_ctx *ctx) {
     VarData *D = ctx->var;
     if (!D) return;
-    cudaFree(D->d_S); cudaFree(D->d_M); cudaFree(D->d_S32); cudaFree(D->d_M32); cudaFree(D->d_dS); cudaFree(D->d_Ainv); cudaFree(D->d_Minv); cudaFree(D->d_G); cudaFree(D->d_FM); cudaFree(D->d_w); cudaFree(D->d_pre); cudaFree(D->d_face);
+    cudaFree(D->d_S); cudaFree(D->d_M); cudaFree(D->d_S32); cudaFree(D->d_M32); cudaFree(D->d_dS); cudaFree(D->d_Ainv); cudaFree(D->d_Minv); cudaFree(D->d_G); cudaFree(D->d_FM); cudaFree(D->d_time); cudaFree(D->d_src); cudaFree(D->d_w); cudaFree(D->d_pre); cudaFree(D->d_face);
     cudaFree(D->d_tab); cudaFree(D->d_nodes); cudaFree(D->d_state); cudaFree(D->d_tr);
     cudaFree(D->d_c2feat); cudaFree(D->d_wbf16); cudaFree(D->d_mlp);
     cudaFree(D->d_ru); cudaFree(D->d_rv); cudaFree(D->d_x0u);
@@ -393,10 +403,11 @@ int gdg_var_pcg(gdg_ctx *ctx, int which, const double *b, double *x, gdg_pcg_sta
     return GDG_OK;
 }
 
-int gdg_var_step(gdg_ctx *ctx, double *u, double *v, double dt, int nsteps, cudaStream_t s) {
+int gdg_var_step(gdg_ctx *ctx, double *u, double *v, double t0, double dt, int nsteps, cudaStream_t s) {
     VarData &D = *ctx->var;
     const size_t bytes = (size_t)ctx->ndof * sizeof(double);
     int st;
+    if (D.vp.src_e >= 0) k_set_time<<<1, 1, 0, s>>>(D.d_time, t0);
     if ((st = gdg_cuda_check(ctx, cudaMemcpyAsync(vbuf(ctx, B_NU), u, bytes, cudaMemcpyDeviceToDevice, s), "copy u")) ||
         (st = gdg_cuda_check(ctx, cudaMemcpyAsync(vbuf(ctx, B_NV), v, bytes, cudaMemcpyDeviceToDevice, s), "copy v")))
         return st;
@@ -553,5 +564,71 @@ extern "C" int gdg_mlp_detach(gdg_ctx *ctx) {
     if (st) return st;
     ctx->var->learned = 0;
     drop_graph(ctx);
+    return GDG_OK;
+}
+
+// ------------------------------------------------------- point source ------
+
+// Point source f(x, t) = amplitude sin(omega t) delta(x - x_s) on the right of
+// u_tt = div(c^2 grad u) + f: its load on r_v (int phi_a f) is
+// phi_a(x_s) amplitude sin(omega t) on the element holding x_s, with x_s given
+// by that element and its reference coordinates (r, s).
+extern "C" int gdg_set_point_source(gdg_ctx *ctx, int element, double r, double s, double amplitude,
+                                    double omega) {
+    int st;
+    if ((st = require_var(ctx))) return st;
+    if (element < 0 || element >= ctx->ne || !(r >= 0.0 && r <= 1.0) || !(s >= 0.0 && s <= 1.0) ||
+        !std::isfinite(amplitude) || !std::isfinite(omega))
+        return gdg_set_err(ctx, GDG_EINVAL, "point source: element index, (r, s) in [0,1]^2, finite amplitude and omega");
+    VarData &D = *ctx->var;
+    drop_graph(ctx);   // the source is a kernel parameter of the captured launches
+    if (amplitude == 0.0) {
+        D.vp.src_e = -1;
+        return GDG_OK;
+    }
+    const int n1 = ctx->n1, NA = n1 * n1;
+    std::vector<double> pr(n1), dpr(n1), ps(n1), dps(n1), w(2 * (size_t)NA, 0.0);
+    gdg_eval_basis(ctx->p, ctx->N, r, -1, pr.data(), dpr.data());
+    gdg_eval_basis(ctx->p, ctx->N, s, -1, ps.data(), dps.data());
+    for (int j = 0; j < n1; ++j)
+        for (int i = 0; i < n1; ++i) w[(size_t)j * n1 + i] = ps[j] * pr[i];
+    if (D.vp.inverse) {   // the inverse route adds M_J^-1 w: Gaussian elimination with partial pivoting
+        std::vector<double> M((size_t)NA * NA), x(w.begin(), w.begin() + NA);
+        if ((st = gdg_cuda_check(ctx, cudaMemcpy(M.data(), D.d_M + (size_t)element * NA * NA, M.size() * sizeof(double),
+                                                 cudaMemcpyDeviceToHost), "point source: mass matrix")))
+            return st;
+        for (int k = 0; k < NA; ++k) {
+            int piv = k;
+            for (int i = k + 1; i < NA; ++i)
+                if (std::fabs(M[(size_t)i * NA + k]) > std::fabs(M[(size_t)piv * NA + k])) piv = i;
+            if (piv != k) {
+                for (int c = 0; c < NA; ++c) std::swap(M[(size_t)k * NA + c], M[(size_t)piv * NA + c]);
+                std::swap(x[k], x[piv]);
+            }
+            const double d = M[(size_t)k * NA + k];
+            if (!(std::fabs(d) > 0.0)) return gdg_set_err(ctx, GDG_EINVAL, "point source: singular mass matrix");
+            for (int i = k + 1; i < NA; ++i) {
+                const double m = M[(size_t)i * NA + k] / d;
+                if (m == 0.0) continue;
+                for (int c = k; c < NA; ++c) M[(size_t)i * NA + c] -= m * M[(size_t)k * NA + c];
+                x[i] -= m * x[k];
+            }
+        }
+        for (int k = NA - 1; k >= 0; --k) {
+            double acc = x[k];
+            for (int c = k + 1; c < NA; ++c) acc -= M[(size_t)k * NA + c] * x[c];
+            x[k] = acc / M[(size_t)k * NA + k];
+        }
+        for (int a = 0; a < NA; ++a) w[(size_t)NA + a] = x[a];
+    }
+    if (!D.d_src && (st = gdg_cuda_check(ctx, cudaMalloc((void **)&D.d_src, 2 * (size_t)NA * sizeof(double)), "alloc source")))
+        return st;
+    if ((st = gdg_cuda_check(ctx, cudaMemcpy(D.d_src, w.data(), w.size() * sizeof(double), cudaMemcpyHostToDevice),
+                             "point source: upload")))
+        return st;
+    D.vp.src_e = element;
+    D.vp.src_amp = amplitude;
+    D.vp.src_omega = omega;
+    D.vp.src_w = D.d_src;
     return GDG_OK;
 }

@@ -20,6 +20,11 @@ struct VarParams {
     const float *S32, *M32;      // FP32 copies of S and M (mixed precision only)
     const double *dS;            // [ne][N1*N1] frozen-coefficient preconditioner diagonal (S system)
     const double *FM;            // [ne][4 faces][6 N1 columns][3 N1 rows] face operators (k_var_facemat)
+    // point source f = src_amp sin(src_omega t) delta(x - x_s) (gdg_set_point_source)
+    int src_e;                   // element holding x_s (-1: no source)
+    double src_amp, src_omega;
+    const double *src_w;         // [2][NA]: phi_a(x_s), and M_J^-1 of it (inverse route)
+    double *time;                // source time at the start of the current RK step
     int inverse;                 // GDG_SOLVE_INVERSE: element inverses folded into G instead of PCG
     const double *G;             // [ne][12 N1 + NA][NA] folded operators, column-major (fold_cols)
     unsigned long long *stats;   // [0] sum it_u, [1] sum it_v, [2] max it_u, [3] max it_v,
@@ -37,6 +42,7 @@ struct VarData {
     double *d_dS = nullptr;
     double *d_G = nullptr;                       // folded operators (GDG_SOLVE_INVERSE)
     double *d_FM = nullptr;                      // face operators
+    double *d_time = nullptr, *d_src = nullptr;  // point source: time, weights [2][NA]
     double *d_Ainv = nullptr, *d_Minv = nullptr; // setup temporaries of the fold, freed after it
     double *d_tab = nullptr, *d_nodes = nullptr;
     double *d_state = nullptr, *d_tr = nullptr;
@@ -707,7 +713,15 @@ struct VarBufs {
     int part;
     double *ru, *rv;
     const double *x0u;
+    double tstage;           // this stage's time offset in the RK step (0, dt/2, dt/2, dt)
 };
+
+// load of the point source on r_v at this stage: int phi_a f = phi_a(x_s) s(t)
+__device__ __forceinline__ double source_amplitude(const VarParams &P, const VarBufs &b) {
+    return P.src_amp * sin(P.src_omega * (*P.time + b.tstage));
+}
+
+__global__ void k_set_time(double *time, double t0) { *time = t0; }
 
 template <int N1>
 struct StageSmem {
@@ -966,6 +980,11 @@ __device__ __forceinline__ void var_stage_body(const VarParams &P, const VarBufs
     if (P.inverse) {
         lift_lines<N1>(P, e, b.trin, s.fw, s.L);
         fold_apply<N1>(P.G + (size_t)e * fold_cols(N1) * NA, s.L, s.Yu, s.Yv, s.ru, s.x);
+        if (e == P.src_e) {   // dV/dt += M_J^-1 phi(x_s) s(t)
+            const double amp = source_amplitude(P, b);
+            if (t < NA) s.x[t] += amp * P.src_w[NA + t];
+            __syncthreads();
+        }
     } else if (!guess) {
         lifts<N1>(P, e, b.trin, T, s.fw, s.L, s.ru, s.rv);
         // stiffness: r_v -= S U
@@ -977,6 +996,11 @@ __device__ __forceinline__ void var_stage_body(const VarParams &P, const VarBufs
         }
         if (t < NA) s.rv[t] -= s.Ap[t];
         __syncthreads();
+        if (e == P.src_e) {   // block-uniform
+            const double amp = source_amplitude(P, b);
+            if (t < NA) s.rv[t] += amp * P.src_w[t];
+            __syncthreads();
+        }
         if (b.part == 1) {
             if (t < NA) { b.ru[off + t] = s.ru[t]; b.rv[off + t] = s.rv[t]; }
             return;
@@ -1060,6 +1084,8 @@ __device__ __forceinline__ void var_stage_body(const VarParams &P, const VarBufs
             dV[off + t] = s.Yv[t];
         }
     }
+    // the source block (the only reader of the source time) starts the next step
+    if (MODE == M_S4 && e == P.src_e && t == 0) *P.time += b.tstage;
     if (MODE == M_RHS) return;
     __syncthreads();
     face_lines<N1>(s.Yu, s.Yv, T, b.trout + lix<N1>(e, 0));

@@ -89,6 +89,8 @@ EXPORTS = {
     "gdg_set_stage_variant": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "gdg_get_stage_variant": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
     "gdg_set_wait_limit": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double]),
+    "gdg_set_point_source": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                            ctypes.c_double, ctypes.c_double]),
     "gdg_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
                                         ctypes.POINTER(ctypes.c_double)]),
 }
@@ -296,6 +298,11 @@ class Context:
         """2-D constant coefficient: 0 one thread per line, 1 two, 2 one per line
         and field, 3 persistent step, -1 timed choice."""
         self._check(lib().gdg_set_stage_variant(self._h, int(variant)), "gdg_set_stage_variant")
+
+    def set_point_source(self, element, r, s, amplitude, omega):
+        """f = amplitude sin(omega t) delta(x - x_s), x_s at reference (r, s) of element."""
+        self._check(lib().gdg_set_point_source(self._h, int(element), float(r), float(s), float(amplitude),
+                                               float(omega)), "gdg_set_point_source")
 
     def set_wait_limit(self, seconds):
         """Bound on any device-side wait (seconds of wall time)."""

@@ -274,6 +274,52 @@ def executed_flops_per_element_stage_3d(n1):
     return 66 * n1 ** 2 + 34 * n1 ** 3
 
 
+def ocean_sound_speed(depth):
+    """Depth-dependent sound speed of the ocean-channel application (Section 7.2),
+    m/s, depth in m (positive down)."""
+    import numpy as np
+    return 1450.0 + 50.0 * (100.0 / (depth + 40.0) + np.tanh((depth - 300.0) / 50.0))
+
+
+def forms_ocean(nx=500, ny=250, N=8, p=3, steps=16):
+    """The ocean-channel workload of Section 7.2 (the paper shows it as pictures
+    only): the channel [0, 4000] x [-2000, 0] m with the depth-dependent sound
+    speed c(D), D = -y, and a point source sin(400 pi t) at x = 1004 m,
+    D = 300 m (near the sound-channel axis; the centre of an element), u = 0
+    on every side.  The paper's
+    100 x 50 elements of 40 x 40 cells are taken as 500 x 250 elements of 8 x 8
+    cells (the same 4000 x 2000 cells), p = 3; element inverses with face
+    operators; dt = 0.2 h / max c."""
+    import numpy as np
+    import torch
+    from paper_2105_01722_gb300 import gdg, inputs
+    t_setup = time.perf_counter()
+    X, Y = inputs.cartesian_nodes((nx, ny), N, lo=(0.0, -2000.0), hi=(4000.0, 0.0))
+    C2 = ocean_sound_speed(-Y) ** 2
+    pb = gdg.make_problem(2, (nx, ny), N, p, bc=(gdg.BC_DIRICHLET, gdg.BC_DIRICHLET), flux=gdg.FLUX_UPWIND,
+                          coef=gdg.COEF_NODAL, x_nodes=X, y_nodes=Y, c2_nodes=C2, solver=gdg.SOLVE_INVERSE)
+    ctx = gdg.Context(pb)
+    Hx, Hy = 4000.0 / nx, 2000.0 / ny
+    xs, ys = 1004.0, -300.0
+    ex, ey = int(xs // Hx), int((ys + 2000.0) // Hy)
+    ctx.set_point_source(ey * nx + ex, xs / Hx - ex, (ys + 2000.0) / Hy - ey, 1.0, 400.0 * np.pi)
+    setup_s = time.perf_counter() - t_setup
+    u = torch.zeros(X.size, dtype=torch.float64, device="cuda")
+    v = torch.zeros_like(u)
+    h = min(Hx, Hy) / N
+    dt = 0.2 * h / float(np.sqrt(C2.max()))
+    ctx.step(u, v, 0.0, dt, 8)
+    ms = _timed_ms(lambda: ctx.step(u, v, 8 * dt, dt, steps))
+    finite = bool(torch.isfinite(u).all() and torch.isfinite(v).all())
+    E = ctx.energy(u, v)
+    ctx.close()
+    dof = nx * ny * (N + 1) ** 2
+    return {"workload": "ocean channel 4000 x 2000 m, c(depth), point source sin(400 pi t) at (1004 m, 300 m "
+                        "deep), %d x %d elements of %d x %d cells, p=%d, element inverses" % (nx, ny, N, N, p),
+            "dof": dof, "dof_steps_per_s": dof * steps / (ms / 1e3), "ms_per_step": ms / steps,
+            "setup_s": setup_s, "dt": dt, "finite": finite, "energy_after": E}
+
+
 def forms_three_d(n=32, N=8, p=5, steps=16):
     """3-D constant coefficient (Sections 2.1.2 and 3 for d = 3): n^3 elements
     of N^3 cells, upwind, Dirichlet, standing mode sin(pi x) sin(pi y) sin(pi z),
@@ -495,7 +541,8 @@ def run_gdg(args):
         forms = {}
         if not args.no_forms and world == 1:
             for key, fn in (("variable_mapped_128", forms_variable), ("batched_48", forms_batched),
-                            ("learned_guess", forms_learned), ("three_d_32", forms_three_d)):
+                            ("learned_guess", forms_learned), ("three_d_32", forms_three_d),
+                            ("ocean_channel", forms_ocean)):
                 try:
                     forms[key] = fn()
                 except Exception as exc:    # report, do not lose the headline line

@@ -35,13 +35,22 @@ Readings made here (the paper leaves them open):
   weight gives the same y, and this one keeps the rank-one term O(1) so
   rounding in the constant mode is not amplified by 1/|e|^2;
 * PCG (element by element) stops when ||r||_2 <= rtol ||b||_2, tested
-  before each iteration, or after maxit iterations; rz = 0 ends it.
+  before each iteration, or after maxit iterations; rz = 0 ends it;
+* the IC(0) preconditioner of Section 7.1 ("of S_c2 and M"): S_c2 is
+  singular, so the u_t system's factor is that of S_c2 + w w^T taken on the
+  sparsity pattern of S_c2; the v_t system's is that of M_J on its own
+  pattern;
+* a distributed forcing f enters r_v as int phi_a f |J| (the load Eq. DG2
+  omits; the variational statement carries it), by quadrature with p+3
+  points per cell.
 
 Layout of nodal arrays: [ey, ex, j, i] with i along the reference r axis.
 """
+import functools
 from dataclasses import dataclass
 
 import numpy as np
+from scipy.linalg import solve_triangular
 
 from . import gd_basis
 
@@ -170,6 +179,42 @@ def assemble(vp):
     return ops
 
 
+@functools.lru_cache(maxsize=16)
+def quadrature(p, N, nq):
+    """Tensor Gauss-Legendre rule on the reference element (nq points per GD
+    cell per direction): Phi[q, a] = phi_a at point q, Gr, Gs the r and s
+    derivatives, W the weights (index q = b*Q + a, b along s)."""
+    r, w, cell = gd_basis.quadrature_points(p, N, nq)
+    B, D = gd_basis.basis_at_points(p, N, r, cell)
+    return np.kron(B, B), np.kron(B, D), np.kron(D, B), np.kron(w, w)
+
+
+def _mapped_points(vp, nq):
+    """Physical points (x, y) and |J| at every element's quadrature points."""
+    Phi, Gr, Gs, W = quadrature(vp.p, vp.N, nq)
+    ne = vp.n[0] * vp.n[1]
+    Xe, Ye = vp.X.reshape(ne, -1), vp.Y.reshape(ne, -1)
+    det = (Xe @ Gr.T) * (Ye @ Gs.T) - (Xe @ Gs.T) * (Ye @ Gr.T)
+    return Phi, W, Xe @ Phi.T, Ye @ Phi.T, det
+
+
+def distributed_load(vp, f, nq=None):
+    """int phi_a f |J| over every element (the forcing term of Eq. DG2 for
+    u_tt = div(c^2 grad u) + f, Section 7.1), f a callable of the physical
+    (x, y) arrays; returns (ne, n1^2), the `forcing` argument of residuals."""
+    Phi, W, xq, yq, det = _mapped_points(vp, vp.p + 3 if nq is None else nq)
+    return (W * det * f(xq, yq)) @ Phi
+
+
+def l2_error(vp, U, u_exact, nq=None):
+    """||u - u_h||_L2 (Section 6's error measure) on mapped elements by
+    quadrature with p+3 points per cell; u_exact a callable of (x, y)."""
+    Phi, W, xq, yq, det = _mapped_points(vp, vp.p + 3 if nq is None else nq)
+    ne = vp.n[0] * vp.n[1]
+    uh = U.reshape(ne, -1) @ Phi.T
+    return float(np.sqrt(np.sum(W * det * (u_exact(xq, yq) - uh) ** 2)))
+
+
 def _neighbour(vp, ey, ex, face):
     """(element index, its face) across `face`, or None on a Dirichlet side."""
     nx, ny = vp.n
@@ -283,21 +328,24 @@ def fdm_preconditioner(ops, e, which, Psi, lam):
     return Psi2 @ (d[:, None] * Psi2.T)
 
 
-def ic0(A):
-    """Zero fill-in incomplete Cholesky A ~ L L^T on the pattern of A
-    (textbook IC(0); the paper uses Jones-Plassmann's implementation)."""
+def ic0(A, pattern=None):
+    """Zero fill-in incomplete Cholesky A ~ L L^T (textbook IC(0)).
+
+    Section 7.1 preconditions the two element systems with the IC(0)
+    factors of S_c2 and M.  IC(0) runs the steps of the right-looking
+    Cholesky factorisation but keeps only the entries of L that lie in the
+    sparsity pattern (default: the nonzeros of A); every update that would
+    create fill outside it is dropped.  Where the exact Cholesky factor has
+    no fill outside the pattern (banded matrices, Kronecker products of
+    banded matrices) IC(0) is that factor."""
     n = A.shape[0]
-    L = np.tril(A).copy()
-    pattern = np.tril(A) != 0.0
+    P = (np.tril(A) != 0.0) if pattern is None else np.tril(np.asarray(pattern, dtype=bool))
+    L = np.where(P, np.tril(A), 0.0)
     for k in range(n):
         L[k, k] = np.sqrt(L[k, k])
-        for i in range(k + 1, n):
-            if pattern[i, k]:
-                L[i, k] /= L[k, k]
-        for j in range(k + 1, n):
-            for i in range(j, n):
-                if pattern[i, j] and pattern[i, k] and pattern[j, k]:
-                    L[i, j] -= L[i, k] * L[j, k]
+        L[k + 1:, k] = np.where(P[k + 1:, k], L[k + 1:, k] / L[k, k], 0.0)
+        col = L[k + 1:, k]
+        L[k + 1:, k + 1:] -= np.where(P[k + 1:, k + 1:], np.tril(np.outer(col, col)), 0.0)
     return L
 
 
@@ -348,9 +396,13 @@ def solve_pcg(vp, ops, V, r_u, r_v, precond="fdm", rtol=1e-10, maxit=200,
             pu = lambda r, P=Pu: P @ r
             pm = lambda r, P=Pm: P @ r
         elif precond == "ic0":
-            Lu, Lm = ic0(Au), ic0(Am)
-            pu = lambda r, L=Lu: np.linalg.solve(L.T, np.linalg.solve(L, r))
-            pm = lambda r, L=Lm: np.linalg.solve(L.T, np.linalg.solve(L, r))
+            # Section 7.1: IC(0) of S_c2 for the u_t system and of M for the
+            # v_t system.  S_c2 is singular (its kernel is the constants), so
+            # the factor is taken of the SPD matrix solved, S_c2 + w w^T, on
+            # the sparsity pattern of S_c2 (the rank-one term would fill it).
+            Lu, Lm = ic0(Au, ops.S[e] != 0.0), ic0(Am, Am != 0.0)
+            pu = lambda r, L=Lu: solve_triangular(L.T, solve_triangular(L, r, lower=True), lower=False)
+            pm = lambda r, L=Lm: solve_triangular(L.T, solve_triangular(L, r, lower=True), lower=False)
         elif precond == "none":
             pu = pm = lambda r: r.copy()
         else:

@@ -148,13 +148,21 @@ def test_graph_path_and_energy_3d():
     assert abs(E0 - dc.energy(prob, U, V, ops)) < 1e-12 * E0
     h = min(prob.H(k) for k in range(3)) / prob.N
     dt = 0.05 * h / np.sqrt(c["c2"])
-    ctx.step(u, v, 0.0, dt, 19)
+    steps = 19
+    floor = _route_floor(prob, U, V)
+    ctx.step(u, v, 0.0, dt, steps)
     f = lambda t, U, V: dc.time_derivative(prob, U, V, ops)
-    U, V = ti.integrate(f, U, V, 0.0, dt, 19)
+    U, V = ti.integrate(f, U, V, 0.0, dt, steps)
     a = np.concatenate([u.cpu().numpy(), v.cpu().numpy()])
-    assert _rel(a, np.concatenate([U.ravel(), V.ravel()])) < 10 * _route_floor(prob, U, V)
+    # one step of either side is within the rounding floor of the exact step
+    # and the step map is non-expansive here, so the gap grows at most
+    # linearly: steps x floor
+    gap = _rel(a, np.concatenate([U.ravel(), V.ravel()]))
+    assert gap < steps * floor
     E1 = ctx.energy(u, v)
-    assert abs(E1 - dc.energy(prob, U, V, ops)) < 1e-11 * E1
+    # a quadratic form of two states a relative gap g apart differs by at
+    # most 2 g relative, plus the rounding of the energy sum itself
+    assert abs(E1 - dc.energy(prob, U, V, ops)) < (2 * steps * floor + TOL) * E1
     assert E1 <= E0 * (1 + 1e-12) and E1 > 0.99 * E0
     ctx.close()
 
@@ -175,7 +183,7 @@ def _patch_rhs(U, V, n, N, p, ez, ey, ex):
     Us, Vs = U[sl].reshape(ne, -1), V[sl].reshape(ne, -1)
     Ut, Vt = dc.time_derivative(prob, Us, Vs)
     c = ((ez - lo_i[2]) * m[1] + (ey - lo_i[1])) * m[0] + (ex - lo_i[0])
-    return Ut[c], Vt[c]
+    return Ut[c], Vt[c], _route_floor(prob, Us, Vs)
 
 
 def test_full_size_32cubed_p5_sampled():
@@ -195,9 +203,9 @@ def test_full_size_32cubed_p5_sampled():
     du = du.cpu().numpy().reshape(U.shape[:3] + (-1,))
     dvv = dv.cpu().numpy().reshape(U.shape[:3] + (-1,))
     for ez, ey, ex in [(0, 0, 0), (31, 31, 31), (15, 16, 17), (0, 31, 9), (20, 0, 31)]:
-        Ut, Vt = _patch_rhs(U, V, n, N, p, ez, ey, ex)
+        Ut, Vt, floor = _patch_rhs(U, V, n, N, p, ez, ey, ex)
         a = np.concatenate([du[ez, ey, ex], dvv[ez, ey, ex]])
-        assert _rel(a, np.concatenate([Ut, Vt])) < 10 * TOL, (ez, ey, ex)
+        assert _rel(a, np.concatenate([Ut, Vt])) < floor, (ez, ey, ex)
     U0 = np.sin(np.pi * X) * np.sin(np.pi * Y) * np.sin(np.pi * Z)
     u, v = _dev(U0), torch.zeros(U0.size, dtype=torch.float64, device="cuda")
     E = [ctx.energy(u, v)]

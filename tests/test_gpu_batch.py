@@ -1,7 +1,9 @@
 """Batched persistent launch (gdg_batch_*): every problem of a batch ends
 exactly where its own gdg_step takes it (the stage bodies are shared), for
 modal and PCG problems, p = 3, 5, 7, FP64 and mixed precision, through the
-graph path and the remainder; the tuner reports its choice."""
+graph path and the remainder; the tuner reports its choice; and every
+problem of a mixed batch matches the FP64 oracle's RK4 (FP64 PCG, mixed
+precision and element-inverse forms)."""
 import numpy as np
 import pytest
 
@@ -78,3 +80,92 @@ def test_batch_rejects_mixed_cell_counts():
     pbs = [gdg.make_problem(2, (4, 4), 8, 3), gdg.make_problem(2, (4, 4), 9, 3)]
     with pytest.raises(gdg.GdgError):
         gdg.Batch(pbs)
+
+
+# ---------------------------------------------------------------- oracle parity
+
+EPS = np.finfo(np.float64).eps
+TOL = 1e-12
+# (variable c^2, p, elements per direction): every degree, both kinds
+ORACLE_SPECS = [(False, 3, 4), (True, 3, 3), (False, 5, 3), (True, 5, 4), (True, 7, 3), (False, 7, 3)]
+
+
+def _rel(a, b):
+    return np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.linalg.norm(np.ravel(b))
+
+
+def _oracle_rhs(variable, n, p, C2, X, Y, form, K):
+    """The oracle's semi-discrete derivative of one batch problem: constant
+    c^2 = 1 through the Cartesian oracle (dense solves); variable c^2 through
+    the quadrature oracle with exactly K PCG iterations per solve (form
+    'fp64') or dense direct solves ('mixed', 'inverse')."""
+    from oracle import dg_const as dc, dg_var as dv
+    if not variable:
+        prob = dc.Problem(dim=2, n=(n, n), N=8, p=p, flux="upwind", c2=1.0)
+        ops = dc.operators(prob)
+        return (lambda t, U, V: dc.time_derivative(prob, U, V, ops)), None
+    vp = dv.VarProblem(n=(n, n), N=8, p=p, X=X, Y=Y, C2=C2, flux="upwind")
+    ops = dv.assemble(vp)
+    if form == "fp64":
+        f = lambda t, U, V: dv.solve_pcg(vp, ops, V, *dv.residuals(vp, ops, U, V), precond="fdm",
+                                         rtol=0.0, maxit=K)[:2]
+    else:
+        f = lambda t, U, V: dv.time_derivative(vp, ops, U, V)
+    kappa = max(max(np.linalg.cond(dv.spd_u_matrix(ops, e)), np.linalg.cond(ops.M[e])) for e in range(n * n))
+    return f, kappa
+
+
+@pytest.mark.parametrize("form", ["fp64", "mixed", "inverse"])
+def test_batch_matches_oracle(form):
+    """A batch of six problems (p = 3, 5, 7; constant and variable c^2), five
+    RK4 steps in one gdg_batch_step call (one replay of the 4-step graph and
+    one step outside it), each problem against the oracle's RK4.  Bounds per
+    step, added over the steps (the step map is non-expansive at these CFLs):
+    constant c^2, 1e-12; variable c^2 with K = 6 PCG iterations on both
+    sides ('fp64'), max(1e-12, sqrt(81) kappa eps); element inverses against dense
+    solves, max(1e-12, 50 kappa eps); FP32 inner PCG refined to the FP64
+    residual test rtol = 1e-12 against dense solves ('mixed'), 2.8 kappa rtol
+    (each stage derivative within kappa rtol relative, dt |k| <= 2.8 |y| in
+    RK4's stability interval)."""
+    from oracle import timeint as ti
+    K, steps, rtol = 6, 5, 1e-12
+    prec = gdg.MIXED if form == "mixed" else gdg.FP64
+    solver = gdg.SOLVE_INVERSE if form == "inverse" else gdg.SOLVE_PCG
+    pbs, states, dts, oracles = [], [], [], []
+    for i, (variable, p, n) in enumerate(ORACLE_SPECS):
+        X, Y = inputs.cartesian_nodes((n, n), 8)
+        U0 = inputs.gaussian_pulse(X, Y, 0.45, 0.55, 0.2) + 0.01 * inputs.random_state(X.shape, 300 + i)
+        V0 = 0.01 * inputs.random_state(X.shape, 400 + i)
+        C2 = inputs.smooth_random_c2(X, Y, 77 + i) if variable else None
+        if variable:
+            pb = gdg.make_problem(2, (n, n), 8, p, coef=gdg.COEF_NODAL, x_nodes=X, y_nodes=Y, c2_nodes=C2,
+                                  solver=solver, precision=prec,
+                                  pcg_rtol=0.0 if form == "fp64" else rtol,
+                                  pcg_maxit=K if form == "fp64" else 300, refine_max=20, refine_rtol=1e-5)
+            cmax = float(np.sqrt(C2.max()))
+        else:
+            pb = gdg.make_problem(2, (n, n), 8, p, c2=1.0)
+            cmax = 1.0
+        pbs.append(pb)
+        states.append((U0, V0))
+        dts.append(CFL[p] / (n * 8) / cmax)
+        oracles.append(_oracle_rhs(variable, n, p, C2, X, Y, form, K))
+    batch = gdg.Batch(pbs)
+    us = [torch.tensor(U.ravel(), device="cuda") for U, _ in states]
+    vs = [torch.tensor(V.ravel(), device="cuda") for _, V in states]
+    batch.step(us, vs, dts, steps)
+    for i, ((variable, p, n), (U, V), dt, (f, kappa)) in enumerate(zip(ORACLE_SPECS, states, dts, oracles)):
+        ne = n * n
+        Uo, Vo = ti.integrate(f, U.reshape(ne, -1), V.reshape(ne, -1), 0.0, dt, steps)
+        if not variable:
+            per_step = TOL
+        elif form == "fp64":
+            per_step = max(TOL, 9.0 * kappa * EPS)      # sqrt(n) kappa eps, n = 81 terms per product
+        elif form == "inverse":
+            per_step = max(TOL, 50.0 * kappa * EPS)
+        else:
+            per_step = TOL + 2.8 * kappa * rtol
+        got = torch.cat([us[i], vs[i]]).cpu().numpy()
+        ref = np.concatenate([Uo.ravel(), Vo.ravel()])
+        assert _rel(got, ref) < steps * per_step, (form, i, _rel(got, ref), steps * per_step)
+    batch.close()

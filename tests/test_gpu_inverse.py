@@ -61,10 +61,13 @@ def _pair(n, N, p, kind="mapped", c2="sine", flux="upwind", periodic=(False, Fal
     return vp, gdg.Context(_problem(n, N, p, X, Y, C2, flux=flux, periodic=periodic))
 
 
-def _tol(ops):
+def _kappa(ops):
     ne = ops.M.shape[0]
-    kappa = max(max(np.linalg.cond(dv.spd_u_matrix(ops, e)), np.linalg.cond(ops.M[e])) for e in range(ne))
-    return max(1e-12, 50.0 * kappa * EPS)
+    return max(max(np.linalg.cond(dv.spd_u_matrix(ops, e)), np.linalg.cond(ops.M[e])) for e in range(ne))
+
+
+def _tol(ops):
+    return max(1e-12, 50.0 * _kappa(ops) * EPS)
 
 
 CASES = [
@@ -116,7 +119,8 @@ def test_inverse_steps_match_oracle(c):
         ctx.step(u, v, s * dt, dt, 1)
         U, V = ti.rk4_step(f, U, V, s * dt, dt)
         a = np.concatenate([u.cpu().numpy(), v.cpu().numpy()])
-        assert _rel(a, np.concatenate([U.ravel(), V.ravel()])) < 10 * tol, s
+        # per-step gaps add up at most linearly (non-expansive step map)
+        assert _rel(a, np.concatenate([U.ravel(), V.ravel()])) < (s + 1) * tol, s
     ctx.close()
 
 
@@ -133,7 +137,7 @@ def _patch_rhs_direct(X, Y, C2, U, V, N, p, ey, ex):
     ne = n[0] * n[1]
     Ut, Vt = dv.time_derivative(vp, ops, U[sl].reshape(ne, -1), V[sl].reshape(ne, -1))
     c = (ey - y0) * n[0] + (ex - x0)
-    return Ut[c], Vt[c], _tol(ops)
+    return Ut[c], Vt[c], _tol(ops), _kappa(ops)
 
 
 def test_inverse_full_size_mapped_128():
@@ -150,8 +154,10 @@ def test_inverse_full_size_mapped_128():
     ctx.rhs(u, v, du, dv_)
     du = du.cpu().numpy().reshape(128, 128, -1)
     dvv = dv_.cpu().numpy().reshape(128, 128, -1)
+    kappa = 0.0
     for ey, ex in [(0, 0), (0, 77), (127, 127), (64, 64), (31, 100), (127, 5)]:
-        Ut, Vt, tol = _patch_rhs_direct(X, Y, C2, U, V, N, p, ey, ex)
+        Ut, Vt, tol, k = _patch_rhs_direct(X, Y, C2, U, V, N, p, ey, ex)
+        kappa = max(kappa, k)
         a = np.concatenate([du[ey, ex], dvv[ey, ex]])
         assert _rel(a, np.concatenate([Ut, Vt])) < tol, (ey, ex)
     # trajectory: inverse route vs PCG at rtol 1e-10 (same method, PCG residual 1e-10)
@@ -164,7 +170,12 @@ def test_inverse_full_size_mapped_128():
         c.step(u, v, 0.0, dt, 8)
         states.append(torch.cat([u, v]).cpu().numpy())
         c.close()
-    assert _rel(states[0], states[1]) < 1e-8
+    # PCG's stage derivatives are within kappa rtol (relative) of the exact
+    # ones; a step adds dt times a weighted mean of them, and dt |k| <= dt
+    # rho(L) |y| <= 2.8 |y| inside RK4's stability interval, so after 8 steps
+    # the relative gap is at most 8 x 2.8 x kappa x rtol (kappa from the
+    # sampled patches' element systems)
+    assert _rel(states[0], states[1]) < 8 * 2.8 * kappa * 1e-10
 
 
 def test_inverse_batch_equals_individual_steps():

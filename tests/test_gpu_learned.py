@@ -51,12 +51,22 @@ def test_forward_and_gradients_match_oracle():
     net.forward(Xd, Y)
     P = _oracle_params(net)
     ref, _ = omlp.forward(P, X.astype(np.float64))
+    # FP32 accumulation of dot products of at most K = 162 terms: each layer
+    # adds at most K u32 (u32 = 2^-24 = 6e-8, 1e-5) relative to its largest
+    # term; tanh does not amplify; three layers: 3e-5 of the output scale
+    # in the worst case, 2e-5 with the random-sign cancellation of sums
     assert np.abs(Y.cpu().numpy() - ref).max() < 2e-5 * np.abs(ref).max()
     loss = float(net.backward(Xd, Td).item())
     gref = _flat(omlp.backward(P, X.astype(np.float64), T.astype(np.float64)))
     lref = omlp.loss(P, X.astype(np.float64), T.astype(np.float64))
+    # the loss sums B x 81 squared FP32 outputs (each within 2e-5, above):
+    # relative 2 x 2e-5 bounds it, and 1e-5 holds with the cancellation of
+    # the output errors' signs
     assert abs(loss - lref) < 1e-5 * lref
     g = net.grad.cpu().numpy().astype(np.float64)
+    # gradients: back through three layers (each <= K u32 = 1e-5) and a
+    # fixed-order FP32 sum over the B = 70 samples (<= B u32 = 4e-6):
+    # 1e-4 covers the product of the layers' factors
     assert np.linalg.norm(g - gref) < 1e-4 * np.linalg.norm(gref)
     # a subset through the index array gives the subset's gradient
     idx = torch.tensor(np.array([5, 60, 0, 33, 12], dtype=np.int32), device="cuda")
@@ -76,6 +86,9 @@ def test_adam_step_and_bf16_refresh():
     m = 0.1 * g / (1 - 0.9)
     v = 0.001 * g.astype(np.float64) ** 2 / (1 - 0.999)
     expect = params - 1e-3 * m / (np.sqrt(v) + 1e-8)
+    # every update is about lr = 1e-3 in size, computed in FP32 (relative
+    # 2^-24) and added to parameters of size <= 0.2 (FP32 spacing 1.5e-8):
+    # the FP32 result is within a few 1e-8 of the FP64 one; 1e-6 bounds it
     assert np.abs(net.params.cpu().numpy() - expect).max() < 1e-6
     w = net.wbf16.cpu().numpy().view(np.uint16).astype(np.uint32) << 16
     wf = w.view(np.float32)
@@ -104,6 +117,7 @@ def test_residuals_and_rows_match_oracle():
     ctx.residuals(u, v, gru, grv)
     a = np.concatenate([gru.cpu().numpy(), grv.cpu().numpy()])
     b = np.concatenate([ru.ravel(), rv.ravel()])
+    # FP64 residuals (no solve): the parity bound of 1e-12
     assert np.linalg.norm(a - b) < 1e-12 * np.linalg.norm(b)
     y = torch.tensor(inputs.random_state(ne * 81, 8), device="cuda")
     Xr = torch.empty(ne * 162, dtype=torch.float32, device="cuda")
@@ -111,6 +125,8 @@ def test_residuals_and_rows_match_oracle():
     ctx.mlp_rows(gru, y, Xr, Tr)
     xref, nr = omlp.features(C2.reshape(ne, 81), ru)
     tref = y.cpu().numpy().reshape(ne, 81) / nr[:, None]
+    # FP32 features and targets of FP64 values: one FP32 rounding (6e-8)
+    # after FP64 arithmetic; 1e-6 leaves room for the norm's FP64 sum
     assert np.abs(Xr.cpu().numpy().reshape(ne, 162) - xref).max() < 1e-6 * max(1.0, np.abs(xref).max())
     assert np.abs(Tr.cpu().numpy().reshape(ne, 81) - tref).max() < 1e-6 * np.abs(tref).max()
     ctx.close()
@@ -126,6 +142,7 @@ def test_guess_path_matches_plain_and_falls_back():
     V = inputs.random_state((16, 81), 10)
     Ut, Vt = dv.time_derivative(vp, ops, U, V)
     ref = np.concatenate([Ut.ravel(), Vt.ravel()])
+    kappa = max(max(np.linalg.cond(dv.spd_u_matrix(ops, e)), np.linalg.cond(ops.M[e])) for e in range(16))
     u, v = torch.tensor(U.ravel(), device="cuda"), torch.tensor(V.ravel(), device="cuda")
     for bias in (0.0, 1e4):
         params = learned.glorot_params(4)
@@ -136,7 +153,9 @@ def test_guess_path_matches_plain_and_falls_back():
         ctx.rhs(u, v, du, dv_)
         su, _ = ctx.step_stats()
         a = np.concatenate([du.cpu().numpy(), dv_.cpu().numpy()])
-        assert np.linalg.norm(a - ref) < 1e-9 * np.linalg.norm(ref), bias
+        # converged at rtol 1e-13: each solve within kappa x rtol (relative)
+        # of the exact one, whatever the starting guess
+        assert np.linalg.norm(a - ref) < (kappa * 1e-13 + 1e-12) * np.linalg.norm(ref), bias
         assert su["guessed"] == 16
         if bias > 0:
             assert su["fell_back"] == 16
@@ -175,6 +194,17 @@ def test_training_lowers_loss_and_guess_stays_exact():
         iters.append(su["mean_iters"])
         states.append(torch.cat([u, v]).cpu().numpy())
         ctx.close()
-    assert iters[1] <= iters[0] + 0.5, iters
+    print("learned guess: u_t PCG mean iters plain %.4f learned %.4f; held-out rel err %.3f" % (iters[0], iters[1], err))
+    # measured: 9.32 plain against 9.35 with the guess (held-out relative
+    # error 0.77) on this 12 x 12 mesh; 5.23 against 5.11 on the 128 x 128
+    # benchmark mesh.  The frozen-coefficient preconditioner cuts the
+    # residual about 100x per iteration, so a guess of relative error e can
+    # save at most log(1/e) / log(100) iterations: 0.06 at e = 0.77.  The
+    # network neither helps nor hurts by more than a quarter iteration here.
+    assert abs(iters[1] - iters[0]) < 0.25, iters
     a, b = states
-    assert np.linalg.norm(a - b) <= 1e-8 * np.linalg.norm(b)
+    # both runs converge every solve to rtol 1e-10 from different starting
+    # points: stage derivatives within kappa rtol of the exact ones, a step
+    # adds dt |k| <= 2.8 |y| of them (RK4 stability interval), 12 steps, two
+    # runs; kappa <= 1e4 for these p = 5 elements (c^2 in [1/2, 2])
+    assert np.linalg.norm(a - b) <= 2 * 12 * 2.8 * 1e4 * 1e-10 * np.linalg.norm(b)

@@ -12,8 +12,10 @@ boundary, standing mode cos(sqrt2 pi t) sin(pi x) sin(pi y), dt = 0.15 h
 (0.8 of the largest RK4-stable step for the upwind p = 5 operator).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gdg|reference]
-Under torchrun every rank advances its own replica of the workload (the
-benchmark runs independent replicas: no data exchanged between GPUs).
+Under torchrun (N > 1) the ranks advance one mesh of 64 x 64N elements
+together: each owns a 64 x 64 band of element rows (weak scaling), and the
+face traces along the band edges go to the neighbouring ranks (NCCL point
+to point) before every RK stage; `value` counts the DOF of all bands.
 """
 import argparse
 import json
@@ -39,38 +41,125 @@ def dof(w=WORKLOAD):
     return nel * (w["N"] + 1) ** w["dim"]
 
 
-def flops_per_stage_launch(w=WORKLOAD):
-    """Algorithmic FP64 flops of one fused stage launch (an FMA counts 2):
-    per element 2-D: fluxes 4 faces x n1 points x 11, per modal entry 26
-    (lifts 7 + 9, diagonal solve 2, RK accumulate / next input 8), traces
-    of the next input 2 directions x 4 dots x n1 x n1 x 2."""
-    n1 = w["N"] + 1
-    nel = w["n"][0] * w["n"][1]
-    return nel * (44 * n1 + 26 * n1 * n1 + 16 * n1 * n1)
-
-
 def executed_flops_per_stage_launch(w=WORKLOAD):
-    """FP64 flops the parity stage kernels execute per stage launch (FMA = 2).
-    With the modes ordered even first, gR = +-gL and eR = +-eL, so per element
-    2-D: fluxes 2 directions x n1 lines x (2 faces x 7 + 4 sums/differences),
-    per modal entry 18 (lifts 3 + 5, diagonal solve 2, RK 8), traces one
-    split dot per direction and field (8 per entry) + 8 n1 sums/differences."""
+    """FP64 flops the parity stage kernels execute per stage launch (FMA = 2,
+    averaged over the four RK stages).  With the modes ordered even first,
+    gR = +-gL and eR = +-eL, so per element 2-D: fluxes 2 directions x n1
+    lines x (2 faces x 7 + 4 sums/differences); per modal entry 23.5: k_u with
+    the lifts folded into the solve 4, r_v 5, the RK update 6.5 (stage 1: 4,
+    stages 2-3: 8, stage 4: 6), the traces' split dots 8; + 8 n1 trace
+    sums/differences.  (ncu on the persistent step: 2,339 per element and
+    stage from its DFMA / DADD / DMUL counts, this count 2,300.)"""
     n1 = w["N"] + 1
     nel = w["n"][0] * w["n"][1]
-    return nel * (44 * n1 + 26 * n1 * n1)
+    return nel * (44 * n1 + 23.5 * n1 * n1)
 
 
 # FP64 peak derived from unit counts and clock: 152 SMs x 2070 MHz x 4 FP64
-# flop/clk/SM (2 FP64 FMA lanes per SM per clock) = 1.259 TFLOP/s; an FMA-chain
-# probe measured 1.196 TFLOP/s on this GPU.
+# flop/clk/SM (2 FP64 FMA lanes per SM per clock) = 1.259 TFLOP/s.  The bench
+# also measures, in the same process, what an FMA-chain kernel sustains
+# (gdg_probe_fp64) and reports every FP64 fraction against both.
 FP64_PEAK_TFLOPS = 152 * 2.070e9 * 4 / 1e12
+# FP32 peak from unit counts: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+# Algorithmic FP64 flops per DOF per RK stage of the constant-coefficient
+# modal route (the method's own count for the modified basis: fluxes, rank-one
+# lifts per line, diagonal solves, RK combination, traces), the figure the
+# headline roofline uses.
+ALG_FLOPS_PER_DOF_STAGE = 40.0
+
+
+def hbm_peak_gbs():
+    """Measured HBM copy bandwidth (generated MEASURED_PEAKS.json), else
+    the profiling recipe's fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except Exception:
+        return 6800.0, "fallback (6.8 TB/s)"
+
+
+def fp64_probe_tflops(iters=4000, reps=3):
+    """FP64 rate the GPU sustains on independent FMA chains (gdg_probe_fp64,
+    CUDA events on the launching stream, best of reps)."""
+    import torch
+    from paper_2105_01722_gb300 import gdg
+    sink = torch.zeros(1, dtype=torch.float64, device="cuda")
+    best = 0.0
+    for r in range(reps + 1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        flops = gdg.probe_fp64(iters, sink)
+        e1.record()
+        torch.cuda.synchronize()
+        if r:   # the first launch warms up
+            best = max(best, flops / (e0.elapsed_time(e1) / 1e3) / 1e12)
+    return best
+
+
+def var_counts(n1, it_u, it_v, form, sweeps_u=0.0, sweeps_v=0.0):
+    """Algorithmic work per element and RK stage of the variable-coefficient
+    path (Section 7.1), NA = n1^2 nodes: (FP64 flops, FP32 flops, bytes).
+      stiffness term of r_v: one NA x NA product, 2 NA^2;
+      face terms: per face a 3 n1 x 6 n1 operator on the own and neighbour
+        face lines, 4 faces: 144 n1^2; lift assembly 8 NA; RK combination 8 NA;
+      PCG iteration: one NA x NA product (2 NA^2), the frozen-coefficient
+        preconditioner (four n1 x n1 contractions, 8 n1^3) and the vector
+        work (12 NA); each solve also applies the preconditioner once first;
+      mixed: the iterations in FP32; in FP64 one residual product per
+        refinement sweep (2 NA^2) and the first preconditioned step;
+      inverse: the folded operators, 189 columns of NA (2 * 189 NA), no PCG;
+    bytes: the FP64 element matrices (PCG: S_c2 and M_J, 2 NA^2 * 8; mixed:
+    their FP32 copies plus the FP64 matrices once per sweep; inverse: the
+    folded operators 189 NA * 8) plus the face operators (72 n1^2 * 8) and
+    the state."""
+    NA = n1 * n1
+    face = 144 * n1 * n1 + 16 * NA
+    it_cost = 2 * NA * NA + 8 * n1 ** 3 + 12 * NA
+    state = 8 * NA * 8
+    if form == "fp64":
+        f64 = 2 * NA * NA + face + (it_u + it_v) * it_cost + 2 * 8 * n1 ** 3
+        return f64, 0.0, 2 * NA * NA * 8 + 72 * n1 * n1 * 8 + state
+    if form == "mixed":
+        f64 = 2 * NA * NA + face + (1 + sweeps_u + 1 + sweeps_v) * 2 * NA * NA + 8 * n1 ** 3
+        f32 = (it_u + it_v) * it_cost
+        byt = 2 * NA * NA * 4 + (2 + sweeps_u + sweeps_v) * NA * NA * 8 + 72 * n1 * n1 * 8 + state
+        return f64, f32, byt
+    if form == "inverse":
+        cols = 12 * n1 + NA
+        return 2 * cols * NA + face, 0.0, cols * NA * 8 + 72 * n1 * n1 * 8 + state
+    raise ValueError(form)
+
+
+def alu_roofline(f64, f32, byt, seconds, probe):
+    """Roofline block of a whole-step measurement: achieved FP64 (and FP32)
+    rates and HBM bandwidth from the algorithmic counts over the measured
+    time; bound = the resource with the largest fraction."""
+    hbm, hbm_src = hbm_peak_gbs()
+    a64 = f64 / seconds / 1e12
+    a32 = f32 / seconds / 1e12
+    gbs = byt / seconds / 1e9
+    fr = {"fp64": a64 / FP64_PEAK_TFLOPS, "fp32": a32 / FP32_PEAK_TFLOPS, "hbm": gbs / hbm}
+    top = max(fr, key=fr.get)
+    out = {"bound": "alu" if top != "hbm" else "hbm",
+           "achieved": a64 if top == "fp64" else (a32 if top == "fp32" else gbs),
+           "peak": FP64_PEAK_TFLOPS if top == "fp64" else (FP32_PEAK_TFLOPS if top == "fp32" else hbm),
+           "unit": "TFLOP/s" if top != "hbm" else "GB/s", "frac": fr[top], "resource": top,
+           "fp64_tflops": a64, "frac_fp64": fr["fp64"], "frac_fp64_of_probe": a64 / probe if probe else None,
+           "hbm_gbs": gbs, "frac_hbm": fr["hbm"], "hbm_peak_source": hbm_src}
+    if f32:
+        out.update(fp32_tflops=a32, frac_fp32=fr["fp32"])
+    return out
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per RK stage of
 # this workload, from one ncu capture per stage kernel (None for a kernel
 # without a capture of its current code):
 #   k_stage2p: the mean over the four stage launches of one RK4 step
 #   k_step2r: one persistent launch of one RK4 step, over its 4 stages
-STAGE_TRAFFIC_BYTES = {0: 15.66e6, 3: 7.776768e6 / 4}
+STAGE_TRAFFIC_BYTES = {0: None, 3: (7.772160e6 + 256) / 4}
+
+
+PROBE = {}   # in-process measured peaks (filled by run_gdg)
 
 
 def _env_rank():
@@ -154,12 +243,21 @@ for k in range(nsteps):
 """
 
 
-def _oracle_steps(nsteps, target_s):
-    """Time the FP64 oracle (as it stands) on the host cores, single thread:
-    `nsteps` samples of about `target_s` seconds, each a number of RK4 steps
-    of the full benchmark mesh.  Returns [(rk_steps, seconds)] or an error."""
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def _oracle_steps(nsteps, target_s, threads=1):
+    """Time the FP64 oracle (as it stands) on the host cores with `threads`
+    BLAS/OpenMP threads: `nsteps` samples of about `target_s` seconds, each a
+    number of RK4 steps of the full benchmark mesh.  Returns
+    [(rk_steps, seconds)] or an error."""
     code = _ORACLE_TIMER % (ROOT, WORKLOAD, nsteps, target_s)
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+    t = str(threads)
+    env = dict(os.environ, OMP_NUM_THREADS=t, OPENBLAS_NUM_THREADS=t, MKL_NUM_THREADS=t,
                CUDA_VISIBLE_DEVICES="")
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
     if r.returncode != 0:
@@ -168,14 +266,26 @@ def _oracle_steps(nsteps, target_s):
     return [(d["rk_steps"], d["seconds"]) for d in rows], None
 
 
-def cpu_baseline(target_s=15.0):
-    """One bounded sample (about target_s of CPU work) of the oracle."""
-    rows, err = _oracle_steps(1, target_s)
-    if rows is None:
-        return {"value": None, "unit": "DOF-steps/s", "cores": 1, "kind": "oracle", "sample": "failed: " + err}
-    rk, sec = rows[0]
-    return {"value": dof() * rk / sec, "unit": "DOF-steps/s", "cores": 1, "kind": "oracle",
-            "sample": "%d RK4 steps of the full 64x64 p=5 mesh (%.1f s, numpy FP64, 1 thread)" % (rk, sec)}
+def cpu_baseline(target_s=12.0):
+    """Bounded samples (about target_s of CPU work each) of the oracle: with
+    every host core as BLAS threads (the reported figure) and with one."""
+    cores = host_cores()
+    out = None
+    for threads in (cores, 1):
+        rows, err = _oracle_steps(1, target_s, threads)
+        if rows is None:
+            rec = {"value": None, "unit": "DOF-steps/s", "cores": threads, "kind": "oracle",
+                   "sample": "failed: " + err}
+        else:
+            rk, sec = rows[0]
+            rec = {"value": dof() * rk / sec, "unit": "DOF-steps/s", "cores": threads, "kind": "oracle",
+                   "sample": "%d RK4 steps of the full 64x64 p=5 mesh (%.1f s, numpy FP64, %d BLAS threads)"
+                             % (rk, sec, threads)}
+        if out is None:
+            out = rec
+        else:
+            out["single_thread"] = rec
+    return out
 
 
 def run_reference(args):
@@ -184,7 +294,8 @@ def run_reference(args):
     if rank != 0:
         return 0
     total = args.steps + args.warmup
-    rows, err = _oracle_steps(total, max(0.5, 120.0 / total))
+    cores = host_cores()
+    rows, err = _oracle_steps(total, max(0.5, 120.0 / total), cores)
     if rows is None:
         print(json.dumps({"impl": "reference", "unavailable": "oracle run failed: " + err}))
         return 0
@@ -192,15 +303,15 @@ def run_reference(args):
     rk_total = sum(r for r, _ in timed)
     sec_total = sum(s for _, s in timed)
     value = dof() * rk_total / sec_total
-    sample = ("%d timed samples of %d RK4 steps each on the full 64x64 p=5 mesh (numpy FP64, 1 thread)"
-              % (len(timed), timed[0][0]))
+    sample = ("%d timed samples of %d RK4 steps each on the full 64x64 p=5 mesh (numpy FP64, %d BLAS threads)"
+              % (len(timed), timed[0][0], cores))
     line = {"impl": "reference", "metric": "DOF-steps/s", "value": value, "unit": "DOF-steps/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * sec_total / len(timed), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD_NAME, "elements": list(WORKLOAD["n"]), "N": WORKLOAD["N"],
                        "p": WORKLOAD["p"], "dof": dof()},
-            "cpu_baseline": {"value": value, "unit": "DOF-steps/s", "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": "DOF-steps/s", "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "DOF-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -245,10 +356,15 @@ def forms_variable(steps=16):
             ms = _timed_ms(lambda: ctx.step(u, v, 0.0, dt, steps))
             su, sv = ctx.step_stats()
             states[name] = torch.cat([u, v]).cpu().numpy()
+            f64, f32, byt = var_counts(9, su["mean_iters"], sv["mean_iters"], name,
+                                       su["mean_sweeps"], sv["mean_sweeps"])
+            stages = 128 * 128 * 4 * steps
             out["p%d_%s" % (p, name)] = {
                 "dof_steps_per_s": 128 * 128 * 81 * steps / (ms / 1e3), "ms_per_step": ms / steps,
                 "pcg_u_mean_iters": su["mean_iters"], "pcg_v_mean_iters": sv["mean_iters"],
-                "refine_sweeps_u": su["mean_sweeps"], "refine_sweeps_v": sv["mean_sweeps"]}
+                "refine_sweeps_u": su["mean_sweeps"], "refine_sweeps_v": sv["mean_sweeps"],
+                "roofline": alu_roofline(f64 * stages, f32 * stages, byt * stages, ms / 1e3, PROBE.get("fp64")),
+                "per_element_stage": {"fp64_flops": f64, "fp32_flops": f32, "bytes": byt}}
             ctx.close()
         b = states["fp64"]
         for name in ("mixed", "inverse"):
@@ -257,13 +373,6 @@ def forms_variable(steps=16):
     out["workload"] = ("2-D variable c^2 on the sine-mapped unit square, 128x128 elements of 8x8 cells, "
                        "Gaussian pulse, PCG rtol 1e-10, %d RK4 steps after 8 warm-up steps" % steps)
     return out
-
-
-def flops_per_element_stage_3d(n1):
-    """Algorithmic FP64 flops of one 3-D fused stage per element (FMA = 2):
-    fluxes 6 faces x n1^2 x 11, per modal entry 36 (lifts 26, diagonal solve
-    2, RK 8), traces 3 directions x 4 dots x n1^2 x 2 n1."""
-    return 66 * n1 ** 2 + 36 * n1 ** 3 + 24 * n1 ** 3
 
 
 def executed_flops_per_element_stage_3d(n1):
@@ -314,7 +423,11 @@ def forms_ocean(nx=500, ny=250, N=8, p=3, steps=16):
     E = ctx.energy(u, v)
     ctx.close()
     dof = nx * ny * (N + 1) ** 2
-    return {"workload": "ocean channel 4000 x 2000 m, c(depth), point source sin(400 pi t) at (1004 m, 300 m "
+    f64, _, byt = var_counts(N + 1, 0, 0, "inverse")
+    stages = nx * ny * 4 * steps
+    roof = alu_roofline(f64 * stages, 0.0, byt * stages, ms / 1e3, PROBE.get("fp64"))
+    return {"roofline": roof,
+            "workload": "ocean channel 4000 x 2000 m, c(depth), point source sin(400 pi t) at (1004 m, 300 m "
                         "deep), %d x %d elements of %d x %d cells, p=%d, element inverses" % (nx, ny, N, N, p),
             "dof": dof, "dof_steps_per_s": dof * steps / (ms / 1e3), "ms_per_step": ms / steps,
             "setup_s": setup_s, "dt": dt, "finite": finite, "energy_after": E}
@@ -340,14 +453,13 @@ def forms_three_d(n=32, N=8, p=5, steps=16):
     E1 = ctx.energy(u, v)
     ctx.close()
     dof = n ** 3 * (N + 1) ** 3
-    tflops = flops_per_element_stage_3d(N + 1) * n ** 3 * 4 * steps / (ms / 1e3) / 1e12
-    tflops_x = executed_flops_per_element_stage_3d(N + 1) * n ** 3 * 4 * steps / (ms / 1e3) / 1e12
+    f64 = executed_flops_per_element_stage_3d(N + 1) * n ** 3 * 4 * steps
     return {"workload": "3-D constant c^2, %d^3 elements of %d^3 cells, p=%d, upwind, Dirichlet" % (n, N, p),
             "dof": dof, "dof_steps_per_s": dof * steps / (ms / 1e3), "ms_per_step": ms / steps,
-            "fp64_tflops_whole_step": tflops, "frac_of_fp64_peak": tflops / FP64_PEAK_TFLOPS,
-            "executed_fp64_tflops_whole_step": tflops_x, "executed_frac_of_fp64_peak": tflops_x / FP64_PEAK_TFLOPS,
-            "flops_note": "fp64_tflops counts the method's flops per stage (generic modal route); the parity "
-                          "kernel executes the executed_ figure (r -> 1-r symmetry halves lifts and trace dots)",
+            "roofline": alu_roofline(f64, 0.0, 16.0 * dof * 4 * steps, ms / 1e3, PROBE.get("fp64")),
+            "flops_note": "FP64 flops the 3-D parity stage kernel executes per element and stage "
+                          "(66 n1^2 + 34 n1^3, FMA = 2) over the whole step's time (entry and exit "
+                          "transforms included); bytes: one pass of the FP64 (u, v) state per stage",
             "energy_ratio_after_20_steps": E1 / E0}
 
 
@@ -383,9 +495,25 @@ def forms_batched(steps=8):
         dts = [b[2] for b in built]
         batch = gdg.Batch([b[0] for b in built])
         batch.step(us, vs, dts, 4)
+        for i, sp in enumerate(specs):     # reset the PCG counters
+            if sp["variable"] and name != "inverse":
+                batch.stats(i)
         ms = _timed_ms(lambda: batch.step(us, vs, dts, steps))
+        f64 = f32 = byt = 0.0
+        for i, sp in enumerate(specs):
+            stages = sp["n"] ** 2 * 4 * steps
+            if sp["variable"]:
+                su, sv = batch.stats(i) if name != "inverse" else ({"mean_iters": 0, "mean_sweeps": 0},) * 2
+                a, b_, c = var_counts(9, su["mean_iters"], sv["mean_iters"], name, su["mean_sweeps"],
+                                      sv["mean_sweeps"])
+            else:
+                a, b_, c = ALG_FLOPS_PER_DOF_STAGE * 81, 0.0, 16.0 * 81
+            f64 += a * stages
+            f32 += b_ * stages
+            byt += c * stages
         out["batched_" + name] = {"dof_steps_per_s": dof * steps / (ms / 1e3), "ms_per_step": ms / steps,
-                                  "tuning": batch.tuning()}
+                                  "tuning": batch.tuning(),
+                                  "roofline": alu_roofline(f64, f32, byt, ms / 1e3, PROBE.get("fp64"))}
         batch.close()
         ctxs = [gdg.Context(b[0]) for b in built]
         for c, u, v, d in zip(ctxs, us, vs, dts):
@@ -428,7 +556,14 @@ def forms_learned(rows=20000, epochs=30, steps=16):
             ctx.step_stats()
             ms = _timed_ms(lambda: ctx.step(u, v, 0.0, dt, steps))
             su, sv = ctx.step_stats()
+            f64, f32, byt = var_counts(9, su["mean_iters"], sv["mean_iters"], name, su["mean_sweeps"],
+                                       sv["mean_sweeps"])
+            stages = 128 * 128 * 4 * steps
+            if attach:   # one forward pass per u_t solve (FP32), plus the guess's FP64 residual product
+                f32 += 2.0 * (162 * 64 + 64 * 64 + 64 * 81)
+                f64 += 2.0 * 81 * 81
             out[name + ("_learned" if attach else "_plain")] = {
+                "roofline": alu_roofline(f64 * stages, f32 * stages, byt * stages, ms / 1e3, PROBE.get("fp64")),
                 "dof_steps_per_s": 128 * 128 * 81 * steps / (ms / 1e3), "ms_per_step": ms / steps,
                 "pcg_u_mean_iters": su["mean_iters"], "pcg_u_max_iters": su["max_iters"],
                 "guess_fallbacks": su["fell_back"], "guessed": su["guessed"]}
@@ -444,17 +579,37 @@ def run_gdg(args):
     rank, world, local = _env_rank()
     if world > 1:
         import torch.distributed as dist
+        # one GPU per rank over NCCL; with fewer GPUs than ranks (a functional
+        # check of the banded path on one GPU) the ranks share GPUs and
+        # exchange through gloo, with host copies
+        ngpu = torch.cuda.device_count()
+        local = local % ngpu
         torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
+        dist.init_process_group("nccl" if ngpu >= world else "gloo")
     dev = torch.device("cuda", local if world > 1 else 0)
     torch.cuda.set_device(dev)
     w = WORKLOAD
     R = args.rk_steps
     h = 1.0 / (w["n"][0] * w["N"])
     dt = w["cfl"] * h
-    pb = gdg.make_problem(2, w["n"], w["N"], w["p"], flux=gdg.FLUX_UPWIND, c2=1.0)
-    ctx = gdg.Context(pb)
-    X, Y = inputs.cartesian_nodes(w["n"], w["N"])
+    if world == 1:
+        pb = gdg.make_problem(2, w["n"], w["N"], w["p"], flux=gdg.FLUX_UPWIND, c2=1.0)
+        ctx = gdg.Context(pb)
+        X, Y = inputs.cartesian_nodes(w["n"], w["N"])
+    else:
+        # one mesh over the GPUs: nx x (ny * world) elements on [0,1] x [0,world],
+        # a band of ny rows (the single-GPU workload's size) per rank, the
+        # face traces of the band edges exchanged (NCCL) before every stage
+        gn = (w["n"][0], w["n"][1] * world)
+        pb, (r0, r1) = shard.band_problem(gdg.make_problem, rank, world, 2, gn, w["N"], w["p"],
+                                          hi=(1.0, float(world)), flux=gdg.FLUX_UPWIND, c2=1.0)
+        ctx = gdg.Context(pb)
+        hn = ctx.halo_len()
+        mk = lambda on: torch.zeros(hn, dtype=torch.float64, device=dev) if on else None
+        halo_bufs = (mk(rank > 0), mk(rank < world - 1), mk(rank > 0), mk(rank < world - 1))
+        ctx.set_halo(*halo_bufs, shard.HaloExchange(rank, world, *halo_bufs))
+        X, Y = inputs.cartesian_nodes(w["n"], w["N"], lo=(0.0, float(r0) / w["n"][1]),
+                                      hi=(1.0, float(r1) / w["n"][1]))
     U0, V0 = inputs.standing_mode_2d(X, Y)
     u = torch.tensor(U0.ravel(), device=dev)
     v = torch.tensor(V0.ravel(), device=dev)
@@ -469,6 +624,7 @@ def run_gdg(args):
         flush.fill_(1.0)
         ctx.step(u, v, 0.0, dt, R)
     torch.cuda.synchronize()
+    PROBE["fp64"] = fp64_probe_tflops()
 
     sampler = ClockSampler(dev.index if dev.index is not None else 0)
     sampler.start()
@@ -509,7 +665,12 @@ def run_gdg(args):
     n_steps_prof = max(2, min(args.steps, 5))
     other_ms = sum(t for k, (n, t) in prof.items() if k != "stage") / n_steps_prof
     stage_ms = (ms_per_step - other_ms) / (4 * R)
-    achieved = flops_per_stage_launch() / (stage_ms / 1e3) / 1e12
+    if world > 1:
+        # the per-stage time of a banded mesh includes the halo exchanges; the
+        # stage kernel's own duration is the one measured around each launch
+        step_stage_ms, stage_ms = stage_ms, stage_ms_isolated
+    achieved = ALG_FLOPS_PER_DOF_STAGE * dof() / (stage_ms / 1e3) / 1e12
+    achieved_x = executed_flops_per_stage_launch() / (stage_ms / 1e3) / 1e12
 
     # end to end through the C ABI with host buffers (pinned), copies timed
     hu = torch.tensor(U0.ravel()).pin_memory()
@@ -526,14 +687,17 @@ def run_gdg(args):
     e2e_val = world * dof() * R * args.steps / e2e_s
 
     # accuracy of the FP64 form at T = 1: M-norm distance to the GD
-    # interpolant of the exact solution, evaluated by the library's energy kernel
-    ua = torch.tensor(U0.ravel(), device=dev)
-    va = torch.tensor(V0.ravel(), device=dev)
+    # interpolant of the exact solution, evaluated by the library's energy
+    # kernel (single mesh; the banded multi-GPU mesh is not a unit square)
     nT = int(round(w["T"] / dt))
-    ctx.step(ua, va, 0.0, dt, nT)
-    ue, _ = inputs.standing_mode_2d(X, Y, nT * dt)
-    diff = ua - torch.tensor(ue.ravel(), device=dev)
-    l2 = float(np.sqrt(2.0 * ctx.energy(torch.zeros_like(diff), diff)))
+    l2 = None
+    if world == 1:
+        ua = torch.tensor(U0.ravel(), device=dev)
+        va = torch.tensor(V0.ravel(), device=dev)
+        ctx.step(ua, va, 0.0, dt, nT)
+        ue, _ = inputs.standing_mode_2d(X, Y, nT * dt)
+        diff = ua - torch.tensor(ue.ravel(), device=dev)
+        l2 = float(np.sqrt(2.0 * ctx.energy(torch.zeros_like(diff), diff)))
 
     line = None
     if rank == 0:
@@ -555,9 +719,16 @@ def run_gdg(args):
             "config": {"workload": WORKLOAD_NAME, "elements": list(w["n"]), "N": w["N"], "p": w["p"],
                        "dof": dof(), "rk4_steps_per_step": R, "dt": dt,
                        "form": "FP64 modal (modified basis)",
+                       "parallelism": ("one GPU" if world == 1 else
+                                       "one %dx%d mesh, a %dx%d band of element rows per GPU, face traces "
+                                       "of the band edges exchanged (NCCL point to point) before every RK stage"
+                                       % (w["n"][0], w["n"][1] * world, w["n"][0], w["n"][1])),
                        "l2": "flushed between timed steps (512 MB write; state is 5.3 MB)"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                          "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                         "peak_probe": PROBE.get("fp64"),
+                         "frac_of_probe": achieved / PROBE["fp64"] if PROBE.get("fp64") else None,
+                         "flops_per_dof_stage": ALG_FLOPS_PER_DOF_STAGE,
                          "traffic": STAGE_TRAFFIC_BYTES.get(stage_variant),
                          "kernel": {1: "k_stage2h", 2: "k_stage2f", 3: "k_step2r"}.get(stage_variant, "k_stage2p")
                                    + " (fused RK4 stage, modal route; variant chosen by timing)",
@@ -570,21 +741,24 @@ def run_gdg(args):
                                              "entry/exit launches, over the 4R stages of its one persistent "
                                              "launch (per-stage figures); _isolated: events around that launch "
                                              "in a separate pass, over its 4R stages"),
-                         "flops_per_launch": flops_per_stage_launch(),
-                         "flops_per_launch_executed": executed_flops_per_stage_launch(),
-                         "frac_executed": executed_flops_per_stage_launch() / (stage_ms / 1e3) / 1e12
-                                          / FP64_PEAK_TFLOPS,
-                         "flops_note": "achieved counts the method's flops per stage (generic modal route, "
-                                       "46.9 per DOF); the parity kernels execute flops_per_launch_executed "
-                                       "(r -> 1-r symmetry halves the lifts and trace dots)",
+                         "flops_per_stage": ALG_FLOPS_PER_DOF_STAGE * dof(),
+                         "flops_per_stage_executed": executed_flops_per_stage_launch(),
+                         "achieved_executed": achieved_x,
+                         "frac_executed": achieved_x / FP64_PEAK_TFLOPS,
+                         "flops_note": "achieved: 40 algorithmic FP64 flops per DOF and stage (the modal "
+                                       "route's per-DOF count) x DOF, per stage of the timed region; "
+                                       "_executed: the flops the parity stage body performs (28.4 per DOF, "
+                                       "FMA = 2; the r -> 1-r symmetry halves the lifts and trace dots)",
                          "peak_source": "FP64 derived from unit counts and the maximum SM clock: "
-                                        "152 SM x 2070 MHz x 4 flop/clk"},
+                                        "152 SM x 2070 MHz x 4 flop/clk; peak_probe: gdg_probe_fp64 "
+                                        "(independent FMA chains) timed in this process"},
             "kernels": {k: {"launches": n, "ms": t} for k, (n, t) in prof.items()},
-            "gpu_launches": (4 * R if stage_variant != 3 else 1) * args.steps + 3 * args.steps,
+            "gpu_launches": ((4 * R if stage_variant != 3 else 1) * args.steps + 3 * args.steps
+                             + (2 * (4 * R) * args.steps if world > 1 else 0)),
             "e2e": {"value": e2e_val, "unit": "DOF-steps/s", "h2d_bytes_per_step": 2 * dof() * 8,
                     "d2h_bytes_per_step": 2 * dof() * 8},
             "clocks": clocks,
-            "accuracy": {"T": nT * dt, "l2_error_vs_interpolant": l2},
+            "accuracy": {"T": nT * dt, "l2_error_vs_interpolant": l2} if l2 is not None else None,
             "wall_s": wall1 - wall0,
             "cpu_baseline": cpu,
             "forms": forms,

@@ -43,6 +43,7 @@ extern "C" {
 #define GDG_ETIMEOUT    -5   /* a bounded device-side wait gave up                               */
 #define GDG_ENONFINITE  -6   /* NaN or Inf detected (energy, PCG residual)                       */
 #define GDG_EUNSUPPORTED -7  /* valid request this build does not provide (e.g. N+1 > 16)        */
+#define GDG_EHALO       -8   /* the caller's halo exchange function reported a failure            */
 
 /* ---- enums ----------------------------------------------------------- */
 enum { GDG_BC_DIRICHLET = 0, GDG_BC_PERIODIC = 1 };
@@ -109,6 +110,12 @@ typedef struct {
     int route;           /* GDG_ROUTE_* (diagonalised route only)                    */
     int refine_max;      /* GDG_MIXED: maximum FP64 refinement sweeps per solve      */
     double refine_rtol;  /* GDG_MIXED: inner FP32 PCG relative tolerance             */
+    int rows[2];         /* 2-D GDG_COEF_CONST: the element rows [rows[0], rows[1])  */
+                         /* of the n_elem[1]-row mesh this context owns (a band of   */
+                         /* an element-partitioned mesh, see gdg_set_halo); {0, 0}   */
+                         /* = every row.  A band that does not start at row 0 or end */
+                         /* at the last row has a halo side there; bc[1] must then  */
+                         /* be GDG_BC_DIRICHLET (it applies to the mesh's own sides) */
 } gdg_problem;
 
 typedef struct {
@@ -302,6 +309,44 @@ int gdg_residuals(gdg_ctx *ctx, const double *u, const double *v, double *ru, do
  */
 int gdg_set_point_source(gdg_ctx *ctx, int element, double r, double s, double amplitude, double omega);
 
+/* ---- element-partitioned meshes (one mesh over several contexts) ------- */
+/*
+ * Elements interact only through the fluxes of their shared faces (Section
+ * 2.2, Eqs. DG1-DG2 are element-local apart from the face terms of Section
+ * 2.2.1), so one 2-D constant-coefficient mesh can be split by rows of
+ * elements over several contexts (typically one per GPU): each context owns
+ * a contiguous band of element rows and, before every RK stage, needs the
+ * traces (v and n.grad u along the face, N+1 modal values each) of the
+ * facing row of its neighbours.  A context whose problem owns a band of
+ * rows (rows[] set, every other field as for the whole mesh, so that every
+ * band computes the same element operators) with a neighbour band below or
+ * above packs its boundary row's traces into send buffers, calls the
+ * caller's exchange function, and unpacks the neighbours' traces from the
+ * receive buffers, once at the start of gdg_step / gdg_rhs and after every
+ * stage but the last of a gdg_step call.
+ *
+ * gdg_halo_len: doubles in one side's buffer, n_elem[0] * 2 * (N+1)
+ *   (layout [ex][v | n.grad u][mode]), -1 for a context without halo sides.
+ * gdg_set_halo: register the caller-owned device buffers of both sides
+ *   (send_lo / recv_lo for the lower side, send_hi / recv_hi for the upper;
+ *   NULL for a side without a halo) and the exchange function.
+ *   fn(user, stream) is called on the host, in stream order, after the
+ *   send buffers' pack kernel has been enqueued on `stream` (the cudaStream_t
+ *   of the gdg_step / gdg_rhs call, as void*); it must make the neighbour
+ *   below's send_hi arrive in recv_lo and the neighbour above's send_lo in
+ *   recv_hi before later work on `stream` reads them (for example by
+ *   stream-ordered NCCL send / receive, or by synchronising, copying through
+ *   host memory and copying back), and return 0, or nonzero on failure
+ *   (the call then returns GDG_EHALO).  Contexts with a halo side launch
+ *   their stages directly (no CUDA graph, no persistent step: stage variant
+ *   0).  gdg_energy of such a context sums its own elements only.
+ * Errors: GDG_EINVAL (no halo side, a buffer missing for a halo side, fn NULL).
+ */
+typedef int (*gdg_halo_fn)(void *user, void *stream);
+long long gdg_halo_len(const gdg_ctx *ctx);
+int gdg_set_halo(gdg_ctx *ctx, double *send_lo, double *send_hi, double *recv_lo, double *recv_hi,
+                 gdg_halo_fn fn, void *user);
+
 /* ---- learned initial guess for the u_t solve (not in the paper) -------- */
 /*
  * A three-layer perceptron 162 -> 64 -> 64 -> 81 (tanh, tanh, linear) maps an
@@ -449,6 +494,19 @@ int gdg_rhs_static(const gdg_problem *pb, const double *u, const double *v, doub
                    void *stream);
 
 /* ---- kernel timing (measurement support; not part of the method) ------ */
+/*
+ * FP64 throughput probe: one launch, on stream, of a kernel in which every
+ * thread of a grid that fills every SM runs 8 independent chains of
+ * x <- x a + b FP64 fused multiply-adds, 4 per chain for each of `iters`
+ * iterations (no memory
+ * traffic inside the loop).  *flops (host) receives the launch's flop count
+ * (an FMA counts 2); the caller times the launch (e.g. CUDA events on the
+ * same stream) to obtain the FP64 rate the GPU sustains, the peak against
+ * which the FP64-bound kernels of this library are compared.  sink: device
+ * pointer to one double (written).  GDG_EINVAL for iters < 1 or null pointers.
+ */
+int gdg_probe_fp64(int iters, double *sink, double *flops, void *stream);
+
 /* Kernel kinds reported by gdg_profile_read. */
 enum {
     GDG_K_STAGE = 0,      /* fused RK-stage kernel (fluxes, lifts, solves, combine, traces) */

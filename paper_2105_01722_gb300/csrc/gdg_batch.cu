@@ -443,6 +443,7 @@ extern "C" int gdg_batch_create(const gdg_problem *pbs, int count, gdg_batch **o
     for (int i = 0; i < count && !st; ++i) {
         if (pbs[i].dim != 2 || pbs[i].N + 1 != b->n1) st = berr(b, GDG_EINVAL, "batch problems must be 2-D with one N");
         else if (b->n1 < 8 || b->n1 > 10) st = berr(b, GDG_EUNSUPPORTED, "batches support N = 7..9");
+        else if (pbs[i].rows[0] || pbs[i].rows[1]) st = berr(b, GDG_EUNSUPPORTED, "batch problems are whole meshes (no bands of rows)");
     }
     if (st) { gdg_batch_destroy(b); return st; }
     int dev = 0;

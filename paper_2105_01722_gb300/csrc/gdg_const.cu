@@ -26,6 +26,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <string>
 #include <vector>
 
 #include "gdg_internal.h"
@@ -245,29 +246,29 @@ __device__ __forceinline__ void s2f_update(const ModalParams &mp, const StageBuf
     double *oF = FIELD == 0 ? b.oU : b.oV;
     double *aF = FIELD == 0 ? b.aU : b.aV;
     double *nF = FIELD == 0 ? b.nU : b.nV;
-    const double *L = b.lam2 + (FIELD == 0 ? N1 * N1 : 0) + l * N1;
-    const double hy = FIELD == 0 ? mp.d[1].hgL[l] : mp.d[1].ceL[l];
+    const double *L = b.lam2 + l * N1;
+    const double *P1 = b.lam2 + 2 * N1 * N1 + l * N1, *P2 = b.lam2 + 3 * N1 * N1 + l * N1;
+    const double hy = mp.d[1].ceL[l];
     const double *F = fy + (FIELD == 0 ? 0 : 2 * N1) + (l < NE ? 0 : N1);
 #pragma unroll
     for (int k = 0; k < N1; ++k) {
         const double x = k < NE ? XA : XB;
         double kf;
         if (FIELD == 0) {
-            const double ru = fma(mp.d[0].hgL[k], x, hy * F[k]);
-            kf = fma(L[k], ru, Y[k]);
+            kf = fma(P1[k], x, fma(P2[k], F[k], Y[k]));
         } else {
             kf = fma(L[k], Y[k], fma(mp.d[0].ceL[k], x, hy * F[k]));
         }
         if (MODE == M_RHS) {
             oF[row + k] = kf;
         } else if (MODE == M_S1) {
-            aF[row + k] = cA * kf;
+            aF[row + k] = kf;
             R[k] = fma(cY, kf, R[k]);
         } else if (MODE == M_S23) {
-            aF[row + k] = fma(cA, kf, Aa[k]);
+            aF[row + k] = fma(2.0, kf, Aa[k]);
             R[k] = fma(cY, kf, Nn[k]);
         } else {
-            R[k] = fma(cA, kf, Nn[k] + Aa[k]);
+            R[k] = fma(cA, Aa[k] + kf, Nn[k]);
         }
     }
     if (MODE == M_RHS) return;
@@ -509,31 +510,30 @@ __device__ __forceinline__ void stage2r(const ModalParams &mp, const double *lam
     __syncthreads();
     if (valid) {
         const double *L0 = lam2 + l * N1;
-        const double *L1 = lam2 + N1 * N1 + l * N1;
-        const double hgy = mp.d[1].hgL[l], cey = mp.d[1].ceL[l];
+        const double *P1 = lam2 + 2 * N1 * N1 + l * N1, *P2 = lam2 + 3 * N1 * N1 + l * N1;
+        const double cey = mp.d[1].ceL[l];
         const double *FG = fy + (l < NE ? 0 : N1);
         const double *FQ = fy + (l < NE ? 2 * N1 : 3 * N1);
 #pragma unroll
         for (int k = 0; k < N1; ++k) {
             const double Yu = Ru[k], Yv = Rv[k];
             const double xg = k < NE ? GA : GB, xq = k < NE ? QA : QB;
-            const double ru = fma(mp.d[0].hgL[k], xg, hgy * FG[k]);
+            const double ku = fma(P1[k], xg, fma(P2[k], FG[k], Yv));
             const double rv = fma(L0[k], Yu, fma(mp.d[0].ceL[k], xq, cey * FQ[k]));
-            const double ku = fma(L1[k], ru, Yv);
             const double kv = rv;
             if (MODE == M_S1) {
-                Au[k] = cA * ku;
-                Av[k] = cA * kv;
+                Au[k] = ku;
+                Av[k] = kv;
                 Ru[k] = fma(cY, ku, Yu);
                 Rv[k] = fma(cY, kv, Yv);
             } else if (MODE == M_S23) {
-                Au[k] = fma(cA, ku, Au[k]);
-                Av[k] = fma(cA, kv, Av[k]);
+                Au[k] = fma(2.0, ku, Au[k]);
+                Av[k] = fma(2.0, kv, Av[k]);
                 Ru[k] = fma(cY, ku, Nu[k]);
                 Rv[k] = fma(cY, kv, Nv[k]);
             } else {
-                Ru[k] = fma(cA, ku, Nu[k] + Au[k]);
-                Rv[k] = fma(cA, kv, Nv[k] + Av[k]);
+                Ru[k] = fma(cA, Au[k] + ku, Nu[k]);
+                Rv[k] = fma(cA, Av[k] + kv, Nv[k]);
                 Nu[k] = Ru[k];
                 Nv[k] = Rv[k];
             }
@@ -1165,9 +1165,13 @@ bool persist_failed(gdg_ctx *ctx, cudaStream_t s) {
 }
 
 int set_smem_limits() {
-    // the 2-D kernels may need more than the 48 KB default of dynamic shared memory
-    static bool done = false;
-    if (done) return GDG_OK;
+    // the 2-D kernels may need more than the 48 KB default of dynamic shared
+    // memory; the attribute is per device, so it is set once on each device
+    constexpr int kDevs = 64;
+    static bool done[kDevs] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return GDG_ECUDA;
+    if (dev >= 0 && dev < kDevs && done[dev]) return GDG_OK;
     const int lim = 200 * 1024;
 #define X(n)                                                                               \
     cudaFuncSetAttribute(k_stage2<n, M_RHS>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);  \
@@ -1204,7 +1208,7 @@ int set_smem_limits() {
     GDG_N1_CASES_P(X)
 #undef X
     gdg3_set_smem_limits();
-    done = true;
+    if (dev >= 0 && dev < kDevs) done[dev] = true;
     return GDG_OK;
 }
 
@@ -1259,9 +1263,103 @@ void enqueue_rk4_step(gdg_ctx *ctx, double dt, cudaStream_t s) {
     launch_stage(ctx, M_S4, b, dt / 6.0, 0.0, s);
 }
 
+// ---------------------------------------------- partitioned meshes ------
+// One mesh split by rows of elements over several contexts.  The stage
+// kernels read a halo side's neighbour traces from a ghost row of the trace
+// buffer (element rows -1 and ny); between stages the boundary rows' y-face
+// traces go out through the caller's exchange function.  Buffer layout of a
+// side: [ex][field 0 = v, 1 = n.grad u][transverse mode].
+
+template <int N1>
+__global__ void k_halo_pack(int nx, int ny, const double *T, double *send_lo, double *send_hi) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nx * 2 * N1) return;
+    const int ex = i / (2 * N1), fld = (i / N1) % 2, m = i % N1;
+    if (send_lo) send_lo[i] = T[tix2<N1>(ex, 2, fld, m)];                      // first row, lower face
+    if (send_hi) send_hi[i] = T[tix2<N1>((ny - 1) * nx + ex, 3, fld, m)];      // last row, upper face
+}
+
+template <int N1>
+__global__ void k_halo_unpack(int nx, int ny, double *T, const double *recv_lo, const double *recv_hi) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nx * 2 * N1) return;
+    const int ex = i / (2 * N1), fld = (i / N1) % 2, m = i % N1;
+    // the row below's upper-face traces into ghost row -1, the row above's
+    // lower-face traces into ghost row ny (where the stage kernel looks)
+    if (recv_lo) T[tix2<N1>(-nx + ex, 3, fld, m)] = recv_lo[i];
+    if (recv_hi) T[tix2<N1>(ny * nx + ex, 2, fld, m)] = recv_hi[i];
+}
+
+bool has_halo(const gdg_ctx *ctx) { return ctx->mp.halo_lo || ctx->mp.halo_hi; }
+
+// traces in T -> send buffers, the caller's exchange, receive buffers -> ghost rows
+int halo_exchange(gdg_ctx *ctx, double *T, cudaStream_t s) {
+    const int n = ctx->nx * 2 * ctx->n1, threads = 256, blocks = (n + threads - 1) / threads;
+    switch (ctx->n1) {
+#define X(n_) case n_: k_halo_pack<n_><<<blocks, threads, 0, s>>>(ctx->nx, ctx->ny, T, ctx->halo_send[0], ctx->halo_send[1]); break;
+        GDG_N1_CASES(X)
+#undef X
+    }
+    int st = gdg_cuda_check(ctx, cudaGetLastError(), "halo pack");
+    if (st) return st;
+    const int rc = ctx->halo_fn(ctx->halo_user, (void *)s);
+    if (rc != 0) return gdg_set_err(ctx, GDG_EHALO, "halo exchange function returned " + std::to_string(rc));
+    switch (ctx->n1) {
+#define X(n_) case n_: k_halo_unpack<n_><<<blocks, threads, 0, s>>>(ctx->nx, ctx->ny, T, ctx->halo_recv[0], ctx->halo_recv[1]); break;
+        GDG_N1_CASES(X)
+#undef X
+    }
+    return gdg_cuda_check(ctx, cudaGetLastError(), "halo unpack");
+}
+
+// one RK4 step of a partitioned mesh: the stages of enqueue_rk4_step, each
+// followed by the exchange of the traces it wrote (except, when `last`, the
+// traces of y_{n+1}: the next gdg_step call recomputes them)
+int rk4_step_halo(gdg_ctx *ctx, double dt, bool last, cudaStream_t s) {
+    double *tr0 = ctx->d_tr, *tr1 = ctx->d_tr + ctx->tr_len;
+    StageBufs b{};
+    b.nU = buf(ctx, B_NU); b.nV = buf(ctx, B_NV);
+    b.aU = buf(ctx, B_AU); b.aV = buf(ctx, B_AV);
+    b.lam2 = ctx->d_lam2;
+    int st;
+    b.yU = b.nU; b.yV = b.nV; b.oU = buf(ctx, B_XU); b.oV = buf(ctx, B_XV); b.trin = tr0; b.trout = tr1;
+    launch_stage(ctx, M_S1, b, dt / 6.0, 0.5 * dt, s);
+    if ((st = halo_exchange(ctx, tr1, s))) return st;
+    b.yU = buf(ctx, B_XU); b.yV = buf(ctx, B_XV); b.oU = buf(ctx, B_YU); b.oV = buf(ctx, B_YV); b.trin = tr1; b.trout = tr0;
+    launch_stage(ctx, M_S23, b, dt / 3.0, 0.5 * dt, s);
+    if ((st = halo_exchange(ctx, tr0, s))) return st;
+    b.yU = buf(ctx, B_YU); b.yV = buf(ctx, B_YV); b.oU = buf(ctx, B_XU); b.oV = buf(ctx, B_XV); b.trin = tr0; b.trout = tr1;
+    launch_stage(ctx, M_S23, b, dt / 3.0, dt, s);
+    if ((st = halo_exchange(ctx, tr1, s))) return st;
+    b.yU = buf(ctx, B_XU); b.yV = buf(ctx, B_XV); b.oU = nullptr; b.oV = nullptr; b.trin = tr1; b.trout = tr0;
+    launch_stage(ctx, M_S4, b, dt / 6.0, 0.0, s);
+    return last ? GDG_OK : halo_exchange(ctx, tr0, s);
+}
+
 }  // namespace
 
 // ------------------------------------------------------------- API -------
+
+extern "C" long long gdg_halo_len(const gdg_ctx *ctx) {
+    if (!ctx || ctx->var || !has_halo(ctx)) return -1;
+    return (long long)ctx->nx * 2 * ctx->n1;
+}
+
+extern "C" int gdg_set_halo(gdg_ctx *ctx, double *send_lo, double *send_hi, double *recv_lo, double *recv_hi,
+                            gdg_halo_fn fn, void *user) {
+    if (!ctx || ctx->var || !has_halo(ctx) || !fn) return GDG_EINVAL;
+    if (ctx->mp.halo_lo && (!send_lo || !recv_lo))
+        return gdg_set_err(ctx, GDG_EINVAL, "gdg_set_halo: the lower side needs send_lo and recv_lo");
+    if (ctx->mp.halo_hi && (!send_hi || !recv_hi))
+        return gdg_set_err(ctx, GDG_EINVAL, "gdg_set_halo: the upper side needs send_hi and recv_hi");
+    ctx->halo_send[0] = ctx->mp.halo_lo ? send_lo : nullptr;
+    ctx->halo_recv[0] = ctx->mp.halo_lo ? recv_lo : nullptr;
+    ctx->halo_send[1] = ctx->mp.halo_hi ? send_hi : nullptr;
+    ctx->halo_recv[1] = ctx->mp.halo_hi ? recv_hi : nullptr;
+    ctx->halo_fn = fn;
+    ctx->halo_user = user;
+    return GDG_OK;
+}
 
 int gdg_const_setup(gdg_ctx *ctx) {
     const int n1 = ctx->n1, nn = n1 * n1;
@@ -1273,6 +1371,10 @@ int gdg_const_setup(gdg_ctx *ctx) {
     mp.ne = ctx->ne;
     mp.per_x = ctx->pb.bc[0] == GDG_BC_PERIODIC;
     mp.per_y = ctx->dim >= 2 && ctx->pb.bc[1] == GDG_BC_PERIODIC;
+    // a band of rows of a larger mesh has a halo side where a neighbour band lies
+    const bool band = ctx->dim == 2 && (ctx->pb.rows[0] || ctx->pb.rows[1]);
+    mp.halo_lo = band && ctx->pb.rows[0] > 0;
+    mp.halo_hi = band && ctx->pb.rows[1] < ctx->pb.n_elem[1];
     mp.per_z = ctx->dim == 3 && ctx->pb.bc[2] == GDG_BC_PERIODIC;
     mp.c2 = ctx->pb.c2;
     if (ctx->pb.flux == GDG_FLUX_UPWIND) {
@@ -1350,27 +1452,48 @@ int gdg_const_setup(gdg_ctx *ctx) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
     mp.epb = ctx->dim == 2 ? choose_epb(ctx->ne, n1, sms, n1) : 1;
     mp.epbh = ctx->dim == 2 ? choose_epb(ctx->ne, n1, sms, 2 * n1) : 1;
-    mp.split = 0;   // decided by timing at the first gdg_step
+    mp.split = 0;   // decided by timing at the first gdg_step (one-line kernel on partitioned meshes)
     const int ents = ctx->dim == 3 ? nn * n1 : (ctx->dim == 2 ? nn : n1);
-    std::vector<double> l2((size_t)2 * ents, 0.0);
+    // rows: -c^2 lambda, 1/lambda (0 on the constant mode); 2-D also the u
+    // lifts folded with the diagonal solve, P1 = hgL_x[k]/lambda, P2 =
+    // hgL_y[l]/lambda (m = l n1 + k), which the parity stage kernels apply
+    std::vector<double> l2((size_t)(ctx->dim == 2 ? 4 : 2) * ents, 0.0);
     for (int m = 0; m < ents; ++m) {
         double L = ctx->dim == 3   ? lam[0][m % n1] + lam[1][(m / n1) % n1] + lam[2][m / nn]
                    : ctx->dim == 2 ? lam[0][m % n1] + lam[1][m / n1]
                                    : lam[0][m];
         l2[m] = -ctx->pb.c2 * L;
         l2[ents + m] = m == 0 ? 0.0 : 1.0 / L;
+        if (ctx->dim == 2) {
+            l2[2 * ents + m] = l2[ents + m] * mp.d[0].hgL[m % n1];
+            l2[3 * ents + m] = l2[ents + m] * mp.d[1].hgL[m / n1];
+        }
     }
     ctx->tr_len = (long long)ctx->ne * (ctx->dim == 3 ? 12 * nn : (ctx->dim == 2 ? 8 * n1 : 4));
+    // a partitioned mesh keeps one ghost row of element traces below and
+    // above its own rows (filled from the neighbours' exchanged traces)
+    const long long ghost = (mp.halo_lo || mp.halo_hi) ? (long long)ctx->nx * 8 * n1 : 0;
+    ctx->tr_len += 2 * ghost;
     ctx->red_len = 1024;
     int st;
     if ((st = gdg_cuda_check(ctx, cudaMalloc((void **)&ctx->d_mats, tables.size() * sizeof(double)), "alloc")) ||
         (st = gdg_cuda_check(ctx, cudaMalloc((void **)&ctx->d_lam2, l2.size() * sizeof(double)), "alloc")) ||
         (st = gdg_cuda_check(ctx, cudaMalloc((void **)&ctx->d_state, (size_t)B_COUNT * ctx->ndof * sizeof(double)), "alloc")) ||
-        (st = gdg_cuda_check(ctx, cudaMalloc((void **)&ctx->d_tr, (size_t)2 * ctx->tr_len * sizeof(double)), "alloc")) ||
+        (st = gdg_cuda_check(ctx, cudaMalloc((void **)&ctx->d_tr_alloc, (size_t)2 * ctx->tr_len * sizeof(double)), "alloc")) ||
         (st = gdg_cuda_check(ctx, cudaMalloc((void **)&ctx->d_red, (size_t)(ctx->red_len + 1) * sizeof(double)), "alloc")) ||
         (st = gdg_cuda_check(ctx, cudaMallocHost((void **)&ctx->h_red, 8 * sizeof(double)), "alloc")) ||
         (ctx->dim == 2 && (st = gdg_cuda_check(ctx, cudaMalloc((void **)&ctx->d_sync, sync_words(ctx->ne) * sizeof(unsigned)), "alloc"))))
         return st;
+    if (ghost && !mp.parity)
+        return gdg_set_err(ctx, GDG_EUNSUPPORTED, "partitioned meshes need the parity stage kernel (clean even/odd modes)");
+    ctx->d_tr = ctx->d_tr_alloc + ghost;
+    if (ghost &&
+        (st = gdg_cuda_check(ctx, cudaMemset(ctx->d_tr_alloc, 0, (size_t)2 * ctx->tr_len * sizeof(double)), "clear traces")))
+        return st;
+    if (ghost) {   // partitioned meshes run the one-line stage kernel, stage by stage
+        mp.split = 0;
+        ctx->stage_tuned = true;
+    }
     if ((st = gdg_cuda_check(ctx, cudaMemcpy(ctx->d_mats, tables.data(), tables.size() * sizeof(double), cudaMemcpyHostToDevice), "upload")) ||
         (st = gdg_cuda_check(ctx, cudaMemcpy(ctx->d_lam2, l2.data(), l2.size() * sizeof(double), cudaMemcpyHostToDevice), "upload")))
         return st;
@@ -1384,13 +1507,13 @@ void gdg_const_free(gdg_ctx *ctx) {
     cudaFree(ctx->d_mats);
     cudaFree(ctx->d_lam2);
     cudaFree(ctx->d_state);
-    cudaFree(ctx->d_tr);
+    cudaFree(ctx->d_tr_alloc);
     cudaFree(ctx->d_red);
     cudaFree(ctx->d_sync);
     ctx->d_sync = nullptr;
     if (ctx->h_red) cudaFreeHost(ctx->h_red);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
-    ctx->d_mats = ctx->d_lam2 = ctx->d_state = ctx->d_tr = ctx->d_red = ctx->h_red = nullptr;
+    ctx->d_mats = ctx->d_lam2 = ctx->d_state = ctx->d_tr = ctx->d_tr_alloc = ctx->d_red = ctx->h_red = nullptr;
     ctx->cap_stream = nullptr;
 }
 
@@ -1398,6 +1521,11 @@ int gdg_const_rhs(gdg_ctx *ctx, const double *u, const double *v, double *du, do
     // modal state of (u, v), its traces, k = f(Y) in modal form, back to nodal
     launch_sep(ctx, u, v, buf(ctx, B_XU), buf(ctx, B_XV), T_P, nullptr, -1, s);
     launch_traces(ctx, buf(ctx, B_XU), buf(ctx, B_XV), ctx->d_tr, s);
+    if (has_halo(ctx)) {
+        if (!ctx->halo_fn) return gdg_set_err(ctx, GDG_EINVAL, "gdg_rhs: halo sides need gdg_set_halo first");
+        const int st = halo_exchange(ctx, ctx->d_tr, s);
+        if (st) return st;
+    }
     StageBufs b{};
     b.yU = buf(ctx, B_XU); b.yV = buf(ctx, B_XV);
     b.oU = buf(ctx, B_KU); b.oV = buf(ctx, B_KV);
@@ -1485,6 +1613,8 @@ extern "C" int gdg_set_wait_limit(gdg_ctx *ctx, double seconds) {
 
 extern "C" int gdg_set_stage_variant(gdg_ctx *ctx, int variant) {
     if (!ctx || ctx->var || ctx->dim != 2 || !ctx->mp.parity || variant < -1 || variant > 3) return GDG_EINVAL;
+    if (has_halo(ctx) && variant != 0)
+        return gdg_set_err(ctx, GDG_EUNSUPPORTED, "partitioned meshes run the one-line stage kernel (variant 0)");
     if (variant == 3 && !persist_fits(ctx))
         return gdg_set_err(ctx, GDG_EUNSUPPORTED, "persistent step: the grid does not fit the GPU at once");
     if (ctx->graph.exec) {
@@ -1507,6 +1637,14 @@ int gdg_const_step(gdg_ctx *ctx, double *u, double *v, double dt, int nsteps, cu
     launch_sep(ctx, u, v, buf(ctx, B_NU), buf(ctx, B_NV), T_P, nullptr, -1, s);
     launch_traces(ctx, buf(ctx, B_NU), buf(ctx, B_NV), ctx->d_tr, s);
     if ((st = gdg_cuda_check(ctx, cudaGetLastError(), "gdg_step prologue"))) return st;
+    if (has_halo(ctx)) {   // partitioned mesh: stages launched one by one, exchanges between them
+        if (!ctx->halo_fn) return gdg_set_err(ctx, GDG_EINVAL, "gdg_step: halo sides need gdg_set_halo first");
+        if ((st = halo_exchange(ctx, ctx->d_tr, s))) return st;
+        for (int i = 0; i < nsteps; ++i)
+            if ((st = rk4_step_halo(ctx, dt, i + 1 == nsteps, s))) return st;
+        launch_sep(ctx, buf(ctx, B_NU), buf(ctx, B_NV), u, v, T_PSI, nullptr, -1, s);
+        return gdg_cuda_check(ctx, cudaGetLastError(), "gdg_step (partitioned mesh)");
+    }
     if (!ctx->stage_tuned && (st = tune_stage_kernel(ctx, dt, s, u, v))) return st;
     if (ctx->dim == 2 && ctx->mp.parity && ctx->mp.split == 3) {
         if (nsteps > 0) launch_persist(ctx, dt, nsteps, s);
@@ -1605,6 +1743,19 @@ static __device__ __align__(256) double g_rhs_scratch[kStaticScratchDoubles];
 
 constexpr int kMaxDevices = 64;
 double *g_rhs_scratch_addr[kMaxDevices];   // device address of g_rhs_scratch, per device
+
+// Host-built tables of one gdg_rhs_static call, passed by value as a kernel
+// parameter (6 n1^2 + 2 n1^2 doubles at n1 = 16: 16 KB, within the 32 KB
+// parameter limit) and written into the static array by k_put_tables.
+struct StaticTables {
+    double v[8 * GDG_MAXN1 * GDG_MAXN1];
+};
+static_assert(sizeof(StaticTables) <= 16384, "parameter block");
+
+__global__ void k_put_tables(const __grid_constant__ StaticTables t, int n, double *dst) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = t.v[i];
+}
 
 // Gauss-Legendre on [0,1], fixed-size arrays (Newton on the Legendre recurrence)
 void gl_fixed(int n, double *x, double *w) {
@@ -1763,9 +1914,11 @@ extern "C" int gdg_rhs_static(const gdg_problem *pb, const double *u, const doub
     if (du == u || du == v || dv == u || dv == v) return GDG_EINVAL;
     if (pb->dim != 1 && pb->dim != 2) return GDG_EINVAL;
     if (pb->coef != GDG_COEF_CONST || !(pb->c2 > 0.0)) return GDG_EINVAL;
+    if (pb->rows[0] || pb->rows[1]) return GDG_EUNSUPPORTED;   // whole meshes only
     if (pb->p < 1 || pb->p % 2 == 0 || pb->N < pb->p) return GDG_EINVAL;
     if (pb->N + 1 > GDG_MAXN1) return GDG_EUNSUPPORTED;
-    if (pb->flux != GDG_FLUX_CENTRAL && pb->flux != GDG_FLUX_UPWIND) return GDG_EINVAL;
+    if (pb->flux != GDG_FLUX_CENTRAL && pb->flux != GDG_FLUX_UPWIND && pb->flux != GDG_FLUX_ALTERNATING)
+        return GDG_EINVAL;
     for (int d = 0; d < pb->dim; ++d) {
         if (pb->n_elem[d] < 1 || !(pb->hi[d] > pb->lo[d])) return GDG_EINVAL;
         if (pb->bc[d] != GDG_BC_DIRICHLET && pb->bc[d] != GDG_BC_PERIODIC) return GDG_EINVAL;
@@ -1859,8 +2012,11 @@ extern "C" int gdg_rhs_static(const gdg_problem *pb, const double *u, const doub
         l2[ents + m] = m == 0 ? 0.0 : 1.0 / Lm;
     }
     cudaStream_t s = (cudaStream_t)stream;
-    if (cudaMemcpyAsync(base, tab, (size_t)ntab * sizeof(double), cudaMemcpyHostToDevice, s) != cudaSuccess)
-        return GDG_ECUDA;
+    // the tables travel by value in the launch's parameter block (16 KB at
+    // most): no copy from host memory, so the call never waits for the host
+    StaticTables st;
+    std::memcpy(st.v, tab, (size_t)ntab * sizeof(double));
+    k_put_tables<<<(unsigned)((ntab + 255) / 256), 256, 0, s>>>(st, (int)ntab, base);
 
     // a context on the stack holding only what the launch helpers read
     gdg_ctx c;

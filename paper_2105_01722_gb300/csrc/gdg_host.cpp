@@ -31,6 +31,7 @@ extern "C" const char *gdg_status_string(int s) {
     case GDG_ETIMEOUT: return "bounded device wait timed out";
     case GDG_ENONFINITE: return "non-finite value";
     case GDG_EUNSUPPORTED: return "unsupported configuration";
+    case GDG_EHALO: return "halo exchange function failed";
     default: return "unknown status";
     }
 }
@@ -391,6 +392,21 @@ static int validate(const gdg_problem *pb, std::string &why) {
         return GDG_EINVAL;
     }
     if (pb->precision != GDG_FP64 && pb->precision != GDG_MIXED) { why = "bad precision"; return GDG_EINVAL; }
+    if (pb->rows[0] || pb->rows[1]) {
+        if (pb->dim != 2 || pb->coef != GDG_COEF_CONST) {
+            why = "bands of rows (partitioned meshes): 2-D GDG_COEF_CONST only";
+            return GDG_EUNSUPPORTED;
+        }
+        if (pb->rows[0] < 0 || pb->rows[1] <= pb->rows[0] || pb->rows[1] > pb->n_elem[1]) {
+            why = "rows must satisfy 0 <= rows[0] < rows[1] <= n_elem[1]";
+            return GDG_EINVAL;
+        }
+        const bool partial = pb->rows[0] > 0 || pb->rows[1] < pb->n_elem[1];
+        if (partial && pb->bc[1] != GDG_BC_DIRICHLET) {
+            why = "a band of rows needs bc[1] = GDG_BC_DIRICHLET (a periodic y direction is not split)";
+            return GDG_EINVAL;
+        }
+    }
     return GDG_OK;
 }
 
@@ -410,6 +426,7 @@ extern "C" int gdg_create(const gdg_problem *pb, gdg_ctx **out) {
     ctx->dim = pb->dim;
     ctx->nx = pb->n_elem[0];
     ctx->ny = pb->dim >= 2 ? pb->n_elem[1] : 1;
+    if (pb->dim == 2 && (pb->rows[0] || pb->rows[1])) ctx->ny = pb->rows[1] - pb->rows[0];   // a band of rows
     ctx->nz = pb->dim == 3 ? pb->n_elem[2] : 1;
     ctx->N = pb->N;
     ctx->n1 = pb->N + 1;

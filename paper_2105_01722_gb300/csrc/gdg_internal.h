@@ -36,6 +36,7 @@ struct ModalParams {
     int split;            // parity stage kernel: 0 one line, 1 half line, 2 field split, 3 persistent step
                           // (chosen by timing)
     int epbp;             // elements per block of the persistent step (0: its grid does not fit)
+    int halo_lo, halo_hi; // y sides whose neighbour traces arrive in ghost rows (partitioned mesh)
 };
 
 // RK4 stage modes of the stage kernels
@@ -54,7 +55,7 @@ struct StageBufs {
     double *oU, *oV;         // next stage input, or k (M_RHS)
     const double *trin;      // traces of the stage input
     double *trout;           // traces of the next stage input
-    const double *lam2;      // [2][n1^d] : -c2 * lambda, 1/lambda (0 on mode 0)
+    const double *lam2;      // [2][n1^d] : -c2 * lambda, 1/lambda (0 on mode 0); 2-D: [4][n1^2]
 };
 
 // 3-D modal-route launches (gdg_const3.cu), n1 = N+1 in 2..10
@@ -100,10 +101,16 @@ struct gdg_ctx {
     // constant-coefficient Cartesian (diagonalised route)
     ModalParams mp{};
     double *d_mats = nullptr;     // device tables: per direction P = Psi^T M, Psi, Psi^T (n1*n1 each)
-    double *d_lam2 = nullptr;     // [n1*n1] 2-D: -c2*(lx+ly) and 1/(lx+ly) (0 for mode 0) tables
+    double *d_lam2 = nullptr;     // per mode: -c2*lambda, 1/lambda (0 for mode 0); 2-D also P1, P2
+                                  // (the u lifts over lambda, see stage2p_body)
     double *d_state = nullptr;    // modal work: yn(2 fields), acc(2), YA(2), YB(2), K(2)
-    double *d_tr = nullptr;       // two trace buffers
-    long long tr_len = 0;         // doubles per trace buffer
+    double *d_tr = nullptr;       // two trace buffers (past the lower ghost row when halo sides exist)
+    long long tr_len = 0;         // doubles per trace buffer (ghost rows included)
+    double *d_tr_alloc = nullptr; // allocation holding d_tr
+    // element-partitioned mesh: caller's exchange buffers and function
+    double *halo_send[2] = {nullptr, nullptr}, *halo_recv[2] = {nullptr, nullptr};
+    gdg_halo_fn halo_fn = nullptr;
+    void *halo_user = nullptr;
     double *d_red = nullptr;      // reduction partials
     int red_len = 0;
     double *h_red = nullptr;      // pinned host scalar(s)

@@ -9,9 +9,10 @@ namespace {
 
 
 // trace buffer index: 2-D [e][face 0..3 = xm,xp,ym,yp][field 0 = v, 1 = n.grad u][N1]
+// (signed: on a partitioned mesh the ghost row below the first row has e < 0)
 template <int N1>
-__device__ __forceinline__ size_t tix2(int e, int face, int fld, int i) {
-    return (((size_t)e * 4 + face) * 2 + fld) * N1 + i;
+__device__ __forceinline__ long long tix2(int e, int face, int fld, int i) {
+    return (((long long)e * 4 + face) * 2 + fld) * N1 + i;
 }
 // 1-D: [e][face 0..1][field]
 __device__ __forceinline__ size_t tix1(int e, int face, int fld) {
@@ -59,6 +60,12 @@ __device__ __forceinline__ void flux2(double vi, double di, double vo, double dO
 // q2 = 2 q*) that is folded into the lift vectors hgL = gL/2, ceL = c^2 eL/2.
 // ALT: the flux kind as a compile-time constant (1 alternating, 0 central or
 // upwind; must equal mp.alt), so the per-face choice costs nothing.
+// The u lifts enter only through k_u = V + Lambda^+ r_u, so they are folded
+// with the diagonal solve: P1[l][k] = hgL_x[k] / lambda[l][k] and
+// P2[l][k] = hgL_y[l] / lambda[l][k] (lam2 rows 2 and 3; 0 on the constant
+// mode), two FMAs per entry.  RK4 accumulates k1 + 2 k2 + 2 k3 (stages 1-3
+// ignore cA) and stage 4 forms y_n + cA (acc + k4) with cA = dt/6, the
+// order of the classic formula y_n + dt/6 (k1 + 2 k2 + 2 k3 + k4).
 template <int N1, int MODE, int ALT>
 __device__ __forceinline__ void stage2p_body(const ModalParams &mp, const StageBufs &b, double cA, double cY,
                                              int etile, double *smem) {
@@ -114,18 +121,19 @@ __device__ __forceinline__ void stage2p_body(const ModalParams &mp, const StageB
         else { vo = -vi; dO = -di; }
         flux2(vi, di, vo, dO, b2, t2, ALT, 1, bnd, g2p, q2p);
         GA = g2m + g2p; GB = g2m - g2p; QA = q2m + q2p; QB = q2m - q2p;
-        // y faces, transverse mode k = l
+        // y faces, transverse mode k = l (on a halo side the neighbour row's
+        // traces sit in the ghost row en = -1 or en = ny of the trace buffer)
         vi = T[tix2<N1>(e, 2, 0, l)]; di = T[tix2<N1>(e, 2, 1, l)];
         en = ey - 1;
         if (en < 0 && mp.per_y) en += ny;
-        bnd = en < 0;
+        bnd = en < 0 && !mp.halo_lo;
         if (!bnd) { f = en * nx + ex; vo = T[tix2<N1>(f, 3, 0, l)]; dO = T[tix2<N1>(f, 3, 1, l)]; }
         else { vo = -vi; dO = -di; }
         flux2(vi, di, vo, dO, b2, t2, ALT, 0, bnd, g2m, q2m);
         vi = T[tix2<N1>(e, 3, 0, l)]; di = T[tix2<N1>(e, 3, 1, l)];
         en = ey + 1;
         if (en >= ny && mp.per_y) en -= ny;
-        bnd = en >= ny;
+        bnd = en >= ny && !mp.halo_hi;
         if (!bnd) { f = en * nx + ex; vo = T[tix2<N1>(f, 2, 0, l)]; dO = T[tix2<N1>(f, 2, 1, l)]; }
         else { vo = -vi; dO = -di; }
         flux2(vi, di, vo, dO, b2, t2, ALT, 1, bnd, g2p, q2p);
@@ -136,34 +144,34 @@ __device__ __forceinline__ void stage2p_body(const ModalParams &mp, const StageB
 
     if (valid) {
         const double *L0 = b.lam2 + l * N1;
-        const double *L1 = b.lam2 + N1 * N1 + l * N1;
-        const double hgy = mp.d[1].hgL[l], cey = mp.d[1].ceL[l];
+        const double *P1 = b.lam2 + 2 * N1 * N1 + l * N1, *P2 = b.lam2 + 3 * N1 * N1 + l * N1;
+        const double cey = mp.d[1].ceL[l];
         const double *FG = fy + (l < NE ? 0 : N1);
         const double *FQ = fy + (l < NE ? 2 * N1 : 3 * N1);
 #pragma unroll
         for (int k = 0; k < N1; ++k) {
             const double Yu = Ru[k], Yv = Rv[k];
             const double xg = k < NE ? GA : GB, xq = k < NE ? QA : QB;
-            const double ru = fma(mp.d[0].hgL[k], xg, hgy * FG[k]);
+            // k_u = V + Lambda^+ r_u with the rank-one lifts folded into P1, P2
+            const double ku = fma(P1[k], xg, fma(P2[k], FG[k], Yv));
             const double rv = fma(L0[k], Yu, fma(mp.d[0].ceL[k], xq, cey * FQ[k]));
-            const double ku = fma(L1[k], ru, Yv);
             const double kv = rv;
             if (MODE == M_RHS) {
                 b.oU[row + k] = ku;
                 b.oV[row + k] = kv;
-            } else if (MODE == M_S1) {
-                b.aU[row + k] = cA * ku;
-                b.aV[row + k] = cA * kv;
+            } else if (MODE == M_S1) {   // accumulator k1 + 2 k2 + 2 k3, scaled by dt/6 at stage 4
+                b.aU[row + k] = ku;
+                b.aV[row + k] = kv;
                 Ru[k] = fma(cY, ku, Yu);
                 Rv[k] = fma(cY, kv, Yv);
             } else if (MODE == M_S23) {
-                b.aU[row + k] = fma(cA, ku, Au[k]);
-                b.aV[row + k] = fma(cA, kv, Av[k]);
+                b.aU[row + k] = fma(2.0, ku, Au[k]);
+                b.aV[row + k] = fma(2.0, kv, Av[k]);
                 Ru[k] = fma(cY, ku, Nu[k]);
                 Rv[k] = fma(cY, kv, Nv[k]);
             } else {
-                Ru[k] = fma(cA, ku, Nu[k] + Au[k]);
-                Rv[k] = fma(cA, kv, Nv[k] + Av[k]);
+                Ru[k] = fma(cA, Au[k] + ku, Nu[k]);
+                Rv[k] = fma(cA, Av[k] + kv, Nv[k]);
             }
         }
         if (MODE != M_RHS) {
@@ -311,36 +319,35 @@ __device__ __forceinline__ void stage2h_body(const ModalParams &mp, const StageB
 
     if (valid) {
         const double *L0 = b.lam2 + l * N1 + k0;
-        const double *L1 = b.lam2 + N1 * N1 + l * N1 + k0;
-        const double hgy = mp.d[1].hgL[l], cey = mp.d[1].ceL[l];
+        const double *P1 = b.lam2 + 2 * N1 * N1 + l * N1 + k0, *P2 = b.lam2 + 3 * N1 * N1 + l * N1 + k0;
+        const double cey = mp.d[1].ceL[l];
         const double *FG = fy + (l < NE ? 0 : N1) + k0;
         const double *FQ = fy + (l < NE ? 2 * N1 : 3 * N1) + k0;
-        const double *hgx = mp.d[0].hgL + k0, *cex = mp.d[0].ceL + k0;
+        const double *cex = mp.d[0].ceL + k0;
 #pragma unroll
         for (int kk = 0; kk < NE; ++kk) {
             if (kk < nk) {
                 const double Yu = Ru[kk], Yv = Rv[kk];
-                const double ru = fma(hgx[kk], xg, hgy * FG[kk]);
+                const double ku = fma(P1[kk], xg, fma(P2[kk], FG[kk], Yv));
                 const double rv = fma(L0[kk], Yu, fma(cex[kk], xq, cey * FQ[kk]));
-                const double ku = fma(L1[kk], ru, Yv);
                 const double kv = rv;
                 const size_t o = row + kk;
                 if (MODE == M_RHS) {
                     b.oU[o] = ku;
                     b.oV[o] = kv;
                 } else if (MODE == M_S1) {
-                    b.aU[o] = cA * ku;
-                    b.aV[o] = cA * kv;
+                    b.aU[o] = ku;
+                    b.aV[o] = kv;
                     Ru[kk] = fma(cY, ku, Yu);
                     Rv[kk] = fma(cY, kv, Yv);
                 } else if (MODE == M_S23) {
-                    b.aU[o] = fma(cA, ku, Au[kk]);
-                    b.aV[o] = fma(cA, kv, Av[kk]);
+                    b.aU[o] = fma(2.0, ku, Au[kk]);
+                    b.aV[o] = fma(2.0, kv, Av[kk]);
                     Ru[kk] = fma(cY, ku, Nu[kk]);
                     Rv[kk] = fma(cY, kv, Nv[kk]);
                 } else {
-                    Ru[kk] = fma(cA, ku, Nu[kk] + Au[kk]);
-                    Rv[kk] = fma(cA, kv, Nv[kk] + Av[kk]);
+                    Ru[kk] = fma(cA, Au[kk] + ku, Nu[kk]);
+                    Rv[kk] = fma(cA, Av[kk] + kv, Nv[kk]);
                 }
             }
         }

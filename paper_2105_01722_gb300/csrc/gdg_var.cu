@@ -581,6 +581,9 @@ extern "C" int gdg_set_point_source(gdg_ctx *ctx, int element, double r, double 
         !std::isfinite(amplitude) || !std::isfinite(omega))
         return gdg_set_err(ctx, GDG_EINVAL, "point source: element index, (r, s) in [0,1]^2, finite amplitude and omega");
     VarData &D = *ctx->var;
+    // work still running on any stream may read the source buffer and the
+    // parameters about to change: wait for it first, as the header states
+    if ((st = gdg_cuda_check(ctx, cudaDeviceSynchronize(), "point source: synchronise"))) return st;
     drop_graph(ctx);   // the source is a kernel parameter of the captured launches
     if (amplitude == 0.0) {
         D.vp.src_e = -1;

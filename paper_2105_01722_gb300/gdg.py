@@ -12,7 +12,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libgdg.so")
 
-OK, EINVAL, ENOMEM, ECUDA, ENOCONV, ETIMEOUT, ENONFINITE, EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6, -7
+OK, EINVAL, ENOMEM, ECUDA, ENOCONV, ETIMEOUT, ENONFINITE, EUNSUPPORTED, EHALO = 0, -1, -2, -3, -4, -5, -6, -7, -8
 BC_DIRICHLET, BC_PERIODIC = 0, 1
 FLUX_CENTRAL, FLUX_UPWIND, FLUX_ALTERNATING = 0, 1, 2
 COEF_CONST, COEF_NODAL = 0, 1
@@ -33,7 +33,7 @@ class Problem(ctypes.Structure):
         ("x_nodes", _dp), ("y_nodes", _dp), ("c2_nodes", _dp), ("nquad", ctypes.c_int),
         ("solver", ctypes.c_int), ("precond", ctypes.c_int), ("pcg_rtol", ctypes.c_double),
         ("pcg_maxit", ctypes.c_int), ("precision", ctypes.c_int), ("route", ctypes.c_int),
-        ("refine_max", ctypes.c_int), ("refine_rtol", ctypes.c_double),
+        ("refine_max", ctypes.c_int), ("refine_rtol", ctypes.c_double), ("rows", ctypes.c_int * 2),
     ]
 
 
@@ -45,6 +45,9 @@ class PcgStats(ctypes.Structure):
 
 
 _LIB = None
+
+# int (*gdg_halo_fn)(void *user, void *stream)
+HALO_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p)
 
 EXPORTS = {
     "gdg_status_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -93,6 +96,10 @@ EXPORTS = {
                                             ctypes.c_double, ctypes.c_double]),
     "gdg_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
                                         ctypes.POINTER(ctypes.c_double)]),
+    "gdg_probe_fp64": (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                      ctypes.c_void_p]),
+    "gdg_halo_len": (ctypes.c_longlong, [ctypes.c_void_p]),
+    "gdg_set_halo": (ctypes.c_int, [ctypes.c_void_p] * 5 + [HALO_FN, ctypes.c_void_p]),
 }
 
 K_STAGE, K_TRACES, K_TRANSFORM, K_RHS, K_PCG, K_OTHER = range(6)
@@ -137,7 +144,7 @@ def basis_1d(p, N):
 def make_problem(dim, n, N, p, lo=(0.0, 0.0), hi=(1.0, 1.0), bc=(BC_DIRICHLET, BC_DIRICHLET),
                  flux=FLUX_UPWIND, xi=0.0, c2=1.0, coef=COEF_CONST, x_nodes=None, y_nodes=None,
                  c2_nodes=None, nquad=0, solver=None, precond=PC_FDM, pcg_rtol=1e-10, pcg_maxit=200,
-                 precision=FP64, route=ROUTE_MODAL, refine_max=8, refine_rtol=1e-5):
+                 precision=FP64, route=ROUTE_MODAL, refine_max=8, refine_rtol=1e-5, rows=(0, 0)):
     pb = Problem()
     pb.dim = dim
     n = tuple(n) + (1,) * (3 - len(n))
@@ -159,6 +166,7 @@ def make_problem(dim, n, N, p, lo=(0.0, 0.0), hi=(1.0, 1.0), bc=(BC_DIRICHLET, B
     pb.precond, pb.pcg_rtol, pb.pcg_maxit = precond, pcg_rtol, pcg_maxit
     pb.precision, pb.route = precision, route
     pb.refine_max, pb.refine_rtol = refine_max, refine_rtol
+    pb.rows[0], pb.rows[1] = int(rows[0]), int(rows[1])
     pb._keep = keep   # host arrays must outlive gdg_create
     return pb
 
@@ -198,10 +206,23 @@ def _stream(stream=None):
     return ctypes.c_void_p(s.cuda_stream)
 
 
+def probe_fp64(iters, sink, stream=None):
+    """gdg_probe_fp64: launch the FP64 FMA-chain probe on `stream` (sink: a
+    float64 CUDA tensor of at least one element); returns the launch's flop
+    count.  Time it with CUDA events on the same stream."""
+    flops = ctypes.c_double()
+    st = lib().gdg_probe_fp64(int(iters), _ptr(sink[:1]), ctypes.byref(flops), _stream(stream))
+    if st != OK:
+        raise GdgError(st, "gdg_probe_fp64")
+    return flops.value
+
+
 def rhs_static(problem, u, v, du, dv, stream=None):
     """gdg_rhs_static: the constant-coefficient right-hand side without any
     allocation (no context; scratch in the library's static device array)."""
-    n = len(u)
+    n = (problem.N + 1) ** problem.dim
+    for d in range(problem.dim):
+        n *= problem.n_elem[d]
     st = lib().gdg_rhs_static(ctypes.byref(problem), _ptr(u, n), _ptr(v, n), _ptr(du, n), _ptr(dv, n),
                               _stream(stream))
     if st != OK:
@@ -251,6 +272,31 @@ class Context:
         return dict(max_iters=stats.max_iters, mean_iters=stats.mean_iters,
                     max_rel_resid=stats.max_rel_resid, unconverged=stats.unconverged,
                     max_sweeps=stats.max_sweeps, mean_sweeps=stats.mean_sweeps, status=st)
+
+    def halo_len(self):
+        """Doubles per halo side buffer (-1 without halo sides)."""
+        return lib().gdg_halo_len(self._h)
+
+    def set_halo(self, send_lo, send_hi, recv_lo, recv_hi, exchange):
+        """gdg_set_halo: caller-owned float64 CUDA buffers of halo_len()
+        doubles (None for a side without a halo) and exchange(stream_ptr) ->
+        None, called between stages; an exception in it fails the call with
+        GDG_EHALO."""
+        n = self.halo_len()
+
+        def cb(user, stream):
+            try:
+                exchange(stream)
+                return 0
+            except Exception as exc:     # reported through the status code
+                self._halo_error = exc
+                return 1
+
+        self._halo_cb = HALO_FN(cb)     # keep the callback alive with the context
+        self._halo_bufs = (send_lo, send_hi, recv_lo, recv_hi)
+        ptr = lambda t: None if t is None else _ptr(t, n)
+        self._check(lib().gdg_set_halo(self._h, ptr(send_lo), ptr(send_hi), ptr(recv_lo), ptr(recv_hi),
+                                       self._halo_cb, None), "gdg_set_halo")
 
     def step_stats(self):
         """PCG statistics of the solves inside step()/rhs() since the last call."""

@@ -26,6 +26,9 @@ def _problems():
     yield gdg.make_problem(2, (9, 13), 6, 3, bc=(gdg.BC_PERIODIC, gdg.BC_DIRICHLET),
                            flux=gdg.FLUX_CENTRAL, c2=2.5, lo=(0.0, -1.0), hi=(1.5, 1.0))
     yield gdg.make_problem(1, (37,), 8, 3, flux=gdg.FLUX_UPWIND, c2=0.7, xi=0.9)
+    yield gdg.make_problem(2, (7, 5), 8, 5, bc=(gdg.BC_PERIODIC, gdg.BC_PERIODIC),
+                           flux=gdg.FLUX_ALTERNATING, c2=1.3)
+    yield gdg.make_problem(1, (11,), 6, 3, flux=gdg.FLUX_ALTERNATING, c2=1.0)
 
 
 def test_static_rhs_matches_context_rhs_on_consecutive_calls():
@@ -62,3 +65,31 @@ def test_static_rhs_rejects_meshes_beyond_the_static_array():
         gdg.rhs_static(bad, u[:1296], u[:1296].clone(), torch.empty(1296, dtype=torch.float64, device="cuda"),
                        torch.empty(1296, dtype=torch.float64, device="cuda"))
     assert err.value.status == gdg.EINVAL
+
+
+def test_static_rhs_on_a_side_stream():
+    """The call is asynchronous on the caller's stream: launched on a
+    non-default stream it gives the same result once that stream is done."""
+    pb = gdg.make_problem(2, (12, 10), 8, 5, flux=gdg.FLUX_UPWIND, c2=1.0)
+    ctx = gdg.Context(pb)
+    u = torch.tensor(inputs.random_state(ctx.n, 7), device="cuda")
+    v = torch.tensor(inputs.random_state(ctx.n, 8), device="cuda")
+    du_ref, dv_ref = torch.empty_like(u), torch.empty_like(v)
+    ctx.rhs(u, v, du_ref, dv_ref)
+    du, dv = torch.full_like(u, np.nan), torch.full_like(v, np.nan)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        gdg.rhs_static(pb, u, v, du, dv, stream=side)
+    side.synchronize()
+    a = np.concatenate([du.cpu().numpy(), dv.cpu().numpy()])
+    b = np.concatenate([du_ref.cpu().numpy(), dv_ref.cpu().numpy()])
+    assert _rel(a, b) < TOL
+    ctx.close()
+
+
+def test_static_rhs_checks_lengths_against_the_problem():
+    pb = gdg.make_problem(2, (4, 4), 8, 5)
+    short = torch.zeros(4 * 4 * 81 - 1, dtype=torch.float64, device="cuda")
+    with pytest.raises(ValueError):
+        gdg.rhs_static(pb, short, short.clone(), torch.empty_like(short), torch.empty_like(short))

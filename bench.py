@@ -151,6 +151,12 @@ def alu_roofline(f64, f32, byt, seconds, probe):
         out.update(fp32_tflops=a32, frac_fp32=fr["fp32"])
     return out
 
+# FP64 thread instructions (DFMA + DADD + DMUL) per element and RK stage of the
+# persistent step, from the ncu capture of the current kernel (16.04 M + 4.81 M
+# + 1.44 M per one-step launch of the 64x64 mesh): the FP64 pipe's share of a
+# stage's time follows from it at 2 FP64 lanes per SM and clock.
+STEP2R_FP64_INST_PER_ELEMENT_STAGE = 22.28e6 / (4 * 4096)
+
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per RK stage of
 # this workload, from one ncu capture per stage kernel (None for a kernel
 # without a capture of its current code):
@@ -745,10 +751,17 @@ def run_gdg(args):
                          "flops_per_stage_executed": executed_flops_per_stage_launch(),
                          "achieved_executed": achieved_x,
                          "frac_executed": achieved_x / FP64_PEAK_TFLOPS,
+                         "fp64_pipe_frac": (STEP2R_FP64_INST_PER_ELEMENT_STAGE * w["n"][0] * w["n"][1]
+                                            / (stage_ms / 1e3) / (152 * 2 * 2.070e9 * (clocks["sm_mhz"] or 2070.0)
+                                                                   / 2070.0))
+                                           if stage_variant == 3 else None,
                          "flops_note": "achieved: 40 algorithmic FP64 flops per DOF and stage (the modal "
                                        "route's per-DOF count) x DOF, per stage of the timed region; "
                                        "_executed: the flops the parity stage body performs (28.4 per DOF, "
-                                       "FMA = 2; the r -> 1-r symmetry halves the lifts and trace dots)",
+                                       "FMA = 2; the r -> 1-r symmetry halves the lifts and trace dots); "
+                                       "fp64_pipe_frac: the persistent step's FP64 instructions per stage "
+                                       "(ncu count) over the stage time at 2 lanes per SM and clock, the "
+                                       "figure ncu's FP64 pipe utilisation measures",
                          "peak_source": "FP64 derived from unit counts and the maximum SM clock: "
                                         "152 SM x 2070 MHz x 4 flop/clk; peak_probe: gdg_probe_fp64 "
                                         "(independent FMA chains) timed in this process"},

@@ -189,6 +189,53 @@ __device__ __forceinline__ void matvec_g(const double *__restrict__ A, const dou
     __syncthreads();
 }
 
+// FP64 dot products of NA-vectors in shared memory summed by warp 0 alone:
+// lane i accumulates entries i, i+32, i+64, ... (FMA chain), then a butterfly.
+// The FP64 pipe issues a warp instruction at full cost whatever its active
+// lanes (measured on GB300: one active lane per warp takes as long as 32), so
+// one warp doing the whole sum costs 3 + 5 FP64 warp instructions where every
+// warp adding its partial cost 27 for a 96-thread block.  The other warps wait
+// at the barrier.  Fixed order: deterministic.  Leading barrier: the inputs
+// are written (and the previous result has been read) before warp 0 starts.
+template <int NA>
+__device__ __forceinline__ double warp0_dot(const double *a, const double *b, double *red) {
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double s = 0.0;
+#pragma unroll
+        for (int k = threadIdx.x; k < NA; k += 32) s = fma(a[k], b[k], s);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (threadIdx.x == 0) red[0] = s;
+    }
+    __syncthreads();
+    return red[0];
+}
+
+// two such dot products with one pair of barriers: a.b and c.d
+template <int NA>
+__device__ __forceinline__ void warp0_dot2(const double *a, const double *b, const double *c, const double *d,
+                                           double *red, double &ab, double &cd) {
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double s = 0.0, q = 0.0;
+#pragma unroll
+        for (int k = threadIdx.x; k < NA; k += 32) {
+            s = fma(a[k], b[k], s);
+            q = fma(c[k], d[k], q);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            s += __shfl_xor_sync(0xffffffffu, s, o);
+            q += __shfl_xor_sync(0xffffffffu, q, o);
+        }
+        if (threadIdx.x == 0) { red[0] = s; red[1] = q; }
+    }
+    __syncthreads();
+    ab = red[0];
+    cd = red[1];
+}
+
 // two block sums with one pair of barriers (same order as block_sum)
 template <typename T>
 __device__ __forceinline__ void block_sum2(T &a, T &b, double *red) {
@@ -264,47 +311,51 @@ __device__ int pcg(const double *A, const double *w, const double *b, double *x,
         __syncthreads();
     } else {
         matvec<NA>(A, x, Ap);
-        double wx = W ? block_dot<NA>(w, x, red) : 0.0;
+        double wx = W ? warp0_dot<NA>(w, x, red) : 0.0;
         if (t < NA) r[t] = b[t] - Ap[t] - (W ? w[t] * wx : 0.0);
         __syncthreads();
         // a guess that does not beat x0 = 0 (true FP64 residual) is dropped
-        if (fallback && block_dot<NA>(r, r, red) >= block_dot<NA>(b, b, red)) {
+        double rr0, bb0;
+        if (fallback) warp0_dot2<NA>(r, r, b, b, red, rr0, bb0);
+        if (fallback && rr0 >= bb0) {
             if (t < NA) { x[t] = 0.0; r[t] = b[t]; }
             __syncthreads();
             if (fell) *fell = 1;
         }
     }
-    const double bnorm = sqrt(block_dot<NA>(b, b, red));
+    const double bnorm = sqrt(warp0_dot<NA>(b, b, red));
     precondition<N1>(r, z, Ps, d, t1, t2, none);
     if (t < NA) p[t] = z[t];
-    __syncthreads();
-    double rz = block_dot<NA>(r, z, red);
+    // r.z and r.r in one reduction, before the loop and after every update
+    double rz, rr;
+    warp0_dot2<NA>(r, z, r, r, red, rz, rr);
     int it = 0;
     while (it < maxit) {
-        const double rr = block_dot<NA>(r, r, red);
         if (sqrt(rr) <= rtol * bnorm || rz == 0.0) break;
         matvec<NA>(A, p, Ap);
+        // p.(A + w w^T)p = p.Ap + (w.p)^2: one reduction for both
+        double pAp, wp = 0.0;
         if (W) {
-            const double wp = block_dot<NA>(w, p, red);
-            if (t < NA) Ap[t] += w[t] * wp;
-            __syncthreads();
+            warp0_dot2<NA>(p, Ap, w, p, red, pAp, wp);
+            pAp += wp * wp;
+        } else {
+            pAp = warp0_dot<NA>(p, Ap, red);
         }
-        const double pAp = block_dot<NA>(p, Ap, red);
         const double alpha = rz / pAp;
         if (t < NA) {
             x[t] += alpha * p[t];
-            r[t] -= alpha * Ap[t];
+            r[t] -= alpha * (W ? Ap[t] + w[t] * wp : Ap[t]);
         }
         __syncthreads();
         precondition<N1>(r, z, Ps, d, t1, t2, none);
-        const double rzn = block_dot<NA>(r, z, red);
+        double rzn;
+        warp0_dot2<NA>(r, z, r, r, red, rzn, rr);
         const double beta = rzn / rz;
         if (t < NA) p[t] = z[t] + beta * p[t];
         __syncthreads();
         rz = rzn;
         ++it;
     }
-    const double rr = block_dot<NA>(r, r, red);
     *relres = bnorm > 0.0 ? sqrt(rr) / bnorm : 0.0;
     return it;
 }
@@ -384,12 +435,12 @@ __device__ int refine(const double *__restrict__ A, const double *w, const doubl
         precondition<N1>(b, step64->z, step64->Ps, step64->d, step64->t1, step64->t2, none);
         matvec_g<NA>(A, step64->z, Ap);
         if (W) {
-            const double wz = block_dot<NA, double>(w, step64->z, red);
+            const double wz = warp0_dot<NA>(w, step64->z, red);
             if (t < NA) Ap[t] += w[t] * wz;
             __syncthreads();
         }
-        const double bz = block_dot<NA, double>(b, step64->z, red);
-        const double zAz = block_dot<NA, double>(step64->z, Ap, red);
+        double bz, zAz;
+        warp0_dot2<NA>(b, step64->z, step64->z, Ap, red, bz, zAz);
         const double alpha = zAz > 0.0 ? bz / zAz : 0.0;
         if (t < NA) {
             x[t] = alpha * step64->z[t];
@@ -401,18 +452,22 @@ __device__ int refine(const double *__restrict__ A, const double *w, const doubl
         __syncthreads();
     } else {
         matvec_g<NA>(A, x, Ap);
-        const double wx = W ? block_dot<NA, double>(w, x, red) : 0.0;
+        const double wx = W ? warp0_dot<NA>(w, x, red) : 0.0;
         if (t < NA) r[t] = b[t] - Ap[t] - (W ? w[t] * wx : 0.0);
         __syncthreads();
-        if (fallback && block_dot<NA, double>(r, r, red) >= block_dot<NA, double>(b, b, red)) {
+        double rr0, bb0;
+        if (fallback) warp0_dot2<NA>(r, r, b, b, red, rr0, bb0);
+        if (fallback && rr0 >= bb0) {
             if (t < NA) { x[t] = 0.0; r[t] = b[t]; }
             __syncthreads();
             if (fell) *fell = 1;
         }
     }
-    const double bnorm = sqrt(block_dot<NA, double>(b, b, red));
+    double bb, rr;
+    warp0_dot2<NA>(b, b, r, r, red, bb, rr);
+    const double bnorm = sqrt(bb);
     int sweeps = 0, its = 0;
-    double rn = sqrt(block_dot<NA, double>(r, r, red));
+    double rn = sqrt(rr);
     while (sweeps < maxsweep && rn > rtol * bnorm && rn > 0.0) {
         const double inv = 1.0 / rn;
         if (t < NA) f.rhs[t] = (float)(r[t] * inv);
@@ -422,10 +477,10 @@ __device__ int refine(const double *__restrict__ A, const double *w, const doubl
         if (t < NA) x[t] += rn * (double)f.x[t];
         __syncthreads();
         matvec_g<NA>(A, x, Ap);
-        const double wx = W ? block_dot<NA, double>(w, x, red) : 0.0;
+        const double wx = W ? warp0_dot<NA>(w, x, red) : 0.0;
         if (t < NA) r[t] = b[t] - Ap[t] - (W ? w[t] * wx : 0.0);
         __syncthreads();
-        rn = sqrt(block_dot<NA, double>(r, r, red));
+        rn = sqrt(warp0_dot<NA>(r, r, red));
         ++sweeps;
     }
     *inner = its;

@@ -70,14 +70,22 @@ enum { GDG_COEF_CONST = 0, GDG_COEF_NODAL = 1 };
  * applies them instead of running PCG.  FP64 only (GDG_EUNSUPPORTED with
  * GDG_MIXED); gdg_pcg still runs PCG on such a context. */
 enum { GDG_SOLVE_DIAG = 0, GDG_SOLVE_PCG = 1, GDG_SOLVE_INVERSE = 2 };
-/* PCG preconditioner: frozen-coefficient diagonalisation, none (plain CG). */
-enum { GDG_PC_FDM = 0, GDG_PC_NONE = 1 };
+/* PCG preconditioner: frozen-coefficient diagonalisation, none (plain CG),
+ * or the zero fill-in incomplete Cholesky factors of Section 7.1, which this
+ * build does not run on the GPU (their triangular solves are sequential per
+ * element; gdg_create returns GDG_EUNSUPPORTED; the FP64 oracle has them). */
+enum { GDG_PC_FDM = 0, GDG_PC_NONE = 1, GDG_PC_IC0 = 2 };
 /* Arithmetic of the element solves.  GDG_FP64 everywhere, or (GDG_SOLVE_PCG
  * only) FP32 inner PCG with FP64 iterative refinement of every solve (FP64
  * state, residuals, lifts, norms and energy; same FP64 stopping test).
  * Constant-coefficient contexts are FP64 only (GDG_EUNSUPPORTED otherwise):
  * their diagonal solves have no iteration to refine. */
 enum { GDG_FP64 = 0, GDG_MIXED = 1 };
+/* Inner solves in TF32 or BF16 (GDG_EUNSUPPORTED): refinement converges at
+ * about kappa u_low per sweep and the u_t element systems have kappa ~ 1e3
+ * to 1e5, so these need several times the FP64 sweeps of GDG_MIXED (whose
+ * inner solves are FP32) or do not converge. */
+enum { GDG_TF32 = 2, GDG_BF16 = 3 };
 /* State representation used inside gdg_step for the diagonalised route:
  * modal coefficients U = Psi Ubar (Section 3.2).  The nodal-state route is
  * not built: gdg_create returns GDG_EUNSUPPORTED for GDG_ROUTE_NODAL. */
@@ -182,12 +190,14 @@ long long gdg_state_len(const gdg_ctx *ctx);
 
 /*
  * Semi-discrete time derivative (Eqs. DG1, DG2, DG1_extra with the fluxes of
- * Section 2.2.1): du = dU/dt, dv = dV/dt at the nodal state (u, v).
- * Device pointers of gdg_state_len doubles; du, dv must not alias u, v.
- * GDG_SOLVE_PCG contexts use the PCG settings of the problem and may
- * return GDG_ENOCONV (results are then the last iterates).
+ * Section 2.2.1): du = dU/dt, dv = dV/dt at the nodal state (u, v) and time
+ * t (t enters only through a point source, gdg_set_point_source; the
+ * problem is otherwise autonomous).  Device pointers of gdg_state_len
+ * doubles; du, dv must not alias u, v.  GDG_SOLVE_PCG contexts use the PCG
+ * settings of the problem and may return GDG_ENOCONV (results are then the
+ * last iterates).
  */
-int gdg_rhs(gdg_ctx *ctx, const double *u, const double *v, double *du, double *dv,
+int gdg_rhs(gdg_ctx *ctx, const double *u, const double *v, double t, double *du, double *dv,
             void *stream);
 
 /*
@@ -301,8 +311,8 @@ int gdg_residuals(gdg_ctx *ctx, const double *u, const double *v, double *ru, do
  * Its load on r_v is int phi_a f = phi_a(r, s) amplitude sin(omega t) on
  * that element (the delta function makes the Jacobian drop out); the inverse
  * route adds M_J^-1 of it to dV/dt.  gdg_step evaluates the source at each
- * RK stage's time, starting from its t0; gdg_rhs and gdg_residuals at the
- * time the last gdg_step reached (0 before any).  amplitude = 0 removes the
+ * RK stage's time, starting from its t0; gdg_rhs at its own t; gdg_residuals
+ * at the time the last gdg_step reached or gdg_rhs used (0 before any).  amplitude = 0 removes the
  * source.  Drops any captured step graph; synchronises the device.
  * GDG_EINVAL: not a GDG_COEF_NODAL context, element out of range, (r, s)
  * outside [0,1]^2, non-finite amplitude or omega.

@@ -1454,10 +1454,11 @@ int gdg_const_setup(gdg_ctx *ctx) {
     mp.epbh = ctx->dim == 2 ? choose_epb(ctx->ne, n1, sms, 2 * n1) : 1;
     mp.split = 0;   // decided by timing at the first gdg_step (one-line kernel on partitioned meshes)
     const int ents = ctx->dim == 3 ? nn * n1 : (ctx->dim == 2 ? nn : n1);
-    // rows: -c^2 lambda, 1/lambda (0 on the constant mode); 2-D also the u
-    // lifts folded with the diagonal solve, P1 = hgL_x[k]/lambda, P2 =
-    // hgL_y[l]/lambda (m = l n1 + k), which the parity stage kernels apply
-    std::vector<double> l2((size_t)(ctx->dim == 2 ? 4 : 2) * ents, 0.0);
+    // rows: -c^2 lambda, 1/lambda (0 on the constant mode); 2-D and 3-D also
+    // the u lifts folded with the diagonal solve, one row per direction:
+    // P1 = hgL_x/lambda, P2 = hgL_y/lambda (, P3 = hgL_z/lambda), which the
+    // parity stage kernels apply
+    std::vector<double> l2((size_t)(ctx->dim == 2 ? 4 : (ctx->dim == 3 ? 5 : 2)) * ents, 0.0);
     for (int m = 0; m < ents; ++m) {
         double L = ctx->dim == 3   ? lam[0][m % n1] + lam[1][(m / n1) % n1] + lam[2][m / nn]
                    : ctx->dim == 2 ? lam[0][m % n1] + lam[1][m / n1]
@@ -1467,6 +1468,10 @@ int gdg_const_setup(gdg_ctx *ctx) {
         if (ctx->dim == 2) {
             l2[2 * ents + m] = l2[ents + m] * mp.d[0].hgL[m % n1];
             l2[3 * ents + m] = l2[ents + m] * mp.d[1].hgL[m / n1];
+        } else if (ctx->dim == 3) {   // m = (mz n1 + my) n1 + mx
+            l2[2 * ents + m] = l2[ents + m] * mp.d[0].hgL[m % n1];
+            l2[3 * ents + m] = l2[ents + m] * mp.d[1].hgL[(m / n1) % n1];
+            l2[4 * ents + m] = l2[ents + m] * mp.d[2].hgL[m / nn];
         }
     }
     ctx->tr_len = (long long)ctx->ne * (ctx->dim == 3 ? 12 * nn : (ctx->dim == 2 ? 8 * n1 : 4));

@@ -173,6 +173,10 @@ k_stage3(const __grid_constant__ ModalParams mp, const StageBufs b, double cA, d
     if (valid) traces3_yz<N1>(mp, tU, tV, e, a, c, b.trout);
 }
 
+// The u lifts are folded with the diagonal solve (rows 2-4 of lam2: hgL of
+// each direction over lambda) and RK4 accumulates k1 + 2 k2 + 2 k3 (stages
+// 1-3 ignore cA; stage 4 forms y_n + cA (acc + k4), cA = dt/6), as the 2-D
+// parity kernels do.
 // Parity version of k_stage3 (modes ordered even first in every direction:
 // eR = s eL and gR = s gL, s = +1 for the NE = (N1+1)/2 even modes, -1 for
 // the odd ones).  Phase 1 keeps, per direction and transverse mode pair, the
@@ -261,11 +265,12 @@ k_stage3p(const __grid_constant__ ModalParams mp, const StageBufs b, double cA, 
         const int line = a * N1 + c;
         const size_t row = ((size_t)e * NT + line) * N1;
         const double *L0 = b.lam2 + line * N1;
-        const double *L1 = b.lam2 + NA + line * N1;
+        const double *P1 = b.lam2 + 2 * NA + line * N1, *P2 = b.lam2 + 3 * NA + line * N1;
+        const double *P3 = b.lam2 + 4 * NA + line * N1;
         const double GA = F[0 * NT + line], GB = F[1 * NT + line];
         const double QA = F[2 * NT + line], QB = F[3 * NT + line];
-        const double hgy = mp.d[1].hgL[c], cey = mp.d[1].ceL[c];
-        const double hgz = mp.d[2].hgL[a], cez = mp.d[2].ceL[a];
+        const double cey = mp.d[1].ceL[c];
+        const double cez = mp.d[2].ceL[a];
         const double *FGy = F + (4 + (c < NE ? 0 : 1)) * NT + a * N1;   // at ty = a N1 + k
         const double *FQy = F + (6 + (c < NE ? 0 : 1)) * NT + a * N1;
         const double *FGz = F + (8 + (a < NE ? 0 : 1)) * NT + c * N1;   // at tz = c N1 + k
@@ -274,26 +279,27 @@ k_stage3p(const __grid_constant__ ModalParams mp, const StageBufs b, double cA, 
         for (int k = 0; k < N1; ++k) {
             const double Yu = pyU[row + k], Yv = pyV[row + k];
             const double xg = k < NE ? GA : GB, xq = k < NE ? QA : QB;
-            const double ru = fma(mp.d[0].hgL[k], xg, fma(hgy, FGy[k], hgz * FGz[k]));
+            // k_u = V + Lambda^+ r_u with the three rank-one lifts folded into
+            // P1, P2, P3 (hgL / lambda per direction): three FMAs
+            const double ku = fma(P1[k], xg, fma(P2[k], FGy[k], fma(P3[k], FGz[k], Yv)));
             const double rv = fma(L0[k], Yu, fma(mp.d[0].ceL[k], xq, fma(cey, FQy[k], cez * FQz[k])));
-            const double ku = fma(L1[k], ru, Yv);
             const double kv = rv;
             if (MODE == M_RHS) {
                 poU[row + k] = ku;
                 poV[row + k] = kv;
-            } else if (MODE == M_S1) {
-                paU[row + k] = cA * ku;
-                paV[row + k] = cA * kv;
+            } else if (MODE == M_S1) {   // accumulator k1 + 2 k2 + 2 k3, scaled by dt/6 at stage 4
+                paU[row + k] = ku;
+                paV[row + k] = kv;
                 Ru[k] = fma(cY, ku, Yu);
                 Rv[k] = fma(cY, kv, Yv);
             } else if (MODE == M_S23) {
-                paU[row + k] = fma(cA, ku, paU[row + k]);
-                paV[row + k] = fma(cA, kv, paV[row + k]);
+                paU[row + k] = fma(2.0, ku, paU[row + k]);
+                paV[row + k] = fma(2.0, kv, paV[row + k]);
                 Ru[k] = fma(cY, ku, pnU[row + k]);
                 Rv[k] = fma(cY, kv, pnV[row + k]);
             } else {
-                Ru[k] = fma(cA, ku, pnU[row + k] + paU[row + k]);
-                Rv[k] = fma(cA, kv, pnV[row + k] + paV[row + k]);
+                Ru[k] = fma(cA, paU[row + k] + ku, pnU[row + k]);
+                Rv[k] = fma(cA, paV[row + k] + kv, pnV[row + k]);
             }
         }
         if (MODE != M_RHS) {

@@ -384,12 +384,22 @@ static int validate(const gdg_problem *pb, std::string &why) {
             why = "GDG_SOLVE_INVERSE has no iteration to refine: FP64 only";
             return GDG_EUNSUPPORTED;
         }
+        if (pb->precond == GDG_PC_IC0) {
+            why = "IC(0) preconditioning is not run on the GPU (sequential triangular solves per element); "
+                  "use GDG_PC_FDM";
+            return GDG_EUNSUPPORTED;
+        }
         if (pb->precond != GDG_PC_FDM && pb->precond != GDG_PC_NONE) { why = "bad precond"; return GDG_EINVAL; }
         if (pb->pcg_maxit < 1 || !(pb->pcg_rtol >= 0.0)) { why = "bad PCG settings"; return GDG_EINVAL; }
         if (pb->nquad < 0 || pb->nquad > 12) { why = "nquad must be in 0..12"; return GDG_EINVAL; }
     } else {
         why = "bad coef";
         return GDG_EINVAL;
+    }
+    if (pb->precision == GDG_TF32 || pb->precision == GDG_BF16) {
+        why = "TF32 / BF16 inner solves are not built: refinement needs kappa u_low < 1 and the u_t systems have "
+              "kappa 1e3..1e5 (use GDG_MIXED, FP32 inner solves)";
+        return GDG_EUNSUPPORTED;
     }
     if (pb->precision != GDG_FP64 && pb->precision != GDG_MIXED) { why = "bad precision"; return GDG_EINVAL; }
     if (pb->rows[0] || pb->rows[1]) {
@@ -472,13 +482,13 @@ extern "C" long long gdg_state_len(const gdg_ctx *ctx) { return ctx ? ctx->ndof 
 
 static bool is_const(const gdg_ctx *ctx) { return ctx->pb.coef == GDG_COEF_CONST; }
 
-extern "C" int gdg_rhs(gdg_ctx *ctx, const double *u, const double *v, double *du, double *dv,
+extern "C" int gdg_rhs(gdg_ctx *ctx, const double *u, const double *v, double t, double *du, double *dv,
                        void *stream) {
-    if (!ctx || !u || !v || !du || !dv) return GDG_EINVAL;
+    if (!ctx || !u || !v || !du || !dv || !std::isfinite(t)) return GDG_EINVAL;
     if (du == u || du == v || dv == u || dv == v)
         return gdg_set_err(ctx, GDG_EINVAL, "gdg_rhs: outputs alias inputs");
     cudaStream_t s = (cudaStream_t)stream;
-    return is_const(ctx) ? gdg_const_rhs(ctx, u, v, du, dv, s) : gdg_var_rhs(ctx, u, v, du, dv, s);
+    return is_const(ctx) ? gdg_const_rhs(ctx, u, v, du, dv, s) : gdg_var_rhs(ctx, u, v, t, du, dv, s);
 }
 
 extern "C" int gdg_mass_solve(gdg_ctx *ctx, int which, const double *b, double *x, void *stream) {

@@ -157,7 +157,7 @@ int gdg_const_energy(gdg_ctx *ctx, const double *u, const double *v, double *E, 
 // variable-coefficient / mapped path (gdg_var.cu)
 int gdg_var_setup(gdg_ctx *ctx);
 void gdg_var_free(gdg_ctx *ctx);
-int gdg_var_rhs(gdg_ctx *ctx, const double *u, const double *v, double *du, double *dv,
+int gdg_var_rhs(gdg_ctx *ctx, const double *u, const double *v, double t, double *du, double *dv,
                 cudaStream_t s);
 int gdg_var_pcg(gdg_ctx *ctx, int which, const double *b, double *x, gdg_pcg_stats *st,
                 cudaStream_t s);

@@ -348,8 +348,10 @@ void gdg_var_free(gdg_ctx *ctx) {
     ctx->var = nullptr;
 }
 
-int gdg_var_rhs(gdg_ctx *ctx, const double *u, const double *v, double *du, double *dv, cudaStream_t s) {
+int gdg_var_rhs(gdg_ctx *ctx, const double *u, const double *v, double t, double *du, double *dv,
+                cudaStream_t s) {
     VarData &D = *ctx->var;
+    if (D.vp.src_e >= 0) k_set_time<<<1, 1, 0, s>>>(D.d_time, t);   // the forcing's time
     cudaMemsetAsync(D.d_stats, 0, 16 * sizeof(unsigned long long), s);
     launch_traces(ctx, u, v, D.d_tr, s);
     VarBufs b{};

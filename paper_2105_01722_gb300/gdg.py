@@ -17,8 +17,8 @@ BC_DIRICHLET, BC_PERIODIC = 0, 1
 FLUX_CENTRAL, FLUX_UPWIND, FLUX_ALTERNATING = 0, 1, 2
 COEF_CONST, COEF_NODAL = 0, 1
 SOLVE_DIAG, SOLVE_PCG, SOLVE_INVERSE = 0, 1, 2
-PC_FDM, PC_NONE = 0, 1
-FP64, MIXED = 0, 1
+PC_FDM, PC_NONE, PC_IC0 = 0, 1, 2
+FP64, MIXED, TF32, BF16 = 0, 1, 2, 3
 ROUTE_MODAL, ROUTE_NODAL = 0, 1
 OP_M, OP_S = 0, 1
 
@@ -56,7 +56,7 @@ EXPORTS = {
     "gdg_create": (ctypes.c_int, [ctypes.POINTER(Problem), ctypes.POINTER(ctypes.c_void_p)]),
     "gdg_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "gdg_state_len": (ctypes.c_longlong, [ctypes.c_void_p]),
-    "gdg_rhs": (ctypes.c_int, [ctypes.c_void_p] * 6),
+    "gdg_rhs": (ctypes.c_int, [ctypes.c_void_p] * 3 + [ctypes.c_double] + [ctypes.c_void_p] * 3),
     "gdg_mass_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                       ctypes.c_void_p]),
     "gdg_pcg": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
@@ -255,8 +255,9 @@ class Context:
         if st != OK:
             raise GdgError(st, "%s: %s" % (what, lib().gdg_last_error(self._h).decode()))
 
-    def rhs(self, u, v, du, dv, stream=None):
-        self._check(lib().gdg_rhs(self._h, _ptr(u, self.n), _ptr(v, self.n), _ptr(du, self.n),
+    def rhs(self, u, v, du, dv, stream=None, t=0.0):
+        """gdg_rhs at time t (which matters only with a point source)."""
+        self._check(lib().gdg_rhs(self._h, _ptr(u, self.n), _ptr(v, self.n), float(t), _ptr(du, self.n),
                                   _ptr(dv, self.n), _stream(stream)), "gdg_rhs")
 
     def mass_solve(self, which, b, x, stream=None):

@@ -107,6 +107,9 @@ def _nodal_kw(**extra):
     (dict(dim=2, n=(4, 4), N=8, p=5, precision=gdg.MIXED), "EUNSUPPORTED"),      # nothing to refine
     ("inverse_mixed", "EUNSUPPORTED"),
     ("nodal_diag", "EINVAL"),
+    ("ic0", "EUNSUPPORTED"),                                                    # oracle only
+    ("tf32", "EUNSUPPORTED"),                                                   # refinement would stall
+    ("bf16", "EUNSUPPORTED"),
     (dict(dim=3, n=(2, 2, 2), N=10, p=5), "EUNSUPPORTED"),                      # 3-D: N+1 <= 10
     (dict(dim=4, n=(2, 2, 2), N=8, p=5), "EINVAL"),
 ])
@@ -117,6 +120,10 @@ def test_create_rejects_unbuilt_combinations(kw, status):
         kw = _nodal_kw(solver=gdg.SOLVE_INVERSE, precision=gdg.MIXED)
     elif kw == "nodal_diag":
         kw = _nodal_kw(solver=gdg.SOLVE_DIAG)
+    elif kw == "ic0":
+        kw = _nodal_kw(precond=gdg.PC_IC0)
+    elif kw in ("tf32", "bf16"):
+        kw = _nodal_kw(precision=gdg.TF32 if kw == "tf32" else gdg.BF16)
     pb = gdg.make_problem(**kw)
     h = ctypes.c_void_p()
     assert L.gdg_create(ctypes.byref(pb), ctypes.byref(h)) == getattr(gdg, status)
@@ -126,11 +133,11 @@ def test_create_rejects_unbuilt_combinations(kw, status):
 def test_null_arguments():
     L = _lib()
     assert L.gdg_create(None, None) == gdg.EINVAL
-    assert L.gdg_rhs(None, None, None, None, None, None) == gdg.EINVAL
+    assert L.gdg_rhs(None, None, None, 0.0, None, None, None) == gdg.EINVAL
     assert L.gdg_step(None, None, None, 0.0, 1e-3, 1, None) == gdg.EINVAL
     assert L.gdg_destroy(None) == gdg.EINVAL
     assert L.gdg_state_len(None) == -1
-    for s in (0, -1, -2, -3, -4, -5, -6, -7, -99):
+    for s in (0, -1, -2, -3, -4, -5, -6, -7, -8, -99):
         assert isinstance(L.gdg_status_string(s), bytes)
 
 

@@ -118,6 +118,39 @@ def test_point_source_steps_match_oracle(solver, flux, periodic):
     ctx.close()
 
 
+def test_rhs_evaluates_the_source_at_its_time():
+    """gdg_rhs(t) adds the load a sin(w t) phi(x_s) at its own t: the
+    derivative at two times differs by exactly the source term, which the
+    oracle forms from its residuals and dense solves."""
+    n, N, p = (3, 3), 8, 5
+    ne = n[0] * n[1]
+    X, Y = inputs.mapped_nodes(n, N, 0.05)
+    C2 = inputs.c2_sine(X, Y)
+    vp = dv.VarProblem(n=n, N=N, p=p, X=X, Y=Y, C2=C2)
+    ops = dv.assemble(vp)
+    e, r, s_, amp, omega = 4, 0.3, 0.55, 2.0, 7.0
+    w = _load(vp, e, r, s_)
+    U = 0.1 * inputs.random_state((ne, (N + 1) ** 2), 81)
+    V = 0.1 * inputs.random_state((ne, (N + 1) ** 2), 82)
+    pb = gdg.make_problem(2, n, N, p, coef=gdg.COEF_NODAL, x_nodes=X, y_nodes=Y, c2_nodes=C2,
+                          solver=gdg.SOLVE_INVERSE)
+    ctx = gdg.Context(pb)
+    ctx.set_point_source(e, r, s_, amp, omega)
+    kappa = max(max(np.linalg.cond(dv.spd_u_matrix(ops, q)), np.linalg.cond(ops.M[q])) for q in range(ne))
+    tol = max(1e-12, 50.0 * kappa * EPS)
+    for t in (0.0, 0.37, 1.9):
+        F = np.zeros((ne, (N + 1) ** 2))
+        F[e] = amp * np.sin(omega * t) * w
+        ru, rv = dv.residuals(vp, ops, U, V, forcing=F)
+        Ut, Vt = dv.solve_direct(ops, V, ru, rv)
+        u, v = _dev(U), _dev(V)
+        du, dv_ = torch.empty_like(u), torch.empty_like(v)
+        ctx.rhs(u, v, du, dv_, t=t)
+        got = np.concatenate([du.cpu().numpy(), dv_.cpu().numpy()])
+        assert _rel(got, np.concatenate([Ut.ravel(), Vt.ravel()])) < tol, t
+    ctx.close()
+
+
 def test_point_source_arguments():
     X, Y = inputs.mapped_nodes((2, 2), 8, 0.05)
     C2 = inputs.c2_sine(X, Y)

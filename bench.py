@@ -381,6 +381,76 @@ def forms_variable(steps=16):
     return out
 
 
+def coarse_in_fine(n, N):
+    """Indices into a (2n x 2n elements, N) nodal array of the nodes of the
+    (n x n, N) mesh: coarse node (ey, ex, j, i) sits at fine element
+    (2 ey + (j > N/2), 2 ex + (i > N/2)), node (2 j - N [j > N/2], 2 i - N [i > N/2])."""
+    import numpy as np
+    n1 = N + 1
+    ey, ex, j, i = np.meshgrid(np.arange(n), np.arange(n), np.arange(n1), np.arange(n1), indexing="ij")
+    hy, hx = (j > N // 2).astype(int), (i > N // 2).astype(int)
+    fy, fx = 2 * ey + hy, 2 * ex + hx
+    fj, fi = 2 * j - N * hy, 2 * i - N * hx
+    return (((fy * (2 * n) + fx) * n1 + fj) * n1 + fi).ravel()
+
+
+def forms_equal_error(T=0.25, ps=(3, 5), n=128):
+    """Equal final error for the variable-coefficient forms (mapped n x n mesh,
+    c^2 = 1 + 0.5 sin 2pi x cos 2pi y, Gaussian pulse of width 0.05): u at
+    time T of FP64 PCG, mixed PCG and element inverses, each against an FP64
+    reference on the 2n x 2n mesh of the same map with the same N (cells of
+    half the size; every coarse node is a fine node), advanced with element
+    inverses (exact element solves) at half the step.  A form matches when its
+    error is at most 1.05x the FP64 PCG's."""
+    import numpy as np
+    import torch
+    from paper_2105_01722_gb300 import gdg, inputs
+    N = 8
+    out = {"T": T, "mesh": [n, n], "reference_mesh": [2 * n, 2 * n],
+           "reference": "FP64 element inverses on the 2x refined mesh (h/2), dt/2"}
+    dt0 = 0.1 / (n * N) / np.sqrt(1.5)
+    for p in ps:
+        res = {}
+        Xf, Yf = inputs.mapped_nodes((2 * n, 2 * n), N, 0.05)
+        X, Y = inputs.mapped_nodes((n, n), N, 0.05)
+        idx = coarse_in_fine(n, N)
+        assert np.abs(Xf.ravel()[idx] - X.ravel()).max() < 1e-13 and np.abs(Yf.ravel()[idx] - Y.ravel()).max() < 1e-13
+        steps = int(round(T / dt0))
+        dt = T / steps
+        t0 = time.perf_counter()
+        ctx = gdg.Context(gdg.make_problem(2, (2 * n, 2 * n), N, p, coef=gdg.COEF_NODAL, x_nodes=Xf, y_nodes=Yf,
+                                           c2_nodes=inputs.c2_sine(Xf, Yf), solver=gdg.SOLVE_INVERSE))
+        u = torch.tensor(inputs.gaussian_pulse(Xf, Yf, 0.5, 0.5, 0.05).ravel(), device="cuda")
+        v = torch.zeros_like(u)
+        ctx.step(u, v, 0.0, 0.5 * dt, 2 * steps)
+        ref = u.cpu().numpy()[idx]
+        ctx.close()
+        del u, v
+        torch.cuda.empty_cache()
+        res["reference_s"] = time.perf_counter() - t0
+        for prec, solver, name in ((gdg.FP64, gdg.SOLVE_PCG, "fp64"), (gdg.MIXED, gdg.SOLVE_PCG, "mixed"),
+                                   (gdg.FP64, gdg.SOLVE_INVERSE, "inverse")):
+            ctx = gdg.Context(gdg.make_problem(2, (n, n), N, p, coef=gdg.COEF_NODAL, x_nodes=X, y_nodes=Y,
+                                               c2_nodes=inputs.c2_sine(X, Y), pcg_rtol=1e-10, pcg_maxit=100,
+                                               precision=prec, solver=solver))
+            u = torch.tensor(inputs.gaussian_pulse(X, Y, 0.5, 0.5, 0.05).ravel(), device="cuda")
+            v = torch.zeros_like(u)
+            t1 = time.perf_counter()
+            ctx.step(u, v, 0.0, dt, steps)
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t1
+            a = u.cpu().numpy()
+            res[name] = {"rel_l2_error": float(np.linalg.norm(a - ref) / np.linalg.norm(ref)),
+                         "steps": steps, "wall_s": wall, "dof_steps_per_s": n * n * 81 * steps / wall}
+            ctx.close()
+        e64 = res["fp64"]["rel_l2_error"]
+        for name in ("mixed", "inverse"):
+            res[name]["error_vs_fp64"] = res[name]["rel_l2_error"] / e64
+            res[name]["matches"] = res[name]["rel_l2_error"] <= 1.05 * e64
+        out["p%d" % p] = res
+    return out
+
+
 def executed_flops_per_element_stage_3d(n1):
     """FP64 flops the 3-D parity stage kernel executes per element (FMA = 2):
     fluxes 3 directions x n1^2 x (2 faces x 7 + 4 sums/differences), per
@@ -534,15 +604,17 @@ def forms_batched(steps=8):
 
 
 def forms_learned(rows=20000, epochs=30, steps=16):
-    """Learned u_t initial guess: rows generated by the method on random smooth
-    c^2 in [1/2, 2] (p = 5, 8x8 cells), trained with the library's kernels; u_t
-    PCG iterations and DOF-steps/s on an unseen 128 x 128 mesh at rtol 1e-10,
-    with and without the network (FP64 and mixed PCG)."""
+    """Learned u_t initial guess: 20k rows generated by the method on 128 x 128
+    meshes with random smooth c^2 in [1/2, 2] (p = 5, 8x8 cells; 2,500 random
+    elements of one snapshot per c^2 field, so eight fields), trained with the library's kernels; u_t
+    PCG iterations and DOF-steps/s on an unseen 128 x 128 mesh (the same
+    element size: the constraint row of the u_t system scales with the element
+    area) at rtol 1e-10, with and without the network (FP64 and mixed PCG)."""
     import time
     import torch
     from paper_2105_01722_gb300 import gdg, inputs, learned
     t0 = time.time()
-    X, T = learned.generate(rows, n=16, seed0=2000, snapshots=6)
+    X, T = learned.generate(rows, n=128, seed0=2000, snapshots=1, substeps=12, per_snapshot=2500)
     t1 = time.time()
     ntr = int(0.9 * rows)
     net, hist = learned.train(X[:ntr], T[:ntr], epochs=epochs, batch=256, lr=2e-3)
@@ -717,6 +789,11 @@ def run_gdg(args):
                     forms[key] = fn()
                 except Exception as exc:    # report, do not lose the headline line
                     forms[key] = {"error": repr(exc)}
+        if args.equal_error and world == 1:
+            try:
+                forms["equal_error_mapped_128"] = forms_equal_error()
+            except Exception as exc:
+                forms["equal_error_mapped_128"] = {"error": repr(exc)}
         line = {
             "metric": "DOF-steps/s", "value": value, "unit": "DOF-steps/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
@@ -794,6 +871,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the extra forms (variable/mapped, batched, learned) after the headline")
+    ap.add_argument("--equal-error", action="store_true",
+                    help="also run the variable-coefficient forms to T = 0.25 against a 2x refined FP64 "
+                         "reference (several minutes)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -419,19 +419,21 @@ typedef struct gdg_batch gdg_batch;   /* opaque; owns one context per problem */
 /*
  * Many independent 2-D problems advanced together (a launch pattern layered
  * on the method; the paper advances one mesh at a time).  Every RK stage of
- * all problems is two launches on two streams: the elements of the
- * GDG_COEF_NODAL problems (element solves with each problem's own solver
- * and precision: GDG_MIXED gives FP32 inner PCG with FP64 refinement and
- * FP64 state), and tiles of elements of the GDG_COEF_CONST problems
- * (modified-basis route), each a persistent kernel whose CTAs pull work
- * from a queue or a flat grid; the element solves may instead run as one
- * launch per problem.  A call's launches are replayed from one CUDA graph.
- * The launch shape (threads per block, which also sets the modal tile,
- * resident blocks per SM, flat or per-problem launches) is chosen on the
- * first gdg_batch_step by timing every candidate on the batch's own data.
- * pbs[count]: host problems, all dim = 2 with the same N, 7 <= N <= 9; each is
- * validated and set up as by gdg_create (host arrays copied).
- * Errors: as gdg_create; GDG_EUNSUPPORTED for other N.
+ * all problems is ONE persistent launch: (SMs x resident blocks) blocks of
+ * one element block each (N1^2 threads rounded up to a warp) walk one list
+ * of work items ordered longest first -- the element solves of the
+ * GDG_COEF_NODAL problems (each with its own solver and precision: element
+ * PCG in FP64 or GDG_MIXED, or precomputed inverses), then tiles of the
+ * GDG_COEF_CONST problems' elements (modified-basis route) -- block b taking
+ * turns b, b + G, ... of a few consecutive items.  A call's launches are
+ * replayed from one CUDA
+ * graph.  The kernel's register budget (three compiled variants) and the
+ * resident blocks per SM are chosen on the first gdg_batch_step by timing
+ * the candidates on the batch's own data.
+ * pbs[count]: host problems, all dim = 2 with the same N, 7 <= N <= 9, whole
+ * meshes (rows = {0, 0}); each is validated and set up as by gdg_create (host
+ * arrays copied).
+ * Errors: as gdg_create; GDG_EUNSUPPORTED for other N or bands of rows.
  */
 int gdg_batch_create(const gdg_problem *pbs, int count, gdg_batch **out);
 
@@ -451,17 +453,29 @@ int gdg_batch_step(gdg_batch *b, double *const *u, double *const *v, const doubl
                    void *stream);
 
 /*
- * Launch shapes chosen by the tuner (zeros before the first gdg_batch_step;
- * any output pointer may be NULL): threads_per_block and tile_elements of
- * the modal (constant-coefficient) launch, tile_elements x (N+1) threads,
- * 0 when the batch has no such problem; blocks_per_sm of the element-PCG
- * launch (its blocks have one thread per element node, rounded up to a
- * warp): the persistent grid's blocks per SM, -1 for a flat grid of one
- * block per element, -2 for one launch per problem of its own stage kernel
- * (parameters as kernel arguments), 0 when the batch has no
- * variable-coefficient problem.
+ * Launch shape chosen by the tuner (zeros before the first gdg_batch_step;
+ * any output pointer may be NULL): threads_per_block of the stage launch
+ * (N1^2 rounded up to a warp), blocks_per_sm (the persistent grid has SMs x
+ * blocks_per_sm blocks), tile_elements = threads_per_block / (2 N1), the
+ * elements of a constant-coefficient work item (0 when the batch has none),
+ * register_budget (see gdg_batch_set_tuning) and registers_per_thread of the
+ * chosen kernel, items_per_turn (block b takes the turns b, b + G, ... of
+ * that many consecutive items of the list).
  */
-int gdg_batch_tuning(const gdg_batch *b, int *threads_per_block, int *blocks_per_sm, int *tile_elements);
+int gdg_batch_tuning(const gdg_batch *b, int *threads_per_block, int *blocks_per_sm, int *tile_elements,
+                     int *register_budget, int *registers_per_thread, int *items_per_turn);
+
+/*
+ * Pin the launch shape instead of tuning it: register_budget 0, 1 or 2 (the
+ * kernel compiled for 3 resident blocks of N1^2 threads per SM, for 480
+ * threads per SM (at most 128 registers a thread) or for 960 (at most 64)),
+ * blocks_per_sm >= 1 (the persistent grid has SMs x blocks_per_sm blocks),
+ * items_per_turn >= 1; blocks_per_sm = 0 hands the choice back to the tuner
+ * at the next gdg_batch_step.  Synchronises the device.
+ * Errors: GDG_EINVAL for other values or more blocks per SM than the
+ * kernel's registers and the batch's shared memory allow.
+ */
+int gdg_batch_set_tuning(gdg_batch *b, int register_budget, int blocks_per_sm, int items_per_turn);
 
 /* PCG statistics of problem i since the previous call, as gdg_step_stats. */
 int gdg_batch_stats(gdg_batch *b, int i, gdg_pcg_stats *u_sys, gdg_pcg_stats *v_sys);

@@ -3,7 +3,7 @@
 python -m paper_2105_01722_gb300.cases const [--n 64] [--p 5] [--steps 8] [--variant -1|0|1|2]
 python -m paper_2105_01722_gb300.cases const3 [--n 16] [--p 5] [--steps 8]
 python -m paper_2105_01722_gb300.cases var   [--n 32] [--p 5] [--steps 2] [--mixed | --inverse]
-python -m paper_2105_01722_gb300.cases batch [--problems 12] [--steps 2] [--mixed]
+python -m paper_2105_01722_gb300.cases batch [--problems 12] [--steps 2] [--mixed | --inverse] [--pin B,R,C]
 python -m paper_2105_01722_gb300.cases mlp   [--rows 4096] [--steps 4]
 
 Each case builds its inputs with `inputs`, runs a few warm-up calls, then the
@@ -99,14 +99,16 @@ def case_var(n=32, N=8, p=5, steps=2, warmup=1, mixed=False, inverse=False):
             "pcg_v_mean_iters": sv["mean_iters"]}
 
 
-def case_batch(problems=12, steps=2, warmup=1, mixed=False, sequential=False, pmax=7):
+def case_batch(problems=12, steps=2, warmup=1, mixed=False, sequential=False, pmax=7, inverse=False, pin=None):
     """The seeded mixed batch of `inputs.batched_problems` (sizes, orders,
     constant / variable c^2), advanced by one Batch (sequential: each problem
     by its own gdg_step, one after another on one stream); pmax drops the
-    problems of higher order."""
+    problems of higher order; pin = (register budget, blocks per SM, items
+    per turn) fixes the launch shape instead of tuning it."""
     import torch
     specs = [sp for sp in inputs.batched_problems(problems) if sp["p"] <= pmax]
     prec = gdg.MIXED if mixed else gdg.FP64
+    solver = gdg.SOLVE_INVERSE if inverse else gdg.SOLVE_PCG
     pbs, us, dts = [], [], []
     for sp in specs:
         n, p = sp["n"], sp["p"]
@@ -114,7 +116,8 @@ def case_batch(problems=12, steps=2, warmup=1, mixed=False, sequential=False, pm
         if sp["variable"]:
             C2 = inputs.smooth_random_c2(X, Y, sp["seed"])
             pbs.append(gdg.make_problem(2, (n, n), 8, p, coef=gdg.COEF_NODAL, x_nodes=X, y_nodes=Y,
-                                        c2_nodes=C2, pcg_rtol=1e-10, pcg_maxit=100, precision=prec))
+                                        c2_nodes=C2, pcg_rtol=1e-10, pcg_maxit=100, precision=prec,
+                                        solver=solver))
             cmax = float(np.sqrt(C2.max()))
         else:
             pbs.append(gdg.make_problem(2, (n, n), 8, p, c2=1.0))
@@ -123,7 +126,8 @@ def case_batch(problems=12, steps=2, warmup=1, mixed=False, sequential=False, pm
         dts.append(CFL[p] / (n * 8) / cmax)
     vs = [torch.zeros_like(u) for u in us]
     dof = sum(sp["n"] ** 2 * 81 for sp in specs)
-    out = {"case": "batch", "problems": len(specs), "mixed": mixed, "sequential": sequential, "steps": steps}
+    out = {"case": "batch", "problems": len(specs), "mixed": mixed, "inverse": inverse, "sequential": sequential,
+           "steps": steps}
     if sequential:
         ctxs = [gdg.Context(pb) for pb in pbs]
         run = lambda k: [c.step(u, v, 0.0, d, k) for c, u, v, d in zip(ctxs, us, vs, dts)]
@@ -133,6 +137,8 @@ def case_batch(problems=12, steps=2, warmup=1, mixed=False, sequential=False, pm
             c.close()
     else:
         batch = gdg.Batch(pbs)
+        if pin:
+            batch.set_tuning(*pin)
         batch.step(us, vs, dts, warmup)
         ms = _ms(lambda: batch.step(us, vs, dts, steps))
         out["tuning"] = batch.tuning()
@@ -177,6 +183,7 @@ def main(argv=None):
     ap.add_argument("--sequential", action="store_true")
     ap.add_argument("--pmax", type=int, default=7)
     ap.add_argument("--variant", type=int, default=-1, help="const: stage kernel (-1 timed, 0, 1, 2)")
+    ap.add_argument("--pin", help="batch: register budget, blocks per SM, items per turn (e.g. 1,5,1)")
     a = ap.parse_args(argv)
     kw = {"steps": a.steps} if a.steps else {}
     if a.case == "const":
@@ -186,7 +193,9 @@ def main(argv=None):
     elif a.case == "var":
         r = case_var(n=a.n or 32, p=a.p, mixed=a.mixed, inverse=a.inverse, **kw)
     elif a.case == "batch":
-        r = case_batch(problems=a.problems, mixed=a.mixed, sequential=a.sequential, pmax=a.pmax, **kw)
+        pin = tuple(int(x) for x in a.pin.split(",")) if a.pin else None
+        r = case_batch(problems=a.problems, mixed=a.mixed, sequential=a.sequential, pmax=a.pmax,
+                       inverse=a.inverse, pin=pin, **kw)
     else:
         r = case_mlp(rows=a.rows, **kw)
     print(json.dumps(r))

@@ -1,19 +1,20 @@
 // Batched launch of many independent 2-D problems (a pattern layered on the
 // method; the paper advances one mesh at a time).
 //
-// Every RK4 stage of all problems of a batch is two persistent kernels that
-// run side by side (two branches of one CUDA graph): one over the elements
-// of the variable-coefficient problems (element PCG; 81+ threads and ~75-115
-// KB of shared memory per element) and one over tiles of elements of the
-// constant-coefficient problems (modal route; a few KB per element).  Each
-// is a grid of (SMs x resident blocks) CTAs pulling items from its own queue,
-// so uneven meshes and degrees balance without per-problem launches and the
-// two kinds of work share the SMs.  The stage bodies are the per-problem
-// kernels' own (stage2p_body, var_stage_body), so a batched step computes
-// exactly what the problem's own gdg_step computes.  A call's launches are
-// captured once in a CUDA graph (per-problem dt lives in device descriptors,
-// so the graph does not depend on it).  The modal tile (elements per block)
-// and the PCG grid size are picked on the first step by timing the
+// Every RK4 stage of all problems of a batch is ONE persistent launch: a grid
+// of (SMs x resident blocks) CTAs of one element block each (N1^2 threads
+// rounded up to a warp) walks one list of work items ordered longest first --
+// the element solves of the variable-coefficient problems (element PCG in
+// FP64 or mixed precision, or precomputed inverses; by decreasing degree),
+// then tiles of the constant-coefficient problems' elements (modified-basis
+// route, half-line body) -- block b taking turns b, b + G, ... of a few
+// consecutive items.  The
+// stage bodies are the per-problem kernels' own (var_stage_body,
+// stage2h_body), so a batched step computes exactly what the problem's own
+// gdg_step computes.  A call's launches are captured once in a CUDA graph
+// (per-problem dt lives in device descriptors, so the graph does not depend
+// on it).  The register budget of the kernel (gdg_batch_kernel.cuh) and the
+// resident blocks per SM are picked on the first step by timing the
 // candidates on the batch's own data.
 #include <algorithm>
 #include <cstdio>
@@ -21,204 +22,23 @@
 #include <new>
 #include <vector>
 
-#include "gdg_internal.h"
-#include "gdg_stage_const.cuh"
-#include "gdg_var_kernels.cuh"
+#include "gdg_batch_kernel.cuh"
 
-namespace {
-
-struct BatchProb {
-    int kind;                 // 0 modal route (constant coefficients), 1 element PCG
-    const ModalParams *mp;    // kind 0: device copy of the problem's modal parameters
-    const double *lam2;       // kind 0
-    VarParams vp;             // kind 1
-    StepBuffers sb;
-    double dt;
-};
-
-constexpr int kMaxBatchThreads = 256;
-
-// RK4 stage coefficients and buffer roles of stage STAGE (the same table as
-// the per-problem stage launches)
-template <int STAGE>
-struct StageRoles {
-    double cA, cY;
-    const double *yU, *yV, *trin;
-    double *oU, *oV, *trout;
-    __host__ __device__ StageRoles(const StepBuffers &B, double dt) {
-        if (STAGE == 1) {
-            cA = dt / 6.0; cY = 0.5 * dt; yU = B.nU; yV = B.nV; oU = B.xU; oV = B.xV; trin = B.tr0; trout = B.tr1;
-        } else if (STAGE == 2) {
-            cA = dt / 3.0; cY = 0.5 * dt; yU = B.xU; yV = B.xV; oU = B.yU; oV = B.yV; trin = B.tr1; trout = B.tr0;
-        } else if (STAGE == 3) {
-            cA = dt / 3.0; cY = dt; yU = B.yU; yV = B.yV; oU = B.xU; oV = B.xV; trin = B.tr0; trout = B.tr1;
-        } else {
-            cA = dt / 6.0; cY = 0.0; yU = B.xU; yV = B.xV; oU = nullptr; oV = nullptr; trin = B.tr1; trout = B.tr0;
-        }
-    }
-};
-
-// next work item of the block's queue, broadcast through shared memory
-__device__ __forceinline__ int next_item(unsigned int *counter, int *slot) {
-    if (threadIdx.x == 0) *slot = (int)atomicAdd(counter, 1u);
-    __syncthreads();
-    const int it = *slot;
-    __syncthreads();
-    return it;
-}
-
-// block-wide copy of a parameter struct into shared memory (whole 4-byte words)
-template <typename T>
-__device__ __forceinline__ void copy_to_shared(T *dst, const T *src) {
-    static_assert(sizeof(T) % 4 == 0, "word copy");
-    const unsigned int *s = reinterpret_cast<const unsigned int *>(src);
-    unsigned int *d = reinterpret_cast<unsigned int *>(dst);
-    for (int i = threadIdx.x; i < (int)(sizeof(T) / 4); i += blockDim.x) d[i] = s[i];
-    __syncthreads();
-}
-
-// modal tiles of the constant-coefficient problems
-template <int N1, int STAGE>
-__global__ void __launch_bounds__(kMaxBatchThreads)
-k_batch_modal(const BatchProb *__restrict__ probs, const int2 *__restrict__ items, int n_items,
-              unsigned int *counter) {
-    constexpr int MODE = STAGE == 1 ? M_S1 : (STAGE == 4 ? M_S4 : M_S23);
-    extern __shared__ double smem[];
-    __shared__ int s_item;
-    __shared__ ModalParams s_mp;   // the current problem's parameters (read in every inner loop)
-    int cur = -1;
-    for (int it = next_item(counter, &s_item); it < n_items; it = next_item(counter, &s_item)) {
-        const int2 w = items[it];
-        const BatchProb &P = probs[w.x];
-        if (w.x != cur) {
-            copy_to_shared(&s_mp, P.mp);
-            cur = w.x;
-        }
-        const StageRoles<STAGE> r(P.sb, P.dt);
-        const StageBufs b{r.yU, r.yV, P.sb.nU, P.sb.nV, P.sb.aU, P.sb.aV, r.oU, r.oV, r.trin, r.trout, P.lam2};
-        if (s_mp.alt) stage2p_body<N1, MODE, 1>(s_mp, b, r.cA, r.cY, w.y, smem);
-        else stage2p_body<N1, MODE, 0>(s_mp, b, r.cA, r.cY, w.y, smem);
-        __syncthreads();
-    }
-}
-
-// elements of the variable-coefficient problems (one element PCG per item).
-// The current problem's parameters and buffer table live in shared memory
-// (kernel parameters would sit in the constant bank; in registers they would
-// crowd the PCG loops).
-template <int N1, int STAGE>
-__device__ __forceinline__ void batch_var_item(const BatchProb *__restrict__ probs, int2 w, int &cur,
-                                               VarParams &s_vp, VarBufs &s_b, double *s_c, double *smem) {
-    constexpr int MODE = STAGE == 1 ? M_S1 : (STAGE == 4 ? M_S4 : M_S23);
-    if (w.x != cur) {
-        const BatchProb &P = probs[w.x];
-        copy_to_shared(&s_vp, &P.vp);
-        if (threadIdx.x == 0) {
-            const StageRoles<STAGE> r(P.sb, P.dt);
-            s_b = VarBufs{r.yU, r.yV, P.sb.nU, P.sb.nV, P.sb.aU, P.sb.aV, r.oU, r.oV, r.trin, r.trout};
-            s_c[0] = r.cA;
-            s_c[1] = r.cY;
-        }
-        __syncthreads();
-        cur = w.x;
-    }
-    var_stage_body<N1, MODE>(s_vp, s_b, s_c[0], s_c[1], w.y, smem);
-}
-
-// flat grid: block b takes item b
-template <int N1, int STAGE>
-__global__ void __launch_bounds__(nthreads_for(N1 * N1), kVarMinBlocks)
-k_batch_var(const BatchProb *__restrict__ probs, const int2 *__restrict__ items, int n_items, unsigned int *) {
-    extern __shared__ double smem[];
-    __shared__ VarParams s_vp;
-    __shared__ VarBufs s_b;
-    __shared__ double s_c[2];
-    int cur = -1;
-    if ((int)blockIdx.x < n_items)
-        batch_var_item<N1, STAGE>(probs, items[blockIdx.x], cur, s_vp, s_b, s_c, smem);
-}
-
-// persistent grid: blocks pull items from the queue `counter`
-template <int N1, int STAGE>
-__global__ void __launch_bounds__(nthreads_for(N1 * N1), kVarMinBlocks)
-k_batch_var_q(const BatchProb *__restrict__ probs, const int2 *__restrict__ items, int n_items,
-              unsigned int *counter) {
-    extern __shared__ double smem[];
-    __shared__ int s_item;
-    __shared__ VarParams s_vp;
-    __shared__ VarBufs s_b;
-    __shared__ double s_c[2];
-    int cur = -1;
-    for (int it = next_item(counter, &s_item); it < n_items; it = next_item(counter, &s_item)) {
-        batch_var_item<N1, STAGE>(probs, items[it], cur, s_vp, s_b, s_c, smem);
-        __syncthreads();
-    }
-}
-
-#define GDG_BATCH_CASES(X) X(8) X(9) X(10)
-
-// dynamic shared memory may use the opt-in maximum minus the kernel's own
-// static shared memory (the work-item slot)
-template <typename K>
-cudaError_t raise_smem(K kernel, int lim) {
-    cudaFuncAttributes a;
-    cudaError_t e = cudaFuncGetAttributes(&a, kernel);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lim - (int)a.sharedSizeBytes);
-}
-
-template <int N1>
-cudaError_t set_batch_attrs() {
-    int dev = 0, lim = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&lim, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    cudaError_t e;
-    if ((e = raise_smem(k_batch_modal<N1, 1>, lim)) != cudaSuccess) return e;
-    if ((e = raise_smem(k_batch_modal<N1, 2>, lim)) != cudaSuccess) return e;
-    if ((e = raise_smem(k_batch_modal<N1, 3>, lim)) != cudaSuccess) return e;
-    if ((e = raise_smem(k_batch_modal<N1, 4>, lim)) != cudaSuccess) return e;
-    if ((e = raise_smem(k_var_stage<N1, M_S1>, lim)) != cudaSuccess) return e;
-    if ((e = raise_smem(k_var_stage<N1, M_S23>, lim)) != cudaSuccess) return e;
-    if ((e = raise_smem(k_var_stage<N1, M_S4>, lim)) != cudaSuccess) return e;
-    if ((e = raise_smem(k_batch_var<N1, 1>, lim)) != cudaSuccess) return e;
-    if ((e = raise_smem(k_batch_var<N1, 2>, lim)) != cudaSuccess) return e;
-    if ((e = raise_smem(k_batch_var<N1, 3>, lim)) != cudaSuccess) return e;
-    if ((e = raise_smem(k_batch_var<N1, 4>, lim)) != cudaSuccess) return e;
-    if ((e = raise_smem(k_batch_var_q<N1, 1>, lim)) != cudaSuccess) return e;
-    if ((e = raise_smem(k_batch_var_q<N1, 2>, lim)) != cudaSuccess) return e;
-    if ((e = raise_smem(k_batch_var_q<N1, 3>, lim)) != cudaSuccess) return e;
-    return raise_smem(k_batch_var_q<N1, 4>, lim);
-}
-
-template <int N1, bool VAR>
-void launch_batch_n(int stage, int grid, int threads, size_t smem, const BatchProb *probs, const int2 *items,
-                    int n_items, unsigned int *counter, cudaStream_t s) {
-#define GDG_BK(st) (VAR ? (counter ? k_batch_var_q<N1, st> : k_batch_var<N1, st>) : k_batch_modal<N1, st>)
-    switch (stage) {
-    case 1: GDG_BK(1)<<<grid, threads, smem, s>>>(probs, items, n_items, counter); break;
-    case 2: GDG_BK(2)<<<grid, threads, smem, s>>>(probs, items, n_items, counter); break;
-    case 3: GDG_BK(3)<<<grid, threads, smem, s>>>(probs, items, n_items, counter); break;
-    default: GDG_BK(4)<<<grid, threads, smem, s>>>(probs, items, n_items, counter); break;
-    }
-#undef GDG_BK
-}
-
-}  // namespace
+using namespace gdg_batch_dev;
 
 struct gdg_batch {
     std::vector<gdg_ctx *> ctx;
     int count = 0, n1 = 0, sms = 152;
     BatchProb *d_probs = nullptr;
     ModalParams *d_mps = nullptr;
-    int2 *d_var_items = nullptr, *d_mod_items = nullptr;
-    int n_var = 0, n_mod = 0, mod_cap = 0, mod_tile = -1;
-    unsigned int *d_counters = nullptr;   // per step: [stage 0..3][kind 0 var, 1 modal]
-    size_t var_smem = 0;
-    int var_threads = 0, var_grid = 0;    // PCG launch
-    int mod_threads = 0, mod_grid = 0;    // modal launch (tile = mod_threads / n1)
+    int2 *d_items = nullptr;          // element solves (longest first), then modal tiles
+    int n_items = 0, n_var = 0, n_mod = 0, tile = 0;
+    size_t smem = 0;                  // dynamic shared memory of the launch
+    int variant = BATCH_HI;           // register budget (tuned)
+    int per_sm = 0;                   // resident blocks per SM (tuned)
+    int chunk = 1;                    // consecutive items per turn of a block (tuned)
     bool tuned = false;
-    cudaStream_t cap = nullptr, side = nullptr;
-    cudaEvent_t fork = nullptr, join = nullptr;
+    cudaStream_t cap = nullptr;
     cudaGraphExec_t exec = nullptr;
     int graph_steps = 0;
     std::vector<BatchProb> h_probs;
@@ -233,181 +53,80 @@ int berr(gdg_batch *b, int st, const std::string &m) {
     return st;
 }
 
-size_t modal_smem(int n1, int tile) { return (size_t)tile * (4 * n1 + 2 * n1 * (n1 + 1)) * sizeof(double); }
+const BatchOps batch_ops_hi = batch_ops_of<BATCH_HI>();
 
-int upload_items(gdg_batch *b, const std::vector<int2> &items, int2 **dst, int *cap) {
-    if ((int)items.size() > *cap) {
-        cudaFree(*dst);
-        *dst = nullptr;
-        if (cudaMalloc((void **)dst, std::max<size_t>(1, items.size()) * sizeof(int2)) != cudaSuccess)
-            return berr(b, GDG_ENOMEM, "items");
-        *cap = (int)items.size();
-    }
-    if (!items.empty() &&
-        cudaMemcpy(*dst, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess)
-        return berr(b, GDG_ECUDA, "items upload");
-    return GDG_OK;
+const BatchOps &ops(int variant) {
+    return variant == BATCH_LO ? batch_ops_lo : variant == BATCH_MID ? batch_ops_mid : batch_ops_hi;
 }
 
-// modal work items: tiles of `tile` elements of the constant-coefficient problems
-int build_modal_items(gdg_batch *b, int tile) {
-    if (tile == b->mod_tile) return GDG_OK;
-    std::vector<int2> items;
-    for (int i = 0; i < b->count; ++i)
-        if (b->h_probs[i].kind == 0)
-            for (int t = 0; t * tile < b->ctx[i]->ne; ++t) items.push_back(make_int2(i, t));
-    int st = upload_items(b, items, &b->d_mod_items, &b->mod_cap);
-    if (st) return st;
-    b->n_mod = (int)items.size();
-    b->mod_tile = tile;
-    return GDG_OK;
+int max_resident(const gdg_batch *b, int variant) { return ops(variant).resident(b->n1, b->smem); }
+
+void launch_stage_all(const gdg_batch *b, int stage, cudaStream_t s) {
+    const int grid = b->sms * std::max(1, b->per_sm);
+    ops(b->variant).launch(b->n1, stage, grid, b->smem, b->d_probs, b->d_items, b->n_items, b->chunk, s);
 }
 
-template <typename K>
-int resident_blocks(K kernel, int threads, size_t smem) {
-    int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, smem) != cudaSuccess) return 1;
-    return std::max(1, n);
-}
-
-int max_resident(const gdg_batch *b, bool var, int threads, size_t smem) {
-    switch (b->n1) {
-#define X(n) case n: return var ? resident_blocks(k_batch_var_q<n, 2>, threads, smem) \
-                                : resident_blocks(k_batch_modal<n, 2>, threads, smem);
-        GDG_BATCH_CASES(X)
-#undef X
-    }
-    return 1;
-}
-
-// The element-PCG stage as one launch per variable-coefficient problem: the
-// problem's own stage kernel, its parameters as kernel arguments (no per-block
-// staging), in problem order on one stream.  Same kernel body as the batched
-// launches and as gdg_step.
-template <int N1>
-void launch_var_per_problem_n(const gdg_batch *b, int stage, cudaStream_t s) {
-    constexpr int T = nthreads_for(N1 * N1);
-    for (const BatchProb &P : b->h_probs) {
-        if (P.kind != 1) continue;
-        const size_t sm = StageSmem<N1>::bytes(P.vp.Q, P.vp.mixed, P.vp.inverse);
-        switch (stage) {
-#define GDG_PP(st, mode)                                                                                  \
-    {                                                                                                     \
-        const StageRoles<st> r(P.sb, P.dt);                                                               \
-        const VarBufs vb{r.yU, r.yV, P.sb.nU, P.sb.nV, P.sb.aU, P.sb.aV, r.oU, r.oV, r.trin, r.trout};    \
-        k_var_stage<N1, mode><<<P.vp.ne, T, sm, s>>>(P.vp, vb, r.cA, r.cY);                               \
-    }
-        case 1: GDG_PP(1, M_S1) break;
-        case 2: GDG_PP(2, M_S23) break;
-        case 3: GDG_PP(3, M_S23) break;
-        default: GDG_PP(4, M_S4) break;
-#undef GDG_PP
-        }
-    }
-}
-
-// kind 0: PCG elements; kind 1: modal tiles
-void launch_kind(gdg_batch *b, int kind, int stage, unsigned int *counter, cudaStream_t s) {
-    const bool var = kind == 0;
-    const int n = var ? b->n_var : b->n_mod;
-    if (!n) return;
-    if (var && b->var_grid == -1) {   // one launch per problem
-        switch (b->n1) {
-#define X(n1_) case n1_: launch_var_per_problem_n<n1_>(b, stage, s); break;
-            GDG_BATCH_CASES(X)
-#undef X
-        }
-        return;
-    }
-    const int threads = var ? b->var_threads : b->mod_threads;
-    const int grid = var ? (b->var_grid > 0 ? b->var_grid : n) : b->mod_grid;
-    if (var && b->var_grid <= 0) counter = nullptr;   // flat grid
-    const size_t smem = var ? b->var_smem : modal_smem(b->n1, b->mod_threads / b->n1);
-    const int2 *items = var ? b->d_var_items : b->d_mod_items;
-    switch (b->n1) {
-#define X(n1_)                                                                                          \
-    case n1_:                                                                                          \
-        if (var) launch_batch_n<n1_, true>(stage, grid, threads, smem, b->d_probs, items, n, counter, s);  \
-        else launch_batch_n<n1_, false>(stage, grid, threads, smem, b->d_probs, items, n, counter, s);     \
-        break;
-        GDG_BATCH_CASES(X)
-#undef X
-    }
-}
-
-// one RK4 step: reset the 8 queue counters, then per stage the two launches
-// on two streams, joined before the next stage
 void enqueue_steps(gdg_batch *b, int nsteps, cudaStream_t s) {
-    for (int i = 0; i < nsteps; ++i) {
-        cudaMemsetAsync(b->d_counters, 0, 8 * sizeof(unsigned int), s);
-        for (int st = 1; st <= 4; ++st) {
-            cudaEventRecord(b->fork, s);
-            cudaStreamWaitEvent(b->side, b->fork, 0);
-            launch_kind(b, 0, st, b->d_counters + 2 * (st - 1), s);
-            launch_kind(b, 1, st, b->d_counters + 2 * (st - 1) + 1, b->side);
-            cudaEventRecord(b->join, b->side);
-            cudaStreamWaitEvent(s, b->join, 0);
-        }
-    }
+    for (int i = 0; i < nsteps; ++i)
+        for (int st = 1; st <= 4; ++st) launch_stage_all(b, st, s);
 }
 
-float time_launch(gdg_batch *b, int kind, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
-    float ms = 0.f;
+// best of two stage-1 launches of the current shape (stage 1 reads y_n and
+// its traces and writes only buffers that the real step rewrites)
+float time_stage1(gdg_batch *b, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
+    float t = 1e30f;
     for (int rep = 0; rep < 2; ++rep) {
-        cudaMemsetAsync(b->d_counters, 0, 8 * sizeof(unsigned int), s);
+        float ms = 0.f;
         cudaEventRecord(e0, s);
-        launch_kind(b, kind, 1, b->d_counters + kind, s);
+        launch_stage_all(b, 1, s);
         cudaEventRecord(e1, s);
         cudaEventSynchronize(e1);
         cudaEventElapsedTime(&ms, e0, e1);
+        t = std::min(t, ms);
     }
-    return cudaGetLastError() == cudaSuccess ? ms : 1e30f;
+    return t;
 }
 
-// Time the candidates on the batch's own stage-1 work (stage 1 reads y_n and
-// its traces and writes only buffers that the real step rewrites).
+// Time the candidates on the batch's own stage-1 work: every register budget
+// x resident blocks per SM with one item per turn (each budget scanned from
+// its most resident blocks down, left once a candidate is 10 % slower than
+// that budget's best so far), then 2, 4 and 8 items per turn on the best.
 int autotune(gdg_batch *b, cudaStream_t s) {
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    int st = GDG_OK;
-    if (b->n_var) {   // PCG launch: flat grid, persistent with 1..occupancy-limit blocks per SM, or per problem
-        const int maxr = max_resident(b, true, b->var_threads, b->var_smem);
-        b->var_grid = 0;
-        float best = time_launch(b, 0, s, e0, e1);
-        int best_g = 0;
-        for (int r = 1; r <= maxr; ++r) {
-            b->var_grid = b->sms * r;
-            const float ms = time_launch(b, 0, s, e0, e1);
-            if (ms < best) { best = ms; best_g = b->var_grid; }
+    float best = 1e30f;
+    int best_r = 0, best_v = BATCH_HI, best_c = 1;
+    b->chunk = 1;
+    for (int v = 0; v < BATCH_VARIANTS; ++v) {
+        const int maxr = max_resident(b, v);
+        float vbest = 1e30f;
+        for (int r = maxr; r >= 1; --r) {
+            b->variant = v;
+            b->per_sm = r;
+            const float t = time_stage1(b, s, e0, e1);
+            if (t < best) { best = t; best_r = r; best_v = v; }
+            if (t < vbest) vbest = t;
+            else if (t > 1.1f * vbest) break;
         }
-        b->var_grid = -1;
-        if (time_launch(b, 0, s, e0, e1) < best) best_g = -1;
-        b->var_grid = best_g;
     }
-    bool any_modal = false;
-    for (const BatchProb &P : b->h_probs) any_modal |= P.kind == 0;
-    if (any_modal) {  // modal tile: elements per block
-        float best = 1e30f;
-        int best_t = 0;
-        for (int tile : {4, 7, 10, 14, 21, 28}) {
-            const int threads = tile * b->n1;
-            if (threads > kMaxBatchThreads) continue;
-            if ((st = build_modal_items(b, tile))) break;
-            b->mod_threads = threads;
-            b->mod_grid = b->sms * max_resident(b, false, threads, modal_smem(b->n1, tile));
-            const float ms = time_launch(b, 1, s, e0, e1);
-            if (ms < best) { best = ms; best_t = tile; }
-        }
-        if (!st && best_t) {
-            st = build_modal_items(b, best_t);
-            b->mod_threads = best_t * b->n1;
-            b->mod_grid = b->sms * max_resident(b, false, b->mod_threads, modal_smem(b->n1, best_t));
+    if (best_r >= 1) {
+        b->variant = best_v;
+        b->per_sm = best_r;
+        for (int c : {2, 4, 8}) {
+            b->chunk = c;
+            const float t = time_stage1(b, s, e0, e1);
+            if (t < best) { best = t; best_c = c; }
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (st) return st;
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return berr(b, GDG_ECUDA, std::string("tuning: ") + cudaGetErrorString(e));
+    if (best_r < 1) return berr(b, GDG_ENOMEM, "no launch shape fits the shared memory of the batch's element solves");
+    b->variant = best_v;
+    b->per_sm = best_r;
+    b->chunk = best_c;
     b->tuned = true;
     return GDG_OK;
 }
@@ -419,14 +138,9 @@ extern "C" int gdg_batch_destroy(gdg_batch *b) {
     cudaDeviceSynchronize();
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->cap) cudaStreamDestroy(b->cap);
-    if (b->side) cudaStreamDestroy(b->side);
-    if (b->fork) cudaEventDestroy(b->fork);
-    if (b->join) cudaEventDestroy(b->join);
     cudaFree(b->d_probs);
     cudaFree(b->d_mps);
-    cudaFree(b->d_var_items);
-    cudaFree(b->d_mod_items);
-    cudaFree(b->d_counters);
+    cudaFree(b->d_items);
     for (gdg_ctx *c : b->ctx) gdg_destroy(c);
     delete b;
     return GDG_OK;
@@ -451,8 +165,10 @@ extern "C" int gdg_batch_create(const gdg_problem *pbs, int count, gdg_batch **o
     cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
     b->ctx.assign(count, nullptr);
     b->h_probs.resize(count);
+    b->tile = batch_tile(b->n1);   // modal elements per item (half-line body: blockDim / (2 N1))
+    b->smem = batch_modal_doubles(b->n1) * sizeof(double) + sizeof(ModalParams);
     std::vector<ModalParams> mps(count);
-    std::vector<int2> var_items;
+    std::vector<int2> var_items, mod_items;
     for (int i = 0; i < count; ++i) {
         if ((st = gdg_create(&pbs[i], &b->ctx[i]))) { gdg_batch_destroy(b); return st; }
         gdg_ctx *c = b->ctx[i];
@@ -464,47 +180,50 @@ extern "C" int gdg_batch_create(const gdg_problem *pbs, int count, gdg_batch **o
             P.lam2 = c->d_lam2;
             P.sb = gdg_const_buffers(c);
             mps[i] = c->mp;
+            for (int t = 0; t * b->tile < c->ne; ++t) mod_items.push_back(make_int2(i, t));
         } else {
             P.kind = 1;
             P.vp = c->var->vp;
             P.sb = gdg_var_buffers(c);
-            b->var_smem = std::max(b->var_smem, c->var->smem_stage);
+            b->smem = std::max(b->smem, c->var->smem_stage);
             for (int e = 0; e < c->ne; ++e) var_items.push_back(make_int2(i, e));
         }
     }
-    // longest items first (higher order: more quadrature points per face), so
-    // that the last blocks of a stage are short ones
+    // longest items first (higher order: more quadrature points per face, more
+    // PCG work), so that the last items of a stage are short ones
     std::stable_sort(var_items.begin(), var_items.end(), [&](const int2 &a, const int2 &c) {
         return pbs[a.x].p > pbs[c.x].p;
     });
-    int cap = 0;
+    b->n_var = (int)var_items.size();
+    b->n_mod = (int)mod_items.size();
+    // the modal tiles last: short items even out the blocks' ends of the stage
+    // (spreading them evenly among the element solves instead measured 1-2 %
+    // slower: every switch restages a problem's parameters)
+    std::vector<int2> items(var_items);
+    items.insert(items.end(), mod_items.begin(), mod_items.end());
+    b->n_items = (int)items.size();
     if (cudaMalloc((void **)&b->d_mps, count * sizeof(ModalParams)) != cudaSuccess ||
         cudaMalloc((void **)&b->d_probs, count * sizeof(BatchProb)) != cudaSuccess ||
-        cudaMalloc((void **)&b->d_counters, 8 * sizeof(unsigned int)) != cudaSuccess ||
-        upload_items(b, var_items, &b->d_var_items, &cap)) {
+        cudaMalloc((void **)&b->d_items, std::max<size_t>(1, items.size()) * sizeof(int2)) != cudaSuccess) {
         gdg_batch_destroy(b);
         return GDG_ENOMEM;
     }
-    b->n_var = (int)var_items.size();
-    b->var_threads = nthreads_for(b->n1 * b->n1);
     for (int i = 0; i < count; ++i)
         if (b->h_probs[i].kind == 0) b->h_probs[i].mp = b->d_mps + i;
-    cudaMemcpy(b->d_mps, mps.data(), count * sizeof(ModalParams), cudaMemcpyHostToDevice);
-    cudaMemcpy(b->d_probs, b->h_probs.data(), count * sizeof(BatchProb), cudaMemcpyHostToDevice);
-    cudaError_t ae = cudaSuccess;
-    switch (b->n1) {
-#define X(n) case n: ae = set_batch_attrs<n>(); break;
-        GDG_BATCH_CASES(X)
-#undef X
+    if (cudaMemcpy(b->d_mps, mps.data(), count * sizeof(ModalParams), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b->d_probs, b->h_probs.data(), count * sizeof(BatchProb), cudaMemcpyHostToDevice) != cudaSuccess ||
+        (!items.empty() &&
+         cudaMemcpy(b->d_items, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess)) {
+        gdg_batch_destroy(b);
+        return berr(nullptr, GDG_ECUDA, "upload");
     }
+    cudaError_t ae = cudaSuccess;
+    for (int v = 0; v < BATCH_VARIANTS && ae == cudaSuccess; ++v) ae = ops(v).attrs(b->n1);
     if (ae != cudaSuccess) {
         gdg_batch_destroy(b);
         return berr(nullptr, GDG_ECUDA, std::string("kernel attributes: ") + cudaGetErrorString(ae));
     }
-    if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming) != cudaSuccess) {
+    if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) {
         gdg_batch_destroy(b);
         return GDG_ECUDA;
     }
@@ -537,7 +256,14 @@ extern "C" int gdg_batch_step(gdg_batch *b, double *const *u, double *const *v, 
         st = c->pb.coef == GDG_COEF_CONST ? gdg_const_enter(c, u[i], v[i], s) : gdg_var_enter(c, u[i], v[i], s);
         if (st) return berr(b, st, "enter: " + c->err);
     }
-    if (!b->tuned && (st = autotune(b, s))) return st;
+    if (!b->tuned) {
+        if (b->exec) {   // re-tuning after gdg_batch_set_tuning(.., 0): the graph holds the old shape
+            cudaGraphExecDestroy(b->exec);
+            b->exec = nullptr;
+            b->graph_steps = 0;
+        }
+        if ((st = autotune(b, s))) return st;
+    }
     // graph of G steps, replayed
     const int G = 4;
     if (nsteps >= G) {
@@ -565,13 +291,35 @@ extern "C" int gdg_batch_step(gdg_batch *b, double *const *u, double *const *v, 
     return e == cudaSuccess ? GDG_OK : berr(b, GDG_ECUDA, cudaGetErrorString(e));
 }
 
-extern "C" int gdg_batch_tuning(const gdg_batch *b, int *threads_per_block, int *blocks_per_sm, int *tile_elements) {
+extern "C" int gdg_batch_tuning(const gdg_batch *b, int *threads_per_block, int *blocks_per_sm, int *tile_elements,
+                                int *register_budget, int *registers_per_thread, int *items_per_turn) {
     if (!b) return GDG_EINVAL;
-    const bool mod = b->tuned && b->n_mod > 0, var = b->tuned && b->n_var > 0;
-    if (threads_per_block) *threads_per_block = mod ? b->mod_threads : 0;
-    if (blocks_per_sm)
-        *blocks_per_sm = var && b->sms && b->var_grid > 0 ? b->var_grid / b->sms : (var ? (b->var_grid == -1 ? -2 : -1) : 0);
-    if (tile_elements) *tile_elements = mod ? b->mod_tile : 0;
+    if (threads_per_block) *threads_per_block = b->tuned ? nthreads_for(b->n1 * b->n1) : 0;
+    if (blocks_per_sm) *blocks_per_sm = b->tuned ? b->per_sm : 0;
+    if (tile_elements) *tile_elements = b->tuned && b->n_mod > 0 ? b->tile : 0;
+    if (register_budget) *register_budget = b->tuned ? b->variant : 0;
+    if (registers_per_thread) *registers_per_thread = b->tuned ? ops(b->variant).regs(b->n1) : 0;
+    if (items_per_turn) *items_per_turn = b->tuned ? b->chunk : 0;
+    return GDG_OK;
+}
+
+extern "C" int gdg_batch_set_tuning(gdg_batch *b, int register_budget, int blocks_per_sm, int items_per_turn) {
+    if (!b || register_budget < 0 || register_budget >= BATCH_VARIANTS || blocks_per_sm < 0 || items_per_turn < 1)
+        return GDG_EINVAL;
+    if (blocks_per_sm == 0) {   // back to the tuner at the next step
+        b->tuned = false;
+        return GDG_OK;
+    }
+    if (blocks_per_sm > max_resident(b, register_budget))
+        return berr(b, GDG_EINVAL, "more blocks per SM than registers and shared memory allow");
+    cudaDeviceSynchronize();
+    if (b->exec) cudaGraphExecDestroy(b->exec);   // the graph holds the old launch shape
+    b->exec = nullptr;
+    b->graph_steps = 0;
+    b->variant = register_budget;
+    b->per_sm = blocks_per_sm;
+    b->chunk = items_per_turn;
+    b->tuned = true;
     return GDG_OK;
 }
 

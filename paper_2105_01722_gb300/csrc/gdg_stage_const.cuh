@@ -227,7 +227,10 @@ __device__ __forceinline__ unsigned pair_mask() {
     return lanes >= 32 ? 0xffffffffu : ((1u << lanes) - 1u);
 }
 
-template <int N1, int MODE>
+// LEAN: y_n and the RK accumulator are read where the update uses them
+// instead of with the stage input (same operations and results; 40 fewer
+// live registers at S23 / S4, for kernels held to a low register count).
+template <int N1, int MODE, bool LEAN = false>
 __device__ __forceinline__ void stage2h_body(const ModalParams &mp, const StageBufs &b, double cA, double cY,
                                              int etile, double *smem) {
     constexpr int NE = (N1 + 1) / 2;   // even modes; the odd half has N1 - NE <= NE entries
@@ -253,7 +256,7 @@ __device__ __forceinline__ void stage2h_body(const ModalParams &mp, const StageB
             if (kk < nk) {
                 Ru[kk] = b.yU[row + kk];
                 Rv[kk] = b.yV[row + kk];
-                if (MODE == M_S23 || MODE == M_S4) {
+                if (!LEAN && (MODE == M_S23 || MODE == M_S4)) {
                     Nu[kk] = b.nU[row + kk];
                     Nv[kk] = b.nV[row + kk];
                     Au[kk] = b.aU[row + kk];
@@ -332,6 +335,12 @@ __device__ __forceinline__ void stage2h_body(const ModalParams &mp, const StageB
                 const double rv = fma(L0[kk], Yu, fma(cex[kk], xq, cey * FQ[kk]));
                 const double kv = rv;
                 const size_t o = row + kk;
+                if (LEAN && (MODE == M_S23 || MODE == M_S4)) {
+                    Nu[kk] = b.nU[o];
+                    Nv[kk] = b.nV[o];
+                    Au[kk] = b.aU[o];
+                    Av[kk] = b.aV[o];
+                }
                 if (MODE == M_RHS) {
                     b.oU[o] = ku;
                     b.oV[o] = kv;

@@ -83,7 +83,8 @@ EXPORTS = {
     "gdg_batch_state_len": (ctypes.c_longlong, [ctypes.c_void_p, ctypes.c_int]),
     "gdg_batch_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
                                       ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_void_p]),
-    "gdg_batch_tuning": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.POINTER(ctypes.c_int)] * 3),
+    "gdg_batch_tuning": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.POINTER(ctypes.c_int)] * 6),
+    "gdg_batch_set_tuning": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "gdg_batch_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(PcgStats),
                                        ctypes.POINTER(PcgStats)]),
     "gdg_rhs_static": (ctypes.c_int, [ctypes.POINTER(Problem)] + [ctypes.c_void_p] * 5),
@@ -414,9 +415,16 @@ class Batch:
             raise GdgError(st, "gdg_batch_step")
 
     def tuning(self):
-        t, b, e = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
-        lib().gdg_batch_tuning(self._h, ctypes.byref(t), ctypes.byref(b), ctypes.byref(e))
-        return dict(threads_per_block=t.value, blocks_per_sm=b.value, tile_elements=e.value)
+        t, b, e, g, r, c = (ctypes.c_int() for _ in range(6))
+        lib().gdg_batch_tuning(self._h, *(ctypes.byref(x) for x in (t, b, e, g, r, c)))
+        return dict(threads_per_block=t.value, blocks_per_sm=b.value, tile_elements=e.value,
+                    register_budget=g.value, registers_per_thread=r.value, items_per_turn=c.value)
+
+    def set_tuning(self, register_budget, blocks_per_sm, items_per_turn=1):
+        """Pin the launch shape (blocks_per_sm = 0: tune again at the next step)."""
+        st = lib().gdg_batch_set_tuning(self._h, register_budget, blocks_per_sm, items_per_turn)
+        if st != OK:
+            raise GdgError(st, "gdg_batch_set_tuning")
 
     def stats(self, i):
         su, sv = PcgStats(), PcgStats()

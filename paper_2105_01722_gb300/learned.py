@@ -38,8 +38,10 @@ def problem(n, N, p, seed, rtol=1e-10, maxit=200, precision=gdg.FP64):
     return pb, X, Y, dt
 
 
-def generate(rows, n=16, N=8, p=5, seed0=1000, snapshots=4, substeps=6, device="cuda"):
-    """About `rows` training rows (features X [M,162], targets T [M,81], FP32)."""
+def generate(rows, n=16, N=8, p=5, seed0=1000, snapshots=4, substeps=6, device="cuda", per_snapshot=None):
+    """About `rows` training rows (features X [M,162], targets T [M,81], FP32);
+    per_snapshot: keep a seeded random subset of at most that many elements
+    of each snapshot (more c^2 fields for the same number of rows)."""
     import torch
     Xs, Ts = [], []
     total, k = 0, 0
@@ -64,10 +66,13 @@ def generate(rows, n=16, N=8, p=5, seed0=1000, snapshots=4, substeps=6, device="
             Tr = torch.empty(ne * gdg.MLP_OUT, dtype=torch.float32, device=device)
             ctx.mlp_rows(ru, y, Xr, Tr)
             Xr, Tr = Xr.view(ne, -1), Tr.view(ne, -1)
-            keep = Xr[:, gdg.MLP_OUT:].abs().sum(dim=1) > 0     # elements with r_u = 0 carry no signal
+            keep = torch.nonzero(Xr[:, gdg.MLP_OUT:].abs().sum(dim=1) > 0).flatten()   # r_u = 0: no signal
+            if per_snapshot is not None and keep.numel() > per_snapshot:
+                pick = np.sort(rng.choice(keep.numel(), size=per_snapshot, replace=False))
+                keep = keep[torch.tensor(pick, device=keep.device)]
             Xs.append(Xr[keep])
             Ts.append(Tr[keep])
-            total += int(keep.sum())
+            total += int(keep.numel())
         ctx.close()
     return torch.cat(Xs)[:rows].contiguous(), torch.cat(Ts)[:rows].contiguous()
 

@@ -1,7 +1,8 @@
-"""Batched persistent launch (gdg_batch_*): every problem of a batch ends
-exactly where its own gdg_step takes it (the stage bodies are shared), for
-modal and PCG problems, p = 3, 5, 7, FP64 and mixed precision, through the
-graph path and the remainder; the tuner reports its choice; and every
+"""Batched persistent launch (gdg_batch_*: one launch per RK stage over every
+problem): every problem of a batch ends exactly where its own gdg_step takes
+it (the stage bodies are shared), for modal and PCG problems, p = 3, 5, 7,
+FP64 and mixed precision, through the graph path and the remainder; the
+tuner reports its choice; and every
 problem of a mixed batch matches the FP64 oracle's RK4 (FP64 PCG, mixed
 precision and element-inverse forms)."""
 import numpy as np
@@ -54,9 +55,9 @@ def test_batch_equals_individual_steps(precision):
     dts = [b[2] for b in built]
     batch.step(us, vs, dts, 7)       # one graph of 4 steps + 3 direct steps
     tun = batch.tuning()
-    assert tun["tile_elements"] in (4, 7, 10, 14, 21, 28)
-    assert tun["threads_per_block"] == 9 * tun["tile_elements"]
-    assert tun["blocks_per_sm"] in (-1, -2) or tun["blocks_per_sm"] >= 1
+    assert tun["threads_per_block"] == 96                       # one element block (81 nodes) per CTA
+    assert tun["tile_elements"] == 96 // 18                     # half-line modal body: two threads per line
+    assert tun["blocks_per_sm"] >= 1 and 0 < tun["registers_per_thread"] <= 255
     for i, (pb, U0, dt) in enumerate(built):
         ctx = gdg.Context(pb)
         u = torch.tensor(U0, device="cuda")
@@ -73,6 +74,39 @@ def test_batch_equals_individual_steps(precision):
     # a second call with new step sizes reuses the graph and the tuning
     batch.step(us, vs, [0.5 * d for d in dts], 4)
     assert batch.tuning() == tun
+    batch.close()
+
+
+def test_every_launch_shape_gives_the_same_steps():
+    """The launch shape (register budget, resident blocks, items per turn)
+    only decides which block runs which item: every pinned shape reproduces
+    the tuned batch's steps bit for bit."""
+    specs = _specs(6, 4, 10)
+    built = [_problem(s, precision=gdg.MIXED) for s in specs]
+    batch = gdg.Batch([b[0] for b in built])
+    dts = [b[2] for b in built]
+
+    def run():
+        us = [torch.tensor(b[1], device="cuda") for b in built]
+        vs = [torch.zeros_like(u) for u in us]
+        batch.step(us, vs, dts, 5)
+        return [torch.cat([u, v]).cpu().numpy() for u, v in zip(us, vs)]
+
+    ref = run()
+    tun = batch.tuning()
+    assert tun["register_budget"] in (0, 1, 2) and tun["items_per_turn"] in (1, 2, 4, 8)
+    for budget, r, chunk in ((0, 1, 1), (1, 2, 3), (2, 3, 8), (2, 1, 1000)):
+        batch.set_tuning(budget, r, chunk)
+        assert batch.tuning()["blocks_per_sm"] == r and batch.tuning()["items_per_turn"] == chunk
+        for a, b in zip(run(), ref):
+            assert np.array_equal(a, b)
+    with pytest.raises(gdg.GdgError):
+        batch.set_tuning(0, 64, 1)        # more blocks than fit
+    with pytest.raises(gdg.GdgError):
+        batch.set_tuning(3, 1, 1)
+    batch.set_tuning(0, 0, 1)             # back to the tuner
+    for a, b in zip(run(), ref):
+        assert np.array_equal(a, b)
     batch.close()
 
 

@@ -208,3 +208,63 @@ def test_training_lowers_loss_and_guess_stays_exact():
     # adds dt |k| <= 2.8 |y| of them (RK4 stability interval), 12 steps, two
     # runs; kappa <= 1e4 for these p = 5 elements (c^2 in [1/2, 2])
     assert np.linalg.norm(a - b) <= 2 * 12 * 2.8 * 1e4 * 1e-10 * np.linalg.norm(b)
+    _guess_quality_study(net)
+
+
+def _guess_quality_study(net):
+    """How good the trained guesses are, element by element, on an unseen
+    12 x 12 mesh (the training meshes' element size: the constraint row w of
+    A scales with the element area, so the network does not carry over to
+    other sizes): the A-norm error of the guess against the exact solution of
+    each u_t system (A = S_c2 + w w^T, the oracle's matrices), and the FP64
+    PCG iterations (frozen-coefficient preconditioner, rtol 1e-10, the
+    oracle's PCG) from 0 and from the guess (with the library's fallback to 0
+    when the guess's residual is not below ||r_u||).  Printed as percentiles
+    and an iteration histogram; the assertions record the measured outcome."""
+    n, seed = 12, 4242
+    pb, Xn, Yn, dt = learned.problem(n, 8, 5, seed=seed, rtol=1e-10)
+    ctx = gdg.Context(pb)
+    u = torch.tensor(inputs.gaussian_pulse(Xn, Yn, 0.5, 0.45, 0.1).ravel(), device="cuda")
+    v = torch.zeros_like(u)
+    ctx.step(u, v, 0.0, dt, 6)
+    ru, rv = torch.empty_like(u), torch.empty_like(u)
+    ctx.residuals(u, v, ru, rv)
+    ne = n * n
+    Xr = torch.empty(ne * gdg.MLP_IN, dtype=torch.float32, device="cuda")
+    ctx.mlp_rows(ru, None, Xr, None)
+    G = torch.empty(ne, gdg.MLP_OUT, dtype=torch.float32, device="cuda")
+    net.forward(Xr.view(ne, -1), G)
+    ctx.close()
+    R = ru.cpu().numpy().reshape(ne, 81)
+    G = G.cpu().numpy().astype(np.float64)
+    vp = dv.VarProblem(n=(n, n), N=8, p=5, X=Xn, Y=Yn, C2=inputs.smooth_random_c2(Xn, Yn, seed))
+    ops = dv.assemble(vp)
+    Psi, lam = dv.reference_diagonalisation(5, 8)
+    errs, it0, itg = [], [], []
+    for e in range(ne):
+        nr = np.linalg.norm(R[e])
+        if nr == 0:
+            continue
+        A = dv.spd_u_matrix(ops, e)
+        y = np.linalg.solve(A, R[e])
+        x0 = nr * G[e]
+        d = x0 - y
+        errs.append(np.sqrt(d @ A @ d / (y @ A @ y)))
+        P = dv.fdm_preconditioner(ops, e, "S", Psi, lam)
+        _, k0, _ = dv.pcg(A, R[e], lambda r: P @ r, None, 1e-10, 200)
+        start = x0 if np.linalg.norm(R[e] - A @ x0) < nr else None
+        _, kg, _ = dv.pcg(A, R[e], lambda r: P @ r, start, 1e-10, 200)
+        it0.append(k0)
+        itg.append(kg)
+    errs, it0, itg = np.array(errs), np.array(it0), np.array(itg)
+    hist = lambda k: dict(zip(*np.unique(k, return_counts=True)))
+    print("guess A-norm rel. error: p10 %.3f  p50 %.3f  p90 %.3f  max %.3f" %
+          (np.percentile(errs, 10), np.percentile(errs, 50), np.percentile(errs, 90), errs.max()))
+    print("PCG iterations from 0: %s mean %.2f; from the guess: %s mean %.2f" %
+          (hist(it0), it0.mean(), hist(itg), itg.mean()))
+    # measured (one GB300): A-norm error p10 0.81, median 0.98, p90 1.39 (the
+    # preconditioner's first step alone reaches about 0.06); mean iterations
+    # 9.36 from zero, 9.41 from the guess (where its residual is not below
+    # ||r_u|| the library starts from zero instead)
+    assert np.median(errs) > 0.1
+    assert np.abs(itg - it0).max() <= 2 and abs(itg.mean() - it0.mean()) < 0.75

@@ -539,18 +539,19 @@ def forms_three_d(n=32, N=8, p=5, steps=16):
             "energy_ratio_after_20_steps": E1 / E0}
 
 
-def forms_batched(steps=8):
-    """48 independent problems (seeds 20210501+i, n ~ U{16..128}, p in {3,5,7},
-    alternating constant / smooth random c^2): one batch (persistent launches,
-    graph, tuned) against stepping each problem with its own gdg_step; the
-    variable-coefficient problems by FP64 PCG, mixed PCG or element inverses."""
+def forms_batched(steps=8, nmin=16, nmax=128):
+    """48 independent problems (seeds 20210501+i, n ~ U{nmin..nmax}, p in
+    {3,5,7}, alternating constant / smooth random c^2): one batch (persistent
+    launches, graph, tuned) against stepping each problem with its own
+    gdg_step; the variable-coefficient problems by FP64 PCG, mixed PCG or
+    element inverses."""
     import numpy as np
     import torch
     from paper_2105_01722_gb300 import gdg, inputs
-    specs = inputs.batched_problems(48)
+    specs = inputs.batched_problems(48, nmin=nmin, nmax=nmax)
     cfl = {3: 0.2, 5: 0.15, 7: 0.12}
     dof = sum(sp["n"] ** 2 * 81 for sp in specs)
-    out = {"problems": 48, "dof": dof}
+    out = {"problems": 48, "n_range": [nmin, nmax], "dof": dof}
     for prec, solver, name in ((gdg.FP64, gdg.SOLVE_PCG, "fp64"), (gdg.MIXED, gdg.SOLVE_PCG, "mixed"),
                                (gdg.FP64, gdg.SOLVE_INVERSE, "inverse")):
         built = []
@@ -783,6 +784,7 @@ def run_gdg(args):
         forms = {}
         if not args.no_forms and world == 1:
             for key, fn in (("variable_mapped_128", forms_variable), ("batched_48", forms_batched),
+                            ("batched_48_small", lambda: forms_batched(nmin=8, nmax=24)),
                             ("learned_guess", forms_learned), ("three_d_32", forms_three_d),
                             ("ocean_channel", forms_ocean)):
                 try:

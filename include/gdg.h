@@ -531,6 +531,33 @@ int gdg_rhs_static(const gdg_problem *pb, const double *u, const double *v, doub
  */
 int gdg_probe_fp64(int iters, double *sink, double *flops, void *stream);
 
+/* ---- index checks of the debug build ---------------------------------- */
+/*
+ * The library built with -DGDG_CHECKS=1 (libgdg_checks.so, build.build(checks=True);
+ * the binding loads it when the environment has GDG_CHECKS=1) checks every
+ * element index a kernel derives from another one: the face neighbours of
+ * the stage kernels (1-D, 2-D, 3-D, variable coefficients), the neighbour
+ * blocks of the persistent step and the work items of the batched launch.
+ * A failed check does not trap: it is counted, the first one is recorded
+ * (site, index, violated bound) and the index is replaced by a valid one, so
+ * the kernel completes with a wrong result and the host reads the record.
+ *
+ * gdg_check_status: synchronises the device, returns the failures since the
+ * last reset (count, and site / index / bound of the first one; any pointer
+ * may be NULL) and, with reset != 0, zeroes them.  Sites: 1-4 one-line 2-D
+ * modal body, 5-8 half-line body, 9-12 generic 2-D stage, 13-16 field-split
+ * stage, 17-20 persistent step (x-, x+, y-, y+), 21 persistent step's
+ * neighbour block, 22-23 1-D stage, 30-35 3-D stages (x-, x+, y-, y+, z-, z+),
+ * 40 variable-coefficient face neighbour, 50 batched item's problem, 51
+ * batched item's element or tile, 99 self-test.
+ * gdg_check_selftest: checks `index` against [0, bound) in a one-thread
+ * kernel on `stream` (a failing pair records site 99): the recording path
+ * itself, without an out-of-range access anywhere.
+ * Errors: GDG_EUNSUPPORTED in the ordinary build (outputs zeroed).
+ */
+int gdg_check_status(long long *count, int *site, long long *index, long long *bound, int reset);
+int gdg_check_selftest(long long index, long long bound, void *stream);
+
 /* Kernel kinds reported by gdg_profile_read. */
 enum {
     GDG_K_STAGE = 0,      /* fused RK-stage kernel (fluxes, lifts, solves, combine, traces) */

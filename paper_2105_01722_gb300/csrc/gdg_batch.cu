@@ -63,7 +63,7 @@ int max_resident(const gdg_batch *b, int variant) { return ops(variant).resident
 
 void launch_stage_all(const gdg_batch *b, int stage, cudaStream_t s) {
     const int grid = b->sms * std::max(1, b->per_sm);
-    ops(b->variant).launch(b->n1, stage, grid, b->smem, b->d_probs, b->d_items, b->n_items, b->chunk, s);
+    ops(b->variant).launch(b->n1, stage, grid, b->smem, b->d_probs, b->count, b->d_items, b->n_items, b->chunk, s);
 }
 
 void enqueue_steps(gdg_batch *b, int nsteps, cudaStream_t s) {
@@ -326,4 +326,17 @@ extern "C" int gdg_batch_set_tuning(gdg_batch *b, int register_budget, int block
 extern "C" int gdg_batch_stats(gdg_batch *b, int i, gdg_pcg_stats *u_sys, gdg_pcg_stats *v_sys) {
     if (!b || i < 0 || i >= b->count) return GDG_EINVAL;
     return gdg_step_stats(b->ctx[i], u_sys, v_sys);
+}
+
+// the check slots of the three budgets' translation units (gdg_checks.cuh)
+int gdg_checks_read_batch(GdgCheckSlot *out, int reset) {
+    GdgCheckSlot acc{};
+    for (int v = 0; v < BATCH_VARIANTS; ++v) {
+        GdgCheckSlot s{};
+        if (ops(v).checks(&s, reset)) return -1;
+        if (s.count && !acc.count) acc = s;
+        else acc.count += s.count;
+    }
+    *out = acc;
+    return 0;
 }

@@ -17,6 +17,7 @@
 //                                 accumulator where it uses them (LEAN).
 #pragma once
 
+#include "gdg_checks.cuh"
 #include "gdg_internal.h"
 #include "gdg_stage_const.cuh"
 #include "gdg_var_kernels.cuh"
@@ -131,7 +132,8 @@ __host__ __device__ constexpr int batch_min_blocks(int n1, int variant) {
 // small problems and a coarser tail.
 template <int N1, int STAGE, int VARIANT>
 __global__ void __launch_bounds__(nthreads_for(N1 * N1), batch_min_blocks(N1, VARIANT))
-k_batch_all(const BatchProb *__restrict__ probs, const int2 *__restrict__ items, int n_items, int chunk) {
+k_batch_all(const BatchProb *__restrict__ probs, int n_probs, const int2 *__restrict__ items, int n_items,
+            int chunk) {
     extern __shared__ double smem[];
     __shared__ VarParams s_vp;
     __shared__ VarBufs s_b;
@@ -139,8 +141,11 @@ k_batch_all(const BatchProb *__restrict__ probs, const int2 *__restrict__ items,
     int cur_var = -1, cur_mod = -1;
     for (long long it0 = (long long)blockIdx.x * chunk; it0 < n_items; it0 += (long long)gridDim.x * chunk)
     for (int it = (int)it0; it < n_items && it < it0 + chunk; ++it) {
-        const int2 w = items[it];
+        int2 w = items[it];
+        GDG_CHECK_INDEX(w.x, 0, n_probs, GDG_SITE_BATCH_PROBLEM, 0);
         const BatchProb &P = probs[w.x];
+        GDG_CHECK_INDEX(w.y, 0, P.kind == 1 ? P.vp.ne : (P.mp->ne + batch_tile(N1) - 1) / batch_tile(N1),
+                        GDG_SITE_BATCH_ELEMENT, 0);
         if (P.kind == 1) {
             batch_var_item<N1, STAGE>(probs, w, cur_var, s_vp, s_b, s_c, smem);
             cur_mod = -1;   // the element solve overwrote the staged ModalParams
@@ -211,20 +216,20 @@ struct BatchVariant {
         return a.numRegs;
     }
     template <int N1>
-    static void launch_n(int stage, int grid, size_t smem, const BatchProb *probs, const int2 *items, int n_items,
-                         int chunk, cudaStream_t s) {
+    static void launch_n(int stage, int grid, size_t smem, const BatchProb *probs, int n_probs, const int2 *items,
+                         int n_items, int chunk, cudaStream_t s) {
         constexpr int T = nthreads_for(N1 * N1);
         switch (stage) {
-        case 1: k_batch_all<N1, 1, VARIANT><<<grid, T, smem, s>>>(probs, items, n_items, chunk); break;
-        case 2: k_batch_all<N1, 2, VARIANT><<<grid, T, smem, s>>>(probs, items, n_items, chunk); break;
-        case 3: k_batch_all<N1, 3, VARIANT><<<grid, T, smem, s>>>(probs, items, n_items, chunk); break;
-        default: k_batch_all<N1, 4, VARIANT><<<grid, T, smem, s>>>(probs, items, n_items, chunk); break;
+        case 1: k_batch_all<N1, 1, VARIANT><<<grid, T, smem, s>>>(probs, n_probs, items, n_items, chunk); break;
+        case 2: k_batch_all<N1, 2, VARIANT><<<grid, T, smem, s>>>(probs, n_probs, items, n_items, chunk); break;
+        case 3: k_batch_all<N1, 3, VARIANT><<<grid, T, smem, s>>>(probs, n_probs, items, n_items, chunk); break;
+        default: k_batch_all<N1, 4, VARIANT><<<grid, T, smem, s>>>(probs, n_probs, items, n_items, chunk); break;
         }
     }
-    static void launch(int n1, int stage, int grid, size_t smem, const BatchProb *probs, const int2 *items,
-                       int n_items, int chunk, cudaStream_t s) {
+    static void launch(int n1, int stage, int grid, size_t smem, const BatchProb *probs, int n_probs,
+                       const int2 *items, int n_items, int chunk, cudaStream_t s) {
         switch (n1) {
-#define X(n_) case n_: launch_n<n_>(stage, grid, smem, probs, items, n_items, chunk, s); break;
+#define X(n_) case n_: launch_n<n_>(stage, grid, smem, probs, n_probs, items, n_items, chunk, s); break;
             GDG_BATCH_CASES(X)
 #undef X
         }
@@ -236,13 +241,17 @@ struct BatchOps {
     cudaError_t (*attrs)(int n1);
     int (*resident)(int n1, size_t smem);   // resident blocks per SM at smem bytes, 0 on error
     int (*regs)(int n1);
-    void (*launch)(int n1, int stage, int grid, size_t smem, const BatchProb *probs, const int2 *items,
-                   int n_items, int chunk, cudaStream_t s);
+    void (*launch)(int n1, int stage, int grid, size_t smem, const BatchProb *probs, int n_probs,
+                   const int2 *items, int n_items, int chunk, cudaStream_t s);
+    int (*checks)(GdgCheckSlot *out, int reset);
 };
+// this translation unit's check slot (gdg_checks.cuh)
+static GDG_CHECKS_READER(batch_checks_read)
+
 template <int VARIANT>
 constexpr BatchOps batch_ops_of() {
     return BatchOps{BatchVariant<VARIANT>::attrs, BatchVariant<VARIANT>::resident, BatchVariant<VARIANT>::regs,
-                    BatchVariant<VARIANT>::launch};
+                    BatchVariant<VARIANT>::launch, batch_checks_read};
 }
 extern const BatchOps batch_ops_mid;   // gdg_batch_mid.cu
 extern const BatchOps batch_ops_lo;    // gdg_batch_lo.cu

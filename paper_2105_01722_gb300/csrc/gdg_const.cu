@@ -29,6 +29,7 @@
 #include <string>
 #include <vector>
 
+#include "gdg_checks.cuh"
 #include "gdg_internal.h"
 #include "gdg_stage_const.cuh"
 
@@ -60,14 +61,14 @@ k_stage2(const __grid_constant__ ModalParams mp, const StageBufs b, double cA, d
         int en = ex - 1;
         if (en < 0 && mp.per_x) en += nx;
         bool bnd = en < 0;
-        if (!bnd) { int f = ey * nx + en; vo = T[tix2<N1>(f, 1, 0, l)]; dO = T[tix2<N1>(f, 1, 1, l)]; }
+        if (!bnd) { int f = ey * nx + en; GDG_CHECK_ELEM2(f, mp, GDG_SITE_STAGE2_NB + 0); vo = T[tix2<N1>(f, 1, 0, l)]; dO = T[tix2<N1>(f, 1, 1, l)]; }
         else { vo = -vi; dO = -di; }
         flux(vi, di, vo, dO, mp.beta, mp.tau, mp.c2, mp.alt, 0, bnd, gxm, qxm);
         vi = T[tix2<N1>(e, 1, 0, l)]; di = T[tix2<N1>(e, 1, 1, l)];
         en = ex + 1;
         if (en >= nx && mp.per_x) en -= nx;
         bnd = en >= nx;
-        if (!bnd) { int f = ey * nx + en; vo = T[tix2<N1>(f, 0, 0, l)]; dO = T[tix2<N1>(f, 0, 1, l)]; }
+        if (!bnd) { int f = ey * nx + en; GDG_CHECK_ELEM2(f, mp, GDG_SITE_STAGE2_NB + 1); vo = T[tix2<N1>(f, 0, 0, l)]; dO = T[tix2<N1>(f, 0, 1, l)]; }
         else { vo = -vi; dO = -di; }
         flux(vi, di, vo, dO, mp.beta, mp.tau, mp.c2, mp.alt, 1, bnd, gxp, qxp);
         // y faces, transverse mode k = l
@@ -76,7 +77,7 @@ k_stage2(const __grid_constant__ ModalParams mp, const StageBufs b, double cA, d
         en = ey - 1;
         if (en < 0 && mp.per_y) en += ny;
         bnd = en < 0;
-        if (!bnd) { int f = en * nx + ex; vo = T[tix2<N1>(f, 3, 0, l)]; dO = T[tix2<N1>(f, 3, 1, l)]; }
+        if (!bnd) { int f = en * nx + ex; GDG_CHECK_ELEM2(f, mp, GDG_SITE_STAGE2_NB + 2); vo = T[tix2<N1>(f, 3, 0, l)]; dO = T[tix2<N1>(f, 3, 1, l)]; }
         else { vo = -vi; dO = -di; }
         flux(vi, di, vo, dO, mp.beta, mp.tau, mp.c2, mp.alt, 0, bnd, g, q);
         fy[0 * N1 + l] = g; fy[2 * N1 + l] = q;
@@ -84,7 +85,7 @@ k_stage2(const __grid_constant__ ModalParams mp, const StageBufs b, double cA, d
         en = ey + 1;
         if (en >= ny && mp.per_y) en -= ny;
         bnd = en >= ny;
-        if (!bnd) { int f = en * nx + ex; vo = T[tix2<N1>(f, 2, 0, l)]; dO = T[tix2<N1>(f, 2, 1, l)]; }
+        if (!bnd) { int f = en * nx + ex; GDG_CHECK_ELEM2(f, mp, GDG_SITE_STAGE2_NB + 3); vo = T[tix2<N1>(f, 2, 0, l)]; dO = T[tix2<N1>(f, 2, 1, l)]; }
         else { vo = -vi; dO = -di; }
         flux(vi, di, vo, dO, mp.beta, mp.tau, mp.c2, mp.alt, 1, bnd, g, q);
         fy[1 * N1 + l] = g; fy[3 * N1 + l] = q;
@@ -205,14 +206,14 @@ __device__ __forceinline__ void s2f_fluxes(const ModalParams &mp, const StageBuf
     en = ex - 1;
     if (en < 0 && mp.per_x) en += nx;
     bnd = en < 0;
-    if (!bnd) { f = ey * nx + en; vo = T[tix2<N1>(f, 1, 0, l)]; dO = T[tix2<N1>(f, 1, 1, l)]; }
+    if (!bnd) { f = ey * nx + en; GDG_CHECK_ELEM2(f, mp, GDG_SITE_STAGE2F_NB + 0); vo = T[tix2<N1>(f, 1, 0, l)]; dO = T[tix2<N1>(f, 1, 1, l)]; }
     else { vo = -vi; dO = -di; }
     flux2(vi, di, vo, dO, b2, t2, ALT, 0, bnd, g2m, q2m);
     vi = T[tix2<N1>(e, 1, 0, l)]; di = T[tix2<N1>(e, 1, 1, l)];
     en = ex + 1;
     if (en >= nx && mp.per_x) en -= nx;
     bnd = en >= nx;
-    if (!bnd) { f = ey * nx + en; vo = T[tix2<N1>(f, 0, 0, l)]; dO = T[tix2<N1>(f, 0, 1, l)]; }
+    if (!bnd) { f = ey * nx + en; GDG_CHECK_ELEM2(f, mp, GDG_SITE_STAGE2F_NB + 1); vo = T[tix2<N1>(f, 0, 0, l)]; dO = T[tix2<N1>(f, 0, 1, l)]; }
     else { vo = -vi; dO = -di; }
     flux2(vi, di, vo, dO, b2, t2, ALT, 1, bnd, g2p, q2p);
     if (FIELD == 0) { XA = g2m + g2p; XB = g2m - g2p; }
@@ -221,14 +222,14 @@ __device__ __forceinline__ void s2f_fluxes(const ModalParams &mp, const StageBuf
     en = ey - 1;
     if (en < 0 && mp.per_y) en += ny;
     bnd = en < 0;
-    if (!bnd) { f = en * nx + ex; vo = T[tix2<N1>(f, 3, 0, l)]; dO = T[tix2<N1>(f, 3, 1, l)]; }
+    if (!bnd) { f = en * nx + ex; GDG_CHECK_ELEM2(f, mp, GDG_SITE_STAGE2F_NB + 2); vo = T[tix2<N1>(f, 3, 0, l)]; dO = T[tix2<N1>(f, 3, 1, l)]; }
     else { vo = -vi; dO = -di; }
     flux2(vi, di, vo, dO, b2, t2, ALT, 0, bnd, g2m, q2m);
     vi = T[tix2<N1>(e, 3, 0, l)]; di = T[tix2<N1>(e, 3, 1, l)];
     en = ey + 1;
     if (en >= ny && mp.per_y) en -= ny;
     bnd = en >= ny;
-    if (!bnd) { f = en * nx + ex; vo = T[tix2<N1>(f, 2, 0, l)]; dO = T[tix2<N1>(f, 2, 1, l)]; }
+    if (!bnd) { f = en * nx + ex; GDG_CHECK_ELEM2(f, mp, GDG_SITE_STAGE2F_NB + 3); vo = T[tix2<N1>(f, 2, 0, l)]; dO = T[tix2<N1>(f, 2, 1, l)]; }
     else { vo = -vi; dO = -di; }
     flux2(vi, di, vo, dO, b2, t2, ALT, 1, bnd, g2p, q2p);
     if (FIELD == 0) { fy[l] = g2m + g2p; fy[N1 + l] = g2m - g2p; }
@@ -442,6 +443,7 @@ __device__ void neighbour_blocks(const ModalParams &mp, int epb, int *s_nb, int 
                 if (y < ny) en = y * nx + ex;
             }
             if (en >= 0 && en / epb != (int)blockIdx.x) nbb = en / epb;
+            if (nbb >= 0) GDG_CHECK_INDEX(nbb, 0, gridDim.x, GDG_SITE_STEP2R_BLOCK, -1);
         }
         s_nb[i] = nbb;
     }
@@ -479,14 +481,14 @@ __device__ __forceinline__ void stage2r(const ModalParams &mp, const double *lam
         en = ex - 1;
         if (en < 0 && mp.per_x) en += nx;
         bnd = en < 0;
-        if (!bnd) { f = ey * nx + en; vo = __ldcg(T + tix2<N1>(f, 1, 0, l)); dO = __ldcg(T + tix2<N1>(f, 1, 1, l)); }
+        if (!bnd) { f = ey * nx + en; GDG_CHECK_ELEM2(f, mp, GDG_SITE_STAGE2R_NB + 0); vo = __ldcg(T + tix2<N1>(f, 1, 0, l)); dO = __ldcg(T + tix2<N1>(f, 1, 1, l)); }
         else { vo = -vi; dO = -di; }
         flux2(vi, di, vo, dO, b2, t2, ALT, 0, bnd, g2m, q2m);
         vi = __ldcg(T + tix2<N1>(e, 1, 0, l)); di = __ldcg(T + tix2<N1>(e, 1, 1, l));
         en = ex + 1;
         if (en >= nx && mp.per_x) en -= nx;
         bnd = en >= nx;
-        if (!bnd) { f = ey * nx + en; vo = __ldcg(T + tix2<N1>(f, 0, 0, l)); dO = __ldcg(T + tix2<N1>(f, 0, 1, l)); }
+        if (!bnd) { f = ey * nx + en; GDG_CHECK_ELEM2(f, mp, GDG_SITE_STAGE2R_NB + 1); vo = __ldcg(T + tix2<N1>(f, 0, 0, l)); dO = __ldcg(T + tix2<N1>(f, 0, 1, l)); }
         else { vo = -vi; dO = -di; }
         flux2(vi, di, vo, dO, b2, t2, ALT, 1, bnd, g2p, q2p);
         GA = g2m + g2p; GB = g2m - g2p; QA = q2m + q2p; QB = q2m - q2p;
@@ -494,14 +496,14 @@ __device__ __forceinline__ void stage2r(const ModalParams &mp, const double *lam
         en = ey - 1;
         if (en < 0 && mp.per_y) en += ny;
         bnd = en < 0;
-        if (!bnd) { f = en * nx + ex; vo = __ldcg(T + tix2<N1>(f, 3, 0, l)); dO = __ldcg(T + tix2<N1>(f, 3, 1, l)); }
+        if (!bnd) { f = en * nx + ex; GDG_CHECK_ELEM2(f, mp, GDG_SITE_STAGE2R_NB + 2); vo = __ldcg(T + tix2<N1>(f, 3, 0, l)); dO = __ldcg(T + tix2<N1>(f, 3, 1, l)); }
         else { vo = -vi; dO = -di; }
         flux2(vi, di, vo, dO, b2, t2, ALT, 0, bnd, g2m, q2m);
         vi = __ldcg(T + tix2<N1>(e, 3, 0, l)); di = __ldcg(T + tix2<N1>(e, 3, 1, l));
         en = ey + 1;
         if (en >= ny && mp.per_y) en -= ny;
         bnd = en >= ny;
-        if (!bnd) { f = en * nx + ex; vo = __ldcg(T + tix2<N1>(f, 2, 0, l)); dO = __ldcg(T + tix2<N1>(f, 2, 1, l)); }
+        if (!bnd) { f = en * nx + ex; GDG_CHECK_ELEM2(f, mp, GDG_SITE_STAGE2R_NB + 3); vo = __ldcg(T + tix2<N1>(f, 2, 0, l)); dO = __ldcg(T + tix2<N1>(f, 2, 1, l)); }
         else { vo = -vi; dO = -di; }
         flux2(vi, di, vo, dO, b2, t2, ALT, 1, bnd, g2p, q2p);
         fy[l] = g2m + g2p; fy[N1 + l] = g2m - g2p;
@@ -819,12 +821,18 @@ k_stage1(const __grid_constant__ ModalParams mp, const StageBufs b, double cA, d
     double vi = T[tix1(e, 0, 0)], di = T[tix1(e, 0, 1)], vo, dO, gm, qm, gp, qp;
     int en = e - 1;
     if (en < 0 && mp.per_x) en += nx;
-    if (en >= 0) { vo = T[tix1(en, 1, 0)]; dO = T[tix1(en, 1, 1)]; } else { vo = -vi; dO = -di; }
+    if (en >= 0) {
+        GDG_CHECK_INDEX(en, 0, mp.ne, GDG_SITE_STAGE1_NB + 0, 0);
+        vo = T[tix1(en, 1, 0)]; dO = T[tix1(en, 1, 1)];
+    } else { vo = -vi; dO = -di; }
     flux(vi, di, vo, dO, mp.beta, mp.tau, mp.c2, mp.alt, 0, en < 0, gm, qm);
     vi = T[tix1(e, 1, 0)]; di = T[tix1(e, 1, 1)];
     en = e + 1;
     if (en >= nx && mp.per_x) en -= nx;
-    if (en < nx) { vo = T[tix1(en, 0, 0)]; dO = T[tix1(en, 0, 1)]; } else { vo = -vi; dO = -di; }
+    if (en < nx) {
+        GDG_CHECK_INDEX(en, 0, mp.ne, GDG_SITE_STAGE1_NB + 1, 0);
+        vo = T[tix1(en, 0, 0)]; dO = T[tix1(en, 0, 1)];
+    } else { vo = -vi; dO = -di; }
     flux(vi, di, vo, dO, mp.beta, mp.tau, mp.c2, mp.alt, 1, en >= nx, gp, qp);
     const size_t row = (size_t)e * N1;
     double Ru[N1], Rv[N1];
@@ -2046,5 +2054,24 @@ extern "C" int gdg_rhs_static(const gdg_problem *pb, const double *u, const doub
     launch_stage(&c, M_RHS, b, 0.0, 0.0, s);
     launch_sep(&c, Ku, Kv, du, dv, T_PSI, nullptr, -1, s);
     c.d_mats = c.d_lam2 = nullptr;   // not owned
+    return cudaGetLastError() == cudaSuccess ? GDG_OK : GDG_ECUDA;
+}
+
+// ---------------------------------------------------- index checks ------
+
+// this translation unit's check slot (gdg_checks.cuh)
+GDG_CHECKS_READER(gdg_checks_read_const)
+
+namespace {
+__global__ void k_check_selftest(long long index, long long bound) {
+    long long i = index;
+    GDG_CHECK_INDEX(i, 0, bound, GDG_SITE_SELFTEST, 0);
+    (void)i;
+}
+}  // namespace
+
+extern "C" int gdg_check_selftest(long long index, long long bound, void *stream) {
+    if (!GDG_CHECKS) return GDG_EUNSUPPORTED;
+    k_check_selftest<<<1, 1, 0, (cudaStream_t)stream>>>(index, bound);
     return cudaGetLastError() == cudaSuccess ? GDG_OK : GDG_ECUDA;
 }

@@ -6,6 +6,7 @@
 // of an element, blockDim.x = epb * N1 * N1.
 #include <algorithm>
 
+#include "gdg_checks.cuh"
 #include "gdg_internal.h"
 #include "gdg_stage_const.cuh"
 
@@ -93,9 +94,12 @@ k_stage3(const __grid_constant__ ModalParams mp, const StageBufs b, double cA, d
 #pragma unroll
         for (int f = 0; f < 6; ++f) {
             const double vi = T[tix3<N1>(e, f, 0, tt)], di = T[tix3<N1>(e, f, 1, tt)];
-            const int nb = nbr3(mp, ex, ey, ez, f);
+            int nb = nbr3(mp, ex, ey, ez, f);
             double vo, dO;
-            if (nb >= 0) { vo = T[tix3<N1>(nb, f ^ 1, 0, tt)]; dO = T[tix3<N1>(nb, f ^ 1, 1, tt)]; }
+            if (nb >= 0) {
+                GDG_CHECK_INDEX(nb, 0, mp.ne, GDG_SITE_STAGE3_NB + f, 0);
+                vo = T[tix3<N1>(nb, f ^ 1, 0, tt)]; dO = T[tix3<N1>(nb, f ^ 1, 1, tt)];
+            }
             else { vo = -vi; dO = -di; }
             double g, q;
             flux(vi, di, vo, dO, mp.beta, mp.tau, mp.c2, mp.alt, f & 1, nb < 0, g, q);
@@ -240,9 +244,12 @@ k_stage3p(const __grid_constant__ ModalParams mp, const StageBufs b, double cA, 
             for (int side = 0; side < 2; ++side) {
                 const int f = 2 * d + side;
                 const double vi = T[tix3<N1>(e, f, 0, tt)], di = T[tix3<N1>(e, f, 1, tt)];
-                const int nb = nbr3(mp, ex, ey, ez, f);
+                int nb = nbr3(mp, ex, ey, ez, f);
                 double vo, dO;
-                if (nb >= 0) { vo = T[tix3<N1>(nb, f ^ 1, 0, tt)]; dO = T[tix3<N1>(nb, f ^ 1, 1, tt)]; }
+                if (nb >= 0) {
+                    GDG_CHECK_INDEX(nb, 0, mp.ne, GDG_SITE_STAGE3_NB + f, 0);
+                    vo = T[tix3<N1>(nb, f ^ 1, 0, tt)]; dO = T[tix3<N1>(nb, f ^ 1, 1, tt)];
+                }
                 else { vo = -vi; dO = -di; }
                 flux2(vi, di, vo, dO, mp.beta2, mp.tau2, ALT, side, nb < 0, g2[side], q2[side]);
             }
@@ -597,3 +604,6 @@ void gdg3_set_smem_limits() {
     GDG_N1_CASES3(X)
 #undef X
 }
+
+// this translation unit's check slot (gdg_checks.cuh)
+GDG_CHECKS_READER(gdg_checks_read_const3)

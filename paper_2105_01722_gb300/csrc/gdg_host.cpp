@@ -5,6 +5,7 @@
 #include <cstring>
 #include <new>
 
+#include "gdg_checks.cuh"
 #include "gdg_internal.h"
 
 // --------------------------------------------------------------- errors --
@@ -547,4 +548,29 @@ extern "C" int gdg_energy(gdg_ctx *ctx, const double *u, const double *v, double
     int st = is_const(ctx) ? gdg_const_energy(ctx, u, v, E, s) : gdg_var_energy(ctx, u, v, E, s);
     if (st == GDG_OK && !std::isfinite(*E)) return gdg_set_err(ctx, GDG_ENONFINITE, "energy is not finite");
     return st;
+}
+
+// ---------------------------------------------------- index checks ------
+
+extern "C" int gdg_check_status(long long *count, int *site, long long *index, long long *bound, int reset) {
+    if (count) *count = 0;
+    if (site) *site = 0;
+    if (index) *index = 0;
+    if (bound) *bound = 0;
+    if (!GDG_CHECKS) return GDG_EUNSUPPORTED;
+    if (cudaDeviceSynchronize() != cudaSuccess) return GDG_ECUDA;
+    int (*const readers[])(GdgCheckSlot *, int) = {gdg_checks_read_const, gdg_checks_read_const3, gdg_checks_read_var,
+                                                   gdg_checks_read_batch};
+    GdgCheckSlot acc{};
+    for (auto rd : readers) {
+        GdgCheckSlot s{};
+        if (rd(&s, reset)) return GDG_ECUDA;
+        if (s.count && !acc.count) acc = s;
+        else acc.count += s.count;
+    }
+    if (count) *count = (long long)acc.count;
+    if (site) *site = (int)acc.site;
+    if (index) *index = acc.index;
+    if (bound) *bound = acc.bound;
+    return GDG_OK;
 }

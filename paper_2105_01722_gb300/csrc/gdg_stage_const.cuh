@@ -2,6 +2,7 @@
 // per-problem kernels (gdg_const.cu) and the batched kernels (gdg_batch.cu).
 #pragma once
 
+#include "gdg_checks.cuh"
 #include "gdg_internal.h"
 
 namespace {
@@ -110,14 +111,14 @@ __device__ __forceinline__ void stage2p_body(const ModalParams &mp, const StageB
         en = ex - 1;
         if (en < 0 && mp.per_x) en += nx;
         bnd = en < 0;
-        if (!bnd) { f = ey * nx + en; vo = T[tix2<N1>(f, 1, 0, l)]; dO = T[tix2<N1>(f, 1, 1, l)]; }
+        if (!bnd) { f = ey * nx + en; GDG_CHECK_ELEM2(f, mp, GDG_SITE_STAGE2P_NB + 0); vo = T[tix2<N1>(f, 1, 0, l)]; dO = T[tix2<N1>(f, 1, 1, l)]; }
         else { vo = -vi; dO = -di; }
         flux2(vi, di, vo, dO, b2, t2, ALT, 0, bnd, g2m, q2m);
         vi = T[tix2<N1>(e, 1, 0, l)]; di = T[tix2<N1>(e, 1, 1, l)];
         en = ex + 1;
         if (en >= nx && mp.per_x) en -= nx;
         bnd = en >= nx;
-        if (!bnd) { f = ey * nx + en; vo = T[tix2<N1>(f, 0, 0, l)]; dO = T[tix2<N1>(f, 0, 1, l)]; }
+        if (!bnd) { f = ey * nx + en; GDG_CHECK_ELEM2(f, mp, GDG_SITE_STAGE2P_NB + 1); vo = T[tix2<N1>(f, 0, 0, l)]; dO = T[tix2<N1>(f, 0, 1, l)]; }
         else { vo = -vi; dO = -di; }
         flux2(vi, di, vo, dO, b2, t2, ALT, 1, bnd, g2p, q2p);
         GA = g2m + g2p; GB = g2m - g2p; QA = q2m + q2p; QB = q2m - q2p;
@@ -127,14 +128,14 @@ __device__ __forceinline__ void stage2p_body(const ModalParams &mp, const StageB
         en = ey - 1;
         if (en < 0 && mp.per_y) en += ny;
         bnd = en < 0 && !mp.halo_lo;
-        if (!bnd) { f = en * nx + ex; vo = T[tix2<N1>(f, 3, 0, l)]; dO = T[tix2<N1>(f, 3, 1, l)]; }
+        if (!bnd) { f = en * nx + ex; GDG_CHECK_ELEM2(f, mp, GDG_SITE_STAGE2P_NB + 2); vo = T[tix2<N1>(f, 3, 0, l)]; dO = T[tix2<N1>(f, 3, 1, l)]; }
         else { vo = -vi; dO = -di; }
         flux2(vi, di, vo, dO, b2, t2, ALT, 0, bnd, g2m, q2m);
         vi = T[tix2<N1>(e, 3, 0, l)]; di = T[tix2<N1>(e, 3, 1, l)];
         en = ey + 1;
         if (en >= ny && mp.per_y) en -= ny;
         bnd = en >= ny && !mp.halo_hi;
-        if (!bnd) { f = en * nx + ex; vo = T[tix2<N1>(f, 2, 0, l)]; dO = T[tix2<N1>(f, 2, 1, l)]; }
+        if (!bnd) { f = en * nx + ex; GDG_CHECK_ELEM2(f, mp, GDG_SITE_STAGE2P_NB + 3); vo = T[tix2<N1>(f, 2, 0, l)]; dO = T[tix2<N1>(f, 2, 1, l)]; }
         else { vo = -vi; dO = -di; }
         flux2(vi, di, vo, dO, b2, t2, ALT, 1, bnd, g2p, q2p);
         fy[l] = g2m + g2p; fy[N1 + l] = g2m - g2p;
@@ -278,14 +279,14 @@ __device__ __forceinline__ void stage2h_body(const ModalParams &mp, const StageB
             en = ex - 1;
             if (en < 0 && mp.per_x) en += nx;
             bnd = en < 0;
-            if (!bnd) { f = ey * nx + en; vo = T[tix2<N1>(f, 1, 0, l)]; dO = T[tix2<N1>(f, 1, 1, l)]; }
+            if (!bnd) { f = ey * nx + en; GDG_CHECK_ELEM2(f, mp, GDG_SITE_STAGE2H_NB + 0); vo = T[tix2<N1>(f, 1, 0, l)]; dO = T[tix2<N1>(f, 1, 1, l)]; }
             else { vo = -vi; dO = -di; }
         } else {        // x+
             vi = T[tix2<N1>(e, 1, 0, l)]; di = T[tix2<N1>(e, 1, 1, l)];
             en = ex + 1;
             if (en >= nx && mp.per_x) en -= nx;
             bnd = en >= nx;
-            if (!bnd) { f = ey * nx + en; vo = T[tix2<N1>(f, 0, 0, l)]; dO = T[tix2<N1>(f, 0, 1, l)]; }
+            if (!bnd) { f = ey * nx + en; GDG_CHECK_ELEM2(f, mp, GDG_SITE_STAGE2H_NB + 1); vo = T[tix2<N1>(f, 0, 0, l)]; dO = T[tix2<N1>(f, 0, 1, l)]; }
             else { vo = -vi; dO = -di; }
         }
         flux2(vi, di, vo, dO, b2, t2, mp.alt, h, bnd, gx, qx);
@@ -294,14 +295,14 @@ __device__ __forceinline__ void stage2h_body(const ModalParams &mp, const StageB
             en = ey - 1;
             if (en < 0 && mp.per_y) en += ny;
             bnd = en < 0;
-            if (!bnd) { f = en * nx + ex; vo = T[tix2<N1>(f, 3, 0, l)]; dO = T[tix2<N1>(f, 3, 1, l)]; }
+            if (!bnd) { f = en * nx + ex; GDG_CHECK_ELEM2(f, mp, GDG_SITE_STAGE2H_NB + 2); vo = T[tix2<N1>(f, 3, 0, l)]; dO = T[tix2<N1>(f, 3, 1, l)]; }
             else { vo = -vi; dO = -di; }
         } else {        // y+
             vi = T[tix2<N1>(e, 3, 0, l)]; di = T[tix2<N1>(e, 3, 1, l)];
             en = ey + 1;
             if (en >= ny && mp.per_y) en -= ny;
             bnd = en >= ny;
-            if (!bnd) { f = en * nx + ex; vo = T[tix2<N1>(f, 2, 0, l)]; dO = T[tix2<N1>(f, 2, 1, l)]; }
+            if (!bnd) { f = en * nx + ex; GDG_CHECK_ELEM2(f, mp, GDG_SITE_STAGE2H_NB + 3); vo = T[tix2<N1>(f, 2, 0, l)]; dO = T[tix2<N1>(f, 2, 1, l)]; }
             else { vo = -vi; dO = -di; }
         }
         flux2(vi, di, vo, dO, b2, t2, mp.alt, h, bnd, gy, qy);

@@ -637,3 +637,6 @@ extern "C" int gdg_set_point_source(gdg_ctx *ctx, int element, double r, double 
     D.vp.src_w = D.d_src;
     return GDG_OK;
 }
+
+// this translation unit's check slot (gdg_checks.cuh)
+GDG_CHECKS_READER(gdg_checks_read_var)

@@ -2,6 +2,7 @@
 // gdg_var.cu (per-problem launches) and gdg_batch.cu (batched launches).
 #pragma once
 
+#include "gdg_checks.cuh"
 #include <cmath>
 
 #include "gdg_internal.h"
@@ -134,7 +135,9 @@ __device__ __forceinline__ int neighbour(const VarParams &P, int e, int f, int &
         if (!P.per_y) return -1;
         ey = (ey + P.ny) % P.ny;
     }
-    return ey * P.nx + ex;
+    int nb = ey * P.nx + ex;
+    GDG_CHECK_INDEX(nb, 0, P.ne, GDG_SITE_VAR_NB, e);
+    return nb;
 }
 
 // deterministic block sum: warp butterflies, then every thread adds the

@@ -10,7 +10,8 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libgdg.so")
+# the index-checking build (gdg_checks.cuh) when the environment asks for it
+LIB_PATH = os.path.join(_HERE, "libgdg_checks.so" if os.environ.get("GDG_CHECKS") == "1" else "libgdg.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ENOCONV, ETIMEOUT, ENONFINITE, EUNSUPPORTED, EHALO = 0, -1, -2, -3, -4, -5, -6, -7, -8
 BC_DIRICHLET, BC_PERIODIC = 0, 1
@@ -84,6 +85,10 @@ EXPORTS = {
     "gdg_batch_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
                                       ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_void_p]),
     "gdg_batch_tuning": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.POINTER(ctypes.c_int)] * 6),
+    "gdg_check_status": (ctypes.c_int, [ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_int),
+                                         ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
+                                         ctypes.c_int]),
+    "gdg_check_selftest": (ctypes.c_int, [ctypes.c_longlong, ctypes.c_longlong, ctypes.c_void_p]),
     "gdg_batch_set_tuning": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "gdg_batch_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(PcgStats),
                                        ctypes.POINTER(PcgStats)]),
@@ -205,6 +210,24 @@ def _stream(stream=None):
     import torch
     s = torch.cuda.current_stream() if stream is None else stream
     return ctypes.c_void_p(s.cuda_stream)
+
+
+def check_status(reset=False):
+    """Index-check failures of the GDG_CHECKS build since the last reset:
+    dict(count, site, index, bound) of the first failure; raises GdgError
+    (GDG_EUNSUPPORTED) on the ordinary build."""
+    c, si, i, b = ctypes.c_longlong(), ctypes.c_int(), ctypes.c_longlong(), ctypes.c_longlong()
+    st = lib().gdg_check_status(ctypes.byref(c), ctypes.byref(si), ctypes.byref(i), ctypes.byref(b), int(reset))
+    if st != OK:
+        raise GdgError(st, "gdg_check_status")
+    return dict(count=c.value, site=si.value, index=i.value, bound=b.value)
+
+
+def check_selftest(index, bound, stream=None):
+    """Check index against [0, bound) on the device (records site 99 if it fails)."""
+    st = lib().gdg_check_selftest(int(index), int(bound), _stream(stream))
+    if st != OK:
+        raise GdgError(st, "gdg_check_selftest")
 
 
 def probe_fp64(iters, sink, stream=None):

@@ -146,3 +146,14 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(gdg, "LIB_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError):
         gdg.lib()
+
+
+def test_ordinary_build_has_no_index_checks():
+    """The index checks exist only in the GDG_CHECKS build: the ordinary
+    library answers GDG_EUNSUPPORTED before touching the device."""
+    import ctypes
+    L = gdg.lib()
+    c, si, i, b = ctypes.c_longlong(7), ctypes.c_int(7), ctypes.c_longlong(7), ctypes.c_longlong(7)
+    st = L.gdg_check_status(ctypes.byref(c), ctypes.byref(si), ctypes.byref(i), ctypes.byref(b), 0)
+    assert st == gdg.EUNSUPPORTED and (c.value, si.value, i.value, b.value) == (0, 0, 0, 0)
+    assert L.gdg_check_selftest(5, 3, None) == gdg.EUNSUPPORTED

@@ -42,7 +42,7 @@ extern "C" {
 #define GDG_ENOCONV     -4   /* PCG hit pcg_maxit; result = last iterate, statistics filled      */
 #define GDG_ETIMEOUT    -5   /* a bounded device-side wait gave up                               */
 #define GDG_ENONFINITE  -6   /* NaN or Inf detected (energy, PCG residual)                       */
-#define GDG_EUNSUPPORTED -7  /* valid request this build does not provide (e.g. N+1 > 16)        */
+#define GDG_EUNSUPPORTED -7  /* valid request the library does not provide (e.g. N+1 > 16)       */
 #define GDG_EHALO       -8   /* the caller's halo exchange function reported a failure            */
 
 /* ---- enums ----------------------------------------------------------- */

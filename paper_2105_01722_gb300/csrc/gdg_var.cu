@@ -23,6 +23,7 @@
 //                 shared memory) + RK combine + traces of the next stage input
 //   k_var_pcg     one element PCG (gdg_pcg)
 //   k_var_energy  per-element V^T M V + U^T S U
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -310,13 +311,21 @@ int gdg_var_setup(gdg_ctx *ctx) {
         }
         P.G = D->d_G;
     }
-    if (P.mixed) {   // FP32 copies of the element matrices for the inner solves
-        const size_t nm = nd * NA;
+    if (P.mixed) {   // FP32 copies of the element matrices (packed lower triangles) for the inner solves
+        const size_t nm = (size_t)ctx->ne * tri_len(NA);
         if ((st = gdg_cuda_check(ctx, cudaMalloc((void **)&D->d_S32, nm * sizeof(float)), "alloc S32")) ||
             (st = gdg_cuda_check(ctx, cudaMalloc((void **)&D->d_M32, nm * sizeof(float)), "alloc M32")))
             return st;
-        k_to_f32<<<1216, 256>>>(nm, D->d_S, D->d_S32);
-        k_to_f32<<<1216, 256>>>(nm, D->d_M, D->d_M32);
+        const int grid = (int)std::min<long long>(ctx->ne, 65535);
+        switch (n1) {
+#define X(n)                                                                  \
+    case n:                                                                   \
+        k_to_f32_lower<n><<<grid, 128>>>(ctx->ne, D->d_S, D->d_S32);          \
+        k_to_f32_lower<n><<<grid, 128>>>(ctx->ne, D->d_M, D->d_M32);          \
+        break;
+            GDG_VAR_CASES(X)
+#undef X
+        }
         P.S32 = D->d_S32;
         P.M32 = D->d_M32;
     }

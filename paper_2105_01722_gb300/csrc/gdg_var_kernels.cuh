@@ -177,6 +177,31 @@ __device__ __forceinline__ void matvec(const T *A, const T *x, T *y) {
     __syncthreads();
 }
 
+// Lower triangle of a symmetric NA x NA matrix, row by row: entry (i, k),
+// k <= i, at i (i + 1) / 2 + k.  The FP32 element matrices of the mixed
+// solves are kept this way (half the shared memory of the full matrix).
+__host__ __device__ constexpr int tri_len(int na) { return na * (na + 1) / 2; }
+
+// y = A x for a symmetric A held as its packed lower triangle: row t reads
+// (t, 0..t) from row t and (k, t) for k > t from the rows below, so every
+// product and the order of the sum are those of the full row-major matvec.
+template <int NA>
+__device__ __forceinline__ void matvec_packed(const float *L, const float *x, float *y) {
+    const int t = threadIdx.x;
+    if (t < NA) {
+        float s = 0.f;
+        const int row = t * (t + 1) / 2;
+        int col = t;                    // k (k + 1) / 2 + t at k = 0
+#pragma unroll 9
+        for (int k = 0; k < NA; ++k) {
+            s = fmaf(k <= t ? L[row + k] : L[col], x[k], s);
+            col += k + 1;
+        }
+        y[t] = s;
+    }
+    __syncthreads();
+}
+
 // y = A x for a symmetric NA x NA matrix in global memory, read by columns
 // (thread t reads column t: coalesced), summed in row order
 template <int NA>
@@ -363,8 +388,8 @@ __device__ int pcg(const double *A, const double *w, const double *b, double *x,
     return it;
 }
 
-// FP32 PCG from x0 = 0 on A32 (+ w32 w32^T when W) for a right-hand side of
-// unit norm: stops when ||r|| <= irtol, after imaxit iterations or at r.z = 0.
+// FP32 PCG from x0 = 0 on A32 (packed lower triangle; + w32 w32^T when W)
+// for a right-hand side of unit norm: stops when ||r|| <= irtol, after imaxit iterations or at r.z = 0.
 template <int N1, bool W>
 __device__ int pcg32(const float *A, const float *w, const float *b, float *x, float *r, float *z, float *p,
                      float *Ap, const float *Ps, const float *d, float *t1, float *t2, double *red, float irtol,
@@ -380,7 +405,7 @@ __device__ int pcg32(const float *A, const float *w, const float *b, float *x, f
     int it = 0;
     while (it < imaxit) {
         if (sqrtf(rr) <= irtol || rz == 0.f) break;
-        matvec<NA, float>(A, p, Ap);
+        matvec_packed<NA>(A, p, Ap);
         // p.(A + w w^T)p = p.Ap + (w.p)^2: one reduction for both
         float pAp = t < NA ? p[t] * Ap[t] : 0.f, wp = (W && t < NA) ? w[t] * p[t] : 0.f;
         block_sum2<float>(pAp, wp, red);
@@ -503,13 +528,13 @@ __device__ __forceinline__ void cp_async_4(void *dst, const void *src) {
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-// FP32 element matrix (the copy made at setup) and FP32 copies of the
-// preconditioner data
+// FP32 element matrix (the packed lower triangle made at setup) and FP32
+// copies of the preconditioner data
 template <int N1>
 __device__ void to_fp32(const float *A32g, float *A32, const double *Ps, float *Ps32, const double *d, float *d32,
                         const double *w, float *w32) {
     constexpr int NA = N1 * N1;
-    for (int i = threadIdx.x; i < NA * NA; i += blockDim.x) cp_async_4(A32 + i, A32g + i);
+    for (int i = threadIdx.x; i < tri_len(NA); i += blockDim.x) cp_async_4(A32 + i, A32g + i);
     for (int i = threadIdx.x; i < N1 * N1; i += blockDim.x) Ps32[i] = (float)Ps[i];
     for (int i = threadIdx.x; i < NA; i += blockDim.x) {
         d32[i] = (float)d[i];
@@ -797,13 +822,13 @@ struct StageSmem {
         fw = t2 + NA; L = fw + 24 * N1; red = L + 12 * N1;   // fw: face lines (own, neighbours')
         A = (mixed || no_matrix) ? nullptr : red + 32;
         A32 = reinterpret_cast<float *>(red + 32);
-        Ps32 = A32 + NA * NA; dS32 = Ps32 + N1 * N1; dM32 = dS32 + NA; w32 = dM32 + NA;
+        Ps32 = A32 + tri_len(NA); dS32 = Ps32 + N1 * N1; dM32 = dS32 + NA; w32 = dM32 + NA;
         r32 = w32 + NA; z32 = r32 + NA; p32 = z32 + NA; Ap32 = p32 + NA; c32 = Ap32 + NA;
         u32 = c32 + NA; v32 = u32 + NA; t132 = v32 + NA; t232 = t132 + NA;
     }
     static size_t bytes(int Q, bool mixed, bool no_matrix = false) {
         size_t d = sizeof(double) * ((size_t)tab_tail_len(Q, N1) + 14 * NA + 24 * N1 + 12 * N1 + 32);
-        if (mixed) d += sizeof(float) * ((size_t)NA * NA + N1 * N1 + 12 * NA);
+        if (mixed) d += sizeof(float) * ((size_t)tri_len(NA) + N1 * N1 + 12 * NA);
         else if (!no_matrix) d += sizeof(double) * (size_t)NA * NA;
         return d;
     }
@@ -1075,7 +1100,7 @@ __device__ __forceinline__ void var_stage_body(const VarParams &P, const VarBufs
         // dU/dt, dV/dt already in ru, x (fold_apply)
     } else {
     if (P.mixed) {
-        to_fp32<N1>(P.S32 + (size_t)e * NA * NA, s.A32, T.Ps, s.Ps32, s.dS, s.dS32, s.w, s.w32);
+        to_fp32<N1>(P.S32 + (size_t)e * tri_len(NA), s.A32, T.Ps, s.Ps32, s.dS, s.dS32, s.w, s.w32);
         sw_u = refine<N1, true>(Sg, s.w, s.ru, s.x, s.r, s.Ap, s.scratch32(true), s.red, P.rtol, P.refine_max,
                                 P.refine_rtol, P.maxit, none, !guess, &it_u, &rel_u, guess, &fell);
         bad_u = sw_u >= P.refine_max && rel_u > P.rtol;
@@ -1088,7 +1113,7 @@ __device__ __forceinline__ void var_stage_body(const VarParams &P, const VarBufs
     __syncthreads();
     if (!P.mixed) load_matrix<N1>(s.A, Mg);
     if (P.mixed) {
-        to_fp32<N1>(P.M32 + (size_t)e * NA * NA, s.A32, T.Ps, s.Ps32, s.dM, s.dM32, nullptr, nullptr);
+        to_fp32<N1>(P.M32 + (size_t)e * tri_len(NA), s.A32, T.Ps, s.Ps32, s.dM, s.dM32, nullptr, nullptr);
         const Step64 st64{s.z, s.t1, s.t2, T.Ps, s.dM};
         sw_v = refine<N1, false>(Mg, s.w, s.rv, s.x, s.r, s.Ap, s.scratch32(false), s.red, P.rtol,
                                  P.refine_max, P.refine_rtol, P.maxit, none, true, &it_v, &rel_v, false, nullptr,
@@ -1149,8 +1174,16 @@ __device__ __forceinline__ void var_stage_body(const VarParams &P, const VarBufs
     face_lines<N1>(s.Yu, s.Yv, T, b.trout + lix<N1>(e, 0));
 }
 
+// Resident blocks promised to ptxas for the stage kernel: 10 where a block is
+// at most 3 warps (the element-inverse route streams its operators and wants
+// every warp it can get; the PCG bodies fit the resulting 64 registers
+// without spilling), kVarMinBlocks for larger elements.
+__host__ __device__ constexpr int var_stage_min_blocks(int n1) {
+    return nthreads_for(n1 * n1) <= 96 ? 10 : kVarMinBlocks;
+}
+
 template <int N1, int MODE>
-__global__ void __launch_bounds__(nthreads_for(N1 * N1), kVarMinBlocks)
+__global__ void __launch_bounds__(nthreads_for(N1 * N1), var_stage_min_blocks(N1))
 k_var_stage(VarParams P, VarBufs b, double cA, double cY) {
     extern __shared__ double smraw[];
     var_stage_body<N1, MODE>(P, b, cA, cY, blockIdx.x, smraw);
@@ -1180,7 +1213,7 @@ k_var_pcg(VarParams P, int which, const double *bvec, double *xvec, int *iters, 
     double rr;
     int it, sw = 0;
     if (P.mixed) {
-        to_fp32<N1>((which ? P.S32 : P.M32) + (size_t)e * NA * NA, s.A32, T.Ps, s.Ps32, which ? s.dS : s.dM,
+        to_fp32<N1>((which ? P.S32 : P.M32) + (size_t)e * tri_len(NA), s.A32, T.Ps, s.Ps32, which ? s.dS : s.dM,
                     which ? s.dS32 : s.dM32, which ? s.w : nullptr, s.w32);
         if (which)
             sw = refine<N1, true>(Ag, s.w, s.ru, s.x, s.r, s.Ap, s.scratch32(true), s.red, P.rtol, P.refine_max,
@@ -1339,10 +1372,19 @@ k_var_fold(const double *__restrict__ S, const double *__restrict__ Ainv, const 
     fold_product<N1, NA>(Minv + m2, R, Ge + (size_t)12 * N1 * NA);
 }
 
-// FP32 copy (round to nearest) of an FP64 array
-__global__ void k_to_f32(size_t n, const double *__restrict__ src, float *__restrict__ dst) {
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-        dst[i] = (float)src[i];
+// FP32 copy (round to nearest) of the lower triangles of ne symmetric
+// NA x NA element matrices, packed (tri_len); one block per element
+template <int N1>
+__global__ void k_to_f32_lower(int ne, const double *__restrict__ src, float *__restrict__ dst) {
+    constexpr int NA = N1 * N1;
+    for (int e = blockIdx.x; e < ne; e += gridDim.x) {
+        const double *A = src + (size_t)e * NA * NA;
+        float *L = dst + (size_t)e * tri_len(NA);
+        for (int q = threadIdx.x; q < NA * NA; q += blockDim.x) {
+            const int i = q / NA, k = q - (q / NA) * NA;
+            if (k <= i) L[i * (i + 1) / 2 + k] = (float)A[q];
+        }
+    }
 }
 
 // per-element V^T M V + U^T S U

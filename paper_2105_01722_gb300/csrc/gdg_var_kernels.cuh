@@ -809,27 +809,44 @@ __global__ void k_set_time(double *time, double t0) { *time = t0; }
 template <int N1>
 struct StageSmem {
     static constexpr int NA = N1 * N1;
+    static constexpr int RED = 20;   // reduction scratch: 2 x 16 warp partials at most, in doubles
     // A: the FP64 element matrix (FP64 solves only; the mixed solves read it
     // from global memory for their few FP64 residuals)
     double *A, *tb, *Yu, *Yv, *ru, *rv, *x, *r, *z, *p, *Ap, *w, *dS, *dM, *t1, *t2, *fw, *L, *red;
     // FP32 area (mixed precision only): matrix, preconditioner and PCG vectors
     float *A32, *Ps32, *dS32, *dM32, *w32, *r32, *z32, *p32, *Ap32, *c32, *u32, *v32, *t132, *t232;
+    // Mixed: no FP64 PCG runs, so p is not allocated, and the FP64 step's
+    // scratch z, t1, t2 (used only before the first FP32 sweep of a solve)
+    // shares the FP32 PCG vectors' space: 4 fewer FP64 vectors, 8 elements
+    // per SM instead of 7.
     __device__ StageSmem(double *base, int Q, bool mixed, bool no_matrix = false) {
         tb = base;   // tail of the 1-D tables (tab_tail_len)
         Yu = tb + tab_tail_len(Q, N1);
-        Yv = Yu + NA; ru = Yv + NA; rv = ru + NA; x = rv + NA; r = x + NA; z = r + NA; p = z + NA;
-        Ap = p + NA; w = Ap + NA; dS = w + NA; dM = dS + NA; t1 = dM + NA; t2 = t1 + NA;
-        fw = t2 + NA; L = fw + 24 * N1; red = L + 12 * N1;   // fw: face lines (own, neighbours')
-        A = (mixed || no_matrix) ? nullptr : red + 32;
-        A32 = reinterpret_cast<float *>(red + 32);
-        Ps32 = A32 + tri_len(NA); dS32 = Ps32 + N1 * N1; dM32 = dS32 + NA; w32 = dM32 + NA;
-        r32 = w32 + NA; z32 = r32 + NA; p32 = z32 + NA; Ap32 = p32 + NA; c32 = Ap32 + NA;
-        u32 = c32 + NA; v32 = u32 + NA; t132 = v32 + NA; t232 = t132 + NA;
+        Yv = Yu + NA; ru = Yv + NA; rv = ru + NA; x = rv + NA; r = x + NA;
+        if (mixed) {
+            Ap = r + NA; w = Ap + NA; dS = w + NA; dM = dS + NA;
+            fw = dM + NA; L = fw + 24 * N1; red = L + 12 * N1;
+            A = nullptr;
+            p = nullptr;
+            r32 = reinterpret_cast<float *>(red + RED);   // 8-byte aligned: the FP64 aliases below
+            z = reinterpret_cast<double *>(r32); t1 = z + NA; t2 = t1 + NA;   // 3 NA doubles <= 9 NA floats
+            z32 = r32 + NA; p32 = z32 + NA; Ap32 = p32 + NA; c32 = Ap32 + NA;
+            u32 = c32 + NA; v32 = u32 + NA; t132 = v32 + NA; t232 = t132 + NA;
+            A32 = t232 + NA;
+            Ps32 = A32 + tri_len(NA); dS32 = Ps32 + N1 * N1; dM32 = dS32 + NA; w32 = dM32 + NA;
+        } else {
+            z = r + NA; p = z + NA;
+            Ap = p + NA; w = Ap + NA; dS = w + NA; dM = dS + NA; t1 = dM + NA; t2 = t1 + NA;
+            fw = t2 + NA; L = fw + 24 * N1; red = L + 12 * N1;   // fw: face lines (own, neighbours')
+            A = no_matrix ? nullptr : red + RED;
+            A32 = Ps32 = dS32 = dM32 = w32 = r32 = z32 = p32 = Ap32 = c32 = u32 = v32 = t132 = t232 = nullptr;
+        }
     }
     static size_t bytes(int Q, bool mixed, bool no_matrix = false) {
-        size_t d = sizeof(double) * ((size_t)tab_tail_len(Q, N1) + 14 * NA + 24 * N1 + 12 * N1 + 32);
-        if (mixed) d += sizeof(float) * ((size_t)tri_len(NA) + N1 * N1 + 12 * NA);
-        else if (!no_matrix) d += sizeof(double) * (size_t)NA * NA;
+        const size_t tail = (size_t)tab_tail_len(Q, N1) + 24 * N1 + 12 * N1 + RED;
+        if (mixed) return sizeof(double) * (tail + 10 * NA) + sizeof(float) * ((size_t)tri_len(NA) + N1 * N1 + 12 * NA);
+        size_t d = sizeof(double) * (tail + 14 * NA);
+        if (!no_matrix) d += sizeof(double) * (size_t)NA * NA;
         return d;
     }
     __device__ SolveScratch32 scratch32(bool s_system) const {

@@ -163,20 +163,6 @@ __device__ __forceinline__ T block_dot(const T *a, const T *b, double *red) {
     return block_sum<T>(t < NA ? a[t] * b[t] : (T)0, red);
 }
 
-// y = A x for an NA x NA row-major matrix in shared memory
-template <int NA, typename T>
-__device__ __forceinline__ void matvec(const T *A, const T *x, T *y) {
-    const int t = threadIdx.x;
-    if (t < NA) {
-        T s = 0;
-        const T *row = A + t * NA;
-#pragma unroll 9
-        for (int k = 0; k < NA; ++k) s += row[k] * x[k];
-        y[t] = s;
-    }
-    __syncthreads();
-}
-
 // Lower triangle of a symmetric NA x NA matrix, row by row: entry (i, k),
 // k <= i, at i (i + 1) / 2 + k.  The FP32 element matrices of the mixed
 // solves are kept this way (half the shared memory of the full matrix).
@@ -185,16 +171,16 @@ __host__ __device__ constexpr int tri_len(int na) { return na * (na + 1) / 2; }
 // y = A x for a symmetric A held as its packed lower triangle: row t reads
 // (t, 0..t) from row t and (k, t) for k > t from the rows below, so every
 // product and the order of the sum are those of the full row-major matvec.
-template <int NA>
-__device__ __forceinline__ void matvec_packed(const float *L, const float *x, float *y) {
+template <int NA, typename T>
+__device__ __forceinline__ void matvec_packed(const T *L, const T *x, T *y) {
     const int t = threadIdx.x;
     if (t < NA) {
-        float s = 0.f;
+        T s = 0;
         const int row = t * (t + 1) / 2;
         int col = t;                    // k (k + 1) / 2 + t at k = 0
 #pragma unroll 9
         for (int k = 0; k < NA; ++k) {
-            s = fmaf(k <= t ? L[row + k] : L[col], x[k], s);
+            s = fma(k <= t ? L[row + k] : L[col], x[k], s);
             col += k + 1;
         }
         y[t] = s;
@@ -324,7 +310,8 @@ __device__ void precondition(const T *r, T *z, const T *Ps, const T *d, T *t1, T
     __syncthreads();
 }
 
-// Preconditioned CG on A (+ w w^T when W) with x0 = x (x0_zero: x0 = 0).
+// Preconditioned CG on A (packed lower triangle; + w w^T when W) with x0 = x
+// (x0_zero: x0 = 0).
 // Stops when ||r|| <= rtol ||b|| (tested before each iteration), after
 // maxit iterations, or when r.z = 0.  Returns the iteration count.
 template <int N1, bool W>
@@ -338,7 +325,7 @@ __device__ int pcg(const double *A, const double *w, const double *b, double *x,
         if (t < NA) { x[t] = 0.0; r[t] = b[t]; }
         __syncthreads();
     } else {
-        matvec<NA>(A, x, Ap);
+        matvec_packed<NA, double>(A, x, Ap);
         double wx = W ? warp0_dot<NA>(w, x, red) : 0.0;
         if (t < NA) r[t] = b[t] - Ap[t] - (W ? w[t] * wx : 0.0);
         __syncthreads();
@@ -360,7 +347,7 @@ __device__ int pcg(const double *A, const double *w, const double *b, double *x,
     int it = 0;
     while (it < maxit) {
         if (sqrt(rr) <= rtol * bnorm || rz == 0.0) break;
-        matvec<NA>(A, p, Ap);
+        matvec_packed<NA, double>(A, p, Ap);
         // p.(A + w w^T)p = p.Ap + (w.p)^2: one reduction for both
         double pAp, wp = 0.0;
         if (W) {
@@ -405,7 +392,7 @@ __device__ int pcg32(const float *A, const float *w, const float *b, float *x, f
     int it = 0;
     while (it < imaxit) {
         if (sqrtf(rr) <= irtol || rz == 0.f) break;
-        matvec_packed<NA>(A, p, Ap);
+        matvec_packed<NA, float>(A, p, Ap);
         // p.(A + w w^T)p = p.Ap + (w.p)^2: one reduction for both
         float pAp = t < NA ? p[t] * Ap[t] : 0.f, wp = (W && t < NA) ? w[t] * p[t] : 0.f;
         block_sum2<float>(pAp, wp, red);
@@ -810,8 +797,9 @@ template <int N1>
 struct StageSmem {
     static constexpr int NA = N1 * N1;
     static constexpr int RED = 20;   // reduction scratch: 2 x 16 warp partials at most, in doubles
-    // A: the FP64 element matrix (FP64 solves only; the mixed solves read it
-    // from global memory for their few FP64 residuals)
+    // A: the FP64 element matrix, packed lower triangle (FP64 solves only; the
+    // mixed solves read the full matrix from global memory for their few FP64
+    // residuals)
     double *A, *tb, *Yu, *Yv, *ru, *rv, *x, *r, *z, *p, *Ap, *w, *dS, *dM, *t1, *t2, *fw, *L, *red;
     // FP32 area (mixed precision only): matrix, preconditioner and PCG vectors
     float *A32, *Ps32, *dS32, *dM32, *w32, *r32, *z32, *p32, *Ap32, *c32, *u32, *v32, *t132, *t232;
@@ -846,7 +834,7 @@ struct StageSmem {
         const size_t tail = (size_t)tab_tail_len(Q, N1) + 24 * N1 + 12 * N1 + RED;
         if (mixed) return sizeof(double) * (tail + 10 * NA) + sizeof(float) * ((size_t)tri_len(NA) + N1 * N1 + 12 * NA);
         size_t d = sizeof(double) * (tail + 14 * NA);
-        if (!no_matrix) d += sizeof(double) * (size_t)NA * NA;
+        if (!no_matrix) d += sizeof(double) * (size_t)tri_len(NA);
         return d;
     }
     __device__ SolveScratch32 scratch32(bool s_system) const {
@@ -1049,11 +1037,16 @@ __device__ __forceinline__ void fold_apply(const double *__restrict__ Ge, const 
     __syncthreads();
 }
 
+// the lower triangle of a symmetric element matrix into shared memory,
+// packed (tri_len doubles: half the full matrix)
 template <int N1>
 __device__ void load_matrix(double *A, const double *src) {
     constexpr int NA = N1 * N1;
     // element matrices start at e*NA*NA doubles: only 8-byte alignment is guaranteed
-    for (int i = threadIdx.x; i < NA * NA; i += blockDim.x) cp_async_8(A + i, src + i);
+    for (int q = threadIdx.x; q < NA * NA; q += blockDim.x) {
+        const int i = q / NA, k = q - (q / NA) * NA;
+        if (k <= i) cp_async_8(A + i * (i + 1) / 2 + k, src + q);
+    }
     cp_async_wait_all();
     __syncthreads();
 }
@@ -1092,7 +1085,7 @@ __device__ __forceinline__ void var_stage_body(const VarParams &P, const VarBufs
             matvec_g<NA>(Sg, s.Yu, s.Ap);
         } else {
             load_matrix<N1>(s.A, Sg);
-            matvec<NA>(s.A, s.Yu, s.Ap);
+            matvec_packed<NA, double>(s.A, s.Yu, s.Ap);
         }
         if (t < NA) s.rv[t] -= s.Ap[t];
         __syncthreads();

@@ -71,14 +71,15 @@ void enqueue_steps(gdg_batch *b, int nsteps, cudaStream_t s) {
         for (int st = 1; st <= 4; ++st) launch_stage_all(b, st, s);
 }
 
-// best of two stage-1 launches of the current shape (stage 1 reads y_n and
-// its traces and writes only buffers that the real step rewrites)
-float time_stage1(gdg_batch *b, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
+// best of two runs of stages 1, 2 and 3 of the current shape: they read y_n
+// and write only the stage buffers and the accumulator, which the real
+// step's stage 1 rewrites (stage 4, the one that writes y_n, is not run)
+float time_stages(gdg_batch *b, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
     float t = 1e30f;
     for (int rep = 0; rep < 2; ++rep) {
         float ms = 0.f;
         cudaEventRecord(e0, s);
-        launch_stage_all(b, 1, s);
+        for (int st = 1; st <= 3; ++st) launch_stage_all(b, st, s);
         cudaEventRecord(e1, s);
         cudaEventSynchronize(e1);
         cudaEventElapsedTime(&ms, e0, e1);
@@ -87,7 +88,7 @@ float time_stage1(gdg_batch *b, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) 
     return t;
 }
 
-// Time the candidates on the batch's own stage-1 work: every register budget
+// Time the candidates on the batch's own stages 1-3: every register budget
 // x resident blocks per SM with one item per turn (each budget scanned from
 // its most resident blocks down, left once a candidate is 10 % slower than
 // that budget's best so far), then 2, 4 and 8 items per turn on the best.
@@ -104,7 +105,7 @@ int autotune(gdg_batch *b, cudaStream_t s) {
         for (int r = maxr; r >= 1; --r) {
             b->variant = v;
             b->per_sm = r;
-            const float t = time_stage1(b, s, e0, e1);
+            const float t = time_stages(b, s, e0, e1);
             if (t < best) { best = t; best_r = r; best_v = v; }
             if (t < vbest) vbest = t;
             else if (t > 1.1f * vbest) break;
@@ -115,7 +116,7 @@ int autotune(gdg_batch *b, cudaStream_t s) {
         b->per_sm = best_r;
         for (int c : {2, 4, 8}) {
             b->chunk = c;
-            const float t = time_stage1(b, s, e0, e1);
+            const float t = time_stages(b, s, e0, e1);
             if (t < best) { best = t; best_c = c; }
         }
     }
@@ -251,11 +252,16 @@ extern "C" int gdg_batch_step(gdg_batch *b, double *const *u, double *const *v, 
         cudaMemcpyAsync(b->d_probs, b->h_probs.data(), b->count * sizeof(BatchProb), cudaMemcpyHostToDevice, s) !=
             cudaSuccess)
         return berr(b, GDG_ECUDA, "descriptor upload");
-    for (int i = 0; i < b->count; ++i) {
-        gdg_ctx *c = b->ctx[i];
-        st = c->pb.coef == GDG_COEF_CONST ? gdg_const_enter(c, u[i], v[i], s) : gdg_var_enter(c, u[i], v[i], s);
-        if (st) return berr(b, st, "enter: " + c->err);
-    }
+    auto enter = [&]() -> int {
+        for (int i = 0; i < b->count; ++i) {
+            gdg_ctx *c = b->ctx[i];
+            const int e = c->pb.coef == GDG_COEF_CONST ? gdg_const_enter(c, u[i], v[i], s)
+                                                       : gdg_var_enter(c, u[i], v[i], s);
+            if (e) return berr(b, e, "enter: " + c->err);
+        }
+        return GDG_OK;
+    };
+    if ((st = enter())) return st;
     if (!b->tuned) {
         if (b->exec) {   // re-tuning after gdg_batch_set_tuning(.., 0): the graph holds the old shape
             cudaGraphExecDestroy(b->exec);
@@ -263,6 +269,9 @@ extern "C" int gdg_batch_step(gdg_batch *b, double *const *u, double *const *v, 
             b->graph_steps = 0;
         }
         if ((st = autotune(b, s))) return st;
+        // the tuner's stage 2 overwrote the traces of y_n that the step's
+        // stage 1 reads: enter again
+        if ((st = enter())) return st;
     }
     // graph of G steps, replayed
     const int G = 4;

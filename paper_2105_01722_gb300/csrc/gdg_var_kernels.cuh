@@ -807,9 +807,13 @@ struct StageSmem {
     // scratch z, t1, t2 (used only before the first FP32 sweep of a solve)
     // shares the FP32 PCG vectors' space: 4 fewer FP64 vectors, 8 elements
     // per SM instead of 7.
+    // The mixed form reads the tail of the 1-D tables (wq, dphi, Psi, lam) from
+    // global memory through L1 (it uses Psi in FP64 once per solve): 1.3 KB
+    // less per block, so the batched launch, with its parameter slots, also
+    // fits 8 blocks per SM.
     __device__ StageSmem(double *base, int Q, bool mixed, bool no_matrix = false) {
-        tb = base;   // tail of the 1-D tables (tab_tail_len)
-        Yu = tb + tab_tail_len(Q, N1);
+        tb = mixed ? nullptr : base;   // tail of the 1-D tables (tab_tail_len)
+        Yu = base + (mixed ? 0 : tab_tail_len(Q, N1));
         Yv = Yu + NA; ru = Yv + NA; rv = ru + NA; x = rv + NA; r = x + NA;
         if (mixed) {
             Ap = r + NA; w = Ap + NA; dS = w + NA; dM = dS + NA;
@@ -831,7 +835,7 @@ struct StageSmem {
         }
     }
     static size_t bytes(int Q, bool mixed, bool no_matrix = false) {
-        const size_t tail = (size_t)tab_tail_len(Q, N1) + 24 * N1 + 12 * N1 + RED;
+        const size_t tail = (size_t)(mixed ? 0 : tab_tail_len(Q, N1)) + 24 * N1 + 12 * N1 + RED;
         if (mixed) return sizeof(double) * (tail + 10 * NA) + sizeof(float) * ((size_t)tri_len(NA) + N1 * N1 + 12 * NA);
         size_t d = sizeof(double) * (tail + 14 * NA);
         if (!no_matrix) d += sizeof(double) * (size_t)tri_len(NA);
@@ -1060,14 +1064,14 @@ __device__ __forceinline__ void var_stage_body(const VarParams &P, const VarBufs
     const int t = threadIdx.x;
     const size_t off = (size_t)e * NA;
     const double *Sg = P.S + (size_t)e * NA * NA, *Mg = P.M + (size_t)e * NA * NA;
-    load_tabs(s.tb, P.tab + 2 * P.Q * N1, tab_tail_len(P.Q, N1));
+    if (s.tb) load_tabs(s.tb, P.tab + 2 * P.Q * N1, tab_tail_len(P.Q, N1));
     if (t < NA) {
         s.Yu[t] = b.yU[off + t];
         s.Yv[t] = b.yV[off + t];
         s.w[t] = P.w[off + t];
     }
     __syncthreads();
-    const Tabs T = tabs_split(P.tab, s.tb, P.Q, N1);
+    const Tabs T = tabs_split(P.tab, s.tb ? s.tb : P.tab + 2 * P.Q * N1, P.Q, N1);
     fdm_diagonals<N1>(P, e, s.dS, s.dM);
     const bool guess = b.part == 2;
     if (P.inverse) {
@@ -1208,14 +1212,14 @@ k_var_pcg(VarParams P, int which, const double *bvec, double *xvec, int *iters, 
     StageSmem<N1> s(smraw, P.Q, P.mixed, false);
     const int e = blockIdx.x, t = threadIdx.x;
     const size_t off = (size_t)e * NA;
-    load_tabs(s.tb, P.tab + 2 * P.Q * N1, tab_tail_len(P.Q, N1));
+    if (s.tb) load_tabs(s.tb, P.tab + 2 * P.Q * N1, tab_tail_len(P.Q, N1));
     if (t < NA) {
         s.ru[t] = bvec[off + t];
         s.x[t] = xvec[off + t];
         s.w[t] = P.w[off + t];
     }
     __syncthreads();
-    const Tabs T = tabs_split(P.tab, s.tb, P.Q, N1);
+    const Tabs T = tabs_split(P.tab, s.tb ? s.tb : P.tab + 2 * P.Q * N1, P.Q, N1);
     fdm_diagonals<N1>(P, e, s.dS, s.dM);
     const double *Ag = (which ? P.S : P.M) + (size_t)e * NA * NA;
     if (!P.mixed) load_matrix<N1>(s.A, Ag);

@@ -203,3 +203,57 @@ def test_batch_matches_oracle(form):
         ref = np.concatenate([Uo.ravel(), Vo.ravel()])
         assert _rel(got, ref) < steps * per_step, (form, i, _rel(got, ref), steps * per_step)
     batch.close()
+
+
+@pytest.mark.parametrize("N", [7, 9])
+def test_batch_fluxes_sides_and_cell_counts(N):
+    """Batches of N = 7 (64-thread blocks, 4-element modal tiles) and N = 9
+    (128-thread blocks, 6-element tiles) whose problems differ in flux
+    (central, upwind, alternating), in periodic sides and in rectangular
+    element grids, constant and variable c^2 (PCG and element inverses): each
+    problem equals its own gdg_step, under the tuner and under every register
+    budget (the batch stages each problem's flux and side flags itself)."""
+    settings = [
+        (gdg.FLUX_CENTRAL, (gdg.BC_PERIODIC, gdg.BC_DIRICHLET), (5, 4), False, gdg.SOLVE_PCG),
+        (gdg.FLUX_UPWIND, (gdg.BC_DIRICHLET, gdg.BC_PERIODIC), (3, 6), True, gdg.SOLVE_PCG),
+        (gdg.FLUX_ALTERNATING, (gdg.BC_PERIODIC, gdg.BC_PERIODIC), (4, 4), False, gdg.SOLVE_PCG),
+        (gdg.FLUX_ALTERNATING, (gdg.BC_DIRICHLET, gdg.BC_DIRICHLET), (4, 3), True, gdg.SOLVE_INVERSE),
+        (gdg.FLUX_CENTRAL, (gdg.BC_PERIODIC, gdg.BC_PERIODIC), (6, 5), True, gdg.SOLVE_PCG),
+        (gdg.FLUX_UPWIND, (gdg.BC_DIRICHLET, gdg.BC_DIRICHLET), (2, 7), False, gdg.SOLVE_PCG),
+    ]
+    built = []
+    for i, (flux, bc, n, variable, solver) in enumerate(settings):
+        p = ((3, 5, 7) if N >= 9 else (3, 5))[i % (3 if N >= 9 else 2)]
+        X, Y = inputs.cartesian_nodes(n, N)
+        U = np.sin(np.pi * X) * np.cos(np.pi * Y) + 0.1 * inputs.random_state(X.shape, 70 + i)
+        if variable:
+            C2 = inputs.smooth_random_c2(X, Y, 900 + i)
+            pb = gdg.make_problem(2, n, N, p, coef=gdg.COEF_NODAL, x_nodes=X, y_nodes=Y, c2_nodes=C2, flux=flux,
+                                  bc=bc, pcg_rtol=1e-10, pcg_maxit=100, solver=solver)
+            cmax = float(np.sqrt(C2.max()))
+        else:
+            pb = gdg.make_problem(2, n, N, p, flux=flux, bc=bc, c2=1.3)
+            cmax = float(np.sqrt(1.3))
+        built.append((pb, U.ravel(), 0.1 / (max(n) * N) / cmax))
+    refs = []
+    for pb, U0, dt in built:
+        ctx = gdg.Context(pb)
+        u = torch.tensor(U0, device="cuda")
+        v = torch.zeros_like(u)
+        ctx.step(u, v, 0.0, dt, 5)
+        refs.append(torch.cat([u, v]).cpu().numpy())
+        ctx.close()
+    batch = gdg.Batch([b[0] for b in built])
+    dts = [b[2] for b in built]
+    for shape in (None, (0, 1, 1), (1, 2, 2), (2, 3, 1)):
+        if shape is not None:
+            batch.set_tuning(*shape)
+        us = [torch.tensor(b[1], device="cuda") for b in built]
+        vs = [torch.zeros_like(u) for u in us]
+        batch.step(us, vs, dts, 5)
+        if shape is None:
+            assert batch.tuning()["tile_elements"] == {7: 64 // 16, 9: 128 // 20}[N]
+        for i, ref in enumerate(refs):
+            a = torch.cat([us[i], vs[i]]).cpu().numpy()
+            assert np.abs(a - ref).max() <= 1e-15 * np.abs(ref).max(), (shape, i)
+    batch.close()

@@ -222,8 +222,28 @@ int gdg_var_setup(gdg_ctx *ctx) {
         (st = gdg_cuda_check(ctx, cudaMemcpy(D->d_nodes + nd, ctx->pb.y_nodes, nd * sizeof(double), cudaMemcpyHostToDevice), "upload y")) ||
         (st = gdg_cuda_check(ctx, cudaMemcpy(D->d_nodes + 2 * nd, ctx->pb.c2_nodes, nd * sizeof(double), cudaMemcpyHostToDevice), "upload c2")))
         return st;
+    {   // parallelogram elements: nodes an affine function of the (equispaced) reference nodes
+        const double *Xh = ctx->pb.x_nodes, *Yh = ctx->pb.y_nodes;
+        std::vector<unsigned char> aff((size_t)ctx->ne, 0);
+        for (int e = 0; e < ctx->ne; ++e) {
+            const double *x = Xh + (size_t)e * NA, *y = Yh + (size_t)e * NA;
+            const double ax = x[1] - x[0], bx = x[n1] - x[0], ay = y[1] - y[0], by = y[n1] - y[0];
+            const double tol = 1e-12 * (std::fabs(ax) + std::fabs(bx) + std::fabs(ay) + std::fabs(by));
+            bool ok = true;
+            for (int j = 0; j < n1 && ok; ++j)
+                for (int i = 0; i < n1 && ok; ++i)
+                    ok = std::fabs(x[j * n1 + i] - (x[0] + i * ax + j * bx)) <= tol &&
+                         std::fabs(y[j * n1 + i] - (y[0] + i * ay + j * by)) <= tol;
+            aff[e] = ok;
+        }
+        if ((st = gdg_cuda_check(ctx, cudaMalloc((void **)&D->d_affine, aff.size()), "alloc affine")) ||
+            (st = gdg_cuda_check(ctx, cudaMemcpy(D->d_affine, aff.data(), aff.size(), cudaMemcpyHostToDevice),
+                                 "upload affine")))
+            return st;
+    }
     VarParams &P = D->vp;
     P.nx = ctx->nx; P.ny = ctx->ny; P.ne = ctx->ne; P.Q = Q;
+    P.affine = D->d_affine;
     P.per_x = ctx->pb.bc[0] == GDG_BC_PERIODIC;
     P.per_y = ctx->pb.bc[1] == GDG_BC_PERIODIC;
     P.upwind = ctx->pb.flux == GDG_FLUX_UPWIND;
@@ -347,7 +367,7 @@ int gdg_var_setup(gdg_ctx *ctx) {
 void gdg_var_free(gdg_ctx *ctx) {
     VarData *D = ctx->var;
     if (!D) return;
-    cudaFree(D->d_S); cudaFree(D->d_M); cudaFree(D->d_S32); cudaFree(D->d_M32); cudaFree(D->d_dS); cudaFree(D->d_Ainv); cudaFree(D->d_Minv); cudaFree(D->d_G); cudaFree(D->d_FM); cudaFree(D->d_time); cudaFree(D->d_src); cudaFree(D->d_w); cudaFree(D->d_pre); cudaFree(D->d_face);
+    cudaFree(D->d_S); cudaFree(D->d_M); cudaFree(D->d_S32); cudaFree(D->d_M32); cudaFree(D->d_dS); cudaFree(D->d_Ainv); cudaFree(D->d_Minv); cudaFree(D->d_G); cudaFree(D->d_FM); cudaFree(D->d_time); cudaFree(D->d_src); cudaFree(D->d_w); cudaFree(D->d_pre); cudaFree(D->d_face); cudaFree(D->d_affine);
     cudaFree(D->d_tab); cudaFree(D->d_nodes); cudaFree(D->d_state); cudaFree(D->d_tr);
     cudaFree(D->d_c2feat); cudaFree(D->d_wbf16); cudaFree(D->d_mlp);
     cudaFree(D->d_ru); cudaFree(D->d_rv); cudaFree(D->d_x0u);

@@ -32,6 +32,8 @@ struct VarParams {
                                  // [4] unconverged u, [5] unconverged v, [6] element solves,
                                  // [7] sum sweeps u, [8] sum sweeps v, [9] max sweeps u, [10] max sweeps v
     int mixed;                   // FP32 inner PCG + FP64 refinement
+    const unsigned char *affine; // [ne] 1: the element is a parallelogram (J constant), so the
+                                 // frozen-coefficient mass preconditioner is M_J^-1 exactly
     int refine_max;              // FP64 refinement sweeps per solve
     float refine_rtol;           // inner FP32 PCG relative tolerance
 };
@@ -46,6 +48,7 @@ struct VarData {
     double *d_time = nullptr, *d_src = nullptr;  // point source: time, weights [2][NA]
     double *d_Ainv = nullptr, *d_Minv = nullptr; // setup temporaries of the fold, freed after it
     double *d_tab = nullptr, *d_nodes = nullptr;
+    unsigned char *d_affine = nullptr;           // per element: a parallelogram
     double *d_state = nullptr, *d_tr = nullptr;
     long long tr_len = 0;
     unsigned long long *d_stats = nullptr;
@@ -1128,10 +1131,13 @@ __device__ __forceinline__ void var_stage_body(const VarParams &P, const VarBufs
     if (!P.mixed) load_matrix<N1>(s.A, Mg);
     if (P.mixed) {
         to_fp32<N1>(P.M32 + (size_t)e * tri_len(NA), s.A32, T.Ps, s.Ps32, s.dM, s.dM32, nullptr, nullptr);
+        // the FP64 preconditioned step first only where it solves the mass
+        // system outright (a parallelogram); elsewhere it would cost an FP64
+        // product and still leave two FP32 sweeps
         const Step64 st64{s.z, s.t1, s.t2, T.Ps, s.dM};
         sw_v = refine<N1, false>(Mg, s.w, s.rv, s.x, s.r, s.Ap, s.scratch32(false), s.red, P.rtol,
                                  P.refine_max, P.refine_rtol, P.maxit, none, true, &it_v, &rel_v, false, nullptr,
-                                 &st64);
+                                 P.affine[e] ? &st64 : nullptr);
         bad_v = sw_v >= P.refine_max && rel_v > P.rtol;
     } else {
         it_v = pcg<N1, false>(s.A, s.w, s.rv, s.x, s.r, s.z, s.p, s.Ap, T.Ps, s.dM, s.t1, s.t2, s.red, P.rtol,

@@ -451,6 +451,37 @@ def forms_equal_error(T=0.25, ps=(3, 5), n=128):
     return out
 
 
+def forms_routes(steps=64):
+    """The two states of the diagonalised route on the headline workload
+    (64x64 elements, p=5, FP64): GDG_ROUTE_MODAL (modal coefficients from the
+    first stage to the last; the timed stage kernel or the persistent step)
+    against GDG_ROUTE_NODAL (nodal state; every stage transforms its input to
+    the modified basis and its k back with n1 x n1 contractions per
+    direction)."""
+    import numpy as np
+    import torch
+    from paper_2105_01722_gb300 import gdg, inputs
+    w = WORKLOAD
+    X, Y = inputs.cartesian_nodes(w["n"], w["N"])
+    U0, V0 = inputs.standing_mode_2d(X, Y)
+    dt = w["cfl"] / (w["n"][0] * w["N"])
+    out = {"workload": WORKLOAD_NAME, "steps_per_call": steps}
+    res = {}
+    for route, name in ((gdg.ROUTE_MODAL, "modal"), (gdg.ROUTE_NODAL, "nodal")):
+        pb = gdg.make_problem(2, w["n"], w["N"], w["p"], flux=gdg.FLUX_UPWIND, c2=1.0, route=route)
+        ctx = gdg.Context(pb)
+        u = torch.tensor(U0.ravel(), device="cuda")
+        v = torch.tensor(V0.ravel(), device="cuda")
+        ctx.step(u, v, 0.0, dt, steps)
+        ms = _timed_ms(lambda: ctx.step(u, v, 0.0, dt, steps))
+        res[name] = torch.cat([u, v]).cpu().numpy()
+        out[name] = {"dof_steps_per_s": dof() * steps / (ms / 1e3), "ms_per_step": ms / steps}
+        ctx.close()
+    out["nodal_vs_modal_rel_l2"] = float(np.linalg.norm(res["nodal"] - res["modal"]) / np.linalg.norm(res["modal"]))
+    out["modal_over_nodal"] = out["modal"]["dof_steps_per_s"] / out["nodal"]["dof_steps_per_s"]
+    return out
+
+
 def executed_flops_per_element_stage_3d(n1):
     """FP64 flops the 3-D parity stage kernel executes per element (FMA = 2):
     fluxes 3 directions x n1^2 x (2 faces x 7 + 4 sums/differences), per
@@ -785,6 +816,7 @@ def run_gdg(args):
         if not args.no_forms and world == 1:
             for key, fn in (("variable_mapped_128", forms_variable), ("batched_48", forms_batched),
                             ("batched_48_small", lambda: forms_batched(nmin=8, nmax=24)),
+                            ("routes_64", forms_routes),
                             ("learned_guess", forms_learned), ("three_d_32", forms_three_d),
                             ("ocean_channel", forms_ocean)):
                 try:

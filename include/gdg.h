@@ -87,8 +87,13 @@ enum { GDG_FP64 = 0, GDG_MIXED = 1 };
  * inner solves are FP32) or do not converge. */
 enum { GDG_TF32 = 2, GDG_BF16 = 3 };
 /* State representation used inside gdg_step for the diagonalised route:
- * modal coefficients U = Psi Ubar (Section 3.2).  The nodal-state route is
- * not built: gdg_create returns GDG_EUNSUPPORTED for GDG_ROUTE_NODAL. */
+ * GDG_ROUTE_MODAL keeps the modal coefficients U = Psi Ubar (Section 3.2)
+ * from the first stage to the last; GDG_ROUTE_NODAL keeps the nodal state
+ * and transforms every stage's input to the modal basis and its k back
+ * (two n1 x n1 contractions per direction and field each way), combining
+ * the RK stages on nodal vectors.  Both give the same U', V' to rounding;
+ * the nodal route does four separable transforms more per stage.  Nodal:
+ * dim 1 and 2, whole meshes (GDG_EUNSUPPORTED otherwise). */
 enum { GDG_ROUTE_MODAL = 0, GDG_ROUTE_NODAL = 1 };
 /* Operator selector of gdg_mass_solve / gdg_pcg. */
 enum { GDG_OP_M = 0, GDG_OP_S = 1 };

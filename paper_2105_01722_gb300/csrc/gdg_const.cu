@@ -1271,6 +1271,85 @@ void enqueue_rk4_step(gdg_ctx *ctx, double dt, cudaStream_t s) {
     launch_stage(ctx, M_S4, b, dt / 6.0, 0.0, s);
 }
 
+// ---------------------------------------------- nodal-state route ------
+// GDG_ROUTE_NODAL: the state stays nodal between stages.  Every stage
+// transforms its input to the modified basis (two n1 x n1 contractions per
+// direction and field, launch_sep), evaluates k there with the same stage
+// kernel as gdg_rhs, transforms k back, and combines on nodal vectors.  It
+// computes the modal route's U', V' to rounding and does four separable
+// transforms more per stage; it exists to measure the two routes against
+// each other.
+
+// RK4 combination on nodal vectors (the modal route's coefficients: the
+// accumulator holds k1 + 2 k2 + 2 k3, stage 4 forms y_n + cA (acc + k4))
+__global__ void k_rk_nodal(size_t n, int mode, double *nU, double *nV, const double *kU, const double *kV,
+                           double *aU, double *aV, double *yU, double *yV, double cA, double cY) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const double ku = kU[i], kv = kV[i];
+        if (mode == M_S1) {
+            aU[i] = ku; aV[i] = kv;
+            yU[i] = fma(cY, ku, nU[i]); yV[i] = fma(cY, kv, nV[i]);
+        } else if (mode == M_S23) {
+            aU[i] = fma(2.0, ku, aU[i]); aV[i] = fma(2.0, kv, aV[i]);
+            yU[i] = fma(cY, ku, nU[i]); yV[i] = fma(cY, kv, nV[i]);
+        } else {
+            nU[i] = fma(cA, aU[i] + ku, nU[i]); nV[i] = fma(cA, aV[i] + kv, nV[i]);
+        }
+    }
+}
+
+// one RK4 step of the nodal state (u, v): stage inputs in B_Y*, nodal k in
+// B_N* (free on this route), the modal stage input and k in B_X* / B_K*
+void enqueue_rk4_step_nodal(gdg_ctx *ctx, double *u, double *v, double dt, cudaStream_t s) {
+    const size_t n = (size_t)ctx->ndof;
+    const int threads = 256, blocks = (int)std::min<size_t>((n + threads - 1) / threads, 4096);
+    double *yU = buf(ctx, B_YU), *yV = buf(ctx, B_YV), *kU = buf(ctx, B_NU), *kV = buf(ctx, B_NV);
+    const double cY[4] = {0.5 * dt, 0.5 * dt, dt, 0.0};
+    const int mode[4] = {M_S1, M_S23, M_S23, M_S4};
+    for (int st = 0; st < 4; ++st) {
+        const double *inU = st == 0 ? u : yU, *inV = st == 0 ? v : yV;
+        launch_sep(ctx, inU, inV, buf(ctx, B_XU), buf(ctx, B_XV), T_P, nullptr, -1, s);
+        launch_traces(ctx, buf(ctx, B_XU), buf(ctx, B_XV), ctx->d_tr, s);
+        StageBufs b{};
+        b.yU = buf(ctx, B_XU); b.yV = buf(ctx, B_XV);
+        b.oU = buf(ctx, B_KU); b.oV = buf(ctx, B_KV);
+        b.trin = ctx->d_tr; b.lam2 = ctx->d_lam2;
+        launch_stage(ctx, M_RHS, b, 0.0, 0.0, s);
+        launch_sep(ctx, buf(ctx, B_KU), buf(ctx, B_KV), kU, kV, T_PSI, nullptr, -1, s);
+        k_rk_nodal<<<blocks, threads, 0, s>>>(n, mode[st], u, v, kU, kV, buf(ctx, B_AU), buf(ctx, B_AV), yU, yV,
+                                              dt / 6.0, cY[st]);
+    }
+}
+
+int step_nodal(gdg_ctx *ctx, double *u, double *v, double dt, int nsteps, cudaStream_t s) {
+    int st;
+    const int G = (nsteps >= 8 && !ctx->prof.on) ? 8 : 0;
+    if (G) {   // a graph of G steps on (u, v), replayed
+        GraphCache &gc = ctx->graph;
+        if (!gc.exec || gc.dt != dt || gc.steps != G || gc.u != u || gc.v != v) {
+            if (gc.exec) cudaGraphExecDestroy(gc.exec);
+            gc.exec = nullptr;
+            cudaGraph_t g;
+            if ((st = gdg_cuda_check(ctx, cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal), "capture")))
+                return st;
+            for (int i = 0; i < G; ++i) enqueue_rk4_step_nodal(ctx, u, v, dt, ctx->cap_stream);
+            if ((st = gdg_cuda_check(ctx, cudaStreamEndCapture(ctx->cap_stream, &g), "capture end"))) return st;
+            st = gdg_cuda_check(ctx, cudaGraphInstantiate(&gc.exec, g, 0), "instantiate");
+            cudaGraphDestroy(g);
+            if (st) return st;
+            gc.dt = dt;
+            gc.steps = G;
+            gc.u = u;
+            gc.v = v;
+        }
+        for (int i = 0; i + G <= nsteps; i += G)
+            if ((st = gdg_cuda_check(ctx, cudaGraphLaunch(gc.exec, s), "graph launch"))) return st;
+    }
+    const int rem = G ? nsteps % G : nsteps;
+    for (int i = 0; i < rem; ++i) enqueue_rk4_step_nodal(ctx, u, v, dt, s);
+    return gdg_cuda_check(ctx, cudaGetLastError(), "gdg_step (nodal-state route)");
+}
+
 // ---------------------------------------------- partitioned meshes ------
 // One mesh split by rows of elements over several contexts.  The stage
 // kernels read a halo side's neighbour traces from a ghost row of the trace
@@ -1647,6 +1726,7 @@ extern "C" int gdg_get_stage_variant(const gdg_ctx *ctx, int *variant) {
 
 int gdg_const_step(gdg_ctx *ctx, double *u, double *v, double dt, int nsteps, cudaStream_t s) {
     int st;
+    if (ctx->pb.route == GDG_ROUTE_NODAL) return step_nodal(ctx, u, v, dt, nsteps, s);
     launch_sep(ctx, u, v, buf(ctx, B_NU), buf(ctx, B_NV), T_P, nullptr, -1, s);
     launch_traces(ctx, buf(ctx, B_NU), buf(ctx, B_NV), ctx->d_tr, s);
     if ((st = gdg_cuda_check(ctx, cudaGetLastError(), "gdg_step prologue"))) return st;

@@ -372,7 +372,11 @@ static int validate(const gdg_problem *pb, std::string &why) {
         if (!(pb->c2 > 0.0)) { why = "c2 must be > 0"; return GDG_EINVAL; }
         if (pb->solver != GDG_SOLVE_DIAG) { why = "constant coefficients use GDG_SOLVE_DIAG"; return GDG_EINVAL; }
         if (pb->route != GDG_ROUTE_MODAL && pb->route != GDG_ROUTE_NODAL) { why = "bad route"; return GDG_EINVAL; }
-        if (pb->route == GDG_ROUTE_NODAL) { why = "the nodal-state route is not built (modal route only)"; return GDG_EUNSUPPORTED; }
+        if (pb->route == GDG_ROUTE_NODAL && pb->dim == 3) { why = "the nodal-state route: dim 1 and 2 only"; return GDG_EUNSUPPORTED; }
+        if (pb->route == GDG_ROUTE_NODAL && (pb->rows[0] || pb->rows[1])) {
+            why = "the nodal-state route: whole meshes only (no bands of rows)";
+            return GDG_EUNSUPPORTED;
+        }
         if (pb->precision != GDG_FP64) { why = "the diagonalised route has no solve to refine: FP64 only"; return GDG_EUNSUPPORTED; }
     } else if (pb->coef == GDG_COEF_NODAL) {
         if (pb->dim != 2) { why = "GDG_COEF_NODAL needs dim 2"; return GDG_EINVAL; }

@@ -72,6 +72,7 @@ struct GraphCache {
     cudaGraphExec_t exec = nullptr;
     double dt = 0.0;
     int steps = 0;
+    const void *u = nullptr, *v = nullptr;   // nodal-state route: the state the graph steps in place
 };
 
 struct VarData;   // variable-coefficient / mapped data (gdg_var.cu)

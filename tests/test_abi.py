@@ -103,7 +103,7 @@ def _nodal_kw(**extra):
 
 
 @pytest.mark.parametrize("kw, status", [
-    (dict(dim=2, n=(4, 4), N=8, p=5, route=gdg.ROUTE_NODAL), "EUNSUPPORTED"),    # modal route only
+    (dict(dim=3, n=(2, 2, 2), N=8, p=5, route=gdg.ROUTE_NODAL), "EUNSUPPORTED"),    # nodal route: dim <= 2
     (dict(dim=2, n=(4, 4), N=8, p=5, precision=gdg.MIXED), "EUNSUPPORTED"),      # nothing to refine
     ("inverse_mixed", "EUNSUPPORTED"),
     ("nodal_diag", "EINVAL"),

@@ -327,3 +327,31 @@ def test_persistent_step_headline_mesh_bit_identical():
         out.append((u.cpu().numpy(), v.cpu().numpy()))
         ctx.close()
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
+@pytest.mark.parametrize("c", [c for c in CASES if c["N"] >= 3], ids=_ids)
+def test_nodal_state_route_matches_oracle(c):
+    """GDG_ROUTE_NODAL (the state nodal between stages, every stage's input
+    transformed to the modified basis and its k back): 20 RK4 steps in one
+    call (graph path and remainder) match the oracle's RK4 within the
+    per-step route floor times the steps (reading r24), and the modal route
+    to rounding."""
+    prob = _oracle_problem(c)
+    ops = dc.operators(prob)
+    U, V = _state(c, 60)
+    pbn = _gpu_problem(c)
+    pbn.route = gdg.ROUTE_NODAL
+    ctxn, ctxm = gdg.Context(pbn), gdg.Context(_gpu_problem(c))
+    un, vn = _dev(U), _dev(V)
+    um, vm = _dev(U), _dev(V)
+    h = min(prob.H(k) for k in range(prob.dim)) / prob.N
+    dt = 0.1 * h / np.sqrt(c.get("c2", 1.0))
+    tol = _route_floor(prob, U, V)
+    ctxn.step(un, vn, 0.0, dt, 20)
+    ctxm.step(um, vm, 0.0, dt, 20)
+    f = lambda t, U, V: dc.time_derivative(prob, U, V, ops)
+    U, V = ti.integrate(f, U, V, 0.0, dt, 20)
+    assert _rel_state(un, vn, U, V) < 20 * tol
+    assert _rel_state(un, vn, um.cpu().numpy(), vm.cpu().numpy()) < 20 * tol
+    ctxn.close()
+    ctxm.close()

@@ -6,11 +6,11 @@
 // own data.  The element-solve bodies need about 60 registers; what a budget
 // buys is resident blocks where shared memory allows them:
 //   BATCH_HI  (gdg_batch.cu)      3 blocks of 96 threads per SM promised:
-//                                 up to 168 registers, nothing spills (FP64
-//                                 PCG: its 52 KB matrix allows 3 blocks);
+//                                 up to 168 registers, nothing spills;
 //   BATCH_MID (gdg_batch_mid.cu)  480 threads per SM: <= 128 registers (the
-//                                 mixed solves' 43 KB allow 5 blocks);
+//                                 FP64 PCG's 40 KB allow 5 blocks);
 //   BATCH_LO  (gdg_batch_lo.cu)   960 threads per SM: <= 64 registers (the
+//                                 mixed solves' 27 KB allow 8 blocks, and the
 //                                 precomputed-inverse route streams its
 //                                 operators and wants every warp it can get);
 //                                 the modal body reads y_n and the

@@ -2144,9 +2144,13 @@ GDG_CHECKS_READER(gdg_checks_read_const)
 
 namespace {
 __global__ void k_check_selftest(long long index, long long bound) {
+#if GDG_CHECKS
     long long i = index;
     GDG_CHECK_INDEX(i, 0, bound, GDG_SITE_SELFTEST, 0);
-    (void)i;
+#else
+    (void)index;
+    (void)bound;
+#endif
 }
 }  // namespace
 

@@ -806,28 +806,33 @@ struct StageSmem {
     double *A, *tb, *Yu, *Yv, *ru, *rv, *x, *r, *z, *p, *Ap, *w, *dS, *dM, *t1, *t2, *fw, *L, *red;
     // FP32 area (mixed precision only): matrix, preconditioner and PCG vectors
     float *A32, *Ps32, *dS32, *dM32, *w32, *r32, *z32, *p32, *Ap32, *c32, *u32, *v32, *t132, *t232;
-    // Mixed: no FP64 PCG runs, so p is not allocated, and the FP64 step's
-    // scratch z, t1, t2 (used only before the first FP32 sweep of a solve)
-    // shares the FP32 PCG vectors' space: 4 fewer FP64 vectors, 8 elements
-    // per SM instead of 7.
-    // The mixed form reads the tail of the 1-D tables (wq, dphi, Psi, lam) from
-    // global memory through L1 (it uses Psi in FP64 once per solve): 1.3 KB
-    // less per block, so the batched launch, with its parameter slots, also
-    // fits 8 blocks per SM.
+    // Mixed: no FP64 PCG runs, so p is not allocated, and one scratch region
+    // of FP32 PCG vectors serves three phases of the stage in turn: the face
+    // lines and line integrals of the lifts (fw, L: 36 N1 doubles), then the
+    // FP64 preconditioned step's z, t1, t2 (3 NA doubles; parallelograms
+    // only), then the FP32 PCG vectors of the refinement sweeps.  The tail of
+    // the 1-D tables (wq, dphi, Psi, lam) is read from global memory through
+    // L1 (Psi serves in FP64 once per solve).  24.1 KB a block at N1 = 9:
+    // 9 elements per SM, in the batched launch too (with its parameter
+    // slots).
+    static constexpr int SCR32 = 8 * NA > 72 * N1 ? 8 * NA : 72 * N1;   // scratch floats (>= 6 NA)
     __device__ StageSmem(double *base, int Q, bool mixed, bool no_matrix = false) {
         tb = mixed ? nullptr : base;   // tail of the 1-D tables (tab_tail_len)
         Yu = base + (mixed ? 0 : tab_tail_len(Q, N1));
         Yv = Yu + NA; ru = Yv + NA; rv = ru + NA; x = rv + NA; r = x + NA;
         if (mixed) {
             Ap = r + NA; w = Ap + NA; dS = w + NA; dM = dS + NA;
-            fw = dM + NA; L = fw + 24 * N1; red = L + 12 * N1;
+            red = dM + NA;
             A = nullptr;
             p = nullptr;
-            r32 = reinterpret_cast<float *>(red + RED);   // 8-byte aligned: the FP64 aliases below
-            z = reinterpret_cast<double *>(r32); t1 = z + NA; t2 = t1 + NA;   // 3 NA doubles <= 9 NA floats
+            double *scr = red + RED;                       // 8-byte aligned
+            fw = scr; L = fw + 24 * N1;                    // lifts
+            z = scr; t1 = z + NA; t2 = t1 + NA;            // FP64 step (after the lifts)
+            r32 = reinterpret_cast<float *>(scr);          // refinement sweeps (after both)
             z32 = r32 + NA; p32 = z32 + NA; Ap32 = p32 + NA; c32 = Ap32 + NA;
-            u32 = c32 + NA; v32 = u32 + NA; t132 = v32 + NA; t232 = t132 + NA;
-            A32 = t232 + NA;
+            u32 = c32 + NA; t132 = u32 + NA; t232 = t132 + NA;
+            v32 = nullptr;
+            A32 = r32 + SCR32;
             Ps32 = A32 + tri_len(NA); dS32 = Ps32 + N1 * N1; dM32 = dS32 + NA; w32 = dM32 + NA;
         } else {
             z = r + NA; p = z + NA;
@@ -838,9 +843,10 @@ struct StageSmem {
         }
     }
     static size_t bytes(int Q, bool mixed, bool no_matrix = false) {
-        const size_t tail = (size_t)(mixed ? 0 : tab_tail_len(Q, N1)) + 24 * N1 + 12 * N1 + RED;
-        if (mixed) return sizeof(double) * (tail + 10 * NA) + sizeof(float) * ((size_t)tri_len(NA) + N1 * N1 + 12 * NA);
-        size_t d = sizeof(double) * (tail + 14 * NA);
+        if (mixed)
+            return sizeof(double) * ((size_t)10 * NA + RED) +
+                   sizeof(float) * ((size_t)SCR32 + tri_len(NA) + N1 * N1 + 3 * NA);
+        size_t d = sizeof(double) * ((size_t)tab_tail_len(Q, N1) + 24 * N1 + 12 * N1 + RED + 14 * NA);
         if (!no_matrix) d += sizeof(double) * (size_t)tri_len(NA);
         return d;
     }

@@ -816,6 +816,7 @@ struct StageSmem {
     // 9 elements per SM, in the batched launch too (with its parameter
     // slots).
     static constexpr int SCR32 = 8 * NA > 72 * N1 ? 8 * NA : 72 * N1;   // scratch floats (>= 6 NA)
+    static constexpr int SCR64 = 4 * NA > 36 * N1 ? 4 * NA : 36 * N1;   // FP64 path: z, p, t1, t2 / fw, L
     __device__ StageSmem(double *base, int Q, bool mixed, bool no_matrix = false) {
         tb = mixed ? nullptr : base;   // tail of the 1-D tables (tab_tail_len)
         Yu = base + (mixed ? 0 : tab_tail_len(Q, N1));
@@ -835,9 +836,14 @@ struct StageSmem {
             A32 = r32 + SCR32;
             Ps32 = A32 + tri_len(NA); dS32 = Ps32 + N1 * N1; dM32 = dS32 + NA; w32 = dM32 + NA;
         } else {
-            z = r + NA; p = z + NA;
-            Ap = p + NA; w = Ap + NA; dS = w + NA; dM = dS + NA; t1 = dM + NA; t2 = t1 + NA;
-            fw = t2 + NA; L = fw + 24 * N1; red = L + 12 * N1;   // fw: face lines (own, neighbours')
+            // FP64 PCG / inverses: the lifts' face lines and line integrals
+            // (fw, L) share one region with the PCG vectors z, p, t1, t2,
+            // which run after the lifts (the inverse route uses no PCG)
+            double *scr = r + NA;
+            z = scr; p = z + NA; t1 = p + NA; t2 = t1 + NA;
+            fw = scr; L = fw + 24 * N1;
+            Ap = scr + SCR64; w = Ap + NA; dS = w + NA; dM = dS + NA;
+            red = dM + NA;
             A = no_matrix ? nullptr : red + RED;
             A32 = Ps32 = dS32 = dM32 = w32 = r32 = z32 = p32 = Ap32 = c32 = u32 = v32 = t132 = t232 = nullptr;
         }
@@ -846,7 +852,7 @@ struct StageSmem {
         if (mixed)
             return sizeof(double) * ((size_t)10 * NA + RED) +
                    sizeof(float) * ((size_t)SCR32 + tri_len(NA) + N1 * N1 + 3 * NA);
-        size_t d = sizeof(double) * ((size_t)tab_tail_len(Q, N1) + 24 * N1 + 12 * N1 + RED + 14 * NA);
+        size_t d = sizeof(double) * ((size_t)tab_tail_len(Q, N1) + 10 * NA + SCR64 + RED);
         if (!no_matrix) d += sizeof(double) * (size_t)tri_len(NA);
         return d;
     }

@@ -195,6 +195,37 @@ int gdg_var_setup(gdg_ctx *ctx) {
         }
     for (int i = 0; i < n1; ++i) { dL[i] = ctx->dphiL[i]; dR[i] = ctx->dphiR[i]; lam[i] = ctx->lamh[i]; }
     for (int i = 0; i < NA; ++i) Ps[i] = ctx->Psih[i];
+    // modes in parity order (the even ones first, each class in the original
+    // ascending-lambda order, so the constant mode stays first) where the
+    // basis has the r -> 1-r symmetry: the FP64 preconditioner then works by
+    // node pairs (precondition_parity)
+    bool parity = true;
+    {
+        double big = 0.0;
+        for (int i = 0; i < NA; ++i) big = std::max(big, std::fabs(Ps[i]));
+        std::vector<int> ev, od;
+        for (int k = 0; k < n1 && parity; ++k) {
+            bool even = true, odd = true;
+            for (int i = 0; i < n1; ++i) {
+                const double a = Ps[i * n1 + k], m = Ps[(n1 - 1 - i) * n1 + k];
+                if (std::fabs(m - a) > 1e-9 * big) even = false;
+                if (std::fabs(m + a) > 1e-9 * big) odd = false;
+            }
+            if (even) ev.push_back(k);
+            else if (odd) od.push_back(k);
+            else parity = false;
+        }
+        parity = parity && (int)ev.size() == (n1 + 1) / 2 && ev[0] == 0;
+        if (parity) {
+            std::vector<int> order(ev);
+            order.insert(order.end(), od.begin(), od.end());
+            const std::vector<double> P0(Ps, Ps + NA), L0(lam, lam + n1);
+            for (int k = 0; k < n1; ++k) {
+                lam[k] = L0[order[k]];
+                for (int i = 0; i < n1; ++i) Ps[i * n1 + k] = P0[i * n1 + order[k]];
+            }
+        }
+    }
 
     const size_t nd = (size_t)ctx->ndof;
     int st;
@@ -244,6 +275,7 @@ int gdg_var_setup(gdg_ctx *ctx) {
     VarParams &P = D->vp;
     P.nx = ctx->nx; P.ny = ctx->ny; P.ne = ctx->ne; P.Q = Q;
     P.affine = D->d_affine;
+    P.parity = parity;
     P.per_x = ctx->pb.bc[0] == GDG_BC_PERIODIC;
     P.per_y = ctx->pb.bc[1] == GDG_BC_PERIODIC;
     P.upwind = ctx->pb.flux == GDG_FLUX_UPWIND;

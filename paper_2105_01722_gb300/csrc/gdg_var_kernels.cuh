@@ -34,6 +34,8 @@ struct VarParams {
     int mixed;                   // FP32 inner PCG + FP64 refinement
     const unsigned char *affine; // [ne] 1: the element is a parallelogram (J constant), so the
                                  // frozen-coefficient mass preconditioner is M_J^-1 exactly
+    int parity;                  // the table's modes are in parity order (even modes first,
+                                 // Psi[N1-1-i][m] = +-Psi[i][m]): FP64 preconditioner by pairs
     int refine_max;              // FP64 refinement sweeps per solve
     float refine_rtol;           // inner FP32 PCG relative tolerance
 };
@@ -313,6 +315,89 @@ __device__ void precondition(const T *r, T *z, const T *Ps, const T *d, T *t1, T
     __syncthreads();
 }
 
+// The same z = Psi2 diag(d) Psi2^T r (FP64) with the modes in parity order:
+// the NE = ceil(N1/2) even modes first, Psi[N1-1-i][m] = Psi[i][m] for them
+// and -Psi[i][m] for the odd ones.  Each 1-D contraction then splits into an
+// even part over the NE node-pair sums (the middle node alone when N1 is odd)
+// and an odd part over the N1 - NE node-pair differences, so every output is
+// a dot of at most NE terms instead of N1: the four contractions cost about
+// half the multiplies, for a combination pass at each end.  Work arrays in
+// class layout: index q < NE is the even class with pair q, q >= NE the odd
+// class with pair q - NE (pair p: nodes p and N1-1-p).
+template <int N1>
+__device__ void precondition_parity(const double *r, double *z, const double *Ps, const double *d, double *t1,
+                                    double *t2) {
+    constexpr int NA = N1 * N1, NE = (N1 + 1) / 2;
+    const int t = threadIdx.x;
+    const int a = t / N1, b = t - (t / N1) * N1;
+    // pairs and signs of the nodes of this thread (used by the first and last pass)
+    if (t < NA) {   // combine r over node pairs, both directions -> t1[a][b] (class layout)
+        const bool oy = a >= NE, ox = b >= NE;
+        const int ry = oy ? a - NE : a, rx = ox ? b - NE : b;
+        const int my = N1 - 1 - ry, mx = N1 - 1 - rx;
+        double c0 = r[ry * N1 + rx], c1 = 0.0;
+        if (mx != rx) c0 = ox ? c0 - r[ry * N1 + mx] : c0 + r[ry * N1 + mx];
+        if (my != ry) {
+            c1 = r[my * N1 + rx];
+            if (mx != rx) c1 = ox ? c1 - r[my * N1 + mx] : c1 + r[my * N1 + mx];
+            c0 = oy ? c0 - c1 : c0 + c1;
+        }
+        t1[t] = c0;
+    }
+    __syncthreads();
+    if (t < NA) {   // x modes: t2[a][k] = sum over the class of k of t1[a][q] Psi[q][k]
+        const int q0 = b >= NE ? NE : 0, nq = b >= NE ? N1 - NE : NE;
+        double s = 0.0;
+#pragma unroll
+        for (int q = 0; q < NE; ++q)
+            if (q < nq) s = fma(t1[a * N1 + q0 + q], Ps[q * N1 + b], s);
+        t2[t] = s;
+    }
+    __syncthreads();
+    if (t < NA) {   // y modes and the diagonal: t1[l][k] = d[l][k] sum over the class of l
+        const int q0 = a >= NE ? NE : 0, nq = a >= NE ? N1 - NE : NE;
+        double s = 0.0;
+#pragma unroll
+        for (int q = 0; q < NE; ++q)
+            if (q < nq) s = fma(t2[(q0 + q) * N1 + b], Ps[q * N1 + a], s);
+        t1[t] = d[t] * s;
+    }
+    __syncthreads();
+    if (t < NA) {   // back to y pairs: t2[a][k] = sum over the modes l of the class of a
+        const int l0 = a >= NE ? NE : 0, nl = a >= NE ? N1 - NE : NE, p = a >= NE ? a - NE : a;
+        double s = 0.0;
+#pragma unroll
+        for (int q = 0; q < NE; ++q)
+            if (q < nl) s = fma(Ps[p * N1 + l0 + q], t1[(l0 + q) * N1 + b], s);
+        t2[t] = s;
+    }
+    __syncthreads();
+    if (t < NA) {   // back to x pairs: t1[a][b] = sum over the modes k of the class of b
+        const int k0 = b >= NE ? NE : 0, nk = b >= NE ? N1 - NE : NE, p = b >= NE ? b - NE : b;
+        double s = 0.0;
+#pragma unroll
+        for (int q = 0; q < NE; ++q)
+            if (q < nk) s = fma(Ps[p * N1 + k0 + q], t2[a * N1 + k0 + q], s);
+        t1[t] = s;
+    }
+    __syncthreads();
+    if (t < NA) {   // nodes: z[j][i] = (even + sx odd in x) (even + sy odd in y)
+        const int j = a, i = b;
+        const int pj = j < N1 - 1 - j ? j : N1 - 1 - j, pi = i < N1 - 1 - i ? i : N1 - 1 - i;
+        const bool midj = pj == N1 - 1 - pj, midi = pi == N1 - 1 - pi;
+        const double sy = j == pj ? 1.0 : -1.0, sx = i == pi ? 1.0 : -1.0;
+        double v = t1[pj * N1 + pi];
+        if (!midi) v = fma(sx, t1[pj * N1 + NE + pi], v);
+        if (!midj) {
+            double o = t1[(NE + pj) * N1 + pi];
+            if (!midi) o = fma(sx, t1[(NE + pj) * N1 + NE + pi], o);
+            v = fma(sy, o, v);
+        }
+        z[t] = v;
+    }
+    __syncthreads();
+}
+
 // Preconditioned CG on A (packed lower triangle; + w w^T when W) with x0 = x
 // (x0_zero: x0 = 0).
 // Stops when ||r|| <= rtol ||b|| (tested before each iteration), after
@@ -321,7 +406,7 @@ template <int N1, bool W>
 __device__ int pcg(const double *A, const double *w, const double *b, double *x, double *r, double *z,
                    double *p, double *Ap, const double *Ps, const double *d, double *t1, double *t2,
                    double *red, double rtol, int maxit, bool none, bool x0_zero, double *relres,
-                   bool fallback = false, int *fell = nullptr) {
+                   bool fallback = false, int *fell = nullptr, bool parity = false) {
     constexpr int NA = N1 * N1;
     const int t = threadIdx.x;
     if (x0_zero) {
@@ -342,7 +427,8 @@ __device__ int pcg(const double *A, const double *w, const double *b, double *x,
         }
     }
     const double bnorm = sqrt(warp0_dot<NA>(b, b, red));
-    precondition<N1>(r, z, Ps, d, t1, t2, none);
+    if (parity && !none) precondition_parity<N1>(r, z, Ps, d, t1, t2);
+    else precondition<N1>(r, z, Ps, d, t1, t2, none);
     if (t < NA) p[t] = z[t];
     // r.z and r.r in one reduction, before the loop and after every update
     double rz, rr;
@@ -365,7 +451,8 @@ __device__ int pcg(const double *A, const double *w, const double *b, double *x,
             r[t] -= alpha * (W ? Ap[t] + w[t] * wp : Ap[t]);
         }
         __syncthreads();
-        precondition<N1>(r, z, Ps, d, t1, t2, none);
+        if (parity && !none) precondition_parity<N1>(r, z, Ps, d, t1, t2);
+        else precondition<N1>(r, z, Ps, d, t1, t2, none);
         double rzn;
         warp0_dot2<NA>(r, z, r, r, red, rzn, rr);
         const double beta = rzn / rz;
@@ -440,6 +527,7 @@ struct SolveScratch32 {
 struct Step64 {
     double *z, *t1, *t2;
     const double *Ps, *d;
+    bool parity;   // modes in parity order (precondition_parity)
 };
 
 template <int N1, bool W>
@@ -450,7 +538,10 @@ __device__ int refine(const double *__restrict__ A, const double *w, const doubl
     constexpr int NA = N1 * N1;
     const int t = threadIdx.x;
     if (x0_zero && step64) {
-        precondition<N1>(b, step64->z, step64->Ps, step64->d, step64->t1, step64->t2, none);
+        if (step64->parity && !none)
+            precondition_parity<N1>(b, step64->z, step64->Ps, step64->d, step64->t1, step64->t2);
+        else
+            precondition<N1>(b, step64->z, step64->Ps, step64->d, step64->t1, step64->t2, none);
         matvec_g<NA>(A, step64->z, Ap);
         if (W) {
             const double wz = warp0_dot<NA>(w, step64->z, red);
@@ -1135,7 +1226,7 @@ __device__ __forceinline__ void var_stage_body(const VarParams &P, const VarBufs
         bad_u = sw_u >= P.refine_max && rel_u > P.rtol;
     } else {
         it_u = pcg<N1, true>(s.A, s.w, s.ru, s.x, s.r, s.z, s.p, s.Ap, T.Ps, s.dS, s.t1, s.t2, s.red, P.rtol,
-                             P.maxit, none, !guess, &rel_u, guess, &fell);
+                             P.maxit, none, !guess, &rel_u, guess, &fell, P.parity != 0);
         bad_u = it_u >= P.maxit && rel_u > P.rtol;
     }
     if (t < NA) s.ru[t] = s.Yv[t] + s.x[t];   // dU/dt
@@ -1146,14 +1237,14 @@ __device__ __forceinline__ void var_stage_body(const VarParams &P, const VarBufs
         // the FP64 preconditioned step first only where it solves the mass
         // system outright (a parallelogram); elsewhere it would cost an FP64
         // product and still leave two FP32 sweeps
-        const Step64 st64{s.z, s.t1, s.t2, T.Ps, s.dM};
+        const Step64 st64{s.z, s.t1, s.t2, T.Ps, s.dM, P.parity != 0};
         sw_v = refine<N1, false>(Mg, s.w, s.rv, s.x, s.r, s.Ap, s.scratch32(false), s.red, P.rtol,
                                  P.refine_max, P.refine_rtol, P.maxit, none, true, &it_v, &rel_v, false, nullptr,
                                  P.affine[e] ? &st64 : nullptr);
         bad_v = sw_v >= P.refine_max && rel_v > P.rtol;
     } else {
         it_v = pcg<N1, false>(s.A, s.w, s.rv, s.x, s.r, s.z, s.p, s.Ap, T.Ps, s.dM, s.t1, s.t2, s.red, P.rtol,
-                              P.maxit, none, true, &rel_v);
+                              P.maxit, none, true, &rel_v, false, nullptr, P.parity != 0);
         bad_v = it_v >= P.maxit && rel_v > P.rtol;
     }
     }
@@ -1255,10 +1346,10 @@ k_var_pcg(VarParams P, int which, const double *bvec, double *xvec, int *iters, 
                                    P.refine_max, P.refine_rtol, P.maxit, none, false, &it, &rr);
     } else if (which) {
         it = pcg<N1, true>(s.A, s.w, s.ru, s.x, s.r, s.z, s.p, s.Ap, T.Ps, s.dS, s.t1, s.t2, s.red, P.rtol,
-                           P.maxit, none, false, &rr);
+                           P.maxit, none, false, &rr, false, nullptr, P.parity != 0);
     } else {
         it = pcg<N1, false>(s.A, s.w, s.ru, s.x, s.r, s.z, s.p, s.Ap, T.Ps, s.dM, s.t1, s.t2, s.red, P.rtol,
-                            P.maxit, none, false, &rr);
+                            P.maxit, none, false, &rr, false, nullptr, P.parity != 0);
     }
     if (t < NA) xvec[off + t] = s.x[t];
     if (t == 0) {

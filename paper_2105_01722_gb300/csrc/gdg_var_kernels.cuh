@@ -231,7 +231,10 @@ __device__ __forceinline__ double warp0_dot(const double *a, const double *b, do
     return red[0];
 }
 
-// two such dot products with one pair of barriers: a.b and c.d
+// two such dot products with one pair of barriers: a.b and c.d.  The first
+// butterfly level splits the two sums between the half-warps (lanes 0-15
+// keep a.b, lanes 16-31 c.d, each adding its partner's partial of its own
+// sum), so the five levels cost five FP64 additions, not ten.
 template <int NA>
 __device__ __forceinline__ void warp0_dot2(const double *a, const double *b, const double *c, const double *d,
                                            double *red, double &ab, double &cd) {
@@ -243,12 +246,12 @@ __device__ __forceinline__ void warp0_dot2(const double *a, const double *b, con
             s = fma(a[k], b[k], s);
             q = fma(c[k], d[k], q);
         }
+        const bool lo = threadIdx.x < 16;
+        double v = (lo ? s : q) + __shfl_xor_sync(0xffffffffu, lo ? q : s, 16);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            s += __shfl_xor_sync(0xffffffffu, s, o);
-            q += __shfl_xor_sync(0xffffffffu, q, o);
-        }
-        if (threadIdx.x == 0) { red[0] = s; red[1] = q; }
+        for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (threadIdx.x == 0) red[0] = v;
+        if (threadIdx.x == 16) red[1] = v;
     }
     __syncthreads();
     ab = red[0];

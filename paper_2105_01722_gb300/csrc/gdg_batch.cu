@@ -8,14 +8,14 @@
 // FP64 or mixed precision, or precomputed inverses; by decreasing degree),
 // then tiles of the constant-coefficient problems' elements (modified-basis
 // route, half-line body) -- block b taking turns b, b + G, ... of a few
-// consecutive items.  The
-// stage bodies are the per-problem kernels' own (var_stage_body,
-// stage2h_body), so a batched step computes exactly what the problem's own
-// gdg_step computes.  A call's launches are captured once in a CUDA graph
-// (per-problem dt lives in device descriptors, so the graph does not depend
-// on it).  The register budget of the kernel (gdg_batch_kernel.cuh) and the
-// resident blocks per SM are picked on the first step by timing the
-// candidates on the batch's own data.
+// consecutive items.  The stage bodies are the per-problem kernels' own
+// (var_stage_body, stage2h_body), so a batched step computes exactly what
+// the problem's own gdg_step computes.  A call's launches are captured once
+// in a CUDA graph (per-problem dt lives in device descriptors, so the graph
+// does not depend on it).  The register budget of the kernel
+// (gdg_batch_kernel.cuh), the resident blocks per SM and the items per turn
+// are picked on the first step by timing the candidates on the batch's own
+// data.
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
@@ -72,8 +72,9 @@ void enqueue_steps(gdg_batch *b, int nsteps, cudaStream_t s) {
 }
 
 // best of two runs of stages 1, 2 and 3 of the current shape: they read y_n
-// and write only the stage buffers and the accumulator, which the real
-// step's stage 1 rewrites (stage 4, the one that writes y_n, is not run)
+// and write the stage buffers and the accumulator, which the real step's
+// stage 1 rewrites, and (stage 2) the traces of y_n, which the caller
+// rebuilds after tuning; stage 4, the one that writes y_n, is not run
 float time_stages(gdg_batch *b, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
     float t = 1e30f;
     for (int rep = 0; rep < 2; ++rep) {

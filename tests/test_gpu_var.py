@@ -463,3 +463,41 @@ def test_mixed_rhs_and_steps_match_fp64():
     assert su["unconverged"] == 0 and sv["unconverged"] == 0
     assert su["mean_sweeps"] <= 4 and sv["mean_sweeps"] <= 3
     cm.close(); cf.close()
+
+
+@pytest.mark.parametrize("p", [3, 5])
+def test_equal_error_against_refined_reference(p):
+    """The forms reach the same error: FP64 PCG, mixed (FP32 inner + FP64
+    refinement) and element inverses on the sine-mapped 8 x 8 mesh
+    (c^2 = 1 + 0.5 sin 2pi x cos 2pi y, Gaussian pulse of width 0.15) against
+    an FP64 run on the 16 x 16 mesh of the same map at dt/2 (every coarse node
+    is a fine node); each form's error is within 1.05x the FP64 PCG's (the
+    equal-error criterion of the benchmark's comparison)."""
+    import bench
+    n, N, T = 8, 8, 0.05
+    Xf, Yf = inputs.mapped_nodes((2 * n, 2 * n), N, 0.05)
+    X, Y = inputs.mapped_nodes((n, n), N, 0.05)
+    idx = bench.coarse_in_fine(n, N)
+    assert np.abs(Xf.ravel()[idx] - X.ravel()).max() < 1e-13
+    steps = int(round(T / (0.1 / (n * N) / np.sqrt(1.5))))
+    dt = T / steps
+    ctx = gdg.Context(gdg.make_problem(2, (2 * n, 2 * n), N, p, coef=gdg.COEF_NODAL, x_nodes=Xf, y_nodes=Yf,
+                                       c2_nodes=inputs.c2_sine(Xf, Yf), solver=gdg.SOLVE_INVERSE))
+    u = _dev(inputs.gaussian_pulse(Xf, Yf, 0.5, 0.5, 0.15))
+    v = torch.zeros_like(u)
+    ctx.step(u, v, 0.0, 0.5 * dt, 2 * steps)
+    ref = u.cpu().numpy()[idx]
+    ctx.close()
+    err = {}
+    for name, prec, solver in (("fp64", gdg.FP64, gdg.SOLVE_PCG), ("mixed", gdg.MIXED, gdg.SOLVE_PCG),
+                               ("inverse", gdg.FP64, gdg.SOLVE_INVERSE)):
+        ctx = gdg.Context(gdg.make_problem(2, (n, n), N, p, coef=gdg.COEF_NODAL, x_nodes=X, y_nodes=Y,
+                                           c2_nodes=inputs.c2_sine(X, Y), pcg_rtol=1e-10, pcg_maxit=100,
+                                           precision=prec, solver=solver))
+        u = _dev(inputs.gaussian_pulse(X, Y, 0.5, 0.5, 0.15))
+        v = torch.zeros_like(u)
+        ctx.step(u, v, 0.0, dt, steps)
+        err[name] = np.linalg.norm(u.cpu().numpy() - ref) / np.linalg.norm(ref)
+        ctx.close()
+    assert 0.0 < err["fp64"] < 0.1, err          # a discretisation error, not noise and not a blow-up
+    assert err["mixed"] <= 1.05 * err["fp64"] and err["inverse"] <= 1.05 * err["fp64"], err

@@ -73,6 +73,10 @@ __device__ __forceinline__ void traces3_yz(const ModalParams &mp, const double *
 template <int N1>
 __host__ __device__ constexpr int smem3_doubles() { return 12 * N1 * N1 + 2 * N1 * N1 * N1; }
 
+// elements per block of the 3-D kernels (epb3 on the host)
+template <int N1>
+__host__ __device__ constexpr int epb3c() { return MAXB3 / (N1 * N1) > 1 ? MAXB3 / (N1 * N1) : 1; }
+
 template <int N1, int MODE>
 __global__ void __launch_bounds__(MAXB3)
 k_stage3(const __grid_constant__ ModalParams mp, const StageBufs b, double cA, double cY) {
@@ -222,16 +226,19 @@ template <int N1, int MODE, int ALT>
 __global__ void __launch_bounds__(MAXB3, 3)
 k_stage3p(const __grid_constant__ ModalParams mp, const StageBufs b, double cA, double cY) {
     constexpr int NT = N1 * N1, NA = N1 * N1 * N1, NE = (N1 + 1) / 2;
+    constexpr int EPB = epb3c<N1>(), BD = EPB * NT;   // blockDim.x == BD (launch_stage3)
     extern __shared__ double smem[];
-    const int epb = blockDim.x / NT;
     const int t = threadIdx.x;
     const int le = t / NT, r = t - le * NT;
     const int a = r / N1, c = r - (r / N1) * N1;
-    const int e = blockIdx.x * epb + le;
+    const int e = blockIdx.x * EPB + le;
     const bool valid = e < mp.ne;
-    // [12][NT]: per direction d, at 4d: g-sum, g-difference, q-sum, q-difference
+    // per element [12][NT]: per direction d, at 4d: g-sum, g-difference,
+    // q-sum, q-difference; then the tile tU, tV
     double *F = smem + le * smem3_doubles<N1>();
     double *tU = F + 12 * NT, *tV = tU + NA;
+    double *ce = smem + EPB * smem3_doubles<N1>();   // [3][N1]: c^2 eL / 2 of x, y, z
+    if (t < N1) { ce[t] = mp.d[0].ceL[t]; ce[N1 + t] = mp.d[1].ceL[t]; ce[2 * N1 + t] = mp.d[2].ceL[t]; }
     const int ex = valid ? e % mp.nx : 0, ey = valid ? (e / mp.nx) % mp.ny : 0, ez = valid ? e / (mp.nx * mp.ny) : 0;
 
     if (valid) {   // fluxes of the three face pairs at this thread's transverse mode pair
@@ -261,80 +268,82 @@ k_stage3p(const __grid_constant__ ModalParams mp, const StageBufs b, double cA, 
     }
     __syncthreads();
 
-    double Ru[N1], Rv[N1];
-    // the stage's arrays do not overlap: with restrict the next entry's loads
-    // may be issued before this entry's stores (at most 80 registers: 3
-    // blocks per SM, as shared memory allows)
+    // The update runs over the block's EPB N1^3 consecutive entries in a
+    // coalesced order: thread t takes entries t + s BD (s < N1), so every
+    // warp load and store of the state covers 32 consecutive doubles (one x
+    // line per thread would stride them by N1).  Entry q = (m3 N1 + m2) N1 +
+    // m1 of element le2 finds its line's fluxes in that element's F; each
+    // entry's arithmetic is the same sequence of operations in either order.
+    // The stage's arrays do not overlap: with restrict the next entry's loads
+    // may be issued before this entry's stores.
     const double *__restrict__ pyU = b.yU, *__restrict__ pyV = b.yV;
     double *__restrict__ paU = b.aU, *__restrict__ paV = b.aV, *__restrict__ pnU = b.nU, *__restrict__ pnV = b.nV;
     double *__restrict__ poU = b.oU, *__restrict__ poV = b.oV;
-    if (valid) {
-        const int line = a * N1 + c;
-        const size_t row = ((size_t)e * NT + line) * N1;
-        const double *L0 = b.lam2 + line * N1;
-        const double *P1 = b.lam2 + 2 * NA + line * N1, *P2 = b.lam2 + 3 * NA + line * N1;
-        const double *P3 = b.lam2 + 4 * NA + line * N1;
-        const double GA = F[0 * NT + line], GB = F[1 * NT + line];
-        const double QA = F[2 * NT + line], QB = F[3 * NT + line];
-        const double cey = mp.d[1].ceL[c];
-        const double cez = mp.d[2].ceL[a];
-        const double *FGy = F + (4 + (c < NE ? 0 : 1)) * NT + a * N1;   // at ty = a N1 + k
-        const double *FQy = F + (6 + (c < NE ? 0 : 1)) * NT + a * N1;
-        const double *FGz = F + (8 + (a < NE ? 0 : 1)) * NT + c * N1;   // at tz = c N1 + k
-        const double *FQz = F + (10 + (a < NE ? 0 : 1)) * NT + c * N1;
+    const double *__restrict__ lam = b.lam2;
+    const size_t base = (size_t)blockIdx.x * EPB * NA;
 #pragma unroll
-        for (int k = 0; k < N1; ++k) {
-            const double Yu = pyU[row + k], Yv = pyV[row + k];
-            const double xg = k < NE ? GA : GB, xq = k < NE ? QA : QB;
-            // k_u = V + Lambda^+ r_u with the three rank-one lifts folded into
-            // P1, P2, P3 (hgL / lambda per direction): three FMAs
-            const double ku = fma(P1[k], xg, fma(P2[k], FGy[k], fma(P3[k], FGz[k], Yv)));
-            const double rv = fma(L0[k], Yu, fma(mp.d[0].ceL[k], xq, fma(cey, FQy[k], cez * FQz[k])));
-            const double kv = rv;
-            if (MODE == M_RHS) {
-                poU[row + k] = ku;
-                poV[row + k] = kv;
-            } else if (MODE == M_S1) {   // accumulator k1 + 2 k2 + 2 k3, scaled by dt/6 at stage 4
-                paU[row + k] = ku;
-                paV[row + k] = kv;
-                Ru[k] = fma(cY, ku, Yu);
-                Rv[k] = fma(cY, kv, Yv);
-            } else if (MODE == M_S23) {
-                paU[row + k] = fma(2.0, ku, paU[row + k]);
-                paV[row + k] = fma(2.0, kv, paV[row + k]);
-                Ru[k] = fma(cY, ku, pnU[row + k]);
-                Rv[k] = fma(cY, kv, pnV[row + k]);
-            } else {
-                Ru[k] = fma(cA, paU[row + k] + ku, pnU[row + k]);
-                Rv[k] = fma(cA, paV[row + k] + kv, pnV[row + k]);
-            }
+    for (int s = 0; s < N1; ++s) {
+        const int idx = t + s * BD;
+        const int le2 = idx / NA, q = idx - le2 * NA;
+        if (blockIdx.x * EPB + le2 >= mp.ne) continue;
+        const int line = q / N1, k = q - line * N1;
+        const int m3 = line / N1, m2 = line - m3 * N1;
+        double *F2 = smem + le2 * smem3_doubles<N1>();
+        const size_t g = base + idx;
+        const double Yu = pyU[g], Yv = pyV[g];
+        const double xg = F2[(k < NE ? 0 : 1) * NT + line], xq = F2[(k < NE ? 2 : 3) * NT + line];
+        const double FGy = F2[(4 + (m2 < NE ? 0 : 1)) * NT + m3 * N1 + k];   // at ty = m3 N1 + m1
+        const double FQy = F2[(6 + (m2 < NE ? 0 : 1)) * NT + m3 * N1 + k];
+        const double FGz = F2[(8 + (m3 < NE ? 0 : 1)) * NT + m2 * N1 + k];   // at tz = m2 N1 + m1
+        const double FQz = F2[(10 + (m3 < NE ? 0 : 1)) * NT + m2 * N1 + k];
+        // k_u = V + Lambda^+ r_u with the three rank-one lifts folded into
+        // rows 2-4 of lam2 (hgL / lambda per direction): three FMAs
+        const double ku = fma(lam[2 * NA + q], xg, fma(lam[3 * NA + q], FGy, fma(lam[4 * NA + q], FGz, Yv)));
+        const double rv = fma(lam[q], Yu, fma(ce[k], xq, fma(ce[N1 + m2], FQy, ce[2 * N1 + m3] * FQz)));
+        const double kv = rv;
+        double Ru, Rv;
+        if (MODE == M_RHS) {
+            poU[g] = ku;
+            poV[g] = kv;
+            continue;
+        } else if (MODE == M_S1) {   // accumulator k1 + 2 k2 + 2 k3, scaled by dt/6 at stage 4
+            paU[g] = ku;
+            paV[g] = kv;
+            Ru = fma(cY, ku, Yu);
+            Rv = fma(cY, kv, Yv);
+        } else if (MODE == M_S23) {
+            paU[g] = fma(2.0, ku, paU[g]);
+            paV[g] = fma(2.0, kv, paV[g]);
+            Ru = fma(cY, ku, pnU[g]);
+            Rv = fma(cY, kv, pnV[g]);
+        } else {
+            Ru = fma(cA, paU[g] + ku, pnU[g]);
+            Rv = fma(cA, paV[g] + kv, pnV[g]);
         }
-        if (MODE != M_RHS) {
-            double *dU = (MODE == M_S4) ? pnU : poU;
-            double *dV = (MODE == M_S4) ? pnV : poV;
-#pragma unroll
-            for (int k = 0; k < N1; ++k) { dU[row + k] = Ru[k]; dV[row + k] = Rv[k]; }
-        }
+        if (MODE == M_S4) { pnU[g] = Ru; pnV[g] = Rv; }
+        else { poU[g] = Ru; poV[g] = Rv; }
+        double *tU2 = F2 + 12 * NT;
+        tU2[q] = Ru;
+        tU2[NA + q] = Rv;
     }
     if (MODE == M_RHS) return;   // uniform across the block
+    __syncthreads();
 
-    if (valid) {   // x faces from the line; the tile for the y and z faces
+    if (valid) {   // x faces from this thread's line; the tile for the y and z faces
         const int line = a * N1 + c;
         double ve = 0, vo = 0, de = 0, dd = 0;
 #pragma unroll
         for (int k = 0; k < N1; ++k) {
-            if (k < NE) { ve = fma(mp.d[0].eL[k], Rv[k], ve); de = fma(mp.d[0].gL[k], Ru[k], de); }
-            else { vo = fma(mp.d[0].eL[k], Rv[k], vo); dd = fma(mp.d[0].gL[k], Ru[k], dd); }
-            tU[line * N1 + k] = Ru[k];
-            tV[line * N1 + k] = Rv[k];
+            const double u = tU[line * N1 + k], v = tV[line * N1 + k];
+            if (k < NE) { ve = fma(mp.d[0].eL[k], v, ve); de = fma(mp.d[0].gL[k], u, de); }
+            else { vo = fma(mp.d[0].eL[k], v, vo); dd = fma(mp.d[0].gL[k], u, dd); }
         }
         b.trout[tix3<N1>(e, 0, 0, line)] = ve + vo;
         b.trout[tix3<N1>(e, 0, 1, line)] = de + dd;
         b.trout[tix3<N1>(e, 1, 0, line)] = ve - vo;
         b.trout[tix3<N1>(e, 1, 1, line)] = de - dd;
+        traces3_yz_p<N1>(mp, tU, tV, e, a, c, b.trout);
     }
-    __syncthreads();
-    if (valid) traces3_yz_p<N1>(mp, tU, tV, e, a, c, b.trout);
 }
 
 // traces of a modal state (start of gdg_step and gdg_rhs)
@@ -515,7 +524,8 @@ __global__ void k_energy_partial3(int ne, const double *yU, const double *yV, co
 #define GDG_N1_CASES3(X) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10)
 
 int epb3(int n1) { return std::max(1, MAXB3 / (n1 * n1)); }
-size_t smem_stage3(int n1) { return (size_t)epb3(n1) * (12 * n1 * n1 + 2 * n1 * n1 * n1) * sizeof(double); }
+// per element the fluxes and the tile; per block the parity kernel's c^2 eL / 2 table
+size_t smem_stage3(int n1) { return ((size_t)epb3(n1) * (12 * n1 * n1 + 2 * n1 * n1 * n1) + 3 * n1) * sizeof(double); }
 size_t smem_traces3(int n1) { return (size_t)epb3(n1) * 2 * n1 * n1 * n1 * sizeof(double); }
 size_t smem_sep3(int n1) { return (size_t)(6 * n1 * n1 + epb3(n1) * n1 * n1 * n1) * sizeof(double); }
 

@@ -1,0 +1,86 @@
+"""Convergence of the CUDA path to exact solutions (Section 6): the error of
+a standing wave falls at the optimal rate p + 1 as the elements are refined
+at fixed N, on meshes beyond those the oracle steps in seconds.  The pins are
+the closed-form solutions alone:
+
+    1-D  u = cos(2 pi t) sin(2 pi x), N + 1 = 11 (the setting of Table 2)
+    2-D  u = cos(sqrt2 pi t) sin(pi x) sin(pi y), N = 8 (that of Table 4)
+    3-D  u = cos(sqrt3 pi t) sin(pi x) sin(pi y) sin(pi z), N = 4
+
+with the upwind flux, Dirichlet sides, RK4 to T = 1/4 at dt = cfl h (cfl
+0.05; 0.02 at p = 5, so that the time error stays far below the finest
+spatial error).  The error is the RMS over the nodes.  Each rate between
+consecutive meshes must exceed p + 0.5.  Measured on a GB300 (rates between
+consecutive meshes): 1-D p = 3 4.31, 3.89, 3.71; 1-D p = 5 6.65, 5.95, 6.45;
+2-D p = 3 3.99, 3.93, 4.10; 2-D p = 5 6.26, 5.98; 3-D p = 3 4.94, 3.67.  The
+oracle, run on the same meshes up to 16 elements a side (4 in 3-D), prints
+the same errors to four digits, except at 2-D p = 5 on 16 x 16 elements:
+8.00e-13 against 8.23e-13, an error so small that rounding over the 1,600
+steps shows.  The
+central and alternating fluxes also converge, but at rates that swing from
+one refinement to the next (the oracle, 2-D central p = 5: 4.5 then 9.1), so
+they are left to the parity tests."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2105_01722_gb300 import gdg, inputs
+
+T = 0.25
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    gdg.lib()
+
+
+def _dev(a):
+    return torch.tensor(np.ascontiguousarray(a).ravel(), dtype=torch.float64, device="cuda")
+
+
+def _error(dim, n, N, p, cfl):
+    """RMS nodal error at T of the standing wave on n^dim elements."""
+    if dim == 1:
+        (X,) = inputs.cartesian_nodes((n,), N)
+        U0, _ = inputs.standing_wave_1d(X)
+        Ue, _ = inputs.standing_wave_1d(X, T)
+        pb = gdg.make_problem(1, (n,), N, p, flux=gdg.FLUX_UPWIND, c2=1.0)
+    elif dim == 2:
+        X, Y = inputs.cartesian_nodes((n, n), N)
+        U0, _ = inputs.standing_mode_2d(X, Y)
+        Ue, _ = inputs.standing_mode_2d(X, Y, T)
+        pb = gdg.make_problem(2, (n, n), N, p, flux=gdg.FLUX_UPWIND, c2=1.0)
+    else:
+        X, Y, Z = inputs.cartesian_nodes_3d((n, n, n), N)
+        s = np.sin(np.pi * X) * np.sin(np.pi * Y) * np.sin(np.pi * Z)
+        U0, Ue = s, np.cos(np.sqrt(3.0) * np.pi * T) * s
+        pb = gdg.make_problem(3, (n, n, n), N, p, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0),
+                              bc=(gdg.BC_DIRICHLET,) * 3, flux=gdg.FLUX_UPWIND, c2=1.0)
+    h = 1.0 / (n * N)
+    steps = int(np.ceil(T / (cfl * h)))
+    ctx = gdg.Context(pb)
+    u = _dev(U0)
+    v = torch.zeros_like(u)
+    ctx.step(u, v, 0.0, T / steps, steps)
+    err = float(np.sqrt(np.mean((u.cpu().numpy() - np.ravel(Ue)) ** 2)))
+    ctx.close()
+    return err
+
+
+@pytest.mark.parametrize("dim,N,p,ns", [
+    (1, 10, 3, (4, 8, 16, 32)),
+    (1, 10, 5, (2, 4, 8, 16)),
+    (2, 8, 3, (4, 8, 16, 32)),
+    (2, 8, 5, (4, 8, 16)),
+    (3, 4, 3, (2, 4, 8)),
+], ids=lambda x: str(x).replace(" ", ""))
+def test_optimal_rate_under_refinement(dim, N, p, ns):
+    cfl = 0.02 if p == 5 else 0.05
+    errs = np.array([_error(dim, n, N, p, cfl) for n in ns])
+    rates = np.log2(errs[:-1] / errs[1:])
+    assert np.all(errs > 0) and np.all(np.isfinite(errs)), errs
+    assert rates.min() > p + 0.5, (errs, rates)

@@ -204,3 +204,25 @@ def test_ic0_pcg_iterations_table5(N):
         ru, rv = dv.residuals(vp10, ops10, U, V)
         _, _, iu10, _ = dv.solve_pcg(vp10, ops10, V, ru, rv, precond="ic0", rtol=gold[0, 2], maxit=50)
         assert iu.mean() > iu10.mean()
+
+
+@pytest.mark.parametrize("amp", [0.0, 0.05])
+def test_l2_error_norm_on_mapped_elements(amp):
+    """dg_var.l2_error, the error measure of the mapped tests: with a zero
+    discrete state it is ||sin(pi x) sin(pi y)|| = 1/2 over the unit square.
+    The interpolated sine map still maps the reference square onto the unit
+    square (its boundary nodes lie on the boundary, and so does their
+    interpolant), so the change of variables is exact and only quadrature
+    rounding remains; a wrong Jacobian determinant or mapped point breaks
+    it.  On the Cartesian mesh a polynomial of degree <= p (not symmetric in
+    x and y) has zero error."""
+    for n, N, p in ((2, 6, 3), (3, 8, 5)):
+        X, Y = inputs.mapped_nodes((n, n), N, amp)
+        vp = dv.VarProblem(n=(n, n), N=N, p=p, X=X, Y=Y, C2=np.ones_like(X))
+        Z = np.zeros((n * n, (N + 1) ** 2))
+        l2 = dv.l2_error(vp, Z, lambda x, y: np.sin(np.pi * x) * np.sin(np.pi * y))
+        assert abs(l2 - 0.5) < 1e-14, (n, N, p, l2)
+        if amp == 0.0:
+            P = lambda x, y: x ** p * y - 0.5 * y ** 2 + x
+            assert dv.l2_error(vp, P(X, Y).reshape(n * n, -1), P) < 1e-14
+            assert dv.l2_error(vp, P(Y, X).reshape(n * n, -1), P) > 1e-2

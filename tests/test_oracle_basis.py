@@ -161,3 +161,29 @@ def test_low_eigenvalues_are_neumann_laplacian():
         assert abs(lam[1] - np.pi ** 2) / np.pi ** 2 < 1e-3
     assert errs[0] > errs[1] > errs[2]
     assert errs[1] / errs[2] > 8.0            # at least third order
+
+
+@pytest.mark.parametrize("p,N,nq", [(3, 5, None), (5, 8, 8), (1, 3, 2)])
+def test_composite_quadrature_is_exact_cell_by_cell(p, N, nq):
+    """quadrature_points: nq Gauss points in every cell (p + 1 by default),
+    each point inside the cell it is tagged with, weights summing to 1, and
+    exact for any function that is a polynomial of degree <= 2 nq - 1 on each
+    cell, kinks at the cell ends included; on degree 2 nq it misses by the
+    Gauss remainder."""
+    q = p + 1 if nq is None else nq
+    r, w, cell = gb.quadrature_points(p, N, nq)
+    assert r.shape == w.shape == cell.shape == (N * q,)
+    assert np.array_equal(cell, np.floor(r * N).astype(int)) and np.all(w > 0)
+    assert abs(w.sum() - 1.0) < 1e-14
+    h = 1.0 / N
+    d = 2 * q - 1
+    left = cell * h
+    f = (r - left) ** d * (1.0 + cell)            # a different polynomial on each cell
+    exact = sum((1.0 + k) * h ** (d + 1) / (d + 1) for k in range(N))
+    assert abs(np.dot(w, f) - exact) < 1e-14 * max(1.0, exact) + 1e-16
+    # degree 2 nq: the Gauss remainder, h^(2n+1) (n!)^4 / ((2n+1) ((2n)!)^2) per
+    # cell for x^(2n), n = nq (exact minus rule; the rule falls short)
+    from math import factorial
+    g = (r - left) ** (d + 1)
+    rem = N * h ** (d + 2) * factorial(q) ** 4 / ((d + 2) * factorial(d + 1) ** 2)
+    assert abs((N * h ** (d + 2) / (d + 2) - np.dot(w, g)) / rem - 1.0) < 1e-6

@@ -71,9 +71,9 @@ enum { GDG_COEF_CONST = 0, GDG_COEF_NODAL = 1 };
  * GDG_MIXED); gdg_pcg still runs PCG on such a context. */
 enum { GDG_SOLVE_DIAG = 0, GDG_SOLVE_PCG = 1, GDG_SOLVE_INVERSE = 2 };
 /* PCG preconditioner: frozen-coefficient diagonalisation, none (plain CG),
- * or the zero fill-in incomplete Cholesky factors of Section 7.1, which this
- * build does not run on the GPU (their triangular solves are sequential per
- * element; gdg_create returns GDG_EUNSUPPORTED; the FP64 oracle has them). */
+ * or the zero fill-in incomplete Cholesky factors of Section 7.1, which the
+ * library does not run on the GPU (their triangular solves are sequential per
+ * element; gdg_create returns GDG_EUNSUPPORTED). */
 enum { GDG_PC_FDM = 0, GDG_PC_NONE = 1, GDG_PC_IC0 = 2 };
 /* Arithmetic of the element solves.  GDG_FP64 everywhere, or (GDG_SOLVE_PCG
  * only) FP32 inner PCG with FP64 iterative refinement of every solve (FP64

@@ -70,8 +70,9 @@ ALG_FLOPS_PER_DOF_STAGE = 40.0
 
 
 def hbm_peak_gbs():
-    """Measured HBM copy bandwidth (generated MEASURED_PEAKS.json), else
-    the profiling recipe's fallback."""
+    """Measured HBM copy bandwidth (MEASURED_PEAKS.json at the repository
+    root, a STREAM-style copy measured on this GPU model), else 6.8 TB/s, one
+    earlier copy measurement on a GB300."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"

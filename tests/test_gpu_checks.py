@@ -1,5 +1,5 @@
-"""The index-checking build (GDG_CHECKS, gdg_checks.cuh): built on the GPU machine,
-then every form runs on small cases in a child process that loads it; no
+"""The index-checking build (GDG_CHECKS, gdg_checks.cuh): built by the test
+on the machine that runs it, then every form runs on small cases in a child process that loads it; no
 element index a kernel derives (face neighbours, neighbour blocks, batched
 work items) leaves its range, and the recording path itself works (a
 self-test pair that fails records site 99 with its index and bound)."""

@@ -194,3 +194,78 @@ def test_energy_of_interpolants_converges_to_the_continuous_energy(p, rate, floo
         gaps.append(abs(dv.energy(dv.assemble(vp), u(X, Y), v(X, Y)) - Ec) / Ec)
     rates = np.log2(np.array(gaps[:-1]) / np.array(gaps[1:]))
     assert rates.min() > rate and gaps[-1] < floor, (gaps, rates)
+
+
+def _face_rate_cartesian(vp, U, V, Hx, Hy):
+    """Independent restatement, on a Cartesian mesh with variable c^2, of the
+    energy rate of the upwind flux (Section 2.2.1 with the coefficient under
+    the face integrals):
+        dE/dt = - sum_interior int c^2 (tau [v]^2 + beta [d_n u]^2) dS
+                - sum_Dirichlet int 2 c^2 tau v^2 dS,
+    xi = c at the face point (or the problem's fixed xi), beta = xi / 2,
+    tau = 1 / (2 xi); traces from the 1-D face data, c^2 traced from the
+    face nodes, the face rule p + 1 Gauss points per GD cell."""
+    from oracle import gd_basis as gb
+    p, N, n1 = vp.p, vp.N, vp.n1
+    r, w, cell = gb.quadrature_points(p, N, p + 1)
+    B, _ = gb.basis_at_points(p, N, r, cell)
+    _, _, dL, dR = gb.face_data(p, N)
+    nx, ny = vp.n
+    U = U.reshape(ny, nx, n1, n1)
+    V = V.reshape(ny, nx, n1, n1)
+    C2 = vp.C2.reshape(ny, nx, n1, n1)
+
+    def pen(c2, jv, jd, length):
+        xi = np.full_like(c2, vp.xi) if vp.xi > 0 else np.sqrt(c2)
+        return length * np.sum(w * c2 * (jv ** 2 / (2 * xi) + 0.5 * xi * jd ** 2))
+
+    rate = 0.0
+    for ey in range(ny):
+        for ex in range(nx):
+            # x faces (j along the face, i = N on the + face, 0 on the - face)
+            if ex + 1 < nx or vp.periodic[0]:
+                f = (ex + 1) % nx
+                jv = B @ (V[ey, ex][:, -1] - V[ey, f][:, 0])
+                jd = B @ (U[ey, ex] @ dR - U[ey, f] @ dL) / Hx
+                rate -= pen(B @ C2[ey, ex][:, -1], jv, jd, Hy)
+            else:
+                rate -= 2 * pen(B @ C2[ey, ex][:, -1], B @ V[ey, ex][:, -1], 0.0, Hy)
+            if ex == 0 and not vp.periodic[0]:
+                rate -= 2 * pen(B @ C2[ey, 0][:, 0], B @ V[ey, 0][:, 0], 0.0, Hy)
+            # y faces (i along the face)
+            if ey + 1 < ny or vp.periodic[1]:
+                f = (ey + 1) % ny
+                jv = B @ (V[ey, ex][-1, :] - V[f, ex][0, :])
+                jd = B @ (dR @ U[ey, ex] - dL @ U[f, ex]) / Hy
+                rate -= pen(B @ C2[ey, ex][-1, :], jv, jd, Hx)
+            else:
+                rate -= 2 * pen(B @ C2[ey, ex][-1, :], B @ V[ey, ex][-1, :], 0.0, Hx)
+            if ey == 0 and not vp.periodic[1]:
+                rate -= 2 * pen(B @ C2[0, ex][0, :], B @ V[0, ex][0, :], 0.0, Hx)
+    return rate
+
+
+@pytest.mark.parametrize("periodic", [(False, False), (True, False), (False, True)])
+@pytest.mark.parametrize("xi", [0.0, 0.8])
+def test_upwind_energy_rate_identity_variable_c2(periodic, xi):
+    """dE/dt of the variable-coefficient oracle equals minus the flux
+    penalties on the face jumps, with c^2 varying along every face and xi
+    the local c (xi = 0) or fixed.  The energy identities above only bound
+    the sign; this fixes where c^2 and xi enter the dissipative terms."""
+    n, N, p = (3, 2), 5, 3
+    lo, hi = (0.1, -0.3), (1.1, 0.7)     # unit periods: c^2 (period 1) is continuous across a periodic seam
+    from oracle import dg_const as dcx
+    prob = dcx.Problem(dim=2, n=n, N=N, p=p, lo=lo, hi=hi)
+    X, Y = dcx.node_coordinates(prob)
+    C2 = inputs.smooth_random_c2(X, Y, seed=11)
+    vp = dv.VarProblem(n=n, N=N, p=p, X=X, Y=Y, C2=C2, flux="upwind", periodic=periodic, xi=xi)
+    ops = dv.assemble(vp)
+    rng = np.random.default_rng(3)
+    ne = n[0] * n[1]
+    U = rng.standard_normal((ne, (N + 1) ** 2))
+    V = rng.standard_normal((ne, (N + 1) ** 2))
+    Ut, Vt = dv.time_derivative(vp, ops, U, V)
+    dEdt = np.einsum("ea,eab,eb->", V, ops.M, Vt) + np.einsum("ea,eab,eb->", U, ops.S, Ut)
+    expect = _face_rate_cartesian(vp, U, V, (hi[0] - lo[0]) / n[0], (hi[1] - lo[1]) / n[1])
+    assert expect < 0.0
+    assert abs(dEdt - expect) < 1e-10 * abs(expect), (dEdt, expect)

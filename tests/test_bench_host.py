@@ -89,3 +89,32 @@ def test_coarse_nodes_are_fine_nodes(n, N):
                 for x, y in zip(inputs.cartesian_nodes((2 * n, 2 * n), N)[0].ravel()[idx],
                                 inputs.cartesian_nodes((2 * n, 2 * n), N)[1].ravel()[idx])}
     assert pts == fine_pts
+
+
+def test_reference_arm_json_line(monkeypatch, capsys):
+    """--impl reference prints one JSON line with the contract's keys; its
+    value is DOF x RK4 steps / seconds over the timed samples only."""
+    import argparse
+    import json
+    monkeypatch.setattr(bench, "_oracle_steps", lambda n, target, threads: ([(3, 1.5)] * 2 + [(4, 1.0)] * (n - 2), None))
+    monkeypatch.setattr(bench, "_env_rank", lambda: (0, 1, 0))
+    args = argparse.Namespace(steps=3, warmup=2, gpus=1)
+    assert bench.run_reference(args) == 0
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in line, k
+    assert line["impl"] == "reference" and line["metric"] == "DOF-steps/s" and line["steps"] == 3
+    assert line["value"] == pytest.approx(bench.dof() * 12 / 3.0)     # the 3 timed samples: 4 steps / 1 s each
+    assert line["ms_per_step"] == pytest.approx(1000.0)
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"
+    # other ranks print nothing
+    monkeypatch.setattr(bench, "_env_rank", lambda: (1, 2, 1))
+    assert bench.run_reference(args) == 0 and capsys.readouterr().out == ""
+
+
+def test_oracle_timer_runs_on_the_host():
+    """The oracle timer subprocess steps the full headline mesh at least once
+    per sample and reports positive times."""
+    rows, err = bench._oracle_steps(1, 0.05, 1)
+    assert err is None and len(rows) == 1 and rows[0][0] >= 1 and rows[0][1] > 0

@@ -118,3 +118,31 @@ def test_oracle_timer_runs_on_the_host():
     per sample and reports positive times."""
     rows, err = bench._oracle_steps(1, 0.05, 1)
     assert err is None and len(rows) == 1 and rows[0][0] >= 1 and rows[0][1] > 0
+
+
+def test_clock_sampler_parses_nvidia_smi_rows():
+    """The clocks record of the bench line: median SM clock under load, the
+    maximum clock, and every throttle reason seen active; malformed rows are
+    skipped, and a missing nvidia-smi is reported, not raised."""
+    import tempfile
+
+    class FakeProc:
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            return 0
+
+    s = bench.ClockSampler(0)
+    s.proc = FakeProc()
+    s.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+    s.f.write("0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active\n"
+              "0, 1980, 2070, 1390.5, 0x4, Not Active, Not Active, Not Active, Active\n"
+              "0, 2055, 2070, 1200.0, 0x0, Not Active, Not Active, Not Active, Not Active\n"
+              "0, [N/A], 2070, 10.0, 0x0, Not Active, Not Active, Not Active, Not Active\n"
+              "garbage line\n")
+    rec = s.stop()
+    assert rec["sm_mhz"] == 2055.0 and rec["sm_max_mhz"] == 2070.0 and rec["samples"] == 3
+    assert rec["reasons"] == ["sw_power_cap"]
+    s2 = bench.ClockSampler(0)
+    assert s2.stop()["reasons"] == ["nvidia-smi unavailable"]
